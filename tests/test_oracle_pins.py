@@ -1,0 +1,457 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these tests re-types an oracle formula: each compares the oracle with
+an independent statement (a Kronecker-assembled operator, a sine-transform
+solve built from its definition, closed-form weights derived by hand, exact
+lattice point counts, discretisation-error rates, or the convergence factors
+printed in the paper's Tables 1-3).
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.sparse.linalg import LinearOperator, eigs
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# independent operator assembly (definition of the discrete operators)
+# --------------------------------------------------------------------------
+
+def _d1(n):
+    """1D second difference from a full line of n+2 values to its n interior points."""
+    D = np.zeros((n, n + 2))
+    for i in range(n):
+        D[i, i], D[i, i + 1], D[i, i + 2] = 1.0, -2.0, 1.0
+    return D
+
+
+def _s1(n):
+    S = np.zeros((n, n + 2))
+    for i in range(n):
+        S[i, i + 1] = 1.0
+    return S
+
+
+def _kron(*ms):
+    out = ms[0]
+    for m in ms[1:]:
+        out = np.kron(out, m)
+    return out
+
+
+def operators(dim, n, order):
+    """(L, M) acting on flattened full grids (C order, x fastest) -> interior.
+
+    order 2: L = sum of 1D second differences / h^2, M = selection.
+    order 4 (Mehrstellen / 19-point): L = Lap + (h^2/6) sum_{a<b} d_a d_b / h^4,
+    M = S + (1/12) sum_a d_a  -- the standard compact fourth-order schemes."""
+    h = 1.0 / (n + 1)
+    D, S = _d1(n), _s1(n)
+
+    def along(axis_ops):
+        # axis_ops[a] applies on axis a (a=0 is x); kron order is (z, y, x)
+        return _kron(*[axis_ops[a] for a in reversed(range(dim))])
+
+    lap = sum(along([D if a == b else S for a in range(dim)]) for b in range(dim)) / h**2
+    sel = along([S] * dim)
+    if order == 2:
+        return lap, sel
+    cross = sum(along([D if a in (b, c) else S for a in range(dim)])
+                for b in range(dim) for c in range(b + 1, dim))
+    L = lap + cross / (6.0 * h**2)
+    M = sel + sum(along([D if a == b else S for a in range(dim)]) for b in range(dim)) / 12.0
+    return L, M
+
+
+def interior(x):
+    return x[(slice(1, -1),) * x.ndim]
+
+
+def rng_grid(dim, n, seed, ring=False):
+    g = np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n + 2,) * dim)
+    if not ring:
+        m = np.zeros_like(g)
+        m[(slice(1, -1),) * dim] = 1.0
+        g = g * m
+    return np.ascontiguousarray(g)
+
+
+# --------------------------------------------------------------------------
+# residuals: Eq. Evpois (5/7-point), Eq. Efos2, Eq. Efos4
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,n", [(2, 7), (2, 15), (3, 7)])
+@pytest.mark.parametrize("order", [2, 4])
+def test_residual_matches_kronecker_operators(dim, n, order):
+    f = rng_grid(dim, n, 1, ring=True)   # order 4 reads f on the ring
+    u = rng_grid(dim, n, 2, ring=False)  # homogeneous Dirichlet ring
+    L, M = operators(dim, n, order)
+    want = M @ f.ravel() - L @ u.ravel()
+    got = interior(O.residual(f, u, order)).ravel()
+    scale = np.abs(L).max()
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * scale)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 15), (3, 7)])
+@pytest.mark.parametrize("order", [2, 4])
+def test_operator_symmetry(dim, n, order):
+    """L (the residual with f = 0, negated) is symmetric under Dirichlet BC."""
+    x = rng_grid(dim, n, 3)
+    y = rng_grid(dim, n, 4)
+    zero = O.grid(dim, n)
+    Lx = -O.residual(zero, x, order)
+    Ly = -O.residual(zero, y, order)
+    a, b = float((Lx * y).sum()), float((x * Ly).sum())
+    assert abs(a - b) <= 1e-12 * max(abs(a), 1.0) * (n + 1) ** 2
+
+
+# --------------------------------------------------------------------------
+# coarsest solve against the sine transform (eigenvectors of the 5/7-point
+# operator, written from their definition)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,n", [(2, 1), (2, 3), (2, 7), (3, 1), (3, 3)])
+def test_coarse_solve_matches_sine_transform(dim, n):
+    H = 0.125
+    r = rng_grid(dim, n, 5)
+    k = np.arange(1, n + 1)
+    S = np.sin(np.outer(k, k) * math.pi / (n + 1)) * math.sqrt(2.0 / (n + 1))  # orthonormal DST-I
+    lam1 = -4.0 / H**2 * np.sin(k * math.pi / (2 * (n + 1))) ** 2
+    rin = interior(r)
+    # transform along every axis
+    rh = rin
+    for ax in range(dim):
+        rh = np.moveaxis(np.tensordot(S, np.moveaxis(rh, ax, 0), axes=(1, 0)), 0, ax)
+    lam = sum(np.meshgrid(*([lam1] * dim), indexing="ij"))
+    vh = rh / lam
+    v = vh
+    for ax in range(dim):
+        v = np.moveaxis(np.tensordot(S, np.moveaxis(v, ax, 0), axes=(1, 0)), 0, ax)
+    got = interior(O.coarse_solve(r, H))
+    np.testing.assert_allclose(got, v, rtol=1e-12, atol=1e-14 * np.abs(v).max())
+
+
+# --------------------------------------------------------------------------
+# fixed point of every variant = the discrete solution (direct solve)
+# --------------------------------------------------------------------------
+
+CASES_FP = [
+    (2, 15, O.DIAG, 2, [1.052]), (2, 15, O.USUAL, 2, [1.121]),
+    (2, 15, O.DIAG, 4, [1.2]), (2, 15, O.USUAL, 4, [1.216]),
+    (3, 7, O.DIAG, 2, [1.11, 1.42, 1.08, 0.99]), (3, 7, O.USUAL, 2, [1.3]),
+    (3, 7, O.DIAG, 4, [0.91, 0.80, 0.70, 1.77]), (3, 7, O.USUAL, 4, [1.7]),
+]
+
+
+@pytest.mark.parametrize("dim,n,hier,order,omega", CASES_FP)
+def test_fixed_point_is_direct_solution(dim, n, hier, order, omega):
+    f = rng_grid(dim, n, 6, ring=True)
+    L, M = operators(dim, n, order)
+    sel = (_kron(*([_s1(n)] * dim)))
+    A = L @ sel.T  # acts on interior values
+    want = np.linalg.solve(A, M @ f.ravel())
+    u, it, rel, _ = O.solve(f, hier=hier, order=order, omega=omega, rtol=1e-14, max_cycles=200)
+    assert rel <= 1e-13, (it, rel)
+    np.testing.assert_allclose(interior(u).ravel(), want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+# --------------------------------------------------------------------------
+# discretisation error: O(h^2) for 5/7-point, O(h^4) for Efos2 / Efos4
+# --------------------------------------------------------------------------
+
+def manufactured(dim, n):
+    x = np.linspace(0.0, 1.0, n + 2)
+    if dim == 2:
+        Y, X = np.meshgrid(x, x, indexing="ij")
+        u = np.sin(math.pi * X) * np.sin(2 * math.pi * Y)
+        f = -5 * math.pi**2 * u
+    else:
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        u = np.sin(math.pi * X) * np.sin(math.pi * Y) * np.sin(2 * math.pi * Z)
+        f = -6 * math.pi**2 * u
+    return np.ascontiguousarray(f), np.ascontiguousarray(u)
+
+
+@pytest.mark.parametrize("dim,sizes", [(2, (15, 31, 63)), (3, (7, 15, 31))])
+@pytest.mark.parametrize("order", [2, 4])
+def test_discretisation_order(dim, sizes, order):
+    errs = []
+    for n in sizes:
+        f, ue = manufactured(dim, n)
+        om = [1.0] if dim == 2 else [1.0] * 4
+        u, it, rel, _ = O.solve(f, order=order, omega=om, rtol=1e-13, max_cycles=200)
+        assert rel <= 1e-13
+        errs.append(np.abs(interior(u) - interior(ue)).max())
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert abs(rates[-1] - order) < 0.15 and all(abs(r - order) < 0.3 for r in rates), (errs, rates)
+
+
+# --------------------------------------------------------------------------
+# restriction stencils: closed-form composite weights
+# --------------------------------------------------------------------------
+
+def test_composite_17_point_restriction_2d():
+    """green -> red -> blue composes to a 17-point stencil (Section 2.1):
+    centre 1/4, axis 3/32, diagonal 1/16, knight moves 1/64, nothing else."""
+    n = 15
+    want = {(0, 0): 1 / 4, (1, 0): 3 / 32, (1, 1): 1 / 16, (2, 1): 1 / 64}
+    a, b = 4, 4  # blue point (8, 8)
+    for dj in range(-3, 4):
+        for di in range(-3, 4):
+            rg = O.grid(2, n)
+            rg[8 + dj, 8 + di] = 1.0
+            rb = O.restrict2d_r2b(O.restrict2d_g2r(rg))
+            key = tuple(sorted((abs(di), abs(dj)), reverse=True))
+            w = want.get(key, 0.0)
+            assert rb[b, a] == pytest.approx(w, abs=1e-15), (di, dj)
+    # weights sum to one: a constant is reproduced away from the boundary
+    rb = O.restrict2d_r2b(O.restrict2d_g2r(np.ones((n + 2, n + 2))))
+    assert rb[4, 4] == pytest.approx(1.0, abs=1e-15)
+
+
+def test_composite_restriction_3d():
+    """green -> red -> magenta -> blue (Eq. Erred, Ermagc, Ermagm, Erblu):
+    by hand the centre weight is 1/2*1/2*1/2 = 1/8 and an axis neighbour's is
+    1/48 (via the red corner) + 1/144 (via four red faces and the magenta
+    corner) + 1/144 (via four red faces and eight magenta centres) = 5/144;
+    the stencil is cubically symmetric and sums to one."""
+    n = 15
+    c = 8
+    W = np.zeros((7, 7, 7))
+    for dk in range(-3, 4):
+        for dj in range(-3, 4):
+            for di in range(-3, 4):
+                rg = O.grid(3, n)
+                rg[c + dk, c + dj, c + di] = 1.0
+                rb = O.restrict3d_m2b(O.restrict3d_r2m(O.restrict3d_g2r(rg)))
+                W[dk + 3, dj + 3, di + 3] = rb[4, 4, 4]
+    assert W[3, 3, 3] == pytest.approx(1 / 8, abs=1e-15)
+    assert W[3, 3, 4] == pytest.approx(5 / 144, abs=1e-15)
+    assert W.sum() == pytest.approx(1.0, abs=1e-14)
+    for perm in [(0, 2, 1), (1, 0, 2), (2, 1, 0)]:
+        np.testing.assert_allclose(W, np.transpose(W, perm), atol=1e-16)
+    np.testing.assert_allclose(W, W[::-1], atol=1e-16)
+
+
+def test_single_step_weights_sum_to_one():
+    n = 15
+    one2, one3 = np.ones((n + 2,) * 2), np.ones((n + 2,) * 3)
+    assert O.restrict2d_g2r(one2)[8, 8] == pytest.approx(1.0)
+    assert O.restrict2d_r2b(one2)[4, 4] == pytest.approx(1.0)
+    assert O.restrict3d_g2r(one3)[8, 8, 8] == pytest.approx(1.0)
+    rm = O.restrict3d_r2m(one3)
+    assert rm[8, 8, 8] == pytest.approx(1.0) and rm[7, 7, 7] == pytest.approx(1.0)
+    assert O.restrict3d_m2b(one3)[4, 4, 4] == pytest.approx(1.0)
+    assert O.restrict_fw(one2)[4, 4] == pytest.approx(1.0)
+    assert O.restrict_fw(one3)[4, 4, 4] == pytest.approx(1.0)
+
+
+# --------------------------------------------------------------------------
+# Jacobi sweeps at p = 1 reproduce quadratics exactly (r = Laplacian of q):
+# this fixes each sweep's weights and its h^2 coefficient (sqrt(2)h on the
+# 2D diagonal grid, FCC/BCC spacings in 3D).
+# --------------------------------------------------------------------------
+
+def _quad(dim, n, h, coeffs):
+    x = np.arange(n + 2) * h
+    if dim == 2:
+        Y, X = np.meshgrid(x, x, indexing="ij")
+        q = coeffs[0] * X * X + coeffs[1] * Y * Y + coeffs[2] * X * Y + coeffs[3] * X + 0.3
+        lap = 2 * coeffs[0] + 2 * coeffs[1]
+    else:
+        Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+        q = (coeffs[0] * X * X + coeffs[1] * Y * Y + coeffs[4] * Z * Z + coeffs[2] * X * Y
+             + coeffs[5] * Y * Z + coeffs[6] * X * Z + coeffs[3] * X + 0.3)
+        lap = 2 * (coeffs[0] + coeffs[1] + coeffs[4])
+    return np.ascontiguousarray(q), np.full_like(q, lap)
+
+
+QUADS = [(1, 0, 0, 0, 0, 0, 0), (0, 1, 0, 0, 0, 0, 0), (0, 0, 1, 0, 0, 0, 0), (0, 0, 0, 0, 1, 0, 0),
+         (0, 0, 0, 0, 0, 1, 0), (0, 0, 0, 0, 0, 0, 1), (0.7, -0.4, 0.9, 1.3, 0.2, -0.5, 0.8)]
+
+
+def _coarse(q):
+    sl = tuple(slice(None, None, 2) for _ in range(q.ndim))
+    return np.ascontiguousarray(q[sl])
+
+
+@pytest.mark.parametrize("coeffs", QUADS)
+def test_jacobi_sweeps_exact_on_quadratics(coeffs):
+    n, h = 15, 1.0 / 16
+    # 2D
+    q, lap = _quad(2, n, h, coeffs)
+    out = np.full_like(q, 9.0)
+    out[0, :], out[-1, :], out[:, 0], out[:, -1] = q[0, :], q[-1, :], q[:, 0], q[:, -1]
+    vr = O.prolong2d_b2r(_coarse(q), lap, h, 1.0, out=out.copy())
+    red = (np.add.outer(np.arange(n + 2), np.arange(n + 2)) % 2 == 0)
+    m = red.copy()
+    m[0, :] = m[-1, :] = m[:, 0] = m[:, -1] = False
+    np.testing.assert_allclose(vr[m], q[m], atol=1e-13)
+    vr_full = np.where(red, q, 5.0)  # only red points (and the ring) may be read
+    vr_full[0, :], vr_full[-1, :], vr_full[:, 0], vr_full[:, -1] = q[0, :], q[-1, :], q[:, 0], q[:, -1]
+    vg = O.prolong2d_r2g(np.ascontiguousarray(vr_full), lap, h, 1.0, out=out.copy())
+    np.testing.assert_allclose(interior(vg), interior(q), atol=1e-13)
+    # 3D
+    q, lap = _quad(3, n, h, coeffs)
+    ring = np.ones_like(q, dtype=bool)
+    ring[1:-1, 1:-1, 1:-1] = False
+    base = np.where(ring, q, 9.0)
+    I = np.indices(q.shape)
+    par = I.sum(0) % 2
+    even = (I % 2 == 0)
+    corners = even.all(0)
+    centres = (~even).all(0)
+    magenta = corners | centres
+    vm = O.prolong3d_b2m(_coarse(q), lap, h, 1.0, out=base.copy())
+    np.testing.assert_allclose(vm[magenta & ~ring], q[magenta & ~ring], atol=1e-13)
+    vm_in = np.ascontiguousarray(np.where(magenta | ring, q, 5.0))
+    vr = O.prolong3d_m2r(vm_in, lap, h, 1.0, 1.0, out=base.copy())
+    redm = (par == 0) & ~ring
+    np.testing.assert_allclose(vr[redm], q[redm], atol=1e-13)
+    vr_in = np.ascontiguousarray(np.where((par == 0) | ring, q, 5.0))
+    vg = O.prolong3d_r2g(vr_in, lap, h, 1.0, out=base.copy())
+    np.testing.assert_allclose(interior(vg), interior(q), atol=1e-13)
+
+
+def test_usual_prolongation_exact_on_harmonic_bilinear():
+    """bilinear/trilinear interpolation reproduces xy (xyz); the red-black
+    Jacobi sweep with r = 0 keeps a harmonic function fixed."""
+    n, h = 15, 1.0 / 16
+    x = np.arange(n + 2) * h
+    Y, X = np.meshgrid(x, x, indexing="ij")
+    q = np.ascontiguousarray(X * Y + 0.5 * X - 0.25 * Y + 0.1)
+    out = q.copy()
+    out[1:-1, 1:-1] = 7.0
+    v = O.prolong_usual(_coarse(q), np.zeros_like(q), h, 1.0, out=out)
+    np.testing.assert_allclose(v, q, atol=1e-13)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    q = np.ascontiguousarray(X * Y * Z + X * Y - Z + 0.2)
+    out = q.copy()
+    out[1:-1, 1:-1, 1:-1] = 7.0
+    v = O.prolong_usual(_coarse(q), np.zeros_like(q), h, 1.0, out=out)
+    np.testing.assert_allclose(v, q, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# level structure: exact lattice point counts, and the paper's flop totals
+# --------------------------------------------------------------------------
+
+def _written(fn, shape_out, *args):
+    out = np.full(shape_out, np.nan)
+    fn(*args, out=out)
+    return int(np.isfinite(out).sum())
+
+
+def test_level_point_counts_and_flops_2d():
+    n = 255
+    N = n * n
+    ones = np.ones((n + 2, n + 2))
+    h = 1.0 / (n + 1)
+    red = _written(O.restrict2d_g2r, ones.shape, ones)
+    assert red == (N + 1) // 2                      # i+j even in [1,n]^2, n odd
+    rb = O.restrict2d_r2b(ones)
+    assert int((interior(rb) != 0).sum()) == ((n - 1) // 2) ** 2
+    vr = np.full(ones.shape, np.nan)
+    O.prolong2d_b2r(_coarse(ones), ones, h, 1.0, out=vr)
+    assert int(np.isfinite(vr).sum()) == ((n + 1) // 2) ** 2 + ((n - 1) // 2) ** 2
+    vg = np.full(ones.shape, np.nan)
+    vg[0, :] = vg[-1, :] = vg[:, 0] = vg[:, -1] = 0.0  # the sweep reads its own ring
+    O.prolong2d_r2g(ones, ones, h, 1.0, out=vg)
+    assert int(np.isfinite(vg).sum()) - 4 * (n + 1) == N
+    # rebuild the per-cycle flop count from the paper's per-point costs
+    want = {l.split()[0]: float(l.split()[1]) for l in open(os.path.join(GOLDEN, "flop_counts.txt"))
+            if l.strip() and not l.startswith("#")}
+    m = int(math.log2(n + 1))
+    diag = usual = 7 * N
+    for k in range(m - 2):
+        nk = 2 ** (m - k) - 1
+        nred, nblue = (nk * nk + 1) // 2, ((nk - 1) // 2) ** 2
+        diag += 6 * nred + 6 * nblue + 6 * nred + 6 * nk * nk
+        usual += 11 * nblue + 8 * nk * nk
+    assert diag / N == pytest.approx(want["diag2d"], rel=0.01)
+    assert usual / N == pytest.approx(want["usual2d"], rel=0.01)
+
+
+def test_level_point_counts_and_flops_3d():
+    n = 31
+    N = n ** 3
+    ones = np.ones((n + 2,) * 3)
+    h = 1.0 / (n + 1)
+    e, o = (n - 1) // 2, (n + 1) // 2  # even / odd indices in [1, n]
+    assert _written(O.restrict3d_g2r, ones.shape, ones) == e**3 + 3 * e * o * o
+    assert _written(O.restrict3d_r2m, ones.shape, ones) == e**3 + o**3
+    vm = np.full(ones.shape, np.nan)
+    O.prolong3d_b2m(_coarse(ones), ones, h, 1.0, out=vm)
+    assert int(np.isfinite(vm).sum()) == e**3 + o**3
+    vr = np.full(ones.shape, np.nan)
+    O.prolong3d_m2r(ones, ones, h, 1.0, 1.0, out=vr)
+    assert int(np.isfinite(vr).sum()) == e**3 + 3 * e * o * o
+    want = {l.split()[0]: float(l.split()[1]) for l in open(os.path.join(GOLDEN, "flop_counts.txt"))
+            if l.strip() and not l.startswith("#")}
+    n_big = 1023  # counts from the same closed forms, large n for the asymptotic totals
+    N = n_big ** 3
+    m = int(math.log2(n_big + 1))
+    diag = usual = 9 * N
+    for t in range(m - 2):
+        nk = 2 ** (m - t) - 1
+        e, o = (nk - 1) // 2, (nk + 1) // 2
+        red, faces, corners, centres = e**3 + 3 * e * o * o, 3 * e * o * o, e**3, o**3
+        diag += 8 * red + 14 * corners + 6 * centres + 10 * corners           # restriction
+        diag += 10 * (centres + corners) + 9 * faces + 14 * corners + 8 * nk**3  # prolongation
+        usual += 30 * corners + 11.25 * nk**3
+    assert diag / N == pytest.approx(want["diag3d"], rel=0.01)
+    assert usual / N == pytest.approx(want["usual3d"], rel=0.01)
+
+
+# --------------------------------------------------------------------------
+# convergence factors of Tables 1-3
+# --------------------------------------------------------------------------
+
+def _golden_rho():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "convergence_factors.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        d, hier, order, om, rho, tol, src = line.split()
+        rows.append((int(d), O.DIAG if hier == "diag" else O.USUAL, int(order),
+                     [float(x) for x in om.split(",")], float(rho), float(tol), src))
+    return rows
+
+
+def spectral_radius(dim, n, hier, order, omega):
+    N = n ** dim
+    f = O.grid(dim, n)
+    sl = (slice(1, -1),) * dim
+
+    def mv(x):
+        u = O.grid(dim, n)
+        u[sl] = x.reshape((n,) * dim)
+        O.vcycle(f, u, hier=hier, order=order, omega=omega)
+        return u[sl].ravel().copy()
+
+    A = LinearOperator((N, N), matvec=mv, dtype=np.float64)
+    vals = eigs(A, k=3, which="LM", return_eigenvectors=False, tol=1e-8, maxiter=5000)
+    return float(np.max(np.abs(vals)))
+
+
+@pytest.mark.parametrize("row", _golden_rho(), ids=lambda r: f"{r[0]}d-{'diag' if r[1] == 0 else 'usual'}-o{r[2]}-{r[3]}")
+def test_convergence_factor_matches_paper_table(row):
+    dim, hier, order, omega, rho_paper, tol, _ = row
+    n = 63 if dim == 2 else 15
+    rho = spectral_radius(dim, n, hier, order, omega)
+    assert abs(rho - rho_paper) <= tol * rho_paper, (rho, rho_paper)
+
+
+def test_simultaneous_jacobi_reading_is_rejected():
+    """Guard for the red-black reading of the conventional sweep: the diagonal
+    cycle at p=1 contracts ~10x per cycle while the conventional one only ~3x,
+    as the paper's Table 1 states (0.099 vs 0.340)."""
+    r_diag = spectral_radius(2, 31, O.DIAG, 2, [1.0])
+    r_usual = spectral_radius(2, 31, O.USUAL, 2, [1.0])
+    assert r_diag < 0.12 and 0.28 < r_usual < 0.4
