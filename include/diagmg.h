@@ -1,0 +1,164 @@
+/*
+ * diagmg.h -- C ABI of the GPU (sm_103a) diagonally oriented multigrid
+ * V-cycle for Poisson's equation, Laplacian(u) = f, with zero Dirichlet data
+ * on the unit square (dim 2) or unit cube (dim 3).
+ *
+ * Method: A.J. Roberts, "Fast and accurate multigrid solution of Poisson's
+ * equation using diagonally oriented grids".  The problem statement is Eq.
+ * Epois / Eq. Evpois (Section 1); the 2D cycle is Section 2, the 3D cycle
+ * Section 3; the conventional 2^-l cycle the paper compares against is
+ * described alongside (Sections 2.1, 2.2, 3.1, 3.2).
+ *
+ * Conventions shared by every call
+ *   - Grids.  n = 2^m - 1 interior points per side, h = 1/(n+1).  A caller
+ *     array is the full grid of (n+2)^dim doubles including the Dirichlet
+ *     ring, x fastest: element (i,j) at [j*pitch + i], (i,j,k) at
+ *     [(k*(n+2) + j)*pitch + i], 0 <= i,j,k <= n+1, pitch >= n+2 elements.
+ *   - Memory.  Every array pointer is caller-owned DEVICE memory on the
+ *     context's device unless the parameter says "host".  The library never
+ *     keeps a caller pointer after a call returns.  All workspace (level
+ *     buffers, norms, control words) is allocated by mg_create and freed by
+ *     mg_destroy; no other call allocates device memory.
+ *   - Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  Calls are stream-ordered; a call that returns a value
+ *     to a host pointer synchronises that stream before returning.
+ *   - Boundary.  The ring of u must be zero (homogeneous Dirichlet data, the
+ *     only case the paper treats).  The ring of f is read only by the
+ *     fourth-order residuals (Eq. Efos2, Eq. Efos4), which reach it.
+ *   - Errors.  Every call returns an mg_status; MG_EINVAL for a bad argument
+ *     (nothing is launched), MG_ECUDA for a CUDA runtime error (the context
+ *     may be unusable), MG_ENOCONV / MG_EDIVERGED from the solvers.  A context
+ *     is not thread-safe: one host thread at a time.
+ *   - Levels.  Level 0 is the finest grid.  Diagonal hierarchy, 2D: level 2k
+ *     is the axis grid of side n_k = 2^(m-k) - 1 ("green"), level 2k+1 the 45
+ *     degree grid ("red", points i+j even of that axis grid).  3D: level 3k
+ *     green (cubic), 3k+1 red (i+j+k even), 3k+2 magenta (corners (e,e,e) and
+ *     centres (o,o,o)).  Conventional hierarchy: level k is the axis grid of
+ *     side n_k.  The coarsest level is the axis grid of side `coarsest`.
+ */
+#ifndef DIAGMG_H
+#define DIAGMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx mg_ctx;
+
+typedef enum {
+    MG_OK = 0,
+    MG_EINVAL = -1,     /* invalid argument; nothing was launched */
+    MG_ENOMEM = -2,     /* device allocation failed in mg_create */
+    MG_ECUDA = -3,      /* CUDA runtime error (message: mg_last_error) */
+    MG_ENOCONV = -4,    /* max_cycles reached above rtol */
+    MG_EDIVERGED = -5,  /* residual became non-finite or grew 1e3-fold */
+    MG_ETIMEOUT = -6    /* a bounded device wait gave up (batched launch) */
+} mg_status;
+
+enum { MG_DIAG = 0, MG_USUAL = 1 };   /* hierarchy */
+enum { MG_FP64 = 0, MG_MIXED = 1 };   /* precision of the level arithmetic */
+
+/* Context description.
+ *   dim        2 or 3
+ *   n          interior points per side, 2^m - 1 with m >= 2
+ *   pitch      elements per row of the caller's full-grid arrays, >= n+2
+ *   hierarchy  MG_DIAG (Sections 2, 3) or MG_USUAL (the conventional cycle)
+ *   order      2 (5/7-point residual) or 4 (Eq. Efos2 / Eq. Efos4)
+ *   precision  MG_FP64: every level in FP64.  MG_MIXED: residual on the
+ *              finest grid and the update u += v in FP64, all levels and
+ *              sweeps in FP32, coarsest solve in FP64 (iterative refinement
+ *              with one FP32 V-cycle per FP64 residual).
+ *   coarsest   interior side of the coarsest axis grid: 1, 3 or 7 (2D), 1 or
+ *              3 (3D), <= n.  It is solved exactly.
+ *   omega      over-relaxation weights multiplying the residual term of the
+ *              Jacobi sweeps.  2D: {p} (Eq. Eajacr, Eq. Eajacb); 3D diagonal:
+ *              {p_m, p_r1, p_r2, p_g} (Eq. Emprolm .. Eq. Egprolr);
+ *              conventional: {p} (2D) or {p_g} (3D).  Unused entries ignored. */
+typedef struct {
+    int dim;
+    int n;
+    int pitch;
+    int hierarchy;
+    int order;
+    int precision;
+    int coarsest;
+    double omega[4];
+} mg_desc;
+
+/* Create a context on the current CUDA device and allocate all of its
+ * workspace.  *out receives the context (NULL on error).  Synchronous. */
+mg_status mg_create(mg_ctx **out, const mg_desc *desc);
+
+/* Free the context and its workspace.  Synchronises the device.  NULL is a no-op. */
+mg_status mg_destroy(mg_ctx *ctx);
+
+/* Number of levels (finest 0 .. coarsest), and for one level the side of the
+ * axis grid its points are indexed on (n_k) and its kind: 0 green/axis,
+ * 1 red (45 degree / FCC), 2 magenta (BCC).  Host-only; no device work. */
+mg_status mg_num_levels(const mg_ctx *ctx, int *num_levels);
+mg_status mg_level_info(const mg_ctx *ctx, int level, int *side, int *kind);
+
+/* Residual on the finest grid (Eq. Evpois): r = f - L_h u with the 5/7-point
+ * Laplacian (order 2), or the compact fourth-order forms Eq. Efos2 (2D) /
+ * Eq. Efos4 (3D) (order 4).  h must equal 1/(n+1).  The result is stored in
+ * the context as the level-0 residual (in the context's level precision) and,
+ * when r is not NULL, also written in FP64 to r (caller pitch, interior points
+ * only).  norm2 (host, nullable) receives sum(r^2) over interior points; the
+ * call then synchronises `stream`. */
+mg_status mg_residual(mg_ctx *ctx, const double *f, const double *u, double h, int order, double *r,
+                      double *norm2, void *stream);
+
+/* One restriction stage on the context's level buffers: r^(level+1) from
+ * r^(level).  Diagonal 2D: Eq. Erest2r (green -> red) or Eq. Erest2b (red ->
+ * blue).  Diagonal 3D: Eq. Erred, Eq. Ermagc + Eq. Ermagm, Eq. Erblu.
+ * Conventional: full weighting (9 / 27 points, Sections 2.1 and 3.1).
+ * 0 <= level < num_levels - 1. */
+mg_status mg_restrict_diag(mg_ctx *ctx, int level, void *stream);
+
+/* Exact solve on the coarsest level: v = L_H^-1 r with the 5/7-point operator
+ * of that grid's spacing H (the paper leaves the coarsest treatment open). */
+mg_status mg_coarse_solve(mg_ctx *ctx, void *stream);
+
+/* One prolongation stage: v^(level) from v^(level+1) and r^(level).
+ * Diagonal 2D: Eq. Eajacr then Eq. Eajacb on a red level; the analogous
+ * green-red sweep on a green level (Section 2.2, weight of Section 2.4).
+ * Diagonal 3D: Eq. Emprolm + Eq. Emprolb (magenta), Eq. Erprolr + Eq. Erprolm
+ * (red), Eq. Egprolg + Eq. Egprolr (green).  Conventional: bilinear /
+ * trilinear interpolation then one red-black ordered Jacobi iteration with
+ * residual weight p (Sections 2.2, 3.2).  omega (host, nullable) overrides
+ * the context's weights for this call.  0 <= level < num_levels - 1. */
+mg_status mg_jacobi_prolong(mg_ctx *ctx, int level, const double *omega, void *stream);
+
+/* Copy a level buffer between the context and a caller full grid of side
+ * n_k (mg_level_info), pitch n_k+2, indexed with that grid's subscripts as
+ * the paper does.  which: 0 = residual r, 1 = correction v.  Only the
+ * interior points of the level are read or written; other entries of the
+ * caller grid are left untouched (get) or ignored (set).  FP64 on the caller
+ * side, converted to the level precision. */
+mg_status mg_level_get(mg_ctx *ctx, int level, int which, double *grid, void *stream);
+mg_status mg_level_set(mg_ctx *ctx, int level, int which, const double *grid, void *stream);
+
+/* One V-cycle in place: r = f - L u, restriction down every level, exact
+ * coarsest solve, Jacobi prolongation up every level, u += v (Sections 2.3,
+ * 3.3).  u: in/out (caller pitch, zero ring). */
+mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *u, void *stream);
+
+/* V-cycles from the warm start u until ||r||_2 / ||r(u=0)||_2 <= rtol, where
+ * r is the residual of the context's order, or until max_cycles cycles.  The
+ * convergence test runs on the device; the host waits once at the end.
+ *   cycles_out  (host, nullable) cycles applied
+ *   relres_out  (host, nullable) final relative residual
+ *   history     (host, nullable, length max_cycles) relative residual after
+ *               each cycle
+ * Returns MG_OK, MG_ENOCONV or MG_EDIVERGED (u holds the last iterate). */
+mg_status mg_solve(mg_ctx *ctx, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
+                   double *relres_out, double *history, void *stream);
+
+/* Message for a status, and the last CUDA error text of this process. */
+const char *mg_strerror(mg_status status);
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIAGMG_H */

@@ -1,0 +1,206 @@
+"""Python API over the C ABI: contexts, solves and the autograd adjoint.
+
+PyTorch supplies device memory and streams only; every step of the method
+runs in the CUDA kernels of libdiagmg.so.  Arrays are CUDA float64 tensors
+holding the full grid (Dirichlet ring included), shape (n+2,)*dim, x the last
+(fastest) axis.
+"""
+
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native as N
+
+# Over-relaxation weights the paper found optimal (Table 1: 2D p; Table 3:
+# 3D p_m, p_r1, p_r2, p_g for the diagonal cycle and p_g for the usual one).
+PAPER_OMEGA = {
+    (2, "diag", 2): (1.052,), (2, "diag", 4): (1.2,),
+    (2, "usual", 2): (1.121,), (2, "usual", 4): (1.216,),
+    (3, "diag", 2): (1.11, 1.42, 1.08, 0.99), (3, "diag", 4): (0.91, 0.80, 0.70, 1.77),
+    (3, "usual", 2): (1.30,), (3, "usual", 4): (1.70,),
+}
+
+
+def default_omega(dim: int, hierarchy: str = "diag", order: int = 2) -> tuple:
+    return PAPER_OMEGA[(dim, hierarchy, order)]
+
+
+def _hier(h):
+    return {"diag": N.MG_DIAG, "usual": N.MG_USUAL}[h]
+
+
+def _prec(p):
+    return {"fp64": N.MG_FP64, "mixed": N.MG_MIXED}[p]
+
+
+class Context:
+    """One solver context (mg_create) for a fixed grid, hierarchy, order and precision."""
+
+    def __init__(self, dim: int, n: int, *, hierarchy: str = "diag", order: int = 2, precision: str = "fp64",
+                 coarsest: int = 3, omega=None, pitch: int | None = None, device=None):
+        self.dim, self.n, self.order = dim, n, order
+        self.hierarchy, self.precision = hierarchy, precision
+        self.pitch = n + 2 if pitch is None else pitch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        om = tuple(default_omega(dim, hierarchy, order) if omega is None else omega)
+        self.omega = om
+        d = N.mg_desc()
+        d.dim, d.n, d.pitch = dim, n, self.pitch
+        d.hierarchy, d.order, d.precision, d.coarsest = _hier(hierarchy), order, _prec(precision), coarsest
+        for i in range(4):
+            d.omega[i] = om[i] if i < len(om) else 1.0
+        self._desc = d
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            N.check(N.lib().mg_create(ctypes.byref(self._h), ctypes.byref(d)), "mg_create")
+        nl = ctypes.c_int()
+        N.check(N.lib().mg_num_levels(self._h, ctypes.byref(nl)), "mg_num_levels")
+        self.num_levels = nl.value
+
+    # -- plumbing ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            N.lib().mg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _grid(self, t: torch.Tensor, name: str):
+        n, dim = self.n, self.dim
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.float64:
+            raise TypeError(f"{name}: expected a CUDA float64 tensor")
+        if t.dim() != dim or tuple(t.shape) != (n + 2,) * dim:
+            raise ValueError(f"{name}: expected shape {(n + 2,) * dim}, got {tuple(t.shape)}")
+        want = (self.pitch,) if dim == 2 else (self.pitch * (n + 2), self.pitch)
+        if t.stride(-1) != 1 or tuple(t.stride()[:-1]) != want:
+            raise ValueError(f"{name}: strides {t.stride()} do not match pitch {self.pitch}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def new_grid(self) -> torch.Tensor:
+        return torch.zeros((self.n + 2,) * self.dim, dtype=torch.float64, device=self.device)
+
+    def level_info(self, level: int):
+        s, k = ctypes.c_int(), ctypes.c_int()
+        N.check(N.lib().mg_level_info(self._h, level, ctypes.byref(s), ctypes.byref(k)), "mg_level_info")
+        return s.value, k.value
+
+    # -- the C ABI, one method per call ------------------------------------
+    def residual(self, f, u, r=None, norm: bool = True):
+        """mg_residual: returns sum(r^2) (float) when norm, else None."""
+        out = ctypes.c_double()
+        rp = self._grid(r, "r") if r is not None else None
+        N.check(N.lib().mg_residual(self._h, self._grid(f, "f"), self._grid(u, "u"), 1.0 / (self.n + 1),
+                                    self.order, rp, ctypes.byref(out) if norm else None, self._stream()),
+                "mg_residual")
+        return out.value if norm else None
+
+    def restrict(self, level: int):
+        N.check(N.lib().mg_restrict_diag(self._h, level, self._stream()), "mg_restrict_diag")
+
+    def coarse_solve(self):
+        N.check(N.lib().mg_coarse_solve(self._h, self._stream()), "mg_coarse_solve")
+
+    def prolong(self, level: int, omega=None):
+        om = None
+        if omega is not None:
+            arr = (ctypes.c_double * 4)(*(list(omega) + [1.0] * (4 - len(omega))))
+            om = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+        N.check(N.lib().mg_jacobi_prolong(self._h, level, om, self._stream()), "mg_jacobi_prolong")
+
+    def level_get(self, level: int, which: str = "r", out: torch.Tensor | None = None) -> torch.Tensor:
+        side, _ = self.level_info(level)
+        g = torch.zeros((side + 2,) * self.dim, dtype=torch.float64, device=self.device) if out is None else out
+        N.check(N.lib().mg_level_get(self._h, level, {"r": 0, "v": 1}[which], ctypes.c_void_p(g.data_ptr()),
+                                     self._stream()), "mg_level_get")
+        return g
+
+    def level_set(self, level: int, which: str, grid: torch.Tensor):
+        side, _ = self.level_info(level)
+        assert grid.is_contiguous() and grid.dtype == torch.float64 and tuple(grid.shape) == (side + 2,) * self.dim
+        N.check(N.lib().mg_level_set(self._h, level, {"r": 0, "v": 1}[which], ctypes.c_void_p(grid.data_ptr()),
+                                     self._stream()), "mg_level_set")
+
+    def vcycle(self, f, u):
+        N.check(N.lib().mg_vcycle(self._h, self._grid(f, "f"), self._grid(u, "u"), self._stream()), "mg_vcycle")
+        return u
+
+    def solve(self, f, u=None, *, rtol: float = 1e-10, max_cycles: int = 100, raise_on_fail: bool = True):
+        """mg_solve from the warm start u (default zeros).  Returns (u, cycles, relres, history)."""
+        u = self.new_grid() if u is None else u
+        cyc, rel = ctypes.c_int(), ctypes.c_double()
+        hist = (ctypes.c_double * max(1, max_cycles))()
+        st = N.lib().mg_solve(self._h, self._grid(f, "f"), self._grid(u, "u"), rtol, max_cycles, ctypes.byref(cyc),
+                              ctypes.byref(rel), hist, self._stream())
+        if raise_on_fail:
+            N.check(st, "mg_solve")
+        return u, cyc.value, rel.value, list(hist[: cyc.value])
+
+
+_CTX_CACHE: dict = {}
+
+
+def _ctx(dim, n, hierarchy, order, precision, coarsest, omega, device):
+    key = (dim, n, hierarchy, order, precision, coarsest, tuple(omega) if omega else None, str(device))
+    c = _CTX_CACHE.get(key)
+    if c is None:
+        c = Context(dim, n, hierarchy=hierarchy, order=order, precision=precision, coarsest=coarsest,
+                    omega=omega, device=device)
+        _CTX_CACHE[key] = c
+    return c
+
+
+def solve(f: torch.Tensor, *, order: int = 2, hierarchy: str = "diag", precision: str = "mixed",
+          rtol: float = 1e-10, max_cycles: int = 100, coarsest: int = 3, omega=None, u0=None):
+    """Solve Laplacian(u) = f (zero Dirichlet ring) on the unit square / cube.
+
+    f: CUDA float64 full grid (n+2,)*dim.  Returns (u, info) with info a dict
+    holding cycles, relres and the residual history."""
+    dim, n = f.dim(), f.shape[0] - 2
+    c = _ctx(dim, n, hierarchy, order, precision, coarsest, omega, f.device)
+    u = u0.clone() if u0 is not None else None
+    u, cyc, rel, hist = c.solve(f.contiguous(), u, rtol=rtol, max_cycles=max_cycles)
+    return u, {"cycles": cyc, "relres": rel, "history": hist}
+
+
+class PoissonSolve(torch.autograd.Function):
+    """u = L^-1 f for the discrete Dirichlet Laplacian, differentiable in f.
+
+    Forward: a multigrid solve to `rtol`.  Backward: L is symmetric under
+    homogeneous Dirichlet data, so the adjoint of the solve is the same solve
+    applied to the incoming gradient: grad_f = L^-1 grad_u (interior points;
+    the ring of grad_f is zero because the ring of f is never read by the
+    second-order operator)."""
+
+    @staticmethod
+    def forward(ctx, f, rtol=1e-10, precision="mixed", max_cycles=100):
+        u, _ = solve(f, order=2, precision=precision, rtol=rtol, max_cycles=max_cycles)
+        ctx.cfg = (rtol, precision, max_cycles)
+        return u
+
+    @staticmethod
+    def backward(ctx, g):
+        rtol, precision, max_cycles = ctx.cfg
+        g = g.contiguous().clone()
+        dim = g.dim()
+        ring = torch.ones_like(g, dtype=torch.bool)
+        ring[(slice(1, -1),) * dim] = False
+        g[ring] = 0.0
+        w, _ = solve(g, order=2, precision=precision, rtol=rtol, max_cycles=max_cycles)
+        return w, None, None, None

@@ -1,0 +1,532 @@
+// mg_host.cu -- C ABI (include/diagmg.h): context, level table and the
+// launch schedule of the V-cycle.  All arithmetic runs in the kernels of
+// mg_stages.cuh; this file only sizes buffers and launches.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/diagmg.h"
+#include "mg_stages.cuh"
+
+using namespace mg;
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+mg_status cuda_fail(cudaError_t e, const char *where) {
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", where, cudaGetErrorString(e));
+    return MG_ECUDA;
+}
+#define CK(call)                                               \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+    } while (0)
+#define CKL(where)                                             \
+    do {                                                       \
+        cudaError_t e_ = cudaGetLastError();                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where);    \
+    } while (0)
+
+int log2_side(int n) {
+    if (n < 1) return -1;
+    long v = (long)n + 1;
+    int m = 0;
+    while ((v & 1) == 0) { v >>= 1; m++; }
+    return v == 1 ? m : -1;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+enum { KIND_AXIS = 0, KIND_RED = 1, KIND_MAG = 2 };
+
+struct Level {
+    int kind;      // KIND_*
+    int side;      // side of the axis grid whose subscripts index this level
+    int k;         // pair / triple / conventional level index (spacing h 2^k)
+    int nb;        // coset arrays: (nb+2) entries per axis (diagonal levels)
+    int pitch;     // elements per row of every array of this level
+    int rows;      // rows per plane (3D)
+    size_t len;    // elements per array
+    int ncos;      // arrays per level (1 axis, 2 or 4 cosets)
+    void *r[4];
+    void *v[4];
+};
+
+}  // namespace
+
+struct mg_ctx {
+    mg_desc d;
+    int m, K, L;        // log2(n+1), coarsenings, last level index
+    double h;
+    size_t esz;         // bytes per level element (8 FP64, 4 MIXED)
+    std::vector<Level> lv;
+    void *pool = nullptr;       // all level arrays
+    double *part = nullptr;     // residual block partial sums
+    int max_blocks = 0;
+    Ctrl *ctl = nullptr;
+    double *hist = nullptr;     // device history, length hist_cap
+    int hist_cap = 0;
+    double *G = nullptr;        // coarsest dense inverse
+    double *scal = nullptr;     // device scalar for norms
+    int dev = 0;
+};
+
+namespace {
+
+// ---- geometry -------------------------------------------------------------
+
+void build_levels(mg_ctx *c) {
+    const int dim = c->d.dim;
+    const int cm = log2_side(c->d.coarsest);
+    c->K = c->m - cm;
+    auto axis = [&](int k) {
+        Level l{};
+        l.kind = KIND_AXIS;
+        l.k = k;
+        l.side = (1 << (c->m - k)) - 1;
+        l.nb = 0;
+        l.pitch = round_up(l.side + 2, 32);
+        l.rows = l.side + 2;
+        l.len = (size_t)l.pitch * l.rows * (dim == 3 ? (size_t)l.rows : 1);
+        l.ncos = 1;
+        return l;
+    };
+    auto coset = [&](int k, int kind) {
+        Level l{};
+        l.kind = kind;
+        l.k = k;
+        l.side = (1 << (c->m - k)) - 1;
+        l.nb = (l.side - 1) / 2;
+        l.pitch = round_up(l.nb + 2, 32);
+        l.rows = l.nb + 2;
+        l.len = (size_t)l.pitch * l.rows * (dim == 3 ? (size_t)l.rows : 1);
+        l.ncos = (dim == 3 && kind == KIND_RED) ? 4 : 2;
+        return l;
+    };
+    c->lv.clear();
+    for (int k = 0; k < c->K; k++) {
+        c->lv.push_back(axis(k));
+        if (c->d.hierarchy == MG_DIAG) {
+            c->lv.push_back(coset(k, KIND_RED));
+            if (dim == 3) c->lv.push_back(coset(k, KIND_MAG));
+        }
+    }
+    c->lv.push_back(axis(c->K));
+    c->L = (int)c->lv.size() - 1;
+}
+
+// dense inverse of the 5/7-point operator on the coarsest grid (side s,
+// spacing H) from its sine eigenbasis: G = S diag(1/lambda) S, S orthonormal
+std::vector<double> coarse_inverse(int dim, int s, double H) {
+    const int nn = dim == 2 ? s * s : s * s * s;
+    std::vector<double> S((size_t)s * s), lam1(s), G((size_t)nn * nn, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int p = 0; p < s; p++) {
+        lam1[p] = -4.0 / (H * H) * std::pow(std::sin((p + 1) * pi / (2.0 * (s + 1))), 2);
+        for (int i = 0; i < s; i++) S[(size_t)i * s + p] = std::sqrt(2.0 / (s + 1)) * std::sin((i + 1) * (p + 1) * pi / (s + 1));
+    }
+    const int nm = nn;
+    for (int q = 0; q < nn; q++) {
+        const int qi = q % s, qj = (q / s) % s, qk = dim == 3 ? q / (s * s) : 0;
+        for (int t = 0; t < nn; t++) {
+            const int ti = t % s, tj = (t / s) % s, tk = dim == 3 ? t / (s * s) : 0;
+            double acc = 0.0;
+            for (int mode = 0; mode < nm; mode++) {
+                const int pi_ = mode % s, pj = (mode / s) % s, pk = dim == 3 ? mode / (s * s) : 0;
+                double lam = lam1[pi_] + lam1[pj] + (dim == 3 ? lam1[pk] : 0.0);
+                double w = S[(size_t)qi * s + pi_] * S[(size_t)ti * s + pi_] * S[(size_t)qj * s + pj] * S[(size_t)tj * s + pj];
+                if (dim == 3) w *= S[(size_t)qk * s + pk] * S[(size_t)tk * s + pk];
+                acc += w / lam;
+            }
+            G[(size_t)q * nn + t] = acc;
+        }
+    }
+    return G;
+}
+
+// ---- launch helpers -------------------------------------------------------
+
+inline cudaStream_t S(void *s) { return (cudaStream_t)s; }
+
+dim3 grid2(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 7) / 8, 1); }
+dim3 grid3(int nx, int ny, int nz) { return dim3((nx + 31) / 32, (ny + 7) / 8, nz); }
+const dim3 B2(32, 8, 1);
+
+template <typename T> A2<T> a2(void *p, const Level &l) { return A2<T>{(T *)p, l.pitch}; }
+template <typename T> A3<T> a3(void *p, const Level &l) { return A3<T>{(T *)p, l.pitch, l.rows}; }
+template <typename T> Red3<T> red3v(void *const *p, const Level &l) {
+    return Red3<T>{a3<T>(p[0], l), a3<T>(p[1], l), a3<T>(p[2], l), a3<T>(p[3], l)};
+}
+template <typename T> Mag3<T> mag3v(void *const *p, const Level &l) { return Mag3<T>{a3<T>(p[0], l), a3<T>(p[1], l)}; }
+
+double spacing(const mg_ctx *c, const Level &l) { return c->h * (double)(1 << l.k); }
+
+// residual of the finest grid into level 0 (+ optional FP64 copy, partials)
+template <typename T>
+void launch_residual(mg_ctx *c, const double *f, const double *u, double *r64, bool rhs_only, const int *done,
+                     cudaStream_t s) {
+    const Level &l0 = c->lv[0];
+    const int n = c->d.n;
+    const double ih2 = 1.0 / (c->h * c->h);
+    if (c->d.dim == 2) {
+        dim3 g = grid2(n, n);
+        auto r = a2<T>(l0.r[0], l0);
+        if (c->d.order == 2) {
+            if (rhs_only) k_res_2d<T, 2, true><<<g, B2, 0, s>>>(f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+            else k_res_2d<T, 2, false><<<g, B2, 0, s>>>(f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+        } else {
+            if (rhs_only) k_res_2d<T, 4, true><<<g, B2, 0, s>>>(f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+            else k_res_2d<T, 4, false><<<g, B2, 0, s>>>(f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+        }
+    } else {
+        dim3 g = grid3(n, n, n);
+        auto r = a3<T>(l0.r[0], l0);
+        const int ur = n + 2;
+        if (c->d.order == 2) {
+            if (rhs_only) k_res_3d<T, 2, true><<<g, B2, 0, s>>>(f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+            else k_res_3d<T, 2, false><<<g, B2, 0, s>>>(f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+        } else {
+            if (rhs_only) k_res_3d<T, 4, true><<<g, B2, 0, s>>>(f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+            else k_res_3d<T, 4, false><<<g, B2, 0, s>>>(f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+        }
+    }
+}
+
+int residual_blocks(const mg_ctx *c) {
+    const int n = c->d.n;
+    dim3 g = c->d.dim == 2 ? grid2(n, n) : grid3(n, n, n);
+    return (int)(g.x * g.y * g.z);
+}
+
+// restriction r^(l+1) <- r^(l)
+template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cudaStream_t s) {
+    const Level &a = c->lv[l], &b = c->lv[l + 1];
+    if (c->d.hierarchy == MG_USUAL) {
+        const int nc = b.side;
+        if (c->d.dim == 2) k_fw_2d<T><<<grid2(nc, nc), B2, 0, s>>>(a2<const T>(a.r[0], a), a2<T>(b.r[0], b), nc, done);
+        else k_fw_3d<T><<<grid3(nc, nc, nc), B2, 0, s>>>(a3<const T>(a.r[0], a), a3<T>(b.r[0], b), nc, done);
+        return;
+    }
+    if (c->d.dim == 2) {
+        if (a.kind == KIND_AXIS) {
+            const int nb = b.nb;
+            k_g2r_2d<T><<<grid2(nb + 1, nb + 1), B2, 0, s>>>(a2<const T>(a.r[0], a), a2<T>(b.r[0], b), a2<T>(b.r[1], b), nb, done);
+        } else {
+            const int nb = a.nb;
+            k_r2b_2d<T><<<grid2(nb, nb), B2, 0, s>>>(a2<const T>(a.r[0], a), a2<const T>(a.r[1], a), a2<T>(b.r[0], b), nb, done);
+        }
+        return;
+    }
+    if (a.kind == KIND_AXIS) {
+        const int nb = b.nb;
+        k_g2r_3d<T><<<grid3(nb + 1, nb + 1, nb + 1), B2, 0, s>>>(a3<const T>(a.r[0], a), red3v<T>(b.r, b), nb, done);
+    } else if (a.kind == KIND_RED) {
+        const int nb = a.nb;
+        k_r2m_3d<T><<<grid3(nb + 1, nb + 1, nb + 1), B2, 0, s>>>(red3v<const T>(a.r, a), mag3v<T>(b.r, b), nb, done);
+    } else {
+        const int nb = a.nb;
+        k_m2b_3d<T><<<grid3(nb, nb, nb), B2, 0, s>>>(mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
+    }
+}
+
+// prolongation v^(l) <- v^(l+1), r^(l); on level 0 with u != nullptr the
+// second half-sweep also applies u += v
+template <typename T>
+void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *done, cudaStream_t s) {
+    const Level &a = c->lv[l], &b = c->lv[l + 1];
+    const double hk = spacing(c, a), hk2 = hk * hk;
+    const int dim = c->d.dim;
+    if (a.kind == KIND_AXIS) {
+        // green-red sweep (diagonal) or interpolation + red-black sweep (conventional)
+        const int n = a.side;
+        const double p = (dim == 3 && c->d.hierarchy == MG_DIAG) ? om[3] : om[0];
+        const T cc = (T)(p * hk2);
+        if (dim == 2) {
+            if (c->d.hierarchy == MG_USUAL)
+                k_usual_odd_2d<T><<<grid2(n, n), B2, 0, s>>>(a2<const T>(b.v[0], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+            else
+                k_r2g_f_2d<T><<<grid2(n, n), B2, 0, s>>>(a2<const T>(b.v[0], b), a2<const T>(b.v[1], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+            if (u)
+                k_r2g_c_upd_2d<T><<<grid2(n, n), B2, 0, s>>>(a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
+            else
+                k_r2g_c_2d<T><<<grid2(n, n), B2, 0, s>>>(a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+        } else {
+            if (c->d.hierarchy == MG_USUAL)
+                k_usual_odd_3d<T><<<grid3(n, n, n), B2, 0, s>>>(a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+            else
+                k_r2g_f_3d<T><<<grid3(n, n, n), B2, 0, s>>>(red3v<const T>(b.v, b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+            if (u)
+                k_r2g_c_upd_3d<T><<<grid3(n, n, n), B2, 0, s>>>(a3<const T>(a.r[0], a), a3<const T>(a.v[0], a), u, c->d.pitch, n + 2, n, cc, done);
+            else
+                k_r2g_c_3d<T><<<grid3(n, n, n), B2, 0, s>>>(a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+        }
+        return;
+    }
+    const int nb = a.nb;
+    if (dim == 2) {  // red level from the blue (next axis) level, Eq. Eajacr, Eq. Eajacb
+        const T cc = (T)(2.0 * om[0] * hk2);
+        k_b2r_oo_2d<T><<<grid2(nb + 1, nb + 1), B2, 0, s>>>(a2<const T>(b.v[0], b), a2<const T>(a.r[1], a), a2<T>(a.v[1], a), nb, cc, done);
+        k_b2r_ee_2d<T><<<grid2(nb, nb), B2, 0, s>>>(a2<const T>(a.v[1], a), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), nb, cc, done);
+        return;
+    }
+    if (a.kind == KIND_MAG) {  // Eq. Emprolm, Eq. Emprolb
+        const T cc = (T)(4.0 * om[0] * hk2);
+        k_b2m_ooo_3d<T><<<grid3(nb + 1, nb + 1, nb + 1), B2, 0, s>>>(a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, done);
+        k_b2m_eee_3d<T><<<grid3(nb, nb, nb), B2, 0, s>>>(a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, done);
+    } else {  // red from magenta: Eq. Erprolr (faces), Eq. Erprolm (corners)
+        const T c1 = (T)(2.0 * om[1] * hk2), c2 = (T)(4.0 * om[2] * hk2);
+        k_m2r_faces_3d<T><<<grid3(nb + 1, nb + 1, nb + 1), B2, 0, s>>>(mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, done);
+        k_m2r_corners_3d<T><<<grid3(nb, nb, nb), B2, 0, s>>>(red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, done);
+    }
+}
+
+template <typename T> void launch_coarse(mg_ctx *c, const int *done, cudaStream_t s) {
+    const Level &l = c->lv[c->L];
+    k_coarse<T><<<1, 512, 0, s>>>((const T *)l.r[0], l.pitch, l.rows, l.side, c->d.dim, c->G, (T *)l.v[0], done);
+}
+
+template <typename T>
+mg_status vcycle_t(mg_ctx *c, const double *f, double *u, const int *done, bool with_residual, cudaStream_t s) {
+    if (with_residual) launch_residual<T>(c, f, u, nullptr, false, done, s);
+    for (int l = 0; l < c->L; l++) launch_restrict<T>(c, l, done, s);
+    launch_coarse<T>(c, done, s);
+    for (int l = c->L - 1; l >= 0; l--) launch_prolong<T>(c, l, c->d.omega, l == 0 ? u : nullptr, done, s);
+    if (c->L == 0) {  // the finest grid is the coarsest: v = L^-1 r exactly
+        const Level &l0 = c->lv[0];
+        const int n = c->d.n;
+        dim3 g = c->d.dim == 2 ? grid2(n, n) : grid3(n, n, n);
+        k_add_axis<T><<<g, B2, 0, s>>>((const T *)l0.v[0], l0.pitch, l0.rows, n, c->d.dim, u, c->d.pitch, n + 2, done);
+    }
+    CKL("vcycle launch");
+    return MG_OK;
+}
+
+bool valid_desc(const mg_desc *d) {
+    if (!d) return false;
+    if (d->dim != 2 && d->dim != 3) return false;
+    const int m = log2_side(d->n), cm = log2_side(d->coarsest);
+    if (m < 2 || cm < 1 || cm > m) return false;
+    if (d->dim == 2 && d->coarsest > 7) return false;
+    if (d->dim == 3 && d->coarsest > 3) return false;
+    if (d->pitch < d->n + 2) return false;
+    if (d->hierarchy != MG_DIAG && d->hierarchy != MG_USUAL) return false;
+    if (d->order != 2 && d->order != 4) return false;
+    if (d->precision != MG_FP64 && d->precision != MG_MIXED) return false;
+    for (int i = 0; i < 4; i++)
+        if (!std::isfinite(d->omega[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+const char *mg_strerror(mg_status st) {
+    switch (st) {
+    case MG_OK: return "ok";
+    case MG_EINVAL: return "invalid argument";
+    case MG_ENOMEM: return "device allocation failed";
+    case MG_ECUDA: return "CUDA runtime error";
+    case MG_ENOCONV: return "not converged within max_cycles";
+    case MG_EDIVERGED: return "residual diverged";
+    case MG_ETIMEOUT: return "bounded device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *mg_last_error(void) { return g_last_error; }
+
+mg_status mg_destroy(mg_ctx *c) {
+    if (!c) return MG_OK;
+    cudaDeviceSynchronize();
+    cudaFree(c->pool);
+    cudaFree(c->part);
+    cudaFree(c->ctl);
+    cudaFree(c->hist);
+    cudaFree(c->G);
+    cudaFree(c->scal);
+    delete c;
+    return MG_OK;
+}
+
+mg_status mg_create(mg_ctx **out, const mg_desc *d) {
+    if (!out) return MG_EINVAL;
+    *out = nullptr;
+    if (!valid_desc(d)) return MG_EINVAL;
+    mg_ctx *c = new (std::nothrow) mg_ctx();
+    if (!c) return MG_ENOMEM;
+    c->d = *d;
+    c->m = log2_side(d->n);
+    c->h = 1.0 / (d->n + 1);
+    c->esz = d->precision == MG_FP64 ? 8 : 4;
+    cudaGetDevice(&c->dev);
+    build_levels(c);
+    size_t total = 0;
+    for (auto &l : c->lv) total += (size_t)l.ncos * 2 * ((l.len * c->esz + 255) / 256 * 256);
+    if (cudaMalloc(&c->pool, total) != cudaSuccess) { cudaGetLastError(); mg_destroy(c); return MG_ENOMEM; }
+    if (cudaMemset(c->pool, 0, total) != cudaSuccess) { mg_destroy(c); return MG_ECUDA; }
+    char *p = (char *)c->pool;
+    for (auto &l : c->lv) {
+        size_t bytes = (l.len * c->esz + 255) / 256 * 256;
+        for (int q = 0; q < l.ncos; q++) { l.r[q] = p; p += bytes; }
+        for (int q = 0; q < l.ncos; q++) { l.v[q] = p; p += bytes; }
+    }
+    c->max_blocks = residual_blocks(c);
+    c->hist_cap = 4096;
+    const Level &lc = c->lv[c->L];
+    const int nn = d->dim == 2 ? lc.side * lc.side : lc.side * lc.side * lc.side;
+    if (cudaMalloc(&c->part, sizeof(double) * c->max_blocks) != cudaSuccess ||
+        cudaMalloc(&c->ctl, sizeof(Ctrl)) != cudaSuccess ||
+        cudaMalloc(&c->hist, sizeof(double) * c->hist_cap) != cudaSuccess ||
+        cudaMalloc(&c->G, sizeof(double) * nn * nn) != cudaSuccess ||
+        cudaMalloc(&c->scal, sizeof(double) * 4) != cudaSuccess) {
+        cudaGetLastError();
+        mg_destroy(c);
+        return MG_ENOMEM;
+    }
+    std::vector<double> G = coarse_inverse(d->dim, lc.side, spacing(c, lc));
+    if (cudaMemcpy(c->G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->ctl, 0, sizeof(Ctrl)) != cudaSuccess) {
+        mg_destroy(c);
+        return cuda_fail(cudaGetLastError(), "mg_create upload");
+    }
+    *out = c;
+    return MG_OK;
+}
+
+mg_status mg_num_levels(const mg_ctx *c, int *num) {
+    if (!c || !num) return MG_EINVAL;
+    *num = c->L + 1;
+    return MG_OK;
+}
+
+mg_status mg_level_info(const mg_ctx *c, int level, int *side, int *kind) {
+    if (!c || level < 0 || level > c->L) return MG_EINVAL;
+    if (side) *side = c->lv[level].side;
+    if (kind) *kind = c->lv[level].kind;
+    return MG_OK;
+}
+
+mg_status mg_residual(mg_ctx *c, const double *f, const double *u, double h, int order, double *r, double *norm2,
+                      void *stream) {
+    if (!c || !f || !u) return MG_EINVAL;
+    if (order != c->d.order) return MG_EINVAL;
+    if (std::fabs(h - c->h) > 1e-15 * c->h) return MG_EINVAL;
+    cudaStream_t s = S(stream);
+    if (c->d.precision == MG_FP64) launch_residual<double>(c, f, u, r, false, nullptr, s);
+    else launch_residual<float>(c, f, u, r, false, nullptr, s);
+    CKL("mg_residual");
+    if (norm2) {
+        k_sum_to<<<1, 1024, 0, s>>>(c->part, c->max_blocks, c->scal);
+        CKL("mg_residual norm");
+        CK(cudaMemcpyAsync(norm2, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return MG_OK;
+}
+
+mg_status mg_restrict_diag(mg_ctx *c, int level, void *stream) {
+    if (!c || level < 0 || level >= c->L) return MG_EINVAL;
+    if (c->d.precision == MG_FP64) launch_restrict<double>(c, level, nullptr, S(stream));
+    else launch_restrict<float>(c, level, nullptr, S(stream));
+    CKL("mg_restrict_diag");
+    return MG_OK;
+}
+
+mg_status mg_coarse_solve(mg_ctx *c, void *stream) {
+    if (!c) return MG_EINVAL;
+    if (c->d.precision == MG_FP64) launch_coarse<double>(c, nullptr, S(stream));
+    else launch_coarse<float>(c, nullptr, S(stream));
+    CKL("mg_coarse_solve");
+    return MG_OK;
+}
+
+mg_status mg_jacobi_prolong(mg_ctx *c, int level, const double *omega, void *stream) {
+    if (!c || level < 0 || level >= c->L) return MG_EINVAL;
+    const double *om = omega ? omega : c->d.omega;
+    if (c->d.precision == MG_FP64) launch_prolong<double>(c, level, om, nullptr, nullptr, S(stream));
+    else launch_prolong<float>(c, level, om, nullptr, nullptr, S(stream));
+    CKL("mg_jacobi_prolong");
+    return MG_OK;
+}
+
+static mg_status level_io(mg_ctx *c, int level, int which, double *grid, int to_level, void *stream) {
+    if (!c || !grid || level < 0 || level > c->L || (which != 0 && which != 1)) return MG_EINVAL;
+    const Level &l = c->lv[level];
+    void *const *arr = which == 0 ? l.r : l.v;
+    const int s = l.side, dim = c->d.dim;
+    dim3 g = dim == 2 ? grid2(s, s) : grid3(s, s, s);
+    void *c0 = arr[0], *c1 = l.ncos > 1 ? arr[1] : nullptr, *c2 = l.ncos > 2 ? arr[2] : nullptr,
+         *c3 = l.ncos > 3 ? arr[3] : nullptr;
+    if (c->d.precision == MG_FP64)
+        k_level_io<double><<<g, B2, 0, S(stream)>>>(dim, l.kind, s, grid, (double *)c0, (double *)c1, (double *)c2,
+                                                    (double *)c3, l.pitch, l.rows, to_level);
+    else
+        k_level_io<float><<<g, B2, 0, S(stream)>>>(dim, l.kind, s, grid, (float *)c0, (float *)c1, (float *)c2,
+                                                   (float *)c3, l.pitch, l.rows, to_level);
+    CKL("mg_level_io");
+    return MG_OK;
+}
+
+mg_status mg_level_get(mg_ctx *c, int level, int which, double *grid, void *stream) {
+    return level_io(c, level, which, grid, 0, stream);
+}
+
+mg_status mg_level_set(mg_ctx *c, int level, int which, const double *grid, void *stream) {
+    return level_io(c, level, which, (double *)grid, 1, stream);
+}
+
+mg_status mg_vcycle(mg_ctx *c, const double *f, double *u, void *stream) {
+    if (!c || !f || !u) return MG_EINVAL;
+    if (c->d.precision == MG_FP64) return vcycle_t<double>(c, f, u, nullptr, true, S(stream));
+    return vcycle_t<float>(c, f, u, nullptr, true, S(stream));
+}
+
+mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
+                   double *relres_out, double *history, void *stream) {
+    if (!c || !f || !u || !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap) return MG_EINVAL;
+    cudaStream_t s = S(stream);
+    const bool fp64 = c->d.precision == MG_FP64;
+    const int *done = &c->ctl->done;
+    k_ctrl_init<<<1, 1, 0, s>>>(c->ctl, rtol, max_cycles);
+    // ||r(u=0)||^2
+    if (fp64) launch_residual<double>(c, f, u, nullptr, true, nullptr, s);
+    else launch_residual<float>(c, f, u, nullptr, true, nullptr, s);
+    k_sum_to<<<1, 1024, 0, s>>>(c->part, c->max_blocks, &c->ctl->f2);
+    CKL("mg_solve init");
+    Ctrl host{};
+    const int chunk = 4;
+    for (int cyc = 0; cyc <= max_cycles; cyc += chunk) {
+        for (int q = 0; q < chunk && cyc + q <= max_cycles; q++) {
+            const int first = (cyc + q) == 0;
+            if (fp64) launch_residual<double>(c, f, u, nullptr, false, first ? nullptr : done, s);
+            else launch_residual<float>(c, f, u, nullptr, false, first ? nullptr : done, s);
+            k_ctrl<<<1, 1024, 0, s>>>(c->part, c->max_blocks, c->ctl, c->hist, first);
+            mg_status st = fp64 ? vcycle_t<double>(c, f, u, done, false, s) : vcycle_t<float>(c, f, u, done, false, s);
+            if (st != MG_OK) return st;
+        }
+        CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (host.done) break;
+    }
+    if (cycles_out) *cycles_out = host.cycles;
+    if (relres_out) *relres_out = host.relres;
+    if (history && host.cycles > 0) {
+        CK(cudaMemcpyAsync(history, c->hist, sizeof(double) * host.cycles, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (host.status == -5) return MG_EDIVERGED;
+    if (host.status == -4 || !host.done) return MG_ENOCONV;
+    return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,567 @@
+// mg_stages.cuh -- per-stage CUDA kernels of the diagonally oriented multigrid
+// V-cycle (A.J. Roberts, "Fast and accurate multigrid solution of Poisson's
+// equation using diagonally oriented grids") and of the conventional cycle.
+//
+// Storage (device, owned by the context):
+//   * An axis level (green grid, conventional level, coarsest grid) of side s
+//     is one array of (s+2) rows (x fastest) incl. the zero Dirichlet ring.
+//   * A diagonal level of the pair/triple whose green grid has side n = 2nb+1
+//     is split into cosets of that green grid by index parity, each a dense
+//     axis-aligned array of (nb+2) entries per axis: an even green index 2a
+//     maps to coset index a (a = 0 and nb+1 are the ring), an odd index 2c+1
+//     maps to c (0..nb).  2D red (i+j even) = cosets EE, OO; 3D red (i+j+k
+//     even) = EEE, OOE, OEO, EOO; 3D magenta = EEE (corners), OOO (centres).
+//     With this split every stencil of the paper reads unit-stride
+//     neighbours of a coset array, and no lattice hole is stored.
+//   * Rings and coset entries outside the lattice are zero and never written.
+//
+// Each kernel computes one stage (a restriction, or one half of a red-black
+// sweep) with one thread per output point.  `done` (nullable) is the device
+// convergence flag of the solver: when set every kernel returns at once.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mg {
+
+template <typename T> struct A2 {  // 2D array view
+    T *p;
+    int pitch;
+    __device__ __forceinline__ T &operator()(int i, int j) const { return p[(size_t)j * pitch + i]; }
+};
+template <typename T> struct A3 {  // 3D array view
+    T *p;
+    int pitch, rows;
+    __device__ __forceinline__ T &operator()(int i, int j, int k) const {
+        return p[((size_t)k * rows + j) * pitch + i];
+    }
+};
+
+__device__ __forceinline__ bool stop(const int *done) { return done != nullptr && *(volatile const int *)done; }
+
+#define MG_IDX2 \
+    const int tx = blockIdx.x * blockDim.x + threadIdx.x; \
+    const int ty = blockIdx.y * blockDim.y + threadIdx.y;
+#define MG_IDX3 \
+    MG_IDX2 const int tz = blockIdx.z;
+
+// ---------------------------------------------------------------------------
+// 2D diagonal hierarchy (Section 2)
+// ---------------------------------------------------------------------------
+
+// value of a red level at green point (x,y), x+y even (EE or OO coset)
+template <typename T> __device__ __forceinline__ T red2(const A2<T> &ee, const A2<T> &oo, int x, int y) {
+    return (x & 1) ? oo(x >> 1, y >> 1) : ee(x >> 1, y >> 1);
+}
+
+// green -> red, Eq. Erest2r: r' = (4r + sum of the 4 axis neighbours)/8 at i+j even.
+// Thread per coset cell (a,b) in [0,nb]^2: OO(a,b) always, EE(a,b) if interior.
+template <typename T>
+__global__ void k_g2r_2d(A2<const T> g, A2<T> ee, A2<T> oo, int nb, const int *done) {
+    if (stop(done)) return;
+    MG_IDX2 const int a = tx, b = ty;
+    if (a > nb || b > nb) return;
+    int i = 2 * a + 1, j = 2 * b + 1;
+    oo(a, b) = (T(4) * g(i, j) + (g(i - 1, j) + g(i + 1, j)) + (g(i, j - 1) + g(i, j + 1))) * T(0.125);
+    if (a >= 1 && b >= 1) {
+        i = 2 * a; j = 2 * b;
+        ee(a, b) = (T(4) * g(i, j) + (g(i - 1, j) + g(i + 1, j)) + (g(i, j - 1) + g(i, j + 1))) * T(0.125);
+    }
+}
+
+// red -> blue, Eq. Erest2b: r' = (4r + sum of the 4 diagonal neighbours)/8 at (e,e)
+template <typename T>
+__global__ void k_r2b_2d(A2<const T> ee, A2<const T> oo, A2<T> blue, int nb, const int *done) {
+    if (stop(done)) return;
+    MG_IDX2 const int a = tx + 1, b = ty + 1;
+    if (a > nb || b > nb) return;
+    blue(a, b) = (T(4) * ee(a, b) + (oo(a - 1, b - 1) + oo(a, b - 1)) + (oo(a - 1, b) + oo(a, b))) * T(0.125);
+}
+
+// blue -> red, Eq. Eajacr: red points that are not blue (OO) from the four
+// diagonal blue values; c = 2 p h^2 (red spacing sqrt(2) h).
+template <typename T>
+__global__ void k_b2r_oo_2d(A2<const T> blue, A2<const T> roo, A2<T> voo, int nb, T c, const int *done) {
+    if (stop(done)) return;
+    MG_IDX2 const int a = tx, b = ty;
+    if (a > nb || b > nb) return;
+    voo(a, b) = ((blue(a, b) + blue(a + 1, b)) + (blue(a, b + 1) + blue(a + 1, b + 1)) - c * roo(a, b)) * T(0.25);
+}
+
+// Eq. Eajacb: blue points (EE) refined from the four new diagonal red values
+template <typename T>
+__global__ void k_b2r_ee_2d(A2<const T> voo, A2<const T> ree, A2<T> vee, int nb, T c, const int *done) {
+    if (stop(done)) return;
+    MG_IDX2 const int a = tx + 1, b = ty + 1;
+    if (a > nb || b > nb) return;
+    vee(a, b) = ((voo(a - 1, b - 1) + voo(a, b - 1)) + (voo(a - 1, b) + voo(a, b)) - c * ree(a, b)) * T(0.25);
+}
+
+// red -> green, first half: green-only points (i+j odd) from the four axis
+// red values; c = p h^2 (Section 2.2, weight of Section 2.4)
+template <typename T>
+__global__ void k_r2g_f_2d(A2<const T> ee, A2<const T> oo, A2<const T> rg, A2<T> vg, int n, T c,
+                           const int *done) {
+    if (stop(done)) return;
+    MG_IDX2 const int i = tx + 1, j = ty + 1;
+    if (i > n || j > n || ((i + j) & 1) == 0) return;
+    T s = (red2(ee, oo, i - 1, j) + red2(ee, oo, i + 1, j)) + (red2(ee, oo, i, j - 1) + red2(ee, oo, i, j + 1));
+    vg(i, j) = (s - c * rg(i, j)) * T(0.25);
+}
+
+// red -> green, second half: red points (i+j even) from the four new green values
+template <typename T>
+__global__ void k_r2g_c_2d(A2<const T> rg, A2<T> vg, int n, T c, const int *done) {
+    if (stop(done)) return;
+    MG_IDX2 const int i = tx + 1, j = ty + 1;
+    if (i > n || j > n || ((i + j) & 1) == 1) return;
+    T s = (vg(i - 1, j) + vg(i + 1, j)) + (vg(i, j - 1) + vg(i, j + 1));
+    vg(i, j) = (s - c * rg(i, j)) * T(0.25);
+}
+
+// finest level: second half fused with the update u += v at every point
+template <typename T>
+__global__ void k_r2g_c_upd_2d(A2<const T> rg, A2<const T> vg, double *u, int up, int n, T c, const int *done) {
+    if (stop(done)) return;
+    MG_IDX2 const int i = tx + 1, j = ty + 1;
+    if (i > n || j > n) return;
+    T v;
+    if ((i + j) & 1) v = vg(i, j);
+    else v = ((vg(i - 1, j) + vg(i + 1, j)) + (vg(i, j - 1) + vg(i, j + 1)) - c * rg(i, j)) * T(0.25);
+    u[(size_t)j * up + i] += (double)v;
+}
+
+// ---------------------------------------------------------------------------
+// 3D diagonal hierarchy (Section 3)
+// ---------------------------------------------------------------------------
+
+template <typename T> struct Red3 { A3<T> eee, ooe, oeo, eoo; };
+template <typename T> struct Mag3 { A3<T> eee, ooo; };
+
+// red level value at green point (x,y,z), x+y+z even
+template <typename T> __device__ __forceinline__ T red3(const Red3<const T> &r, int x, int y, int z) {
+    const int px = x & 1, py = y & 1;
+    const int a = x >> 1, b = y >> 1, c = z >> 1;
+    if (px && py) return r.ooe(a, b, c);
+    if (px) return r.oeo(a, b, c);
+    if (py) return r.eoo(a, b, c);
+    return r.eee(a, b, c);
+}
+
+// green -> red, Eq. Erred: (6r + 6 axis neighbours)/12 at i+j+k even.
+// Thread per cell (a,b,c) in [0,nb]^3 holding EEE, OOE, OEO, EOO points.
+template <typename T>
+__global__ void k_g2r_3d(A3<const T> g, Red3<T> red, int nb, const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int a = tx, b = ty, c = tz;
+    if (a > nb || b > nb || c > nb) return;
+    auto avg = [&](int i, int j, int k) {
+        return (T(6) * g(i, j, k) + (g(i + 1, j, k) + g(i - 1, j, k)) + (g(i, j + 1, k) + g(i, j - 1, k)) +
+                (g(i, j, k + 1) + g(i, j, k - 1))) * T(1.0 / 12.0);
+    };
+    if (a >= 1 && b >= 1 && c >= 1) red.eee(a, b, c) = avg(2 * a, 2 * b, 2 * c);
+    if (c >= 1) red.ooe(a, b, c) = avg(2 * a + 1, 2 * b + 1, 2 * c);
+    if (b >= 1) red.oeo(a, b, c) = avg(2 * a + 1, 2 * b, 2 * c + 1);
+    if (a >= 1) red.eoo(a, b, c) = avg(2 * a, 2 * b + 1, 2 * c + 1);
+}
+
+// sum of the 12 face-centre (FCC) neighbours of the corner (2a,2b,2c)
+template <typename T>
+__device__ __forceinline__ T fcc12(const A3<const T> &ooe, const A3<const T> &oeo, const A3<const T> &eoo, int a,
+                                   int b, int c) {
+    T s1 = (ooe(a - 1, b - 1, c) + ooe(a, b - 1, c)) + (ooe(a - 1, b, c) + ooe(a, b, c));
+    T s2 = (oeo(a - 1, b, c - 1) + oeo(a, b, c - 1)) + (oeo(a - 1, b, c) + oeo(a, b, c));
+    T s3 = (eoo(a, b - 1, c - 1) + eoo(a, b, c - 1)) + (eoo(a, b - 1, c) + eoo(a, b, c));
+    return s1 + s2 + s3;
+}
+
+// red -> magenta: corners, Eq. Ermagc (12r + 12 FCC neighbours)/24; centres,
+// Eq. Ermagm mean of the 6 face-centre neighbours.  Thread per cell in [0,nb]^3.
+template <typename T>
+__global__ void k_r2m_3d(Red3<const T> red, Mag3<T> mag, int nb, const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int a = tx, b = ty, c = tz;
+    if (a > nb || b > nb || c > nb) return;
+    if (a >= 1 && b >= 1 && c >= 1)
+        mag.eee(a, b, c) = (T(12) * red.eee(a, b, c) + fcc12(red.ooe, red.oeo, red.eoo, a, b, c)) * T(1.0 / 24.0);
+    mag.ooo(a, b, c) = ((red.eoo(a, b, c) + red.eoo(a + 1, b, c)) + (red.oeo(a, b, c) + red.oeo(a, b + 1, c)) +
+                        (red.ooe(a, b, c) + red.ooe(a, b, c + 1))) * T(1.0 / 6.0);
+}
+
+// sum of the 8 centres around the corner (2a,2b,2c)
+template <typename T> __device__ __forceinline__ T ctr8(const A3<const T> &ooo, int a, int b, int c) {
+    return ((ooo(a - 1, b - 1, c - 1) + ooo(a, b - 1, c - 1)) + (ooo(a - 1, b, c - 1) + ooo(a, b, c - 1))) +
+           ((ooo(a - 1, b - 1, c) + ooo(a, b - 1, c)) + (ooo(a - 1, b, c) + ooo(a, b, c)));
+}
+
+// magenta -> blue, Eq. Erblu: (8r + 8 centre neighbours)/16 at the blue corners
+template <typename T>
+__global__ void k_m2b_3d(Mag3<const T> mag, A3<T> blue, int nb, const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int a = tx + 1, b = ty + 1, c = tz + 1;
+    if (a > nb || b > nb || c > nb) return;
+    blue(a, b, c) = (T(8) * mag.eee(a, b, c) + ctr8(mag.ooo, a, b, c)) * T(0.0625);
+}
+
+// Eq. Emprolm: magenta centres from the 8 blue corners; c = 4 p_m h^2
+template <typename T>
+__global__ void k_b2m_ooo_3d(A3<const T> blue, A3<const T> rooo, A3<T> vooo, int nb, T cc, const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int a = tx, b = ty, c = tz;
+    if (a > nb || b > nb || c > nb) return;
+    T s = ((blue(a, b, c) + blue(a + 1, b, c)) + (blue(a, b + 1, c) + blue(a + 1, b + 1, c))) +
+          ((blue(a, b, c + 1) + blue(a + 1, b, c + 1)) + (blue(a, b + 1, c + 1) + blue(a + 1, b + 1, c + 1)));
+    vooo(a, b, c) = (s - cc * rooo(a, b, c)) * T(0.125);
+}
+
+// Eq. Emprolb: blue corners refined from the 8 new centres
+template <typename T>
+__global__ void k_b2m_eee_3d(A3<const T> vooo, A3<const T> reee, A3<T> veee, int nb, T cc, const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int a = tx + 1, b = ty + 1, c = tz + 1;
+    if (a > nb || b > nb || c > nb) return;
+    veee(a, b, c) = (ctr8(vooo, a, b, c) - cc * reee(a, b, c)) * T(0.125);
+}
+
+// Eq. Erprolr and its cyclic permutations: red face centres from the two
+// magenta centres along the face normal (weight 2) and the four in-plane
+// magenta corners; c1 = 2 p_r1 h^2.  Thread per cell in [0,nb]^3.
+template <typename T>
+__global__ void k_m2r_faces_3d(Mag3<const T> vm, Red3<const T> rr, Red3<T> vr, int nb, T c1, const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int a = tx, b = ty, c = tz;
+    if (a > nb || b > nb || c > nb) return;
+    if (c >= 1) {  // (2a+1, 2b+1, 2c): normal z
+        T ctr = vm.ooo(a, b, c - 1) + vm.ooo(a, b, c);
+        T cor = (vm.eee(a, b, c) + vm.eee(a + 1, b, c)) + (vm.eee(a, b + 1, c) + vm.eee(a + 1, b + 1, c));
+        vr.ooe(a, b, c) = (T(2) * ctr + cor - c1 * rr.ooe(a, b, c)) * T(0.125);
+    }
+    if (b >= 1) {  // (2a+1, 2b, 2c+1): normal y
+        T ctr = vm.ooo(a, b - 1, c) + vm.ooo(a, b, c);
+        T cor = (vm.eee(a, b, c) + vm.eee(a + 1, b, c)) + (vm.eee(a, b, c + 1) + vm.eee(a + 1, b, c + 1));
+        vr.oeo(a, b, c) = (T(2) * ctr + cor - c1 * rr.oeo(a, b, c)) * T(0.125);
+    }
+    if (a >= 1) {  // (2a, 2b+1, 2c+1): normal x
+        T ctr = vm.ooo(a - 1, b, c) + vm.ooo(a, b, c);
+        T cor = (vm.eee(a, b, c) + vm.eee(a, b + 1, c)) + (vm.eee(a, b, c + 1) + vm.eee(a, b + 1, c + 1));
+        vr.eoo(a, b, c) = (T(2) * ctr + cor - c1 * rr.eoo(a, b, c)) * T(0.125);
+    }
+}
+
+// Eq. Erprolm: magenta corners (red EEE) from the 12 new face centres; c2 = 4 p_r2 h^2
+template <typename T>
+__global__ void k_m2r_corners_3d(Red3<const T> vr_faces, A3<const T> reee, A3<T> veee, int nb, T c2,
+                                 const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int a = tx + 1, b = ty + 1, c = tz + 1;
+    if (a > nb || b > nb || c > nb) return;
+    veee(a, b, c) = (fcc12(vr_faces.ooe, vr_faces.oeo, vr_faces.eoo, a, b, c) - c2 * reee(a, b, c)) * T(1.0 / 12.0);
+}
+
+// Eq. Egprolg: green-only points (i+j+k odd) from the six axis red values; c = p_g h^2
+template <typename T>
+__global__ void k_r2g_f_3d(Red3<const T> vr, A3<const T> rg, A3<T> vg, int n, T cc, const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
+    if (i > n || j > n || k > n || ((i + j + k) & 1) == 0) return;
+    T s = (red3(vr, i - 1, j, k) + red3(vr, i + 1, j, k)) + (red3(vr, i, j - 1, k) + red3(vr, i, j + 1, k)) +
+          (red3(vr, i, j, k - 1) + red3(vr, i, j, k + 1));
+    vg(i, j, k) = (s - cc * rg(i, j, k)) * T(1.0 / 6.0);
+}
+
+// Eq. Egprolr: red points (i+j+k even) from the six new green values
+template <typename T>
+__global__ void k_r2g_c_3d(A3<const T> rg, A3<T> vg, int n, T cc, const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
+    if (i > n || j > n || k > n || ((i + j + k) & 1) == 1) return;
+    T s = (vg(i - 1, j, k) + vg(i + 1, j, k)) + (vg(i, j - 1, k) + vg(i, j + 1, k)) +
+          (vg(i, j, k - 1) + vg(i, j, k + 1));
+    vg(i, j, k) = (s - cc * rg(i, j, k)) * T(1.0 / 6.0);
+}
+
+template <typename T>
+__global__ void k_r2g_c_upd_3d(A3<const T> rg, A3<const T> vg, double *u, int up, int urows, int n, T cc,
+                               const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
+    if (i > n || j > n || k > n) return;
+    T v;
+    if ((i + j + k) & 1) v = vg(i, j, k);
+    else
+        v = ((vg(i - 1, j, k) + vg(i + 1, j, k)) + (vg(i, j - 1, k) + vg(i, j + 1, k)) +
+             (vg(i, j, k - 1) + vg(i, j, k + 1)) - cc * rg(i, j, k)) * T(1.0 / 6.0);
+    u[((size_t)k * urows + j) * up + i] += (double)v;
+}
+
+// ---------------------------------------------------------------------------
+// Conventional 2^-l hierarchy
+// ---------------------------------------------------------------------------
+
+// full weighting (1/16)[1 2 1]x[1 2 1]
+template <typename T>
+__global__ void k_fw_2d(A2<const T> f, A2<T> cg, int nc, const int *done) {
+    if (stop(done)) return;
+    MG_IDX2 const int a = tx + 1, b = ty + 1;
+    if (a > nc || b > nc) return;
+    const int i = 2 * a, j = 2 * b;
+    T s = T(4) * f(i, j) + T(2) * ((f(i - 1, j) + f(i + 1, j)) + (f(i, j - 1) + f(i, j + 1))) +
+          ((f(i - 1, j - 1) + f(i + 1, j - 1)) + (f(i - 1, j + 1) + f(i + 1, j + 1)));
+    cg(a, b) = s * T(0.0625);
+}
+
+// full weighting (1/64)[1 2 1]^3
+template <typename T>
+__global__ void k_fw_3d(A3<const T> f, A3<T> cg, int nc, const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int a = tx + 1, b = ty + 1, c = tz + 1;
+    if (a > nc || b > nc || c > nc) return;
+    T s = T(0);
+    for (int dk = -1; dk <= 1; dk++) {
+        T wk = dk == 0 ? T(2) : T(1);
+        for (int dj = -1; dj <= 1; dj++) {
+            T wj = dj == 0 ? T(2) : T(1);
+            T row = T(2) * f(2 * a, 2 * b + dj, 2 * c + dk) + (f(2 * a - 1, 2 * b + dj, 2 * c + dk) +
+                                                               f(2 * a + 1, 2 * b + dj, 2 * c + dk));
+            s += wk * wj * row;
+        }
+    }
+    cg(a, b, c) = s * T(1.0 / 64.0);
+}
+
+template <typename T> __device__ __forceinline__ T interp2(const A2<const T> &vc, int i, int j) {
+    const int a0 = i >> 1, a1 = (i + 1) >> 1, b0 = j >> 1, b1 = (j + 1) >> 1;
+    return ((vc(a0, b0) + vc(a1, b0)) + (vc(a0, b1) + vc(a1, b1))) * T(0.25);
+}
+template <typename T> __device__ __forceinline__ T interp3(const A3<const T> &vc, int i, int j, int k) {
+    const int a0 = i >> 1, a1 = (i + 1) >> 1, b0 = j >> 1, b1 = (j + 1) >> 1, c0 = k >> 1, c1 = (k + 1) >> 1;
+    return (((vc(a0, b0, c0) + vc(a1, b0, c0)) + (vc(a0, b1, c0) + vc(a1, b1, c0))) +
+            ((vc(a0, b0, c1) + vc(a1, b0, c1)) + (vc(a0, b1, c1) + vc(a1, b1, c1)))) * T(0.125);
+}
+
+// conventional prolongation, first half of the red-black Jacobi iteration:
+// points with odd index sum from the bilinearly interpolated coarse values of
+// their axis neighbours (the interpolated values at odd points are never read)
+template <typename T>
+__global__ void k_usual_odd_2d(A2<const T> vc, A2<const T> rg, A2<T> vg, int n, T c, const int *done) {
+    if (stop(done)) return;
+    MG_IDX2 const int i = tx + 1, j = ty + 1;
+    if (i > n || j > n || ((i + j) & 1) == 0) return;
+    T s = (interp2(vc, i - 1, j) + interp2(vc, i + 1, j)) + (interp2(vc, i, j - 1) + interp2(vc, i, j + 1));
+    vg(i, j) = (s - c * rg(i, j)) * T(0.25);
+}
+template <typename T>
+__global__ void k_usual_odd_3d(A3<const T> vc, A3<const T> rg, A3<T> vg, int n, T c, const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
+    if (i > n || j > n || k > n || ((i + j + k) & 1) == 0) return;
+    T s = (interp3(vc, i - 1, j, k) + interp3(vc, i + 1, j, k)) + (interp3(vc, i, j - 1, k) + interp3(vc, i, j + 1, k)) +
+          (interp3(vc, i, j, k - 1) + interp3(vc, i, j, k + 1));
+    vg(i, j, k) = (s - c * rg(i, j, k)) * T(1.0 / 6.0);
+}
+// the second half (even index sum) is k_r2g_c_2d / k_r2g_c_3d (and their update variants)
+
+// ---------------------------------------------------------------------------
+// residuals, norms, coarsest solve, level import/export
+// ---------------------------------------------------------------------------
+
+// block sum of a double, result valid in thread 0; blockDim.x*blockDim.y*blockDim.z <= 1024
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        v = tid < (nt + 31) / 32 ? sh[tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
+// r = f - L_h u (Eq. Evpois, 5-point) or Eq. Efos2 (ORDER 4); RHS_ONLY: u = 0.
+// Writes r (level precision) and, if r64 != nullptr, the FP64 value to the
+// caller grid; block partial sums of r^2 to part[block].
+template <typename T, int ORDER, bool RHS_ONLY>
+__global__ void k_res_2d(const double *__restrict__ f, const double *__restrict__ u, int up, int n, double ih2,
+                         A2<T> r, double *r64, double *part, const int *done) {
+    __shared__ double sh[32];
+    if (stop(done)) return;
+    MG_IDX2 const int i = tx + 1, j = ty + 1;
+    double sq = 0.0;
+    if (i <= n && j <= n) {
+        const size_t c = (size_t)j * up + i;
+        double res;
+        if (ORDER == 2) {
+            res = f[c];
+            if (!RHS_ONLY) res = fma(-ih2, ((u[c - 1] + u[c + 1]) + (u[c - up] + u[c + up])) - 4.0 * u[c], res);
+        } else {
+            res = (8.0 * f[c] + ((f[c - 1] + f[c + 1]) + (f[c - up] + f[c + up]))) * (1.0 / 12.0);
+            if (!RHS_ONLY) {
+                double ax = (u[c - 1] + u[c + 1]) + (u[c - up] + u[c + up]);
+                double dg = (u[c - up - 1] + u[c - up + 1]) + (u[c + up - 1] + u[c + up + 1]);
+                res = fma(-ih2 * (1.0 / 6.0), fma(4.0, ax, dg) - 20.0 * u[c], res);
+            }
+        }
+        r(i, j) = (T)res;
+        if (r64) r64[c] = res;
+        sq = res * res;
+    }
+    double s = block_sum(sq, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x + gridDim.x * blockIdx.y] = s;
+}
+
+// 3D: 7-point (ORDER 2) or Eq. Efos4 19-point (ORDER 4)
+template <typename T, int ORDER, bool RHS_ONLY>
+__global__ void k_res_3d(const double *__restrict__ f, const double *__restrict__ u, int up, int urows, int n,
+                         double ih2, A3<T> r, double *r64, double *part, const int *done) {
+    __shared__ double sh[32];
+    if (stop(done)) return;
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
+    double sq = 0.0;
+    if (i <= n && j <= n) {
+        const size_t pl = (size_t)urows * up;
+        const size_t c = k * pl + (size_t)j * up + i;
+        double res;
+        if (ORDER == 2) {
+            res = f[c];
+            if (!RHS_ONLY) {
+                double ax = ((u[c - 1] + u[c + 1]) + (u[c - up] + u[c + up])) + (u[c - pl] + u[c + pl]);
+                res = fma(-ih2, ax - 6.0 * u[c], res);
+            }
+        } else {
+            res = (6.0 * f[c] + ((f[c - 1] + f[c + 1]) + (f[c - up] + f[c + up]) + (f[c - pl] + f[c + pl]))) *
+                  (1.0 / 12.0);
+            if (!RHS_ONLY) {
+                double ax = ((u[c - 1] + u[c + 1]) + (u[c - up] + u[c + up])) + (u[c - pl] + u[c + pl]);
+                double ed = ((u[c - up - 1] + u[c - up + 1]) + (u[c + up - 1] + u[c + up + 1])) +
+                            ((u[c - pl - up] + u[c - pl + up]) + (u[c + pl - up] + u[c + pl + up])) +
+                            ((u[c - pl - 1] + u[c - pl + 1]) + (u[c + pl - 1] + u[c + pl + 1]));
+                res = fma(-ih2 * (1.0 / 6.0), fma(2.0, ax, ed) - 24.0 * u[c], res);
+            }
+        }
+        r(i, j, k) = (T)res;
+        if (r64) r64[c] = res;
+        sq = res * res;
+    }
+    double s = block_sum(sq, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = s;
+}
+
+// Solver control word, one per context (device memory)
+struct Ctrl {
+    double f2;      // ||r(u=0)||^2
+    double r2;      // ||r||^2 of the current iterate
+    double relres;  // sqrt(r2/f2)
+    double rel0;    // relative residual of the warm start
+    double rtol;
+    int done;       // 1: stop every kernel of the remaining cycles
+    int cycles;     // corrections applied
+    int max_cycles;
+    int status;     // 0 ok, -4 not converged, -5 diverged
+};
+
+// deterministic sum of part[0..nblk) by one block of 1024 threads (fixed order)
+__device__ __forceinline__ double sum_parts(const double *part, int nblk, double *sh) {
+    double v = 0.0;
+    for (int q = threadIdx.x; q < nblk; q += blockDim.x) v += part[q];
+    return block_sum(v, sh);
+}
+
+// after the residual of the warm start (first = 1) or of a new iterate:
+// record the history, decide whether to stop.
+__global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, int first) {
+    __shared__ double sh[32];
+    if (!first && ctl->done) return;
+    double s = sum_parts(part, nblk, sh);
+    if (threadIdx.x != 0) return;
+    ctl->r2 = s;
+    double rel = ctl->f2 > 0.0 ? sqrt(s / ctl->f2) : 0.0;
+    ctl->relres = rel;
+    if (first) ctl->rel0 = rel;
+    else hist[ctl->cycles - 1] = rel;
+    if (!(rel == rel) || rel > 1e3 * fmax(ctl->rel0, 1.0)) {
+        ctl->status = -5;
+        ctl->done = 1;
+    } else if (rel <= ctl->rtol) {
+        ctl->done = 1;
+    } else if (ctl->cycles >= ctl->max_cycles) {
+        ctl->status = -4;
+        ctl->done = 1;
+    } else {
+        ctl->cycles += 1;  // this cycle will apply a correction
+    }
+}
+
+__global__ void k_ctrl_init(Ctrl *ctl, double rtol, int max_cycles) {
+    ctl->r2 = 0.0; ctl->relres = 0.0; ctl->rel0 = 0.0; ctl->rtol = rtol;
+    ctl->done = 0; ctl->cycles = 0; ctl->max_cycles = max_cycles; ctl->status = 0;
+}
+
+__global__ void k_sum_to(const double *part, int nblk, double *out) {
+    __shared__ double sh[32];
+    double s = sum_parts(part, nblk, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// exact coarsest solve: v = G r with the dense inverse G (FP64) of the
+// 5/7-point operator of the coarsest grid.  One block.
+template <typename T>
+__global__ void k_coarse(const T *r, int pitch, int rows, int nc, int dim, const double *G, T *v, const int *done) {
+    if (stop(done)) return;
+    const int nn = dim == 2 ? nc * nc : nc * nc * nc;
+    for (int q = threadIdx.x; q < nn; q += blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < nn; t++) {
+            const int i = t % nc + 1, j = (t / nc) % nc + 1, k = dim == 3 ? t / (nc * nc) + 1 : 0;
+            s += G[(size_t)q * nn + t] * (double)r[((size_t)k * rows + j) * pitch + i];
+        }
+        const int i = q % nc + 1, j = (q / nc) % nc + 1, k = dim == 3 ? q / (nc * nc) + 1 : 0;
+        v[((size_t)k * rows + j) * pitch + i] = (T)s;
+    }
+}
+
+// u += v on an axis level (only used when the finest grid is the coarsest)
+template <typename T>
+__global__ void k_add_axis(const T *v, int pitch, int rows, int n, int dim, double *u, int up, int urows,
+                           const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = dim == 3 ? tz + 1 : 0;
+    if (i > n || j > n) return;
+    u[((size_t)k * urows + j) * up + i] += (double)v[((size_t)k * rows + j) * pitch + i];
+}
+
+// Level import/export between a caller full grid of side s (pitch s+2, FP64)
+// and the level's coset arrays.  kind: 0 axis, 1 red, 2 magenta.
+template <typename T>
+__global__ void k_level_io(int dim, int kind, int s, double *grid, T *c0, T *c1, T *c2, T *c3, int pitch, int rows,
+                           int to_level) {
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = dim == 3 ? tz + 1 : 0;
+    if (i > s || j > s || (dim == 3 && k > s)) return;
+    const size_t gidx = ((size_t)k * (s + 2) + j) * (size_t)(s + 2) + i;
+    T *arr = nullptr;
+    int x = i, y = j, z = k;
+    if (kind == 0) {
+        arr = c0;
+    } else {
+        const int px = i & 1, py = j & 1, pz = k & 1;
+        x = i >> 1; y = j >> 1; z = k >> 1;
+        if (dim == 2) {
+            if (px != py) return;
+            arr = px ? c1 : c0;
+        } else if (kind == 1) {
+            if (((px + py + pz) & 1) != 0) return;
+            arr = (px && py) ? c1 : px ? c2 : py ? c3 : c0;
+        } else {
+            if (!(px == py && py == pz)) return;
+            arr = px ? c1 : c0;
+        }
+    }
+    T &cell = arr[((size_t)z * rows + y) * pitch + x];
+    if (to_level) cell = (T)grid[gidx];
+    else grid[gidx] = (double)cell;
+}
+
+}  // namespace mg

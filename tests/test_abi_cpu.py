@@ -1,0 +1,81 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every function include/diagmg.h declares, rejects invalid descriptions before
+touching CUDA, and the binding has no CPU fallback."""
+
+import ctypes
+import os
+
+import pytest
+
+from paper_math_9907190_gb300 import _native as N
+from paper_math_9907190_gb300 import build as B
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return N.lib()
+
+
+def test_library_exports_every_declared_function(lib):
+    declared = N.header_functions()
+    assert len(declared) >= 14
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(N.SIGNATURES) <= set(declared)
+
+
+def _desc(**kw):
+    d = N.mg_desc()
+    base = dict(dim=2, n=63, pitch=65, hierarchy=N.MG_DIAG, order=2, precision=N.MG_FP64, coarsest=3)
+    base.update(kw)
+    for k, v in base.items():
+        setattr(d, k, v)
+    for i in range(4):
+        d.omega[i] = 1.0
+    return d
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=1), dict(dim=4), dict(n=64), dict(n=1), dict(n=0), dict(n=-1), dict(pitch=64),
+    dict(hierarchy=2), dict(order=3), dict(precision=7), dict(coarsest=2), dict(coarsest=127),
+    dict(dim=3, n=15, pitch=17, coarsest=7), dict(coarsest=15),
+])
+def test_create_rejects_invalid_descriptions(lib, bad):
+    h = ctypes.c_void_p()
+    st = lib.mg_create(ctypes.byref(h), ctypes.byref(_desc(**bad)))
+    assert st == N.MG_EINVAL and not h.value
+
+
+def test_nan_omega_rejected(lib):
+    d = _desc()
+    d.omega[1] = float("nan")
+    h = ctypes.c_void_p()
+    assert lib.mg_create(ctypes.byref(h), ctypes.byref(d)) == N.MG_EINVAL
+
+
+def test_null_arguments_rejected(lib):
+    assert lib.mg_create(None, ctypes.byref(_desc())) == N.MG_EINVAL
+    assert lib.mg_num_levels(None, None) == N.MG_EINVAL
+    assert lib.mg_level_info(None, 0, None, None) == N.MG_EINVAL
+    assert lib.mg_residual(None, None, None, 1.0, 2, None, None, None) == N.MG_EINVAL
+    assert lib.mg_restrict_diag(None, 0, None) == N.MG_EINVAL
+    assert lib.mg_jacobi_prolong(None, 0, None, None) == N.MG_EINVAL
+    assert lib.mg_coarse_solve(None, None) == N.MG_EINVAL
+    assert lib.mg_vcycle(None, None, None, None) == N.MG_EINVAL
+    assert lib.mg_solve(None, None, None, 1e-10, 10, None, None, None, None) == N.MG_EINVAL
+    assert lib.mg_level_get(None, 0, 0, None, None) == N.MG_EINVAL
+    assert lib.mg_destroy(None) == N.MG_OK
+
+
+def test_strerror(lib):
+    for st in (0, -1, -2, -3, -4, -5, -6):
+        assert lib.mg_strerror(st)
+    assert lib.mg_strerror(N.MG_ENOCONV) == b"not converged within max_cycles"
+
+
+def test_binding_fails_loudly_without_library(monkeypatch):
+    monkeypatch.setattr(N, "_lib", None)
+    monkeypatch.setattr(N, "LIB_PATH", os.path.join(os.path.dirname(N.LIB_PATH), "missing-libdiagmg.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        N.lib()

@@ -1,0 +1,263 @@
+"""GPU parity: every CUDA stage and the whole V-cycle against the CPU oracle.
+
+All calls go through the C ABI (via the ctypes binding).  FP64 parity bar: the
+stages and V-cycle iterates agree with the oracle to 1e-12 relative (the
+bound the method's statement of work sets; the rounding-order differences of
+the GPU are ~1e-16 per operation and the V-cycle is a contraction).  The mixed
+path must reach a 1e-10 relative residual, and its solution is compared with
+the oracle's converged FP64 solution.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_math_9907190_gb300 import Context, default_omega
+from paper_math_9907190_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DEV = torch.device("cuda", 0)
+TOL = 1e-12
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def H(t):
+    return t.detach().cpu().numpy()
+
+
+def lattice(dim, side, kind):
+    idx = np.indices((side + 2,) * dim)
+    inter = np.all((idx >= 1) & (idx <= side), axis=0)
+    if kind == 0:
+        return inter
+    if kind == 1:
+        return inter & (idx.sum(0) % 2 == 0)
+    par = idx % 2
+    return inter & (np.all(par == 0, axis=0) | np.all(par == 1, axis=0))
+
+
+def rand_on(dim, side, kind, seed):
+    g = np.random.default_rng(seed).uniform(-1, 1, size=(side + 2,) * dim)
+    return np.ascontiguousarray(np.where(lattice(dim, side, kind), g, 0.0))
+
+
+def assert_close(got, want, mask=None, tol=TOL):
+    if mask is not None:
+        got, want = got[mask], want[mask]
+    scale = max(np.abs(want).max(), 1e-300)
+    err = np.abs(got - want).max() / scale
+    assert err <= tol, f"max rel err {err:.3e}"
+
+
+def oracle_restrict(dim, hier, kind, r):
+    if hier == "usual":
+        return O.restrict_fw(r)
+    if dim == 2:
+        return O.restrict2d_g2r(r) if kind == 0 else O.restrict2d_r2b(r)
+    return {0: O.restrict3d_g2r, 1: O.restrict3d_r2m, 2: O.restrict3d_m2b}[kind](r)
+
+
+def oracle_prolong(dim, hier, kind, vc, r, h, om):
+    if hier == "usual":
+        return O.prolong_usual(vc, r, h, om[0])
+    if dim == 2:
+        return O.prolong2d_b2r(vc, r, h, om[0]) if kind == 1 else O.prolong2d_r2g(vc, r, h, om[0])
+    if kind == 2:
+        return O.prolong3d_b2m(vc, r, h, om[0])
+    if kind == 1:
+        return O.prolong3d_m2r(vc, r, h, om[1], om[2])
+    return O.prolong3d_r2g(vc, r, h, om[3])
+
+
+STAGE_CASES = [(2, 63, "diag"), (2, 127, "diag"), (2, 63, "usual"), (3, 15, "diag"), (3, 31, "diag"),
+               (3, 15, "usual")]
+
+
+@pytest.mark.parametrize("dim,n,hier", STAGE_CASES)
+def test_restriction_stages(dim, n, hier):
+    with Context(dim, n, hierarchy=hier) as c:
+        for l in range(c.num_levels - 1):
+            side, kind = c.level_info(l)
+            side1, kind1 = c.level_info(l + 1)
+            r = rand_on(dim, side, kind, 10 + l)
+            c.level_set(l, "r", T(r))
+            c.restrict(l)
+            got = H(c.level_get(l + 1, "r"))
+            want = oracle_restrict(dim, hier, kind, r)
+            assert_close(got, want, lattice(dim, side1, kind1))
+
+
+@pytest.mark.parametrize("dim,n,hier", STAGE_CASES)
+def test_prolongation_stages(dim, n, hier):
+    om = (1.3, 0.9, 1.15, 0.8) if dim == 3 and hier == "diag" else (1.07,)
+    with Context(dim, n, hierarchy=hier, omega=om) as c:
+        for l in range(c.num_levels - 1):
+            side, kind = c.level_info(l)
+            side1, kind1 = c.level_info(l + 1)
+            vc = rand_on(dim, side1, kind1, 20 + l)
+            r = rand_on(dim, side, kind, 30 + l)
+            c.level_set(l + 1, "v", T(vc))
+            c.level_set(l, "r", T(r))
+            c.prolong(l)
+            got = H(c.level_get(l, "v"))
+            want = oracle_prolong(dim, hier, kind, vc, r, 1.0 / (side + 1), om)
+            assert_close(got, want, lattice(dim, side, kind))
+
+
+@pytest.mark.parametrize("dim,n,coarsest", [(2, 63, 3), (2, 63, 1), (2, 63, 7), (3, 15, 3), (3, 15, 1)])
+def test_coarse_solve(dim, n, coarsest):
+    with Context(dim, n, coarsest=coarsest) as c:
+        L = c.num_levels - 1
+        side, kind = c.level_info(L)
+        assert side == coarsest and kind == 0
+        r = rand_on(dim, side, 0, 40)
+        c.level_set(L, "r", T(r))
+        c.coarse_solve()
+        got = H(c.level_get(L, "v"))
+        want = O.coarse_solve(r, 1.0 / (side + 1))
+        assert_close(got, want, lattice(dim, side, 0))
+
+
+@pytest.mark.parametrize("dim,n", [(2, 63), (2, 255), (3, 15), (3, 31)])
+@pytest.mark.parametrize("order", [2, 4])
+def test_residual(dim, n, order):
+    f = I.uniform_f(dim, n, 1)
+    u = I.zero_ring(I.uniform_f(dim, n, 2))
+    with Context(dim, n, order=order) as c:
+        r = c.new_grid()
+        norm2 = c.residual(T(f), T(u), r)
+        want = O.residual(f, u, order)
+        assert_close(H(r), want, lattice(dim, n, 0), tol=1e-13)
+        assert norm2 == pytest.approx(O.norm2_interior(want), rel=1e-12)
+        got0 = H(c.level_get(0, "r"))
+        assert_close(got0, want, lattice(dim, n, 0), tol=1e-13)
+
+
+def test_residual_with_padded_pitch():
+    n, pitch = 63, 80
+    f = I.uniform_f(2, n, 1)
+    u = I.zero_ring(I.uniform_f(2, n, 2))
+    fp = np.zeros((n + 2, pitch))
+    up = np.zeros((n + 2, pitch))
+    fp[:, : n + 2], up[:, : n + 2] = f, u
+    with Context(2, n, pitch=pitch) as c:
+        ft, ut = T(fp)[:, : n + 2], T(up)[:, : n + 2]
+        rt = torch.zeros((n + 2, pitch), dtype=torch.float64, device=DEV)[:, : n + 2]
+        c.residual(ft, ut, rt)
+        assert_close(H(rt), O.residual(f, u, 2), lattice(2, n, 0), tol=1e-13)
+
+
+VC_CASES = [
+    (2, 63, "diag", 2, (1.0,)), (2, 63, "diag", 2, (1.052,)), (2, 63, "usual", 2, (1.0,)),
+    (2, 63, "usual", 2, (1.121,)), (2, 63, "diag", 4, (1.2,)), (2, 63, "usual", 4, (1.216,)),
+    (2, 127, "diag", 2, (1.052,)), (2, 3, "diag", 2, (1.0,)), (2, 7, "diag", 2, (1.0,)),
+    (3, 15, "diag", 2, (1.0, 1.0, 1.0, 1.0)), (3, 15, "diag", 2, (1.11, 1.42, 1.08, 0.99)),
+    (3, 15, "usual", 2, (1.30,)), (3, 15, "diag", 4, (0.91, 0.80, 0.70, 1.77)), (3, 31, "diag", 2, (1.11, 1.42, 1.08, 0.99)),
+    (3, 3, "diag", 2, (1.0, 1.0, 1.0, 1.0)), (3, 7, "usual", 4, (1.7,)),
+]
+
+
+def _f_for(dim, n):
+    return I.square_small(n) if dim == 2 else I.cube(n)
+
+
+@pytest.mark.parametrize("dim,n,hier,order,om", VC_CASES)
+def test_vcycle_iterates_match_oracle(dim, n, hier, order, om):
+    f = _f_for(dim, n)
+    uo = O.grid(dim, n)
+    with Context(dim, n, hierarchy=hier, order=order, omega=om) as c:
+        ug = c.new_grid()
+        ft = T(f)
+        for cyc in range(12):
+            O.vcycle(f, uo, hier=O.DIAG if hier == "diag" else O.USUAL, order=order, omega=list(om))
+            c.vcycle(ft, ug)
+            got = H(ug)
+            rel = np.linalg.norm(got - uo) / np.linalg.norm(uo)
+            assert rel <= TOL, f"cycle {cyc}: rel {rel:.3e}"
+
+
+@pytest.mark.parametrize("coarsest", [1, 3, 7])
+def test_vcycle_coarsest_variants(coarsest):
+    n = 63
+    f = I.square_small(n)
+    uo = O.grid(2, n)
+    with Context(2, n, coarsest=coarsest, omega=(1.052,)) as c:
+        ug = c.new_grid()
+        for _ in range(4):
+            O.vcycle(f, uo, coarsest=coarsest, omega=[1.052])
+            c.vcycle(T(f), ug)
+        assert np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo) <= TOL
+
+
+@pytest.mark.parametrize("dim,n,hier", [(2, 63, "diag"), (2, 63, "usual"), (3, 15, "diag"), (3, 31, "usual")])
+def test_solve_fp64_matches_oracle(dim, n, hier):
+    f = _f_for(dim, n)
+    om = default_omega(dim, hier, 2)
+    uo, it_o, rel_o, hist_o = O.solve(f, hier=O.DIAG if hier == "diag" else O.USUAL, omega=list(om), rtol=1e-10)
+    with Context(dim, n, hierarchy=hier, omega=om) as c:
+        ug, it_g, rel_g, hist_g = c.solve(T(f), rtol=1e-10, max_cycles=100)
+    assert it_g == it_o
+    assert rel_g <= 1e-10
+    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-6)
+    assert np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo) <= TOL
+
+
+@pytest.mark.parametrize("dim,n,hier,order", [(2, 63, "diag", 2), (2, 255, "diag", 2), (2, 255, "diag", 4),
+                                               (2, 255, "usual", 2), (3, 31, "diag", 2), (3, 31, "usual", 2),
+                                               (3, 31, "diag", 4)])
+def test_solve_mixed_reaches_tolerance(dim, n, hier, order):
+    f = I.uniform_f(dim, n, 1) if dim == 2 else I.cube(n)
+    om = default_omega(dim, hier, order)
+    uo, _, _, _ = O.solve(f, hier=O.DIAG if hier == "diag" else O.USUAL, order=order, omega=list(om),
+                          rtol=1e-13, max_cycles=200)
+    with Context(dim, n, hierarchy=hier, order=order, precision="mixed", omega=om) as c:
+        ug, it, rel, hist = c.solve(T(f), rtol=1e-10, max_cycles=200)
+    assert rel <= 1e-10
+    # independent check of the final residual with the oracle
+    r = O.residual(f, H(ug), order)
+    f0 = O.residual(f, O.grid(dim, n), order)
+    assert math.sqrt(O.norm2_interior(r) / O.norm2_interior(f0)) <= 1.05e-10
+    err = np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo)
+    assert err <= 1e-8, err
+
+
+def test_solve_reports_nonconvergence():
+    f = I.square_small(63)
+    with Context(2, 63) as c:
+        u, it, rel, hist = c.solve(T(f), rtol=1e-14, max_cycles=3, raise_on_fail=False)
+        assert it == 3 and rel > 1e-14 and len(hist) == 3
+
+
+def test_solve_warm_start_already_converged():
+    f = I.square_small(63)
+    with Context(2, 63, omega=(1.052,)) as c:
+        u, it, rel, _ = c.solve(T(f), rtol=1e-10)
+        u2, it2, rel2, _ = c.solve(T(f), u.clone(), rtol=1e-10)
+        assert it2 == 0 and rel2 == pytest.approx(rel, rel=1e-6)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 4095), (3, 255)])
+def test_full_size_vcycle_matches_oracle(dim, n):
+    """The benchmarked sizes: two FP64 V-cycles compared element by element."""
+    f = I.square_large(n) if dim == 2 else I.cube(n)
+    om = default_omega(dim, "diag", 2)
+    uo = O.grid(dim, n)
+    with Context(dim, n, omega=om) as c:
+        ug = c.new_grid()
+        ft = T(f)
+        for _ in range(2):
+            O.vcycle(f, uo, omega=list(om))
+            c.vcycle(ft, ug)
+        got = H(ug)
+    assert np.linalg.norm(got - uo) / np.linalg.norm(uo) <= TOL
