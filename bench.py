@@ -1,0 +1,310 @@
+#!/usr/bin/env python3
+"""Benchmark: unknowns/s to a 1e-10 relative residual for the diagonally
+oriented multigrid solve of Poisson's equation on one GB300 per rank.
+
+A step is one complete solve, from u = 0 to ||f - L u|| / ||f|| <= 1e-10, of
+the 2D unit-square problem with h = 1/4096 (4095^2 = 16.8M unknowns, f ~
+U[-1,1] seed 1) by the diagonal V-cycle in mixed precision (FP64 residual and
+update, FP32 levels).  Under torchrun every rank solves its own replica
+(weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the CPU FP64 oracle (the reference arm of this
+benchmark) on the host cores: each step is one oracle V-cycle on the same
+problem, and the metric is extrapolated from the cycles the oracle needs.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "unknowns/s to 1e-10 rel. residual (2D 4096², 3D 256³), % HBM roofline"
+UNIT = "unknowns/s"
+N_SIDE = 4095
+RTOL = 1e-10
+WORKLOAD = "2D unit square, h=1/4096 (4095^2 = 16.8M unknowns), f ~ U[-1,1] seed 1, zero Dirichlet; " \
+           "diagonal V-cycle (p=1.052), mixed FP64/FP32, solve from u=0 to 1e-10 relative residual"
+
+# Algorithmic cost of the probed kernel family per finest unknown:
+# family 0 = finest-grid residual (+ squared norm): reads u, f (FP64), writes r.
+PROBE = {
+    "family": 0,
+    "name": "finest residual r = f - L u (FP64) + sum r^2",
+    "bytes_per_point": {"mixed": 8 + 8 + 4, "fp64": 8 + 8 + 8},
+    "fp64_flops_per_point": 7 + 2,
+}
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# nominal FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        time.sleep(0.25)
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 7 and p[0].replace(".", "").isdigit():
+                    rows.append(p)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][1]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())}
+
+
+def oracle_cpu_baseline(f, u_gpu=None, max_seconds=60.0):
+    """The oracle as it stands (single-threaded C, FP64) solving the full
+    workload from u = 0 to 1e-10; returns the baseline dict and its solution."""
+    import oracle as O
+    t0 = time.perf_counter()
+    u, cycles, rel, hist = O.solve(f, omega=[1.052], rtol=RTOL, max_cycles=40)
+    dt = time.perf_counter() - t0
+    out = {"value": N_SIDE**2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"one full oracle solve of the benchmark workload ({cycles} FP64 V-cycles to "
+                     f"relres {rel:.2e}, {dt:.1f} s on 1 host core)"}
+    return out, u
+
+
+def run_reference(args):
+    """Reference arm: the CPU FP64 oracle, one V-cycle per step, on rank 0."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_math_9907190_gb300 import inputs as I
+    f = I.square_large(N_SIDE)
+    u = O.grid(2, N_SIDE)
+    f0 = math.sqrt(O.norm2_interior(O.residual(f, u)))
+    times, rels = [], []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.vcycle(f, u, omega=[1.052])
+        dt = time.perf_counter() - t0
+        rels.append(math.sqrt(O.norm2_interior(O.residual(f, u))) / f0)
+        if s >= args.warmup:
+            times.append(dt)
+    t_cycle = statistics.mean(times)
+    hit = next((i + 1 for i, r in enumerate(rels) if r <= RTOL), None)
+    if hit is None:  # extrapolate from the measured contraction of the last cycles
+        rho = (rels[-1] / rels[max(0, len(rels) - 4)]) ** (1.0 / min(3, len(rels) - 1))
+        hit = len(rels) + math.ceil(math.log(RTOL / rels[-1]) / math.log(rho))
+    value = N_SIDE**2 / (t_cycle * hit)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_cycle * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("mixed FP64/FP32", "FP64 CPU oracle"),
+                       "step": "one oracle V-cycle", "cycles_to_rtol": hit},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.warmup + args.steps} oracle V-cycles of the full workload; "
+                                       f"{hit} cycles reach 1e-10"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu", action="store_true", help="short run (warm-up + one solve) for an ncu launch list")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_math_9907190_gb300 import Context
+    from paper_math_9907190_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    f_host = I.square_large(N_SIDE)
+    N = N_SIDE**2
+    f = torch.from_numpy(f_host).to(dev)
+    ctx = Context(2, N_SIDE, hierarchy="diag", order=2, precision="mixed", omega=(1.052,))
+    u = ctx.new_grid()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        u.zero_()
+        return ctx.solve(f, u, rtol=RTOL, max_cycles=60)
+
+    warm = max(args.warmup, 3)  # at least three untimed warm-up steps
+    for _ in range(warm):
+        step()
+    if args.ncu:  # short run for an ncu launch list: the warm-up solves plus one solve
+        step()
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_run": True, "launches": ctx.launch_count()}))
+        ctx.close()
+        return 0
+    barrier()
+    launches0 = ctx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        cycles = []
+        for _ in range(args.steps):
+            _, cyc, rel, hist = step()
+            cycles.append(cyc)
+        ev1.record(stream)
+        barrier()
+    launches = ctx.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * N / (ms_max * 1e-3)
+
+    # end to end through the public API: pinned host f in, host u out, every step
+    f_pin = torch.from_numpy(f_host).pin_memory()
+    u_pin = torch.empty_like(f_pin).pin_memory()
+    f_dev = torch.empty_like(f)
+    for _ in range(2):
+        f_dev.copy_(f_pin, non_blocking=True)
+        uu, _, _, _ = ctx.solve(f_dev, torch.zeros_like(f_dev), rtol=RTOL, max_cycles=60)
+        u_pin.copy_(uu, non_blocking=True)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        f_dev.copy_(f_pin, non_blocking=True)
+        uu, _, _, _ = ctx.solve(f_dev, torch.zeros_like(f_dev), rtol=RTOL, max_cycles=60)
+        u_pin.copy_(uu, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = torch.tensor([e0.elapsed_time(e1) / args.steps], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
+    e2e_ms = float(e2e_ms.item())
+
+    # live probe of the dominant kernel: the same V-cycle, its finest residual bracketed by events
+    ctx.probe_set(PROBE["family"])
+    uu = torch.zeros_like(f)
+    for _ in range(args.steps):
+        ctx.vcycle(f, uu)
+    nprobe, probe_ms = ctx.probe_read()
+    ctx.probe_set(-1)
+    avg_ms = probe_ms / max(nprobe, 1)
+    peaks = read_peaks()
+    flops = PROBE["fp64_flops_per_point"] * N
+    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
+    bytes_ = PROBE["bytes_per_point"]["mixed"] * N
+    roofline = {"bound": "alu", "kernel": PROBE["name"], "achieved": achieved_tf,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                "traffic": None, "avg_launch_ms": avg_ms,
+                "hbm_side": {"achieved_gbs": bytes_ / (avg_ms * 1e-3) / 1e9,
+                             "peak_gbs": peaks.get("hbm_gbs", 6800.0),
+                             "frac": bytes_ / (avg_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
+                "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal, derived)"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": warm, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64/f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dim": 2, "n": N_SIDE, "hierarchy": "diag", "precision": "mixed",
+                       "rtol": RTOL, "cycles": cycles[-1], "relres": rel,
+                       "vcycles_per_s": world * cycles[-1] / (ms_max * 1e-3),
+                       "l2": "inputs larger than L2 (f and u 134 MB each; ~1 GB moved per cycle)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk.summary(),
+            "e2e": {"value": world * N / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(f_pin.numel() * 8), "d2h_bytes_per_step": int(u_pin.numel() * 8)},
+            "gpu_launches": int(launches),
+            "roofline": roofline}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, u_orc = oracle_cpu_baseline(f_host)
+        line["cpu_baseline"] = cb
+        ug = u.cpu().numpy()
+        line["config"]["rel_err_vs_oracle"] = float(np.linalg.norm(ug - u_orc) / np.linalg.norm(u_orc))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

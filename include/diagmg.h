@@ -154,6 +154,18 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *u, void *stream);
 mg_status mg_solve(mg_ctx *ctx, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
                    double *relres_out, double *history, void *stream);
 
+/* Diagnostics (no paper counterpart).  mg_launch_count: kernels this context
+ * has launched since creation (host counter).  mg_probe_set: when family >= 0,
+ * every later launch of that kernel family is bracketed with CUDA events on
+ * its stream (family 0: finest-grid residual / down pass, 1: finest-grid
+ * prolongation and update, 2: all other level stages, 3: control kernels;
+ * -1 turns the probe off).  mg_probe_read synchronises `stream` and returns
+ * the probed launches and their summed device time in ms since the last
+ * mg_probe_set.  Event objects are created by the first mg_probe_set. */
+mg_status mg_launch_count(const mg_ctx *ctx, long long *launches);
+mg_status mg_probe_set(mg_ctx *ctx, int family);
+mg_status mg_probe_read(mg_ctx *ctx, long long *launches, double *ms, void *stream);
+
 /* Message for a status, and the last CUDA error text of this process. */
 const char *mg_strerror(mg_status status);
 const char *mg_last_error(void);

@@ -101,6 +101,21 @@ class Context:
         N.check(N.lib().mg_level_info(self._h, level, ctypes.byref(s), ctypes.byref(k)), "mg_level_info")
         return s.value, k.value
 
+    # -- diagnostics ---------------------------------------------------------
+    def launch_count(self) -> int:
+        v = ctypes.c_longlong()
+        N.check(N.lib().mg_launch_count(self._h, ctypes.byref(v)), "mg_launch_count")
+        return v.value
+
+    def probe_set(self, family: int):
+        N.check(N.lib().mg_probe_set(self._h, family), "mg_probe_set")
+
+    def probe_read(self):
+        """(launches, total ms) of the probed kernel family since probe_set."""
+        n, ms = ctypes.c_longlong(), ctypes.c_double()
+        N.check(N.lib().mg_probe_read(self._h, ctypes.byref(n), ctypes.byref(ms), self._stream()), "mg_probe_read")
+        return n.value, ms.value
+
     # -- the C ABI, one method per call ------------------------------------
     def residual(self, f, u, r=None, norm: bool = True):
         """mg_residual: returns sum(r^2) (float) when norm, else None."""

@@ -74,6 +74,13 @@ struct mg_ctx {
     double *G = nullptr;        // coarsest dense inverse
     double *scal = nullptr;     // device scalar for norms
     int dev = 0;
+    // launch accounting and the optional event probe of one kernel family
+    long long launches = 0;
+    int probe_tag = -1;
+    std::vector<cudaEvent_t> pev;  // start/end pairs
+    int pev_used = 0;
+    long long probe_n = 0;
+    double probe_ms = 0.0;
 };
 
 namespace {
@@ -153,6 +160,43 @@ std::vector<double> coarse_inverse(int dim, int s, double H) {
 
 inline cudaStream_t S(void *s) { return (cudaStream_t)s; }
 
+// kernel families for the probe (mg_probe_set)
+enum { TAG_RESIDUAL = 0, TAG_FINEST_UP = 1, TAG_LEVELS = 2, TAG_CONTROL = 3 };
+
+// Counts every launch; brackets the launch with events when its family is probed.
+struct Launch {
+    mg_ctx *c;
+    cudaStream_t s;
+    int slot = -1;
+    Launch(mg_ctx *c_, int tag, cudaStream_t s_) : c(c_), s(s_) {
+        c->launches++;
+        if (c->probe_tag == tag && 2 * c->pev_used + 1 < (int)c->pev.size()) {
+            slot = c->pev_used++;
+            cudaEventRecord(c->pev[2 * slot], s);
+        }
+    }
+    ~Launch() {
+        if (slot >= 0) cudaEventRecord(c->pev[2 * slot + 1], s);
+    }
+};
+#define LAUNCH(tag, kern, grid, block, ...)            \
+    do {                                               \
+        Launch l_(c, tag, s);                          \
+        kern<<<grid, block, 0, s>>>(__VA_ARGS__);      \
+    } while (0)
+
+// accumulate the probe events of completed work (call after a stream sync)
+void probe_collect(mg_ctx *c) {
+    for (int q = 0; q < c->pev_used; q++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->pev[2 * q], c->pev[2 * q + 1]) == cudaSuccess) {
+            c->probe_ms += ms;
+            c->probe_n += 1;
+        }
+    }
+    c->pev_used = 0;
+}
+
 dim3 grid2(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 7) / 8, 1); }
 dim3 grid3(int nx, int ny, int nz) { return dim3((nx + 31) / 32, (ny + 7) / 8, nz); }
 const dim3 B2(32, 8, 1);
@@ -177,22 +221,22 @@ void launch_residual(mg_ctx *c, const double *f, const double *u, double *r64, b
         dim3 g = grid2(n, n);
         auto r = a2<T>(l0.r[0], l0);
         if (c->d.order == 2) {
-            if (rhs_only) k_res_2d<T, 2, true><<<g, B2, 0, s>>>(f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
-            else k_res_2d<T, 2, false><<<g, B2, 0, s>>>(f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+            if (rhs_only) LAUNCH(TAG_RESIDUAL, (k_res_2d<T, 2, true>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+            else LAUNCH(TAG_RESIDUAL, (k_res_2d<T, 2, false>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
         } else {
-            if (rhs_only) k_res_2d<T, 4, true><<<g, B2, 0, s>>>(f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
-            else k_res_2d<T, 4, false><<<g, B2, 0, s>>>(f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+            if (rhs_only) LAUNCH(TAG_RESIDUAL, (k_res_2d<T, 4, true>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+            else LAUNCH(TAG_RESIDUAL, (k_res_2d<T, 4, false>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
         }
     } else {
         dim3 g = grid3(n, n, n);
         auto r = a3<T>(l0.r[0], l0);
         const int ur = n + 2;
         if (c->d.order == 2) {
-            if (rhs_only) k_res_3d<T, 2, true><<<g, B2, 0, s>>>(f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
-            else k_res_3d<T, 2, false><<<g, B2, 0, s>>>(f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+            if (rhs_only) LAUNCH(TAG_RESIDUAL, (k_res_3d<T, 2, true>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+            else LAUNCH(TAG_RESIDUAL, (k_res_3d<T, 2, false>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
         } else {
-            if (rhs_only) k_res_3d<T, 4, true><<<g, B2, 0, s>>>(f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
-            else k_res_3d<T, 4, false><<<g, B2, 0, s>>>(f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+            if (rhs_only) LAUNCH(TAG_RESIDUAL, (k_res_3d<T, 4, true>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+            else LAUNCH(TAG_RESIDUAL, (k_res_3d<T, 4, false>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
         }
     }
 }
@@ -208,29 +252,29 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
     const Level &a = c->lv[l], &b = c->lv[l + 1];
     if (c->d.hierarchy == MG_USUAL) {
         const int nc = b.side;
-        if (c->d.dim == 2) k_fw_2d<T><<<grid2(nc, nc), B2, 0, s>>>(a2<const T>(a.r[0], a), a2<T>(b.r[0], b), nc, done);
-        else k_fw_3d<T><<<grid3(nc, nc, nc), B2, 0, s>>>(a3<const T>(a.r[0], a), a3<T>(b.r[0], b), nc, done);
+        if (c->d.dim == 2) LAUNCH(TAG_LEVELS, (k_fw_2d<T>), grid2(nc, nc), B2, a2<const T>(a.r[0], a), a2<T>(b.r[0], b), nc, done);
+        else LAUNCH(TAG_LEVELS, (k_fw_3d<T>), grid3(nc, nc, nc), B2, a3<const T>(a.r[0], a), a3<T>(b.r[0], b), nc, done);
         return;
     }
     if (c->d.dim == 2) {
         if (a.kind == KIND_AXIS) {
             const int nb = b.nb;
-            k_g2r_2d<T><<<grid2(nb + 1, nb + 1), B2, 0, s>>>(a2<const T>(a.r[0], a), a2<T>(b.r[0], b), a2<T>(b.r[1], b), nb, done);
+            LAUNCH(TAG_LEVELS, (k_g2r_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(a.r[0], a), a2<T>(b.r[0], b), a2<T>(b.r[1], b), nb, done);
         } else {
             const int nb = a.nb;
-            k_r2b_2d<T><<<grid2(nb, nb), B2, 0, s>>>(a2<const T>(a.r[0], a), a2<const T>(a.r[1], a), a2<T>(b.r[0], b), nb, done);
+            LAUNCH(TAG_LEVELS, (k_r2b_2d<T>), grid2(nb, nb), B2, a2<const T>(a.r[0], a), a2<const T>(a.r[1], a), a2<T>(b.r[0], b), nb, done);
         }
         return;
     }
     if (a.kind == KIND_AXIS) {
         const int nb = b.nb;
-        k_g2r_3d<T><<<grid3(nb + 1, nb + 1, nb + 1), B2, 0, s>>>(a3<const T>(a.r[0], a), red3v<T>(b.r, b), nb, done);
+        LAUNCH(TAG_LEVELS, (k_g2r_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(a.r[0], a), red3v<T>(b.r, b), nb, done);
     } else if (a.kind == KIND_RED) {
         const int nb = a.nb;
-        k_r2m_3d<T><<<grid3(nb + 1, nb + 1, nb + 1), B2, 0, s>>>(red3v<const T>(a.r, a), mag3v<T>(b.r, b), nb, done);
+        LAUNCH(TAG_LEVELS, (k_r2m_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, red3v<const T>(a.r, a), mag3v<T>(b.r, b), nb, done);
     } else {
         const int nb = a.nb;
-        k_m2b_3d<T><<<grid3(nb, nb, nb), B2, 0, s>>>(mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
+        LAUNCH(TAG_LEVELS, (k_m2b_3d<T>), grid3(nb, nb, nb), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
     }
 }
 
@@ -248,46 +292,46 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
         const T cc = (T)(p * hk2);
         if (dim == 2) {
             if (c->d.hierarchy == MG_USUAL)
-                k_usual_odd_2d<T><<<grid2(n, n), B2, 0, s>>>(a2<const T>(b.v[0], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+                LAUNCH(TAG_LEVELS, (k_usual_odd_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
             else
-                k_r2g_f_2d<T><<<grid2(n, n), B2, 0, s>>>(a2<const T>(b.v[0], b), a2<const T>(b.v[1], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+                LAUNCH(TAG_LEVELS, (k_r2g_f_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(b.v[1], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
             if (u)
-                k_r2g_c_upd_2d<T><<<grid2(n, n), B2, 0, s>>>(a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
+                LAUNCH(TAG_FINEST_UP, (k_r2g_c_upd_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
             else
-                k_r2g_c_2d<T><<<grid2(n, n), B2, 0, s>>>(a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+                LAUNCH(TAG_LEVELS, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
         } else {
             if (c->d.hierarchy == MG_USUAL)
-                k_usual_odd_3d<T><<<grid3(n, n, n), B2, 0, s>>>(a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+                LAUNCH(TAG_LEVELS, (k_usual_odd_3d<T>), grid3(n, n, n), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
             else
-                k_r2g_f_3d<T><<<grid3(n, n, n), B2, 0, s>>>(red3v<const T>(b.v, b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+                LAUNCH(TAG_LEVELS, (k_r2g_f_3d<T>), grid3(n, n, n), B2, red3v<const T>(b.v, b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
             if (u)
-                k_r2g_c_upd_3d<T><<<grid3(n, n, n), B2, 0, s>>>(a3<const T>(a.r[0], a), a3<const T>(a.v[0], a), u, c->d.pitch, n + 2, n, cc, done);
+                LAUNCH(TAG_FINEST_UP, (k_r2g_c_upd_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<const T>(a.v[0], a), u, c->d.pitch, n + 2, n, cc, done);
             else
-                k_r2g_c_3d<T><<<grid3(n, n, n), B2, 0, s>>>(a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+                LAUNCH(TAG_LEVELS, (k_r2g_c_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
         }
         return;
     }
     const int nb = a.nb;
     if (dim == 2) {  // red level from the blue (next axis) level, Eq. Eajacr, Eq. Eajacb
         const T cc = (T)(2.0 * om[0] * hk2);
-        k_b2r_oo_2d<T><<<grid2(nb + 1, nb + 1), B2, 0, s>>>(a2<const T>(b.v[0], b), a2<const T>(a.r[1], a), a2<T>(a.v[1], a), nb, cc, done);
-        k_b2r_ee_2d<T><<<grid2(nb, nb), B2, 0, s>>>(a2<const T>(a.v[1], a), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), nb, cc, done);
+        LAUNCH(TAG_LEVELS, (k_b2r_oo_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[1], a), a2<T>(a.v[1], a), nb, cc, done);
+        LAUNCH(TAG_LEVELS, (k_b2r_ee_2d<T>), grid2(nb, nb), B2, a2<const T>(a.v[1], a), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), nb, cc, done);
         return;
     }
     if (a.kind == KIND_MAG) {  // Eq. Emprolm, Eq. Emprolb
         const T cc = (T)(4.0 * om[0] * hk2);
-        k_b2m_ooo_3d<T><<<grid3(nb + 1, nb + 1, nb + 1), B2, 0, s>>>(a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, done);
-        k_b2m_eee_3d<T><<<grid3(nb, nb, nb), B2, 0, s>>>(a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, done);
+        LAUNCH(TAG_LEVELS, (k_b2m_ooo_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, done);
+        LAUNCH(TAG_LEVELS, (k_b2m_eee_3d<T>), grid3(nb, nb, nb), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, done);
     } else {  // red from magenta: Eq. Erprolr (faces), Eq. Erprolm (corners)
         const T c1 = (T)(2.0 * om[1] * hk2), c2 = (T)(4.0 * om[2] * hk2);
-        k_m2r_faces_3d<T><<<grid3(nb + 1, nb + 1, nb + 1), B2, 0, s>>>(mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, done);
-        k_m2r_corners_3d<T><<<grid3(nb, nb, nb), B2, 0, s>>>(red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, done);
+        LAUNCH(TAG_LEVELS, (k_m2r_faces_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, done);
+        LAUNCH(TAG_LEVELS, (k_m2r_corners_3d<T>), grid3(nb, nb, nb), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, done);
     }
 }
 
 template <typename T> void launch_coarse(mg_ctx *c, const int *done, cudaStream_t s) {
     const Level &l = c->lv[c->L];
-    k_coarse<T><<<1, 512, 0, s>>>((const T *)l.r[0], l.pitch, l.rows, l.side, c->d.dim, c->G, (T *)l.v[0], done);
+    LAUNCH(TAG_LEVELS, (k_coarse<T>), 1, 512, (const T *)l.r[0], l.pitch, l.rows, l.side, c->d.dim, c->G, (T *)l.v[0], done);
 }
 
 template <typename T>
@@ -300,7 +344,7 @@ mg_status vcycle_t(mg_ctx *c, const double *f, double *u, const int *done, bool 
         const Level &l0 = c->lv[0];
         const int n = c->d.n;
         dim3 g = c->d.dim == 2 ? grid2(n, n) : grid3(n, n, n);
-        k_add_axis<T><<<g, B2, 0, s>>>((const T *)l0.v[0], l0.pitch, l0.rows, n, c->d.dim, u, c->d.pitch, n + 2, done);
+        LAUNCH(TAG_FINEST_UP, (k_add_axis<T>), g, B2, (const T *)l0.v[0], l0.pitch, l0.rows, n, c->d.dim, u, c->d.pitch, n + 2, done);
     }
     CKL("vcycle launch");
     return MG_OK;
@@ -348,6 +392,7 @@ const char *mg_last_error(void) { return g_last_error; }
 mg_status mg_destroy(mg_ctx *c) {
     if (!c) return MG_OK;
     cudaDeviceSynchronize();
+    for (auto e : c->pev) cudaEventDestroy(e);
     cudaFree(c->pool);
     cudaFree(c->part);
     cudaFree(c->ctl);
@@ -426,7 +471,7 @@ mg_status mg_residual(mg_ctx *c, const double *f, const double *u, double h, int
     else launch_residual<float>(c, f, u, r, false, nullptr, s);
     CKL("mg_residual");
     if (norm2) {
-        k_sum_to<<<1, 1024, 0, s>>>(c->part, c->max_blocks, c->scal);
+        LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, c->max_blocks, c->scal);
         CKL("mg_residual norm");
         CK(cudaMemcpyAsync(norm2, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -463,15 +508,16 @@ static mg_status level_io(mg_ctx *c, int level, int which, double *grid, int to_
     if (!c || !grid || level < 0 || level > c->L || (which != 0 && which != 1)) return MG_EINVAL;
     const Level &l = c->lv[level];
     void *const *arr = which == 0 ? l.r : l.v;
-    const int s = l.side, dim = c->d.dim;
-    dim3 g = dim == 2 ? grid2(s, s) : grid3(s, s, s);
+    const int side = l.side, dim = c->d.dim;
+    cudaStream_t s = S(stream);
+    dim3 g = dim == 2 ? grid2(side, side) : grid3(side, side, side);
     void *c0 = arr[0], *c1 = l.ncos > 1 ? arr[1] : nullptr, *c2 = l.ncos > 2 ? arr[2] : nullptr,
          *c3 = l.ncos > 3 ? arr[3] : nullptr;
     if (c->d.precision == MG_FP64)
-        k_level_io<double><<<g, B2, 0, S(stream)>>>(dim, l.kind, s, grid, (double *)c0, (double *)c1, (double *)c2,
+        LAUNCH(TAG_CONTROL, (k_level_io<double>), g, B2, dim, l.kind, side, grid, (double *)c0, (double *)c1, (double *)c2,
                                                     (double *)c3, l.pitch, l.rows, to_level);
     else
-        k_level_io<float><<<g, B2, 0, S(stream)>>>(dim, l.kind, s, grid, (float *)c0, (float *)c1, (float *)c2,
+        LAUNCH(TAG_CONTROL, (k_level_io<float>), g, B2, dim, l.kind, side, grid, (float *)c0, (float *)c1, (float *)c2,
                                                    (float *)c3, l.pitch, l.rows, to_level);
     CKL("mg_level_io");
     return MG_OK;
@@ -497,11 +543,11 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
     cudaStream_t s = S(stream);
     const bool fp64 = c->d.precision == MG_FP64;
     const int *done = &c->ctl->done;
-    k_ctrl_init<<<1, 1, 0, s>>>(c->ctl, rtol, max_cycles);
+    LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
     // ||r(u=0)||^2
     if (fp64) launch_residual<double>(c, f, u, nullptr, true, nullptr, s);
     else launch_residual<float>(c, f, u, nullptr, true, nullptr, s);
-    k_sum_to<<<1, 1024, 0, s>>>(c->part, c->max_blocks, &c->ctl->f2);
+    LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, c->max_blocks, &c->ctl->f2);
     CKL("mg_solve init");
     Ctrl host{};
     const int chunk = 4;
@@ -510,12 +556,13 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
             const int first = (cyc + q) == 0;
             if (fp64) launch_residual<double>(c, f, u, nullptr, false, first ? nullptr : done, s);
             else launch_residual<float>(c, f, u, nullptr, false, first ? nullptr : done, s);
-            k_ctrl<<<1, 1024, 0, s>>>(c->part, c->max_blocks, c->ctl, c->hist, first);
+            LAUNCH(TAG_CONTROL, (k_ctrl), 1, 1024, c->part, c->max_blocks, c->ctl, c->hist, first);
             mg_status st = fp64 ? vcycle_t<double>(c, f, u, done, false, s) : vcycle_t<float>(c, f, u, done, false, s);
             if (st != MG_OK) return st;
         }
         CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        probe_collect(c);
         if (host.done) break;
     }
     if (cycles_out) *cycles_out = host.cycles;
@@ -526,6 +573,34 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
     }
     if (host.status == -5) return MG_EDIVERGED;
     if (host.status == -4 || !host.done) return MG_ENOCONV;
+    return MG_OK;
+}
+
+mg_status mg_launch_count(const mg_ctx *c, long long *launches) {
+    if (!c || !launches) return MG_EINVAL;
+    *launches = c->launches;
+    return MG_OK;
+}
+
+mg_status mg_probe_set(mg_ctx *c, int family) {
+    if (!c || family < -1 || family > TAG_CONTROL) return MG_EINVAL;
+    if (family >= 0 && c->pev.empty()) {
+        c->pev.resize(1024);
+        for (auto &e : c->pev) CK(cudaEventCreate(&e));
+    }
+    c->probe_tag = family;
+    c->pev_used = 0;
+    c->probe_n = 0;
+    c->probe_ms = 0.0;
+    return MG_OK;
+}
+
+mg_status mg_probe_read(mg_ctx *c, long long *launches, double *ms, void *stream) {
+    if (!c) return MG_EINVAL;
+    CK(cudaStreamSynchronize(S(stream)));
+    probe_collect(c);
+    if (launches) *launches = c->probe_n;
+    if (ms) *ms = c->probe_ms;
     return MG_OK;
 }
 

@@ -209,7 +209,7 @@ def test_solve_fp64_matches_oracle(dim, n, hier):
         ug, it_g, rel_g, hist_g = c.solve(T(f), rtol=1e-10, max_cycles=100)
     assert it_g == it_o
     assert rel_g <= 1e-10
-    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-6)
+    np.testing.assert_allclose(hist_g, hist_o, rtol=1e-6, atol=1e-13)
     assert np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo) <= TOL
 
 
