@@ -166,6 +166,33 @@ mg_status mg_launch_count(const mg_ctx *ctx, long long *launches);
 mg_status mg_probe_set(mg_ctx *ctx, int family);
 mg_status mg_probe_read(mg_ctx *ctx, long long *launches, double *ms, void *stream);
 
+/* Residual and squared norm without any device allocation (the paper has no
+ * counterpart; this serves callers that may not allocate device memory: code
+ * inside another framework's allocator or fixed memory budget, latency-bound
+ * loops where cudaMalloc/cudaFree could stall the device, plug-ins that keep
+ * no workspace between calls).  No context is needed.
+ *   r = f - L_h u exactly as mg_residual computes it for the same order
+ *   (5/7-point, or Eq. Efos2 / Eq. Efos4 with order 4); h must be 1/(n+1).
+ *   f, u      caller device arrays, full grid (n+2)^dim, row pitch `pitch`
+ *   r         caller device array (same layout) receiving r on the interior
+ *             points, or NULL
+ *   norm2     caller DEVICE pointer to one double receiving sum(r^2) over the
+ *             interior, or NULL; written in stream order (no host sync)
+ * Scratch: one partial sum per 256-thread block lives in a static device
+ * array of 65536 doubles (512 KiB, resident on every GPU that loads this
+ * library until the process exits).  Sizes needing more -- 2D n > 4095, 3D
+ * n > 255 -- are rejected with MG_EINVAL before anything is launched, as are
+ * other invalid arguments.  Every call overwrites the partial sums it uses
+ * before reading them, so no state carries over between calls; but all calls
+ * on one device share the array, so calls that may overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and keeps it; make that first call before any stream
+ * capture.  Allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+mg_status mg_residual_noalloc(int dim, int n, int pitch, double h, int order, const double *f, const double *u,
+                              double *r, double *norm2, void *stream);
+
 /* Message for a status, and the last CUDA error text of this process. */
 const char *mg_strerror(mg_status status);
 const char *mg_last_error(void);

@@ -44,6 +44,7 @@ SIGNATURES = {
     "mg_launch_count": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "mg_probe_set": (_i, [_vp, _i]),
     "mg_probe_read": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _dp, _vp]),
+    "mg_residual_noalloc": (_i, [_i, _i, _i, _d, _i, _vp, _vp, _vp, _vp, _vp]),
     "mg_strerror": (ctypes.c_char_p, [_i]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
