@@ -39,7 +39,7 @@ RTOL = 1e-10
 WORKLOAD = "2D unit square, h=1/4096 (4095^2 = 16.8M unknowns), f ~ U[-1,1] seed 1, zero Dirichlet; " \
            "diagonal V-cycle (p=1.052), mixed FP64/FP32, solve from u=0 to 1e-10 relative residual"
 
-# Algorithmic cost of the probed kernel family per finest unknown (see DESIGN.md):
+# Algorithmic cost of the probed kernel family per finest unknown:
 # family 0 = finest-grid residual (+ squared norm): reads u, f (FP64), writes r.
 PROBE = {
     "family": 0,
