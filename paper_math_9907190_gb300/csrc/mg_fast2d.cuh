@@ -1,0 +1,437 @@
+// mg_fast2d.cuh -- fused 2D kernels of the diagonal V-cycle (Section 2).
+//
+// Per cycle: k_res0_2d (finest residual, the only FP64 stencil work),
+// k_down_pair_2d (green -> red -> blue restriction of one pair, Eq. Erest2r
+// then Eq. Erest2b, in a shared-memory tile), k_coarse_cta_2d (all pairs below
+// a size cut-off, the coarsest solve and their Jacobi prolongation in one
+// thread block, shared memory only), and k_up_pair_2d (blue -> red -> green
+// Jacobi prolongation of one pair, Eq. Eajacr, Eq. Eajacb and the green-red
+// sweep, in a shared-memory tile; on the finest pair fused with u += v).
+//
+// Tiles are indexed by coset cells: cell (a,b) of a pair whose green grid has
+// side n = 2nb+1 holds the green points (2a,2b) EE, (2a+1,2b) OE, (2a,2b+1) EO
+// and (2a+1,2b+1) OO; a, b in [0, nb].  Out-of-range neighbours read zero
+// (the Dirichlet ring).
+#pragma once
+#include "mg_stages.cuh"
+
+namespace mg {
+
+
+template <typename T> struct SqAcc;                     // per-thread sum of r^2
+template <> struct SqAcc<float> {                       // mixed: FP32 squares
+    float s = 0.f;
+    __device__ void add(double r) { const float q = (float)r; s = fmaf(q, q, s); }
+    __device__ double get() const { return (double)s; }
+};
+template <> struct SqAcc<double> {
+    double s = 0.0;
+    __device__ void add(double r) { s = fma(r, r, s); }
+    __device__ double get() const { return s; }
+};
+
+constexpr int RES_ROWS = 8;  // rows per thread of the residual kernel
+
+// Finest-grid residual, 2D.  Block 32x8 threads; a thread marches RES_ROWS
+// rows down one column keeping the vertical neighbours in registers.
+//   ORDER 2: r = f - (sum4 u - 4u)/h^2                            (Eq. Evpois)
+//   ORDER 4: r = ft - (4 sum4axis u + sum4diag u - 20u)/(6h^2)    (Eq. Efos2)
+//            with ft = (8f + sum4 f)/12 precomputed once per solve.
+// Writes r in the level precision and the block's sum of r^2 to part[].
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(256) k_res0_2d(const double *__restrict__ f, const double *__restrict__ u,
+                                                 int up, int n, double ih2, A2<T> r, double *part,
+                                                 const int *done) {
+    __shared__ double sh[32];
+    if (stop(done)) return;
+    const int i = blockIdx.x * 32 + threadIdx.x + 1;
+    const int j0 = (blockIdx.y * 8 + threadIdx.y) * RES_ROWS + 1;
+    SqAcc<T> acc;
+    if (i <= n && j0 <= n) {
+        const double *uc = u + (size_t)j0 * up + i;
+        const double *fc = f + (size_t)j0 * up + i;
+        double um = uc[-up], u0 = uc[0];
+        double wm = 0, w0 = 0, em = 0, e0 = 0;  // diagonal neighbours (order 4)
+        if (ORDER == 4) { wm = uc[-up - 1]; em = uc[-up + 1]; w0 = uc[-1]; e0 = uc[1]; }
+#pragma unroll
+        for (int q = 0; q < RES_ROWS; q++) {
+            if (j0 + q > n) break;
+            const double upn = uc[up];
+            double res;
+            if (ORDER == 2) {
+                const double s = (uc[-1] + uc[1]) + (um + upn);
+                res = fma(-ih2, fma(-4.0, u0, s), fc[0]);
+            } else {
+                const double wp = uc[up - 1], ep = uc[up + 1];
+                const double ax = (w0 + e0) + (um + upn);
+                const double dg = (wm + em) + (wp + ep);
+                res = fma(-ih2 * (1.0 / 6.0), fma(-20.0, u0, fma(4.0, ax, dg)), fc[0]);
+                wm = w0; em = e0; w0 = wp; e0 = ep;
+            }
+            r(i, j0 + q) = (T)res;
+            acc.add(res);
+            um = u0; u0 = upn;
+            uc += up; fc += up;
+        }
+    }
+    double s = block_sum(acc.get(), sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x + gridDim.x * blockIdx.y] = s;
+}
+
+// ft = (8f + sum4 f)/12 on the interior (order-4 right-hand side of Eq. Efos2)
+__global__ void k_rhs4_2d(const double *__restrict__ f, int up, int n, double *ft) {
+    MG_IDX2 const int i = tx + 1, j = ty + 1;
+    if (i > n || j > n) return;
+    const size_t c = (size_t)j * up + i;
+    ft[c] = (8.0 * f[c] + ((f[c - 1] + f[c + 1]) + (f[c - up] + f[c + up]))) * (1.0 / 12.0);
+}
+
+// ---------------------------------------------------------------------------
+// pair restriction: green -> red (Eq. Erest2r) -> blue (Eq. Erest2b)
+// ---------------------------------------------------------------------------
+constexpr int DTA = 32, DTB = 16;  // cells per tile (x, y); block 32x8
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_down_pair_2d(A2<const T> g, A2<T> ee, A2<T> oo, A2<T> blue, int nb,
+                                                      const int *done) {
+    constexpr int GX = 2 * DTA + 3, GY = 2 * DTB + 3;  // green x in [2a0-2, 2a0+2DTA]
+    constexpr int OX = DTA + 1, OY = DTB + 1;          // OO cells a in [a0-1, a0+DTA)
+    __shared__ T sg[GY][GX];
+    __shared__ T so[OY][OX + 1];
+    if (stop(done)) return;
+    const int a0 = blockIdx.x * DTA, b0 = blockIdx.y * DTB;
+    const int n = 2 * nb + 1;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    for (int q = tid; q < GX * GY; q += 256) {
+        const int x = 2 * a0 - 2 + q % GX, y = 2 * b0 - 2 + q / GX;
+        sg[q / GX][q % GX] = (x >= 0 && x <= n + 1 && y >= 0 && y <= n + 1) ? g(x, y) : T(0);
+    }
+    __syncthreads();
+    // OO(c,d) at green (2c+1, 2d+1) -> smem index (2c+1) - (2a0-2) = 2(c-a0)+3
+    for (int q = tid; q < OX * OY; q += 256) {
+        const int cx = q % OX, cy = q / OX;  // c = a0-1+cx
+        const int c = a0 - 1 + cx, d = b0 - 1 + cy;
+        T v = T(0);
+        if (c >= 0 && c <= nb && d >= 0 && d <= nb) {
+            const int x = 2 * cx + 1, y = 2 * cy + 1;
+            v = (T(4) * sg[y][x] + (sg[y][x - 1] + sg[y][x + 1]) + (sg[y - 1][x] + sg[y + 1][x])) * T(0.125);
+            if (cx >= 1 && cy >= 1) oo(c, d) = v;
+        }
+        so[cy][cx] = v;
+    }
+    __syncthreads();
+    for (int q = tid; q < DTA * DTB; q += 256) {
+        const int ax = q % DTA, by = q / DTA;
+        const int a = a0 + ax, b = b0 + by;
+        if (a < 1 || a > nb || b < 1 || b > nb) continue;
+        const int x = 2 * ax + 2, y = 2 * by + 2;  // green (2a, 2b)
+        const T e = (T(4) * sg[y][x] + (sg[y][x - 1] + sg[y][x + 1]) + (sg[y - 1][x] + sg[y + 1][x])) * T(0.125);
+        ee(a, b) = e;
+        // diagonal red neighbours OO(a-1..a, b-1..b) = so[by..by+1][ax..ax+1]
+        blue(a, b) = (T(4) * e + (so[by][ax] + so[by][ax + 1]) + (so[by + 1][ax] + so[by + 1][ax + 1])) * T(0.125);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pair prolongation: blue -> red (Eq. Eajacr, Eq. Eajacb) -> green (the
+// green-red sweep); FINEST: u += v instead of storing v
+// ---------------------------------------------------------------------------
+constexpr int UTA = 32, UTB = 16;
+
+template <typename T> struct UpSmem {
+    T b[UTB + 5][UTA + 5];     // blue v, cells [a0-2, a0+UTA+2]
+    T roo[UTB + 4][UTA + 4];   // OO cells [a0-2, a0+UTA+1]
+    T ree[UTB + 3][UTA + 3];   // EE cells [a0-1, a0+UTA+1]
+    T voo[UTB + 4][UTA + 4];
+    T vee[UTB + 3][UTA + 3];
+    T rg[2 * UTB + 4][2 * UTA + 4];  // green r, x in [2a0-2, 2a0+2UTA+1]
+    T voe[UTB + 2][UTA + 2];   // F cells [a0-1, a0+UTA]
+    T veo[UTB + 2][UTA + 2];
+};
+
+template <typename T, bool FINEST>
+__global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T> ree, A2<const T> roo,
+                                                    A2<const T> rg, A2<T> vg, double *u, int up, int nb,
+                                                    T c2, T c1, const int *done) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    UpSmem<T> &S = *reinterpret_cast<UpSmem<T> *>(smraw);
+    if (stop(done)) return;
+    const int a0 = blockIdx.x * UTA, b0 = blockIdx.y * UTB;
+    const int n = 2 * nb + 1;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    // loads
+    for (int q = tid; q < (UTA + 5) * (UTB + 5); q += 256) {
+        const int x = q % (UTA + 5), y = q / (UTA + 5);
+        const int a = a0 - 2 + x, b = b0 - 2 + y;
+        S.b[y][x] = (a >= 0 && a <= nb + 1 && b >= 0 && b <= nb + 1) ? blue(a, b) : T(0);
+    }
+    for (int q = tid; q < (UTA + 4) * (UTB + 4); q += 256) {
+        const int x = q % (UTA + 4), y = q / (UTA + 4);
+        const int a = a0 - 2 + x, b = b0 - 2 + y;
+        S.roo[y][x] = (a >= 0 && a <= nb && b >= 0 && b <= nb) ? roo(a, b) : T(0);
+    }
+    for (int q = tid; q < (UTA + 3) * (UTB + 3); q += 256) {
+        const int x = q % (UTA + 3), y = q / (UTA + 3);
+        const int a = a0 - 1 + x, b = b0 - 1 + y;
+        S.ree[y][x] = (a >= 1 && a <= nb && b >= 1 && b <= nb) ? ree(a, b) : T(0);
+    }
+    for (int q = tid; q < (2 * UTA + 4) * (2 * UTB + 4); q += 256) {
+        const int x = q % (2 * UTA + 4), y = q / (2 * UTA + 4);
+        const int gx = 2 * a0 - 2 + x, gy = 2 * b0 - 2 + y;
+        S.rg[y][x] = (gx >= 1 && gx <= n && gy >= 1 && gy <= n) ? rg(gx, gy) : T(0);
+    }
+    __syncthreads();
+    // red points not blue: OO(c,d), c in [a0-2, a0+UTA+1]; smem x = c - a0 + 2 in voo and in b
+    for (int q = tid; q < (UTA + 4) * (UTB + 4); q += 256) {
+        const int x = q % (UTA + 4), y = q / (UTA + 4);
+        const int c = a0 - 2 + x, d = b0 - 2 + y;
+        T v = T(0);
+        if (c >= 0 && c <= nb && d >= 0 && d <= nb)
+            v = ((S.b[y][x] + S.b[y][x + 1]) + (S.b[y + 1][x] + S.b[y + 1][x + 1]) - c2 * S.roo[y][x]) * T(0.25);
+        S.voo[y][x] = v;
+    }
+    __syncthreads();
+    // blue points refined: EE(a,b), a in [a0-1, a0+UTA+1]; smem x = a - a0 + 1; OO(a-1) at voo x = a - a0 + 1
+    for (int q = tid; q < (UTA + 3) * (UTB + 3); q += 256) {
+        const int x = q % (UTA + 3), y = q / (UTA + 3);
+        const int a = a0 - 1 + x, b = b0 - 1 + y;
+        T v = T(0);
+        if (a >= 1 && a <= nb && b >= 1 && b <= nb)
+            v = ((S.voo[y][x] + S.voo[y][x + 1]) + (S.voo[y + 1][x] + S.voo[y + 1][x + 1]) - c2 * S.ree[y][x]) *
+                T(0.25);
+        S.vee[y][x] = v;
+    }
+    __syncthreads();
+    // green-only points: OE(a,b) at (2a+1, 2b), EO(a,b) at (2a, 2b+1); cells [a0-1, a0+UTA]
+    for (int q = tid; q < (UTA + 2) * (UTB + 2); q += 256) {
+        const int x = q % (UTA + 2), y = q / (UTA + 2);
+        const int a = a0 - 1 + x, b = b0 - 1 + y;
+        // EE(a,b) at vee[y][x]; EE(a+1,b) vee[y][x+1]; EE(a,b+1) vee[y+1][x]
+        // OO(a,b) at voo[y+1][x+1]; OO(a,b-1) voo[y][x+1]; OO(a-1,b) voo[y+1][x]
+        // green (2a+1, 2b) at rg[2y][2x+1]; (2a, 2b+1) at rg[2y+1][2x]
+        T voe = T(0), veo = T(0);
+        if (a >= 0 && a <= nb && b >= 1 && b <= nb)
+            voe = ((S.vee[y][x] + S.vee[y][x + 1]) + (S.voo[y][x + 1] + S.voo[y + 1][x + 1]) - c1 * S.rg[2 * y][2 * x + 1]) *
+                  T(0.25);
+        if (a >= 1 && a <= nb && b >= 0 && b <= nb)
+            veo = ((S.voo[y + 1][x] + S.voo[y + 1][x + 1]) + (S.vee[y][x] + S.vee[y + 1][x]) - c1 * S.rg[2 * y + 1][2 * x]) *
+                  T(0.25);
+        S.voe[y][x] = voe;
+        S.veo[y][x] = veo;
+    }
+    __syncthreads();
+    // red points of the own cells from the new green values, then store / update
+    for (int q = tid; q < UTA * UTB; q += 256) {
+        const int xa = q % UTA, yb = q / UTA;
+        const int a = a0 + xa, b = b0 + yb;
+        if (a > nb || b > nb) continue;
+        const int x = xa + 1, y = yb + 1;  // F smem index of cell (a,b)
+        // EE(a,b) at (2a,2b): OE(a-1,b), OE(a,b), EO(a,b-1), EO(a,b)
+        T vEE = T(0);
+        if (a >= 1 && b >= 1)
+            vEE = ((S.voe[y][x - 1] + S.voe[y][x]) + (S.veo[y - 1][x] + S.veo[y][x]) - c1 * S.rg[2 * y][2 * x]) * T(0.25);
+        // OO(a,b) at (2a+1,2b+1): EO(a,b), EO(a+1,b), OE(a,b), OE(a,b+1)
+        const T vOO = ((S.veo[y][x] + S.veo[y][x + 1]) + (S.voe[y][x] + S.voe[y + 1][x]) - c1 * S.rg[2 * y + 1][2 * x + 1]) *
+                      T(0.25);
+        const T vOE = S.voe[y][x], vEO = S.veo[y][x];
+        const int i = 2 * a, j = 2 * b;
+        if (FINEST) {
+            double *ur0 = u + (size_t)j * up + i;       // row 2b: (2a, 2b), (2a+1, 2b)
+            double *ur1 = ur0 + up;                     // row 2b+1
+            if (b >= 1) {
+                if (a >= 1) ur0[0] += widen(vEE);
+                ur0[1] += widen(vOE);
+            }
+            if (a >= 1) ur1[0] += widen(vEO);
+            ur1[1] += widen(vOO);
+        } else {
+            if (b >= 1) {
+                if (a >= 1) vg(i, j) = vEE;
+                vg(i + 1, j) = vOE;
+            }
+            if (a >= 1) vg(i, j + 1) = vEO;
+            vg(i + 1, j + 1) = vOO;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// coarse pairs in one thread block, all in shared memory
+// ---------------------------------------------------------------------------
+constexpr int CTA_MAX_PAIRS = 12;
+
+struct CoarsePlan2d {
+    int kc, K;                        // pairs kc..K-1 run here; level K is the coarsest grid
+    int nk[CTA_MAX_PAIRS + 1];        // green side of pair k - kc (and the coarsest)
+    int og_r[CTA_MAX_PAIRS + 1], og_v[CTA_MAX_PAIRS + 1];  // smem offsets (elements), green r / v
+    int oe_r[CTA_MAX_PAIRS], oo_r[CTA_MAX_PAIRS], oe_v[CTA_MAX_PAIRS], oo_v[CTA_MAX_PAIRS];
+    int total;                        // smem elements
+    double c2[CTA_MAX_PAIRS], c1[CTA_MAX_PAIRS];  // 2 p h_k^2 (red), p h_k^2 (green)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const T> rg_in, A2<T> vg_out,
+                                                        const double *G, const int *done) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+    if (stop(done)) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int q = tid; q < P.total; q += nt) sm[q] = T(0);
+    __syncthreads();
+    const int npair = P.K - P.kc;
+    {   // load the green residual of pair kc
+        const int n = P.nk[0];
+        A2<T> g{sm + P.og_r[0], n + 2};
+        for (int q = tid; q < n * n; q += nt) {
+            const int i = q % n + 1, j = q / n + 1;
+            g(i, j) = rg_in(i, j);
+        }
+    }
+    __syncthreads();
+    for (int p = 0; p < npair; p++) {
+        const int n = P.nk[p], nb = (n - 1) / 2;
+        A2<T> g{sm + P.og_r[p], n + 2}, ee{sm + P.oe_r[p], nb + 2}, oo{sm + P.oo_r[p], nb + 2};
+        A2<T> bl{sm + P.og_r[p + 1], nb + 2};
+        for (int q = tid; q < (nb + 1) * (nb + 1); q += nt) {  // Eq. Erest2r
+            const int a = q % (nb + 1), b = q / (nb + 1);
+            int i = 2 * a + 1, j = 2 * b + 1;
+            oo(a, b) = (T(4) * g(i, j) + (g(i - 1, j) + g(i + 1, j)) + (g(i, j - 1) + g(i, j + 1))) * T(0.125);
+            if (a >= 1 && b >= 1) {
+                i = 2 * a; j = 2 * b;
+                ee(a, b) = (T(4) * g(i, j) + (g(i - 1, j) + g(i + 1, j)) + (g(i, j - 1) + g(i, j + 1))) * T(0.125);
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < nb * nb; q += nt) {  // Eq. Erest2b
+            const int a = q % nb + 1, b = q / nb + 1;
+            bl(a, b) = (T(4) * ee(a, b) + (oo(a - 1, b - 1) + oo(a, b - 1)) + (oo(a - 1, b) + oo(a, b))) * T(0.125);
+        }
+        __syncthreads();
+    }
+    {   // exact solve on the coarsest grid
+        const int s = P.nk[npair], nn = s * s;
+        A2<T> r{sm + P.og_r[npair], s + 2}, v{sm + P.og_v[npair], s + 2};
+        for (int q = tid; q < nn; q += nt) {
+            double acc = 0.0;
+            for (int t = 0; t < nn; t++) acc += G[(size_t)q * nn + t] * (double)r(t % s + 1, t / s + 1);
+            v(q % s + 1, q / s + 1) = (T)acc;
+        }
+    }
+    __syncthreads();
+    for (int p = npair - 1; p >= 0; p--) {
+        const int n = P.nk[p], nb = (n - 1) / 2;
+        A2<T> rgr{sm + P.og_r[p], n + 2}, vgr{sm + P.og_v[p], n + 2};
+        A2<T> ree{sm + P.oe_r[p], nb + 2}, roo{sm + P.oo_r[p], nb + 2};
+        A2<T> vee{sm + P.oe_v[p], nb + 2}, voo{sm + P.oo_v[p], nb + 2};
+        A2<T> vbl{sm + P.og_v[p + 1], nb + 2};
+        const T c2 = (T)P.c2[p], c1 = (T)P.c1[p];
+        for (int q = tid; q < (nb + 1) * (nb + 1); q += nt) {  // Eq. Eajacr
+            const int a = q % (nb + 1), b = q / (nb + 1);
+            voo(a, b) = ((vbl(a, b) + vbl(a + 1, b)) + (vbl(a, b + 1) + vbl(a + 1, b + 1)) - c2 * roo(a, b)) * T(0.25);
+        }
+        __syncthreads();
+        for (int q = tid; q < nb * nb; q += nt) {  // Eq. Eajacb
+            const int a = q % nb + 1, b = q / nb + 1;
+            vee(a, b) = ((voo(a - 1, b - 1) + voo(a, b - 1)) + (voo(a - 1, b) + voo(a, b)) - c2 * ree(a, b)) * T(0.25);
+        }
+        __syncthreads();
+        for (int q = tid; q < n * n; q += nt) {  // green-only points
+            const int i = q % n + 1, j = q / n + 1;
+            if (((i + j) & 1) == 0) continue;
+            auto red = [&](int x, int y) { return (x & 1) ? voo(x >> 1, y >> 1) : vee(x >> 1, y >> 1); };
+            vgr(i, j) = ((red(i - 1, j) + red(i + 1, j)) + (red(i, j - 1) + red(i, j + 1)) - c1 * rgr(i, j)) * T(0.25);
+        }
+        __syncthreads();
+        for (int q = tid; q < n * n; q += nt) {  // red points
+            const int i = q % n + 1, j = q / n + 1;
+            if ((i + j) & 1) continue;
+            vgr(i, j) = ((vgr(i - 1, j) + vgr(i + 1, j)) + (vgr(i, j - 1) + vgr(i, j + 1)) - c1 * rgr(i, j)) * T(0.25);
+        }
+        __syncthreads();
+    }
+    {
+        const int n = P.nk[0];
+        A2<T> g{sm + P.og_v[0], n + 2};
+        for (int q = tid; q < n * n; q += nt) {
+            const int i = q % n + 1, j = q / n + 1;
+            vg_out(i, j) = g(i, j);
+        }
+    }
+}
+
+}  // namespace mg
+
+namespace mg {
+
+constexpr int RES3_PLANES = 8;  // planes per thread of the 3D residual kernel
+
+// Finest-grid residual, 3D.  Block 32x8 threads over (x, y); a thread marches
+// RES3_PLANES planes in z keeping the z neighbours in registers.
+//   ORDER 2: r = f - (sum6 u - 6u)/h^2
+//   ORDER 4: r = ft - (2 sum6 u + sum12 u - 24u)/(6h^2)   (Eq. Efos4, ft precomputed)
+template <typename T, int ORDER>
+__global__ void __launch_bounds__(256) k_res0_3d(const double *__restrict__ f, const double *__restrict__ u,
+                                                 int up, int n, double ih2, A3<T> r, double *part,
+                                                 const int *done) {
+    __shared__ double sh[32];
+    if (stop(done)) return;
+    const int i = blockIdx.x * 32 + threadIdx.x + 1, j = blockIdx.y * 8 + threadIdx.y + 1;
+    const int k0 = blockIdx.z * RES3_PLANES + 1;
+    const size_t pl = (size_t)up * (n + 2);
+    SqAcc<T> acc;
+    if (i <= n && j <= n) {
+        const double *uc = u + k0 * pl + (size_t)j * up + i;
+        const double *fc = f + k0 * pl + (size_t)j * up + i;
+        double ud = uc[-(long)pl], u0 = uc[0];
+#pragma unroll
+        for (int q = 0; q < RES3_PLANES; q++) {
+            if (k0 + q > n) break;
+            const double uu = uc[pl];
+            double res;
+            if (ORDER == 2) {
+                const double s = ((uc[-1] + uc[1]) + (uc[-up] + uc[up])) + (ud + uu);
+                res = fma(-ih2, fma(-6.0, u0, s), fc[0]);
+            } else {
+                const double ax = ((uc[-1] + uc[1]) + (uc[-up] + uc[up])) + (ud + uu);
+                const double ed = ((uc[-up - 1] + uc[-up + 1]) + (uc[up - 1] + uc[up + 1])) +
+                                  ((uc[-(long)pl - up] + uc[-(long)pl + up]) + (uc[pl - up] + uc[pl + up])) +
+                                  ((uc[-(long)pl - 1] + uc[-(long)pl + 1]) + (uc[pl - 1] + uc[pl + 1]));
+                res = fma(-ih2 * (1.0 / 6.0), fma(-24.0, u0, fma(2.0, ax, ed)), fc[0]);
+            }
+            r(i, j, k0 + q) = (T)res;
+            acc.add(res);
+            ud = u0; u0 = uu;
+            uc += pl; fc += pl;
+        }
+    }
+    double s = block_sum(acc.get(), sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = s;
+}
+
+// ft = (6f + sum6 f)/12 on the interior (order-4 right-hand side of Eq. Efos4)
+__global__ void k_rhs4_3d(const double *__restrict__ f, int up, int n, double *ft) {
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
+    if (i > n || j > n) return;
+    const size_t pl = (size_t)up * (n + 2);
+    const size_t c = k * pl + (size_t)j * up + i;
+    ft[c] = (6.0 * f[c] + ((f[c - 1] + f[c + 1]) + (f[c - up] + f[c + up]) + (f[c - pl] + f[c + pl]))) * (1.0 / 12.0);
+}
+
+// finest 3D level, second half of the green-red sweep (Eq. Egprolr) fused with
+// u += v; the f32 -> f64 widening uses integer operations
+template <typename T>
+__global__ void k_r2g_c_upd_fast_3d(A3<const T> rg, A3<const T> vg, double *u, int up, int urows, int n, T cc,
+                                    const int *done) {
+    if (stop(done)) return;
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
+    if (i > n || j > n || k > n) return;
+    T v;
+    if ((i + j + k) & 1) v = vg(i, j, k);
+    else
+        v = ((vg(i - 1, j, k) + vg(i + 1, j, k)) + (vg(i, j - 1, k) + vg(i, j + 1, k)) +
+             (vg(i, j, k - 1) + vg(i, j, k + 1)) - cc * rg(i, j, k)) * T(1.0 / 6.0);
+    u[((size_t)k * urows + j) * up + i] += widen(v);
+}
+
+}  // namespace mg

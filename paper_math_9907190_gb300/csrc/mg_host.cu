@@ -10,6 +10,7 @@
 
 #include "../../include/diagmg.h"
 #include "mg_stages.cuh"
+#include "mg_fast2d.cuh"
 
 using namespace mg;
 
@@ -81,6 +82,23 @@ struct mg_ctx {
     int pev_used = 0;
     long long probe_n = 0;
     double probe_ms = 0.0;
+    // fused 2D diagonal path
+    bool fast2d = false;
+    int kc = 0;                 // first pair run by the coarse thread block
+    CoarsePlan2d plan2d{};
+    size_t plan_bytes = 0;
+    double *ft = nullptr;       // order-4 right-hand side (caller pitch), FP64
+    int nparts = 0;             // partial sums written by the last residual
+    // the solver graph (prefix + device-driven loop over V-cycles), cached per arguments
+    bool capturing = false;
+    cudaStream_t cs1 = nullptr, cs2 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    const double *g_f = nullptr;
+    double *g_u = nullptr;
+    double g_rtol = -1.0;
+    int g_max = -1;
+    long long g_prefix_kernels = 0, g_body_kernels = 0;
 };
 
 namespace {
@@ -170,7 +188,7 @@ struct Launch {
     int slot = -1;
     Launch(mg_ctx *c_, int tag, cudaStream_t s_) : c(c_), s(s_) {
         c->launches++;
-        if (c->probe_tag == tag && 2 * c->pev_used + 1 < (int)c->pev.size()) {
+        if (!c->capturing && c->probe_tag == tag && 2 * c->pev_used + 1 < (int)c->pev.size()) {
             slot = c->pev_used++;
             cudaEventRecord(c->pev[2 * slot], s);
         }
@@ -183,6 +201,12 @@ struct Launch {
     do {                                               \
         Launch l_(c, tag, s);                          \
         kern<<<grid, block, 0, s>>>(__VA_ARGS__);      \
+    } while (0)
+
+#define LAUNCH_SMEM(tag, kern, grid, block, smem, ...) \
+    do {                                               \
+        Launch l_(c, tag, s);                          \
+        kern<<<grid, block, smem, s>>>(__VA_ARGS__);   \
     } while (0)
 
 // accumulate the probe events of completed work (call after a stream sync)
@@ -305,7 +329,7 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
             else
                 LAUNCH(TAG_LEVELS, (k_r2g_f_3d<T>), grid3(n, n, n), B2, red3v<const T>(b.v, b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
             if (u)
-                LAUNCH(TAG_FINEST_UP, (k_r2g_c_upd_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<const T>(a.v[0], a), u, c->d.pitch, n + 2, n, cc, done);
+                LAUNCH(TAG_FINEST_UP, (k_r2g_c_upd_fast_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<const T>(a.v[0], a), u, c->d.pitch, n + 2, n, cc, done);
             else
                 LAUNCH(TAG_LEVELS, (k_r2g_c_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
         }
@@ -334,9 +358,115 @@ template <typename T> void launch_coarse(mg_ctx *c, const int *done, cudaStream_
     LAUNCH(TAG_LEVELS, (k_coarse<T>), 1, 512, (const T *)l.r[0], l.pitch, l.rows, l.side, c->d.dim, c->G, (T *)l.v[0], done);
 }
 
+// ---- fused 2D diagonal path ------------------------------------------------
+
+void plan_fast2d(mg_ctx *c) {
+    c->fast2d = c->d.dim == 2 && c->d.hierarchy == MG_DIAG;
+    if (!c->fast2d) return;
+    // pairs whose green grid has side <= 63 run in one thread block
+    int kc = 0;
+    while (kc < c->K && c->lv[2 * kc].side > 63) kc++;
+    c->kc = kc;
+    CoarsePlan2d &P = c->plan2d;
+    P = CoarsePlan2d{};
+    P.kc = kc;
+    P.K = c->K;
+    int off = 0;
+    auto take = [&](int elems) { int o = off; off += (elems + 3) / 4 * 4; return o; };
+    const int npair = c->K - kc;
+    for (int p = 0; p <= npair; p++) {
+        const int n = c->lv[2 * (kc + p)].side;
+        P.nk[p] = n;
+        P.og_r[p] = take((n + 2) * (n + 2));
+        P.og_v[p] = take((n + 2) * (n + 2));
+        if (p < npair) {
+            const int nb = (n - 1) / 2, e = (nb + 2) * (nb + 2);
+            P.oe_r[p] = take(e); P.oo_r[p] = take(e); P.oe_v[p] = take(e); P.oo_v[p] = take(e);
+            const double hk = c->h * (double)(1 << (kc + p));
+            P.c2[p] = 2.0 * c->d.omega[0] * hk * hk;
+            P.c1[p] = c->d.omega[0] * hk * hk;
+        }
+    }
+    P.total = off;
+    c->plan_bytes = (size_t)off * c->esz;
+}
+
+// finest residual for every configuration: column (2D) / plane (3D) marching,
+// FP64 stencil, level-precision output, FP32 squares in mixed precision
+template <typename T> int launch_res_fast(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
+    const int n = c->d.n;
+    const Level &l0 = c->lv[0];
+    const double ih2 = 1.0 / (c->h * c->h);
+    const double *fr = c->d.order == 4 ? c->ft : f;
+    dim3 g;
+    if (c->d.dim == 2) {
+        g = dim3((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
+        if (c->d.order == 2)
+            LAUNCH(TAG_RESIDUAL, (k_res0_2d<T, 2>), g, B2, fr, u, c->d.pitch, n, ih2, a2<T>(l0.r[0], l0), c->part, done);
+        else
+            LAUNCH(TAG_RESIDUAL, (k_res0_2d<T, 4>), g, B2, fr, u, c->d.pitch, n, ih2, a2<T>(l0.r[0], l0), c->part, done);
+    } else {
+        g = dim3((n + 31) / 32, (n + 7) / 8, (n + RES3_PLANES - 1) / RES3_PLANES);
+        if (c->d.order == 2)
+            LAUNCH(TAG_RESIDUAL, (k_res0_3d<T, 2>), g, B2, fr, u, c->d.pitch, n, ih2, a3<T>(l0.r[0], l0), c->part, done);
+        else
+            LAUNCH(TAG_RESIDUAL, (k_res0_3d<T, 4>), g, B2, fr, u, c->d.pitch, n, ih2, a3<T>(l0.r[0], l0), c->part, done);
+    }
+    c->nparts = (int)(g.x * g.y * g.z);
+    return c->nparts;
+}
+
+// order-4 right-hand side (computed once per solve / per mg_vcycle call)
+void launch_rhs4(mg_ctx *c, const double *f, cudaStream_t s) {
+    const int n = c->d.n;
+    if (c->d.dim == 2) LAUNCH(TAG_CONTROL, (k_rhs4_2d), grid2(n, n), B2, f, c->d.pitch, n, c->ft);
+    else LAUNCH(TAG_CONTROL, (k_rhs4_3d), grid3(n, n, n), B2, f, c->d.pitch, n, c->ft);
+}
+
+template <typename T> void vcycle_fast2d(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
+    for (int k = 0; k < c->kc; k++) {
+        const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
+        const int nb = r.nb;
+        dim3 grid((nb + DTA) / DTA, (nb + DTB) / DTB, 1);
+        LAUNCH(TAG_LEVELS, (k_down_pair_2d<T>), grid, B2, a2<const T>(g.r[0], g), a2<T>(r.r[0], r), a2<T>(r.r[1], r),
+               a2<T>(b.r[0], b), nb, done);
+    }
+    {
+        const Level &g = c->lv[2 * c->kc];
+        LAUNCH_SMEM(TAG_LEVELS, (k_coarse_cta_2d<T>), 1, 1024, c->plan_bytes, c->plan2d, a2<const T>(g.r[0], g),
+                    a2<T>(g.v[0], g), c->G, done);
+    }
+    for (int k = c->kc - 1; k >= 0; k--) {
+        const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
+        const int nb = r.nb;
+        const double hk = spacing(c, g), p = c->d.omega[0];
+        const T c2 = (T)(2.0 * p * hk * hk), c1 = (T)(p * hk * hk);
+        dim3 grid((nb + UTA) / UTA, (nb + UTB) / UTB, 1);
+        if (k == 0)
+            LAUNCH_SMEM(TAG_FINEST_UP, (k_up_pair_2d<T, true>), grid, B2, sizeof(UpSmem<T>), a2<const T>(b.v[0], b),
+                        a2<const T>(r.r[0], r), a2<const T>(r.r[1], r), a2<const T>(g.r[0], g), a2<T>(g.v[0], g), u,
+                        c->d.pitch, nb, c2, c1, done);
+        else
+            LAUNCH_SMEM(TAG_LEVELS, (k_up_pair_2d<T, false>), grid, B2, sizeof(UpSmem<T>), a2<const T>(b.v[0], b),
+                        a2<const T>(r.r[0], r), a2<const T>(r.r[1], r), a2<const T>(g.r[0], g), a2<T>(g.v[0], g), u,
+                        c->d.pitch, nb, c2, c1, done);
+    }
+    if (c->kc == 0) {  // the whole hierarchy ran in the coarse block: apply v to u
+        const Level &l0 = c->lv[0];
+        const int n = c->d.n;
+        LAUNCH(TAG_FINEST_UP, (k_add_axis<T>), grid2(n, n), B2, (const T *)l0.v[0], l0.pitch, l0.rows, n, 2, u,
+               c->d.pitch, n + 2, done);
+    }
+}
+
 template <typename T>
 mg_status vcycle_t(mg_ctx *c, const double *f, double *u, const int *done, bool with_residual, cudaStream_t s) {
-    if (with_residual) launch_residual<T>(c, f, u, nullptr, false, done, s);
+    if (with_residual) launch_res_fast<T>(c, f, u, done, s);
+    if (c->fast2d) {
+        vcycle_fast2d<T>(c, u, done, s);
+        CKL("vcycle launch");
+        return MG_OK;
+    }
     for (int l = 0; l < c->L; l++) launch_restrict<T>(c, l, done, s);
     launch_coarse<T>(c, done, s);
     for (int l = c->L - 1; l >= 0; l--) launch_prolong<T>(c, l, c->d.omega, l == 0 ? u : nullptr, done, s);
@@ -393,12 +523,17 @@ mg_status mg_destroy(mg_ctx *c) {
     if (!c) return MG_OK;
     cudaDeviceSynchronize();
     for (auto e : c->pev) cudaEventDestroy(e);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->cs1) cudaStreamDestroy(c->cs1);
+    if (c->cs2) cudaStreamDestroy(c->cs2);
     cudaFree(c->pool);
     cudaFree(c->part);
     cudaFree(c->ctl);
     cudaFree(c->hist);
     cudaFree(c->G);
     cudaFree(c->scal);
+    cudaFree(c->ft);
     delete c;
     return MG_OK;
 }
@@ -426,6 +561,30 @@ mg_status mg_create(mg_ctx **out, const mg_desc *d) {
         for (int q = 0; q < l.ncos; q++) { l.v[q] = p; p += bytes; }
     }
     c->max_blocks = residual_blocks(c);
+    plan_fast2d(c);
+    if (c->fast2d) {
+        cudaError_t e1, e2, e3;
+        if (d->precision == MG_FP64) {
+            e1 = cudaFuncSetAttribute(k_coarse_cta_2d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
+            e2 = cudaFuncSetAttribute(k_up_pair_2d<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpSmem<double>));
+            e3 = cudaFuncSetAttribute(k_up_pair_2d<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpSmem<double>));
+        } else {
+            e1 = cudaFuncSetAttribute(k_coarse_cta_2d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
+            e2 = cudaFuncSetAttribute(k_up_pair_2d<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpSmem<float>));
+            e3 = cudaFuncSetAttribute(k_up_pair_2d<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpSmem<float>));
+        }
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            mg_destroy(c);
+            return cuda_fail(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3, "mg_create shared-memory attributes");
+        }
+    }
+    if (d->order == 4 &&
+        cudaMalloc(&c->ft, sizeof(double) * (size_t)d->pitch * (d->n + 2) * (d->dim == 3 ? (size_t)(d->n + 2) : 1)) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        mg_destroy(c);
+        return MG_ENOMEM;
+    }
     c->hist_cap = 4096;
     const Level &lc = c->lv[c->L];
     const int nn = d->dim == 2 ? lc.side * lc.side : lc.side * lc.side * lc.side;
@@ -437,6 +596,11 @@ mg_status mg_create(mg_ctx **out, const mg_desc *d) {
         cudaGetLastError();
         mg_destroy(c);
         return MG_ENOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&c->cs1, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess) {
+        mg_destroy(c);
+        return cuda_fail(cudaGetLastError(), "mg_create streams");
     }
     std::vector<double> G = coarse_inverse(d->dim, lc.side, spacing(c, lc));
     if (cudaMemcpy(c->G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -533,38 +697,98 @@ mg_status mg_level_set(mg_ctx *c, int level, int which, const double *grid, void
 
 mg_status mg_vcycle(mg_ctx *c, const double *f, double *u, void *stream) {
     if (!c || !f || !u) return MG_EINVAL;
+    if (c->d.order == 4) {
+        cudaStream_t s = S(stream);
+        launch_rhs4(c, f, s);
+    }
     if (c->d.precision == MG_FP64) return vcycle_t<double>(c, f, u, nullptr, true, S(stream));
     return vcycle_t<float>(c, f, u, nullptr, true, S(stream));
+}
+
+// residual of the current iterate into level 0 (+ partial sums); returns their count
+static int solve_residual(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
+    return c->d.precision == MG_FP64 ? launch_res_fast<double>(c, f, u, done, s)
+                                     : launch_res_fast<float>(c, f, u, done, s);
+}
+
+// Record the whole solve as one graph: prefix (control init, norm of the
+// right-hand side, residual of the warm start, first control step) and a
+// conditional WHILE node whose body is one V-cycle, the residual of the new
+// iterate and the control step that sets the loop condition to "not done".
+static mg_status build_solve_graph(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles) {
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    const bool fp64 = c->d.precision == MG_FP64;
+    const int *done = &c->ctl->done;
+    cudaStream_t s = c->cs1;
+    c->capturing = true;
+    const long long l0 = c->launches;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
+    cudaGraphConditionalHandle loop;
+    CK(cudaGraphConditionalHandleCreate(&loop, g, 0, cudaGraphCondAssignDefault));
+    LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
+    if (fp64) launch_residual<double>(c, f, u, nullptr, true, nullptr, s);
+    else launch_residual<float>(c, f, u, nullptr, true, nullptr, s);
+    LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, c->max_blocks, &c->ctl->f2);
+    if (c->d.order == 4) launch_rhs4(c, f, s);
+    int np = solve_residual(c, f, u, nullptr, s);
+    LAUNCH(TAG_CONTROL, (k_ctrl), 1, 1024, c->part, np, c->ctl, c->hist, 1, loop, 1);
+    c->g_prefix_kernels = c->launches - l0;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CK(cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+    // loop body, captured on a second stream into the WHILE node's graph
+    cudaStream_t s2 = c->cs2;
+    CK(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const long long l1 = c->launches;
+    {
+        cudaStream_t s_saved = s;
+        (void)s_saved;
+        mg_status stv = fp64 ? vcycle_t<double>(c, f, u, done, false, s2) : vcycle_t<float>(c, f, u, done, false, s2);
+        if (stv != MG_OK) { cudaStreamEndCapture(s2, &body); cudaStreamEndCapture(s, &g); c->capturing = false; return stv; }
+        int np2 = solve_residual(c, f, u, nullptr, s2);
+        {
+            cudaStream_t s_ = s2;
+            Launch l_(c, TAG_CONTROL, s_);
+            k_ctrl<<<1, 1024, 0, s_>>>(c->part, np2, c->ctl, c->hist, 0, loop, 1);
+        }
+    }
+    c->g_body_kernels = c->launches - l1;
+    CK(cudaStreamEndCapture(s2, &body));
+    CK(cudaStreamEndCapture(s, &g));
+    c->capturing = false;
+    c->launches = l0;  // counted when the graph runs
+    c->graph = g;
+    CK(cudaGraphInstantiate(&c->gexec, g, 0));
+    c->g_f = f; c->g_u = u; c->g_rtol = rtol; c->g_max = max_cycles;
+    return MG_OK;
 }
 
 mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
                    double *relres_out, double *history, void *stream) {
     if (!c || !f || !u || !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap) return MG_EINVAL;
     cudaStream_t s = S(stream);
-    const bool fp64 = c->d.precision == MG_FP64;
-    const int *done = &c->ctl->done;
-    LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
-    // ||r(u=0)||^2
-    if (fp64) launch_residual<double>(c, f, u, nullptr, true, nullptr, s);
-    else launch_residual<float>(c, f, u, nullptr, true, nullptr, s);
-    LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, c->max_blocks, &c->ctl->f2);
-    CKL("mg_solve init");
-    Ctrl host{};
-    const int chunk = 4;
-    for (int cyc = 0; cyc <= max_cycles; cyc += chunk) {
-        for (int q = 0; q < chunk && cyc + q <= max_cycles; q++) {
-            const int first = (cyc + q) == 0;
-            if (fp64) launch_residual<double>(c, f, u, nullptr, false, first ? nullptr : done, s);
-            else launch_residual<float>(c, f, u, nullptr, false, first ? nullptr : done, s);
-            LAUNCH(TAG_CONTROL, (k_ctrl), 1, 1024, c->part, c->max_blocks, c->ctl, c->hist, first);
-            mg_status st = fp64 ? vcycle_t<double>(c, f, u, done, false, s) : vcycle_t<float>(c, f, u, done, false, s);
-            if (st != MG_OK) return st;
-        }
-        CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        probe_collect(c);
-        if (host.done) break;
+    if (!c->gexec || c->g_f != f || c->g_u != u || c->g_rtol != rtol || c->g_max != max_cycles) {
+        mg_status st = build_solve_graph(c, f, u, rtol, max_cycles);
+        if (st != MG_OK) return st;
     }
+    CK(cudaGraphLaunch(c->gexec, s));
+    Ctrl host{};
+    CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    c->launches += c->g_prefix_kernels + (long long)host.cycles * c->g_body_kernels;
     if (cycles_out) *cycles_out = host.cycles;
     if (relres_out) *relres_out = host.relres;
     if (history && host.cycles > 0) {

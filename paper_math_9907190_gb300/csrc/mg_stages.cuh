@@ -40,6 +40,19 @@ template <typename T> struct A3 {  // 3D array view
 
 __device__ __forceinline__ bool stop(const int *done) { return done != nullptr && *(volatile const int *)done; }
 
+// f32 -> f64 widening with integer operations (the FP64 pipe is the scarce
+// resource on this GPU).  Exact for normal numbers and zero; FP32 subnormals
+// (|x| < 2^-126) map to signed zero.
+__device__ __forceinline__ double widen(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned ax = b & 0x7fffffffu;
+    unsigned hi = (ax >> 3) + 0x38000000u;
+    hi = ax >= 0x00800000u ? hi : 0u;
+    hi |= b & 0x80000000u;
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+
 #define MG_IDX2 \
     const int tx = blockIdx.x * blockDim.x + threadIdx.x; \
     const int ty = blockIdx.y * blockDim.y + threadIdx.y;
@@ -129,7 +142,7 @@ __global__ void k_r2g_c_upd_2d(A2<const T> rg, A2<const T> vg, double *u, int up
     T v;
     if ((i + j) & 1) v = vg(i, j);
     else v = ((vg(i - 1, j) + vg(i + 1, j)) + (vg(i, j - 1) + vg(i, j + 1)) - c * rg(i, j)) * T(0.25);
-    u[(size_t)j * up + i] += (double)v;
+    u[(size_t)j * up + i] += widen(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -292,7 +305,7 @@ __global__ void k_r2g_c_upd_3d(A3<const T> rg, A3<const T> vg, double *u, int up
     else
         v = ((vg(i - 1, j, k) + vg(i + 1, j, k)) + (vg(i, j - 1, k) + vg(i, j + 1, k)) +
              (vg(i, j, k - 1) + vg(i, j, k + 1)) - cc * rg(i, j, k)) * T(1.0 / 6.0);
-    u[((size_t)k * urows + j) * up + i] += (double)v;
+    u[((size_t)k * urows + j) * up + i] += widen(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -471,10 +484,15 @@ __device__ __forceinline__ double sum_parts(const double *part, int nblk, double
 }
 
 // after the residual of the warm start (first = 1) or of a new iterate:
-// record the history, decide whether to stop.
-__global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, int first) {
+// record the history, decide whether to stop.  Inside the solver's graph
+// (use_loop = 1) it also sets the graph's loop condition to "not done".
+__global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, int first,
+                       cudaGraphConditionalHandle loop, int use_loop) {
     __shared__ double sh[32];
-    if (!first && ctl->done) return;
+    if (!first && ctl->done) {
+        if (use_loop && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
+        return;
+    }
     double s = sum_parts(part, nblk, sh);
     if (threadIdx.x != 0) return;
     ctl->r2 = s;
@@ -493,6 +511,7 @@ __global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, in
     } else {
         ctl->cycles += 1;  // this cycle will apply a correction
     }
+    if (use_loop) cudaGraphSetConditional(loop, ctl->done ? 0u : 1u);
 }
 
 __global__ void k_ctrl_init(Ctrl *ctl, double rtol, int max_cycles) {
