@@ -154,6 +154,31 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *u, void *stream);
 mg_status mg_solve(mg_ctx *ctx, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
                    double *relres_out, double *history, void *stream);
 
+/* Batches of independent problems (no paper counterpart: the paper solves
+ * one problem at a time).  A batch holds nprob 2D or 3D problems of sides
+ * n[0..nprob) (each 2^m - 1), all with the same hierarchy, order (2 only),
+ * precision, coarsest side and omega[4] (host).  Problems of equal side are
+ * grouped; every kernel of a group processes all of its problems in one
+ * launch (grid z = problem), and one CUDA graph holds a device-driven loop
+ * per group as parallel branches, so a batched solve is a single graph
+ * launch.  Each problem stops on its own convergence test; a group's loop
+ * ends when all of its problems are done.  mg_batch_create allocates all
+ * workspace (synchronous).
+ *   f, u        host arrays of nprob DEVICE pointers; problem p's full grid,
+ *               pitch n[p]+2, zero ring of u; u is the warm start, in/out
+ *   cycles_out  host, nullable, nprob entries; relres_out likewise
+ * Returns MG_OK, MG_ENOCONV or MG_EDIVERGED if any problem did not converge
+ * or diverged (the per-problem outputs say which), MG_EINVAL, MG_ECUDA.
+ * max_cycles <= 256.  The graph is rebuilt when f, u, rtol or max_cycles
+ * differ from the previous call. */
+typedef struct mg_batch mg_batch;
+mg_status mg_batch_create(mg_batch **out, int dim, int nprob, const int *n, int hierarchy, int order,
+                          int precision, int coarsest, const double *omega);
+mg_status mg_batch_destroy(mg_batch *batch);
+mg_status mg_solve_batched(mg_batch *batch, const double *const *f, double *const *u, double rtol, int max_cycles,
+                           int *cycles_out, double *relres_out, void *stream);
+mg_status mg_batch_launch_count(const mg_batch *batch, long long *launches);
+
 /* Diagnostics (no paper counterpart).  mg_launch_count: kernels this context
  * has launched since creation (host counter).  mg_probe_set: when family >= 0,
  * every later launch of that kernel family is bracketed with CUDA events on

@@ -8,7 +8,7 @@ that needs it does, and fails loudly if it is not built.
 """
 
 from .api import (  # noqa: F401
-    Context, PoissonSolve, default_omega, solve,
+    Batch, Context, PoissonSolve, default_omega, solve,
 )
 
-__all__ = ["Context", "PoissonSolve", "default_omega", "solve"]
+__all__ = ["Batch", "Context", "PoissonSolve", "default_omega", "solve"]

@@ -45,6 +45,10 @@ SIGNATURES = {
     "mg_probe_set": (_i, [_vp, _i]),
     "mg_probe_read": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _dp, _vp]),
     "mg_residual_noalloc": (_i, [_i, _i, _i, _d, _i, _vp, _vp, _vp, _vp, _vp]),
+    "mg_batch_create": (_i, [ctypes.POINTER(_vp), _i, _i, _ip, _i, _i, _i, _i, _dp]),
+    "mg_batch_destroy": (_i, [_vp]),
+    "mg_solve_batched": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i, _ip, _dp, _vp]),
+    "mg_batch_launch_count": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "mg_strerror": (ctypes.c_char_p, [_i]),
     "mg_last_error": (ctypes.c_char_p, []),
 }

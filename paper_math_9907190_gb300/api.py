@@ -168,6 +168,69 @@ class Context:
         return u, cyc.value, rel.value, list(hist[: cyc.value])
 
 
+class Batch:
+    """Many independent problems solved together (mg_batch_create / mg_solve_batched).
+
+    sides: interior side n_b = 2^k - 1 of every problem.  Problems of equal
+    side share kernel launches; the whole batched solve is one graph launch."""
+
+    def __init__(self, dim: int, sides, *, hierarchy: str = "diag", precision: str = "mixed", coarsest: int = 3,
+                 omega=None, device=None):
+        self.dim, self.sides = dim, [int(x) for x in sides]
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        om = tuple(default_omega(dim, hierarchy, 2) if omega is None else omega)
+        arr = (ctypes.c_double * 4)(*(list(om) + [1.0] * (4 - len(om))))
+        ns = (ctypes.c_int * len(self.sides))(*self.sides)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            N.check(N.lib().mg_batch_create(ctypes.byref(self._h), dim, len(self.sides), ns, _hier(hierarchy), 2,
+                                            _prec(precision), coarsest, arr), "mg_batch_create")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            N.lib().mg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def launch_count(self) -> int:
+        v = ctypes.c_longlong()
+        N.check(N.lib().mg_batch_launch_count(self._h, ctypes.byref(v)), "mg_batch_launch_count")
+        return v.value
+
+    def solve(self, fs, us=None, *, rtol: float = 1e-10, max_cycles: int = 100, raise_on_fail: bool = True):
+        """fs: list of CUDA float64 full grids; us: warm starts (default zeros).
+        Returns (us, cycles, relres) with per-problem lists."""
+        nb = len(self.sides)
+        assert len(fs) == nb
+        if us is None:
+            us = [torch.zeros_like(f) for f in fs]
+        for f, u, n in zip(fs, us, self.sides):
+            for t in (f, u):
+                if t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != (n + 2,) * self.dim:
+                    raise ValueError("batch arrays must be contiguous float64 full grids of side n+2")
+        fp = (ctypes.c_void_p * nb)(*[f.data_ptr() for f in fs])
+        up = (ctypes.c_void_p * nb)(*[u.data_ptr() for u in us])
+        cyc = (ctypes.c_int * nb)()
+        rel = (ctypes.c_double * nb)()
+        stream = ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        st = N.lib().mg_solve_batched(self._h, fp, up, rtol, max_cycles, cyc, rel, stream)
+        if raise_on_fail:
+            N.check(st, "mg_solve_batched")
+        return us, list(cyc), list(rel)
+
+
 _CTX_CACHE: dict = {}
 
 
@@ -194,28 +257,57 @@ def solve(f: torch.Tensor, *, order: int = 2, hierarchy: str = "diag", precision
     return u, {"cycles": cyc, "relres": rel, "history": hist}
 
 
+_BATCH_CACHE: dict = {}
+
+
+def _batch(dim, sides, precision, device):
+    key = (dim, tuple(sides), precision, str(device))
+    b = _BATCH_CACHE.get(key)
+    if b is None:
+        b = Batch(dim, sides, precision=precision, device=device)
+        _BATCH_CACHE[key] = b
+    return b
+
+
+def _solve_any(f, rtol, precision, max_cycles):
+    """Solve one problem (f: (n+2,)*dim, dim 2 or 3) or a stack of 3D problems
+    of one size (f: (B, n+2, n+2, n+2)) as one batch."""
+    if f.dim() == 4:
+        dim = f.dim() - 1
+        nb, n = f.shape[0], f.shape[1] - 2
+        bt = _batch(dim, [n] * nb, precision, f.device)
+        fs = [f[b].contiguous() for b in range(nb)]
+        us = [torch.zeros_like(x) for x in fs]
+        us, _, _ = bt.solve(fs, us, rtol=rtol, max_cycles=max_cycles)
+        return torch.stack(us)
+    u, _ = solve(f, order=2, precision=precision, rtol=rtol, max_cycles=max_cycles)
+    return u
+
+
+def _interior_only(g):
+    g = g.contiguous().clone()
+    ring = torch.ones(g.shape[-3:] if g.dim() == 4 else g.shape, dtype=torch.bool, device=g.device)
+    ring[(slice(1, -1),) * ring.dim()] = False
+    g[..., ring] = 0.0
+    return g
+
+
 class PoissonSolve(torch.autograd.Function):
     """u = L^-1 f for the discrete Dirichlet Laplacian, differentiable in f.
 
-    Forward: a multigrid solve to `rtol`.  Backward: L is symmetric under
+    f: one full grid (n+2,)*dim, or a stack (B, n+2, n+2, n+2) of 3D problems.
+    Forward: multigrid solves to `rtol`.  Backward: L is symmetric under
     homogeneous Dirichlet data, so the adjoint of the solve is the same solve
-    applied to the incoming gradient: grad_f = L^-1 grad_u (interior points;
-    the ring of grad_f is zero because the ring of f is never read by the
-    second-order operator)."""
+    applied to the incoming gradient, grad_f = L^-1 grad_u on the interior (the
+    ring of f is not read by the second-order operator, so its gradient is 0)."""
 
     @staticmethod
     def forward(ctx, f, rtol=1e-10, precision="mixed", max_cycles=100):
-        u, _ = solve(f, order=2, precision=precision, rtol=rtol, max_cycles=max_cycles)
         ctx.cfg = (rtol, precision, max_cycles)
-        return u
+        return _solve_any(f, rtol, precision, max_cycles)
 
     @staticmethod
     def backward(ctx, g):
         rtol, precision, max_cycles = ctx.cfg
-        g = g.contiguous().clone()
-        dim = g.dim()
-        ring = torch.ones_like(g, dtype=torch.bool)
-        ring[(slice(1, -1),) * dim] = False
-        g[ring] = 0.0
-        w, _ = solve(g, order=2, precision=precision, rtol=rtol, max_cycles=max_cycles)
+        w = _solve_any(_interior_only(g), rtol, precision, max_cycles)
         return w, None, None, None

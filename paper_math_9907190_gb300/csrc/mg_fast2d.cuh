@@ -38,12 +38,16 @@ constexpr int RES_ROWS = 8;  // rows per thread of the residual kernel
 //   ORDER 4: r = ft - (4 sum4axis u + sum4diag u - 20u)/(6h^2)    (Eq. Efos2)
 //            with ft = (8f + sum4 f)/12 precomputed once per solve.
 // Writes r in the level precision and the block's sum of r^2 to part[].
+// Grid z: one slice per problem of the batch.
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(256) k_res0_2d(const double *__restrict__ f, const double *__restrict__ u,
                                                  int up, int n, double ih2, A2<T> r, double *part,
-                                                 const int *done) {
+                                                 const int *done, Bt B) {
     __shared__ double sh[32];
-    if (stop(done)) return;
+    const int prob = blockIdx.z;
+    if (stop(bt_done(done, prob, B))) return;
+    if (B.ftab) { f = B.ftab[prob]; u = B.utab[prob]; }
+    r = bt_at(r, prob, B);
     const int i = blockIdx.x * 32 + threadIdx.x + 1;
     const int j0 = (blockIdx.y * 8 + threadIdx.y) * RES_ROWS + 1;
     SqAcc<T> acc;
@@ -75,7 +79,8 @@ __global__ void __launch_bounds__(256) k_res0_2d(const double *__restrict__ f, c
         }
     }
     double s = block_sum(acc.get(), sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x + gridDim.x * blockIdx.y] = s;
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        part[(size_t)prob * B.nparts + blockIdx.x + gridDim.x * blockIdx.y] = s;
 }
 
 // ft = (8f + sum4 f)/12 on the interior (order-4 right-hand side of Eq. Efos2)
@@ -87,21 +92,23 @@ __global__ void k_rhs4_2d(const double *__restrict__ f, int up, int n, double *f
 }
 
 // ---------------------------------------------------------------------------
-// pair restriction: green -> red (Eq. Erest2r) -> blue (Eq. Erest2b)
+// pair restriction: green -> red (Eq. Erest2r) -> blue (Eq. Erest2b), one
+// tile of TA x TB coset cells per 256-thread block, grid z = problem
 // ---------------------------------------------------------------------------
-constexpr int DTA = 32, DTB = 16;  // cells per tile (x, y); block 32x8
-
-template <typename T>
+template <typename T, int TA, int TB>
 __global__ void __launch_bounds__(256) k_down_pair_2d(A2<const T> g, A2<T> ee, A2<T> oo, A2<T> blue, int nb,
-                                                      const int *done) {
-    constexpr int GX = 2 * DTA + 3, GY = 2 * DTB + 3;  // green x in [2a0-2, 2a0+2DTA]
-    constexpr int OX = DTA + 1, OY = DTB + 1;          // OO cells a in [a0-1, a0+DTA)
+                                                      const int *done, Bt B) {
+    constexpr int GX = 2 * TA + 3, GY = 2 * TB + 3;  // green x in [2a0-2, 2a0+2TA]
+    constexpr int OX = TA + 1, OY = TB + 1;          // OO cells a in [a0-1, a0+TA)
     __shared__ T sg[GY][GX];
     __shared__ T so[OY][OX + 1];
-    if (stop(done)) return;
-    const int a0 = blockIdx.x * DTA, b0 = blockIdx.y * DTB;
+    const int prob = blockIdx.z;
+    if (stop(bt_done(done, prob, B))) return;
+    g = bt_at(g, prob, B); ee = bt_at(ee, prob, B); oo = bt_at(oo, prob, B); blue = bt_at(blue, prob, B);
+    const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
     const int n = 2 * nb + 1;
     const int tid = threadIdx.x + 32 * threadIdx.y;
+#pragma unroll 4
     for (int q = tid; q < GX * GY; q += 256) {
         const int x = 2 * a0 - 2 + q % GX, y = 2 * b0 - 2 + q / GX;
         sg[q / GX][q % GX] = (x >= 0 && x <= n + 1 && y >= 0 && y <= n + 1) ? g(x, y) : T(0);
@@ -120,8 +127,8 @@ __global__ void __launch_bounds__(256) k_down_pair_2d(A2<const T> g, A2<T> ee, A
         so[cy][cx] = v;
     }
     __syncthreads();
-    for (int q = tid; q < DTA * DTB; q += 256) {
-        const int ax = q % DTA, by = q / DTA;
+    for (int q = tid; q < TA * TB; q += 256) {
+        const int ax = q % TA, by = q / TA;
         const int a = a0 + ax, b = b0 + by;
         if (a < 1 || a > nb || b < 1 || b > nb) continue;
         const int x = 2 * ax + 2, y = 2 * by + 2;  // green (2a, 2b)
@@ -136,54 +143,60 @@ __global__ void __launch_bounds__(256) k_down_pair_2d(A2<const T> g, A2<T> ee, A
 // pair prolongation: blue -> red (Eq. Eajacr, Eq. Eajacb) -> green (the
 // green-red sweep); FINEST: u += v instead of storing v
 // ---------------------------------------------------------------------------
-constexpr int UTA = 32, UTB = 16;
-
-template <typename T> struct UpSmem {
-    T b[UTB + 5][UTA + 5];     // blue v, cells [a0-2, a0+UTA+2]
-    T roo[UTB + 4][UTA + 4];   // OO cells [a0-2, a0+UTA+1]
-    T ree[UTB + 3][UTA + 3];   // EE cells [a0-1, a0+UTA+1]
-    T voo[UTB + 4][UTA + 4];
-    T vee[UTB + 3][UTA + 3];
-    T rg[2 * UTB + 4][2 * UTA + 4];  // green r, x in [2a0-2, 2a0+2UTA+1]
-    T voe[UTB + 2][UTA + 2];   // F cells [a0-1, a0+UTA]
-    T veo[UTB + 2][UTA + 2];
+template <typename T, int TA, int TB> struct UpSmem {
+    T b[TB + 5][TA + 5];     // blue v, cells [a0-2, a0+TA+2]
+    T roo[TB + 4][TA + 4];   // OO cells [a0-2, a0+TA+1]
+    T ree[TB + 3][TA + 3];   // EE cells [a0-1, a0+TA+1]
+    T voo[TB + 4][TA + 4];
+    T vee[TB + 3][TA + 3];
+    T rg[2 * TB + 4][2 * TA + 4];  // green r, x in [2a0-2, 2a0+2TA+1]
+    T voe[TB + 2][TA + 2];   // F cells [a0-1, a0+TA]
+    T veo[TB + 2][TA + 2];
 };
 
-template <typename T, bool FINEST>
+template <typename T, bool FINEST, int TA, int TB>
 __global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T> ree, A2<const T> roo,
                                                     A2<const T> rg, A2<T> vg, double *u, int up, int nb,
-                                                    T c2, T c1, const int *done) {
+                                                    T c2, T c1, const int *done, Bt B) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    UpSmem<T> &S = *reinterpret_cast<UpSmem<T> *>(smraw);
-    if (stop(done)) return;
-    const int a0 = blockIdx.x * UTA, b0 = blockIdx.y * UTB;
+    UpSmem<T, TA, TB> &S = *reinterpret_cast<UpSmem<T, TA, TB> *>(smraw);
+    const int prob = blockIdx.z;
+    if (stop(bt_done(done, prob, B))) return;
+    blue = bt_at(blue, prob, B); ree = bt_at(ree, prob, B); roo = bt_at(roo, prob, B);
+    rg = bt_at(rg, prob, B); vg = bt_at(vg, prob, B);
+    if (B.utab) u = B.utab[prob];
+    const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
     const int n = 2 * nb + 1;
     const int tid = threadIdx.x + 32 * threadIdx.y;
     // loads
-    for (int q = tid; q < (UTA + 5) * (UTB + 5); q += 256) {
-        const int x = q % (UTA + 5), y = q / (UTA + 5);
+#pragma unroll 4
+    for (int q = tid; q < (TA + 5) * (TB + 5); q += 256) {
+        const int x = q % (TA + 5), y = q / (TA + 5);
         const int a = a0 - 2 + x, b = b0 - 2 + y;
         S.b[y][x] = (a >= 0 && a <= nb + 1 && b >= 0 && b <= nb + 1) ? blue(a, b) : T(0);
     }
-    for (int q = tid; q < (UTA + 4) * (UTB + 4); q += 256) {
-        const int x = q % (UTA + 4), y = q / (UTA + 4);
+#pragma unroll 4
+    for (int q = tid; q < (TA + 4) * (TB + 4); q += 256) {
+        const int x = q % (TA + 4), y = q / (TA + 4);
         const int a = a0 - 2 + x, b = b0 - 2 + y;
         S.roo[y][x] = (a >= 0 && a <= nb && b >= 0 && b <= nb) ? roo(a, b) : T(0);
     }
-    for (int q = tid; q < (UTA + 3) * (UTB + 3); q += 256) {
-        const int x = q % (UTA + 3), y = q / (UTA + 3);
+#pragma unroll 4
+    for (int q = tid; q < (TA + 3) * (TB + 3); q += 256) {
+        const int x = q % (TA + 3), y = q / (TA + 3);
         const int a = a0 - 1 + x, b = b0 - 1 + y;
         S.ree[y][x] = (a >= 1 && a <= nb && b >= 1 && b <= nb) ? ree(a, b) : T(0);
     }
-    for (int q = tid; q < (2 * UTA + 4) * (2 * UTB + 4); q += 256) {
-        const int x = q % (2 * UTA + 4), y = q / (2 * UTA + 4);
+#pragma unroll 4
+    for (int q = tid; q < (2 * TA + 4) * (2 * TB + 4); q += 256) {
+        const int x = q % (2 * TA + 4), y = q / (2 * TA + 4);
         const int gx = 2 * a0 - 2 + x, gy = 2 * b0 - 2 + y;
         S.rg[y][x] = (gx >= 1 && gx <= n && gy >= 1 && gy <= n) ? rg(gx, gy) : T(0);
     }
     __syncthreads();
-    // red points not blue: OO(c,d), c in [a0-2, a0+UTA+1]; smem x = c - a0 + 2 in voo and in b
-    for (int q = tid; q < (UTA + 4) * (UTB + 4); q += 256) {
-        const int x = q % (UTA + 4), y = q / (UTA + 4);
+    // red points not blue: OO(c,d), c in [a0-2, a0+TA+1]; smem x = c - a0 + 2 in voo and in b
+    for (int q = tid; q < (TA + 4) * (TB + 4); q += 256) {
+        const int x = q % (TA + 4), y = q / (TA + 4);
         const int c = a0 - 2 + x, d = b0 - 2 + y;
         T v = T(0);
         if (c >= 0 && c <= nb && d >= 0 && d <= nb)
@@ -191,9 +204,9 @@ __global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T
         S.voo[y][x] = v;
     }
     __syncthreads();
-    // blue points refined: EE(a,b), a in [a0-1, a0+UTA+1]; smem x = a - a0 + 1; OO(a-1) at voo x = a - a0 + 1
-    for (int q = tid; q < (UTA + 3) * (UTB + 3); q += 256) {
-        const int x = q % (UTA + 3), y = q / (UTA + 3);
+    // blue points refined: EE(a,b), a in [a0-1, a0+TA+1]; smem x = a - a0 + 1; OO(a-1) at voo x = a - a0 + 1
+    for (int q = tid; q < (TA + 3) * (TB + 3); q += 256) {
+        const int x = q % (TA + 3), y = q / (TA + 3);
         const int a = a0 - 1 + x, b = b0 - 1 + y;
         T v = T(0);
         if (a >= 1 && a <= nb && b >= 1 && b <= nb)
@@ -202,9 +215,9 @@ __global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T
         S.vee[y][x] = v;
     }
     __syncthreads();
-    // green-only points: OE(a,b) at (2a+1, 2b), EO(a,b) at (2a, 2b+1); cells [a0-1, a0+UTA]
-    for (int q = tid; q < (UTA + 2) * (UTB + 2); q += 256) {
-        const int x = q % (UTA + 2), y = q / (UTA + 2);
+    // green-only points: OE(a,b) at (2a+1, 2b), EO(a,b) at (2a, 2b+1); cells [a0-1, a0+TA]
+    for (int q = tid; q < (TA + 2) * (TB + 2); q += 256) {
+        const int x = q % (TA + 2), y = q / (TA + 2);
         const int a = a0 - 1 + x, b = b0 - 1 + y;
         // EE(a,b) at vee[y][x]; EE(a+1,b) vee[y][x+1]; EE(a,b+1) vee[y+1][x]
         // OO(a,b) at voo[y+1][x+1]; OO(a,b-1) voo[y][x+1]; OO(a-1,b) voo[y+1][x]
@@ -221,8 +234,8 @@ __global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T
     }
     __syncthreads();
     // red points of the own cells from the new green values, then store / update
-    for (int q = tid; q < UTA * UTB; q += 256) {
-        const int xa = q % UTA, yb = q / UTA;
+    for (int q = tid; q < TA * TB; q += 256) {
+        const int xa = q % TA, yb = q / TA;
         const int a = a0 + xa, b = b0 + yb;
         if (a > nb || b > nb) continue;
         const int x = xa + 1, y = yb + 1;  // F smem index of cell (a,b)
@@ -271,10 +284,13 @@ struct CoarsePlan2d {
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const T> rg_in, A2<T> vg_out,
-                                                        const double *G, const int *done) {
+                                                        const double *G, const int *done, Bt B) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sm = reinterpret_cast<T *>(smraw);
-    if (stop(done)) return;
+    const int prob = blockIdx.z;
+    if (stop(bt_done(done, prob, B))) return;
+    rg_in = bt_at(rg_in, prob, B);
+    vg_out = bt_at(vg_out, prob, B);
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int q = tid; q < P.total; q += nt) sm[q] = T(0);
     __syncthreads();
@@ -372,11 +388,15 @@ constexpr int RES3_PLANES = 8;  // planes per thread of the 3D residual kernel
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(256) k_res0_3d(const double *__restrict__ f, const double *__restrict__ u,
                                                  int up, int n, double ih2, A3<T> r, double *part,
-                                                 const int *done) {
+                                                 const int *done, Bt B) {
     __shared__ double sh[32];
-    if (stop(done)) return;
+    const int prob = bt_prob(B), bz = bt_z(B);
+    if (stop(bt_done(done, prob, B))) return;
+    if (B.ftab) { f = B.ftab[prob]; u = B.utab[prob]; }
+    r = bt_at(r, prob, B);
+    part += (size_t)prob * B.nparts;
     const int i = blockIdx.x * 32 + threadIdx.x + 1, j = blockIdx.y * 8 + threadIdx.y + 1;
-    const int k0 = blockIdx.z * RES3_PLANES + 1;
+    const int k0 = bz * RES3_PLANES + 1;
     const size_t pl = (size_t)up * (n + 2);
     SqAcc<T> acc;
     if (i <= n && j <= n) {
@@ -406,12 +426,12 @@ __global__ void __launch_bounds__(256) k_res0_3d(const double *__restrict__ f, c
     }
     double s = block_sum(acc.get(), sh);
     if (threadIdx.x == 0 && threadIdx.y == 0)
-        part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = s;
+        part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz)] = s;
 }
 
 // ft = (6f + sum6 f)/12 on the interior (order-4 right-hand side of Eq. Efos4)
 __global__ void k_rhs4_3d(const double *__restrict__ f, int up, int n, double *ft) {
-    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
+    MG_IDX2 const int i = tx + 1, j = ty + 1, k = (int)blockIdx.z + 1;
     if (i > n || j > n) return;
     const size_t pl = (size_t)up * (n + 2);
     const size_t c = k * pl + (size_t)j * up + i;
@@ -422,8 +442,12 @@ __global__ void k_rhs4_3d(const double *__restrict__ f, int up, int n, double *f
 // u += v; the f32 -> f64 widening uses integer operations
 template <typename T>
 __global__ void k_r2g_c_upd_fast_3d(A3<const T> rg, A3<const T> vg, double *u, int up, int urows, int n, T cc,
-                                    const int *done) {
-    if (stop(done)) return;
+                                    const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    rg = bt_at(rg, prob_, B);
+    vg = bt_at(vg, prob_, B);
+    if (B.utab) u = B.utab[prob_];
     MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
     if (i > n || j > n || k > n) return;
     T v;

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/diagmg.h"
@@ -88,9 +89,16 @@ struct mg_ctx {
     CoarsePlan2d plan2d{};
     size_t plan_bytes = 0;
     double *ft = nullptr;       // order-4 right-hand side (caller pitch), FP64
-    int nparts = 0;             // partial sums written by the last residual
+    int nparts = 0;             // partial sums written by the last residual (per problem)
+    // batch: nprob problems of this size, level pools pstride bytes apart,
+    // f/u from device pointer tables (nullptr for a single problem)
+    int nprob = 1;
+    size_t pstride = 0;
+    const double **ftab = nullptr;
+    double **utab = nullptr;
     // the solver graph (prefix + device-driven loop over V-cycles), cached per arguments
     bool capturing = false;
+    bool use_graph = true;      // DIAGMG_SOLVE_GRAPH=0: host-driven loop (same kernels; for profilers)
     cudaStream_t cs1 = nullptr, cs2 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -209,6 +217,29 @@ struct Launch {
         kern<<<grid, block, smem, s>>>(__VA_ARGS__);   \
     } while (0)
 
+// grid and batch descriptor of one launch: z blocks of one problem, times nprob
+struct BL {
+    dim3 dims;
+    Bt bt;
+};
+BL bl(const mg_ctx *c, dim3 g) {
+    Bt b{c->pstride, (int)g.z, (int)(sizeof(Ctrl) / sizeof(int)), (int)(g.x * g.y * g.z), c->ftab, c->utab};
+    g.z *= (unsigned)c->nprob;
+    return BL{g, b};
+}
+#define LAUNCH_B(tag, kern, grd, block, ...)                    \
+    do {                                                        \
+        BL bl_ = bl(c, grd);                                    \
+        Launch l_(c, tag, s);                                   \
+        kern<<<bl_.dims, block, 0, s>>>(__VA_ARGS__, bl_.bt);   \
+    } while (0)
+#define LAUNCH_SMEM_B(tag, kern, grd, block, smem, ...)         \
+    do {                                                        \
+        BL bl_ = bl(c, grd);                                    \
+        Launch l_(c, tag, s);                                   \
+        kern<<<bl_.dims, block, smem, s>>>(__VA_ARGS__, bl_.bt); \
+    } while (0)
+
 // accumulate the probe events of completed work (call after a stream sync)
 void probe_collect(mg_ctx *c) {
     for (int q = 0; q < c->pev_used; q++) {
@@ -245,22 +276,22 @@ void launch_residual(mg_ctx *c, const double *f, const double *u, double *r64, b
         dim3 g = grid2(n, n);
         auto r = a2<T>(l0.r[0], l0);
         if (c->d.order == 2) {
-            if (rhs_only) LAUNCH(TAG_RESIDUAL, (k_res_2d<T, 2, true>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
-            else LAUNCH(TAG_RESIDUAL, (k_res_2d<T, 2, false>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+            if (rhs_only) LAUNCH_B(TAG_RESIDUAL, (k_res_2d<T, 2, true>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+            else LAUNCH_B(TAG_RESIDUAL, (k_res_2d<T, 2, false>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
         } else {
-            if (rhs_only) LAUNCH(TAG_RESIDUAL, (k_res_2d<T, 4, true>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
-            else LAUNCH(TAG_RESIDUAL, (k_res_2d<T, 4, false>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+            if (rhs_only) LAUNCH_B(TAG_RESIDUAL, (k_res_2d<T, 4, true>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
+            else LAUNCH_B(TAG_RESIDUAL, (k_res_2d<T, 4, false>), g, B2, f, u, c->d.pitch, n, ih2, r, r64, c->part, done);
         }
     } else {
         dim3 g = grid3(n, n, n);
         auto r = a3<T>(l0.r[0], l0);
         const int ur = n + 2;
         if (c->d.order == 2) {
-            if (rhs_only) LAUNCH(TAG_RESIDUAL, (k_res_3d<T, 2, true>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
-            else LAUNCH(TAG_RESIDUAL, (k_res_3d<T, 2, false>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+            if (rhs_only) LAUNCH_B(TAG_RESIDUAL, (k_res_3d<T, 2, true>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+            else LAUNCH_B(TAG_RESIDUAL, (k_res_3d<T, 2, false>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
         } else {
-            if (rhs_only) LAUNCH(TAG_RESIDUAL, (k_res_3d<T, 4, true>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
-            else LAUNCH(TAG_RESIDUAL, (k_res_3d<T, 4, false>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+            if (rhs_only) LAUNCH_B(TAG_RESIDUAL, (k_res_3d<T, 4, true>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
+            else LAUNCH_B(TAG_RESIDUAL, (k_res_3d<T, 4, false>), g, B2, f, u, c->d.pitch, ur, n, ih2, r, r64, c->part, done);
         }
     }
 }
@@ -276,29 +307,29 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
     const Level &a = c->lv[l], &b = c->lv[l + 1];
     if (c->d.hierarchy == MG_USUAL) {
         const int nc = b.side;
-        if (c->d.dim == 2) LAUNCH(TAG_LEVELS, (k_fw_2d<T>), grid2(nc, nc), B2, a2<const T>(a.r[0], a), a2<T>(b.r[0], b), nc, done);
-        else LAUNCH(TAG_LEVELS, (k_fw_3d<T>), grid3(nc, nc, nc), B2, a3<const T>(a.r[0], a), a3<T>(b.r[0], b), nc, done);
+        if (c->d.dim == 2) LAUNCH_B(TAG_LEVELS, (k_fw_2d<T>), grid2(nc, nc), B2, a2<const T>(a.r[0], a), a2<T>(b.r[0], b), nc, done);
+        else LAUNCH_B(TAG_LEVELS, (k_fw_3d<T>), grid3(nc, nc, nc), B2, a3<const T>(a.r[0], a), a3<T>(b.r[0], b), nc, done);
         return;
     }
     if (c->d.dim == 2) {
         if (a.kind == KIND_AXIS) {
             const int nb = b.nb;
-            LAUNCH(TAG_LEVELS, (k_g2r_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(a.r[0], a), a2<T>(b.r[0], b), a2<T>(b.r[1], b), nb, done);
+            LAUNCH_B(TAG_LEVELS, (k_g2r_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(a.r[0], a), a2<T>(b.r[0], b), a2<T>(b.r[1], b), nb, done);
         } else {
             const int nb = a.nb;
-            LAUNCH(TAG_LEVELS, (k_r2b_2d<T>), grid2(nb, nb), B2, a2<const T>(a.r[0], a), a2<const T>(a.r[1], a), a2<T>(b.r[0], b), nb, done);
+            LAUNCH_B(TAG_LEVELS, (k_r2b_2d<T>), grid2(nb, nb), B2, a2<const T>(a.r[0], a), a2<const T>(a.r[1], a), a2<T>(b.r[0], b), nb, done);
         }
         return;
     }
     if (a.kind == KIND_AXIS) {
         const int nb = b.nb;
-        LAUNCH(TAG_LEVELS, (k_g2r_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(a.r[0], a), red3v<T>(b.r, b), nb, done);
+        LAUNCH_B(TAG_LEVELS, (k_g2r_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(a.r[0], a), red3v<T>(b.r, b), nb, done);
     } else if (a.kind == KIND_RED) {
         const int nb = a.nb;
-        LAUNCH(TAG_LEVELS, (k_r2m_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, red3v<const T>(a.r, a), mag3v<T>(b.r, b), nb, done);
+        LAUNCH_B(TAG_LEVELS, (k_r2m_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, red3v<const T>(a.r, a), mag3v<T>(b.r, b), nb, done);
     } else {
         const int nb = a.nb;
-        LAUNCH(TAG_LEVELS, (k_m2b_3d<T>), grid3(nb, nb, nb), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
+        LAUNCH_B(TAG_LEVELS, (k_m2b_3d<T>), grid3(nb, nb, nb), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
     }
 }
 
@@ -316,46 +347,46 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
         const T cc = (T)(p * hk2);
         if (dim == 2) {
             if (c->d.hierarchy == MG_USUAL)
-                LAUNCH(TAG_LEVELS, (k_usual_odd_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_LEVELS, (k_usual_odd_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
             else
-                LAUNCH(TAG_LEVELS, (k_r2g_f_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(b.v[1], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_LEVELS, (k_r2g_f_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(b.v[1], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
             if (u)
-                LAUNCH(TAG_FINEST_UP, (k_r2g_c_upd_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
+                LAUNCH_B(TAG_FINEST_UP, (k_r2g_c_upd_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
             else
-                LAUNCH(TAG_LEVELS, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_LEVELS, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
         } else {
             if (c->d.hierarchy == MG_USUAL)
-                LAUNCH(TAG_LEVELS, (k_usual_odd_3d<T>), grid3(n, n, n), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_LEVELS, (k_usual_odd_3d<T>), grid3(n, n, n), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
             else
-                LAUNCH(TAG_LEVELS, (k_r2g_f_3d<T>), grid3(n, n, n), B2, red3v<const T>(b.v, b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_LEVELS, (k_r2g_f_3d<T>), grid3(n, n, n), B2, red3v<const T>(b.v, b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
             if (u)
-                LAUNCH(TAG_FINEST_UP, (k_r2g_c_upd_fast_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<const T>(a.v[0], a), u, c->d.pitch, n + 2, n, cc, done);
+                LAUNCH_B(TAG_FINEST_UP, (k_r2g_c_upd_fast_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<const T>(a.v[0], a), u, c->d.pitch, n + 2, n, cc, done);
             else
-                LAUNCH(TAG_LEVELS, (k_r2g_c_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_LEVELS, (k_r2g_c_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
         }
         return;
     }
     const int nb = a.nb;
     if (dim == 2) {  // red level from the blue (next axis) level, Eq. Eajacr, Eq. Eajacb
         const T cc = (T)(2.0 * om[0] * hk2);
-        LAUNCH(TAG_LEVELS, (k_b2r_oo_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[1], a), a2<T>(a.v[1], a), nb, cc, done);
-        LAUNCH(TAG_LEVELS, (k_b2r_ee_2d<T>), grid2(nb, nb), B2, a2<const T>(a.v[1], a), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), nb, cc, done);
+        LAUNCH_B(TAG_LEVELS, (k_b2r_oo_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[1], a), a2<T>(a.v[1], a), nb, cc, done);
+        LAUNCH_B(TAG_LEVELS, (k_b2r_ee_2d<T>), grid2(nb, nb), B2, a2<const T>(a.v[1], a), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), nb, cc, done);
         return;
     }
     if (a.kind == KIND_MAG) {  // Eq. Emprolm, Eq. Emprolb
         const T cc = (T)(4.0 * om[0] * hk2);
-        LAUNCH(TAG_LEVELS, (k_b2m_ooo_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, done);
-        LAUNCH(TAG_LEVELS, (k_b2m_eee_3d<T>), grid3(nb, nb, nb), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, done);
+        LAUNCH_B(TAG_LEVELS, (k_b2m_ooo_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, done);
+        LAUNCH_B(TAG_LEVELS, (k_b2m_eee_3d<T>), grid3(nb, nb, nb), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, done);
     } else {  // red from magenta: Eq. Erprolr (faces), Eq. Erprolm (corners)
         const T c1 = (T)(2.0 * om[1] * hk2), c2 = (T)(4.0 * om[2] * hk2);
-        LAUNCH(TAG_LEVELS, (k_m2r_faces_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, done);
-        LAUNCH(TAG_LEVELS, (k_m2r_corners_3d<T>), grid3(nb, nb, nb), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, done);
+        LAUNCH_B(TAG_LEVELS, (k_m2r_faces_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, done);
+        LAUNCH_B(TAG_LEVELS, (k_m2r_corners_3d<T>), grid3(nb, nb, nb), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, done);
     }
 }
 
 template <typename T> void launch_coarse(mg_ctx *c, const int *done, cudaStream_t s) {
     const Level &l = c->lv[c->L];
-    LAUNCH(TAG_LEVELS, (k_coarse<T>), 1, 512, (const T *)l.r[0], l.pitch, l.rows, l.side, c->d.dim, c->G, (T *)l.v[0], done);
+    LAUNCH_B(TAG_LEVELS, (k_coarse<T>), dim3(1, 1, 1), 512, (const T *)l.r[0], l.pitch, l.rows, l.side, c->d.dim, c->G, (T *)l.v[0], done);
 }
 
 // ---- fused 2D diagonal path ------------------------------------------------
@@ -402,15 +433,15 @@ template <typename T> int launch_res_fast(mg_ctx *c, const double *f, const doub
     if (c->d.dim == 2) {
         g = dim3((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
         if (c->d.order == 2)
-            LAUNCH(TAG_RESIDUAL, (k_res0_2d<T, 2>), g, B2, fr, u, c->d.pitch, n, ih2, a2<T>(l0.r[0], l0), c->part, done);
+            LAUNCH_B(TAG_RESIDUAL, (k_res0_2d<T, 2>), g, B2, fr, u, c->d.pitch, n, ih2, a2<T>(l0.r[0], l0), c->part, done);
         else
-            LAUNCH(TAG_RESIDUAL, (k_res0_2d<T, 4>), g, B2, fr, u, c->d.pitch, n, ih2, a2<T>(l0.r[0], l0), c->part, done);
+            LAUNCH_B(TAG_RESIDUAL, (k_res0_2d<T, 4>), g, B2, fr, u, c->d.pitch, n, ih2, a2<T>(l0.r[0], l0), c->part, done);
     } else {
         g = dim3((n + 31) / 32, (n + 7) / 8, (n + RES3_PLANES - 1) / RES3_PLANES);
         if (c->d.order == 2)
-            LAUNCH(TAG_RESIDUAL, (k_res0_3d<T, 2>), g, B2, fr, u, c->d.pitch, n, ih2, a3<T>(l0.r[0], l0), c->part, done);
+            LAUNCH_B(TAG_RESIDUAL, (k_res0_3d<T, 2>), g, B2, fr, u, c->d.pitch, n, ih2, a3<T>(l0.r[0], l0), c->part, done);
         else
-            LAUNCH(TAG_RESIDUAL, (k_res0_3d<T, 4>), g, B2, fr, u, c->d.pitch, n, ih2, a3<T>(l0.r[0], l0), c->part, done);
+            LAUNCH_B(TAG_RESIDUAL, (k_res0_3d<T, 4>), g, B2, fr, u, c->d.pitch, n, ih2, a3<T>(l0.r[0], l0), c->part, done);
     }
     c->nparts = (int)(g.x * g.y * g.z);
     return c->nparts;
@@ -423,40 +454,79 @@ void launch_rhs4(mg_ctx *c, const double *f, cudaStream_t s) {
     else LAUNCH(TAG_CONTROL, (k_rhs4_3d), grid3(n, n, n), B2, f, c->d.pitch, n, c->ft);
 }
 
+// tile of coset cells per block: large pairs 32x16, middle 16x8, small 8x8
+// (small pairs are latency-bound; smaller tiles give them more blocks)
+int tile_class(int nb) { return nb + 1 >= 1024 ? 0 : nb + 1 >= 256 ? 1 : 2; }
+
+template <typename T, int TA, int TB>
+void launch_down_pair(mg_ctx *c, int k, const int *done, cudaStream_t s) {
+    const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
+    const int nb = r.nb;
+    dim3 grid((nb + TA) / TA, (nb + TB) / TB, 1);
+    LAUNCH_B(TAG_LEVELS, (k_down_pair_2d<T, TA, TB>), grid, B2, a2<const T>(g.r[0], g), a2<T>(r.r[0], r),
+             a2<T>(r.r[1], r), a2<T>(b.r[0], b), nb, done);
+}
+
+template <typename T, int TA, int TB>
+void launch_up_pair(mg_ctx *c, int k, double *u, const int *done, cudaStream_t s) {
+    const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
+    const int nb = r.nb;
+    const double hk = spacing(c, g), p = c->d.omega[0];
+    const T c2 = (T)(2.0 * p * hk * hk), c1 = (T)(p * hk * hk);
+    dim3 grid((nb + TA) / TA, (nb + TB) / TB, 1);
+    const size_t sm = sizeof(UpSmem<T, TA, TB>);
+    if (k == 0)
+        LAUNCH_SMEM_B(TAG_FINEST_UP, (k_up_pair_2d<T, true, TA, TB>), grid, B2, sm, a2<const T>(b.v[0], b),
+                      a2<const T>(r.r[0], r), a2<const T>(r.r[1], r), a2<const T>(g.r[0], g), a2<T>(g.v[0], g), u,
+                      c->d.pitch, nb, c2, c1, done);
+    else
+        LAUNCH_SMEM_B(TAG_LEVELS, (k_up_pair_2d<T, false, TA, TB>), grid, B2, sm, a2<const T>(b.v[0], b),
+                      a2<const T>(r.r[0], r), a2<const T>(r.r[1], r), a2<const T>(g.r[0], g), a2<T>(g.v[0], g), u,
+                      c->d.pitch, nb, c2, c1, done);
+}
+
 template <typename T> void vcycle_fast2d(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     for (int k = 0; k < c->kc; k++) {
-        const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
-        const int nb = r.nb;
-        dim3 grid((nb + DTA) / DTA, (nb + DTB) / DTB, 1);
-        LAUNCH(TAG_LEVELS, (k_down_pair_2d<T>), grid, B2, a2<const T>(g.r[0], g), a2<T>(r.r[0], r), a2<T>(r.r[1], r),
-               a2<T>(b.r[0], b), nb, done);
+        switch (tile_class(c->lv[2 * k + 1].nb)) {
+        case 0: launch_down_pair<T, 32, 16>(c, k, done, s); break;
+        case 1: launch_down_pair<T, 16, 8>(c, k, done, s); break;
+        default: launch_down_pair<T, 8, 8>(c, k, done, s); break;
+        }
     }
     {
         const Level &g = c->lv[2 * c->kc];
-        LAUNCH_SMEM(TAG_LEVELS, (k_coarse_cta_2d<T>), 1, 1024, c->plan_bytes, c->plan2d, a2<const T>(g.r[0], g),
-                    a2<T>(g.v[0], g), c->G, done);
+        LAUNCH_SMEM_B(TAG_LEVELS, (k_coarse_cta_2d<T>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan2d,
+                      a2<const T>(g.r[0], g), a2<T>(g.v[0], g), c->G, done);
     }
     for (int k = c->kc - 1; k >= 0; k--) {
-        const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
-        const int nb = r.nb;
-        const double hk = spacing(c, g), p = c->d.omega[0];
-        const T c2 = (T)(2.0 * p * hk * hk), c1 = (T)(p * hk * hk);
-        dim3 grid((nb + UTA) / UTA, (nb + UTB) / UTB, 1);
-        if (k == 0)
-            LAUNCH_SMEM(TAG_FINEST_UP, (k_up_pair_2d<T, true>), grid, B2, sizeof(UpSmem<T>), a2<const T>(b.v[0], b),
-                        a2<const T>(r.r[0], r), a2<const T>(r.r[1], r), a2<const T>(g.r[0], g), a2<T>(g.v[0], g), u,
-                        c->d.pitch, nb, c2, c1, done);
-        else
-            LAUNCH_SMEM(TAG_LEVELS, (k_up_pair_2d<T, false>), grid, B2, sizeof(UpSmem<T>), a2<const T>(b.v[0], b),
-                        a2<const T>(r.r[0], r), a2<const T>(r.r[1], r), a2<const T>(g.r[0], g), a2<T>(g.v[0], g), u,
-                        c->d.pitch, nb, c2, c1, done);
+        switch (tile_class(c->lv[2 * k + 1].nb)) {
+        case 0: launch_up_pair<T, 32, 16>(c, k, u, done, s); break;
+        case 1: launch_up_pair<T, 16, 8>(c, k, u, done, s); break;
+        default: launch_up_pair<T, 8, 8>(c, k, u, done, s); break;
+        }
     }
     if (c->kc == 0) {  // the whole hierarchy ran in the coarse block: apply v to u
         const Level &l0 = c->lv[0];
         const int n = c->d.n;
-        LAUNCH(TAG_FINEST_UP, (k_add_axis<T>), grid2(n, n), B2, (const T *)l0.v[0], l0.pitch, l0.rows, n, 2, u,
-               c->d.pitch, n + 2, done);
+        LAUNCH_B(TAG_FINEST_UP, (k_add_axis<T>), grid2(n, n), B2, (const T *)l0.v[0], l0.pitch, l0.rows, n, 2, u,
+                 c->d.pitch, n + 2, done);
     }
+}
+
+template <typename T> cudaError_t set_smem_attrs(const mg_ctx *c) {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_cta_2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
+#define MG_UP_ATTR(TA, TB)                                                                                         \
+    if (e == cudaSuccess)                                                                                          \
+        e = cudaFuncSetAttribute(k_up_pair_2d<T, true, TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                 (int)sizeof(UpSmem<T, TA, TB>));                                                  \
+    if (e == cudaSuccess)                                                                                          \
+        e = cudaFuncSetAttribute(k_up_pair_2d<T, false, TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                 (int)sizeof(UpSmem<T, TA, TB>));
+    MG_UP_ATTR(32, 16)
+    MG_UP_ATTR(16, 8)
+    MG_UP_ATTR(8, 8)
+#undef MG_UP_ATTR
+    return e;
 }
 
 template <typename T>
@@ -474,7 +544,7 @@ mg_status vcycle_t(mg_ctx *c, const double *f, double *u, const int *done, bool 
         const Level &l0 = c->lv[0];
         const int n = c->d.n;
         dim3 g = c->d.dim == 2 ? grid2(n, n) : grid3(n, n, n);
-        LAUNCH(TAG_FINEST_UP, (k_add_axis<T>), g, B2, (const T *)l0.v[0], l0.pitch, l0.rows, n, c->d.dim, u, c->d.pitch, n + 2, done);
+        LAUNCH_B(TAG_FINEST_UP, (k_add_axis<T>), g, B2, (const T *)l0.v[0], l0.pitch, l0.rows, n, c->d.dim, u, c->d.pitch, n + 2, done);
     }
     CKL("vcycle launch");
     return MG_OK;
@@ -534,14 +604,18 @@ mg_status mg_destroy(mg_ctx *c) {
     cudaFree(c->G);
     cudaFree(c->scal);
     cudaFree(c->ft);
+    cudaFree(c->ftab);
+    cudaFree(c->utab);
     delete c;
     return MG_OK;
 }
 
-mg_status mg_create(mg_ctx **out, const mg_desc *d) {
+// A context for nprob problems of one description (nprob = 1: mg_create).
+static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     if (!out) return MG_EINVAL;
     *out = nullptr;
-    if (!valid_desc(d)) return MG_EINVAL;
+    if (!valid_desc(d) || nprob < 1) return MG_EINVAL;
+    if (nprob > 1 && d->order != 2) return MG_EINVAL;
     mg_ctx *c = new (std::nothrow) mg_ctx();
     if (!c) return MG_ENOMEM;
     c->d = *d;
@@ -552,8 +626,10 @@ mg_status mg_create(mg_ctx **out, const mg_desc *d) {
     build_levels(c);
     size_t total = 0;
     for (auto &l : c->lv) total += (size_t)l.ncos * 2 * ((l.len * c->esz + 255) / 256 * 256);
-    if (cudaMalloc(&c->pool, total) != cudaSuccess) { cudaGetLastError(); mg_destroy(c); return MG_ENOMEM; }
-    if (cudaMemset(c->pool, 0, total) != cudaSuccess) { mg_destroy(c); return MG_ECUDA; }
+    c->nprob = nprob;
+    c->pstride = nprob > 1 ? total : 0;
+    if (cudaMalloc(&c->pool, total * nprob) != cudaSuccess) { cudaGetLastError(); mg_destroy(c); return MG_ENOMEM; }
+    if (cudaMemset(c->pool, 0, total * nprob) != cudaSuccess) { mg_destroy(c); return MG_ECUDA; }
     char *p = (char *)c->pool;
     for (auto &l : c->lv) {
         size_t bytes = (l.len * c->esz + 255) / 256 * 256;
@@ -563,19 +639,10 @@ mg_status mg_create(mg_ctx **out, const mg_desc *d) {
     c->max_blocks = residual_blocks(c);
     plan_fast2d(c);
     if (c->fast2d) {
-        cudaError_t e1, e2, e3;
-        if (d->precision == MG_FP64) {
-            e1 = cudaFuncSetAttribute(k_coarse_cta_2d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
-            e2 = cudaFuncSetAttribute(k_up_pair_2d<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpSmem<double>));
-            e3 = cudaFuncSetAttribute(k_up_pair_2d<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpSmem<double>));
-        } else {
-            e1 = cudaFuncSetAttribute(k_coarse_cta_2d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
-            e2 = cudaFuncSetAttribute(k_up_pair_2d<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpSmem<float>));
-            e3 = cudaFuncSetAttribute(k_up_pair_2d<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpSmem<float>));
-        }
-        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+        const cudaError_t e = d->precision == MG_FP64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c);
+        if (e != cudaSuccess) {
             mg_destroy(c);
-            return cuda_fail(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3, "mg_create shared-memory attributes");
+            return cuda_fail(e, "mg_create shared-memory attributes");
         }
     }
     if (d->order == 4 &&
@@ -585,17 +652,27 @@ mg_status mg_create(mg_ctx **out, const mg_desc *d) {
         mg_destroy(c);
         return MG_ENOMEM;
     }
-    c->hist_cap = 4096;
+    c->hist_cap = nprob > 1 ? 256 : 4096;
     const Level &lc = c->lv[c->L];
     const int nn = d->dim == 2 ? lc.side * lc.side : lc.side * lc.side * lc.side;
-    if (cudaMalloc(&c->part, sizeof(double) * c->max_blocks) != cudaSuccess ||
-        cudaMalloc(&c->ctl, sizeof(Ctrl)) != cudaSuccess ||
-        cudaMalloc(&c->hist, sizeof(double) * c->hist_cap) != cudaSuccess ||
+    if (nprob > 1 && (cudaMalloc(&c->ftab, sizeof(double *) * nprob) != cudaSuccess ||
+                      cudaMalloc(&c->utab, sizeof(double *) * nprob) != cudaSuccess)) {
+        cudaGetLastError();
+        mg_destroy(c);
+        return MG_ENOMEM;
+    }
+    if (cudaMalloc(&c->part, sizeof(double) * c->max_blocks * nprob) != cudaSuccess ||
+        cudaMalloc(&c->ctl, sizeof(Ctrl) * nprob) != cudaSuccess ||
+        cudaMalloc(&c->hist, sizeof(double) * c->hist_cap * nprob) != cudaSuccess ||
         cudaMalloc(&c->G, sizeof(double) * nn * nn) != cudaSuccess ||
         cudaMalloc(&c->scal, sizeof(double) * 4) != cudaSuccess) {
         cudaGetLastError();
         mg_destroy(c);
         return MG_ENOMEM;
+    }
+    {
+        const char *ev = std::getenv("DIAGMG_SOLVE_GRAPH");
+        c->use_graph = !(ev && ev[0] == '0');
     }
     if (cudaStreamCreateWithFlags(&c->cs1, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess) {
@@ -604,13 +681,15 @@ mg_status mg_create(mg_ctx **out, const mg_desc *d) {
     }
     std::vector<double> G = coarse_inverse(d->dim, lc.side, spacing(c, lc));
     if (cudaMemcpy(c->G, G.data(), sizeof(double) * G.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(c->ctl, 0, sizeof(Ctrl)) != cudaSuccess) {
+        cudaMemset(c->ctl, 0, sizeof(Ctrl) * nprob) != cudaSuccess) {
         mg_destroy(c);
         return cuda_fail(cudaGetLastError(), "mg_create upload");
     }
     *out = c;
     return MG_OK;
 }
+
+mg_status mg_create(mg_ctx **out, const mg_desc *d) { return create_ctx(out, d, 1); }
 
 mg_status mg_num_levels(const mg_ctx *c, int *num) {
     if (!c || !num) return MG_EINVAL;
@@ -711,31 +790,48 @@ static int solve_residual(mg_ctx *c, const double *f, const double *u, const int
                                      : launch_res_fast<float>(c, f, u, done, s);
 }
 
-// Record the whole solve as one graph: prefix (control init, norm of the
-// right-hand side, residual of the warm start, first control step) and a
-// conditional WHILE node whose body is one V-cycle, the residual of the new
-// iterate and the control step that sets the loop condition to "not done".
-static mg_status build_solve_graph(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles) {
-    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+// control step after a residual: single problem (k_ctrl sets the loop
+// condition itself) or a batch (one block per problem, then "any active")
+static void launch_ctrl(mg_ctx *c, int np, int first, cudaGraphConditionalHandle loop, int use_loop, cudaStream_t s) {
+    if (c->nprob == 1) {
+        LAUNCH(TAG_CONTROL, (k_ctrl), 1, 1024, c->part, np, c->ctl, c->hist, first, loop, use_loop);
+    } else {
+        LAUNCH(TAG_CONTROL, (k_ctrl_b), c->nprob, 1024, c->part, np, c->ctl, c->hist, c->hist_cap, first);
+        LAUNCH(TAG_CONTROL, (k_any_active), 1, 1024, c->ctl, c->nprob, loop, use_loop, (int *)nullptr);
+    }
+}
+
+// Record one solve into the capture active on stream s: prefix (control
+// init, norm of the right-hand side, residual of the warm start, first
+// control step) and a conditional WHILE node whose body -- recorded on s2 --
+// is one V-cycle, the residual of the new iterate and the control step that
+// sets the loop condition to "not done" (for a batch: "any not done").
+static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, cudaStream_t s,
+                               cudaStream_t s2) {
     const bool fp64 = c->d.precision == MG_FP64;
     const int *done = &c->ctl->done;
-    cudaStream_t s = c->cs1;
     c->capturing = true;
     const long long l0 = c->launches;
-    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     cudaStreamCaptureStatus st;
     cudaGraph_t g = nullptr;
     CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
     cudaGraphConditionalHandle loop;
     CK(cudaGraphConditionalHandleCreate(&loop, g, 0, cudaGraphCondAssignDefault));
-    LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
+    if (c->nprob == 1) {
+        LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
+    } else {
+        LAUNCH(TAG_CONTROL, (k_ctrl_init_b), (c->nprob + 255) / 256, 256, c->ctl, c->nprob, rtol, max_cycles);
+    }
     if (fp64) launch_residual<double>(c, f, u, nullptr, true, nullptr, s);
     else launch_residual<float>(c, f, u, nullptr, true, nullptr, s);
-    LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, c->max_blocks, &c->ctl->f2);
+    if (c->nprob == 1) {
+        LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, c->max_blocks, &c->ctl->f2);
+    } else {
+        LAUNCH(TAG_CONTROL, (k_sum_to_b), c->nprob, 1024, c->part, c->max_blocks, c->ctl);
+    }
     if (c->d.order == 4) launch_rhs4(c, f, s);
     int np = solve_residual(c, f, u, nullptr, s);
-    LAUNCH(TAG_CONTROL, (k_ctrl), 1, 1024, c->part, np, c->ctl, c->hist, 1, loop, 1);
+    launch_ctrl(c, np, 1, loop, 1, s);
     c->g_prefix_kernels = c->launches - l0;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
@@ -749,30 +845,77 @@ static mg_status build_solve_graph(mg_ctx *c, const double *f, double *u, double
     CK(cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
-    // loop body, captured on a second stream into the WHILE node's graph
-    cudaStream_t s2 = c->cs2;
     CK(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const long long l1 = c->launches;
-    {
-        cudaStream_t s_saved = s;
-        (void)s_saved;
-        mg_status stv = fp64 ? vcycle_t<double>(c, f, u, done, false, s2) : vcycle_t<float>(c, f, u, done, false, s2);
-        if (stv != MG_OK) { cudaStreamEndCapture(s2, &body); cudaStreamEndCapture(s, &g); c->capturing = false; return stv; }
-        int np2 = solve_residual(c, f, u, nullptr, s2);
-        {
-            cudaStream_t s_ = s2;
-            Launch l_(c, TAG_CONTROL, s_);
-            k_ctrl<<<1, 1024, 0, s_>>>(c->part, np2, c->ctl, c->hist, 0, loop, 1);
-        }
+    mg_status stv = fp64 ? vcycle_t<double>(c, f, u, done, false, s2) : vcycle_t<float>(c, f, u, done, false, s2);
+    if (stv != MG_OK) {
+        cudaStreamEndCapture(s2, &body);
+        c->capturing = false;
+        return stv;
     }
+    const int np2 = solve_residual(c, f, u, nullptr, s2);
+    launch_ctrl(c, np2, 0, loop, 1, s2);
     c->g_body_kernels = c->launches - l1;
     CK(cudaStreamEndCapture(s2, &body));
-    CK(cudaStreamEndCapture(s, &g));
     c->capturing = false;
     c->launches = l0;  // counted when the graph runs
+    return MG_OK;
+}
+
+static mg_status build_solve_graph(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles) {
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    cudaStream_t s = c->cs1;
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    mg_status st = capture_solve(c, f, u, rtol, max_cycles, s, c->cs2);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != MG_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     c->graph = g;
     CK(cudaGraphInstantiate(&c->gexec, g, 0));
     c->g_f = f; c->g_u = u; c->g_rtol = rtol; c->g_max = max_cycles;
+    return MG_OK;
+}
+
+// The same schedule driven from the host (one control-word read per 4 cycles);
+// used when graphs are disabled, e.g. under a kernel profiler.
+static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles,
+                                 int *cycles_out, double *relres_out, double *history, cudaStream_t s) {
+    const bool fp64 = c->d.precision == MG_FP64;
+    const int *done = &c->ctl->done;
+    cudaGraphConditionalHandle none = 0;
+    LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
+    if (fp64) launch_residual<double>(c, f, u, nullptr, true, nullptr, s);
+    else launch_residual<float>(c, f, u, nullptr, true, nullptr, s);
+    LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, c->max_blocks, &c->ctl->f2);
+    if (c->d.order == 4) launch_rhs4(c, f, s);
+    int np = solve_residual(c, f, u, nullptr, s);
+    launch_ctrl(c, np, 1, none, 0, s);
+    CKL("mg_solve init");
+    Ctrl host{};
+    for (int cyc = 0; cyc < max_cycles; cyc += 4) {
+        for (int q = 0; q < 4 && cyc + q < max_cycles; q++) {
+            mg_status st = fp64 ? vcycle_t<double>(c, f, u, done, false, s) : vcycle_t<float>(c, f, u, done, false, s);
+            if (st != MG_OK) return st;
+            np = solve_residual(c, f, u, done, s);
+            launch_ctrl(c, np, 0, none, 0, s);
+        }
+        CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        probe_collect(c);
+        if (host.done) break;
+    }
+    CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (cycles_out) *cycles_out = host.cycles;
+    if (relres_out) *relres_out = host.relres;
+    if (history && host.cycles > 0) {
+        CK(cudaMemcpyAsync(history, c->hist, sizeof(double) * host.cycles, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (host.status == -5) return MG_EDIVERGED;
+    if (host.status == -4 || !host.done) return MG_ENOCONV;
     return MG_OK;
 }
 
@@ -780,6 +923,7 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
                    double *relres_out, double *history, void *stream) {
     if (!c || !f || !u || !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap) return MG_EINVAL;
     cudaStream_t s = S(stream);
+    if (!c->use_graph) return solve_host_loop(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, s);
     if (!c->gexec || c->g_f != f || c->g_u != u || c->g_rtol != rtol || c->g_max != max_cycles) {
         mg_status st = build_solve_graph(c, f, u, rtol, max_cycles);
         if (st != MG_OK) return st;
@@ -797,6 +941,163 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
     }
     if (host.status == -5) return MG_EDIVERGED;
     if (host.status == -4 || !host.done) return MG_ENOCONV;
+    return MG_OK;
+}
+
+}  // extern "C"
+
+// ---- batches of independent problems --------------------------------------
+
+struct mg_batch {
+    int dim = 0, nprob = 0;
+    std::vector<int> side;                 // per problem
+    std::vector<mg_ctx *> grp;             // one context per distinct side
+    std::vector<std::vector<int>> members; // problem ids of each group, in order
+    cudaStream_t cs = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<const double *> g_f;
+    std::vector<double *> g_u;
+    double g_rtol = -1.0;
+    int g_max = -1;
+    std::vector<Ctrl> host;                // control words read back after a solve
+};
+
+extern "C" {
+
+mg_status mg_batch_destroy(mg_batch *b) {
+    if (!b) return MG_OK;
+    cudaDeviceSynchronize();
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cs) cudaStreamDestroy(b->cs);
+    for (auto c : b->grp) mg_destroy(c);
+    delete b;
+    return MG_OK;
+}
+
+mg_status mg_batch_create(mg_batch **out, int dim, int nprob, const int *n, int hierarchy, int order,
+                          int precision, int coarsest, const double *omega) {
+    if (!out || !n || nprob < 1 || !omega) return MG_EINVAL;
+    *out = nullptr;
+    mg_batch *b = new (std::nothrow) mg_batch();
+    if (!b) return MG_ENOMEM;
+    b->dim = dim;
+    b->nprob = nprob;
+    b->side.assign(n, n + nprob);
+    std::vector<int> sides(b->side);
+    std::sort(sides.begin(), sides.end());
+    sides.erase(std::unique(sides.begin(), sides.end()), sides.end());
+    for (int sd : sides) {
+        mg_desc d{};
+        d.dim = dim; d.n = sd; d.pitch = sd + 2; d.hierarchy = hierarchy; d.order = order;
+        d.precision = precision; d.coarsest = coarsest;
+        for (int q = 0; q < 4; q++) d.omega[q] = omega[q];
+        std::vector<int> mem;
+        for (int p = 0; p < nprob; p++)
+            if (b->side[p] == sd) mem.push_back(p);
+        mg_ctx *c = nullptr;
+        mg_status st = valid_desc(&d) ? create_ctx(&c, &d, (int)mem.size()) : MG_EINVAL;
+        if (st != MG_OK) { mg_batch_destroy(b); return st; }
+        b->grp.push_back(c);
+        b->members.push_back(mem);
+    }
+    if (cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        mg_batch_destroy(b);
+        return cuda_fail(cudaGetLastError(), "mg_batch_create");
+    }
+    b->join.resize(b->grp.size());
+    for (auto &e : b->join)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            mg_batch_destroy(b);
+            return cuda_fail(cudaGetLastError(), "mg_batch_create");
+        }
+    *out = b;
+    return MG_OK;
+}
+
+mg_status mg_solve_batched(mg_batch *b, const double *const *f, double *const *u, double rtol, int max_cycles,
+                           int *cycles_out, double *relres_out, void *stream) {
+    if (!b || !f || !u || !(rtol >= 0.0) || max_cycles < 0) return MG_EINVAL;
+    for (int p = 0; p < b->nprob; p++)
+        if (!f[p] || !u[p]) return MG_EINVAL;
+    for (auto c : b->grp)
+        if (max_cycles > c->hist_cap) return MG_EINVAL;
+    cudaStream_t s = S(stream);
+    const bool same = b->gexec && b->g_rtol == rtol && b->g_max == max_cycles &&
+                      std::equal(f, f + b->nprob, b->g_f.begin()) && std::equal(u, u + b->nprob, b->g_u.begin());
+    if (!same) {
+        // per-group pointer tables, then one graph: a WHILE branch per group
+        for (size_t g = 0; g < b->grp.size(); g++) {
+            mg_ctx *c = b->grp[g];
+            std::vector<const double *> ft;
+            std::vector<double *> ut;
+            for (int p : b->members[g]) { ft.push_back(f[p]); ut.push_back(u[p]); }
+            if (c->nprob > 1) {
+                CK(cudaMemcpy(c->ftab, ft.data(), sizeof(double *) * ft.size(), cudaMemcpyHostToDevice));
+                CK(cudaMemcpy(c->utab, ut.data(), sizeof(double *) * ut.size(), cudaMemcpyHostToDevice));
+            }
+        }
+        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        CK(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+        CK(cudaEventRecord(b->fork, b->cs));
+        mg_status st = MG_OK;
+        for (size_t g = 0; g < b->grp.size() && st == MG_OK; g++) {
+            mg_ctx *c = b->grp[g];
+            const int p0 = b->members[g][0];
+            if (cudaStreamWaitEvent(c->cs1, b->fork, 0) != cudaSuccess) { st = MG_ECUDA; break; }
+            st = capture_solve(c, f[p0], u[p0], rtol, max_cycles, c->cs1, c->cs2);
+            if (st == MG_OK && (cudaEventRecord(b->join[g], c->cs1) != cudaSuccess ||
+                                cudaStreamWaitEvent(b->cs, b->join[g], 0) != cudaSuccess))
+                st = MG_ECUDA;
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(b->cs, &graph);
+        if (st != MG_OK) { if (graph) cudaGraphDestroy(graph); return st == MG_ECUDA ? cuda_fail(cudaGetLastError(), "mg_solve_batched capture") : st; }
+        if (e != cudaSuccess) return cuda_fail(e, "mg_solve_batched capture");
+        b->graph = graph;
+        CK(cudaGraphInstantiate(&b->gexec, graph, 0));
+        b->g_f.assign(f, f + b->nprob);
+        b->g_u.assign(u, u + b->nprob);
+        b->g_rtol = rtol;
+        b->g_max = max_cycles;
+    }
+    CK(cudaGraphLaunch(b->gexec, s));
+    b->host.resize(b->nprob);
+    bool diverged = false, noconv = false;
+    for (size_t g = 0; g < b->grp.size(); g++) {
+        mg_ctx *c = b->grp[g];
+        std::vector<Ctrl> ctl(c->nprob);
+        CK(cudaMemcpyAsync(ctl.data(), c->ctl, sizeof(Ctrl) * c->nprob, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        int maxc = 0;
+        for (int q = 0; q < c->nprob; q++) {
+            const int p = b->members[g][q];
+            b->host[p] = ctl[q];
+            maxc = std::max(maxc, ctl[q].cycles);
+            if (cycles_out) cycles_out[p] = ctl[q].cycles;
+            if (relres_out) relres_out[p] = ctl[q].relres;
+            diverged |= ctl[q].status == -5;
+            noconv |= ctl[q].status == -4 || !ctl[q].done;
+        }
+        c->launches += c->g_prefix_kernels + (long long)maxc * c->g_body_kernels;
+    }
+    if (diverged) return MG_EDIVERGED;
+    if (noconv) return MG_ENOCONV;
+    return MG_OK;
+}
+
+mg_status mg_batch_launch_count(const mg_batch *b, long long *launches) {
+    if (!b || !launches) return MG_EINVAL;
+    long long t = 0;
+    for (auto c : b->grp) t += c->launches;
+    *launches = t;
     return MG_OK;
 }
 

@@ -22,6 +22,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <type_traits>
 
 namespace mg {
 
@@ -40,6 +41,38 @@ template <typename T> struct A3 {  // 3D array view
 
 __device__ __forceinline__ bool stop(const int *done) { return done != nullptr && *(volatile const int *)done; }
 
+// Batch descriptor: a context holds `nprob` problems of one size.  Every level
+// array of problem p lies `p * pstride` bytes after problem 0's; grid z holds
+// `zper` blocks per problem; f/u come from device pointer tables (nullptr for
+// a single problem: the kernel's own f/u are used); problem p's control word
+// starts `p * ctl_stride` ints after problem 0's, its partial sums `p * nparts`
+// doubles after problem 0's.
+struct Bt {
+    size_t pstride;
+    int zper;
+    int ctl_stride;
+    int nparts;
+    const double *const *ftab;
+    double *const *utab;
+};
+__device__ __forceinline__ int bt_prob(const Bt &B) { return blockIdx.z / B.zper; }
+__device__ __forceinline__ int bt_z(const Bt &B) { return blockIdx.z % B.zper; }
+template <typename T> __device__ __forceinline__ T *bt_ptr(T *q, int p, const Bt &B) {
+    return reinterpret_cast<T *>(reinterpret_cast<char *>(const_cast<typename std::remove_const<T>::type *>(q)) +
+                                 (size_t)p * B.pstride);
+}
+template <typename T> __device__ __forceinline__ A2<T> bt_at(A2<T> v, int p, const Bt &B) {
+    v.p = bt_ptr(v.p, p, B);
+    return v;
+}
+template <typename T> __device__ __forceinline__ A3<T> bt_at(A3<T> v, int p, const Bt &B) {
+    v.p = bt_ptr(v.p, p, B);
+    return v;
+}
+__device__ __forceinline__ const int *bt_done(const int *done, int p, const Bt &B) {
+    return done ? done + (size_t)p * B.ctl_stride : nullptr;
+}
+
 // f32 -> f64 widening with integer operations (the FP64 pipe is the scarce
 // resource on this GPU).  Exact for normal numbers and zero; FP32 subnormals
 // (|x| < 2^-126) map to signed zero.
@@ -57,7 +90,7 @@ __device__ __forceinline__ double widen(double x) { return x; }
     const int tx = blockIdx.x * blockDim.x + threadIdx.x; \
     const int ty = blockIdx.y * blockDim.y + threadIdx.y;
 #define MG_IDX3 \
-    MG_IDX2 const int tz = blockIdx.z;
+    MG_IDX2 const int tz = bt_z(B);
 
 // ---------------------------------------------------------------------------
 // 2D diagonal hierarchy (Section 2)
@@ -71,8 +104,12 @@ template <typename T> __device__ __forceinline__ T red2(const A2<T> &ee, const A
 // green -> red, Eq. Erest2r: r' = (4r + sum of the 4 axis neighbours)/8 at i+j even.
 // Thread per coset cell (a,b) in [0,nb]^2: OO(a,b) always, EE(a,b) if interior.
 template <typename T>
-__global__ void k_g2r_2d(A2<const T> g, A2<T> ee, A2<T> oo, int nb, const int *done) {
-    if (stop(done)) return;
+__global__ void k_g2r_2d(A2<const T> g, A2<T> ee, A2<T> oo, int nb, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    g = bt_at(g, prob_, B);
+    ee = bt_at(ee, prob_, B);
+    oo = bt_at(oo, prob_, B);
     MG_IDX2 const int a = tx, b = ty;
     if (a > nb || b > nb) return;
     int i = 2 * a + 1, j = 2 * b + 1;
@@ -85,8 +122,12 @@ __global__ void k_g2r_2d(A2<const T> g, A2<T> ee, A2<T> oo, int nb, const int *d
 
 // red -> blue, Eq. Erest2b: r' = (4r + sum of the 4 diagonal neighbours)/8 at (e,e)
 template <typename T>
-__global__ void k_r2b_2d(A2<const T> ee, A2<const T> oo, A2<T> blue, int nb, const int *done) {
-    if (stop(done)) return;
+__global__ void k_r2b_2d(A2<const T> ee, A2<const T> oo, A2<T> blue, int nb, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    ee = bt_at(ee, prob_, B);
+    oo = bt_at(oo, prob_, B);
+    blue = bt_at(blue, prob_, B);
     MG_IDX2 const int a = tx + 1, b = ty + 1;
     if (a > nb || b > nb) return;
     blue(a, b) = (T(4) * ee(a, b) + (oo(a - 1, b - 1) + oo(a, b - 1)) + (oo(a - 1, b) + oo(a, b))) * T(0.125);
@@ -95,8 +136,12 @@ __global__ void k_r2b_2d(A2<const T> ee, A2<const T> oo, A2<T> blue, int nb, con
 // blue -> red, Eq. Eajacr: red points that are not blue (OO) from the four
 // diagonal blue values; c = 2 p h^2 (red spacing sqrt(2) h).
 template <typename T>
-__global__ void k_b2r_oo_2d(A2<const T> blue, A2<const T> roo, A2<T> voo, int nb, T c, const int *done) {
-    if (stop(done)) return;
+__global__ void k_b2r_oo_2d(A2<const T> blue, A2<const T> roo, A2<T> voo, int nb, T c, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    blue = bt_at(blue, prob_, B);
+    roo = bt_at(roo, prob_, B);
+    voo = bt_at(voo, prob_, B);
     MG_IDX2 const int a = tx, b = ty;
     if (a > nb || b > nb) return;
     voo(a, b) = ((blue(a, b) + blue(a + 1, b)) + (blue(a, b + 1) + blue(a + 1, b + 1)) - c * roo(a, b)) * T(0.25);
@@ -104,8 +149,12 @@ __global__ void k_b2r_oo_2d(A2<const T> blue, A2<const T> roo, A2<T> voo, int nb
 
 // Eq. Eajacb: blue points (EE) refined from the four new diagonal red values
 template <typename T>
-__global__ void k_b2r_ee_2d(A2<const T> voo, A2<const T> ree, A2<T> vee, int nb, T c, const int *done) {
-    if (stop(done)) return;
+__global__ void k_b2r_ee_2d(A2<const T> voo, A2<const T> ree, A2<T> vee, int nb, T c, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    voo = bt_at(voo, prob_, B);
+    ree = bt_at(ree, prob_, B);
+    vee = bt_at(vee, prob_, B);
     MG_IDX2 const int a = tx + 1, b = ty + 1;
     if (a > nb || b > nb) return;
     vee(a, b) = ((voo(a - 1, b - 1) + voo(a, b - 1)) + (voo(a - 1, b) + voo(a, b)) - c * ree(a, b)) * T(0.25);
@@ -115,8 +164,13 @@ __global__ void k_b2r_ee_2d(A2<const T> voo, A2<const T> ree, A2<T> vee, int nb,
 // red values; c = p h^2 (Section 2.2, weight of Section 2.4)
 template <typename T>
 __global__ void k_r2g_f_2d(A2<const T> ee, A2<const T> oo, A2<const T> rg, A2<T> vg, int n, T c,
-                           const int *done) {
-    if (stop(done)) return;
+                           const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    ee = bt_at(ee, prob_, B);
+    oo = bt_at(oo, prob_, B);
+    rg = bt_at(rg, prob_, B);
+    vg = bt_at(vg, prob_, B);
     MG_IDX2 const int i = tx + 1, j = ty + 1;
     if (i > n || j > n || ((i + j) & 1) == 0) return;
     T s = (red2(ee, oo, i - 1, j) + red2(ee, oo, i + 1, j)) + (red2(ee, oo, i, j - 1) + red2(ee, oo, i, j + 1));
@@ -125,8 +179,11 @@ __global__ void k_r2g_f_2d(A2<const T> ee, A2<const T> oo, A2<const T> rg, A2<T>
 
 // red -> green, second half: red points (i+j even) from the four new green values
 template <typename T>
-__global__ void k_r2g_c_2d(A2<const T> rg, A2<T> vg, int n, T c, const int *done) {
-    if (stop(done)) return;
+__global__ void k_r2g_c_2d(A2<const T> rg, A2<T> vg, int n, T c, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    rg = bt_at(rg, prob_, B);
+    vg = bt_at(vg, prob_, B);
     MG_IDX2 const int i = tx + 1, j = ty + 1;
     if (i > n || j > n || ((i + j) & 1) == 1) return;
     T s = (vg(i - 1, j) + vg(i + 1, j)) + (vg(i, j - 1) + vg(i, j + 1));
@@ -135,8 +192,12 @@ __global__ void k_r2g_c_2d(A2<const T> rg, A2<T> vg, int n, T c, const int *done
 
 // finest level: second half fused with the update u += v at every point
 template <typename T>
-__global__ void k_r2g_c_upd_2d(A2<const T> rg, A2<const T> vg, double *u, int up, int n, T c, const int *done) {
-    if (stop(done)) return;
+__global__ void k_r2g_c_upd_2d(A2<const T> rg, A2<const T> vg, double *u, int up, int n, T c, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    rg = bt_at(rg, prob_, B);
+    vg = bt_at(vg, prob_, B);
+    if (B.utab) u = B.utab[prob_];
     MG_IDX2 const int i = tx + 1, j = ty + 1;
     if (i > n || j > n) return;
     T v;
@@ -151,6 +212,14 @@ __global__ void k_r2g_c_upd_2d(A2<const T> rg, A2<const T> vg, double *u, int up
 
 template <typename T> struct Red3 { A3<T> eee, ooe, oeo, eoo; };
 template <typename T> struct Mag3 { A3<T> eee, ooo; };
+template <typename T> __device__ __forceinline__ Red3<T> bt_at(Red3<T> r, int p, const Bt &B) {
+    r.eee = bt_at(r.eee, p, B); r.ooe = bt_at(r.ooe, p, B); r.oeo = bt_at(r.oeo, p, B); r.eoo = bt_at(r.eoo, p, B);
+    return r;
+}
+template <typename T> __device__ __forceinline__ Mag3<T> bt_at(Mag3<T> m, int p, const Bt &B) {
+    m.eee = bt_at(m.eee, p, B); m.ooo = bt_at(m.ooo, p, B);
+    return m;
+}
 
 // red level value at green point (x,y,z), x+y+z even
 template <typename T> __device__ __forceinline__ T red3(const Red3<const T> &r, int x, int y, int z) {
@@ -165,8 +234,11 @@ template <typename T> __device__ __forceinline__ T red3(const Red3<const T> &r, 
 // green -> red, Eq. Erred: (6r + 6 axis neighbours)/12 at i+j+k even.
 // Thread per cell (a,b,c) in [0,nb]^3 holding EEE, OOE, OEO, EOO points.
 template <typename T>
-__global__ void k_g2r_3d(A3<const T> g, Red3<T> red, int nb, const int *done) {
-    if (stop(done)) return;
+__global__ void k_g2r_3d(A3<const T> g, Red3<T> red, int nb, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    g = bt_at(g, prob_, B);
+    red = bt_at(red, prob_, B);
     MG_IDX3 const int a = tx, b = ty, c = tz;
     if (a > nb || b > nb || c > nb) return;
     auto avg = [&](int i, int j, int k) {
@@ -192,8 +264,11 @@ __device__ __forceinline__ T fcc12(const A3<const T> &ooe, const A3<const T> &oe
 // red -> magenta: corners, Eq. Ermagc (12r + 12 FCC neighbours)/24; centres,
 // Eq. Ermagm mean of the 6 face-centre neighbours.  Thread per cell in [0,nb]^3.
 template <typename T>
-__global__ void k_r2m_3d(Red3<const T> red, Mag3<T> mag, int nb, const int *done) {
-    if (stop(done)) return;
+__global__ void k_r2m_3d(Red3<const T> red, Mag3<T> mag, int nb, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    red = bt_at(red, prob_, B);
+    mag = bt_at(mag, prob_, B);
     MG_IDX3 const int a = tx, b = ty, c = tz;
     if (a > nb || b > nb || c > nb) return;
     if (a >= 1 && b >= 1 && c >= 1)
@@ -210,8 +285,11 @@ template <typename T> __device__ __forceinline__ T ctr8(const A3<const T> &ooo, 
 
 // magenta -> blue, Eq. Erblu: (8r + 8 centre neighbours)/16 at the blue corners
 template <typename T>
-__global__ void k_m2b_3d(Mag3<const T> mag, A3<T> blue, int nb, const int *done) {
-    if (stop(done)) return;
+__global__ void k_m2b_3d(Mag3<const T> mag, A3<T> blue, int nb, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    mag = bt_at(mag, prob_, B);
+    blue = bt_at(blue, prob_, B);
     MG_IDX3 const int a = tx + 1, b = ty + 1, c = tz + 1;
     if (a > nb || b > nb || c > nb) return;
     blue(a, b, c) = (T(8) * mag.eee(a, b, c) + ctr8(mag.ooo, a, b, c)) * T(0.0625);
@@ -219,8 +297,12 @@ __global__ void k_m2b_3d(Mag3<const T> mag, A3<T> blue, int nb, const int *done)
 
 // Eq. Emprolm: magenta centres from the 8 blue corners; c = 4 p_m h^2
 template <typename T>
-__global__ void k_b2m_ooo_3d(A3<const T> blue, A3<const T> rooo, A3<T> vooo, int nb, T cc, const int *done) {
-    if (stop(done)) return;
+__global__ void k_b2m_ooo_3d(A3<const T> blue, A3<const T> rooo, A3<T> vooo, int nb, T cc, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    blue = bt_at(blue, prob_, B);
+    rooo = bt_at(rooo, prob_, B);
+    vooo = bt_at(vooo, prob_, B);
     MG_IDX3 const int a = tx, b = ty, c = tz;
     if (a > nb || b > nb || c > nb) return;
     T s = ((blue(a, b, c) + blue(a + 1, b, c)) + (blue(a, b + 1, c) + blue(a + 1, b + 1, c))) +
@@ -230,8 +312,12 @@ __global__ void k_b2m_ooo_3d(A3<const T> blue, A3<const T> rooo, A3<T> vooo, int
 
 // Eq. Emprolb: blue corners refined from the 8 new centres
 template <typename T>
-__global__ void k_b2m_eee_3d(A3<const T> vooo, A3<const T> reee, A3<T> veee, int nb, T cc, const int *done) {
-    if (stop(done)) return;
+__global__ void k_b2m_eee_3d(A3<const T> vooo, A3<const T> reee, A3<T> veee, int nb, T cc, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    vooo = bt_at(vooo, prob_, B);
+    reee = bt_at(reee, prob_, B);
+    veee = bt_at(veee, prob_, B);
     MG_IDX3 const int a = tx + 1, b = ty + 1, c = tz + 1;
     if (a > nb || b > nb || c > nb) return;
     veee(a, b, c) = (ctr8(vooo, a, b, c) - cc * reee(a, b, c)) * T(0.125);
@@ -241,8 +327,12 @@ __global__ void k_b2m_eee_3d(A3<const T> vooo, A3<const T> reee, A3<T> veee, int
 // magenta centres along the face normal (weight 2) and the four in-plane
 // magenta corners; c1 = 2 p_r1 h^2.  Thread per cell in [0,nb]^3.
 template <typename T>
-__global__ void k_m2r_faces_3d(Mag3<const T> vm, Red3<const T> rr, Red3<T> vr, int nb, T c1, const int *done) {
-    if (stop(done)) return;
+__global__ void k_m2r_faces_3d(Mag3<const T> vm, Red3<const T> rr, Red3<T> vr, int nb, T c1, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    vm = bt_at(vm, prob_, B);
+    rr = bt_at(rr, prob_, B);
+    vr = bt_at(vr, prob_, B);
     MG_IDX3 const int a = tx, b = ty, c = tz;
     if (a > nb || b > nb || c > nb) return;
     if (c >= 1) {  // (2a+1, 2b+1, 2c): normal z
@@ -265,8 +355,12 @@ __global__ void k_m2r_faces_3d(Mag3<const T> vm, Red3<const T> rr, Red3<T> vr, i
 // Eq. Erprolm: magenta corners (red EEE) from the 12 new face centres; c2 = 4 p_r2 h^2
 template <typename T>
 __global__ void k_m2r_corners_3d(Red3<const T> vr_faces, A3<const T> reee, A3<T> veee, int nb, T c2,
-                                 const int *done) {
-    if (stop(done)) return;
+                                 const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    vr_faces = bt_at(vr_faces, prob_, B);
+    reee = bt_at(reee, prob_, B);
+    veee = bt_at(veee, prob_, B);
     MG_IDX3 const int a = tx + 1, b = ty + 1, c = tz + 1;
     if (a > nb || b > nb || c > nb) return;
     veee(a, b, c) = (fcc12(vr_faces.ooe, vr_faces.oeo, vr_faces.eoo, a, b, c) - c2 * reee(a, b, c)) * T(1.0 / 12.0);
@@ -274,8 +368,12 @@ __global__ void k_m2r_corners_3d(Red3<const T> vr_faces, A3<const T> reee, A3<T>
 
 // Eq. Egprolg: green-only points (i+j+k odd) from the six axis red values; c = p_g h^2
 template <typename T>
-__global__ void k_r2g_f_3d(Red3<const T> vr, A3<const T> rg, A3<T> vg, int n, T cc, const int *done) {
-    if (stop(done)) return;
+__global__ void k_r2g_f_3d(Red3<const T> vr, A3<const T> rg, A3<T> vg, int n, T cc, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    vr = bt_at(vr, prob_, B);
+    rg = bt_at(rg, prob_, B);
+    vg = bt_at(vg, prob_, B);
     MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
     if (i > n || j > n || k > n || ((i + j + k) & 1) == 0) return;
     T s = (red3(vr, i - 1, j, k) + red3(vr, i + 1, j, k)) + (red3(vr, i, j - 1, k) + red3(vr, i, j + 1, k)) +
@@ -285,8 +383,11 @@ __global__ void k_r2g_f_3d(Red3<const T> vr, A3<const T> rg, A3<T> vg, int n, T 
 
 // Eq. Egprolr: red points (i+j+k even) from the six new green values
 template <typename T>
-__global__ void k_r2g_c_3d(A3<const T> rg, A3<T> vg, int n, T cc, const int *done) {
-    if (stop(done)) return;
+__global__ void k_r2g_c_3d(A3<const T> rg, A3<T> vg, int n, T cc, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    rg = bt_at(rg, prob_, B);
+    vg = bt_at(vg, prob_, B);
     MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
     if (i > n || j > n || k > n || ((i + j + k) & 1) == 1) return;
     T s = (vg(i - 1, j, k) + vg(i + 1, j, k)) + (vg(i, j - 1, k) + vg(i, j + 1, k)) +
@@ -296,8 +397,12 @@ __global__ void k_r2g_c_3d(A3<const T> rg, A3<T> vg, int n, T cc, const int *don
 
 template <typename T>
 __global__ void k_r2g_c_upd_3d(A3<const T> rg, A3<const T> vg, double *u, int up, int urows, int n, T cc,
-                               const int *done) {
-    if (stop(done)) return;
+                               const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    rg = bt_at(rg, prob_, B);
+    vg = bt_at(vg, prob_, B);
+    if (B.utab) u = B.utab[prob_];
     MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
     if (i > n || j > n || k > n) return;
     T v;
@@ -314,8 +419,11 @@ __global__ void k_r2g_c_upd_3d(A3<const T> rg, A3<const T> vg, double *u, int up
 
 // full weighting (1/16)[1 2 1]x[1 2 1]
 template <typename T>
-__global__ void k_fw_2d(A2<const T> f, A2<T> cg, int nc, const int *done) {
-    if (stop(done)) return;
+__global__ void k_fw_2d(A2<const T> f, A2<T> cg, int nc, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    f = bt_at(f, prob_, B);
+    cg = bt_at(cg, prob_, B);
     MG_IDX2 const int a = tx + 1, b = ty + 1;
     if (a > nc || b > nc) return;
     const int i = 2 * a, j = 2 * b;
@@ -326,8 +434,11 @@ __global__ void k_fw_2d(A2<const T> f, A2<T> cg, int nc, const int *done) {
 
 // full weighting (1/64)[1 2 1]^3
 template <typename T>
-__global__ void k_fw_3d(A3<const T> f, A3<T> cg, int nc, const int *done) {
-    if (stop(done)) return;
+__global__ void k_fw_3d(A3<const T> f, A3<T> cg, int nc, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    f = bt_at(f, prob_, B);
+    cg = bt_at(cg, prob_, B);
     MG_IDX3 const int a = tx + 1, b = ty + 1, c = tz + 1;
     if (a > nc || b > nc || c > nc) return;
     T s = T(0);
@@ -357,16 +468,24 @@ template <typename T> __device__ __forceinline__ T interp3(const A3<const T> &vc
 // points with odd index sum from the bilinearly interpolated coarse values of
 // their axis neighbours (the interpolated values at odd points are never read)
 template <typename T>
-__global__ void k_usual_odd_2d(A2<const T> vc, A2<const T> rg, A2<T> vg, int n, T c, const int *done) {
-    if (stop(done)) return;
+__global__ void k_usual_odd_2d(A2<const T> vc, A2<const T> rg, A2<T> vg, int n, T c, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    vc = bt_at(vc, prob_, B);
+    rg = bt_at(rg, prob_, B);
+    vg = bt_at(vg, prob_, B);
     MG_IDX2 const int i = tx + 1, j = ty + 1;
     if (i > n || j > n || ((i + j) & 1) == 0) return;
     T s = (interp2(vc, i - 1, j) + interp2(vc, i + 1, j)) + (interp2(vc, i, j - 1) + interp2(vc, i, j + 1));
     vg(i, j) = (s - c * rg(i, j)) * T(0.25);
 }
 template <typename T>
-__global__ void k_usual_odd_3d(A3<const T> vc, A3<const T> rg, A3<T> vg, int n, T c, const int *done) {
-    if (stop(done)) return;
+__global__ void k_usual_odd_3d(A3<const T> vc, A3<const T> rg, A3<T> vg, int n, T c, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    vc = bt_at(vc, prob_, B);
+    rg = bt_at(rg, prob_, B);
+    vg = bt_at(vg, prob_, B);
     MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
     if (i > n || j > n || k > n || ((i + j + k) & 1) == 0) return;
     T s = (interp3(vc, i - 1, j, k) + interp3(vc, i + 1, j, k)) + (interp3(vc, i, j - 1, k) + interp3(vc, i, j + 1, k)) +
@@ -398,9 +517,15 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 // caller grid; block partial sums of r^2 to part[block].
 template <typename T, int ORDER, bool RHS_ONLY>
 __global__ void k_res_2d(const double *__restrict__ f, const double *__restrict__ u, int up, int n, double ih2,
-                         A2<T> r, double *r64, double *part, const int *done) {
+                         A2<T> r, double *r64, double *part, const int *done, Bt B) {
     __shared__ double sh[32];
-    if (stop(done)) return;
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    if (B.ftab) f = B.ftab[prob_];
+    if (B.utab) u = B.utab[prob_];
+    r = bt_at(r, prob_, B);
+    if (B.ftab) r64 = nullptr;
+    part += (size_t)prob_ * B.nparts;
     MG_IDX2 const int i = tx + 1, j = ty + 1;
     double sq = 0.0;
     if (i <= n && j <= n) {
@@ -428,9 +553,15 @@ __global__ void k_res_2d(const double *__restrict__ f, const double *__restrict_
 // 3D: 7-point (ORDER 2) or Eq. Efos4 19-point (ORDER 4)
 template <typename T, int ORDER, bool RHS_ONLY>
 __global__ void k_res_3d(const double *__restrict__ f, const double *__restrict__ u, int up, int urows, int n,
-                         double ih2, A3<T> r, double *r64, double *part, const int *done) {
+                         double ih2, A3<T> r, double *r64, double *part, const int *done, Bt B) {
     __shared__ double sh[32];
-    if (stop(done)) return;
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    if (B.ftab) f = B.ftab[prob_];
+    if (B.utab) u = B.utab[prob_];
+    r = bt_at(r, prob_, B);
+    if (B.ftab) r64 = nullptr;
+    part += (size_t)prob_ * B.nparts;
     MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
     double sq = 0.0;
     if (i <= n && j <= n) {
@@ -460,7 +591,7 @@ __global__ void k_res_3d(const double *__restrict__ f, const double *__restrict_
     }
     double s = block_sum(sq, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0)
-        part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z)] = s;
+        part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bt_z(B))] = s;
 }
 
 // Solver control word, one per context (device memory)
@@ -519,6 +650,60 @@ __global__ void k_ctrl_init(Ctrl *ctl, double rtol, int max_cycles) {
     ctl->done = 0; ctl->cycles = 0; ctl->max_cycles = max_cycles; ctl->status = 0;
 }
 
+// per problem of a batch (one block each): f2 = sum of that problem's partials
+__global__ void k_sum_to_b(const double *part, int nblk, Ctrl *ctl) {
+    __shared__ double sh[32];
+    double s = sum_parts(part + (size_t)blockIdx.x * nblk, nblk, sh);
+    if (threadIdx.x == 0) ctl[blockIdx.x].f2 = s;
+}
+
+__global__ void k_ctrl_init_b(Ctrl *ctl, int nprob, double rtol, int max_cycles) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nprob; p += gridDim.x * blockDim.x) {
+        Ctrl &c = ctl[p];
+        c.r2 = 0.0; c.relres = 0.0; c.rel0 = 0.0; c.rtol = rtol;
+        c.done = 0; c.cycles = 0; c.max_cycles = max_cycles; c.status = 0;
+    }
+}
+
+// per problem of a batch (one block each): the control step of k_ctrl, with the
+// history of problem p at hist + p * hist_cap
+__global__ void k_ctrl_b(const double *part, int nblk, Ctrl *ctl, double *hist, int hist_cap, int first) {
+    __shared__ double sh[32];
+    const int p = blockIdx.x;
+    Ctrl *c = ctl + p;
+    if (!first && c->done) return;
+    double s = sum_parts(part + (size_t)p * nblk, nblk, sh);
+    if (threadIdx.x != 0) return;
+    c->r2 = s;
+    double rel = c->f2 > 0.0 ? sqrt(s / c->f2) : 0.0;
+    c->relres = rel;
+    if (first) c->rel0 = rel;
+    else hist[(size_t)p * hist_cap + c->cycles - 1] = rel;
+    if (!(rel == rel) || rel > 1e3 * fmax(c->rel0, 1.0)) {
+        c->status = -5; c->done = 1;
+    } else if (rel <= c->rtol) {
+        c->done = 1;
+    } else if (c->cycles >= c->max_cycles) {
+        c->status = -4; c->done = 1;
+    } else {
+        c->cycles += 1;
+    }
+}
+
+// loop condition of a batch: continue while any problem is not done
+__global__ void k_any_active(const Ctrl *ctl, int nprob, cudaGraphConditionalHandle loop, int use_loop, int *active) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < nprob; p += blockDim.x)
+        if (!ctl[p].done) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (active) *active = any;
+        if (use_loop) cudaGraphSetConditional(loop, any ? 1u : 0u);
+    }
+}
+
 __global__ void k_sum_to(const double *part, int nblk, double *out) {
     __shared__ double sh[32];
     double s = sum_parts(part, nblk, sh);
@@ -528,8 +713,11 @@ __global__ void k_sum_to(const double *part, int nblk, double *out) {
 // exact coarsest solve: v = G r with the dense inverse G (FP64) of the
 // 5/7-point operator of the coarsest grid.  One block.
 template <typename T>
-__global__ void k_coarse(const T *r, int pitch, int rows, int nc, int dim, const double *G, T *v, const int *done) {
-    if (stop(done)) return;
+__global__ void k_coarse(const T *r, int pitch, int rows, int nc, int dim, const double *G, T *v, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    r = bt_ptr(r, prob_, B);
+    v = bt_ptr(v, prob_, B);
     const int nn = dim == 2 ? nc * nc : nc * nc * nc;
     for (int q = threadIdx.x; q < nn; q += blockDim.x) {
         double s = 0.0;
@@ -545,8 +733,11 @@ __global__ void k_coarse(const T *r, int pitch, int rows, int nc, int dim, const
 // u += v on an axis level (only used when the finest grid is the coarsest)
 template <typename T>
 __global__ void k_add_axis(const T *v, int pitch, int rows, int n, int dim, double *u, int up, int urows,
-                           const int *done) {
-    if (stop(done)) return;
+                           const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    v = bt_ptr(v, prob_, B);
+    if (B.utab) u = B.utab[prob_];
     MG_IDX3 const int i = tx + 1, j = ty + 1, k = dim == 3 ? tz + 1 : 0;
     if (i > n || j > n) return;
     u[((size_t)k * urows + j) * up + i] += (double)v[((size_t)k * rows + j) * pitch + i];
@@ -557,7 +748,7 @@ __global__ void k_add_axis(const T *v, int pitch, int rows, int n, int dim, doub
 template <typename T>
 __global__ void k_level_io(int dim, int kind, int s, double *grid, T *c0, T *c1, T *c2, T *c3, int pitch, int rows,
                            int to_level) {
-    MG_IDX3 const int i = tx + 1, j = ty + 1, k = dim == 3 ? tz + 1 : 0;
+    MG_IDX2 const int i = tx + 1, j = ty + 1, k = dim == 3 ? (int)blockIdx.z + 1 : 0;
     if (i > s || j > s || (dim == 3 && k > s)) return;
     const size_t gidx = ((size_t)k * (s + 2) + j) * (size_t)(s + 2) + i;
     T *arr = nullptr;
