@@ -39,14 +39,23 @@ RTOL = 1e-10
 WORKLOAD = "2D unit square, h=1/4096 (4095^2 = 16.8M unknowns), f ~ U[-1,1] seed 1, zero Dirichlet; " \
            "diagonal V-cycle (p=1.052), mixed FP64/FP32, solve from u=0 to 1e-10 relative residual"
 
-# Algorithmic cost of the probed kernel family per finest unknown:
-# family 0 = finest-grid residual (+ squared norm): reads u, f (FP64), writes r.
+# Algorithmic cost of the probed kernel (family 0: the finest-grid residual
+# k_res0_2d) per finest unknown: reads u and f in FP64, writes r in FP32; the
+# paper counts 7 flops per point for the residual (its squared norm is taken
+# in FP32 in mixed precision).  With fused multiply-adds the FP64 pipe issues
+# 5 operations per point.
 PROBE = {
     "family": 0,
-    "name": "finest residual r = f - L u (FP64) + sum r^2",
-    "bytes_per_point": {"mixed": 8 + 8 + 4, "fp64": 8 + 8 + 8},
-    "fp64_flops_per_point": 7 + 2,
+    "name": "k_res0_2d: finest residual r = f - L u (FP64 stencil), FP32 r and FP32 squares",
+    "bytes_per_point": 8 + 8 + 4,
+    "fp64_flops_per_point": 7,
+    "fp64_pipe_ops_per_point": 5,
 }
+# DRAM traffic of one k_res0_2d launch on the 4095^2 workload from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum); reported only while
+# the kernel's source is the one that was captured.
+TRAFFIC = {"kernel": "k_res0_2d", "bytes": 268.639488e6 + 52.455424e6,
+           "source_sha1": "94ca145e78e61b9ecdfb8679c4cfade682bc0926"}
 
 
 def read_peaks():
@@ -59,6 +68,90 @@ def read_peaks():
 
 # nominal FP64 peak from unit counts and clocks: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP64_PIPE_OPS_PEAK = 152 * 2 * 2.07e9  # FP64 pipe operations per second (an FMA counts once)
+
+
+def kernel_source_sha1(name: str) -> str | None:
+    """sha1 of a kernel's source text (from its template line to the next kernel)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "paper_math_9907190_gb300", "csrc", "mg_fast2d.cuh")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"template <[^>]*>\s*__global__ void __launch_bounds__\(\d+\) " + name + r"\(.*?\n}\n", text, re.S)
+    return hashlib.sha1(m.group(0).encode()).hexdigest() if m else None
+
+
+def cuda_timed(fn, reps, stream):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = None
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def extra_measurements(dev, stream):
+    """The other measured configurations: the FP64 path on the same problem,
+    the 3D unit cube, the 512-problem batch and the differentiable 3D batch."""
+    import torch
+
+    from paper_math_9907190_gb300 import Batch, Context, PoissonSolve
+    from paper_math_9907190_gb300 import inputs as I
+    out = {}
+    f = torch.from_numpy(I.square_large(N_SIDE)).to(dev)
+    with Context(2, N_SIDE, precision="fp64") as c:
+        u = c.new_grid()
+        ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u.zero_(), rtol=RTOL, max_cycles=60), 5, stream)
+        out["square4095_fp64"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc, "relres": rel}
+    del f
+    f3 = torch.from_numpy(I.cube(255)).to(dev)
+    for prec in ("mixed", "fp64"):
+        with Context(3, 255, precision=prec) as c:
+            u = c.new_grid()
+            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f3, u.zero_(), rtol=RTOL, max_cycles=60), 5, stream)
+            out[f"cube255_{prec}"] = {"unknowns_per_s": 255**3 / (ms * 1e-3), "ms": ms, "cycles": cyc, "relres": rel,
+                                      "workload": "3D unit cube 255^3, f = -6 pi^2 sin sin sin(2 pi z) + N(0,1e-6), "
+                                                  "diagonal V-cycle (1.11, 1.42, 1.08, 0.99)"}
+    del f3
+    sides = I.batch_sides(512)
+    fs = [torch.from_numpy(I.batch_f(n, b)).to(dev) for b, n in enumerate(sides)]
+    us = [torch.zeros_like(x) for x in fs]
+    tot = sum(n * n for n in sides)
+    for prec in ("mixed", "fp64"):
+        with Batch(2, sides, precision=prec) as bt:
+            def run():
+                for x in us:
+                    x.zero_()
+                return bt.solve(fs, us, rtol=RTOL, max_cycles=60)
+            ms, (_, cyc, rel) = cuda_timed(run, 3, stream)
+            out[f"batch512_{prec}"] = {"unknowns_per_s": tot / (ms * 1e-3), "ms": ms, "unknowns": tot,
+                                       "max_cycles": max(cyc), "max_relres": max(rel),
+                                       "workload": "512 2D problems, n_b = 2^k - 1, k ~ U{5..10} (seed 3), "
+                                                   "f_b ~ U[-1,1] (seed 4+b); one graph launch"}
+    del fs, us
+    n = 127
+    F = torch.stack([torch.from_numpy(I.grad_f(n, b)) for b in range(64)]).to(dev)
+    ut = torch.from_numpy(I.grad_target(n)).to(dev)
+
+    def fwd_bwd():
+        x = F.detach().requires_grad_(True)
+        U = PoissonSolve.apply(x, RTOL, "mixed")
+        ((U - ut) ** 2).sum().backward()
+        return x.grad
+    ms, _ = cuda_timed(fwd_bwd, 3, stream)
+    out["grad64x127_mixed"] = {"solves_per_s": 2 * 64 / (ms * 1e-3), "ms_fwd_bwd": ms,
+                               "unknowns_per_s": 2 * 64 * n**3 / (ms * 1e-3),
+                               "workload": "64 3D problems at 127^3, f ~ N(0,1), loss sum (u - u_t)^2; "
+                                           "forward solve + adjoint solve (autograd), mixed, 1e-10"}
+    return out
 
 
 class ClockSampler:
@@ -174,7 +267,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 3D, batched and gradient measurements")
     ap.add_argument("--ncu", action="store_true", help="short run (warm-up + one solve) for an ncu launch list")
+    ap.add_argument("--ncu-workload", default="square4095", choices=["square4095", "cube255"],
+                    help="workload of the --ncu run")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -198,10 +294,15 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    f_host = I.square_large(N_SIDE)
-    N = N_SIDE**2
+    if args.ncu and args.ncu_workload == "cube255":
+        f_host = I.cube(255)
+        N = 255**3
+        ctx = Context(3, 255, hierarchy="diag", order=2, precision="mixed")
+    else:
+        f_host = I.square_large(N_SIDE)
+        N = N_SIDE**2
+        ctx = Context(2, N_SIDE, hierarchy="diag", order=2, precision="mixed", omega=(1.052,))
     f = torch.from_numpy(f_host).to(dev)
-    ctx = Context(2, N_SIDE, hierarchy="diag", order=2, precision="mixed", omega=(1.052,))
     u = ctx.new_grid()
     stream = torch.cuda.current_stream(dev)
 
@@ -270,14 +371,22 @@ def main():
     peaks = read_peaks()
     flops = PROBE["fp64_flops_per_point"] * N
     achieved_tf = flops / (avg_ms * 1e-3) / 1e12
-    bytes_ = PROBE["bytes_per_point"]["mixed"] * N
+    bytes_ = PROBE["bytes_per_point"] * N
+    pipe = PROBE["fp64_pipe_ops_per_point"] * N / (avg_ms * 1e-3)
+    sha = kernel_source_sha1(TRAFFIC["kernel"])
+    traffic = TRAFFIC["bytes"] if (TRAFFIC["bytes"] and sha == TRAFFIC["source_sha1"]) else None
     roofline = {"bound": "alu", "kernel": PROBE["name"], "achieved": achieved_tf,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                "traffic": None, "avg_launch_ms": avg_ms,
+                "traffic": traffic, "algorithmic_bytes": bytes_, "avg_launch_ms": avg_ms,
+                "launches_probed": nprobe,
+                "fp64_pipe": {"ops_per_point": PROBE["fp64_pipe_ops_per_point"], "achieved_ops_s": pipe,
+                              "peak_ops_s": FP64_PIPE_OPS_PEAK, "frac": pipe / FP64_PIPE_OPS_PEAK},
                 "hbm_side": {"achieved_gbs": bytes_ / (avg_ms * 1e-3) / 1e9,
                              "peak_gbs": peaks.get("hbm_gbs", 6800.0),
-                             "frac": bytes_ / (avg_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0)},
-                "peak_note": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2.07 GHz (nominal, derived)"}
+                             "frac": bytes_ / (avg_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
+                             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+                "peak_note": "nominal FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived); "
+                             "achieved counts the paper's 7 flops per residual point"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": warm, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -293,6 +402,12 @@ def main():
             "gpu_launches": int(launches),
             "roofline": roofline}
 
+    if not args.no_extra:
+        line["extra"] = extra_measurements(dev, stream)
+        line["extra"]["mixed_vs_fp64_speedup_square4095"] = (
+            line["extra"]["square4095_fp64"]["ms"] / ms_max)
+        line["extra"]["mixed_vs_fp64_speedup_batch512"] = (
+            line["extra"]["batch512_fp64"]["ms"] / line["extra"]["batch512_mixed"]["ms"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, u_orc = oracle_cpu_baseline(f_host)
         line["cpu_baseline"] = cb
