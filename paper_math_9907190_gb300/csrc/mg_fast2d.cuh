@@ -97,13 +97,14 @@ __global__ void k_rhs4_2d(const double *__restrict__ f, int up, int n, double *f
 // ---------------------------------------------------------------------------
 template <typename T, int TA, int TB>
 __global__ void __launch_bounds__(256) k_down_pair_2d(A2<const T> g, A2<T> ee, A2<T> oo, A2<T> blue, int nb,
-                                                      const int *done, Bt B) {
+                                                      const T *galt, const int *par, const int *done, Bt B) {
     constexpr int GX = 2 * TA + 3, GY = 2 * TB + 3;  // green x in [2a0-2, 2a0+2TA]
     constexpr int OX = TA + 1, OY = TB + 1;          // OO cells a in [a0-1, a0+TA)
     __shared__ T sg[GY][GX];
     __shared__ T so[OY][OX + 1];
     const int prob = blockIdx.z;
     if (stop(bt_done(done, prob, B))) return;
+    if (galt && par[(size_t)prob * B.ctl_stride]) g.p = galt;  // the current one of two green buffers
     g = bt_at(g, prob, B); ee = bt_at(ee, prob, B); oo = bt_at(oo, prob, B); blue = bt_at(blue, prob, B);
     const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
     const int n = 2 * nb + 1;
@@ -456,6 +457,380 @@ __global__ void k_r2g_c_upd_fast_3d(A3<const T> rg, A3<const T> vg, double *u, i
         v = ((vg(i - 1, j, k) + vg(i + 1, j, k)) + (vg(i, j - 1, k) + vg(i, j + 1, k)) +
              (vg(i, j, k - 1) + vg(i, j, k + 1)) - cc * rg(i, j, k)) * T(1.0 / 6.0);
     u[((size_t)k * urows + j) * up + i] += widen(v);
+}
+
+}  // namespace mg
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// coarse triples (3D) in one thread block, all in shared memory: Eq. Erred,
+// Ermagc/Ermagm, Erblu down; the exact coarsest solve; Eq. Emprolm/Emprolb,
+// Erprolr/Erprolm, Egprolg/Egprolr up
+// ---------------------------------------------------------------------------
+constexpr int CTA3_MAX = 8;
+
+struct CoarsePlan3d {
+    int kc, K;
+    int nk[CTA3_MAX + 1];
+    int og_r[CTA3_MAX + 1], og_v[CTA3_MAX + 1];          // green grids (side n+2)^3
+    int orr[CTA3_MAX][4], orv[CTA3_MAX][4];              // red cosets EEE, OOE, OEO, EOO ((nb+2)^3)
+    int omr[CTA3_MAX][2], omv[CTA3_MAX][2];              // magenta cosets EEE, OOO
+    int total;
+    double cm[CTA3_MAX], cr1[CTA3_MAX], cr2[CTA3_MAX], cg[CTA3_MAX];  // 4p_m h^2, 2p_r1 h^2, 4p_r2 h^2, p_g h^2
+};
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const T> rg_in, A3<T> vg_out,
+                                                        const double *G, const int *done, Bt B) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+    const int prob = blockIdx.z;
+    if (stop(bt_done(done, prob, B))) return;
+    rg_in = bt_at(rg_in, prob, B);
+    vg_out = bt_at(vg_out, prob, B);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int q = tid; q < P.total; q += nt) sm[q] = T(0);
+    __syncthreads();
+    const int ntri = P.K - P.kc;
+    auto G3 = [&](int off, int n) { return A3<T>{sm + off, n + 2, n + 2}; };
+    auto C3 = [&](int off, int nb) { return A3<T>{sm + off, nb + 2, nb + 2}; };
+    {
+        const int n = P.nk[0];
+        A3<T> g = G3(P.og_r[0], n);
+        for (int q = tid; q < n * n * n; q += nt) {
+            const int i = q % n + 1, j = (q / n) % n + 1, k = q / (n * n) + 1;
+            g(i, j, k) = rg_in(i, j, k);
+        }
+    }
+    __syncthreads();
+    for (int t = 0; t < ntri; t++) {
+        const int n = P.nk[t], nb = (n - 1) / 2, nc = nb + 1;
+        A3<T> g = G3(P.og_r[t], n);
+        A3<T> eee = C3(P.orr[t][0], nb), ooe = C3(P.orr[t][1], nb), oeo = C3(P.orr[t][2], nb), eoo = C3(P.orr[t][3], nb);
+        A3<T> me = C3(P.omr[t][0], nb), mo = C3(P.omr[t][1], nb);
+        A3<T> bl = G3(P.og_r[t + 1], nb);
+        for (int q = tid; q < nc * nc * nc; q += nt) {  // Eq. Erred
+            const int a = q % nc, b = (q / nc) % nc, c = q / (nc * nc);
+            auto avg = [&](int i, int j, int k) {
+                return (T(6) * g(i, j, k) + (g(i + 1, j, k) + g(i - 1, j, k)) + (g(i, j + 1, k) + g(i, j - 1, k)) +
+                        (g(i, j, k + 1) + g(i, j, k - 1))) * T(1.0 / 12.0);
+            };
+            if (a >= 1 && b >= 1 && c >= 1) eee(a, b, c) = avg(2 * a, 2 * b, 2 * c);
+            if (c >= 1) ooe(a, b, c) = avg(2 * a + 1, 2 * b + 1, 2 * c);
+            if (b >= 1) oeo(a, b, c) = avg(2 * a + 1, 2 * b, 2 * c + 1);
+            if (a >= 1) eoo(a, b, c) = avg(2 * a, 2 * b + 1, 2 * c + 1);
+        }
+        __syncthreads();
+        for (int q = tid; q < nc * nc * nc; q += nt) {  // Eq. Ermagc, Eq. Ermagm
+            const int a = q % nc, b = (q / nc) % nc, c = q / (nc * nc);
+            if (a >= 1 && b >= 1 && c >= 1)
+                me(a, b, c) = (T(12) * eee(a, b, c) +
+                               fcc12(A3<const T>{ooe.p, ooe.pitch, ooe.rows}, A3<const T>{oeo.p, oeo.pitch, oeo.rows},
+                                     A3<const T>{eoo.p, eoo.pitch, eoo.rows}, a, b, c)) * T(1.0 / 24.0);
+            mo(a, b, c) = ((eoo(a, b, c) + eoo(a + 1, b, c)) + (oeo(a, b, c) + oeo(a, b + 1, c)) +
+                           (ooe(a, b, c) + ooe(a, b, c + 1))) * T(1.0 / 6.0);
+        }
+        __syncthreads();
+        for (int q = tid; q < nb * nb * nb; q += nt) {  // Eq. Erblu
+            const int a = q % nb + 1, b = (q / nb) % nb + 1, c = q / (nb * nb) + 1;
+            bl(a, b, c) = (T(8) * me(a, b, c) + ctr8(A3<const T>{mo.p, mo.pitch, mo.rows}, a, b, c)) * T(0.0625);
+        }
+        __syncthreads();
+    }
+    {   // exact solve on the coarsest grid
+        const int s = P.nk[ntri], nn = s * s * s;
+        A3<T> r = G3(P.og_r[ntri], s), v = G3(P.og_v[ntri], s);
+        for (int q = tid; q < nn; q += nt) {
+            double acc = 0.0;
+            for (int t = 0; t < nn; t++) acc += G[(size_t)q * nn + t] * (double)r(t % s + 1, (t / s) % s + 1, t / (s * s) + 1);
+            v(q % s + 1, (q / s) % s + 1, q / (s * s) + 1) = (T)acc;
+        }
+    }
+    __syncthreads();
+    for (int t = ntri - 1; t >= 0; t--) {
+        const int n = P.nk[t], nb = (n - 1) / 2, nc = nb + 1;
+        A3<T> rg = G3(P.og_r[t], n), vg = G3(P.og_v[t], n), vb = G3(P.og_v[t + 1], nb);
+        A3<T> r_e = C3(P.orr[t][0], nb), r_ooe = C3(P.orr[t][1], nb), r_oeo = C3(P.orr[t][2], nb), r_eoo = C3(P.orr[t][3], nb);
+        A3<T> v_e = C3(P.orv[t][0], nb), v_ooe = C3(P.orv[t][1], nb), v_oeo = C3(P.orv[t][2], nb), v_eoo = C3(P.orv[t][3], nb);
+        A3<T> rme = C3(P.omr[t][0], nb), rmo = C3(P.omr[t][1], nb), vme = C3(P.omv[t][0], nb), vmo = C3(P.omv[t][1], nb);
+        const T cm = (T)P.cm[t], c1 = (T)P.cr1[t], c2 = (T)P.cr2[t], cg = (T)P.cg[t];
+        for (int q = tid; q < nc * nc * nc; q += nt) {  // Eq. Emprolm: centres
+            const int a = q % nc, b = (q / nc) % nc, c = q / (nc * nc);
+            T s = ((vb(a, b, c) + vb(a + 1, b, c)) + (vb(a, b + 1, c) + vb(a + 1, b + 1, c))) +
+                  ((vb(a, b, c + 1) + vb(a + 1, b, c + 1)) + (vb(a, b + 1, c + 1) + vb(a + 1, b + 1, c + 1)));
+            vmo(a, b, c) = (s - cm * rmo(a, b, c)) * T(0.125);
+        }
+        __syncthreads();
+        for (int q = tid; q < nb * nb * nb; q += nt) {  // Eq. Emprolb: blue corners
+            const int a = q % nb + 1, b = (q / nb) % nb + 1, c = q / (nb * nb) + 1;
+            vme(a, b, c) = (ctr8(A3<const T>{vmo.p, vmo.pitch, vmo.rows}, a, b, c) - cm * rme(a, b, c)) * T(0.125);
+        }
+        __syncthreads();
+        for (int q = tid; q < nc * nc * nc; q += nt) {  // Eq. Erprolr: red face centres
+            const int a = q % nc, b = (q / nc) % nc, c = q / (nc * nc);
+            if (c >= 1) {
+                T ctr = vmo(a, b, c - 1) + vmo(a, b, c);
+                T cor = (vme(a, b, c) + vme(a + 1, b, c)) + (vme(a, b + 1, c) + vme(a + 1, b + 1, c));
+                v_ooe(a, b, c) = (T(2) * ctr + cor - c1 * r_ooe(a, b, c)) * T(0.125);
+            }
+            if (b >= 1) {
+                T ctr = vmo(a, b - 1, c) + vmo(a, b, c);
+                T cor = (vme(a, b, c) + vme(a + 1, b, c)) + (vme(a, b, c + 1) + vme(a + 1, b, c + 1));
+                v_oeo(a, b, c) = (T(2) * ctr + cor - c1 * r_oeo(a, b, c)) * T(0.125);
+            }
+            if (a >= 1) {
+                T ctr = vmo(a - 1, b, c) + vmo(a, b, c);
+                T cor = (vme(a, b, c) + vme(a, b + 1, c)) + (vme(a, b, c + 1) + vme(a, b + 1, c + 1));
+                v_eoo(a, b, c) = (T(2) * ctr + cor - c1 * r_eoo(a, b, c)) * T(0.125);
+            }
+        }
+        __syncthreads();
+        for (int q = tid; q < nb * nb * nb; q += nt) {  // Eq. Erprolm: magenta corners
+            const int a = q % nb + 1, b = (q / nb) % nb + 1, c = q / (nb * nb) + 1;
+            v_e(a, b, c) = (fcc12(A3<const T>{v_ooe.p, v_ooe.pitch, v_ooe.rows}, A3<const T>{v_oeo.p, v_oeo.pitch, v_oeo.rows},
+                                  A3<const T>{v_eoo.p, v_eoo.pitch, v_eoo.rows}, a, b, c) - c2 * r_e(a, b, c)) * T(1.0 / 12.0);
+        }
+        __syncthreads();
+        Red3<const T> vr{A3<const T>{v_e.p, v_e.pitch, v_e.rows}, A3<const T>{v_ooe.p, v_ooe.pitch, v_ooe.rows},
+                         A3<const T>{v_oeo.p, v_oeo.pitch, v_oeo.rows}, A3<const T>{v_eoo.p, v_eoo.pitch, v_eoo.rows}};
+        for (int q = tid; q < n * n * n; q += nt) {  // Eq. Egprolg: green-only points
+            const int i = q % n + 1, j = (q / n) % n + 1, k = q / (n * n) + 1;
+            if (((i + j + k) & 1) == 0) continue;
+            T s = (red3(vr, i - 1, j, k) + red3(vr, i + 1, j, k)) + (red3(vr, i, j - 1, k) + red3(vr, i, j + 1, k)) +
+                  (red3(vr, i, j, k - 1) + red3(vr, i, j, k + 1));
+            vg(i, j, k) = (s - cg * rg(i, j, k)) * T(1.0 / 6.0);
+        }
+        __syncthreads();
+        for (int q = tid; q < n * n * n; q += nt) {  // Eq. Egprolr: red points
+            const int i = q % n + 1, j = (q / n) % n + 1, k = q / (n * n) + 1;
+            if ((i + j + k) & 1) continue;
+            T s = (vg(i - 1, j, k) + vg(i + 1, j, k)) + (vg(i, j - 1, k) + vg(i, j + 1, k)) +
+                  (vg(i, j, k - 1) + vg(i, j, k + 1));
+            vg(i, j, k) = (s - cg * rg(i, j, k)) * T(1.0 / 6.0);
+        }
+        __syncthreads();
+    }
+    {
+        const int n = P.nk[0];
+        A3<T> g = G3(P.og_v[0], n);
+        for (int q = tid; q < n * n * n; q += nt) {
+            const int i = q % n + 1, j = (q / n) % n + 1, k = q / (n * n) + 1;
+            vg_out(i, j, k) = g(i, j, k);
+        }
+    }
+}
+
+}  // namespace mg
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// Finest pair of a mixed-precision solve, fused with the next residual.
+//
+// u_new = u + v and r_new = f - L u_new = r - L v.  The correction v is FP32;
+// L v = (sum of the four axis neighbours of v - 4 v)/h^2 is formed from the
+// four exact FP32 differences v_nb - v (two-sum) summed as a float-float pair,
+// whose error is ~2^-46 |v_nb - v|, far below the FP64 rounding of r; only
+// r - (ih2 * hi + ih2 * lo) and u + v run on the FP64 pipe (3 operations per
+// point instead of the 6 of a separate residual).  r is carried in FP64 (r64)
+// from one cycle to the next; its FP32 copy feeds the levels and the norm.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bv = s - a;
+    const float av = s - bv;
+    e = (a - av) + (b - bv);
+}
+
+// hi + lo ~= (n0 - c) + (n1 - c) + (n2 - c) + (n3 - c)
+__device__ __forceinline__ void lap_sum(float n0, float n1, float n2, float n3, float c, float &hi, float &lo) {
+    float d0, d1, d2, d3, e0, e1, e2, e3, t, e4, e5, e6;
+    two_sum(n0, -c, d0, e0);
+    two_sum(n1, -c, d1, e1);
+    two_sum(n2, -c, d2, e2);
+    two_sum(n3, -c, d3, e3);
+    two_sum(d0, d1, t, e4);
+    two_sum(t, d2, t, e5);
+    two_sum(t, d3, t, e6);
+    hi = t;
+    lo = ((e0 + e1) + (e2 + e3)) + ((e4 + e5) + e6);
+}
+
+template <int TA, int TB> struct UpRRSmem {
+    float b[TB + 7][TA + 7];       // blue v, cells [a0-3, a0+TA+3]
+    float roo[TB + 6][TA + 6];     // OO cells [a0-3, a0+TA+2]
+    float voo[TB + 6][TA + 6];
+    float ree[TB + 5][TA + 5];     // EE cells [a0-2, a0+TA+2]
+    float vee[TB + 5][TA + 5];
+    float rg[2 * TB + 8][2 * TA + 8];  // green r, x in [2a0-4, 2a0+2TA+3]
+    float voe[TB + 4][TA + 4];     // F cells [a0-2, a0+TA+1]
+    float veo[TB + 4][TA + 4];
+    float vce[TB + 2][TA + 2];     // C cells [a0-1, a0+TA]: green EE and OO points
+    float vco[TB + 2][TA + 2];
+};
+
+template <int TA, int TB>
+__global__ void __launch_bounds__(256) k_up0_rr_2d(A2<const float> blue, A2<const float> ree, A2<const float> roo,
+                                                   A2<float> rga, float *rgb, double *r64, int rp, double *u, int up,
+                                                   int nb, float c2, float c1, double ih2, double *part,
+                                                   const int *par, const int *done, Bt B) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    UpRRSmem<TA, TB> &S = *reinterpret_cast<UpRRSmem<TA, TB> *>(smraw);
+    __shared__ double sh[32];
+    const int prob = blockIdx.z;
+    if (stop(bt_done(done, prob, B))) return;
+    // read the current green residual buffer, write the new residual into the other
+    const bool p1 = par[(size_t)prob * B.ctl_stride] != 0;
+    A2<float> rg = rga, rnew = rga;
+    (p1 ? rg : rnew).p = rgb;
+    blue = bt_at(blue, prob, B); ree = bt_at(ree, prob, B); roo = bt_at(roo, prob, B);
+    rg = bt_at(rg, prob, B); rnew = bt_at(rnew, prob, B);
+    r64 = bt_ptr(r64, prob, B);
+    if (B.utab) u = B.utab[prob];
+    part += (size_t)prob * B.nparts;
+    const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
+    const int n = 2 * nb + 1;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+#pragma unroll 4
+    for (int q = tid; q < (TA + 7) * (TB + 7); q += 256) {
+        const int x = q % (TA + 7), y = q / (TA + 7);
+        const int a = a0 - 3 + x, b = b0 - 3 + y;
+        S.b[y][x] = (a >= 0 && a <= nb + 1 && b >= 0 && b <= nb + 1) ? blue(a, b) : 0.f;
+    }
+#pragma unroll 4
+    for (int q = tid; q < (TA + 6) * (TB + 6); q += 256) {
+        const int x = q % (TA + 6), y = q / (TA + 6);
+        const int a = a0 - 3 + x, b = b0 - 3 + y;
+        S.roo[y][x] = (a >= 0 && a <= nb && b >= 0 && b <= nb) ? roo(a, b) : 0.f;
+    }
+#pragma unroll 4
+    for (int q = tid; q < (TA + 5) * (TB + 5); q += 256) {
+        const int x = q % (TA + 5), y = q / (TA + 5);
+        const int a = a0 - 2 + x, b = b0 - 2 + y;
+        S.ree[y][x] = (a >= 1 && a <= nb && b >= 1 && b <= nb) ? ree(a, b) : 0.f;
+    }
+#pragma unroll 4
+    for (int q = tid; q < (2 * TA + 8) * (2 * TB + 8); q += 256) {
+        const int x = q % (2 * TA + 8), y = q / (2 * TA + 8);
+        const int gx = 2 * a0 - 4 + x, gy = 2 * b0 - 4 + y;
+        S.rg[y][x] = (gx >= 1 && gx <= n && gy >= 1 && gy <= n) ? rg(gx, gy) : 0.f;
+    }
+    __syncthreads();
+    // red OO (Eq. Eajacr), cells [a0-3, a0+TA+2]: smem x = c - a0 + 3 in voo and b
+    for (int q = tid; q < (TA + 6) * (TB + 6); q += 256) {
+        const int x = q % (TA + 6), y = q / (TA + 6);
+        const int c = a0 - 3 + x, d = b0 - 3 + y;
+        float v = 0.f;
+        if (c >= 0 && c <= nb && d >= 0 && d <= nb)
+            v = ((S.b[y][x] + S.b[y][x + 1]) + (S.b[y + 1][x] + S.b[y + 1][x + 1]) - c2 * S.roo[y][x]) * 0.25f;
+        S.voo[y][x] = v;
+    }
+    __syncthreads();
+    // red EE (Eq. Eajacb), cells [a0-2, a0+TA+2]: OO(a-1) at voo x = a - a0 + 2 = x
+    for (int q = tid; q < (TA + 5) * (TB + 5); q += 256) {
+        const int x = q % (TA + 5), y = q / (TA + 5);
+        const int a = a0 - 2 + x, b = b0 - 2 + y;
+        float v = 0.f;
+        if (a >= 1 && a <= nb && b >= 1 && b <= nb)
+            v = ((S.voo[y][x] + S.voo[y][x + 1]) + (S.voo[y + 1][x] + S.voo[y + 1][x + 1]) - c2 * S.ree[y][x]) * 0.25f;
+        S.vee[y][x] = v;
+    }
+    __syncthreads();
+    // green-only points, cells [a0-2, a0+TA+1]; EE(a) at vee x, OO(a) at voo x+1, green (2a+1,2b) at rg[2y][2x+1]
+    for (int q = tid; q < (TA + 4) * (TB + 4); q += 256) {
+        const int x = q % (TA + 4), y = q / (TA + 4);
+        const int a = a0 - 2 + x, b = b0 - 2 + y;
+        float voe = 0.f, veo = 0.f;
+        if (a >= 0 && a <= nb && b >= 1 && b <= nb)
+            voe = ((S.vee[y][x] + S.vee[y][x + 1]) + (S.voo[y][x + 1] + S.voo[y + 1][x + 1]) - c1 * S.rg[2 * y][2 * x + 1]) *
+                  0.25f;
+        if (a >= 1 && a <= nb && b >= 0 && b <= nb)
+            veo = ((S.voo[y + 1][x] + S.voo[y + 1][x + 1]) + (S.vee[y][x] + S.vee[y + 1][x]) - c1 * S.rg[2 * y + 1][2 * x]) *
+                  0.25f;
+        S.voe[y][x] = voe;
+        S.veo[y][x] = veo;
+    }
+    __syncthreads();
+    // red points (green C) of cells [a0-1, a0+TA]; F smem index of cell a is a - a0 + 2 = x + 1
+    for (int q = tid; q < (TA + 2) * (TB + 2); q += 256) {
+        const int x = q % (TA + 2), y = q / (TA + 2);
+        const int a = a0 - 1 + x, b = b0 - 1 + y;
+        const int fx = x + 1, fy = y + 1;
+        float vEE = 0.f, vOO = 0.f;
+        if (a >= 1 && a <= nb && b >= 1 && b <= nb)
+            vEE = ((S.voe[fy][fx - 1] + S.voe[fy][fx]) + (S.veo[fy - 1][fx] + S.veo[fy][fx]) - c1 * S.rg[2 * fy][2 * fx]) * 0.25f;
+        if (a >= 0 && a <= nb && b >= 0 && b <= nb)
+            vOO = ((S.veo[fy][fx] + S.veo[fy][fx + 1]) + (S.voe[fy][fx] + S.voe[fy + 1][fx]) - c1 * S.rg[2 * fy + 1][2 * fx + 1]) *
+                  0.25f;
+        S.vce[y][x] = vEE;
+        S.vco[y][x] = vOO;
+    }
+    __syncthreads();
+    // green v at fine (gx, gy) with gx in [2a0-2, 2a0+2TA+1]
+    auto vat = [&](int gx, int gy) -> float {
+        const int a = gx >> 1, b = gy >> 1;
+        const int cx = a - a0 + 1, cy = b - b0 + 1;  // C index; F index = C index + 1
+        if (gx & 1) return (gy & 1) ? S.vco[cy][cx] : S.voe[cy + 1][cx + 1];
+        return (gy & 1) ? S.veo[cy + 1][cx + 1] : S.vce[cy][cx];
+    };
+    float sq = 0.f;
+    for (int q = tid; q < 4 * TA * TB; q += 256) {
+        // fine points of the own cells, row-major over a 2TA x 2TB block
+        const int lx = q % (2 * TA), ly = q / (2 * TA);
+        const int i = 2 * a0 + lx, j = 2 * b0 + ly;
+        if (i < 1 || i > n || j < 1 || j > n) continue;
+        const float vc = vat(i, j);
+        float hi, lo;
+        lap_sum(vat(i - 1, j), vat(i + 1, j), vat(i, j - 1), vat(i, j + 1), vc, hi, lo);
+        const size_t cu = (size_t)j * up + i, cr = (size_t)j * rp + i;
+        u[cu] += widen(vc);
+        const double rn = fma(-ih2, widen(hi), fma(-ih2, widen(lo), r64[cr]));
+        r64[cr] = rn;
+        const float rf = (float)rn;
+        rnew(i, j) = rf;
+        sq = fmaf(rf, rf, sq);
+    }
+    const double s = block_sum((double)sq, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x + gridDim.x * blockIdx.y] = s;
+}
+
+// finest residual, written both in the level precision (FP32) and in FP64 to
+// r64 (the carried residual of the fused update); otherwise as k_res0_2d
+__global__ void __launch_bounds__(256) k_res0_64_2d(const double *__restrict__ f, const double *__restrict__ u,
+                                                    int up, int n, double ih2, A2<float> r, double *r64, int rp,
+                                                    double *part, const int *done, Bt B) {
+    __shared__ double sh[32];
+    const int prob = blockIdx.z;
+    if (stop(bt_done(done, prob, B))) return;
+    if (B.ftab) { f = B.ftab[prob]; u = B.utab[prob]; }
+    r = bt_at(r, prob, B);
+    r64 = bt_ptr(r64, prob, B);
+    const int i = blockIdx.x * 32 + threadIdx.x + 1;
+    const int j0 = (blockIdx.y * 8 + threadIdx.y) * RES_ROWS + 1;
+    float acc = 0.f;
+    if (i <= n && j0 <= n) {
+        const double *uc = u + (size_t)j0 * up + i;
+        const double *fc = f + (size_t)j0 * up + i;
+        double um = uc[-up], u0 = uc[0];
+#pragma unroll
+        for (int q = 0; q < RES_ROWS; q++) {
+            if (j0 + q > n) break;
+            const double upn = uc[up];
+            const double s = (uc[-1] + uc[1]) + (um + upn);
+            const double res = fma(-ih2, fma(-4.0, u0, s), fc[0]);
+            const float rf = (float)res;
+            r(i, j0 + q) = rf;
+            r64[(size_t)(j0 + q) * rp + i] = res;
+            acc = fmaf(rf, rf, acc);
+            um = u0; u0 = upn;
+            uc += up; fc += up;
+        }
+    }
+    double s = block_sum((double)acc, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        part[(size_t)prob * B.nparts + blockIdx.x + gridDim.x * blockIdx.y] = s;
 }
 
 }  // namespace mg

@@ -88,6 +88,15 @@ struct mg_ctx {
     int kc = 0;                 // first pair run by the coarse thread block
     CoarsePlan2d plan2d{};
     size_t plan_bytes = 0;
+    // mixed 2D: finest pair fused with the next residual (carried FP64 residual
+    // r64 and a second FP32 finest-residual buffer r32b, both in the pool)
+    bool rr = false;
+    void *r64 = nullptr;
+    void *r32b = nullptr;
+    int r64_pitch = 0;
+    // 3D diagonal path: triples with side <= 15 in one thread block
+    bool fast3d = false;
+    CoarsePlan3d plan3d{};
     double *ft = nullptr;       // order-4 right-hand side (caller pitch), FP64
     int nparts = 0;             // partial sums written by the last residual (per problem)
     // batch: nprob problems of this size, level pools pstride bytes apart,
@@ -424,6 +433,39 @@ void plan_fast2d(mg_ctx *c) {
 
 // finest residual for every configuration: column (2D) / plane (3D) marching,
 // FP64 stencil, level-precision output, FP32 squares in mixed precision
+void plan_fast3d(mg_ctx *c) {
+    c->fast3d = c->d.dim == 3 && c->d.hierarchy == MG_DIAG;
+    if (!c->fast3d) return;
+    int kc = 0;
+    while (kc < c->K && c->lv[3 * kc].side > 15) kc++;
+    c->kc = kc;
+    CoarsePlan3d &P = c->plan3d;
+    P = CoarsePlan3d{};
+    P.kc = kc;
+    P.K = c->K;
+    int off = 0;
+    auto take = [&](int elems) { int o = off; off += (elems + 3) / 4 * 4; return o; };
+    const int ntri = c->K - kc;
+    for (int t = 0; t <= ntri; t++) {
+        const int n = c->lv[3 * (kc + t)].side, g = (n + 2) * (n + 2) * (n + 2);
+        P.nk[t] = n;
+        P.og_r[t] = take(g);
+        P.og_v[t] = take(g);
+        if (t < ntri) {
+            const int nb = (n - 1) / 2, e = (nb + 2) * (nb + 2) * (nb + 2);
+            for (int q = 0; q < 4; q++) { P.orr[t][q] = take(e); P.orv[t][q] = take(e); }
+            for (int q = 0; q < 2; q++) { P.omr[t][q] = take(e); P.omv[t][q] = take(e); }
+            const double hk = c->h * (double)(1 << (kc + t)), h2 = hk * hk;
+            P.cm[t] = 4.0 * c->d.omega[0] * h2;
+            P.cr1[t] = 2.0 * c->d.omega[1] * h2;
+            P.cr2[t] = 4.0 * c->d.omega[2] * h2;
+            P.cg[t] = c->d.omega[3] * h2;
+        }
+    }
+    P.total = off;
+    c->plan_bytes = (size_t)off * c->esz;
+}
+
 template <typename T> int launch_res_fast(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
     const int n = c->d.n;
     const Level &l0 = c->lv[0];
@@ -459,12 +501,14 @@ void launch_rhs4(mg_ctx *c, const double *f, cudaStream_t s) {
 int tile_class(int nb) { return nb + 1 >= 1024 ? 0 : nb + 1 >= 256 ? 1 : 2; }
 
 template <typename T, int TA, int TB>
-void launch_down_pair(mg_ctx *c, int k, const int *done, cudaStream_t s) {
+void launch_down_pair(mg_ctx *c, int k, const int *done, cudaStream_t s, bool alt = false) {
     const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
     const int nb = r.nb;
     dim3 grid((nb + TA) / TA, (nb + TB) / TB, 1);
+    const T *galt = (alt && k == 0 && c->rr) ? (const T *)c->r32b : nullptr;
+    const int *par = galt ? &c->ctl->par : nullptr;
     LAUNCH_B(TAG_LEVELS, (k_down_pair_2d<T, TA, TB>), grid, B2, a2<const T>(g.r[0], g), a2<T>(r.r[0], r),
-             a2<T>(r.r[1], r), a2<T>(b.r[0], b), nb, done);
+             a2<T>(r.r[1], r), a2<T>(b.r[0], b), nb, galt, par, done);
 }
 
 template <typename T, int TA, int TB>
@@ -513,6 +557,60 @@ template <typename T> void vcycle_fast2d(mg_ctx *c, double *u, const int *done, 
     }
 }
 
+template <int TA, int TB> int launch_up0_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
+    const Level &g = c->lv[0], &r = c->lv[1], &b = c->lv[2];
+    const int nb = r.nb;
+    const double hk = c->h, p = c->d.omega[0];
+    dim3 grid((nb + TA) / TA, (nb + TB) / TB, 1);
+    LAUNCH_SMEM_B(TAG_FINEST_UP, (k_up0_rr_2d<TA, TB>), grid, B2, sizeof(UpRRSmem<TA, TB>), a2<const float>(b.v[0], b),
+                  a2<const float>(r.r[0], r), a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b,
+                  (double *)c->r64, c->r64_pitch, u, c->d.pitch, nb, (float)(2.0 * p * hk * hk), (float)(p * hk * hk),
+                  1.0 / (hk * hk), c->part, &c->ctl->par, done);
+    return (int)(grid.x * grid.y);
+}
+
+// one cycle of the fused mixed 2D path: restriction, coarse block, prolongation,
+// and the finest pair fused with u += v and the next residual; returns the
+// number of norm partial sums written per problem
+int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
+    for (int k = 0; k < c->kc; k++) {
+        switch (tile_class(c->lv[2 * k + 1].nb)) {
+        case 0: launch_down_pair<float, 32, 16>(c, k, done, s, true); break;
+        case 1: launch_down_pair<float, 16, 8>(c, k, done, s, true); break;
+        default: launch_down_pair<float, 8, 8>(c, k, done, s, true); break;
+        }
+    }
+    {
+        const Level &g = c->lv[2 * c->kc];
+        LAUNCH_SMEM_B(TAG_LEVELS, (k_coarse_cta_2d<float>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan2d,
+                      a2<const float>(g.r[0], g), a2<float>(g.v[0], g), c->G, done);
+    }
+    for (int k = c->kc - 1; k >= 1; k--) {
+        switch (tile_class(c->lv[2 * k + 1].nb)) {
+        case 0: launch_up_pair<float, 32, 16>(c, k, u, done, s); break;
+        case 1: launch_up_pair<float, 16, 8>(c, k, u, done, s); break;
+        default: launch_up_pair<float, 8, 8>(c, k, u, done, s); break;
+        }
+    }
+    switch (tile_class(c->lv[1].nb)) {
+    case 0: return launch_up0_rr<32, 16>(c, u, done, s);
+    case 1: return launch_up0_rr<16, 8>(c, u, done, s);
+    default: return launch_up0_rr<8, 8>(c, u, done, s);
+    }
+}
+
+// direct FP64 residual of the fused path (start of a solve): FP32 copy in the
+// current buffer (parity 0 at the start) and the carried FP64 residual
+int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
+    const int n = c->d.n;
+    const Level &l0 = c->lv[0];
+    dim3 g((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
+    LAUNCH_B(TAG_RESIDUAL, (k_res0_64_2d), g, B2, f, u, c->d.pitch, n, 1.0 / (c->h * c->h), a2<float>(l0.r[0], l0),
+             (double *)c->r64, c->r64_pitch, c->part, done);
+    c->nparts = (int)(g.x * g.y);
+    return c->nparts;
+}
+
 template <typename T> cudaError_t set_smem_attrs(const mg_ctx *c) {
     cudaError_t e = cudaFuncSetAttribute(k_coarse_cta_2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
 #define MG_UP_ATTR(TA, TB)                                                                                         \
@@ -526,6 +624,12 @@ template <typename T> cudaError_t set_smem_attrs(const mg_ctx *c) {
     MG_UP_ATTR(16, 8)
     MG_UP_ATTR(8, 8)
 #undef MG_UP_ATTR
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_up0_rr_2d<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpRRSmem<32, 16>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_up0_rr_2d<16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpRRSmem<16, 8>));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_up0_rr_2d<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpRRSmem<8, 8>));
     return e;
 }
 
@@ -534,6 +638,22 @@ mg_status vcycle_t(mg_ctx *c, const double *f, double *u, const int *done, bool 
     if (with_residual) launch_res_fast<T>(c, f, u, done, s);
     if (c->fast2d) {
         vcycle_fast2d<T>(c, u, done, s);
+        CKL("vcycle launch");
+        return MG_OK;
+    }
+    if (c->fast3d) {
+        const int lc = 3 * c->kc;  // first level run by the coarse block
+        for (int l = 0; l < lc; l++) launch_restrict<T>(c, l, done, s);
+        const Level &g = c->lv[lc];
+        LAUNCH_SMEM_B(TAG_LEVELS, (k_coarse_cta_3d<T>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan3d,
+                      a3<const T>(g.r[0], g), a3<T>(g.v[0], g), c->G, done);
+        for (int l = lc - 1; l >= 0; l--) launch_prolong<T>(c, l, c->d.omega, l == 0 ? u : nullptr, done, s);
+        if (lc == 0) {
+            const Level &l0 = c->lv[0];
+            const int n = c->d.n;
+            LAUNCH_B(TAG_FINEST_UP, (k_add_axis<T>), grid3(n, n, n), B2, (const T *)l0.v[0], l0.pitch, l0.rows, n, 3, u,
+                     c->d.pitch, n + 2, done);
+        }
         CKL("vcycle launch");
         return MG_OK;
     }
@@ -626,6 +746,11 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     build_levels(c);
     size_t total = 0;
     for (auto &l : c->lv) total += (size_t)l.ncos * 2 * ((l.len * c->esz + 255) / 256 * 256);
+    // fused update + residual of the mixed 2D diagonal solve (needs at least one pair outside the coarse block)
+    c->rr = d->dim == 2 && d->hierarchy == MG_DIAG && d->precision == MG_MIXED && d->order == 2 && d->n > 63;
+    const size_t r64_bytes = c->rr ? ((size_t)c->lv[0].pitch * c->lv[0].rows * 8 + 255) / 256 * 256 : 0;
+    const size_t r32_bytes = c->rr ? (c->lv[0].len * 4 + 255) / 256 * 256 : 0;
+    total += r64_bytes + r32_bytes;
     c->nprob = nprob;
     c->pstride = nprob > 1 ? total : 0;
     if (cudaMalloc(&c->pool, total * nprob) != cudaSuccess) { cudaGetLastError(); mg_destroy(c); return MG_ENOMEM; }
@@ -636,8 +761,23 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
         for (int q = 0; q < l.ncos; q++) { l.r[q] = p; p += bytes; }
         for (int q = 0; q < l.ncos; q++) { l.v[q] = p; p += bytes; }
     }
+    if (c->rr) {
+        c->r64 = p; p += r64_bytes;
+        c->r32b = p; p += r32_bytes;
+        c->r64_pitch = c->lv[0].pitch;
+    }
     c->max_blocks = residual_blocks(c);
     plan_fast2d(c);
+    plan_fast3d(c);
+    if (c->fast3d) {
+        const cudaError_t e = d->precision == MG_FP64
+            ? cudaFuncSetAttribute(k_coarse_cta_3d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes)
+            : cudaFuncSetAttribute(k_coarse_cta_3d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
+        if (e != cudaSuccess) {
+            mg_destroy(c);
+            return cuda_fail(e, "mg_create shared-memory attributes (3D)");
+        }
+    }
     if (c->fast2d) {
         const cudaError_t e = d->precision == MG_FP64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c);
         if (e != cudaSuccess) {
@@ -786,6 +926,7 @@ mg_status mg_vcycle(mg_ctx *c, const double *f, double *u, void *stream) {
 
 // residual of the current iterate into level 0 (+ partial sums); returns their count
 static int solve_residual(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
+    if (c->rr) return launch_res_rr(c, f, u, done, s);
     return c->d.precision == MG_FP64 ? launch_res_fast<double>(c, f, u, done, s)
                                      : launch_res_fast<float>(c, f, u, done, s);
 }
@@ -847,13 +988,18 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     CK(cudaStreamUpdateCaptureDependencies(s, &wnode, nullptr, 1, cudaStreamSetCaptureDependencies));
     CK(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const long long l1 = c->launches;
-    mg_status stv = fp64 ? vcycle_t<double>(c, f, u, done, false, s2) : vcycle_t<float>(c, f, u, done, false, s2);
-    if (stv != MG_OK) {
-        cudaStreamEndCapture(s2, &body);
-        c->capturing = false;
-        return stv;
+    int np2;
+    if (c->rr) {
+        np2 = vcycle_rr(c, u, done, s2);
+    } else {
+        mg_status stv = fp64 ? vcycle_t<double>(c, f, u, done, false, s2) : vcycle_t<float>(c, f, u, done, false, s2);
+        if (stv != MG_OK) {
+            cudaStreamEndCapture(s2, &body);
+            c->capturing = false;
+            return stv;
+        }
+        np2 = solve_residual(c, f, u, nullptr, s2);
     }
-    const int np2 = solve_residual(c, f, u, nullptr, s2);
     launch_ctrl(c, np2, 0, loop, 1, s2);
     c->g_body_kernels = c->launches - l1;
     CK(cudaStreamEndCapture(s2, &body));
@@ -896,9 +1042,13 @@ static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double r
     Ctrl host{};
     for (int cyc = 0; cyc < max_cycles; cyc += 4) {
         for (int q = 0; q < 4 && cyc + q < max_cycles; q++) {
-            mg_status st = fp64 ? vcycle_t<double>(c, f, u, done, false, s) : vcycle_t<float>(c, f, u, done, false, s);
-            if (st != MG_OK) return st;
-            np = solve_residual(c, f, u, done, s);
+            if (c->rr) {
+                np = vcycle_rr(c, u, done, s);
+            } else {
+                mg_status st = fp64 ? vcycle_t<double>(c, f, u, done, false, s) : vcycle_t<float>(c, f, u, done, false, s);
+                if (st != MG_OK) return st;
+                np = solve_residual(c, f, u, done, s);
+            }
             launch_ctrl(c, np, 0, none, 0, s);
         }
         CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));

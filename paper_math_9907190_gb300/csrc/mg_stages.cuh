@@ -605,6 +605,7 @@ struct Ctrl {
     int cycles;     // corrections applied
     int max_cycles;
     int status;     // 0 ok, -4 not converged, -5 diverged
+    int par;        // which of the two FP32 finest residual buffers is current (fused update path)
 };
 
 // deterministic sum of part[0..nblk) by one block of 1024 threads (fixed order)
@@ -626,6 +627,7 @@ __global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, in
     }
     double s = sum_parts(part, nblk, sh);
     if (threadIdx.x != 0) return;
+    if (!first) ctl->par ^= 1;
     ctl->r2 = s;
     double rel = ctl->f2 > 0.0 ? sqrt(s / ctl->f2) : 0.0;
     ctl->relres = rel;
@@ -647,7 +649,7 @@ __global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, in
 
 __global__ void k_ctrl_init(Ctrl *ctl, double rtol, int max_cycles) {
     ctl->r2 = 0.0; ctl->relres = 0.0; ctl->rel0 = 0.0; ctl->rtol = rtol;
-    ctl->done = 0; ctl->cycles = 0; ctl->max_cycles = max_cycles; ctl->status = 0;
+    ctl->done = 0; ctl->cycles = 0; ctl->max_cycles = max_cycles; ctl->status = 0; ctl->par = 0;
 }
 
 // per problem of a batch (one block each): f2 = sum of that problem's partials
@@ -661,7 +663,7 @@ __global__ void k_ctrl_init_b(Ctrl *ctl, int nprob, double rtol, int max_cycles)
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nprob; p += gridDim.x * blockDim.x) {
         Ctrl &c = ctl[p];
         c.r2 = 0.0; c.relres = 0.0; c.rel0 = 0.0; c.rtol = rtol;
-        c.done = 0; c.cycles = 0; c.max_cycles = max_cycles; c.status = 0;
+        c.done = 0; c.cycles = 0; c.max_cycles = max_cycles; c.status = 0; c.par = 0;
     }
 }
 
@@ -674,6 +676,7 @@ __global__ void k_ctrl_b(const double *part, int nblk, Ctrl *ctl, double *hist, 
     if (!first && c->done) return;
     double s = sum_parts(part + (size_t)p * nblk, nblk, sh);
     if (threadIdx.x != 0) return;
+    if (!first) c->par ^= 1;
     c->r2 = s;
     double rel = c->f2 > 0.0 ? sqrt(s / c->f2) : 0.0;
     c->relres = rel;
