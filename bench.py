@@ -39,23 +39,23 @@ RTOL = 1e-10
 WORKLOAD = "2D unit square, h=1/4096 (4095^2 = 16.8M unknowns), f ~ U[-1,1] seed 1, zero Dirichlet; " \
            "diagonal V-cycle (p=1.052), mixed FP64/FP32, solve from u=0 to 1e-10 relative residual"
 
-# Algorithmic cost of the probed kernel (family 0: the finest-grid residual
-# k_res0_2d) per finest unknown: reads u and f in FP64, writes r in FP32; the
-# paper counts 7 flops per point for the residual (its squared norm is taken
-# in FP32 in mixed precision).  With fused multiply-adds the FP64 pipe issues
-# 5 operations per point.
+# The dominant kernel of the mixed solve is the finest pair fused with the
+# next residual (k_up0_rr_2d, probe family 1).  Algorithmic bytes per finest
+# unknown: reads u (8), the carried FP64 residual (8), the FP32 residual (4),
+# the red residual (N/2 x 4 B = 2) and the blue correction (N/4 x 4 B = 1);
+# writes u (8), the FP64 residual (8), the new FP32 residual (4): 43 B.  FP64
+# pipe operations per point: 3 (u + v, and r - ih2 (hi + lo) as two FMAs).
 PROBE = {
-    "family": 0,
-    "name": "k_res0_2d: finest residual r = f - L u (FP64 stencil), FP32 r and FP32 squares",
-    "bytes_per_point": 8 + 8 + 4,
-    "fp64_flops_per_point": 7,
-    "fp64_pipe_ops_per_point": 5,
+    "family": 1,
+    "name": "k_up0_rr_2d<32,16>: finest Jacobi prolongation + u += v + carried residual r -= L v",
+    "bytes_per_point": 43,
+    "fp64_pipe_ops_per_point": 3,
 }
-# DRAM traffic of one k_res0_2d launch on the 4095^2 workload from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum); reported only while
-# the kernel's source is the one that was captured.
-TRAFFIC = {"kernel": "k_res0_2d", "bytes": 268.639488e6 + 52.455424e6,
-           "source_sha1": "94ca145e78e61b9ecdfb8679c4cfade682bc0926"}
+# DRAM traffic of one launch on the 4095^2 workload from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the
+# kernel's source is the one that was captured.
+TRAFFIC = {"kernel": "k_up0_rr_2d", "bytes": 386.268672e6 + 279.316224e6,
+           "source_sha1": "d5594066fc62ed22db3e19ef69ade811602face8"}
 
 
 def read_peaks():
@@ -111,6 +111,13 @@ def extra_measurements(dev, stream):
         u = c.new_grid()
         ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u.zero_(), rtol=RTOL, max_cycles=60), 5, stream)
         out["square4095_fp64"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc, "relres": rel}
+    for prec in ("mixed", "fp64"):  # the conventional 2^-l V-cycle the paper compares with
+        with Context(2, N_SIDE, hierarchy="usual", precision=prec) as c:
+            u = c.new_grid()
+            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u.zero_(), rtol=RTOL, max_cycles=80), 3, stream)
+            out[f"square4095_usual_{prec}"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc,
+                                               "relres": rel, "workload": "same problem, conventional V-cycle "
+                                               "(full weighting, bilinear + red-black Jacobi, p = 1.121)"}
     del f
     f3 = torch.from_numpy(I.cube(255)).to(dev)
     for prec in ("mixed", "fp64"):
@@ -279,6 +286,7 @@ def main():
     import torch.distributed as dist
 
     from paper_math_9907190_gb300 import Context
+    from paper_math_9907190_gb300 import dist as D
     from paper_math_9907190_gb300 import inputs as I
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -332,10 +340,7 @@ def main():
         barrier()
     launches = ctx.launch_count() - launches0
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = D.max_over_ranks(ms, dev)
     value = world * N / (ms_max * 1e-3)
 
     # end to end through the public API: pinned host f in, host u out, every step
@@ -355,38 +360,31 @@ def main():
         u_pin.copy_(uu, non_blocking=True)
     e1.record(stream)
     barrier()
-    e2e_ms = torch.tensor([e0.elapsed_time(e1) / args.steps], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2e_ms.item())
+    e2e_ms = D.max_over_ranks(e0.elapsed_time(e1) / args.steps, dev)
 
-    # live probe of the dominant kernel: the same V-cycle, its finest residual bracketed by events
+    # live probe of the dominant kernel inside the same solve: every launch of
+    # its family bracketed by CUDA events on the launching stream (the solver
+    # runs its host-driven loop while probed; the kernels are the same)
     ctx.probe_set(PROBE["family"])
-    uu = torch.zeros_like(f)
     for _ in range(args.steps):
-        ctx.vcycle(f, uu)
+        step()
     nprobe, probe_ms = ctx.probe_read()
     ctx.probe_set(-1)
     avg_ms = probe_ms / max(nprobe, 1)
     peaks = read_peaks()
-    flops = PROBE["fp64_flops_per_point"] * N
-    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
     bytes_ = PROBE["bytes_per_point"] * N
+    achieved = bytes_ / (avg_ms * 1e-3) / 1e9
     pipe = PROBE["fp64_pipe_ops_per_point"] * N / (avg_ms * 1e-3)
     sha = kernel_source_sha1(TRAFFIC["kernel"])
     traffic = TRAFFIC["bytes"] if (TRAFFIC["bytes"] and sha == TRAFFIC["source_sha1"]) else None
-    roofline = {"bound": "alu", "kernel": PROBE["name"], "achieved": achieved_tf,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                "traffic": traffic, "algorithmic_bytes": bytes_, "avg_launch_ms": avg_ms,
-                "launches_probed": nprobe,
+    roofline = {"bound": "hbm", "kernel": PROBE["name"], "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": traffic, "algorithmic_bytes": bytes_,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
+                "avg_launch_ms": avg_ms, "launches_probed": nprobe,
                 "fp64_pipe": {"ops_per_point": PROBE["fp64_pipe_ops_per_point"], "achieved_ops_s": pipe,
-                              "peak_ops_s": FP64_PIPE_OPS_PEAK, "frac": pipe / FP64_PIPE_OPS_PEAK},
-                "hbm_side": {"achieved_gbs": bytes_ / (avg_ms * 1e-3) / 1e9,
-                             "peak_gbs": peaks.get("hbm_gbs", 6800.0),
-                             "frac": bytes_ / (avg_ms * 1e-3) / 1e9 / peaks.get("hbm_gbs", 6800.0),
-                             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
-                "peak_note": "nominal FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived); "
-                             "achieved counts the paper's 7 flops per residual point"}
+                              "peak_ops_s": FP64_PIPE_OPS_PEAK, "frac": pipe / FP64_PIPE_OPS_PEAK,
+                              "peak_note": "152 SMs x 2 FP64 ops/clk x 2.07 GHz (nominal, derived)"}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": warm, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
@@ -408,6 +406,8 @@ def main():
             line["extra"]["square4095_fp64"]["ms"] / ms_max)
         line["extra"]["mixed_vs_fp64_speedup_batch512"] = (
             line["extra"]["batch512_fp64"]["ms"] / line["extra"]["batch512_mixed"]["ms"])
+        line["extra"]["diag_vs_usual_speedup_square4095_mixed"] = (
+            line["extra"]["square4095_usual_mixed"]["ms"] / ms_max)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, u_orc = oracle_cpu_baseline(f_host)
         line["cpu_baseline"] = cb

@@ -154,6 +154,34 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *u, void *stream);
 mg_status mg_solve(mg_ctx *ctx, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
                    double *relres_out, double *history, void *stream);
 
+/* Replace the context's over-relaxation weights (same meaning as
+ * mg_desc.omega, host, 4 entries). */
+mg_status mg_set_omega(mg_ctx *ctx, const double *omega);
+
+/* Convergence factor of the context's V-cycle (the paper's rho, Tables 1-3:
+ * the slowest decay of the error) by power iteration on its error
+ * propagation: with f = 0 every V-cycle maps the error u to u + B(-L u); u is
+ * renormalised after each cycle and rho_out (host) is the geometric mean of
+ * the norm ratios of cycles skip..cycles-1.  zero_f: caller device array of
+ * zeros (full grid, caller pitch; order 4 reads its ring too); u: caller
+ * device array holding the start vector (zero ring), overwritten.
+ * 2 <= cycles <= 4096, 0 <= skip < cycles.  Synchronous. */
+mg_status mg_rho(mg_ctx *ctx, const double *zero_f, double *u, int cycles, int skip, double *rho_out,
+                 void *stream);
+
+/* Two-stage fourth-order solve (Section 2.4, and Section 3.4 for 3D: the
+ * fourth-order solution is best reached by first converging with second-order
+ * residuals, then refining with a few fourth-order V-cycles).  ctx must have
+ * order 4.  Stage 1 runs the context's V-cycle on the second-order residual
+ * r = f - L_h u with weights omega2 (host, 4 entries; NULL: the context's)
+ * until its relative residual <= rtol2 (or max_cycles); stage 2 continues from
+ * that u with the fourth-order residual (Eq. Efos2 / Eq. Efos4) and the
+ * context's weights until ||f~ - L u|| / ||f~|| <= rtol.  Cycle counts of the
+ * stages (host, nullable) and the final fourth-order relative residual. */
+mg_status mg_solve_two_stage(mg_ctx *ctx, const double *f, double *u, const double *omega2, double rtol2,
+                             double rtol, int max_cycles, int *cycles2_out, int *cycles4_out, double *relres_out,
+                             void *stream);
+
 /* Batches of independent problems (no paper counterpart: the paper solves
  * one problem at a time).  A batch holds nprob 2D or 3D problems of sides
  * n[0..nprob) (each 2^m - 1), all with the same hierarchy, order (2 only),
@@ -178,6 +206,27 @@ mg_status mg_batch_destroy(mg_batch *batch);
 mg_status mg_solve_batched(mg_batch *batch, const double *const *f, double *const *u, double rtol, int max_cycles,
                            int *cycles_out, double *relres_out, void *stream);
 mg_status mg_batch_launch_count(const mg_batch *batch, long long *launches);
+
+/* Autotuning (no paper counterpart).  mg_tune times, on this context's own
+ * buffers with the caller's f and u, the size cut-off below which whole
+ * pairs/triples run in one thread block (whole V-cycles for each candidate)
+ * and the tile shape of every pair kernel (each kernel alone, three shapes),
+ * and keeps the fastest.  The choice is appended to the cache file
+ * `cache_path` (NULL: the file named by the environment variable
+ * DIAGMG_TUNE_CACHE; neither: no file) as one JSON object per line keyed by
+ * device name, dim, n, hierarchy, precision and batch size; a later mg_tune
+ * with a matching entry applies it without measuring.  u is scratch and is
+ * left zero (interior and ring).  measured_out (host, nullable): 1 if timed,
+ * 0 if taken from the cache or nothing is tunable.  Synchronous.
+ * mg_tune_info reports the cut-off (0 = default) and the tile class of each
+ * pair kernel outside the thread block (0: 32x16 cells, 1: 16x8, 2: 8x8);
+ * tiles_down / tiles_up need 32 entries.  mg_batch_tune does the same for
+ * every size group of a batch (f, u as in mg_solve_batched). */
+mg_status mg_tune(mg_ctx *ctx, const double *f, double *u, const char *cache_path, int *measured_out,
+                  void *stream);
+mg_status mg_tune_info(const mg_ctx *ctx, int *cut_side, int *npairs, int *tiles_down, int *tiles_up);
+mg_status mg_batch_tune(mg_batch *batch, const double *const *f, double *const *u, const char *cache_path,
+                        void *stream);
 
 /* Diagnostics (no paper counterpart).  mg_launch_count: kernels this context
  * has launched since creation (host counter).  mg_probe_set: when family >= 0,

@@ -49,6 +49,12 @@ SIGNATURES = {
     "mg_batch_destroy": (_i, [_vp]),
     "mg_solve_batched": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i, _ip, _dp, _vp]),
     "mg_batch_launch_count": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "mg_tune": (_i, [_vp, _vp, _vp, ctypes.c_char_p, _ip, _vp]),
+    "mg_set_omega": (_i, [_vp, _dp]),
+    "mg_rho": (_i, [_vp, _vp, _vp, _i, _i, _dp, _vp]),
+    "mg_solve_two_stage": (_i, [_vp, _vp, _vp, _dp, _d, _d, _i, _ip, _ip, _dp, _vp]),
+    "mg_tune_info": (_i, [_vp, _ip, _ip, _ip, _ip]),
+    "mg_batch_tune": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.c_char_p, _vp]),
     "mg_strerror": (ctypes.c_char_p, [_i]),
     "mg_last_error": (ctypes.c_char_p, []),
 }

@@ -116,6 +116,60 @@ class Context:
         N.check(N.lib().mg_probe_read(self._h, ctypes.byref(n), ctypes.byref(ms), self._stream()), "mg_probe_read")
         return n.value, ms.value
 
+    def solve_two_stage(self, f, u=None, *, omega2=None, rtol2: float = 1e-4, rtol: float = 1e-10,
+                        max_cycles: int = 100, raise_on_fail: bool = True):
+        """mg_solve_two_stage (order-4 context): second-order V-cycles to rtol2,
+        then fourth-order cycles to rtol.  Returns (u, cycles2, cycles4, relres)."""
+        if self.order != 4:
+            raise ValueError("two-stage solves need an order-4 context")
+        u = self.new_grid() if u is None else u
+        om2 = default_omega(self.dim, self.hierarchy, 2) if omega2 is None else omega2
+        arr = (ctypes.c_double * 4)(*(list(om2) + [1.0] * (4 - len(om2))))
+        c2, c4, rel = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        st = N.lib().mg_solve_two_stage(self._h, self._grid(f, "f"), self._grid(u, "u"), arr, rtol2, rtol, max_cycles,
+                                        ctypes.byref(c2), ctypes.byref(c4), ctypes.byref(rel), self._stream())
+        if raise_on_fail:
+            N.check(st, "mg_solve_two_stage")
+        return u, c2.value, c4.value, rel.value
+
+    def set_omega(self, omega):
+        """mg_set_omega: new over-relaxation weights for later cycles."""
+        arr = (ctypes.c_double * 4)(*(list(omega) + [1.0] * (4 - len(omega))))
+        N.check(N.lib().mg_set_omega(self._h, arr), "mg_set_omega")
+        self.omega = tuple(omega)
+
+    def rho(self, cycles: int = 60, skip: int = 40, seed: int = 0) -> float:
+        """mg_rho: convergence factor of the V-cycle by power iteration from a
+        seeded random start (interior U[-1, 1])."""
+        g = torch.Generator(device="cpu").manual_seed(seed)
+        u = torch.rand((self.n + 2,) * self.dim, generator=g, dtype=torch.float64) * 2 - 1
+        ring = torch.ones_like(u, dtype=torch.bool)
+        ring[(slice(1, -1),) * self.dim] = False
+        u[ring] = 0.0
+        u = u.to(self.device)
+        z = torch.zeros_like(u)
+        out = ctypes.c_double()
+        N.check(N.lib().mg_rho(self._h, self._grid(z, "zero_f"), self._grid(u, "u"), cycles, skip, ctypes.byref(out),
+                               self._stream()), "mg_rho")
+        return out.value
+
+    def tune(self, f, u=None, cache: str | None = None) -> bool:
+        """mg_tune: measure (or take from the cache file) the coarse-block
+        cut-off and the tile shape of every pair kernel; u is scratch, left 0.
+        Returns True when it measured."""
+        u = self.new_grid() if u is None else u
+        measured = ctypes.c_int()
+        N.check(N.lib().mg_tune(self._h, self._grid(f, "f"), self._grid(u, "u"),
+                                cache.encode() if cache else None, ctypes.byref(measured), self._stream()), "mg_tune")
+        return bool(measured.value)
+
+    def tune_info(self):
+        """(cut-off side (0 = default), tile classes of the down kernels, of the up kernels)."""
+        cut, npair = ctypes.c_int(), ctypes.c_int()
+        dn, upv = (ctypes.c_int * 32)(), (ctypes.c_int * 32)()
+        N.check(N.lib().mg_tune_info(self._h, ctypes.byref(cut), ctypes.byref(npair), dn, upv), "mg_tune_info")
+        return cut.value, list(dn[: npair.value]), list(upv[: npair.value])
+
     # -- the C ABI, one method per call ------------------------------------
     def residual(self, f, u, r=None, norm: bool = True):
         """mg_residual: returns sum(r^2) (float) when norm, else None."""
@@ -208,6 +262,16 @@ class Batch:
         v = ctypes.c_longlong()
         N.check(N.lib().mg_batch_launch_count(self._h, ctypes.byref(v)), "mg_batch_launch_count")
         return v.value
+
+    def tune(self, fs, us=None, cache: str | None = None):
+        """mg_batch_tune: tune every size group (us are scratch, left zero)."""
+        nb = len(self.sides)
+        us = [torch.zeros_like(f) for f in fs] if us is None else us
+        fp = (ctypes.c_void_p * nb)(*[f.data_ptr() for f in fs])
+        up = (ctypes.c_void_p * nb)(*[u.data_ptr() for u in us])
+        stream = ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        N.check(N.lib().mg_batch_tune(self._h, fp, up, cache.encode() if cache else None, stream), "mg_batch_tune")
+        return us
 
     def solve(self, fs, us=None, *, rtol: float = 1e-10, max_cycles: int = 100, raise_on_fail: bool = True):
         """fs: list of CUDA float64 full grids; us: warm starts (default zeros).

@@ -17,6 +17,12 @@
 
 namespace mg {
 
+// loop of a 256-thread block over the points (x, y) of a W x H region, the
+// points spread evenly over all threads (x fastest)
+#define MG_FOR2(W, H)                                                                             \
+    for (int q_ = threadIdx.x + 32 * threadIdx.y, x = 0, y = 0;                                   \
+         q_ < (W) * (H) && ((x = q_ % (W)), (y = q_ / (W)), true); q_ += 256)
+
 
 template <typename T> struct SqAcc;                     // per-thread sum of r^2
 template <> struct SqAcc<float> {                       // mixed: FP32 squares
@@ -109,31 +115,30 @@ __global__ void __launch_bounds__(256) k_down_pair_2d(A2<const T> g, A2<T> ee, A
     const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
     const int n = 2 * nb + 1;
     const int tid = threadIdx.x + 32 * threadIdx.y;
-#pragma unroll 4
-    for (int q = tid; q < GX * GY; q += 256) {
-        const int x = 2 * a0 - 2 + q % GX, y = 2 * b0 - 2 + q / GX;
-        sg[q / GX][q % GX] = (x >= 0 && x <= n + 1 && y >= 0 && y <= n + 1) ? g(x, y) : T(0);
+    MG_FOR2(GX, GY) {
+        const int gx = 2 * a0 - 2 + x, gy = 2 * b0 - 2 + y;
+        sg[y][x] = (gx >= 0 && gx <= n + 1 && gy >= 0 && gy <= n + 1) ? g(gx, gy) : T(0);
     }
     __syncthreads();
     // OO(c,d) at green (2c+1, 2d+1) -> smem index (2c+1) - (2a0-2) = 2(c-a0)+3
-    for (int q = tid; q < OX * OY; q += 256) {
-        const int cx = q % OX, cy = q / OX;  // c = a0-1+cx
+    MG_FOR2(OX, OY) {
+        const int cx = x, cy = y;  // c = a0-1+cx
         const int c = a0 - 1 + cx, d = b0 - 1 + cy;
         T v = T(0);
         if (c >= 0 && c <= nb && d >= 0 && d <= nb) {
-            const int x = 2 * cx + 1, y = 2 * cy + 1;
-            v = (T(4) * sg[y][x] + (sg[y][x - 1] + sg[y][x + 1]) + (sg[y - 1][x] + sg[y + 1][x])) * T(0.125);
+            const int sx = 2 * cx + 1, sy = 2 * cy + 1;
+            v = (T(4) * sg[sy][sx] + (sg[sy][sx - 1] + sg[sy][sx + 1]) + (sg[sy - 1][sx] + sg[sy + 1][sx])) * T(0.125);
             if (cx >= 1 && cy >= 1) oo(c, d) = v;
         }
         so[cy][cx] = v;
     }
     __syncthreads();
-    for (int q = tid; q < TA * TB; q += 256) {
-        const int ax = q % TA, by = q / TA;
+    MG_FOR2(TA, TB) {
+        const int ax = x, by = y;
         const int a = a0 + ax, b = b0 + by;
         if (a < 1 || a > nb || b < 1 || b > nb) continue;
-        const int x = 2 * ax + 2, y = 2 * by + 2;  // green (2a, 2b)
-        const T e = (T(4) * sg[y][x] + (sg[y][x - 1] + sg[y][x + 1]) + (sg[y - 1][x] + sg[y + 1][x])) * T(0.125);
+        const int sx = 2 * ax + 2, sy = 2 * by + 2;  // green (2a, 2b)
+        const T e = (T(4) * sg[sy][sx] + (sg[sy][sx - 1] + sg[sy][sx + 1]) + (sg[sy - 1][sx] + sg[sy + 1][sx])) * T(0.125);
         ee(a, b) = e;
         // diagonal red neighbours OO(a-1..a, b-1..b) = so[by..by+1][ax..ax+1]
         blue(a, b) = (T(4) * e + (so[by][ax] + so[by][ax + 1]) + (so[by + 1][ax] + so[by + 1][ax + 1])) * T(0.125);
@@ -170,34 +175,25 @@ __global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T
     const int n = 2 * nb + 1;
     const int tid = threadIdx.x + 32 * threadIdx.y;
     // loads
-#pragma unroll 4
-    for (int q = tid; q < (TA + 5) * (TB + 5); q += 256) {
-        const int x = q % (TA + 5), y = q / (TA + 5);
+MG_FOR2(TA + 5, TB + 5) {
         const int a = a0 - 2 + x, b = b0 - 2 + y;
         S.b[y][x] = (a >= 0 && a <= nb + 1 && b >= 0 && b <= nb + 1) ? blue(a, b) : T(0);
     }
-#pragma unroll 4
-    for (int q = tid; q < (TA + 4) * (TB + 4); q += 256) {
-        const int x = q % (TA + 4), y = q / (TA + 4);
+MG_FOR2(TA + 4, TB + 4) {
         const int a = a0 - 2 + x, b = b0 - 2 + y;
         S.roo[y][x] = (a >= 0 && a <= nb && b >= 0 && b <= nb) ? roo(a, b) : T(0);
     }
-#pragma unroll 4
-    for (int q = tid; q < (TA + 3) * (TB + 3); q += 256) {
-        const int x = q % (TA + 3), y = q / (TA + 3);
+MG_FOR2(TA + 3, TB + 3) {
         const int a = a0 - 1 + x, b = b0 - 1 + y;
         S.ree[y][x] = (a >= 1 && a <= nb && b >= 1 && b <= nb) ? ree(a, b) : T(0);
     }
-#pragma unroll 4
-    for (int q = tid; q < (2 * TA + 4) * (2 * TB + 4); q += 256) {
-        const int x = q % (2 * TA + 4), y = q / (2 * TA + 4);
+MG_FOR2(2 * TA + 4, 2 * TB + 4) {
         const int gx = 2 * a0 - 2 + x, gy = 2 * b0 - 2 + y;
         S.rg[y][x] = (gx >= 1 && gx <= n && gy >= 1 && gy <= n) ? rg(gx, gy) : T(0);
     }
     __syncthreads();
     // red points not blue: OO(c,d), c in [a0-2, a0+TA+1]; smem x = c - a0 + 2 in voo and in b
-    for (int q = tid; q < (TA + 4) * (TB + 4); q += 256) {
-        const int x = q % (TA + 4), y = q / (TA + 4);
+    MG_FOR2(TA + 4, TB + 4) {
         const int c = a0 - 2 + x, d = b0 - 2 + y;
         T v = T(0);
         if (c >= 0 && c <= nb && d >= 0 && d <= nb)
@@ -206,8 +202,7 @@ __global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T
     }
     __syncthreads();
     // blue points refined: EE(a,b), a in [a0-1, a0+TA+1]; smem x = a - a0 + 1; OO(a-1) at voo x = a - a0 + 1
-    for (int q = tid; q < (TA + 3) * (TB + 3); q += 256) {
-        const int x = q % (TA + 3), y = q / (TA + 3);
+    MG_FOR2(TA + 3, TB + 3) {
         const int a = a0 - 1 + x, b = b0 - 1 + y;
         T v = T(0);
         if (a >= 1 && a <= nb && b >= 1 && b <= nb)
@@ -217,8 +212,7 @@ __global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T
     }
     __syncthreads();
     // green-only points: OE(a,b) at (2a+1, 2b), EO(a,b) at (2a, 2b+1); cells [a0-1, a0+TA]
-    for (int q = tid; q < (TA + 2) * (TB + 2); q += 256) {
-        const int x = q % (TA + 2), y = q / (TA + 2);
+    MG_FOR2(TA + 2, TB + 2) {
         const int a = a0 - 1 + x, b = b0 - 1 + y;
         // EE(a,b) at vee[y][x]; EE(a+1,b) vee[y][x+1]; EE(a,b+1) vee[y+1][x]
         // OO(a,b) at voo[y+1][x+1]; OO(a,b-1) voo[y][x+1]; OO(a-1,b) voo[y+1][x]
@@ -235,19 +229,18 @@ __global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T
     }
     __syncthreads();
     // red points of the own cells from the new green values, then store / update
-    for (int q = tid; q < TA * TB; q += 256) {
-        const int xa = q % TA, yb = q / TA;
-        const int a = a0 + xa, b = b0 + yb;
+    MG_FOR2(TA, TB) {
+        const int a = a0 + x, b = b0 + y;
         if (a > nb || b > nb) continue;
-        const int x = xa + 1, y = yb + 1;  // F smem index of cell (a,b)
+        const int fx = x + 1, fy = y + 1;  // F smem index of cell (a,b)
         // EE(a,b) at (2a,2b): OE(a-1,b), OE(a,b), EO(a,b-1), EO(a,b)
         T vEE = T(0);
         if (a >= 1 && b >= 1)
-            vEE = ((S.voe[y][x - 1] + S.voe[y][x]) + (S.veo[y - 1][x] + S.veo[y][x]) - c1 * S.rg[2 * y][2 * x]) * T(0.25);
+            vEE = ((S.voe[fy][fx - 1] + S.voe[fy][fx]) + (S.veo[fy - 1][fx] + S.veo[fy][fx]) - c1 * S.rg[2 * fy][2 * fx]) * T(0.25);
         // OO(a,b) at (2a+1,2b+1): EO(a,b), EO(a+1,b), OE(a,b), OE(a,b+1)
-        const T vOO = ((S.veo[y][x] + S.veo[y][x + 1]) + (S.voe[y][x] + S.voe[y + 1][x]) - c1 * S.rg[2 * y + 1][2 * x + 1]) *
+        const T vOO = ((S.veo[fy][fx] + S.veo[fy][fx + 1]) + (S.voe[fy][fx] + S.voe[fy + 1][fx]) - c1 * S.rg[2 * fy + 1][2 * fx + 1]) *
                       T(0.25);
-        const T vOE = S.voe[y][x], vEO = S.veo[y][x];
+        const T vOE = S.voe[fy][fx], vEO = S.veo[fy][fx];
         const int i = 2 * a, j = 2 * b;
         if (FINEST) {
             double *ur0 = u + (size_t)j * up + i;       // row 2b: (2a, 2b), (2a+1, 2b)
@@ -671,11 +664,12 @@ template <int TA, int TB> struct UpRRSmem {
     float vco[TB + 2][TA + 2];
 };
 
+
 template <int TA, int TB>
 __global__ void __launch_bounds__(256) k_up0_rr_2d(A2<const float> blue, A2<const float> ree, A2<const float> roo,
-                                                   A2<float> rga, float *rgb, double *r64, int rp, double *u, int up,
-                                                   int nb, float c2, float c1, double ih2, double *part,
-                                                   const int *par, const int *done, Bt B) {
+                                                   A2<float> rga, float *rgb, double *__restrict__ r64, int rp,
+                                                   double *__restrict__ u, int up, int nb, float c2, float c1,
+                                                   double ih2, double *part, const int *par, const int *done, Bt B) {
     extern __shared__ __align__(16) unsigned char smraw[];
     UpRRSmem<TA, TB> &S = *reinterpret_cast<UpRRSmem<TA, TB> *>(smraw);
     __shared__ double sh[32];
@@ -692,35 +686,25 @@ __global__ void __launch_bounds__(256) k_up0_rr_2d(A2<const float> blue, A2<cons
     part += (size_t)prob * B.nparts;
     const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
     const int n = 2 * nb + 1;
-    const int tid = threadIdx.x + 32 * threadIdx.y;
-#pragma unroll 4
-    for (int q = tid; q < (TA + 7) * (TB + 7); q += 256) {
-        const int x = q % (TA + 7), y = q / (TA + 7);
+    MG_FOR2(TA + 7, TB + 7) {
         const int a = a0 - 3 + x, b = b0 - 3 + y;
         S.b[y][x] = (a >= 0 && a <= nb + 1 && b >= 0 && b <= nb + 1) ? blue(a, b) : 0.f;
     }
-#pragma unroll 4
-    for (int q = tid; q < (TA + 6) * (TB + 6); q += 256) {
-        const int x = q % (TA + 6), y = q / (TA + 6);
+    MG_FOR2(TA + 6, TB + 6) {
         const int a = a0 - 3 + x, b = b0 - 3 + y;
         S.roo[y][x] = (a >= 0 && a <= nb && b >= 0 && b <= nb) ? roo(a, b) : 0.f;
     }
-#pragma unroll 4
-    for (int q = tid; q < (TA + 5) * (TB + 5); q += 256) {
-        const int x = q % (TA + 5), y = q / (TA + 5);
+    MG_FOR2(TA + 5, TB + 5) {
         const int a = a0 - 2 + x, b = b0 - 2 + y;
         S.ree[y][x] = (a >= 1 && a <= nb && b >= 1 && b <= nb) ? ree(a, b) : 0.f;
     }
-#pragma unroll 4
-    for (int q = tid; q < (2 * TA + 8) * (2 * TB + 8); q += 256) {
-        const int x = q % (2 * TA + 8), y = q / (2 * TA + 8);
+    MG_FOR2(2 * TA + 8, 2 * TB + 8) {
         const int gx = 2 * a0 - 4 + x, gy = 2 * b0 - 4 + y;
         S.rg[y][x] = (gx >= 1 && gx <= n && gy >= 1 && gy <= n) ? rg(gx, gy) : 0.f;
     }
     __syncthreads();
-    // red OO (Eq. Eajacr), cells [a0-3, a0+TA+2]: smem x = c - a0 + 3 in voo and b
-    for (int q = tid; q < (TA + 6) * (TB + 6); q += 256) {
-        const int x = q % (TA + 6), y = q / (TA + 6);
+    // red OO (Eq. Eajacr), cells [a0-3, a0+TA+2]
+    MG_FOR2(TA + 6, TB + 6) {
         const int c = a0 - 3 + x, d = b0 - 3 + y;
         float v = 0.f;
         if (c >= 0 && c <= nb && d >= 0 && d <= nb)
@@ -728,9 +712,8 @@ __global__ void __launch_bounds__(256) k_up0_rr_2d(A2<const float> blue, A2<cons
         S.voo[y][x] = v;
     }
     __syncthreads();
-    // red EE (Eq. Eajacb), cells [a0-2, a0+TA+2]: OO(a-1) at voo x = a - a0 + 2 = x
-    for (int q = tid; q < (TA + 5) * (TB + 5); q += 256) {
-        const int x = q % (TA + 5), y = q / (TA + 5);
+    // red EE (Eq. Eajacb), cells [a0-2, a0+TA+2]
+    MG_FOR2(TA + 5, TB + 5) {
         const int a = a0 - 2 + x, b = b0 - 2 + y;
         float v = 0.f;
         if (a >= 1 && a <= nb && b >= 1 && b <= nb)
@@ -738,9 +721,8 @@ __global__ void __launch_bounds__(256) k_up0_rr_2d(A2<const float> blue, A2<cons
         S.vee[y][x] = v;
     }
     __syncthreads();
-    // green-only points, cells [a0-2, a0+TA+1]; EE(a) at vee x, OO(a) at voo x+1, green (2a+1,2b) at rg[2y][2x+1]
-    for (int q = tid; q < (TA + 4) * (TB + 4); q += 256) {
-        const int x = q % (TA + 4), y = q / (TA + 4);
+    // green-only points, cells [a0-2, a0+TA+1]
+    MG_FOR2(TA + 4, TB + 4) {
         const int a = a0 - 2 + x, b = b0 - 2 + y;
         float voe = 0.f, veo = 0.f;
         if (a >= 0 && a <= nb && b >= 1 && b <= nb)
@@ -753,9 +735,8 @@ __global__ void __launch_bounds__(256) k_up0_rr_2d(A2<const float> blue, A2<cons
         S.veo[y][x] = veo;
     }
     __syncthreads();
-    // red points (green C) of cells [a0-1, a0+TA]; F smem index of cell a is a - a0 + 2 = x + 1
-    for (int q = tid; q < (TA + 2) * (TB + 2); q += 256) {
-        const int x = q % (TA + 2), y = q / (TA + 2);
+    // red points (green C) of cells [a0-1, a0+TA]
+    MG_FOR2(TA + 2, TB + 2) {
         const int a = a0 - 1 + x, b = b0 - 1 + y;
         const int fx = x + 1, fy = y + 1;
         float vEE = 0.f, vOO = 0.f;
@@ -768,32 +749,70 @@ __global__ void __launch_bounds__(256) k_up0_rr_2d(A2<const float> blue, A2<cons
         S.vco[y][x] = vOO;
     }
     __syncthreads();
-    // green v at fine (gx, gy) with gx in [2a0-2, 2a0+2TA+1]
-    auto vat = [&](int gx, int gy) -> float {
-        const int a = gx >> 1, b = gy >> 1;
-        const int cx = a - a0 + 1, cy = b - b0 + 1;  // C index; F index = C index + 1
-        if (gx & 1) return (gy & 1) ? S.vco[cy][cx] : S.voe[cy + 1][cx + 1];
-        return (gy & 1) ? S.veo[cy + 1][cx + 1] : S.vce[cy][cx];
-    };
+    // own cells: the four green points of cell (a,b) and their four axis
+    // neighbours (C index (cx, cy) = (a-a0+1, b-b0+1), F index = C index + 1)
     float sq = 0.f;
-    for (int q = tid; q < 4 * TA * TB; q += 256) {
-        // fine points of the own cells, row-major over a 2TA x 2TB block
-        const int lx = q % (2 * TA), ly = q / (2 * TA);
-        const int i = 2 * a0 + lx, j = 2 * b0 + ly;
-        if (i < 1 || i > n || j < 1 || j > n) continue;
-        const float vc = vat(i, j);
+    auto point = [&](int i, int j, float v, float w, float e, float s_, float nn) {
         float hi, lo;
-        lap_sum(vat(i - 1, j), vat(i + 1, j), vat(i, j - 1), vat(i, j + 1), vc, hi, lo);
+        lap_sum(w, e, s_, nn, v, hi, lo);
         const size_t cu = (size_t)j * up + i, cr = (size_t)j * rp + i;
-        u[cu] += widen(vc);
+        u[cu] += widen(v);
         const double rn = fma(-ih2, widen(hi), fma(-ih2, widen(lo), r64[cr]));
         r64[cr] = rn;
         const float rf = (float)rn;
         rnew(i, j) = rf;
         sq = fmaf(rf, rf, sq);
+    };
+    MG_FOR2(TA, TB) {
+        const int a = a0 + x, b = b0 + y;
+        if (a > nb || b > nb) continue;
+        const int cx = x + 1, cy = y + 1, fx = x + 2, fy = y + 2;
+        const int i = 2 * a, j = 2 * b;
+        if (a >= 1 && b >= 1)  // EE at (2a, 2b): OE(a-1,b), OE(a,b), EO(a,b-1), EO(a,b)
+            point(i, j, S.vce[cy][cx], S.voe[fy][fx - 1], S.voe[fy][fx], S.veo[fy - 1][fx], S.veo[fy][fx]);
+        if (b >= 1)            // OE at (2a+1, 2b): EE(a,b), EE(a+1,b), OO(a,b-1), OO(a,b)
+            point(i + 1, j, S.voe[fy][fx], S.vce[cy][cx], S.vce[cy][cx + 1], S.vco[cy - 1][cx], S.vco[cy][cx]);
+        if (a >= 1)            // EO at (2a, 2b+1): OO(a-1,b), OO(a,b), EE(a,b), EE(a,b+1)
+            point(i, j + 1, S.veo[fy][fx], S.vco[cy][cx - 1], S.vco[cy][cx], S.vce[cy][cx], S.vce[cy + 1][cx]);
+        // OO at (2a+1, 2b+1): EO(a,b), EO(a+1,b), OE(a,b), OE(a,b+1)
+        point(i + 1, j + 1, S.vco[cy][cx], S.veo[fy][fx], S.veo[fy][fx + 1], S.voe[fy][fx], S.voe[fy + 1][fx]);
     }
     const double s = block_sum((double)sq, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x + gridDim.x * blockIdx.y] = s;
+}
+
+// sum of f^2 over the interior (the norm of the right-hand side of an order-2
+// solve): FP32 squares per thread, FP64 block sums; grid as k_res0_2d (2D) or
+// k_res0_3d (3D) so the partial count matches
+template <int DIM>
+__global__ void __launch_bounds__(256) k_norm_f(const double *__restrict__ f, int up, int n, double *part,
+                                                const int *done, Bt B) {
+    __shared__ double sh[32];
+    const int prob = bt_prob(B), bz = bt_z(B);
+    if (stop(bt_done(done, prob, B))) return;
+    if (B.ftab) f = B.ftab[prob];
+    part += (size_t)prob * B.nparts;
+    const int i = blockIdx.x * 32 + threadIdx.x + 1;
+    float acc = 0.f;
+    if (DIM == 2) {
+        const int j0 = (blockIdx.y * 8 + threadIdx.y) * RES_ROWS + 1;
+        if (i <= n)
+            for (int q = 0; q < RES_ROWS && j0 + q <= n; q++) {
+                const float v = (float)f[(size_t)(j0 + q) * up + i];
+                acc = fmaf(v, v, acc);
+            }
+    } else {
+        const int j = blockIdx.y * 8 + threadIdx.y + 1, k0 = bz * RES3_PLANES + 1;
+        const size_t pl = (size_t)up * (n + 2);
+        if (i <= n && j <= n)
+            for (int q = 0; q < RES3_PLANES && k0 + q <= n; q++) {
+                const float v = (float)f[(k0 + q) * pl + (size_t)j * up + i];
+                acc = fmaf(v, v, acc);
+            }
+    }
+    const double s = block_sum((double)acc, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz)] = s;
 }
 
 // finest residual, written both in the level precision (FP32) and in FP64 to
@@ -831,6 +850,86 @@ __global__ void __launch_bounds__(256) k_res0_64_2d(const double *__restrict__ f
     double s = block_sum((double)acc, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         part[(size_t)prob * B.nparts + blockIdx.x + gridDim.x * blockIdx.y] = s;
+}
+
+}  // namespace mg
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// 3D finest triple: both halves of the green-red sweep (Eq. Egprolg, then
+// Eq. Egprolr) in one shared-memory tile of GX x GY x GZ green points, fused
+// with u += v (FINEST) or storing v.  F (odd index sum) points are computed on
+// the tile plus a one-point halo from the red values, then the C (even) points
+// of the tile from the new F values.
+// ---------------------------------------------------------------------------
+constexpr int GX3 = 32, GY3 = 8, GZ3 = 4;
+
+template <typename T, bool FINEST>
+__global__ void __launch_bounds__(256) k_up_green_3d(Red3<const T> vr, A3<const T> rg, A3<T> vg, double *u, int up,
+                                                     int n, T cg, const int *done, Bt B) {
+    constexpr int RX = GX3 + 4, RY = GY3 + 4, RZ = GZ3 + 4;  // red region: tile +- 2
+    constexpr int VX = GX3 + 2, VY = GY3 + 2, VZ = GZ3 + 2;  // F / r region: tile +- 1
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *R = reinterpret_cast<T *>(smraw);
+    T *G = R + RX * RY * RZ;
+    T *V = G + VX * VY * VZ;
+    const int prob = bt_prob(B), bz = bt_z(B);
+    if (stop(bt_done(done, prob, B))) return;
+    vr = bt_at(vr, prob, B);
+    rg = bt_at(rg, prob, B);
+    vg = bt_at(vg, prob, B);
+    if (B.utab) u = B.utab[prob];
+    const int x0 = blockIdx.x * GX3 + 1, y0 = blockIdx.y * GY3 + 1, z0 = bz * GZ3 + 1;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    // red values at even-parity points of the tile +- 2 (zero outside the interior)
+#pragma unroll 4
+    for (int q = tid; q < RX * RY * RZ; q += 256) {
+        const int lx = q % RX, ly = (q / RX) % RY, lz = q / (RX * RY);
+        const int x = x0 - 2 + lx, y = y0 - 2 + ly, z = z0 - 2 + lz;
+        T v = T(0);
+        if (((x + y + z) & 1) == 0 && x >= 1 && x <= n && y >= 1 && y <= n && z >= 1 && z <= n) v = red3(vr, x, y, z);
+        R[q] = v;
+    }
+#pragma unroll 4
+    for (int q = tid; q < VX * VY * VZ; q += 256) {
+        const int lx = q % VX, ly = (q / VX) % VY, lz = q / (VX * VY);
+        const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
+        G[q] = (x >= 1 && x <= n && y >= 1 && y <= n && z >= 1 && z <= n) ? rg(x, y, z) : T(0);
+    }
+    __syncthreads();
+    auto Ri = [&](int lx, int ly, int lz) { return R[(lz * RY + ly) * RX + lx]; };  // region +-2 coordinates
+    // F points on the tile +- 1
+    for (int q = tid; q < VX * VY * VZ; q += 256) {
+        const int lx = q % VX, ly = (q / VX) % VY, lz = q / (VX * VY);
+        const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
+        T v = T(0);
+        if (((x + y + z) & 1) && x >= 1 && x <= n && y >= 1 && y <= n && z >= 1 && z <= n) {
+            const int rx = lx + 1, ry = ly + 1, rz = lz + 1;
+            const T s = (Ri(rx - 1, ry, rz) + Ri(rx + 1, ry, rz)) + (Ri(rx, ry - 1, rz) + Ri(rx, ry + 1, rz)) +
+                        (Ri(rx, ry, rz - 1) + Ri(rx, ry, rz + 1));
+            v = (s - cg * G[q]) * T(1.0 / 6.0);
+        }
+        V[q] = v;
+    }
+    __syncthreads();
+    auto Vi = [&](int lx, int ly, int lz) { return V[(lz * VY + ly) * VX + lx]; };
+    for (int q = tid; q < GX3 * GY3 * GZ3; q += 256) {
+        const int tx = q % GX3, ty = (q / GX3) % GY3, tz = q / (GX3 * GY3);
+        const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+        if (x > n || y > n || z > n) continue;
+        const int lx = tx + 1, ly = ty + 1, lz = tz + 1;
+        T v;
+        if ((x + y + z) & 1) {
+            v = Vi(lx, ly, lz);
+        } else {
+            const T s = (Vi(lx - 1, ly, lz) + Vi(lx + 1, ly, lz)) + (Vi(lx, ly - 1, lz) + Vi(lx, ly + 1, lz)) +
+                        (Vi(lx, ly, lz - 1) + Vi(lx, ly, lz + 1));
+            v = (s - cg * G[(lz * VY + ly) * VX + lx]) * T(1.0 / 6.0);
+        }
+        if (FINEST) u[((size_t)z * (n + 2) + y) * up + x] += widen(v);
+        else vg(x, y, z) = v;
+    }
 }
 
 }  // namespace mg

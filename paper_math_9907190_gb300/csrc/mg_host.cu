@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "../../include/diagmg.h"
@@ -94,6 +95,10 @@ struct mg_ctx {
     void *r64 = nullptr;
     void *r32b = nullptr;
     int r64_pitch = 0;
+    // tuned choices (mg_tune): tile class per pair for the down / up kernels
+    // (-1: the size rule), side cut-off of the coarse thread block (0: default)
+    int tile_dn[32], tile_up[32];
+    int cut_side = 0;
     // 3D diagonal path: triples with side <= 15 in one thread block
     bool fast3d = false;
     CoarsePlan3d plan3d{};
@@ -115,6 +120,8 @@ struct mg_ctx {
     double *g_u = nullptr;
     double g_rtol = -1.0;
     int g_max = -1;
+    int g_order = 0;
+    double g_omega[4] = {0, 0, 0, 0};
     long long g_prefix_kernels = 0, g_body_kernels = 0;
 };
 
@@ -363,6 +370,15 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
                 LAUNCH_B(TAG_FINEST_UP, (k_r2g_c_upd_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
             else
                 LAUNCH_B(TAG_LEVELS, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+        } else if (c->d.hierarchy == MG_DIAG) {  // both green-red half-sweeps in one tile kernel
+            const dim3 g3((n + GX3 - 1) / GX3, (n + GY3 - 1) / GY3, (n + GZ3 - 1) / GZ3);
+            const size_t sm = sizeof(T) * ((GX3 + 4) * (GY3 + 4) * (GZ3 + 4) + 2 * (GX3 + 2) * (GY3 + 2) * (GZ3 + 2));
+            if (u)
+                LAUNCH_SMEM_B(TAG_FINEST_UP, (k_up_green_3d<T, true>), g3, B2, sm, red3v<const T>(b.v, b),
+                              a3<const T>(a.r[0], a), a3<T>(a.v[0], a), u, c->d.pitch, n, cc, done);
+            else
+                LAUNCH_SMEM_B(TAG_LEVELS, (k_up_green_3d<T, false>), g3, B2, sm, red3v<const T>(b.v, b),
+                              a3<const T>(a.r[0], a), a3<T>(a.v[0], a), u, c->d.pitch, n, cc, done);
         } else {
             if (c->d.hierarchy == MG_USUAL)
                 LAUNCH_B(TAG_LEVELS, (k_usual_odd_3d<T>), grid3(n, n, n), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
@@ -403,9 +419,10 @@ template <typename T> void launch_coarse(mg_ctx *c, const int *done, cudaStream_
 void plan_fast2d(mg_ctx *c) {
     c->fast2d = c->d.dim == 2 && c->d.hierarchy == MG_DIAG;
     if (!c->fast2d) return;
-    // pairs whose green grid has side <= 63 run in one thread block
+    // pairs whose green grid has side <= 63 (or the tuned cut-off) run in one thread block
+    const int cut = c->cut_side > 0 ? c->cut_side : 63;
     int kc = 0;
-    while (kc < c->K && c->lv[2 * kc].side > 63) kc++;
+    while (kc < c->K && c->lv[2 * kc].side > cut) kc++;
     c->kc = kc;
     CoarsePlan2d &P = c->plan2d;
     P = CoarsePlan2d{};
@@ -436,8 +453,9 @@ void plan_fast2d(mg_ctx *c) {
 void plan_fast3d(mg_ctx *c) {
     c->fast3d = c->d.dim == 3 && c->d.hierarchy == MG_DIAG;
     if (!c->fast3d) return;
+    const int cut = c->cut_side > 0 ? c->cut_side : 15;
     int kc = 0;
-    while (kc < c->K && c->lv[3 * kc].side > 15) kc++;
+    while (kc < c->K && c->lv[3 * kc].side > cut) kc++;
     c->kc = kc;
     CoarsePlan3d &P = c->plan3d;
     P = CoarsePlan3d{};
@@ -529,9 +547,27 @@ void launch_up_pair(mg_ctx *c, int k, double *u, const int *done, cudaStream_t s
                       c->d.pitch, nb, c2, c1, done);
 }
 
+int tile_dn(const mg_ctx *c, int k) { return c->tile_dn[k] >= 0 ? c->tile_dn[k] : tile_class(c->lv[2 * k + 1].nb); }
+int tile_up(const mg_ctx *c, int k) { return c->tile_up[k] >= 0 ? c->tile_up[k] : tile_class(c->lv[2 * k + 1].nb); }
+
+template <typename T> void down_pair(mg_ctx *c, int k, int cls, const int *done, cudaStream_t s, bool alt) {
+    switch (cls) {
+    case 0: launch_down_pair<T, 32, 16>(c, k, done, s, alt); break;
+    case 1: launch_down_pair<T, 16, 8>(c, k, done, s, alt); break;
+    default: launch_down_pair<T, 8, 8>(c, k, done, s, alt); break;
+    }
+}
+template <typename T> void up_pair(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s) {
+    switch (cls) {
+    case 0: launch_up_pair<T, 32, 16>(c, k, u, done, s); break;
+    case 1: launch_up_pair<T, 16, 8>(c, k, u, done, s); break;
+    default: launch_up_pair<T, 8, 8>(c, k, u, done, s); break;
+    }
+}
+
 template <typename T> void vcycle_fast2d(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     for (int k = 0; k < c->kc; k++) {
-        switch (tile_class(c->lv[2 * k + 1].nb)) {
+        switch (tile_dn(c, k)) {
         case 0: launch_down_pair<T, 32, 16>(c, k, done, s); break;
         case 1: launch_down_pair<T, 16, 8>(c, k, done, s); break;
         default: launch_down_pair<T, 8, 8>(c, k, done, s); break;
@@ -543,7 +579,7 @@ template <typename T> void vcycle_fast2d(mg_ctx *c, double *u, const int *done, 
                       a2<const T>(g.r[0], g), a2<T>(g.v[0], g), c->G, done);
     }
     for (int k = c->kc - 1; k >= 0; k--) {
-        switch (tile_class(c->lv[2 * k + 1].nb)) {
+        switch (tile_up(c, k)) {
         case 0: launch_up_pair<T, 32, 16>(c, k, u, done, s); break;
         case 1: launch_up_pair<T, 16, 8>(c, k, u, done, s); break;
         default: launch_up_pair<T, 8, 8>(c, k, u, done, s); break;
@@ -574,7 +610,7 @@ template <int TA, int TB> int launch_up0_rr(mg_ctx *c, double *u, const int *don
 // number of norm partial sums written per problem
 int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     for (int k = 0; k < c->kc; k++) {
-        switch (tile_class(c->lv[2 * k + 1].nb)) {
+        switch (tile_dn(c, k)) {
         case 0: launch_down_pair<float, 32, 16>(c, k, done, s, true); break;
         case 1: launch_down_pair<float, 16, 8>(c, k, done, s, true); break;
         default: launch_down_pair<float, 8, 8>(c, k, done, s, true); break;
@@ -586,13 +622,13 @@ int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
                       a2<const float>(g.r[0], g), a2<float>(g.v[0], g), c->G, done);
     }
     for (int k = c->kc - 1; k >= 1; k--) {
-        switch (tile_class(c->lv[2 * k + 1].nb)) {
+        switch (tile_up(c, k)) {
         case 0: launch_up_pair<float, 32, 16>(c, k, u, done, s); break;
         case 1: launch_up_pair<float, 16, 8>(c, k, u, done, s); break;
         default: launch_up_pair<float, 8, 8>(c, k, u, done, s); break;
         }
     }
-    switch (tile_class(c->lv[1].nb)) {
+    switch (tile_up(c, 0)) {
     case 0: return launch_up0_rr<32, 16>(c, u, done, s);
     case 1: return launch_up0_rr<16, 8>(c, u, done, s);
     default: return launch_up0_rr<8, 8>(c, u, done, s);
@@ -739,6 +775,7 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     mg_ctx *c = new (std::nothrow) mg_ctx();
     if (!c) return MG_ENOMEM;
     c->d = *d;
+    for (int q = 0; q < 32; q++) c->tile_dn[q] = c->tile_up[q] = -1;
     c->m = log2_side(d->n);
     c->h = 1.0 / (d->n + 1);
     c->esz = d->precision == MG_FP64 ? 8 : 4;
@@ -770,9 +807,12 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     plan_fast2d(c);
     plan_fast3d(c);
     if (c->fast3d) {
-        const cudaError_t e = d->precision == MG_FP64
+        const int gsm = (int)(sizeof(double) * ((GX3 + 4) * (GY3 + 4) * (GZ3 + 4) + 2 * (GX3 + 2) * (GY3 + 2) * (GZ3 + 2)));
+        cudaError_t e = d->precision == MG_FP64
             ? cudaFuncSetAttribute(k_coarse_cta_3d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes)
             : cudaFuncSetAttribute(k_coarse_cta_3d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_up_green_3d<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_up_green_3d<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
         if (e != cudaSuccess) {
             mg_destroy(c);
             return cuda_fail(e, "mg_create shared-memory attributes (3D)");
@@ -924,6 +964,27 @@ mg_status mg_vcycle(mg_ctx *c, const double *f, double *u, void *stream) {
     return vcycle_t<float>(c, f, u, nullptr, true, S(stream));
 }
 
+// partial sums of ||f~||^2 (f~ = f for order 2, the Mehrstellen / 19-point
+// right-hand side for order 4); returns the partial count per problem
+static int launch_rhs_norm(mg_ctx *c, const double *f, const double *u, cudaStream_t s) {
+    const bool fp64 = c->d.precision == MG_FP64;
+    if (c->d.order == 4) {
+        if (fp64) launch_residual<double>(c, f, u, nullptr, true, nullptr, s);
+        else launch_residual<float>(c, f, u, nullptr, true, nullptr, s);
+        return c->max_blocks;
+    }
+    const int n = c->d.n;
+    dim3 g;
+    if (c->d.dim == 2) {
+        g = dim3((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
+        LAUNCH_B(TAG_CONTROL, (k_norm_f<2>), g, B2, f, c->d.pitch, n, c->part, (const int *)nullptr);
+    } else {
+        g = dim3((n + 31) / 32, (n + 7) / 8, (n + RES3_PLANES - 1) / RES3_PLANES);
+        LAUNCH_B(TAG_CONTROL, (k_norm_f<3>), g, B2, f, c->d.pitch, n, c->part, (const int *)nullptr);
+    }
+    return (int)(g.x * g.y * g.z);
+}
+
 // residual of the current iterate into level 0 (+ partial sums); returns their count
 static int solve_residual(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
     if (c->rr) return launch_res_rr(c, f, u, done, s);
@@ -963,12 +1024,11 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     } else {
         LAUNCH(TAG_CONTROL, (k_ctrl_init_b), (c->nprob + 255) / 256, 256, c->ctl, c->nprob, rtol, max_cycles);
     }
-    if (fp64) launch_residual<double>(c, f, u, nullptr, true, nullptr, s);
-    else launch_residual<float>(c, f, u, nullptr, true, nullptr, s);
+    const int nfp = launch_rhs_norm(c, f, u, s);
     if (c->nprob == 1) {
-        LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, c->max_blocks, &c->ctl->f2);
+        LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, nfp, &c->ctl->f2);
     } else {
-        LAUNCH(TAG_CONTROL, (k_sum_to_b), c->nprob, 1024, c->part, c->max_blocks, c->ctl);
+        LAUNCH(TAG_CONTROL, (k_sum_to_b), c->nprob, 1024, c->part, nfp, c->ctl);
     }
     if (c->d.order == 4) launch_rhs4(c, f, s);
     int np = solve_residual(c, f, u, nullptr, s);
@@ -1003,6 +1063,12 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     launch_ctrl(c, np2, 0, loop, 1, s2);
     c->g_body_kernels = c->launches - l1;
     CK(cudaStreamEndCapture(s2, &body));
+    if (c->rr) {  // the carried residual ignores the rounding of u: report a direct one
+        const long long l2 = c->launches;
+        const int np3 = launch_res_rr(c, f, u, nullptr, s);
+        LAUNCH(TAG_CONTROL, (k_final_true), c->nprob, 1024, c->part, np3, c->ctl);
+        c->g_prefix_kernels += c->launches - l2;
+    }
     c->capturing = false;
     c->launches = l0;  // counted when the graph runs
     return MG_OK;
@@ -1021,6 +1087,8 @@ static mg_status build_solve_graph(mg_ctx *c, const double *f, double *u, double
     c->graph = g;
     CK(cudaGraphInstantiate(&c->gexec, g, 0));
     c->g_f = f; c->g_u = u; c->g_rtol = rtol; c->g_max = max_cycles;
+    c->g_order = c->d.order;
+    for (int q = 0; q < 4; q++) c->g_omega[q] = c->d.omega[q];
     return MG_OK;
 }
 
@@ -1032,9 +1100,8 @@ static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double r
     const int *done = &c->ctl->done;
     cudaGraphConditionalHandle none = 0;
     LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
-    if (fp64) launch_residual<double>(c, f, u, nullptr, true, nullptr, s);
-    else launch_residual<float>(c, f, u, nullptr, true, nullptr, s);
-    LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, c->max_blocks, &c->ctl->f2);
+    const int nfp = launch_rhs_norm(c, f, u, s);
+    LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, nfp, &c->ctl->f2);
     if (c->d.order == 4) launch_rhs4(c, f, s);
     int np = solve_residual(c, f, u, nullptr, s);
     launch_ctrl(c, np, 1, none, 0, s);
@@ -1056,6 +1123,10 @@ static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double r
         probe_collect(c);
         if (host.done) break;
     }
+    if (c->rr) {
+        const int np3 = launch_res_rr(c, f, u, nullptr, s);
+        LAUNCH(TAG_CONTROL, (k_final_true), c->nprob, 1024, c->part, np3, c->ctl);
+    }
     CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (cycles_out) *cycles_out = host.cycles;
@@ -1073,8 +1144,11 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
                    double *relres_out, double *history, void *stream) {
     if (!c || !f || !u || !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap) return MG_EINVAL;
     cudaStream_t s = S(stream);
-    if (!c->use_graph) return solve_host_loop(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, s);
-    if (!c->gexec || c->g_f != f || c->g_u != u || c->g_rtol != rtol || c->g_max != max_cycles) {
+    // a probe needs one event pair per launch, which a replayed graph cannot give
+    if (!c->use_graph || c->probe_tag >= 0)
+        return solve_host_loop(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, s);
+    if (!c->gexec || c->g_f != f || c->g_u != u || c->g_rtol != rtol || c->g_max != max_cycles ||
+        c->g_order != c->d.order || std::memcmp(c->g_omega, c->d.omega, sizeof c->g_omega) != 0) {
         mg_status st = build_solve_graph(c, f, u, rtol, max_cycles);
         if (st != MG_OK) return st;
     }
@@ -1091,6 +1165,87 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
     }
     if (host.status == -5) return MG_EDIVERGED;
     if (host.status == -4 || !host.done) return MG_ENOCONV;
+    return MG_OK;
+}
+
+// Section 2.4 / 3.4: a fourth-order solution is reached fastest by first
+// converging the second-order problem (its V-cycles contract ~10x faster) and
+// then running a few cycles on the fourth-order residual.
+mg_status mg_solve_two_stage(mg_ctx *c, const double *f, double *u, const double *omega2, double rtol2, double rtol,
+                             int max_cycles, int *cycles2_out, int *cycles4_out, double *relres_out, void *stream) {
+    if (!c || !f || !u || c->d.order != 4 || !(rtol2 >= 0.0)) return MG_EINVAL;
+    double om4[4];
+    std::memcpy(om4, c->d.omega, sizeof om4);
+    // stage 1: the same levels and schedule with the second-order residual
+    c->d.order = 2;
+    if (omega2) std::memcpy(c->d.omega, omega2, sizeof om4);
+    plan_fast2d(c);
+    plan_fast3d(c);
+    int cyc2 = 0;
+    double rel2 = 0.0;
+    mg_status st = mg_solve(c, f, u, rtol2, max_cycles, &cyc2, &rel2, nullptr, stream);
+    c->d.order = 4;
+    std::memcpy(c->d.omega, om4, sizeof om4);
+    plan_fast2d(c);
+    plan_fast3d(c);
+    if (st != MG_OK && st != MG_ENOCONV) return st;
+    int cyc4 = 0;
+    st = mg_solve(c, f, u, rtol, max_cycles, &cyc4, relres_out, nullptr, stream);
+    if (cycles2_out) *cycles2_out = cyc2;
+    if (cycles4_out) *cycles4_out = cyc4;
+    return st;
+}
+
+mg_status mg_set_omega(mg_ctx *c, const double *omega) {
+    if (!c || !omega) return MG_EINVAL;
+    for (int q = 0; q < 4; q++)
+        if (!std::isfinite(omega[q])) return MG_EINVAL;
+    std::memcpy(c->d.omega, omega, sizeof c->d.omega);
+    plan_fast2d(c);
+    plan_fast3d(c);
+    return MG_OK;
+}
+
+// Convergence factor of the V-cycle by power iteration on its error
+// propagation u <- u + B(0 - L u) (f = 0): the geometric mean of the norm
+// ratios of the last (cycles - skip) cycles, u renormalised every cycle.
+mg_status mg_rho(mg_ctx *c, const double *zero_f, double *u, int cycles, int skip, double *rho_out, void *stream) {
+    if (!c || !zero_f || !u || !rho_out || cycles < 2 || skip < 0 || skip >= cycles || cycles > c->hist_cap ||
+        c->nprob != 1)
+        return MG_EINVAL;
+    cudaStream_t s = S(stream);
+    const bool fp64 = c->d.precision == MG_FP64;
+    const int n = c->d.n;
+    const dim3 g = c->d.dim == 2 ? grid2(n, n) : grid3(n, n, n);
+    auto norm_u = [&]() {
+        dim3 gn;
+        if (c->d.dim == 2) {
+            gn = dim3((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
+            LAUNCH_B(TAG_CONTROL, (k_norm_f<2>), gn, B2, u, c->d.pitch, n, c->part, (const int *)nullptr);
+        } else {
+            gn = dim3((n + 31) / 32, (n + 7) / 8, (n + RES3_PLANES - 1) / RES3_PLANES);
+            LAUNCH_B(TAG_CONTROL, (k_norm_f<3>), gn, B2, u, c->d.pitch, n, c->part, (const int *)nullptr);
+        }
+        return (int)(gn.x * gn.y * gn.z);
+    };
+    if (c->d.order == 4) launch_rhs4(c, zero_f, s);
+    int np = norm_u();
+    LAUNCH(TAG_CONTROL, (k_rho_record), 1, 1024, c->part, np, c->scal, c->hist, 0);
+    LAUNCH(TAG_CONTROL, (k_scale_grid), g, B2, u, c->d.pitch, n, c->d.dim, c->scal);
+    for (int q = 0; q < cycles; q++) {
+        mg_status st = fp64 ? vcycle_t<double>(c, zero_f, u, nullptr, true, s) : vcycle_t<float>(c, zero_f, u, nullptr, true, s);
+        if (st != MG_OK) return st;
+        np = norm_u();
+        LAUNCH(TAG_CONTROL, (k_rho_record), 1, 1024, c->part, np, c->scal, c->hist, q);
+        LAUNCH(TAG_CONTROL, (k_scale_grid), g, B2, u, c->d.pitch, n, c->d.dim, c->scal);
+    }
+    CKL("mg_rho");
+    std::vector<double> ratio(cycles);
+    CK(cudaMemcpyAsync(ratio.data(), c->hist, sizeof(double) * cycles, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double lg = 0.0;
+    for (int q = skip; q < cycles; q++) lg += std::log(std::max(ratio[q], 1e-300));
+    *rho_out = std::exp(lg / (cycles - skip));
     return MG_OK;
 }
 
@@ -1248,6 +1403,222 @@ mg_status mg_batch_launch_count(const mg_batch *b, long long *launches) {
     long long t = 0;
     for (auto c : b->grp) t += c->launches;
     *launches = t;
+    return MG_OK;
+}
+
+}  // extern "C"
+
+// ---- autotuning -------------------------------------------------------------
+
+namespace {
+
+std::string tune_key(const mg_ctx *c) {
+    cudaDeviceProp pr{};
+    cudaGetDeviceProperties(&pr, c->dev);
+    char buf[320];
+    std::snprintf(buf, sizeof buf, "\"device\": \"%s\", \"dim\": %d, \"n\": %d, \"hier\": %d, \"prec\": %d, \"nprob\": %d",
+                  pr.name, c->d.dim, c->d.n, c->d.hierarchy, c->d.precision, c->nprob);
+    return buf;
+}
+
+int ntiles(const mg_ctx *c) { return c->fast2d ? c->kc : 0; }
+
+// one JSON object per line: {<key>, "cut": C, "down": [..], "up": [..]}
+bool cache_lookup(const char *path, const std::string &key, mg_ctx *c) {
+    FILE *fp = std::fopen(path, "r");
+    if (!fp) return false;
+    char line[2048];
+    bool found = false;
+    while (std::fgets(line, sizeof line, fp)) {
+        if (!std::strstr(line, key.c_str())) continue;
+        const char *q = std::strstr(line, "\"cut\": ");
+        if (!q) continue;
+        int cut = std::atoi(q + 7);
+        int dn[32], upv[32], ndn = 0, nup = 0;
+        auto read_list = [&](const char *name, int *out, int &cnt) {
+            const char *r = std::strstr(line, name);
+            if (!r) return;
+            r = std::strchr(r, '[');
+            if (!r) return;
+            r++;
+            while (*r && *r != ']' && cnt < 32) {
+                char *end = nullptr;
+                long v = std::strtol(r, &end, 10);
+                if (end == r) break;
+                out[cnt++] = (int)v;
+                r = end;
+                while (*r == ',' || *r == ' ') r++;
+            }
+        };
+        read_list("\"down\"", dn, ndn);
+        read_list("\"up\"", upv, nup);
+        c->cut_side = cut;
+        for (int q2 = 0; q2 < 32; q2++) c->tile_dn[q2] = c->tile_up[q2] = -1;
+        for (int q2 = 0; q2 < ndn; q2++) c->tile_dn[q2] = dn[q2];
+        for (int q2 = 0; q2 < nup; q2++) c->tile_up[q2] = upv[q2];
+        found = true;
+    }
+    std::fclose(fp);
+    return found;
+}
+
+void cache_append(const char *path, const std::string &key, const mg_ctx *c) {
+    FILE *fp = std::fopen(path, "a");
+    if (!fp) return;
+    std::fprintf(fp, "{%s, \"cut\": %d, \"down\": [", key.c_str(), c->cut_side);
+    for (int k = 0; k < ntiles(c); k++) std::fprintf(fp, "%s%d", k ? ", " : "", c->tile_dn[k]);
+    std::fprintf(fp, "], \"up\": [");
+    for (int k = 0; k < ntiles(c); k++) std::fprintf(fp, "%s%d", k ? ", " : "", c->tile_up[k]);
+    std::fprintf(fp, "]}\n");
+    std::fclose(fp);
+}
+
+void replan(mg_ctx *c) {
+    plan_fast2d(c);
+    plan_fast3d(c);
+    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+}
+
+// Measure and apply: the coarse-block cut-off by whole V-cycles, then the tile
+// class of every pair kernel by timing it alone on the context's buffers.
+mg_status tune_measure(mg_ctx *c, const double *f, double *u, cudaStream_t s) {
+    const bool fp64 = c->d.precision == MG_FP64;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto timeit = [&](auto fn, int reps) {
+        fn();
+        cudaEventRecord(e0, s);
+        for (int q = 0; q < reps; q++) fn();
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / reps;
+    };
+    auto vcyc = [&]() {
+        if (fp64) vcycle_t<double>(c, f, u, nullptr, true, s);
+        else vcycle_t<float>(c, f, u, nullptr, true, s);
+    };
+    vcyc();  // realistic contents in every level buffer
+    std::vector<int> cuts = c->fast2d ? std::vector<int>{15, 31, 63} : std::vector<int>{7, 15};
+    int best_cut = 0;
+    float best = 1e30f;
+    for (int cut : cuts) {
+        c->cut_side = cut;
+        replan(c);
+        const float ms = timeit(vcyc, 5);
+        if (ms < best) { best = ms; best_cut = cut; }
+    }
+    c->cut_side = best_cut;
+    replan(c);
+    if (c->fast2d) {
+        for (int k = 0; k < c->kc && k < 32; k++) {
+            float bd = 1e30f, bu = 1e30f;
+            for (int cls = 0; cls < 3; cls++) {
+                const float md = fp64 ? timeit([&] { down_pair<double>(c, k, cls, nullptr, s, false); }, 5)
+                                      : timeit([&] { down_pair<float>(c, k, cls, nullptr, s, false); }, 5);
+                if (md < bd) { bd = md; c->tile_dn[k] = cls; }
+                float mu;
+                if (k == 0 && c->rr) {
+                    const int keep = c->tile_up[0];
+                    c->tile_up[0] = cls;
+                    mu = timeit([&] {
+                        switch (cls) {
+                        case 0: launch_up0_rr<32, 16>(c, u, nullptr, s); break;
+                        case 1: launch_up0_rr<16, 8>(c, u, nullptr, s); break;
+                        default: launch_up0_rr<8, 8>(c, u, nullptr, s); break;
+                        }
+                    }, 5);
+                    c->tile_up[0] = keep;
+                } else {
+                    mu = fp64 ? timeit([&] { up_pair<double>(c, k, cls, k == 0 ? u : nullptr, nullptr, s); }, 5)
+                              : timeit([&] { up_pair<float>(c, k, cls, k == 0 ? u : nullptr, nullptr, s); }, 5);
+                }
+                if (mu < bu) { bu = mu; c->tile_up[k] = cls; }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CKL("mg_tune");
+    return MG_OK;
+}
+
+mg_status zero_u(mg_ctx *c, double *u, cudaStream_t s) {
+    const size_t rows = (size_t)(c->d.n + 2) * (c->d.dim == 3 ? (size_t)(c->d.n + 2) : 1);
+    CK(cudaMemset2DAsync(u, sizeof(double) * c->d.pitch, 0, sizeof(double) * (c->d.n + 2), rows, s));
+    return MG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mg_status mg_tune(mg_ctx *c, const double *f, double *u, const char *cache_path, int *measured_out, void *stream) {
+    if (!c || !f || !u) return MG_EINVAL;
+    if (measured_out) *measured_out = 0;
+    if (!c->fast2d && !c->fast3d) return MG_OK;  // nothing tunable on this path
+    const char *path = cache_path ? cache_path : std::getenv("DIAGMG_TUNE_CACHE");
+    const std::string key = tune_key(c);
+    if (path && cache_lookup(path, key, c)) {
+        replan(c);
+        return MG_OK;
+    }
+    cudaStream_t s = S(stream);
+    mg_status st = tune_measure(c, f, u, s);
+    if (st != MG_OK) return st;
+    st = zero_u(c, u, s);
+    if (st != MG_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    if (path) cache_append(path, key, c);
+    if (measured_out) *measured_out = 1;
+    return MG_OK;
+}
+
+mg_status mg_tune_info(const mg_ctx *c, int *cut_side, int *npairs, int *tiles_down, int *tiles_up) {
+    if (!c) return MG_EINVAL;
+    if (cut_side) *cut_side = c->cut_side;
+    if (npairs) *npairs = ntiles(c);
+    for (int k = 0; k < ntiles(c); k++) {
+        if (tiles_down) tiles_down[k] = tile_dn(c, k);
+        if (tiles_up) tiles_up[k] = tile_up(c, k);
+    }
+    return MG_OK;
+}
+
+mg_status mg_batch_tune(mg_batch *b, const double *const *f, double *const *u, const char *cache_path,
+                        void *stream) {
+    if (!b || !f || !u) return MG_EINVAL;
+    cudaStream_t s = S(stream);
+    for (size_t g = 0; g < b->grp.size(); g++) {
+        mg_ctx *c = b->grp[g];
+        std::vector<const double *> ft;
+        std::vector<double *> ut;
+        for (int p : b->members[g]) { ft.push_back(f[p]); ut.push_back(u[p]); }
+        if (c->nprob > 1) {
+            CK(cudaMemcpy(c->ftab, ft.data(), sizeof(double *) * ft.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(c->utab, ut.data(), sizeof(double *) * ut.size(), cudaMemcpyHostToDevice));
+        }
+        if (!c->fast2d && !c->fast3d) continue;
+        const char *path = cache_path ? cache_path : std::getenv("DIAGMG_TUNE_CACHE");
+        const std::string key = tune_key(c);
+        if (path && cache_lookup(path, key, c)) {
+            replan(c);
+            continue;
+        }
+        mg_status st = tune_measure(c, ft[0], ut[0], s);
+        if (st != MG_OK) return st;
+        for (double *up : ut) {
+            st = zero_u(c, up, s);
+            if (st != MG_OK) return st;
+        }
+        CK(cudaStreamSynchronize(s));
+        if (path) cache_append(path, key, c);
+    }
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     return MG_OK;
 }
 

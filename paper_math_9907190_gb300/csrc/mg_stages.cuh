@@ -693,6 +693,21 @@ __global__ void k_ctrl_b(const double *part, int nblk, Ctrl *ctl, double *hist, 
     }
 }
 
+// after a solve that carried its residual from cycle to cycle: replace the
+// reported relative residual by the one of a direct FP64 residual of the final
+// iterate (one block per problem); above rtol the solve counts as not converged
+__global__ void k_final_true(const double *part, int nblk, Ctrl *ctl) {
+    __shared__ double sh[32];
+    const int p = blockIdx.x;
+    Ctrl *c = ctl + p;
+    const double s = sum_parts(part + (size_t)p * nblk, nblk, sh);
+    if (threadIdx.x != 0) return;
+    const double rel = c->f2 > 0.0 ? sqrt(s / c->f2) : 0.0;
+    c->r2 = s;
+    c->relres = rel;
+    if (c->status == 0 && !(rel <= c->rtol)) c->status = -4;
+}
+
 // loop condition of a batch: continue while any problem is not done
 __global__ void k_any_active(const Ctrl *ctl, int nprob, cudaGraphConditionalHandle loop, int use_loop, int *active) {
     __shared__ int any;
@@ -705,6 +720,23 @@ __global__ void k_any_active(const Ctrl *ctl, int nprob, cudaGraphConditionalHan
         if (active) *active = any;
         if (use_loop) cudaGraphSetConditional(loop, any ? 1u : 0u);
     }
+}
+
+// power iteration step: ratio[c] = ||u|| / ||u before the cycle|| (the latter
+// is 1 after normalisation), then u <- u / ||u|| on the interior
+__global__ void k_rho_record(const double *part, int nblk, double *scal, double *ratio, int c) {
+    __shared__ double sh[32];
+    const double s = sum_parts(part, nblk, sh);
+    if (threadIdx.x == 0) {
+        const double nrm = sqrt(s);
+        ratio[c] = nrm;
+        scal[0] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    }
+}
+__global__ void k_scale_grid(double *u, int up, int n, int dim, const double *scal) {
+    MG_IDX2 const int i = tx + 1, j = ty + 1, k = dim == 3 ? (int)blockIdx.z + 1 : 0;
+    if (i > n || j > n) return;
+    u[((size_t)k * (n + 2) + j) * up + i] *= scal[0];
 }
 
 __global__ void k_sum_to(const double *part, int nblk, double *out) {
