@@ -933,3 +933,186 @@ __global__ void __launch_bounds__(256) k_up_green_3d(Red3<const T> vr, A3<const 
 }
 
 }  // namespace mg
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// 3D finest triple, green-red sweep (Eq. Egprolg then Eq. Egprolr) in one tile
+// of 32 x 8 x 4 green points.  The red level is staged as its four cosets
+// (coalesced loads of dense arrays), the F (odd) points are computed on the
+// tile +- 2, the C (even) points on the tile +- 1.  RR: the mixed solve's
+// fused update -- u += v and the carried residual r -= L v, with L v from
+// exact FP32 differences summed as a float-float pair (see lap_sum) --
+// otherwise FINEST: u += v, or v stored.
+// ---------------------------------------------------------------------------
+constexpr int TX3 = 32, TY3 = 8, TZ3 = 4;
+constexpr int CX3 = TX3 / 2 + 3, CY3 = TY3 / 2 + 3, CZ3 = TZ3 / 2 + 3;  // coset cells of the tile +- 3
+constexpr int WX3 = TX3 + 4, WY3 = TY3 + 4, WZ3 = TZ3 + 4;              // fine region of the tile +- 2
+
+template <typename T> struct Green3Smem {
+    T red[4][CZ3][CY3][CX3];  // EEE, OOE, OEO, EOO
+    T v[WZ3][WY3][WX3];       // F at odd points (tile +- 2), C at even points (tile +- 1)
+    T r[WZ3][WY3][WX3];       // green residual
+};
+
+// hi + lo ~= sum over six neighbours of (n_q - c)
+__device__ __forceinline__ void lap_sum6(const float *nb, float c, float &hi, float &lo) {
+    float d[6], e[6];
+#pragma unroll
+    for (int q = 0; q < 6; q++) two_sum(nb[q], -c, d[q], e[q]);
+    float t = d[0], ee = 0.f, ex;
+#pragma unroll
+    for (int q = 1; q < 6; q++) { two_sum(t, d[q], t, ex); ee += ex; }
+    hi = t;
+    lo = ee + (((e[0] + e[1]) + (e[2] + e[3])) + (e[4] + e[5]));
+}
+
+template <typename T, bool RR, bool FINEST>
+__global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> rga, const T *rgb, A3<T> vg,
+                                                  double *__restrict__ r64, int rp, double *__restrict__ u, int up,
+                                                  int n, T cg, double ih2, double *part, const int *par,
+                                                  const int *done, Bt B) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Green3Smem<T> &S = *reinterpret_cast<Green3Smem<T> *>(smraw);
+    __shared__ double sh[32];
+    const int prob = bt_prob(B), bz = bt_z(B);
+    if (stop(bt_done(done, prob, B))) return;
+    A3<const T> rg = rga;
+    A3<T> rnew{const_cast<T *>(rga.p), rga.pitch, rga.rows};
+    if (RR && par[(size_t)prob * B.ctl_stride]) rg.p = rgb;
+    else if (RR) rnew.p = const_cast<T *>(rgb);
+    vr = bt_at(vr, prob, B);
+    rg = bt_at(rg, prob, B);
+    rnew = bt_at(rnew, prob, B);
+    vg = bt_at(vg, prob, B);
+    if (RR) r64 = bt_ptr(r64, prob, B);
+    if (B.utab) u = B.utab[prob];
+    if (RR) part += (size_t)prob * B.nparts;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    const int x0 = blockIdx.x * TX3 + 1, y0 = blockIdx.y * TY3 + 1, z0 = bz * TZ3 + 1;
+    const int ca = (x0 - 3) >> 1, cb = (y0 - 3) >> 1, cc = (z0 - 3) >> 1;  // first coset cell
+    // the four red cosets over the tile +- 3 (a coset point outside the interior reads 0)
+    const A3<const T> *cos[4] = {&vr.eee, &vr.ooe, &vr.oeo, &vr.eoo};
+    const int px[4] = {0, 1, 1, 0}, py[4] = {0, 1, 0, 1}, pz[4] = {0, 0, 1, 1};
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        for (int q = tid; q < CX3 * CY3 * CZ3; q += 256) {
+            const int lx = q % CX3, ly = (q / CX3) % CY3, lz = q / (CX3 * CY3);
+            const int a = ca + lx, b = cb + ly, c = cc + lz;
+            const int x = 2 * a + px[s], y = 2 * b + py[s], z = 2 * c + pz[s];
+            S.red[s][lz][ly][lx] = (x >= 1 && x <= n && y >= 1 && y <= n && z >= 1 && z <= n) ? (*cos[s])(a, b, c) : T(0);
+        }
+    }
+    for (int q = tid; q < WX3 * WY3 * WZ3; q += 256) {
+        const int lx = q % WX3, ly = (q / WX3) % WY3, lz = q / (WX3 * WY3);
+        const int x = x0 - 2 + lx, y = y0 - 2 + ly, z = z0 - 2 + lz;
+        S.r[lz][ly][lx] = (x >= 1 && x <= n && y >= 1 && y <= n && z >= 1 && z <= n) ? rg(x, y, z) : T(0);
+    }
+    __syncthreads();
+    // red value at fine (x, y, z), x + y + z even, within the tile +- 3
+    auto red = [&](int x, int y, int z) -> T {
+        const int s = (x & 1) ? ((y & 1) ? 1 : 2) : ((y & 1) ? 3 : 0);
+        return S.red[s][(z >> 1) - cc][(y >> 1) - cb][(x >> 1) - ca];
+    };
+    // F points (odd index sum) on the tile +- 2: per row the WX3/2 points of that parity
+    for (int q = tid; q < (WX3 / 2) * WY3 * WZ3; q += 256) {
+        const int hx = q % (WX3 / 2), ly = (q / (WX3 / 2)) % WY3, lz = q / ((WX3 / 2) * WY3);
+        const int y = y0 - 2 + ly, z = z0 - 2 + lz;
+        const int xs = x0 - 2, p = (y + z + 1) & 1;          // x parity of the odd points of this row
+        const int lx = 2 * hx + ((p - xs) & 1), x = xs + lx;
+        T val = T(0);
+        if (x >= 1 && x <= n && y >= 1 && y <= n && z >= 1 && z <= n) {
+            const T s = (red(x - 1, y, z) + red(x + 1, y, z)) + (red(x, y - 1, z) + red(x, y + 1, z)) +
+                        (red(x, y, z - 1) + red(x, y, z + 1));
+            val = (s - cg * S.r[lz][ly][lx]) * T(1.0 / 6.0);
+        }
+        S.v[lz][ly][lx] = val;
+    }
+    __syncthreads();
+    // C points (even index sum) on the tile +- 1
+    for (int q = tid; q < ((WX3 - 2) / 2) * (WY3 - 2) * (WZ3 - 2); q += 256) {
+        const int hx = q % ((WX3 - 2) / 2), my = (q / ((WX3 - 2) / 2)) % (WY3 - 2), mz = q / (((WX3 - 2) / 2) * (WY3 - 2));
+        const int ly = my + 1, lz = mz + 1;
+        const int y = y0 - 2 + ly, z = z0 - 2 + lz;
+        const int xs = x0 - 1, p = (y + z) & 1;               // x parity of the even points of this row
+        const int lx = 1 + 2 * hx + ((p - xs) & 1), x = x0 - 2 + lx;
+        T val = T(0);
+        if (x >= 1 && x <= n && y >= 1 && y <= n && z >= 1 && z <= n) {
+            const T s = (S.v[lz][ly][lx - 1] + S.v[lz][ly][lx + 1]) + (S.v[lz][ly - 1][lx] + S.v[lz][ly + 1][lx]) +
+                        (S.v[lz - 1][ly][lx] + S.v[lz + 1][ly][lx]);
+            val = (s - cg * S.r[lz][ly][lx]) * T(1.0 / 6.0);
+        }
+        S.v[lz][ly][lx] = val;
+    }
+    __syncthreads();
+    float sq = 0.f;
+    for (int q = tid; q < TX3 * TY3 * TZ3; q += 256) {
+        const int tx = q % TX3, ty = (q / TX3) % TY3, tz = q / (TX3 * TY3);
+        const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
+        if (x > n || y > n || z > n) continue;
+        const int lx = tx + 2, ly = ty + 2, lz = tz + 2;
+        const T v = S.v[lz][ly][lx];
+        if (RR) {
+            const float nb[6] = {(float)S.v[lz][ly][lx - 1], (float)S.v[lz][ly][lx + 1], (float)S.v[lz][ly - 1][lx],
+                                 (float)S.v[lz][ly + 1][lx], (float)S.v[lz - 1][ly][lx], (float)S.v[lz + 1][ly][lx]};
+            float hi, lo;
+            lap_sum6(nb, (float)v, hi, lo);
+            const size_t cu = ((size_t)z * (n + 2) + y) * up + x, cr = ((size_t)z * (n + 2) + y) * rp + x;
+            u[cu] += widen(v);
+            const double rn = fma(-ih2, widen(hi), fma(-ih2, widen(lo), r64[cr]));
+            r64[cr] = rn;
+            const float rf = (float)rn;
+            rnew(x, y, z) = (T)rf;
+            sq = fmaf(rf, rf, sq);
+        } else if (FINEST) {
+            u[((size_t)z * (n + 2) + y) * up + x] += widen(v);
+        } else {
+            vg(x, y, z) = v;
+        }
+    }
+    if (RR) {
+        const double s = block_sum((double)sq, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz)] = s;
+    }
+}
+
+// 3D direct residual writing both the FP32 copy and the carried FP64 residual
+__global__ void __launch_bounds__(256) k_res0_64_3d(const double *__restrict__ f, const double *__restrict__ u,
+                                                    int up, int n, double ih2, A3<float> r, double *r64, int rp,
+                                                    double *part, const int *done, Bt B) {
+    __shared__ double sh[32];
+    const int prob = bt_prob(B), bz = bt_z(B);
+    if (stop(bt_done(done, prob, B))) return;
+    if (B.ftab) { f = B.ftab[prob]; u = B.utab[prob]; }
+    r = bt_at(r, prob, B);
+    r64 = bt_ptr(r64, prob, B);
+    part += (size_t)prob * B.nparts;
+    const int i = blockIdx.x * 32 + threadIdx.x + 1, j = blockIdx.y * 8 + threadIdx.y + 1;
+    const int k0 = bz * RES3_PLANES + 1;
+    const size_t pl = (size_t)up * (n + 2), pr = (size_t)rp * (n + 2);
+    float acc = 0.f;
+    if (i <= n && j <= n) {
+        const double *uc = u + k0 * pl + (size_t)j * up + i;
+        const double *fc = f + k0 * pl + (size_t)j * up + i;
+        double ud = uc[-(long)pl], u0 = uc[0];
+#pragma unroll
+        for (int q = 0; q < RES3_PLANES; q++) {
+            if (k0 + q > n) break;
+            const double uu = uc[pl];
+            const double s = ((uc[-1] + uc[1]) + (uc[-up] + uc[up])) + (ud + uu);
+            const double res = fma(-ih2, fma(-6.0, u0, s), fc[0]);
+            const float rf = (float)res;
+            r(i, j, k0 + q) = rf;
+            r64[(k0 + q) * pr + (size_t)j * rp + i] = res;
+            acc = fmaf(rf, rf, acc);
+            ud = u0; u0 = uu;
+            uc += pl; fc += pl;
+        }
+    }
+    double s = block_sum((double)acc, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0)
+        part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz)] = s;
+}
+
+}  // namespace mg

@@ -319,7 +319,7 @@ int residual_blocks(const mg_ctx *c) {
 }
 
 // restriction r^(l+1) <- r^(l)
-template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cudaStream_t s) {
+template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cudaStream_t s, bool alt = false) {
     const Level &a = c->lv[l], &b = c->lv[l + 1];
     if (c->d.hierarchy == MG_USUAL) {
         const int nc = b.side;
@@ -339,7 +339,10 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
     }
     if (a.kind == KIND_AXIS) {
         const int nb = b.nb;
-        LAUNCH_B(TAG_LEVELS, (k_g2r_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(a.r[0], a), red3v<T>(b.r, b), nb, done);
+        const T *galt = (alt && l == 0 && c->rr) ? (const T *)c->r32b : nullptr;
+        const int *par = galt ? &c->ctl->par : nullptr;
+        LAUNCH_B(TAG_LEVELS, (k_g2r_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(a.r[0], a), red3v<T>(b.r, b), nb,
+                 galt, par, done);
     } else if (a.kind == KIND_RED) {
         const int nb = a.nb;
         LAUNCH_B(TAG_LEVELS, (k_r2m_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, red3v<const T>(a.r, a), mag3v<T>(b.r, b), nb, done);
@@ -371,14 +374,16 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
             else
                 LAUNCH_B(TAG_LEVELS, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
         } else if (c->d.hierarchy == MG_DIAG) {  // both green-red half-sweeps in one tile kernel
-            const dim3 g3((n + GX3 - 1) / GX3, (n + GY3 - 1) / GY3, (n + GZ3 - 1) / GZ3);
-            const size_t sm = sizeof(T) * ((GX3 + 4) * (GY3 + 4) * (GZ3 + 4) + 2 * (GX3 + 2) * (GY3 + 2) * (GZ3 + 2));
+            const dim3 g3((n + TX3 - 1) / TX3, (n + TY3 - 1) / TY3, (n + TZ3 - 1) / TZ3);
+            const size_t sm = sizeof(Green3Smem<T>);
             if (u)
-                LAUNCH_SMEM_B(TAG_FINEST_UP, (k_up_green_3d<T, true>), g3, B2, sm, red3v<const T>(b.v, b),
-                              a3<const T>(a.r[0], a), a3<T>(a.v[0], a), u, c->d.pitch, n, cc, done);
+                LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_3d<T, false, true>), g3, B2, sm, red3v<const T>(b.v, b),
+                              a3<const T>(a.r[0], a), (const T *)nullptr, a3<T>(a.v[0], a), (double *)nullptr, 0, u,
+                              c->d.pitch, n, cc, 0.0, (double *)nullptr, (const int *)nullptr, done);
             else
-                LAUNCH_SMEM_B(TAG_LEVELS, (k_up_green_3d<T, false>), g3, B2, sm, red3v<const T>(b.v, b),
-                              a3<const T>(a.r[0], a), a3<T>(a.v[0], a), u, c->d.pitch, n, cc, done);
+                LAUNCH_SMEM_B(TAG_LEVELS, (k_green_3d<T, false, false>), g3, B2, sm, red3v<const T>(b.v, b),
+                              a3<const T>(a.r[0], a), (const T *)nullptr, a3<T>(a.v[0], a), (double *)nullptr, 0, u,
+                              c->d.pitch, n, cc, 0.0, (double *)nullptr, (const int *)nullptr, done);
         } else {
             if (c->d.hierarchy == MG_USUAL)
                 LAUNCH_B(TAG_LEVELS, (k_usual_odd_3d<T>), grid3(n, n, n), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
@@ -640,11 +645,37 @@ int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
 int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
     const int n = c->d.n;
     const Level &l0 = c->lv[0];
+    if (c->d.dim == 3) {
+        dim3 g3((n + 31) / 32, (n + 7) / 8, (n + RES3_PLANES - 1) / RES3_PLANES);
+        LAUNCH_B(TAG_RESIDUAL, (k_res0_64_3d), g3, B2, f, u, c->d.pitch, n, 1.0 / (c->h * c->h), a3<float>(l0.r[0], l0),
+                 (double *)c->r64, c->r64_pitch, c->part, done);
+        c->nparts = (int)(g3.x * g3.y * g3.z);
+        return c->nparts;
+    }
     dim3 g((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
     LAUNCH_B(TAG_RESIDUAL, (k_res0_64_2d), g, B2, f, u, c->d.pitch, n, 1.0 / (c->h * c->h), a2<float>(l0.r[0], l0),
              (double *)c->r64, c->r64_pitch, c->part, done);
     c->nparts = (int)(g.x * g.y);
     return c->nparts;
+}
+
+// one cycle of the fused mixed 3D path; returns the partial sums per problem
+int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
+    const int lc = 3 * c->kc;
+    for (int l = 0; l < lc; l++) launch_restrict<float>(c, l, done, s, true);
+    const Level &gk = c->lv[lc];
+    LAUNCH_SMEM_B(TAG_LEVELS, (k_coarse_cta_3d<float>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan3d,
+                  a3<const float>(gk.r[0], gk), a3<float>(gk.v[0], gk), c->G, done);
+    for (int l = lc - 1; l >= 1; l--) launch_prolong<float>(c, l, c->d.omega, nullptr, done, s);
+    const Level &a = c->lv[0], &b = c->lv[1];
+    const int n = c->d.n;
+    const double h2 = c->h * c->h;
+    const dim3 g3((n + TX3 - 1) / TX3, (n + TY3 - 1) / TY3, (n + TZ3 - 1) / TZ3);
+    LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_3d<float, true, true>), g3, B2, sizeof(Green3Smem<float>),
+                  red3v<const float>(b.v, b), a3<const float>(a.r[0], a), (const float *)c->r32b, a3<float>(a.v[0], a),
+                  (double *)c->r64, c->r64_pitch, u, c->d.pitch, n, (float)(c->d.omega[3] * h2), 1.0 / h2, c->part,
+                  &c->ctl->par, done);
+    return (int)(g3.x * g3.y * g3.z);
 }
 
 template <typename T> cudaError_t set_smem_attrs(const mg_ctx *c) {
@@ -784,8 +815,8 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     size_t total = 0;
     for (auto &l : c->lv) total += (size_t)l.ncos * 2 * ((l.len * c->esz + 255) / 256 * 256);
     // fused update + residual of the mixed 2D diagonal solve (needs at least one pair outside the coarse block)
-    c->rr = d->dim == 2 && d->hierarchy == MG_DIAG && d->precision == MG_MIXED && d->order == 2 && d->n > 63;
-    const size_t r64_bytes = c->rr ? ((size_t)c->lv[0].pitch * c->lv[0].rows * 8 + 255) / 256 * 256 : 0;
+    c->rr = d->hierarchy == MG_DIAG && d->precision == MG_MIXED && d->order == 2 && d->n > (d->dim == 2 ? 63 : 15);
+    const size_t r64_bytes = c->rr ? (c->lv[0].len * 8 + 255) / 256 * 256 : 0;
     const size_t r32_bytes = c->rr ? (c->lv[0].len * 4 + 255) / 256 * 256 : 0;
     total += r64_bytes + r32_bytes;
     c->nprob = nprob;
@@ -811,8 +842,13 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
         cudaError_t e = d->precision == MG_FP64
             ? cudaFuncSetAttribute(k_coarse_cta_3d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes)
             : cudaFuncSetAttribute(k_coarse_cta_3d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_up_green_3d<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_up_green_3d<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, gsm);
+        (void)gsm;
+        const int g64 = (int)sizeof(Green3Smem<double>), g32 = (int)sizeof(Green3Smem<float>);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<float, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
         if (e != cudaSuccess) {
             mg_destroy(c);
             return cuda_fail(e, "mg_create shared-memory attributes (3D)");
@@ -1050,7 +1086,7 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     const long long l1 = c->launches;
     int np2;
     if (c->rr) {
-        np2 = vcycle_rr(c, u, done, s2);
+        np2 = c->d.dim == 3 ? vcycle_rr3(c, u, done, s2) : vcycle_rr(c, u, done, s2);
     } else {
         mg_status stv = fp64 ? vcycle_t<double>(c, f, u, done, false, s2) : vcycle_t<float>(c, f, u, done, false, s2);
         if (stv != MG_OK) {
@@ -1110,7 +1146,7 @@ static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double r
     for (int cyc = 0; cyc < max_cycles; cyc += 4) {
         for (int q = 0; q < 4 && cyc + q < max_cycles; q++) {
             if (c->rr) {
-                np = vcycle_rr(c, u, done, s);
+                np = c->d.dim == 3 ? vcycle_rr3(c, u, done, s) : vcycle_rr(c, u, done, s);
             } else {
                 mg_status st = fp64 ? vcycle_t<double>(c, f, u, done, false, s) : vcycle_t<float>(c, f, u, done, false, s);
                 if (st != MG_OK) return st;

@@ -234,9 +234,10 @@ template <typename T> __device__ __forceinline__ T red3(const Red3<const T> &r, 
 // green -> red, Eq. Erred: (6r + 6 axis neighbours)/12 at i+j+k even.
 // Thread per cell (a,b,c) in [0,nb]^3 holding EEE, OOE, OEO, EOO points.
 template <typename T>
-__global__ void k_g2r_3d(A3<const T> g, Red3<T> red, int nb, const int *done, Bt B) {
+__global__ void k_g2r_3d(A3<const T> g, Red3<T> red, int nb, const T *galt, const int *par, const int *done, Bt B) {
     const int prob_ = bt_prob(B);
     if (stop(bt_done(done, prob_, B))) return;
+    if (galt && par[(size_t)prob_ * B.ctl_stride]) g.p = galt;  // the current one of two green buffers
     g = bt_at(g, prob_, B);
     red = bt_at(red, prob_, B);
     MG_IDX3 const int a = tx, b = ty, c = tz;

@@ -263,13 +263,13 @@ def test_full_size_vcycle_matches_oracle(dim, n):
     assert np.linalg.norm(got - uo) / np.linalg.norm(uo) <= TOL
 
 
-@pytest.mark.parametrize("n", [127, 1023, 4095])
-def test_mixed_carried_residual_equals_direct_residual(n):
+@pytest.mark.parametrize("dim,n", [(2, 127), (2, 1023), (2, 4095), (3, 63), (3, 255)])
+def test_mixed_carried_residual_equals_direct_residual(dim, n):
     """The mixed 2D solve carries its FP64 residual from cycle to cycle
     (r <- r - L v); at the end it must agree with a direct FP64 residual of
     the returned u, and both must meet the tolerance."""
-    f = T(I.square_large(n) if n == 4095 else I.uniform_f(2, n, 9))
-    with Context(2, n, precision="mixed") as c:
+    f = T(I.square_large(n) if n == 4095 else I.uniform_f(dim, n, 9))
+    with Context(dim, n, precision="mixed") as c:
         u, it, rel, hist = c.solve(f, rtol=1e-10)
         r2 = c.residual(f, u)
         f2 = c.residual(f, torch.zeros_like(u))
