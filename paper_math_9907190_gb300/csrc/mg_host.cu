@@ -373,7 +373,7 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
                 LAUNCH_B(TAG_FINEST_UP, (k_r2g_c_upd_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
             else
                 LAUNCH_B(TAG_LEVELS, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
-        } else if (c->d.hierarchy == MG_DIAG) {  // both green-red half-sweeps in one tile kernel
+        } else if (c->d.hierarchy == MG_DIAG && sizeof(T) == 4) {  // FP32: both half-sweeps in one tile kernel
             const dim3 g3((n + TX3 - 1) / TX3, (n + TY3 - 1) / TY3, (n + TZ3 - 1) / TZ3);
             const size_t sm = sizeof(Green3Smem<T>);
             if (u)
