@@ -619,15 +619,21 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
 namespace mg {
 
 // ---------------------------------------------------------------------------
-// Finest pair of a mixed-precision solve, fused with the next residual.
+// Finest pair of a mixed-precision 2D solve, fused with u += v and the next
+// residual.
 //
-// u_new = u + v and r_new = f - L u_new = r - L v.  The correction v is FP32;
-// L v = (sum of the four axis neighbours of v - 4 v)/h^2 is formed from the
-// four exact FP32 differences v_nb - v (two-sum) summed as a float-float pair,
-// whose error is ~2^-46 |v_nb - v|, far below the FP64 rounding of r; only
-// r - (ih2 * hi + ih2 * lo) and u + v run on the FP64 pipe (3 operations per
-// point instead of the 6 of a separate residual).  r is carried in FP64 (r64)
-// from one cycle to the next; its FP32 copy feeds the levels and the norm.
+// The residual is carried from cycle to cycle as a float-float pair
+// r = hi + lo: hi is the FP32 residual that the levels and the norm read
+// (double-buffered by Ctrl.par, since the sweep reads it in a halo), lo a
+// second FP32 array.  A cycle's correction v (FP32) gives
+//   u_new = u + v          (the one FP64 operation per point)
+//   r_new = r - L v,       L v = s2 * sum over the four axis neighbours of (v_nb - v)
+// where each difference v_nb - v is exact as a two-sum pair, the four pairs
+// are accumulated as a float-float pair, s2 = 1/h^2 is a power of two
+// (n = 2^m - 1) so the scaling is exact, and the subtraction is a float-float
+// operation.  Its error is ~2^-47 (|r| + s2 sum |v_nb - v|), far below the
+// FP64 rounding of a direct residual of u_new; a direct FP64 residual starts
+// and ends every solve.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -651,134 +657,246 @@ __device__ __forceinline__ void lap_sum(float n0, float n1, float n2, float n3, 
     lo = ((e0 + e1) + (e2 + e3)) + ((e4 + e5) + e6);
 }
 
-template <int TA, int TB> struct UpRRSmem {
-    float b[TB + 7][TA + 7];       // blue v, cells [a0-3, a0+TA+3]
-    float roo[TB + 6][TA + 6];     // OO cells [a0-3, a0+TA+2]
-    float voo[TB + 6][TA + 6];
-    float ree[TB + 5][TA + 5];     // EE cells [a0-2, a0+TA+2]
-    float vee[TB + 5][TA + 5];
-    float rg[2 * TB + 8][2 * TA + 8];  // green r, x in [2a0-4, 2a0+2TA+3]
-    float voe[TB + 4][TA + 4];     // F cells [a0-2, a0+TA+1]
-    float veo[TB + 4][TA + 4];
-    float vce[TB + 2][TA + 2];     // C cells [a0-1, a0+TA]: green EE and OO points
-    float vco[TB + 2][TA + 2];
-};
+// (nh, nl) ~= (hi + lo) - s2 * (lh + ll), s2 a power of two
+__device__ __forceinline__ void ff_sub(float hi, float lo, float lh, float ll, float s2, float &nh, float &nl) {
+    float s, e;
+    two_sum(hi, -s2 * lh, s, e);
+    two_sum(s, fmaf(-s2, ll, lo) + e, nh, nl);
+}
 
+// Work decomposition of k_up0_ff_2d.  A cell (a,b) is the four green points
+// (2a..2a+1, 2b..2b+1).  A warp owns 32*FF_K consecutive cell columns (FF_K
+// per lane) and walks a strip of cell rows upward, holding every
+// intermediate row in registers: x neighbours come from the adjacent lane by
+// shuffle, y neighbours from earlier steps.  The chain reaches -2..+3 cells in
+// x, so a warp writes its middle FF_W cells (an even count, so that the four
+// points of a lane's two cells are one aligned 16-byte group of every green
+// row); a strip starts 4 rows early to fill the chain (those steps write
+// nothing).  Blocks are persistent: warps take (column, strip) items in turn.
+constexpr int FF_K = 2;
+constexpr int FF_W = 32 * FF_K - 6;
+constexpr int FF_WARPS = 4;
 
-template <int TA, int TB>
-__global__ void __launch_bounds__(256) k_up0_rr_2d(A2<const float> blue, A2<const float> ree, A2<const float> roo,
-                                                   A2<float> rga, float *rgb, double *__restrict__ r64, int rp,
-                                                   double *__restrict__ u, int up, int nb, float c2, float c1,
-                                                   double ih2, double *part, const int *par, const int *done, Bt B) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    UpRRSmem<TA, TB> &S = *reinterpret_cast<UpRRSmem<TA, TB> *>(smraw);
+// Step b of a strip: load blue row b+3, red rows b+2 and green-residual rows
+// 2b+2, 2b+3; form red OO row b+2 (Eq. Eajacr) and red EE row b+2
+// (Eq. Eajacb) with c2 = 2 p h^2, the green-only points of cell row b+1, the
+// re-relaxed red points EE of row b+1 and OO of row b (the red-to-green sweep
+// of Section 2.2, c1 = p h^2); then apply v to the four points of every own
+// cell of row b.  Values outside the interior are zero, as in the oracle.
+// VU: u is 16-byte aligned with an even pitch (vector access to u).
+template <bool VU>
+__global__ void __launch_bounds__(32 * FF_WARPS) k_up0_ff_2d(A2<const float> blue, A2<const float> ree,
+                                                             A2<const float> roo, A2<float> rga, float *rgb,
+                                                             float *__restrict__ rlo, double *__restrict__ u, int up,
+                                                             int nb, float c2, float c1, float s2, int tb,
+                                                             double *part, const int *par, const int *done, Bt B) {
     __shared__ double sh[32];
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int K = FF_K;
     const int prob = blockIdx.z;
     if (stop(bt_done(done, prob, B))) return;
-    // read the current green residual buffer, write the new residual into the other
     const bool p1 = par[(size_t)prob * B.ctl_stride] != 0;
     A2<float> rg = rga, rnew = rga;
     (p1 ? rg : rnew).p = rgb;
     blue = bt_at(blue, prob, B); ree = bt_at(ree, prob, B); roo = bt_at(roo, prob, B);
     rg = bt_at(rg, prob, B); rnew = bt_at(rnew, prob, B);
-    r64 = bt_ptr(r64, prob, B);
+    rlo = bt_ptr(rlo, prob, B);
     if (B.utab) u = B.utab[prob];
     part += (size_t)prob * B.nparts;
-    const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
-    const int n = 2 * nb + 1;
-    MG_FOR2(TA + 7, TB + 7) {
-        const int a = a0 - 3 + x, b = b0 - 3 + y;
-        S.b[y][x] = (a >= 0 && a <= nb + 1 && b >= 0 && b <= nb + 1) ? blue(a, b) : 0.f;
-    }
-    MG_FOR2(TA + 6, TB + 6) {
-        const int a = a0 - 3 + x, b = b0 - 3 + y;
-        S.roo[y][x] = (a >= 0 && a <= nb && b >= 0 && b <= nb) ? roo(a, b) : 0.f;
-    }
-    MG_FOR2(TA + 5, TB + 5) {
-        const int a = a0 - 2 + x, b = b0 - 2 + y;
-        S.ree[y][x] = (a >= 1 && a <= nb && b >= 1 && b <= nb) ? ree(a, b) : 0.f;
-    }
-    MG_FOR2(2 * TA + 8, 2 * TB + 8) {
-        const int gx = 2 * a0 - 4 + x, gy = 2 * b0 - 4 + y;
-        S.rg[y][x] = (gx >= 1 && gx <= n && gy >= 1 && gy <= n) ? rg(gx, gy) : 0.f;
-    }
-    __syncthreads();
-    // red OO (Eq. Eajacr), cells [a0-3, a0+TA+2]
-    MG_FOR2(TA + 6, TB + 6) {
-        const int c = a0 - 3 + x, d = b0 - 3 + y;
-        float v = 0.f;
-        if (c >= 0 && c <= nb && d >= 0 && d <= nb)
-            v = ((S.b[y][x] + S.b[y][x + 1]) + (S.b[y + 1][x] + S.b[y + 1][x + 1]) - c2 * S.roo[y][x]) * 0.25f;
-        S.voo[y][x] = v;
-    }
-    __syncthreads();
-    // red EE (Eq. Eajacb), cells [a0-2, a0+TA+2]
-    MG_FOR2(TA + 5, TB + 5) {
-        const int a = a0 - 2 + x, b = b0 - 2 + y;
-        float v = 0.f;
-        if (a >= 1 && a <= nb && b >= 1 && b <= nb)
-            v = ((S.voo[y][x] + S.voo[y][x + 1]) + (S.voo[y + 1][x] + S.voo[y + 1][x + 1]) - c2 * S.ree[y][x]) * 0.25f;
-        S.vee[y][x] = v;
-    }
-    __syncthreads();
-    // green-only points, cells [a0-2, a0+TA+1]
-    MG_FOR2(TA + 4, TB + 4) {
-        const int a = a0 - 2 + x, b = b0 - 2 + y;
-        float voe = 0.f, veo = 0.f;
-        if (a >= 0 && a <= nb && b >= 1 && b <= nb)
-            voe = ((S.vee[y][x] + S.vee[y][x + 1]) + (S.voo[y][x + 1] + S.voo[y + 1][x + 1]) - c1 * S.rg[2 * y][2 * x + 1]) *
-                  0.25f;
-        if (a >= 1 && a <= nb && b >= 0 && b <= nb)
-            veo = ((S.voo[y + 1][x] + S.voo[y + 1][x + 1]) + (S.vee[y][x] + S.vee[y + 1][x]) - c1 * S.rg[2 * y + 1][2 * x]) *
-                  0.25f;
-        S.voe[y][x] = voe;
-        S.veo[y][x] = veo;
-    }
-    __syncthreads();
-    // red points (green C) of cells [a0-1, a0+TA]
-    MG_FOR2(TA + 2, TB + 2) {
-        const int a = a0 - 1 + x, b = b0 - 1 + y;
-        const int fx = x + 1, fy = y + 1;
-        float vEE = 0.f, vOO = 0.f;
-        if (a >= 1 && a <= nb && b >= 1 && b <= nb)
-            vEE = ((S.voe[fy][fx - 1] + S.voe[fy][fx]) + (S.veo[fy - 1][fx] + S.veo[fy][fx]) - c1 * S.rg[2 * fy][2 * fx]) * 0.25f;
-        if (a >= 0 && a <= nb && b >= 0 && b <= nb)
-            vOO = ((S.veo[fy][fx] + S.veo[fy][fx + 1]) + (S.voe[fy][fx] + S.voe[fy + 1][fx]) - c1 * S.rg[2 * fy + 1][2 * fx + 1]) *
-                  0.25f;
-        S.vce[y][x] = vEE;
-        S.vco[y][x] = vOO;
-    }
-    __syncthreads();
-    // own cells: the four green points of cell (a,b) and their four axis
-    // neighbours (C index (cx, cy) = (a-a0+1, b-b0+1), F index = C index + 1)
+    const int lane = threadIdx.x;
+    const int n = 2 * nb + 1, gp = rga.pitch;
+    const int ncol = (nb + FF_W) / FF_W, nstrip = (nb + tb) / tb;
     float sq = 0.f;
-    auto point = [&](int i, int j, float v, float w, float e, float s_, float nn) {
-        float hi, lo;
-        lap_sum(w, e, s_, nn, v, hi, lo);
-        const size_t cu = (size_t)j * up + i, cr = (size_t)j * rp + i;
-        u[cu] += widen(v);
-        const double rn = fma(-ih2, widen(hi), fma(-ih2, widen(lo), r64[cr]));
-        r64[cr] = rn;
-        const float rf = (float)rn;
-        rnew(i, j) = rf;
-        sq = fmaf(rf, rf, sq);
-    };
-    MG_FOR2(TA, TB) {
-        const int a = a0 + x, b = b0 + y;
-        if (a > nb || b > nb) continue;
-        const int cx = x + 1, cy = y + 1, fx = x + 2, fy = y + 2;
-        const int i = 2 * a, j = 2 * b;
-        if (a >= 1 && b >= 1)  // EE at (2a, 2b): OE(a-1,b), OE(a,b), EO(a,b-1), EO(a,b)
-            point(i, j, S.vce[cy][cx], S.voe[fy][fx - 1], S.voe[fy][fx], S.veo[fy - 1][fx], S.veo[fy][fx]);
-        if (b >= 1)            // OE at (2a+1, 2b): EE(a,b), EE(a+1,b), OO(a,b-1), OO(a,b)
-            point(i + 1, j, S.voe[fy][fx], S.vce[cy][cx], S.vce[cy][cx + 1], S.vco[cy - 1][cx], S.vco[cy][cx]);
-        if (a >= 1)            // EO at (2a, 2b+1): OO(a-1,b), OO(a,b), EE(a,b), EE(a,b+1)
-            point(i, j + 1, S.veo[fy][fx], S.vco[cy][cx - 1], S.vco[cy][cx], S.vce[cy][cx], S.vce[cy + 1][cx]);
-        // OO at (2a+1, 2b+1): EO(a,b), EO(a+1,b), OE(a,b), OE(a,b+1)
-        point(i + 1, j + 1, S.vco[cy][cx], S.veo[fy][fx], S.veo[fy][fx + 1], S.voe[fy][fx], S.voe[fy + 1][fx]);
+    for (int it = blockIdx.x * FF_WARPS + threadIdx.y; it < ncol * nstrip; it += gridDim.x * FF_WARPS) {
+        const int col = it % ncol, strip = it / ncol;
+        const int A = col * FF_W - 2, a0 = A + K * lane;
+        // nb is odd and a0 even: the lane's K cells are all in [0, nb] or all outside
+        const bool in = a0 >= 0 && a0 <= nb;
+        const bool own = in && a0 >= A + 2 && a0 < A + 2 + FF_W;
+        bool pos[K];  // column of cell k holds green points with even x (a >= 1)
+#pragma unroll
+        for (int k = 0; k < K; k++) pos[k] = in && a0 + k >= 1;
+        const int b0 = strip * tb, b1 = min(b0 + tb, nb + 1), bs = max(b0 - 4, -2);
+        // chain state, rows relative to the step's b
+        float bl2[K], oo0[K], oo1[K], ee1[K], oe0[K], eom[K], eo0[K], ce0[K], com[K], r0[2 * K], r1[2 * K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            bl2[k] = oo0[k] = oo1[k] = ee1[k] = oe0[k] = eom[k] = eo0[k] = ce0[k] = com[k] = 0.f;
+            r0[2 * k] = r0[2 * k + 1] = r1[2 * k] = r1[2 * k + 1] = 0.f;
+        }
+        if (in && bs + 2 >= 0) {
+            const float2 q = *reinterpret_cast<const float2 *>(&blue(a0, bs + 2));
+            bl2[0] = q.x; bl2[1] = q.y;
+        }
+        for (int b = bs; b < b1; b++) {
+            float bl3[K], ro2[K], re2[K], g2[2 * K], g3[2 * K];
+#pragma unroll
+            for (int k = 0; k < K; k++) bl3[k] = ro2[k] = re2[k] = g2[2 * k] = g2[2 * k + 1] = g3[2 * k] = g3[2 * k + 1] = 0.f;
+            if (in) {
+                if (b + 3 <= nb + 1) {
+                    const float2 q = *reinterpret_cast<const float2 *>(&blue(a0, b + 3));
+                    bl3[0] = q.x; bl3[1] = q.y;
+                }
+                if (b + 2 >= 0 && b + 2 <= nb) {
+                    const float2 q = *reinterpret_cast<const float2 *>(&roo(a0, b + 2));
+                    const float2 w = *reinterpret_cast<const float2 *>(&ree(a0, b + 2));
+                    ro2[0] = q.x; ro2[1] = q.y; re2[0] = w.x; re2[1] = w.y;
+                }
+                if (2 * b + 2 >= 1 && 2 * b + 2 <= n) {
+                    const float4 q = *reinterpret_cast<const float4 *>(&rg(2 * a0, 2 * b + 2));
+                    g2[0] = q.x; g2[1] = q.y; g2[2] = q.z; g2[3] = q.w;
+                }
+                if (2 * b + 3 >= 1 && 2 * b + 3 <= n) {
+                    const float4 q = *reinterpret_cast<const float4 *>(&rg(2 * a0, 2 * b + 3));
+                    g3[0] = q.x; g3[1] = q.y; g3[2] = q.z; g3[3] = q.w;
+                }
+            }
+            // the own cells' u and lo of cell row b (rows 2b, 2b+1), issued before the chain
+            const bool upd = own && b >= b0;
+            const bool row0 = b >= 1;  // green row 2b is interior
+            double u0[2 * K], u1[2 * K];
+            float l0[2 * K], l1[2 * K];
+#pragma unroll
+            for (int q = 0; q < 2 * K; q++) { u0[q] = u1[q] = 0.0; l0[q] = l1[q] = 0.f; }
+            double *ur0 = u + (size_t)(2 * b) * up + 2 * a0, *ur1 = ur0 + up;
+            float *lr0 = rlo + (size_t)(2 * b) * gp + 2 * a0, *lr1 = lr0 + gp;
+            if (upd) {
+                if (row0) {
+                    const float4 q = *reinterpret_cast<const float4 *>(lr0);
+                    l0[0] = q.x; l0[1] = q.y; l0[2] = q.z; l0[3] = q.w;
+                }
+                {
+                    const float4 q = *reinterpret_cast<const float4 *>(lr1);
+                    l1[0] = q.x; l1[1] = q.y; l1[2] = q.z; l1[3] = q.w;
+                }
+                if (VU) {
+                    if (row0) {
+                        const double2 p = reinterpret_cast<const double2 *>(ur0)[0], q = reinterpret_cast<const double2 *>(ur0)[1];
+                        u0[0] = p.x; u0[1] = p.y; u0[2] = q.x; u0[3] = q.y;
+                    }
+                    const double2 p = reinterpret_cast<const double2 *>(ur1)[0], q = reinterpret_cast<const double2 *>(ur1)[1];
+                    u1[0] = p.x; u1[1] = p.y; u1[2] = q.x; u1[3] = q.y;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 2 * K; q++) {
+                        const bool px = (q & 1) || pos[q >> 1];  // green x = 2a0+q is interior
+                        if (row0 && px) u0[q] = ur0[q];
+                        if (px) u1[q] = ur1[q];
+                    }
+                }
+            }
+            // ---- the chain
+            const bool y_oo2 = b + 2 >= 0 && b + 2 <= nb, y_ee2 = b + 2 >= 1 && b + 2 <= nb;
+            const bool y_oe1 = b + 1 >= 1 && b + 1 <= nb, y_eo1 = b + 1 >= 0 && b + 1 <= nb;
+            const bool y_co0 = b >= 0 && b <= nb;
+            float oo2[K], ee2[K], oe1[K], eo1[K], ce1[K], co0[K];
+            {
+                const float bl2R = __shfl_down_sync(FULL, bl2[0], 1), bl3R = __shfl_down_sync(FULL, bl3[0], 1);
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    const float r2 = k + 1 < K ? bl2[k + 1] : bl2R, r3 = k + 1 < K ? bl3[k + 1] : bl3R;
+                    oo2[k] = (in && y_oo2) ? ((bl2[k] + r2) + (bl3[k] + r3) - c2 * ro2[k]) * 0.25f : 0.f;
+                }
+            }
+            const float oo1L = __shfl_up_sync(FULL, oo1[K - 1], 1), oo2L = __shfl_up_sync(FULL, oo2[K - 1], 1);
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const float l1v = k > 0 ? oo1[k - 1] : oo1L, l2v = k > 0 ? oo2[k - 1] : oo2L;
+                ee2[k] = (pos[k] && y_ee2) ? ((l1v + oo1[k]) + (l2v + oo2[k]) - c2 * re2[k]) * 0.25f : 0.f;
+            }
+            {
+                const float ee1R = __shfl_down_sync(FULL, ee1[0], 1);
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    const float er = k + 1 < K ? ee1[k + 1] : ee1R, ol = k > 0 ? oo1[k - 1] : oo1L;
+                    oe1[k] = (in && y_oe1) ? ((ee1[k] + er) + (oo0[k] + oo1[k]) - c1 * g2[2 * k + 1]) * 0.25f : 0.f;
+                    eo1[k] = (pos[k] && y_eo1) ? ((ol + oo1[k]) + (ee1[k] + ee2[k]) - c1 * g3[2 * k]) * 0.25f : 0.f;
+                }
+            }
+            const float oe1L = __shfl_up_sync(FULL, oe1[K - 1], 1), eo0R = __shfl_down_sync(FULL, eo0[0], 1);
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const float ol = k > 0 ? oe1[k - 1] : oe1L, er = k + 1 < K ? eo0[k + 1] : eo0R;
+                ce1[k] = (pos[k] && y_oe1) ? ((ol + oe1[k]) + (eo0[k] + eo1[k]) - c1 * g2[2 * k]) * 0.25f : 0.f;
+                co0[k] = (in && y_co0) ? ((eo0[k] + er) + (oe0[k] + oe1[k]) - c1 * r1[2 * k + 1]) * 0.25f : 0.f;
+            }
+            // ---- apply v to the own cells of row b
+            const float oe0L = __shfl_up_sync(FULL, oe0[K - 1], 1), ce0R = __shfl_down_sync(FULL, ce0[0], 1);
+            const float co0L = __shfl_up_sync(FULL, co0[K - 1], 1);
+            if (upd) {
+                float h0[2 * K], h1[2 * K];
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    const float oel = k > 0 ? oe0[k - 1] : oe0L, cer = k + 1 < K ? ce0[k + 1] : ce0R;
+                    const float col_ = k > 0 ? co0[k - 1] : co0L, eor = k + 1 < K ? eo0[k + 1] : eo0R;
+                    float lh, ll, nh, nl;
+                    // EE (2a, 2b)
+                    nh = nl = 0.f;
+                    if (pos[k] && row0) {
+                        lap_sum(oel, oe0[k], eom[k], eo0[k], ce0[k], lh, ll);
+                        ff_sub(r0[2 * k], l0[2 * k], lh, ll, s2, nh, nl);
+                        u0[2 * k] += widen(ce0[k]);
+                    }
+                    h0[2 * k] = nh; l0[2 * k] = nl;
+                    // OE (2a+1, 2b)
+                    nh = nl = 0.f;
+                    if (row0) {
+                        lap_sum(ce0[k], cer, com[k], co0[k], oe0[k], lh, ll);
+                        ff_sub(r0[2 * k + 1], l0[2 * k + 1], lh, ll, s2, nh, nl);
+                        u0[2 * k + 1] += widen(oe0[k]);
+                    }
+                    h0[2 * k + 1] = nh; l0[2 * k + 1] = nl;
+                    // EO (2a, 2b+1)
+                    nh = nl = 0.f;
+                    if (pos[k]) {
+                        lap_sum(col_, co0[k], ce0[k], ce1[k], eo0[k], lh, ll);
+                        ff_sub(r1[2 * k], l1[2 * k], lh, ll, s2, nh, nl);
+                        u1[2 * k] += widen(eo0[k]);
+                    }
+                    h1[2 * k] = nh; l1[2 * k] = nl;
+                    // OO (2a+1, 2b+1)
+                    lap_sum(eo0[k], eor, oe0[k], oe1[k], co0[k], lh, ll);
+                    ff_sub(r1[2 * k + 1], l1[2 * k + 1], lh, ll, s2, nh, nl);
+                    u1[2 * k + 1] += widen(co0[k]);
+                    h1[2 * k + 1] = nh; l1[2 * k + 1] = nl;
+                }
+#pragma unroll
+                for (int q = 0; q < 2 * K; q++) sq = fmaf(h0[q], h0[q], fmaf(h1[q], h1[q], sq));
+                float *hr0 = &rnew(2 * a0, 2 * b), *hr1 = hr0 + gp;
+                if (row0) {
+                    *reinterpret_cast<float4 *>(hr0) = make_float4(h0[0], h0[1], h0[2], h0[3]);
+                    *reinterpret_cast<float4 *>(lr0) = make_float4(l0[0], l0[1], l0[2], l0[3]);
+                }
+                *reinterpret_cast<float4 *>(hr1) = make_float4(h1[0], h1[1], h1[2], h1[3]);
+                *reinterpret_cast<float4 *>(lr1) = make_float4(l1[0], l1[1], l1[2], l1[3]);
+                if (VU) {
+                    if (row0) {
+                        reinterpret_cast<double2 *>(ur0)[0] = make_double2(u0[0], u0[1]);
+                        reinterpret_cast<double2 *>(ur0)[1] = make_double2(u0[2], u0[3]);
+                    }
+                    reinterpret_cast<double2 *>(ur1)[0] = make_double2(u1[0], u1[1]);
+                    reinterpret_cast<double2 *>(ur1)[1] = make_double2(u1[2], u1[3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 2 * K; q++) {
+                        const bool px = (q & 1) || pos[q >> 1];
+                        if (row0 && px) ur0[q] = u0[q];
+                        if (px) ur1[q] = u1[q];
+                    }
+                }
+            }
+            // ---- advance the chain one cell row
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                bl2[k] = bl3[k]; oo0[k] = oo1[k]; oo1[k] = oo2[k]; ee1[k] = ee2[k]; oe0[k] = oe1[k];
+                eom[k] = eo0[k]; eo0[k] = eo1[k]; ce0[k] = ce1[k]; com[k] = co0[k];
+                r0[2 * k] = g2[2 * k]; r0[2 * k + 1] = g2[2 * k + 1];
+                r1[2 * k] = g3[2 * k]; r1[2 * k + 1] = g3[2 * k + 1];
+            }
+        }
     }
     const double s = block_sum((double)sq, sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x + gridDim.x * blockIdx.y] = s;
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x] = s;
 }
 
 // sum of f^2 over the interior (the norm of the right-hand side of an order-2
@@ -815,17 +933,18 @@ __global__ void __launch_bounds__(256) k_norm_f(const double *__restrict__ f, in
         part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz)] = s;
 }
 
-// finest residual, written both in the level precision (FP32) and in FP64 to
-// r64 (the carried residual of the fused update); otherwise as k_res0_2d
+// finest residual as the float-float pair of the fused update: hi = the FP32
+// rounding of the FP64 residual (the level's residual), lo = the FP32 rounding
+// of the remainder (array rlo, pitch rp); otherwise as k_res0_2d
 __global__ void __launch_bounds__(256) k_res0_64_2d(const double *__restrict__ f, const double *__restrict__ u,
-                                                    int up, int n, double ih2, A2<float> r, double *r64, int rp,
+                                                    int up, int n, double ih2, A2<float> r, float *rlo, int rp,
                                                     double *part, const int *done, Bt B) {
     __shared__ double sh[32];
     const int prob = blockIdx.z;
     if (stop(bt_done(done, prob, B))) return;
     if (B.ftab) { f = B.ftab[prob]; u = B.utab[prob]; }
     r = bt_at(r, prob, B);
-    r64 = bt_ptr(r64, prob, B);
+    rlo = bt_ptr(rlo, prob, B);
     const int i = blockIdx.x * 32 + threadIdx.x + 1;
     const int j0 = (blockIdx.y * 8 + threadIdx.y) * RES_ROWS + 1;
     float acc = 0.f;
@@ -841,7 +960,7 @@ __global__ void __launch_bounds__(256) k_res0_64_2d(const double *__restrict__ f
             const double res = fma(-ih2, fma(-4.0, u0, s), fc[0]);
             const float rf = (float)res;
             r(i, j0 + q) = rf;
-            r64[(size_t)(j0 + q) * rp + i] = res;
+            rlo[(size_t)(j0 + q) * rp + i] = (float)(res - (double)rf);
             acc = fmaf(rf, rf, acc);
             um = u0; u0 = upn;
             uc += up; fc += up;
@@ -941,9 +1060,9 @@ namespace mg {
 // of 32 x 8 x 4 green points.  The red level is staged as its four cosets
 // (coalesced loads of dense arrays), the F (odd) points are computed on the
 // tile +- 2, the C (even) points on the tile +- 1.  RR: the mixed solve's
-// fused update -- u += v and the carried residual r -= L v, with L v from
-// exact FP32 differences summed as a float-float pair (see lap_sum) --
-// otherwise FINEST: u += v, or v stored.
+// fused update -- u += v and the carried float-float residual r -= L v, as in
+// k_up0_ff_2d with six neighbours (s2 = 1/h^2) -- otherwise FINEST: u += v,
+// or v stored.
 // ---------------------------------------------------------------------------
 constexpr int TX3 = 32, TY3 = 8, TZ3 = 4;
 constexpr int CX3 = TX3 / 2 + 3, CY3 = TY3 / 2 + 3, CZ3 = TZ3 / 2 + 3;  // coset cells of the tile +- 3
@@ -969,8 +1088,8 @@ __device__ __forceinline__ void lap_sum6(const float *nb, float c, float &hi, fl
 
 template <typename T, bool RR, bool FINEST>
 __global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> rga, const T *rgb, A3<T> vg,
-                                                  double *__restrict__ r64, int rp, double *__restrict__ u, int up,
-                                                  int n, T cg, double ih2, double *part, const int *par,
+                                                  float *__restrict__ rlo, int rp, double *__restrict__ u, int up,
+                                                  int n, T cg, float s2, double *part, const int *par,
                                                   const int *done, Bt B) {
     extern __shared__ __align__(16) unsigned char smraw[];
     Green3Smem<T> &S = *reinterpret_cast<Green3Smem<T> *>(smraw);
@@ -985,7 +1104,7 @@ __global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> 
     rg = bt_at(rg, prob, B);
     rnew = bt_at(rnew, prob, B);
     vg = bt_at(vg, prob, B);
-    if (RR) r64 = bt_ptr(r64, prob, B);
+    if (RR) rlo = bt_ptr(rlo, prob, B);
     if (B.utab) u = B.utab[prob];
     if (RR) part += (size_t)prob * B.nparts;
     const int tid = threadIdx.x + 32 * threadIdx.y;
@@ -1059,11 +1178,11 @@ __global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> 
             lap_sum6(nb, (float)v, hi, lo);
             const size_t cu = ((size_t)z * (n + 2) + y) * up + x, cr = ((size_t)z * (n + 2) + y) * rp + x;
             u[cu] += widen(v);
-            const double rn = fma(-ih2, widen(hi), fma(-ih2, widen(lo), r64[cr]));
-            r64[cr] = rn;
-            const float rf = (float)rn;
-            rnew(x, y, z) = (T)rf;
-            sq = fmaf(rf, rf, sq);
+            float nh, nl;
+            ff_sub((float)S.r[lz][ly][lx], rlo[cr], hi, lo, s2, nh, nl);
+            rlo[cr] = nl;
+            rnew(x, y, z) = (T)nh;
+            sq = fmaf(nh, nh, sq);
         } else if (FINEST) {
             u[((size_t)z * (n + 2) + y) * up + x] += widen(v);
         } else {
@@ -1079,14 +1198,14 @@ __global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> 
 
 // 3D direct residual writing both the FP32 copy and the carried FP64 residual
 __global__ void __launch_bounds__(256) k_res0_64_3d(const double *__restrict__ f, const double *__restrict__ u,
-                                                    int up, int n, double ih2, A3<float> r, double *r64, int rp,
+                                                    int up, int n, double ih2, A3<float> r, float *rlo, int rp,
                                                     double *part, const int *done, Bt B) {
     __shared__ double sh[32];
     const int prob = bt_prob(B), bz = bt_z(B);
     if (stop(bt_done(done, prob, B))) return;
     if (B.ftab) { f = B.ftab[prob]; u = B.utab[prob]; }
     r = bt_at(r, prob, B);
-    r64 = bt_ptr(r64, prob, B);
+    rlo = bt_ptr(rlo, prob, B);
     part += (size_t)prob * B.nparts;
     const int i = blockIdx.x * 32 + threadIdx.x + 1, j = blockIdx.y * 8 + threadIdx.y + 1;
     const int k0 = bz * RES3_PLANES + 1;
@@ -1104,7 +1223,7 @@ __global__ void __launch_bounds__(256) k_res0_64_3d(const double *__restrict__ f
             const double res = fma(-ih2, fma(-6.0, u0, s), fc[0]);
             const float rf = (float)res;
             r(i, j, k0 + q) = rf;
-            r64[(k0 + q) * pr + (size_t)j * rp + i] = res;
+            rlo[(k0 + q) * pr + (size_t)j * rp + i] = (float)(res - (double)rf);
             acc = fmaf(rf, rf, acc);
             ud = u0; u0 = uu;
             uc += pl; fc += pl;

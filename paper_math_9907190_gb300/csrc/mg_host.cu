@@ -89,12 +89,13 @@ struct mg_ctx {
     int kc = 0;                 // first pair run by the coarse thread block
     CoarsePlan2d plan2d{};
     size_t plan_bytes = 0;
-    // mixed 2D: finest pair fused with the next residual (carried FP64 residual
-    // r64 and a second FP32 finest-residual buffer r32b, both in the pool)
+    // mixed path: finest pair (2D) / triple (3D) fused with the next residual,
+    // carried as a float-float pair (hi in the finest level's residual buffers,
+    // double-buffered with r32b; lo in rlo; green pitch, in the pool)
     bool rr = false;
-    void *r64 = nullptr;
+    void *rlo = nullptr;
     void *r32b = nullptr;
-    int r64_pitch = 0;
+    int ff_blocks = 0;          // resident blocks of k_up0_ff_2d (persistent grid)
     // tuned choices (mg_tune): tile class per pair for the down / up kernels
     // (-1: the size rule), side cut-off of the coarse thread block (0: default)
     int tile_dn[32], tile_up[32];
@@ -378,12 +379,12 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
             const size_t sm = sizeof(Green3Smem<T>);
             if (u)
                 LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_3d<T, false, true>), g3, B2, sm, red3v<const T>(b.v, b),
-                              a3<const T>(a.r[0], a), (const T *)nullptr, a3<T>(a.v[0], a), (double *)nullptr, 0, u,
-                              c->d.pitch, n, cc, 0.0, (double *)nullptr, (const int *)nullptr, done);
+                              a3<const T>(a.r[0], a), (const T *)nullptr, a3<T>(a.v[0], a), (float *)nullptr, 0, u,
+                              c->d.pitch, n, cc, 0.f, (double *)nullptr, (const int *)nullptr, done);
             else
                 LAUNCH_SMEM_B(TAG_LEVELS, (k_green_3d<T, false, false>), g3, B2, sm, red3v<const T>(b.v, b),
-                              a3<const T>(a.r[0], a), (const T *)nullptr, a3<T>(a.v[0], a), (double *)nullptr, 0, u,
-                              c->d.pitch, n, cc, 0.0, (double *)nullptr, (const int *)nullptr, done);
+                              a3<const T>(a.r[0], a), (const T *)nullptr, a3<T>(a.v[0], a), (float *)nullptr, 0, u,
+                              c->d.pitch, n, cc, 0.f, (double *)nullptr, (const int *)nullptr, done);
         } else {
             if (c->d.hierarchy == MG_USUAL)
                 LAUNCH_B(TAG_LEVELS, (k_usual_odd_3d<T>), grid3(n, n, n), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
@@ -598,16 +599,30 @@ template <typename T> void vcycle_fast2d(mg_ctx *c, double *u, const int *done, 
     }
 }
 
-template <int TA, int TB> int launch_up0_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
+// strip height (cell rows) of k_up0_ff_2d per tile class
+int ff_strip(int cls) { return cls == 0 ? 32 : cls == 1 ? 16 : 8; }
+
+// the finest pair of the mixed 2D solve (k_up0_ff_2d); returns the partial
+// sums written per problem
+int launch_up0_ff(mg_ctx *c, double *u, int cls, const int *done, cudaStream_t s) {
     const Level &g = c->lv[0], &r = c->lv[1], &b = c->lv[2];
-    const int nb = r.nb;
+    const int nb = r.nb, tb = ff_strip(cls);
     const double hk = c->h, p = c->d.omega[0];
-    dim3 grid((nb + TA) / TA, (nb + TB) / TB, 1);
-    LAUNCH_SMEM_B(TAG_FINEST_UP, (k_up0_rr_2d<TA, TB>), grid, B2, sizeof(UpRRSmem<TA, TB>), a2<const float>(b.v[0], b),
-                  a2<const float>(r.r[0], r), a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b,
-                  (double *)c->r64, c->r64_pitch, u, c->d.pitch, nb, (float)(2.0 * p * hk * hk), (float)(p * hk * hk),
-                  1.0 / (hk * hk), c->part, &c->ctl->par, done);
-    return (int)(grid.x * grid.y);
+    const int items = ((nb + FF_W) / FF_W) * ((nb + tb) / tb);
+    const int per = std::max(1, c->ff_blocks / c->nprob);
+    const dim3 grid(std::min((items + FF_WARPS - 1) / FF_WARPS, per), 1, 1);
+    const dim3 blk(32, FF_WARPS, 1);
+    const bool vu = c->nprob == 1 && ((uintptr_t)u % 16) == 0 && c->d.pitch % 2 == 0;
+    const float c2 = (float)(2.0 * p * hk * hk), c1 = (float)(p * hk * hk), s2 = (float)(1.0 / (hk * hk));
+    if (vu)
+        LAUNCH_B(TAG_FINEST_UP, (k_up0_ff_2d<true>), grid, blk, a2<const float>(b.v[0], b), a2<const float>(r.r[0], r),
+                 a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b, (float *)c->rlo, u, c->d.pitch,
+                 nb, c2, c1, s2, tb, c->part, &c->ctl->par, done);
+    else
+        LAUNCH_B(TAG_FINEST_UP, (k_up0_ff_2d<false>), grid, blk, a2<const float>(b.v[0], b), a2<const float>(r.r[0], r),
+                 a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b, (float *)c->rlo, u, c->d.pitch,
+                 nb, c2, c1, s2, tb, c->part, &c->ctl->par, done);
+    return (int)grid.x;
 }
 
 // one cycle of the fused mixed 2D path: restriction, coarse block, prolongation,
@@ -633,28 +648,24 @@ int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
         default: launch_up_pair<float, 8, 8>(c, k, u, done, s); break;
         }
     }
-    switch (tile_up(c, 0)) {
-    case 0: return launch_up0_rr<32, 16>(c, u, done, s);
-    case 1: return launch_up0_rr<16, 8>(c, u, done, s);
-    default: return launch_up0_rr<8, 8>(c, u, done, s);
-    }
+    return launch_up0_ff(c, u, tile_up(c, 0), done, s);
 }
 
-// direct FP64 residual of the fused path (start of a solve): FP32 copy in the
-// current buffer (parity 0 at the start) and the carried FP64 residual
+// direct FP64 residual of the fused path (start and end of a solve) as the
+// carried float-float pair: hi in the current buffer (parity 0 at the start), lo in rlo
 int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
     const int n = c->d.n;
     const Level &l0 = c->lv[0];
     if (c->d.dim == 3) {
         dim3 g3((n + 31) / 32, (n + 7) / 8, (n + RES3_PLANES - 1) / RES3_PLANES);
         LAUNCH_B(TAG_RESIDUAL, (k_res0_64_3d), g3, B2, f, u, c->d.pitch, n, 1.0 / (c->h * c->h), a3<float>(l0.r[0], l0),
-                 (double *)c->r64, c->r64_pitch, c->part, done);
+                 (float *)c->rlo, l0.pitch, c->part, done);
         c->nparts = (int)(g3.x * g3.y * g3.z);
         return c->nparts;
     }
     dim3 g((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
     LAUNCH_B(TAG_RESIDUAL, (k_res0_64_2d), g, B2, f, u, c->d.pitch, n, 1.0 / (c->h * c->h), a2<float>(l0.r[0], l0),
-             (double *)c->r64, c->r64_pitch, c->part, done);
+             (float *)c->rlo, l0.pitch, c->part, done);
     c->nparts = (int)(g.x * g.y);
     return c->nparts;
 }
@@ -673,7 +684,7 @@ int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     const dim3 g3((n + TX3 - 1) / TX3, (n + TY3 - 1) / TY3, (n + TZ3 - 1) / TZ3);
     LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_3d<float, true, true>), g3, B2, sizeof(Green3Smem<float>),
                   red3v<const float>(b.v, b), a3<const float>(a.r[0], a), (const float *)c->r32b, a3<float>(a.v[0], a),
-                  (double *)c->r64, c->r64_pitch, u, c->d.pitch, n, (float)(c->d.omega[3] * h2), 1.0 / h2, c->part,
+                  (float *)c->rlo, a.pitch, u, c->d.pitch, n, (float)(c->d.omega[3] * h2), (float)(1.0 / h2), c->part,
                   &c->ctl->par, done);
     return (int)(g3.x * g3.y * g3.z);
 }
@@ -691,12 +702,6 @@ template <typename T> cudaError_t set_smem_attrs(const mg_ctx *c) {
     MG_UP_ATTR(16, 8)
     MG_UP_ATTR(8, 8)
 #undef MG_UP_ATTR
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_up0_rr_2d<32, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpRRSmem<32, 16>));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_up0_rr_2d<16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpRRSmem<16, 8>));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_up0_rr_2d<8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(UpRRSmem<8, 8>));
     return e;
 }
 
@@ -816,9 +821,8 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     for (auto &l : c->lv) total += (size_t)l.ncos * 2 * ((l.len * c->esz + 255) / 256 * 256);
     // fused update + residual of the mixed 2D diagonal solve (needs at least one pair outside the coarse block)
     c->rr = d->hierarchy == MG_DIAG && d->precision == MG_MIXED && d->order == 2 && d->n > (d->dim == 2 ? 63 : 15);
-    const size_t r64_bytes = c->rr ? (c->lv[0].len * 8 + 255) / 256 * 256 : 0;
     const size_t r32_bytes = c->rr ? (c->lv[0].len * 4 + 255) / 256 * 256 : 0;
-    total += r64_bytes + r32_bytes;
+    total += 2 * r32_bytes;
     c->nprob = nprob;
     c->pstride = nprob > 1 ? total : 0;
     if (cudaMalloc(&c->pool, total * nprob) != cudaSuccess) { cudaGetLastError(); mg_destroy(c); return MG_ENOMEM; }
@@ -830,9 +834,8 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
         for (int q = 0; q < l.ncos; q++) { l.v[q] = p; p += bytes; }
     }
     if (c->rr) {
-        c->r64 = p; p += r64_bytes;
+        c->rlo = p; p += r32_bytes;
         c->r32b = p; p += r32_bytes;
-        c->r64_pitch = c->lv[0].pitch;
     }
     c->max_blocks = residual_blocks(c);
     plan_fast2d(c);
@@ -855,7 +858,14 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
         }
     }
     if (c->fast2d) {
-        const cudaError_t e = d->precision == MG_FP64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c);
+        cudaError_t e = d->precision == MG_FP64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c);
+        if (e == cudaSuccess && c->rr && d->dim == 2) {
+            // persistent grid of the finest pair: every block resident at once
+            int per_sm = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_up0_ff_2d<false>, 32 * FF_WARPS, 0);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+            c->ff_blocks = std::max(1, per_sm * sms);
+        }
         if (e != cudaSuccess) {
             mg_destroy(c);
             return cuda_fail(e, "mg_create shared-memory attributes");
@@ -1558,16 +1568,7 @@ mg_status tune_measure(mg_ctx *c, const double *f, double *u, cudaStream_t s) {
                 if (md < bd) { bd = md; c->tile_dn[k] = cls; }
                 float mu;
                 if (k == 0 && c->rr) {
-                    const int keep = c->tile_up[0];
-                    c->tile_up[0] = cls;
-                    mu = timeit([&] {
-                        switch (cls) {
-                        case 0: launch_up0_rr<32, 16>(c, u, nullptr, s); break;
-                        case 1: launch_up0_rr<16, 8>(c, u, nullptr, s); break;
-                        default: launch_up0_rr<8, 8>(c, u, nullptr, s); break;
-                        }
-                    }, 5);
-                    c->tile_up[0] = keep;
+                    mu = timeit([&] { launch_up0_ff(c, u, cls, nullptr, s); }, 5);
                 } else {
                     mu = fp64 ? timeit([&] { up_pair<double>(c, k, cls, k == 0 ? u : nullptr, nullptr, s); }, 5)
                               : timeit([&] { up_pair<float>(c, k, cls, k == 0 ? u : nullptr, nullptr, s); }, 5);
