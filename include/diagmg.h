@@ -219,7 +219,9 @@ mg_status mg_batch_launch_count(const mg_batch *batch, long long *launches);
  * left zero (interior and ring).  measured_out (host, nullable): 1 if timed,
  * 0 if taken from the cache or nothing is tunable.  Synchronous.
  * mg_tune_info reports the cut-off (0 = default) and the tile class of each
- * pair kernel outside the thread block (0: 32x16 cells, 1: 16x8, 2: 8x8);
+ * pair kernel outside the thread block (FP64 levels: tiles of 0: 32x16 cells,
+ * 1: 16x8, 2: 8x8; FP32 levels: strips of 0: 32, 1: 16, 2: 8 cell rows for
+ * the prolongation and 16, 8, 4 for the restriction);
  * tiles_down / tiles_up need 32 entries.  mg_batch_tune does the same for
  * every size group of a batch (f, u as in mg_solve_batched). */
 mg_status mg_tune(mg_ctx *ctx, const double *f, double *u, const char *cache_path, int *measured_out,
@@ -233,7 +235,8 @@ mg_status mg_batch_tune(mg_batch *batch, const double *const *f, double *const *
  * every later launch of that kernel family is bracketed with CUDA events on
  * its stream (family 0: finest-grid residual / down pass, 1: finest-grid
  * prolongation and update, 2: all other level stages, 3: control kernels;
- * -1 turns the probe off).  mg_probe_read synchronises `stream` and returns
+ * 4, 5, 6: the parts of family 2 -- restriction, prolongation of the coarser
+ * levels, the coarse thread block; -1 turns the probe off).  mg_probe_read synchronises `stream` and returns
  * the probed launches and their summed device time in ms since the last
  * mg_probe_set.  Event objects are created by the first mg_probe_set. */
 mg_status mg_launch_count(const mg_ctx *ctx, long long *launches);

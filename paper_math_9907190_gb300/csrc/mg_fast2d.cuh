@@ -27,7 +27,7 @@ namespace mg {
 template <typename T> struct SqAcc;                     // per-thread sum of r^2
 template <> struct SqAcc<float> {                       // mixed: FP32 squares
     float s = 0.f;
-    __device__ void add(double r) { const float q = (float)r; s = fmaf(q, q, s); }
+    __device__ void add(double r) { const float q = narrow(r); s = fmaf(q, q, s); }
     __device__ double get() const { return (double)s; }
 };
 template <> struct SqAcc<double> {
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_res0_2d(const double *__restrict__ f, c
                 res = fma(-ih2 * (1.0 / 6.0), fma(-20.0, u0, fma(4.0, ax, dg)), fc[0]);
                 wm = w0; em = e0; w0 = wp; e0 = ep;
             }
-            r(i, j0 + q) = (T)res;
+            r(i, j0 + q) = lvl<T>(res);
             acc.add(res);
             um = u0; u0 = upn;
             uc += up; fc += up;
@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(256) k_res0_3d(const double *__restrict__ f, c
                                   ((uc[-(long)pl - 1] + uc[-(long)pl + 1]) + (uc[pl - 1] + uc[pl + 1]));
                 res = fma(-ih2 * (1.0 / 6.0), fma(-24.0, u0, fma(2.0, ax, ed)), fc[0]);
             }
-            r(i, j, k0 + q) = (T)res;
+            r(i, j, k0 + q) = lvl<T>(res);
             acc.add(res);
             ud = u0; u0 = uu;
             uc += pl; fc += pl;
@@ -683,31 +683,70 @@ constexpr int FF_WARPS = 4;
 // re-relaxed red points EE of row b+1 and OO of row b (the red-to-green sweep
 // of Section 2.2, c1 = p h^2); then apply v to the four points of every own
 // cell of row b.  Values outside the interior are zero, as in the oracle.
-// VU: u is 16-byte aligned with an even pitch (vector access to u).
-template <bool VU>
-__global__ void __launch_bounds__(32 * FF_WARPS) k_up0_ff_2d(A2<const float> blue, A2<const float> ree,
-                                                             A2<const float> roo, A2<float> rga, float *rgb,
-                                                             float *__restrict__ rlo, double *__restrict__ u, int up,
-                                                             int nb, float c2, float c1, float s2, int tb,
-                                                             double *part, const int *par, const int *done, Bt B) {
+// MODE: UP_RR the mixed finest pair (u += v and the carried residual, rga/rgb
+// double-buffered by par); UP_ADD u += v; UP_STORE v stored in vg (a coarser
+// pair).  VU: u is 16-byte aligned with an even pitch (vector access to u).
+enum { UP_RR = 0, UP_ADD = 1, UP_STORE = 2 };
+
+// Asynchronous global -> shared copies (cp.async), used to keep one step of
+// every warp's inputs in flight while it computes the current step.  Each
+// lane copies and later reads only its own slots, so a lane's own
+// wait_group orders them; src_bytes 0 fills the slot with zeros (the address
+// is then not read and must only be a valid pointer).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool ok) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// one step's inputs of one warp in shared memory (slot = lane): the chain's
+// blue row b+3, red OO / EE rows b+2 and green residual rows 2b+2, 2b+3 over
+// the lane's two cells; u of the own cells' green rows 2b, 2b+1 (two FP64
+// pairs per row) and the residual's lo part of those rows
+struct FFChain {
+    float4 g2[32], g3[32];
+    float2 bl[32], ro[32], re[32];
+};
+struct FFU {
+    double2 u[2][2][32];
+};
+struct FFL {
+    float4 l[2][32];
+};
+
+template <int MODE, bool VU>
+__global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue, A2<const float> ree,
+                                                            A2<const float> roo, A2<float> rga, float *rgb, A2<float> vg,
+                                                            float *__restrict__ rlo, double *__restrict__ u, int up,
+                                                            int nb, float c2, float c1, float s2, int tb,
+                                                            double *part, const int *par, const int *done, Bt B) {
     __shared__ double sh[32];
+    __shared__ FFChain SC[FF_WARPS][2];
+    __shared__ FFU SU[MODE != UP_STORE ? FF_WARPS : 1][2];
+    __shared__ FFL SL[MODE == UP_RR ? FF_WARPS : 1][2];
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int K = FF_K;
+    constexpr bool RR = MODE == UP_RR, UPD = MODE != UP_STORE;
     const int prob = blockIdx.z;
     if (stop(bt_done(done, prob, B))) return;
-    const bool p1 = par[(size_t)prob * B.ctl_stride] != 0;
     A2<float> rg = rga, rnew = rga;
-    (p1 ? rg : rnew).p = rgb;
+    if (RR) (par[(size_t)prob * B.ctl_stride] != 0 ? rg : rnew).p = rgb;
     blue = bt_at(blue, prob, B); ree = bt_at(ree, prob, B); roo = bt_at(roo, prob, B);
-    rg = bt_at(rg, prob, B); rnew = bt_at(rnew, prob, B);
-    rlo = bt_ptr(rlo, prob, B);
-    if (B.utab) u = B.utab[prob];
-    part += (size_t)prob * B.nparts;
-    const int lane = threadIdx.x;
+    rg = bt_at(rg, prob, B); rnew = bt_at(rnew, prob, B); vg = bt_at(vg, prob, B);
+    if (RR) rlo = bt_ptr(rlo, prob, B);
+    if (UPD && B.utab) u = B.utab[prob];
+    if (RR) part += (size_t)prob * B.nparts;
+    const int lane = threadIdx.x, w = threadIdx.y;
     const int n = 2 * nb + 1, gp = rga.pitch;
     const int ncol = (nb + FF_W) / FF_W, nstrip = (nb + tb) / tb;
     float sq = 0.f;
-    for (int it = blockIdx.x * FF_WARPS + threadIdx.y; it < ncol * nstrip; it += gridDim.x * FF_WARPS) {
+    for (int it = blockIdx.x * FF_WARPS + w; it < ncol * nstrip; it += gridDim.x * FF_WARPS) {
         const int col = it % ncol, strip = it / ncol;
         const int A = col * FF_W - 2, a0 = A + K * lane;
         // nb is odd and a0 even: the lane's K cells are all in [0, nb] or all outside
@@ -717,6 +756,40 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up0_ff_2d(A2<const float> blu
 #pragma unroll
         for (int k = 0; k < K; k++) pos[k] = in && a0 + k >= 1;
         const int b0 = strip * tb, b1 = min(b0 + tb, nb + 1), bs = max(b0 - 4, -2);
+        const int ac = in ? a0 : 0;  // a valid column for the addresses of zero-filled copies
+        // stage the inputs of step bb into buffer st
+        auto issue = [&](int st, int bb) {
+            FFChain &C = SC[w][st];
+            cp_async8(&C.bl[lane], &blue(ac, in && bb + 3 <= nb + 1 ? bb + 3 : 0), in && bb + 3 <= nb + 1);
+            const bool r2 = in && bb + 2 >= 0 && bb + 2 <= nb;
+            cp_async8(&C.ro[lane], &roo(ac, r2 ? bb + 2 : 0), r2);
+            cp_async8(&C.re[lane], &ree(ac, r2 ? bb + 2 : 0), r2);
+            const bool y2 = in && 2 * bb + 2 >= 1 && 2 * bb + 2 <= n, y3 = in && 2 * bb + 3 >= 1 && 2 * bb + 3 <= n;
+            cp_async16(&C.g2[lane], &rg(2 * ac, y2 ? 2 * bb + 2 : 0), y2);
+            cp_async16(&C.g3[lane], &rg(2 * ac, y3 ? 2 * bb + 3 : 0), y3);
+            if (UPD && own && bb >= b0) {
+                const bool row0 = bb >= 1;
+#pragma unroll
+                for (int r = 0; r < 2; r++) {
+                    const int y = 2 * bb + r;
+                    const bool ok = r == 1 || row0;
+                    const double *src = u + (size_t)(ok ? y : 1) * up + 2 * a0;
+                    if (VU) {
+                        cp_async16(&SU[w][st].u[r][0][lane], src, ok);
+                        cp_async16(&SU[w][st].u[r][1][lane], src + 2, ok);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 2 * K; q++) {
+                            const bool px = ok && ((q & 1) || pos[q >> 1]);
+                            double *d = q < 2 ? &SU[w][st].u[r][0][lane].x : &SU[w][st].u[r][1][lane].x;
+                            cp_async8(d + (q & 1), src + q, px);
+                        }
+                    }
+                    if (RR) cp_async16(&SL[w][st].l[r][lane], rlo + (size_t)(ok ? y : 1) * gp + 2 * a0, ok);
+                }
+            }
+            cp_async_commit();
+        };
         // chain state, rows relative to the step's b
         float bl2[K], oo0[K], oo1[K], ee1[K], oe0[K], eom[K], eo0[K], ce0[K], com[K], r0[2 * K], r1[2 * K];
 #pragma unroll
@@ -728,63 +801,26 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up0_ff_2d(A2<const float> blu
             const float2 q = *reinterpret_cast<const float2 *>(&blue(a0, bs + 2));
             bl2[0] = q.x; bl2[1] = q.y;
         }
+        issue(0, bs);
         for (int b = bs; b < b1; b++) {
+            const int st = (b - bs) & 1;
+            if (b + 1 < b1) issue(st ^ 1, b + 1);
+            else cp_async_commit();
+            cp_async_wait1();  // this lane's copies of step b have landed
             float bl3[K], ro2[K], re2[K], g2[2 * K], g3[2 * K];
-#pragma unroll
-            for (int k = 0; k < K; k++) bl3[k] = ro2[k] = re2[k] = g2[2 * k] = g2[2 * k + 1] = g3[2 * k] = g3[2 * k + 1] = 0.f;
-            if (in) {
-                if (b + 3 <= nb + 1) {
-                    const float2 q = *reinterpret_cast<const float2 *>(&blue(a0, b + 3));
-                    bl3[0] = q.x; bl3[1] = q.y;
-                }
-                if (b + 2 >= 0 && b + 2 <= nb) {
-                    const float2 q = *reinterpret_cast<const float2 *>(&roo(a0, b + 2));
-                    const float2 w = *reinterpret_cast<const float2 *>(&ree(a0, b + 2));
-                    ro2[0] = q.x; ro2[1] = q.y; re2[0] = w.x; re2[1] = w.y;
-                }
-                if (2 * b + 2 >= 1 && 2 * b + 2 <= n) {
-                    const float4 q = *reinterpret_cast<const float4 *>(&rg(2 * a0, 2 * b + 2));
-                    g2[0] = q.x; g2[1] = q.y; g2[2] = q.z; g2[3] = q.w;
-                }
-                if (2 * b + 3 >= 1 && 2 * b + 3 <= n) {
-                    const float4 q = *reinterpret_cast<const float4 *>(&rg(2 * a0, 2 * b + 3));
-                    g3[0] = q.x; g3[1] = q.y; g3[2] = q.z; g3[3] = q.w;
-                }
+            {
+                const FFChain &C = SC[w][st];
+                const float2 x = C.bl[lane], y = C.ro[lane], z = C.re[lane];
+                const float4 p = C.g2[lane], q = C.g3[lane];
+                bl3[0] = x.x; bl3[1] = x.y; ro2[0] = y.x; ro2[1] = y.y; re2[0] = z.x; re2[1] = z.y;
+                g2[0] = p.x; g2[1] = p.y; g2[2] = p.z; g2[3] = p.w;
+                g3[0] = q.x; g3[1] = q.y; g3[2] = q.z; g3[3] = q.w;
             }
-            // the own cells' u and lo of cell row b (rows 2b, 2b+1), issued before the chain
             const bool upd = own && b >= b0;
             const bool row0 = b >= 1;  // green row 2b is interior
-            double u0[2 * K], u1[2 * K];
-            float l0[2 * K], l1[2 * K];
-#pragma unroll
-            for (int q = 0; q < 2 * K; q++) { u0[q] = u1[q] = 0.0; l0[q] = l1[q] = 0.f; }
-            double *ur0 = u + (size_t)(2 * b) * up + 2 * a0, *ur1 = ur0 + up;
-            float *lr0 = rlo + (size_t)(2 * b) * gp + 2 * a0, *lr1 = lr0 + gp;
-            if (upd) {
-                if (row0) {
-                    const float4 q = *reinterpret_cast<const float4 *>(lr0);
-                    l0[0] = q.x; l0[1] = q.y; l0[2] = q.z; l0[3] = q.w;
-                }
-                {
-                    const float4 q = *reinterpret_cast<const float4 *>(lr1);
-                    l1[0] = q.x; l1[1] = q.y; l1[2] = q.z; l1[3] = q.w;
-                }
-                if (VU) {
-                    if (row0) {
-                        const double2 p = reinterpret_cast<const double2 *>(ur0)[0], q = reinterpret_cast<const double2 *>(ur0)[1];
-                        u0[0] = p.x; u0[1] = p.y; u0[2] = q.x; u0[3] = q.y;
-                    }
-                    const double2 p = reinterpret_cast<const double2 *>(ur1)[0], q = reinterpret_cast<const double2 *>(ur1)[1];
-                    u1[0] = p.x; u1[1] = p.y; u1[2] = q.x; u1[3] = q.y;
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 2 * K; q++) {
-                        const bool px = (q & 1) || pos[q >> 1];  // green x = 2a0+q is interior
-                        if (row0 && px) u0[q] = ur0[q];
-                        if (px) u1[q] = ur1[q];
-                    }
-                }
-            }
+            const int yo = upd ? 2 * b : 0, xo = upd ? 2 * a0 : 0;  // pointers formed for own cells only
+            double *ur0 = UPD ? u + (size_t)yo * up + xo : nullptr, *ur1 = UPD ? ur0 + up : nullptr;
+            float *lr0 = RR ? rlo + (size_t)yo * gp + xo : nullptr, *lr1 = RR ? lr0 + gp : nullptr;
             // ---- the chain
             const bool y_oo2 = b + 2 >= 0 && b + 2 <= nb, y_ee2 = b + 2 >= 1 && b + 2 <= nb;
             const bool y_oe1 = b + 1 >= 1 && b + 1 <= nb, y_eo1 = b + 1 >= 0 && b + 1 <= nb;
@@ -823,7 +859,25 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up0_ff_2d(A2<const float> blu
             // ---- apply v to the own cells of row b
             const float oe0L = __shfl_up_sync(FULL, oe0[K - 1], 1), ce0R = __shfl_down_sync(FULL, ce0[0], 1);
             const float co0L = __shfl_up_sync(FULL, co0[K - 1], 1);
-            if (upd) {
+            if (!UPD && upd) {
+                float *v0 = &vg(xo, yo), *v1 = v0 + vg.pitch;
+                if (row0) *reinterpret_cast<float4 *>(v0) = make_float4(ce0[0], oe0[0], ce0[1], oe0[1]);
+                *reinterpret_cast<float4 *>(v1) = make_float4(eo0[0], co0[0], eo0[1], co0[1]);
+            }
+            if (UPD && upd) {
+                double u0[2 * K], u1[2 * K];
+                float l0[2 * K], l1[2 * K];
+                {
+                    const double2 a = SU[w][st].u[0][0][lane], bq = SU[w][st].u[0][1][lane];
+                    const double2 c = SU[w][st].u[1][0][lane], d = SU[w][st].u[1][1][lane];
+                    u0[0] = a.x; u0[1] = a.y; u0[2] = bq.x; u0[3] = bq.y;
+                    u1[0] = c.x; u1[1] = c.y; u1[2] = d.x; u1[3] = d.y;
+                }
+                if (RR) {
+                    const float4 a = SL[w][st].l[0][lane], c = SL[w][st].l[1][lane];
+                    l0[0] = a.x; l0[1] = a.y; l0[2] = a.z; l0[3] = a.w;
+                    l1[0] = c.x; l1[1] = c.y; l1[2] = c.z; l1[3] = c.w;
+                }
                 float h0[2 * K], h1[2 * K];
 #pragma unroll
                 for (int k = 0; k < K; k++) {
@@ -833,42 +887,52 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up0_ff_2d(A2<const float> blu
                     // EE (2a, 2b)
                     nh = nl = 0.f;
                     if (pos[k] && row0) {
-                        lap_sum(oel, oe0[k], eom[k], eo0[k], ce0[k], lh, ll);
-                        ff_sub(r0[2 * k], l0[2 * k], lh, ll, s2, nh, nl);
+                        if (RR) {
+                            lap_sum(oel, oe0[k], eom[k], eo0[k], ce0[k], lh, ll);
+                            ff_sub(r0[2 * k], l0[2 * k], lh, ll, s2, nh, nl);
+                        }
                         u0[2 * k] += widen(ce0[k]);
                     }
                     h0[2 * k] = nh; l0[2 * k] = nl;
                     // OE (2a+1, 2b)
                     nh = nl = 0.f;
                     if (row0) {
-                        lap_sum(ce0[k], cer, com[k], co0[k], oe0[k], lh, ll);
-                        ff_sub(r0[2 * k + 1], l0[2 * k + 1], lh, ll, s2, nh, nl);
+                        if (RR) {
+                            lap_sum(ce0[k], cer, com[k], co0[k], oe0[k], lh, ll);
+                            ff_sub(r0[2 * k + 1], l0[2 * k + 1], lh, ll, s2, nh, nl);
+                        }
                         u0[2 * k + 1] += widen(oe0[k]);
                     }
                     h0[2 * k + 1] = nh; l0[2 * k + 1] = nl;
                     // EO (2a, 2b+1)
                     nh = nl = 0.f;
                     if (pos[k]) {
-                        lap_sum(col_, co0[k], ce0[k], ce1[k], eo0[k], lh, ll);
-                        ff_sub(r1[2 * k], l1[2 * k], lh, ll, s2, nh, nl);
+                        if (RR) {
+                            lap_sum(col_, co0[k], ce0[k], ce1[k], eo0[k], lh, ll);
+                            ff_sub(r1[2 * k], l1[2 * k], lh, ll, s2, nh, nl);
+                        }
                         u1[2 * k] += widen(eo0[k]);
                     }
                     h1[2 * k] = nh; l1[2 * k] = nl;
                     // OO (2a+1, 2b+1)
-                    lap_sum(eo0[k], eor, oe0[k], oe1[k], co0[k], lh, ll);
-                    ff_sub(r1[2 * k + 1], l1[2 * k + 1], lh, ll, s2, nh, nl);
+                    if (RR) {
+                        lap_sum(eo0[k], eor, oe0[k], oe1[k], co0[k], lh, ll);
+                        ff_sub(r1[2 * k + 1], l1[2 * k + 1], lh, ll, s2, nh, nl);
+                    }
                     u1[2 * k + 1] += widen(co0[k]);
                     h1[2 * k + 1] = nh; l1[2 * k + 1] = nl;
                 }
+                if (RR) {
 #pragma unroll
-                for (int q = 0; q < 2 * K; q++) sq = fmaf(h0[q], h0[q], fmaf(h1[q], h1[q], sq));
-                float *hr0 = &rnew(2 * a0, 2 * b), *hr1 = hr0 + gp;
-                if (row0) {
-                    *reinterpret_cast<float4 *>(hr0) = make_float4(h0[0], h0[1], h0[2], h0[3]);
-                    *reinterpret_cast<float4 *>(lr0) = make_float4(l0[0], l0[1], l0[2], l0[3]);
+                    for (int q = 0; q < 2 * K; q++) sq = fmaf(h0[q], h0[q], fmaf(h1[q], h1[q], sq));
+                    float *hr0 = &rnew(xo, yo), *hr1 = hr0 + gp;
+                    if (row0) {
+                        *reinterpret_cast<float4 *>(hr0) = make_float4(h0[0], h0[1], h0[2], h0[3]);
+                        *reinterpret_cast<float4 *>(lr0) = make_float4(l0[0], l0[1], l0[2], l0[3]);
+                    }
+                    *reinterpret_cast<float4 *>(hr1) = make_float4(h1[0], h1[1], h1[2], h1[3]);
+                    *reinterpret_cast<float4 *>(lr1) = make_float4(l1[0], l1[1], l1[2], l1[3]);
                 }
-                *reinterpret_cast<float4 *>(hr1) = make_float4(h1[0], h1[1], h1[2], h1[3]);
-                *reinterpret_cast<float4 *>(lr1) = make_float4(l1[0], l1[1], l1[2], l1[3]);
                 if (VU) {
                     if (row0) {
                         reinterpret_cast<double2 *>(ur0)[0] = make_double2(u0[0], u0[1]);
@@ -894,9 +958,76 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up0_ff_2d(A2<const float> blu
                 r1[2 * k] = g3[2 * k]; r1[2 * k + 1] = g3[2 * k + 1];
             }
         }
+        cp_async_wait0();
     }
-    const double s = block_sum((double)sq, sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x] = s;
+    if (RR) {
+        const double s = block_sum((double)sq, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pair restriction green -> red -> blue (Eq. Erest2r, then Eq. Erest2b) as a
+// warp-streaming kernel over FP32 levels, with the decomposition of
+// k_up_ff_2d: a warp owns 64 cell columns (2 per lane) and walks a strip of
+// cell rows; the green rows 2b-1..2b+2 of step b are held in registers (two
+// loaded per step), x neighbours come by shuffle.  Red OO of cell row b
+// needs the green neighbours at +-1, red EE the same, blue(a,b) the OO
+// values of cells a-1..a of rows b-1..b, so a warp writes its middle FD_W
+// cells and a strip starts one row early.  galt/par: the finest green
+// residual of the mixed solve is double-buffered (Ctrl.par picks the current).
+// ---------------------------------------------------------------------------
+constexpr int FD_W = 60;
+
+__global__ void __launch_bounds__(32 * FF_WARPS) k_down_ff_2d(A2<const float> g, A2<float> ee, A2<float> oo,
+                                                              A2<float> blue, int nb, int tb, const float *galt,
+                                                              const int *par, const int *done, Bt B) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int prob = blockIdx.z;
+    if (stop(bt_done(done, prob, B))) return;
+    if (galt && par[(size_t)prob * B.ctl_stride]) g.p = galt;
+    g = bt_at(g, prob, B); ee = bt_at(ee, prob, B); oo = bt_at(oo, prob, B); blue = bt_at(blue, prob, B);
+    const int lane = threadIdx.x;
+    const int n = 2 * nb + 1;
+    const int ncol = (nb + FD_W) / FD_W, nstrip = (nb + tb) / tb;
+    for (int it = blockIdx.x * FF_WARPS + threadIdx.y; it < ncol * nstrip; it += gridDim.x * FF_WARPS) {
+        const int col = it % ncol, strip = it / ncol;
+        const int A = col * FD_W - 2, a0 = A + 2 * lane;
+        const bool in = a0 >= 0 && a0 <= nb;  // nb odd, a0 even: both cells in [0, nb] or neither
+        const bool own = in && a0 >= A + 2 && a0 < A + 2 + FD_W;
+        const bool pos0 = a0 >= 1;            // cell a0 has EE / blue points (a >= 1)
+        const int b0 = strip * tb, b1 = min(b0 + tb, nb + 1), bs = max(b0 - 1, 0);
+        auto row = [&](int y) -> float4 {
+            if (in && y >= 0 && y <= n + 1) return *reinterpret_cast<const float4 *>(&g(2 * a0, y));
+            return make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        // green rows 2b-1 .. 2b+2 of step b; the next step's two rows are
+        // loaded one step ahead
+        float4 gm = row(2 * bs - 1), g0 = row(2 * bs), g1 = row(2 * bs + 1), g2 = row(2 * bs + 2);
+        float om0 = 0.f, om1 = 0.f;  // OO(a0, b-1), OO(a0+1, b-1)
+        for (int b = bs; b < b1; b++) {
+            const float4 n1 = row(2 * b + 3), n2 = row(2 * b + 4);
+            const float g0L = __shfl_up_sync(FULL, g0.w, 1), g1R = __shfl_down_sync(FULL, g1.x, 1);
+            // red EE of cells a0, a0+1 at green (2a, 2b); OO at (2a+1, 2b+1)
+            const bool yb = b >= 1;
+            const float e0 = (pos0 && yb) ? (4.f * g0.x + (g0L + g0.y) + (gm.x + g1.x)) * 0.125f : 0.f;
+            const float e1 = (in && yb) ? (4.f * g0.z + (g0.y + g0.w) + (gm.z + g1.z)) * 0.125f : 0.f;
+            const float o0 = in ? (4.f * g1.y + (g1.x + g1.z) + (g0.y + g2.y)) * 0.125f : 0.f;
+            const float o1 = in ? (4.f * g1.w + (g1.z + g1R) + (g0.w + g2.w)) * 0.125f : 0.f;
+            // OO(a0-1, b-1) and OO(a0-1, b) from the left lane
+            const float omL = __shfl_up_sync(FULL, om1, 1), o0L = __shfl_up_sync(FULL, o1, 1);
+            const float bl0 = (pos0 && yb) ? (4.f * e0 + (omL + om0) + (o0L + o0)) * 0.125f : 0.f;
+            const float bl1 = (in && yb) ? (4.f * e1 + (om0 + om1) + (o0 + o1)) * 0.125f : 0.f;
+            if (own && b >= b0) {
+                *reinterpret_cast<float2 *>(&oo(a0, b)) = make_float2(o0, o1);
+                if (yb) {
+                    *reinterpret_cast<float2 *>(&ee(a0, b)) = make_float2(e0, e1);
+                    *reinterpret_cast<float2 *>(&blue(a0, b)) = make_float2(bl0, bl1);
+                }
+            }
+            gm = g1; g0 = g2; g1 = n1; g2 = n2; om0 = o0; om1 = o1;
+        }
+    }
 }
 
 // sum of f^2 over the interior (the norm of the right-hand side of an order-2
@@ -916,7 +1047,7 @@ __global__ void __launch_bounds__(256) k_norm_f(const double *__restrict__ f, in
         const int j0 = (blockIdx.y * 8 + threadIdx.y) * RES_ROWS + 1;
         if (i <= n)
             for (int q = 0; q < RES_ROWS && j0 + q <= n; q++) {
-                const float v = (float)f[(size_t)(j0 + q) * up + i];
+                const float v = narrow(f[(size_t)(j0 + q) * up + i]);
                 acc = fmaf(v, v, acc);
             }
     } else {
@@ -924,7 +1055,7 @@ __global__ void __launch_bounds__(256) k_norm_f(const double *__restrict__ f, in
         const size_t pl = (size_t)up * (n + 2);
         if (i <= n && j <= n)
             for (int q = 0; q < RES3_PLANES && k0 + q <= n; q++) {
-                const float v = (float)f[(k0 + q) * pl + (size_t)j * up + i];
+                const float v = narrow(f[(k0 + q) * pl + (size_t)j * up + i]);
                 acc = fmaf(v, v, acc);
             }
     }
@@ -933,42 +1064,97 @@ __global__ void __launch_bounds__(256) k_norm_f(const double *__restrict__ f, in
         part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz)] = s;
 }
 
-// finest residual as the float-float pair of the fused update: hi = the FP32
-// rounding of the FP64 residual (the level's residual), lo = the FP32 rounding
-// of the remainder (array rlo, pitch rp); otherwise as k_res0_2d
-__global__ void __launch_bounds__(256) k_res0_64_2d(const double *__restrict__ f, const double *__restrict__ u,
-                                                    int up, int n, double ih2, A2<float> r, float *rlo, int rp,
-                                                    double *part, const int *done, Bt B) {
+// (hi, lo) = the FP32 rounding of x and the FP32 rounding of the remainder
+// x - hi, with no FP64-pipe instruction: the remainder is a whole number D of ulps of
+// x (|D| <= 2^28; the difference of the two bit patterns, both in x's binade or
+// hi at its upper end), converted to FP32 and scaled by that ulp, a power of
+// two.  Below |x| ~ 2^-74 lo is 0.
+__device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
+    hi = narrow(x);
+    const long long X = __double_as_longlong(x), H = __double_as_longlong(widen(hi));
+    const int fe = (int)((X >> 52) & 0x7ff) - 948;  // FP32 biased exponent of 2^(e - 1075), x's ulp
+    const float l = fe > 0 ? i2f_rn((int)(X - H)) * __int_as_float(fe << 23) : 0.f;
+    lo = X < 0 ? -l : l;
+}
+
+__device__ __forceinline__ unsigned long long bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// Direct FP64 residual r = f - L u (Eq. Evpois) of the fused mixed path.
+// START (start of a solve): r as the float-float pair hi (the level's buffer
+// r) and lo (rlo, pitch rp), partial sums of hi^2 to part and of f^2 (FP32
+// squares: the norm of the right-hand side) to fpart.  Where u and its four
+// neighbours are all zero r = f, and a warp whose points all are skips the
+// FP64 arithmetic (a solve from u = 0 then moves bytes only).  Otherwise (end
+// of a solve): only the partial sums of r^2, nothing written.
+template <bool START>
+__global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f, const double *__restrict__ u,
+                                                   int up, int n, double ih2, A2<float> r, float *rlo, int rp,
+                                                   double *part, double *fpart, const int *done, Bt B) {
     __shared__ double sh[32];
     const int prob = blockIdx.z;
     if (stop(bt_done(done, prob, B))) return;
     if (B.ftab) { f = B.ftab[prob]; u = B.utab[prob]; }
-    r = bt_at(r, prob, B);
-    rlo = bt_ptr(rlo, prob, B);
+    if (START) { r = bt_at(r, prob, B); rlo = bt_ptr(rlo, prob, B); }
     const int i = blockIdx.x * 32 + threadIdx.x + 1;
     const int j0 = (blockIdx.y * 8 + threadIdx.y) * RES_ROWS + 1;
-    float acc = 0.f;
+    float acc = 0.f, facc = 0.f;
     if (i <= n && j0 <= n) {
-        const double *uc = u + (size_t)j0 * up + i;
-        const double *fc = f + (size_t)j0 * up + i;
-        double um = uc[-up], u0 = uc[0];
-#pragma unroll
-        for (int q = 0; q < RES_ROWS; q++) {
-            if (j0 + q > n) break;
-            const double upn = uc[up];
-            const double s = (uc[-1] + uc[1]) + (um + upn);
-            const double res = fma(-ih2, fma(-4.0, u0, s), fc[0]);
-            const float rf = (float)res;
-            r(i, j0 + q) = rf;
-            rlo[(size_t)(j0 + q) * rp + i] = (float)(res - (double)rf);
-            acc = fmaf(rf, rf, acc);
-            um = u0; u0 = upn;
-            uc += up; fc += up;
+        const double *u0p = u + (size_t)j0 * up + i;
+        const double *f0p = f + (size_t)j0 * up + i;
+        const int rows = min(RES_ROWS, n + 1 - j0);
+        bool zero = false;
+        if (START) {  // u and its neighbours zero at every point of the thread?
+            unsigned long long ob = bits(u0p[-up]) | bits(u0p[(size_t)rows * up]);
+            for (int q = 0; q < rows; q++) {
+                const double *c = u0p + (size_t)q * up;
+                ob |= bits(c[-1]) | bits(c[0]) | bits(c[1]);
+            }
+            zero = (ob << 1) == 0;
         }
+        // warp-uniform: either no FP64 arithmetic at all (two separate loops,
+        // so that the stencil is branched over rather than predicated) or the
+        // full stencil
+        auto rows_loop = [&](auto zero_tag) {
+            constexpr bool Z = decltype(zero_tag)::value;
+            const double *uc = u0p, *fc = f0p;
+            double um = Z ? 0.0 : uc[-up], u0 = Z ? 0.0 : uc[0];
+#pragma unroll
+            for (int q = 0; q < RES_ROWS; q++) {
+                if (q >= rows) break;
+                const double fv = fc[0];
+                double res = fv, upn = 0.0;
+                if (!Z) {
+                    upn = uc[up];
+                    const double s = (uc[-1] + uc[1]) + (um + upn);
+                    res = fma(-ih2, fma(-4.0, u0, s), fv);
+                }
+                float hi;
+                if (START) {
+                    float lo;
+                    split_f64(res, hi, lo);
+                    r(i, j0 + q) = hi;
+                    rlo[(size_t)(j0 + q) * rp + i] = lo;
+                    const float ff = Z ? hi : narrow(fv);
+                    facc = fmaf(ff, ff, facc);
+                } else {
+                    hi = narrow(res);
+                }
+                acc = fmaf(hi, hi, acc);
+                um = u0; u0 = upn;
+                uc += up; fc += up;
+            }
+        };
+        if (__all_sync(__activemask(), zero)) rows_loop(std::true_type{});
+        else rows_loop(std::false_type{});
     }
-    double s = block_sum((double)acc, sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        part[(size_t)prob * B.nparts + blockIdx.x + gridDim.x * blockIdx.y] = s;
+    const size_t slot = (size_t)prob * B.nparts + blockIdx.x + gridDim.x * blockIdx.y;
+    const double s = block_sum((double)acc, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[slot] = s;
+    if (START) {
+        __syncthreads();
+        const double sf = block_sum((double)facc, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0) fpart[slot] = sf;
+    }
 }
 
 }  // namespace mg
@@ -1196,42 +1382,75 @@ __global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> 
     }
 }
 
-// 3D direct residual writing both the FP32 copy and the carried FP64 residual
-__global__ void __launch_bounds__(256) k_res0_64_3d(const double *__restrict__ f, const double *__restrict__ u,
-                                                    int up, int n, double ih2, A3<float> r, float *rlo, int rp,
-                                                    double *part, const int *done, Bt B) {
+// 3D direct residual of the fused mixed path (7-point), as k_res_rr_2d:
+// RES3_PLANES planes per thread marching in z
+template <bool START>
+__global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f, const double *__restrict__ u,
+                                                   int up, int n, double ih2, A3<float> r, float *rlo, int rp,
+                                                   double *part, double *fpart, const int *done, Bt B) {
     __shared__ double sh[32];
     const int prob = bt_prob(B), bz = bt_z(B);
     if (stop(bt_done(done, prob, B))) return;
     if (B.ftab) { f = B.ftab[prob]; u = B.utab[prob]; }
-    r = bt_at(r, prob, B);
-    rlo = bt_ptr(rlo, prob, B);
-    part += (size_t)prob * B.nparts;
+    if (START) { r = bt_at(r, prob, B); rlo = bt_ptr(rlo, prob, B); }
     const int i = blockIdx.x * 32 + threadIdx.x + 1, j = blockIdx.y * 8 + threadIdx.y + 1;
     const int k0 = bz * RES3_PLANES + 1;
     const size_t pl = (size_t)up * (n + 2), pr = (size_t)rp * (n + 2);
-    float acc = 0.f;
+    float acc = 0.f, facc = 0.f;
     if (i <= n && j <= n) {
-        const double *uc = u + k0 * pl + (size_t)j * up + i;
-        const double *fc = f + k0 * pl + (size_t)j * up + i;
-        double ud = uc[-(long)pl], u0 = uc[0];
-#pragma unroll
-        for (int q = 0; q < RES3_PLANES; q++) {
-            if (k0 + q > n) break;
-            const double uu = uc[pl];
-            const double s = ((uc[-1] + uc[1]) + (uc[-up] + uc[up])) + (ud + uu);
-            const double res = fma(-ih2, fma(-6.0, u0, s), fc[0]);
-            const float rf = (float)res;
-            r(i, j, k0 + q) = rf;
-            rlo[(k0 + q) * pr + (size_t)j * rp + i] = (float)(res - (double)rf);
-            acc = fmaf(rf, rf, acc);
-            ud = u0; u0 = uu;
-            uc += pl; fc += pl;
+        const double *u0p = u + k0 * pl + (size_t)j * up + i;
+        const double *f0p = f + k0 * pl + (size_t)j * up + i;
+        const int planes = min(RES3_PLANES, n + 1 - k0);
+        bool zero = false;
+        if (START) {  // u and its neighbours zero at every point of the thread?
+            unsigned long long ob = bits(u0p[-(long)pl]) | bits(u0p[(size_t)planes * pl]);
+            for (int q = 0; q < planes; q++) {
+                const double *c = u0p + (size_t)q * pl;
+                ob |= bits(c[-1]) | bits(c[0]) | bits(c[1]) | bits(c[-up]) | bits(c[up]);
+            }
+            zero = (ob << 1) == 0;
         }
+        auto planes_loop = [&](auto zero_tag) {
+            constexpr bool Z = decltype(zero_tag)::value;
+            const double *uc = u0p, *fc = f0p;
+            double ud = Z ? 0.0 : uc[-(long)pl], u0 = Z ? 0.0 : uc[0];
+#pragma unroll
+            for (int q = 0; q < RES3_PLANES; q++) {
+                if (q >= planes) break;
+                const double fv = fc[0];
+                double res = fv, uu = 0.0;
+                if (!Z) {
+                    uu = uc[pl];
+                    const double s = ((uc[-1] + uc[1]) + (uc[-up] + uc[up])) + (ud + uu);
+                    res = fma(-ih2, fma(-6.0, u0, s), fv);
+                }
+                float hi;
+                if (START) {
+                    float lo;
+                    split_f64(res, hi, lo);
+                    r(i, j, k0 + q) = hi;
+                    rlo[(k0 + q) * pr + (size_t)j * rp + i] = lo;
+                    const float ff = Z ? hi : narrow(fv);
+                    facc = fmaf(ff, ff, facc);
+                } else {
+                    hi = narrow(res);
+                }
+                acc = fmaf(hi, hi, acc);
+                ud = u0; u0 = uu;
+                uc += pl; fc += pl;
+            }
+        };
+        if (__all_sync(__activemask(), zero)) planes_loop(std::true_type{});
+        else planes_loop(std::false_type{});
     }
-    double s = block_sum((double)acc, sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0)
-        part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz)] = s;
+    const size_t slot = (size_t)prob * B.nparts + blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz);
+    const double s = block_sum((double)acc, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) part[slot] = s;
+    if (START) {
+        __syncthreads();
+        const double sf = block_sum((double)facc, sh);
+        if (threadIdx.x == 0 && threadIdx.y == 0) fpart[slot] = sf;
+    }
 }
 
 }  // namespace mg

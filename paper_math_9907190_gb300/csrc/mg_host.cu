@@ -95,7 +95,6 @@ struct mg_ctx {
     bool rr = false;
     void *rlo = nullptr;
     void *r32b = nullptr;
-    int ff_blocks = 0;          // resident blocks of k_up0_ff_2d (persistent grid)
     // tuned choices (mg_tune): tile class per pair for the down / up kernels
     // (-1: the size rule), side cut-off of the coarse thread block (0: default)
     int tile_dn[32], tile_up[32];
@@ -205,6 +204,9 @@ inline cudaStream_t S(void *s) { return (cudaStream_t)s; }
 
 // kernel families for the probe (mg_probe_set)
 enum { TAG_RESIDUAL = 0, TAG_FINEST_UP = 1, TAG_LEVELS = 2, TAG_CONTROL = 3 };
+// sub-families of TAG_LEVELS (probed as 4, 5, 6): restriction, prolongation
+// of the coarser levels, the coarse thread block
+enum { TAG_DOWN = TAG_LEVELS | 4 << 4, TAG_UP = TAG_LEVELS | 5 << 4, TAG_COARSE = TAG_LEVELS | 6 << 4 };
 
 // Counts every launch; brackets the launch with events when its family is probed.
 struct Launch {
@@ -213,7 +215,8 @@ struct Launch {
     int slot = -1;
     Launch(mg_ctx *c_, int tag, cudaStream_t s_) : c(c_), s(s_) {
         c->launches++;
-        if (!c->capturing && c->probe_tag == tag && 2 * c->pev_used + 1 < (int)c->pev.size()) {
+        const bool hit = c->probe_tag >= 0 && (c->probe_tag == (tag & 15) || ((tag >> 4) && c->probe_tag == tag >> 4));
+        if (!c->capturing && hit && 2 * c->pev_used + 1 < (int)c->pev.size()) {
             slot = c->pev_used++;
             cudaEventRecord(c->pev[2 * slot], s);
         }
@@ -324,17 +327,17 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
     const Level &a = c->lv[l], &b = c->lv[l + 1];
     if (c->d.hierarchy == MG_USUAL) {
         const int nc = b.side;
-        if (c->d.dim == 2) LAUNCH_B(TAG_LEVELS, (k_fw_2d<T>), grid2(nc, nc), B2, a2<const T>(a.r[0], a), a2<T>(b.r[0], b), nc, done);
-        else LAUNCH_B(TAG_LEVELS, (k_fw_3d<T>), grid3(nc, nc, nc), B2, a3<const T>(a.r[0], a), a3<T>(b.r[0], b), nc, done);
+        if (c->d.dim == 2) LAUNCH_B(TAG_DOWN, (k_fw_2d<T>), grid2(nc, nc), B2, a2<const T>(a.r[0], a), a2<T>(b.r[0], b), nc, done);
+        else LAUNCH_B(TAG_DOWN, (k_fw_3d<T>), grid3(nc, nc, nc), B2, a3<const T>(a.r[0], a), a3<T>(b.r[0], b), nc, done);
         return;
     }
     if (c->d.dim == 2) {
         if (a.kind == KIND_AXIS) {
             const int nb = b.nb;
-            LAUNCH_B(TAG_LEVELS, (k_g2r_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(a.r[0], a), a2<T>(b.r[0], b), a2<T>(b.r[1], b), nb, done);
+            LAUNCH_B(TAG_DOWN, (k_g2r_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(a.r[0], a), a2<T>(b.r[0], b), a2<T>(b.r[1], b), nb, done);
         } else {
             const int nb = a.nb;
-            LAUNCH_B(TAG_LEVELS, (k_r2b_2d<T>), grid2(nb, nb), B2, a2<const T>(a.r[0], a), a2<const T>(a.r[1], a), a2<T>(b.r[0], b), nb, done);
+            LAUNCH_B(TAG_DOWN, (k_r2b_2d<T>), grid2(nb, nb), B2, a2<const T>(a.r[0], a), a2<const T>(a.r[1], a), a2<T>(b.r[0], b), nb, done);
         }
         return;
     }
@@ -342,14 +345,14 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
         const int nb = b.nb;
         const T *galt = (alt && l == 0 && c->rr) ? (const T *)c->r32b : nullptr;
         const int *par = galt ? &c->ctl->par : nullptr;
-        LAUNCH_B(TAG_LEVELS, (k_g2r_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(a.r[0], a), red3v<T>(b.r, b), nb,
+        LAUNCH_B(TAG_DOWN, (k_g2r_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(a.r[0], a), red3v<T>(b.r, b), nb,
                  galt, par, done);
     } else if (a.kind == KIND_RED) {
         const int nb = a.nb;
-        LAUNCH_B(TAG_LEVELS, (k_r2m_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, red3v<const T>(a.r, a), mag3v<T>(b.r, b), nb, done);
+        LAUNCH_B(TAG_DOWN, (k_r2m_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, red3v<const T>(a.r, a), mag3v<T>(b.r, b), nb, done);
     } else {
         const int nb = a.nb;
-        LAUNCH_B(TAG_LEVELS, (k_m2b_3d<T>), grid3(nb, nb, nb), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
+        LAUNCH_B(TAG_DOWN, (k_m2b_3d<T>), grid3(nb, nb, nb), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
     }
 }
 
@@ -367,13 +370,13 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
         const T cc = (T)(p * hk2);
         if (dim == 2) {
             if (c->d.hierarchy == MG_USUAL)
-                LAUNCH_B(TAG_LEVELS, (k_usual_odd_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_UP, (k_usual_odd_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
             else
-                LAUNCH_B(TAG_LEVELS, (k_r2g_f_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(b.v[1], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_UP, (k_r2g_f_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(b.v[1], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
             if (u)
                 LAUNCH_B(TAG_FINEST_UP, (k_r2g_c_upd_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
             else
-                LAUNCH_B(TAG_LEVELS, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_UP, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
         } else if (c->d.hierarchy == MG_DIAG && sizeof(T) == 4) {  // FP32: both half-sweeps in one tile kernel
             const dim3 g3((n + TX3 - 1) / TX3, (n + TY3 - 1) / TY3, (n + TZ3 - 1) / TZ3);
             const size_t sm = sizeof(Green3Smem<T>);
@@ -382,42 +385,42 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
                               a3<const T>(a.r[0], a), (const T *)nullptr, a3<T>(a.v[0], a), (float *)nullptr, 0, u,
                               c->d.pitch, n, cc, 0.f, (double *)nullptr, (const int *)nullptr, done);
             else
-                LAUNCH_SMEM_B(TAG_LEVELS, (k_green_3d<T, false, false>), g3, B2, sm, red3v<const T>(b.v, b),
+                LAUNCH_SMEM_B(TAG_UP, (k_green_3d<T, false, false>), g3, B2, sm, red3v<const T>(b.v, b),
                               a3<const T>(a.r[0], a), (const T *)nullptr, a3<T>(a.v[0], a), (float *)nullptr, 0, u,
                               c->d.pitch, n, cc, 0.f, (double *)nullptr, (const int *)nullptr, done);
         } else {
             if (c->d.hierarchy == MG_USUAL)
-                LAUNCH_B(TAG_LEVELS, (k_usual_odd_3d<T>), grid3(n, n, n), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_UP, (k_usual_odd_3d<T>), grid3(n, n, n), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
             else
-                LAUNCH_B(TAG_LEVELS, (k_r2g_f_3d<T>), grid3(n, n, n), B2, red3v<const T>(b.v, b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_UP, (k_r2g_f_3d<T>), grid3(n, n, n), B2, red3v<const T>(b.v, b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
             if (u)
                 LAUNCH_B(TAG_FINEST_UP, (k_r2g_c_upd_fast_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<const T>(a.v[0], a), u, c->d.pitch, n + 2, n, cc, done);
             else
-                LAUNCH_B(TAG_LEVELS, (k_r2g_c_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
+                LAUNCH_B(TAG_UP, (k_r2g_c_3d<T>), grid3(n, n, n), B2, a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
         }
         return;
     }
     const int nb = a.nb;
     if (dim == 2) {  // red level from the blue (next axis) level, Eq. Eajacr, Eq. Eajacb
         const T cc = (T)(2.0 * om[0] * hk2);
-        LAUNCH_B(TAG_LEVELS, (k_b2r_oo_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[1], a), a2<T>(a.v[1], a), nb, cc, done);
-        LAUNCH_B(TAG_LEVELS, (k_b2r_ee_2d<T>), grid2(nb, nb), B2, a2<const T>(a.v[1], a), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), nb, cc, done);
+        LAUNCH_B(TAG_UP, (k_b2r_oo_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[1], a), a2<T>(a.v[1], a), nb, cc, done);
+        LAUNCH_B(TAG_UP, (k_b2r_ee_2d<T>), grid2(nb, nb), B2, a2<const T>(a.v[1], a), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), nb, cc, done);
         return;
     }
     if (a.kind == KIND_MAG) {  // Eq. Emprolm, Eq. Emprolb
         const T cc = (T)(4.0 * om[0] * hk2);
-        LAUNCH_B(TAG_LEVELS, (k_b2m_ooo_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, done);
-        LAUNCH_B(TAG_LEVELS, (k_b2m_eee_3d<T>), grid3(nb, nb, nb), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, done);
+        LAUNCH_B(TAG_UP, (k_b2m_ooo_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, done);
+        LAUNCH_B(TAG_UP, (k_b2m_eee_3d<T>), grid3(nb, nb, nb), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, done);
     } else {  // red from magenta: Eq. Erprolr (faces), Eq. Erprolm (corners)
         const T c1 = (T)(2.0 * om[1] * hk2), c2 = (T)(4.0 * om[2] * hk2);
-        LAUNCH_B(TAG_LEVELS, (k_m2r_faces_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, done);
-        LAUNCH_B(TAG_LEVELS, (k_m2r_corners_3d<T>), grid3(nb, nb, nb), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, done);
+        LAUNCH_B(TAG_UP, (k_m2r_faces_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, done);
+        LAUNCH_B(TAG_UP, (k_m2r_corners_3d<T>), grid3(nb, nb, nb), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, done);
     }
 }
 
 template <typename T> void launch_coarse(mg_ctx *c, const int *done, cudaStream_t s) {
     const Level &l = c->lv[c->L];
-    LAUNCH_B(TAG_LEVELS, (k_coarse<T>), dim3(1, 1, 1), 512, (const T *)l.r[0], l.pitch, l.rows, l.side, c->d.dim, c->G, (T *)l.v[0], done);
+    LAUNCH_B(TAG_COARSE, (k_coarse<T>), dim3(1, 1, 1), 512, (const T *)l.r[0], l.pitch, l.rows, l.side, c->d.dim, c->G, (T *)l.v[0], done);
 }
 
 // ---- fused 2D diagonal path ------------------------------------------------
@@ -531,7 +534,7 @@ void launch_down_pair(mg_ctx *c, int k, const int *done, cudaStream_t s, bool al
     dim3 grid((nb + TA) / TA, (nb + TB) / TB, 1);
     const T *galt = (alt && k == 0 && c->rr) ? (const T *)c->r32b : nullptr;
     const int *par = galt ? &c->ctl->par : nullptr;
-    LAUNCH_B(TAG_LEVELS, (k_down_pair_2d<T, TA, TB>), grid, B2, a2<const T>(g.r[0], g), a2<T>(r.r[0], r),
+    LAUNCH_B(TAG_DOWN, (k_down_pair_2d<T, TA, TB>), grid, B2, a2<const T>(g.r[0], g), a2<T>(r.r[0], r),
              a2<T>(r.r[1], r), a2<T>(b.r[0], b), nb, galt, par, done);
 }
 
@@ -548,49 +551,67 @@ void launch_up_pair(mg_ctx *c, int k, double *u, const int *done, cudaStream_t s
                       a2<const T>(r.r[0], r), a2<const T>(r.r[1], r), a2<const T>(g.r[0], g), a2<T>(g.v[0], g), u,
                       c->d.pitch, nb, c2, c1, done);
     else
-        LAUNCH_SMEM_B(TAG_LEVELS, (k_up_pair_2d<T, false, TA, TB>), grid, B2, sm, a2<const T>(b.v[0], b),
+        LAUNCH_SMEM_B(TAG_UP, (k_up_pair_2d<T, false, TA, TB>), grid, B2, sm, a2<const T>(b.v[0], b),
                       a2<const T>(r.r[0], r), a2<const T>(r.r[1], r), a2<const T>(g.r[0], g), a2<T>(g.v[0], g), u,
                       c->d.pitch, nb, c2, c1, done);
 }
 
-int tile_dn(const mg_ctx *c, int k) { return c->tile_dn[k] >= 0 ? c->tile_dn[k] : tile_class(c->lv[2 * k + 1].nb); }
-int tile_up(const mg_ctx *c, int k) { return c->tile_up[k] >= 0 ? c->tile_up[k] : tile_class(c->lv[2 * k + 1].nb); }
+// Kernel class of pair k.  FP64 levels: shared-memory tiles 0: 32x16 cells,
+// 1: 16x8, 2: 8x8.  FP32 levels: 0-2 the warp-streaming kernels (strips of
+// 32/16/8 cell rows up, 16/8/4 down), 3-5 the shared-memory tiles in the
+// order above.  Untuned: by size, as measured on the 4095^2 hierarchy (the
+// finest pair of the fused mixed solve is always streaming).
+constexpr int NCLS_FP32 = 6;
+int tile_default(const mg_ctx *c, int k, bool up) {
+    const int cells = c->lv[2 * k + 1].nb + 1, cls = tile_class(cells - 1);
+    if (c->esz == 8) return cls;
+    if (up) {
+        if (k == 0 && c->rr) return 0;
+        return cells >= 512 ? 2 : cells >= 128 ? 4 : 5;
+    }
+    return cells >= 1024 ? 1 : cells >= 512 ? 2 : cls + 3;
+}
+int tile_dn(const mg_ctx *c, int k) { return c->tile_dn[k] >= 0 ? c->tile_dn[k] : tile_default(c, k, false); }
+int tile_up(const mg_ctx *c, int k) { return c->tile_up[k] >= 0 ? c->tile_up[k] : tile_default(c, k, true); }
+
+void launch_down_ff(mg_ctx *c, int k, int cls, const int *done, cudaStream_t s, bool alt);
+int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s);
 
 template <typename T> void down_pair(mg_ctx *c, int k, int cls, const int *done, cudaStream_t s, bool alt) {
+    if (sizeof(T) == 4) {
+        if (cls < 3) { launch_down_ff(c, k, cls, done, s, alt); return; }
+        cls -= 3;
+    }
     switch (cls) {
     case 0: launch_down_pair<T, 32, 16>(c, k, done, s, alt); break;
     case 1: launch_down_pair<T, 16, 8>(c, k, done, s, alt); break;
     default: launch_down_pair<T, 8, 8>(c, k, done, s, alt); break;
     }
 }
-template <typename T> void up_pair(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s) {
+// returns the partial sums written per problem (the finest pair of the fused
+// mixed solve) or 0
+template <typename T> int up_pair(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s) {
+    if (sizeof(T) == 4) {
+        if (k == 0 && c->rr) return launch_up_ff(c, 0, cls < 3 ? cls : 0, u, done, s);
+        if (cls < 3) return launch_up_ff(c, k, cls, u, done, s);
+        cls -= 3;
+    }
     switch (cls) {
     case 0: launch_up_pair<T, 32, 16>(c, k, u, done, s); break;
     case 1: launch_up_pair<T, 16, 8>(c, k, u, done, s); break;
     default: launch_up_pair<T, 8, 8>(c, k, u, done, s); break;
     }
+    return 0;
 }
 
 template <typename T> void vcycle_fast2d(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
-    for (int k = 0; k < c->kc; k++) {
-        switch (tile_dn(c, k)) {
-        case 0: launch_down_pair<T, 32, 16>(c, k, done, s); break;
-        case 1: launch_down_pair<T, 16, 8>(c, k, done, s); break;
-        default: launch_down_pair<T, 8, 8>(c, k, done, s); break;
-        }
-    }
+    for (int k = 0; k < c->kc; k++) down_pair<T>(c, k, tile_dn(c, k), done, s, false);
     {
         const Level &g = c->lv[2 * c->kc];
-        LAUNCH_SMEM_B(TAG_LEVELS, (k_coarse_cta_2d<T>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan2d,
+        LAUNCH_SMEM_B(TAG_COARSE, (k_coarse_cta_2d<T>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan2d,
                       a2<const T>(g.r[0], g), a2<T>(g.v[0], g), c->G, done);
     }
-    for (int k = c->kc - 1; k >= 0; k--) {
-        switch (tile_up(c, k)) {
-        case 0: launch_up_pair<T, 32, 16>(c, k, u, done, s); break;
-        case 1: launch_up_pair<T, 16, 8>(c, k, u, done, s); break;
-        default: launch_up_pair<T, 8, 8>(c, k, u, done, s); break;
-        }
-    }
+    for (int k = c->kc - 1; k >= 0; k--) up_pair<T>(c, k, tile_up(c, k), u, done, s);
     if (c->kc == 0) {  // the whole hierarchy ran in the coarse block: apply v to u
         const Level &l0 = c->lv[0];
         const int n = c->d.n;
@@ -599,75 +620,100 @@ template <typename T> void vcycle_fast2d(mg_ctx *c, double *u, const int *done, 
     }
 }
 
-// strip height (cell rows) of k_up0_ff_2d per tile class
+// strip height (cell rows) of the warp-streaming pair kernels per tile class:
+// the prolongation's chain needs 4 rows to fill, the restriction's 1
 int ff_strip(int cls) { return cls == 0 ? 32 : cls == 1 ? 16 : 8; }
+int fd_strip(int cls) { return cls == 0 ? 16 : cls == 1 ? 8 : 4; }
 
-// the finest pair of the mixed 2D solve (k_up0_ff_2d); returns the partial
-// sums written per problem
-int launch_up0_ff(mg_ctx *c, double *u, int cls, const int *done, cudaStream_t s) {
-    const Level &g = c->lv[0], &r = c->lv[1], &b = c->lv[2];
+// one warp per (column, strip) item
+dim3 ff_grid(int items) { return dim3((items + FF_WARPS - 1) / FF_WARPS, 1, 1); }
+
+// FP32 pair k restriction (k_down_ff_2d)
+void launch_down_ff(mg_ctx *c, int k, int cls, const int *done, cudaStream_t s, bool alt) {
+    const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
+    const int nb = r.nb, tb = fd_strip(cls);
+    const dim3 grid = ff_grid(((nb + FD_W) / FD_W) * ((nb + tb) / tb));
+    const float *galt = (alt && k == 0 && c->rr) ? (const float *)c->r32b : nullptr;
+    LAUNCH_B(TAG_DOWN, (k_down_ff_2d), grid, dim3(32, FF_WARPS, 1), a2<const float>(g.r[0], g),
+             a2<float>(r.r[0], r), a2<float>(r.r[1], r), a2<float>(b.r[0], b), nb, tb, galt,
+             galt ? &c->ctl->par : nullptr, done);
+}
+
+// FP32 pair k prolongation (k_up_ff_2d): the finest pair of the fused mixed
+// solve with the carried residual (rr), the finest pair otherwise with u += v,
+// a coarser pair with v stored; returns the partial sums written per problem
+// (rr) or 0
+int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s) {
+    const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
     const int nb = r.nb, tb = ff_strip(cls);
-    const double hk = c->h, p = c->d.omega[0];
+    const double hk = spacing(c, g), p = c->d.omega[0];
     const int items = ((nb + FF_W) / FF_W) * ((nb + tb) / tb);
-    const int per = std::max(1, c->ff_blocks / c->nprob);
-    const dim3 grid(std::min((items + FF_WARPS - 1) / FF_WARPS, per), 1, 1);
+    const bool rr = k == 0 && c->rr, add = k == 0 && !c->rr;
+    const dim3 grid = ff_grid(items);
     const dim3 blk(32, FF_WARPS, 1);
-    const bool vu = c->nprob == 1 && ((uintptr_t)u % 16) == 0 && c->d.pitch % 2 == 0;
+    const bool vu = k == 0 && c->nprob == 1 && ((uintptr_t)u % 16) == 0 && c->d.pitch % 2 == 0;
     const float c2 = (float)(2.0 * p * hk * hk), c1 = (float)(p * hk * hk), s2 = (float)(1.0 / (hk * hk));
-    if (vu)
-        LAUNCH_B(TAG_FINEST_UP, (k_up0_ff_2d<true>), grid, blk, a2<const float>(b.v[0], b), a2<const float>(r.r[0], r),
-                 a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b, (float *)c->rlo, u, c->d.pitch,
-                 nb, c2, c1, s2, tb, c->part, &c->ctl->par, done);
-    else
-        LAUNCH_B(TAG_FINEST_UP, (k_up0_ff_2d<false>), grid, blk, a2<const float>(b.v[0], b), a2<const float>(r.r[0], r),
-                 a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b, (float *)c->rlo, u, c->d.pitch,
-                 nb, c2, c1, s2, tb, c->part, &c->ctl->par, done);
-    return (int)grid.x;
+    const int tag = k == 0 ? TAG_FINEST_UP : TAG_UP;
+#define MG_UPFF(MODE, VU)                                                                                          \
+    LAUNCH_B(tag, (k_up_ff_2d<MODE, VU>), grid, blk, a2<const float>(b.v[0], b), a2<const float>(r.r[0], r),     \
+             a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b, a2<float>(g.v[0], g),           \
+             (float *)c->rlo, u, c->d.pitch, nb, c2, c1, s2, tb, c->part, rr ? &c->ctl->par : nullptr, done)
+    if (rr) {
+        if (vu) MG_UPFF(UP_RR, true);
+        else MG_UPFF(UP_RR, false);
+    } else if (add) {
+        if (vu) MG_UPFF(UP_ADD, true);
+        else MG_UPFF(UP_ADD, false);
+    } else {
+        MG_UPFF(UP_STORE, false);
+    }
+#undef MG_UPFF
+    return rr ? (int)grid.x : 0;
 }
 
 // one cycle of the fused mixed 2D path: restriction, coarse block, prolongation,
 // and the finest pair fused with u += v and the next residual; returns the
 // number of norm partial sums written per problem
 int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
-    for (int k = 0; k < c->kc; k++) {
-        switch (tile_dn(c, k)) {
-        case 0: launch_down_pair<float, 32, 16>(c, k, done, s, true); break;
-        case 1: launch_down_pair<float, 16, 8>(c, k, done, s, true); break;
-        default: launch_down_pair<float, 8, 8>(c, k, done, s, true); break;
-        }
-    }
+    for (int k = 0; k < c->kc; k++) down_pair<float>(c, k, tile_dn(c, k), done, s, true);
     {
         const Level &g = c->lv[2 * c->kc];
-        LAUNCH_SMEM_B(TAG_LEVELS, (k_coarse_cta_2d<float>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan2d,
+        LAUNCH_SMEM_B(TAG_COARSE, (k_coarse_cta_2d<float>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan2d,
                       a2<const float>(g.r[0], g), a2<float>(g.v[0], g), c->G, done);
     }
-    for (int k = c->kc - 1; k >= 1; k--) {
-        switch (tile_up(c, k)) {
-        case 0: launch_up_pair<float, 32, 16>(c, k, u, done, s); break;
-        case 1: launch_up_pair<float, 16, 8>(c, k, u, done, s); break;
-        default: launch_up_pair<float, 8, 8>(c, k, u, done, s); break;
-        }
-    }
-    return launch_up0_ff(c, u, tile_up(c, 0), done, s);
+    for (int k = c->kc - 1; k >= 1; k--) up_pair<float>(c, k, tile_up(c, k), u, done, s);
+    return up_pair<float>(c, 0, tile_up(c, 0), u, done, s);
 }
 
-// direct FP64 residual of the fused path (start and end of a solve) as the
-// carried float-float pair: hi in the current buffer (parity 0 at the start), lo in rlo
-int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
+// direct FP64 residual of the fused path.  start: the carried float-float
+// pair (hi in the current buffer, parity 0 at the start; lo in rlo), partial
+// sums of r^2 at part and of f^2 right after every problem's (fpart); end of
+// a solve: the partial sums of r^2 only.  Returns the partial sums per problem.
+int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s, bool start) {
     const int n = c->d.n;
     const Level &l0 = c->lv[0];
+    const double ih2 = 1.0 / (c->h * c->h);
+    dim3 g = c->d.dim == 3 ? dim3((n + 31) / 32, (n + 7) / 8, (n + RES3_PLANES - 1) / RES3_PLANES)
+                           : dim3((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
+    const int np = (int)(g.x * g.y * g.z);
+    double *fpart = start ? c->part + (size_t)np * c->nprob : nullptr;
     if (c->d.dim == 3) {
-        dim3 g3((n + 31) / 32, (n + 7) / 8, (n + RES3_PLANES - 1) / RES3_PLANES);
-        LAUNCH_B(TAG_RESIDUAL, (k_res0_64_3d), g3, B2, f, u, c->d.pitch, n, 1.0 / (c->h * c->h), a3<float>(l0.r[0], l0),
-                 (float *)c->rlo, l0.pitch, c->part, done);
-        c->nparts = (int)(g3.x * g3.y * g3.z);
-        return c->nparts;
+        if (start)
+            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_3d<true>), g, B2, f, u, c->d.pitch, n, ih2, a3<float>(l0.r[0], l0),
+                     (float *)c->rlo, l0.pitch, c->part, fpart, done);
+        else
+            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_3d<false>), g, B2, f, u, c->d.pitch, n, ih2, a3<float>(l0.r[0], l0),
+                     (float *)c->rlo, l0.pitch, c->part, fpart, done);
+    } else {
+        if (start)
+            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_2d<true>), g, B2, f, u, c->d.pitch, n, ih2, a2<float>(l0.r[0], l0),
+                     (float *)c->rlo, l0.pitch, c->part, fpart, done);
+        else
+            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_2d<false>), g, B2, f, u, c->d.pitch, n, ih2, a2<float>(l0.r[0], l0),
+                     (float *)c->rlo, l0.pitch, c->part, fpart, done);
     }
-    dim3 g((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
-    LAUNCH_B(TAG_RESIDUAL, (k_res0_64_2d), g, B2, f, u, c->d.pitch, n, 1.0 / (c->h * c->h), a2<float>(l0.r[0], l0),
-             (float *)c->rlo, l0.pitch, c->part, done);
-    c->nparts = (int)(g.x * g.y);
-    return c->nparts;
+    c->nparts = np;
+    return np;
 }
 
 // one cycle of the fused mixed 3D path; returns the partial sums per problem
@@ -675,7 +721,7 @@ int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     const int lc = 3 * c->kc;
     for (int l = 0; l < lc; l++) launch_restrict<float>(c, l, done, s, true);
     const Level &gk = c->lv[lc];
-    LAUNCH_SMEM_B(TAG_LEVELS, (k_coarse_cta_3d<float>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan3d,
+    LAUNCH_SMEM_B(TAG_COARSE, (k_coarse_cta_3d<float>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan3d,
                   a3<const float>(gk.r[0], gk), a3<float>(gk.v[0], gk), c->G, done);
     for (int l = lc - 1; l >= 1; l--) launch_prolong<float>(c, l, c->d.omega, nullptr, done, s);
     const Level &a = c->lv[0], &b = c->lv[1];
@@ -717,7 +763,7 @@ mg_status vcycle_t(mg_ctx *c, const double *f, double *u, const int *done, bool 
         const int lc = 3 * c->kc;  // first level run by the coarse block
         for (int l = 0; l < lc; l++) launch_restrict<T>(c, l, done, s);
         const Level &g = c->lv[lc];
-        LAUNCH_SMEM_B(TAG_LEVELS, (k_coarse_cta_3d<T>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan3d,
+        LAUNCH_SMEM_B(TAG_COARSE, (k_coarse_cta_3d<T>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan3d,
                       a3<const T>(g.r[0], g), a3<T>(g.v[0], g), c->G, done);
         for (int l = lc - 1; l >= 0; l--) launch_prolong<T>(c, l, c->d.omega, l == 0 ? u : nullptr, done, s);
         if (lc == 0) {
@@ -858,14 +904,7 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
         }
     }
     if (c->fast2d) {
-        cudaError_t e = d->precision == MG_FP64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c);
-        if (e == cudaSuccess && c->rr && d->dim == 2) {
-            // persistent grid of the finest pair: every block resident at once
-            int per_sm = 0, sms = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_up0_ff_2d<false>, 32 * FF_WARPS, 0);
-            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
-            c->ff_blocks = std::max(1, per_sm * sms);
-        }
+        const cudaError_t e = d->precision == MG_FP64 ? set_smem_attrs<double>(c) : set_smem_attrs<float>(c);
         if (e != cudaSuccess) {
             mg_destroy(c);
             return cuda_fail(e, "mg_create shared-memory attributes");
@@ -1033,7 +1072,7 @@ static int launch_rhs_norm(mg_ctx *c, const double *f, const double *u, cudaStre
 
 // residual of the current iterate into level 0 (+ partial sums); returns their count
 static int solve_residual(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
-    if (c->rr) return launch_res_rr(c, f, u, done, s);
+    if (c->rr) return launch_res_rr(c, f, u, done, s, true);
     return c->d.precision == MG_FP64 ? launch_res_fast<double>(c, f, u, done, s)
                                      : launch_res_fast<float>(c, f, u, done, s);
 }
@@ -1047,6 +1086,37 @@ static void launch_ctrl(mg_ctx *c, int np, int first, cudaGraphConditionalHandle
         LAUNCH(TAG_CONTROL, (k_ctrl_b), c->nprob, 1024, c->part, np, c->ctl, c->hist, c->hist_cap, first);
         LAUNCH(TAG_CONTROL, (k_any_active), 1, 1024, c->ctl, c->nprob, loop, use_loop, (int *)nullptr);
     }
+}
+
+// Prefix of a solve: control words, the norm of the right-hand side, the
+// residual of the warm start and the first control step (which sets the loop
+// condition when use_loop).  The fused mixed path takes the norm of f from
+// its start residual kernel.
+static void solve_prefix(mg_ctx *c, const double *f, const double *u, double rtol, int max_cycles,
+                         cudaGraphConditionalHandle loop, int use_loop, cudaStream_t s) {
+    if (c->nprob == 1) {
+        LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
+    } else {
+        LAUNCH(TAG_CONTROL, (k_ctrl_init_b), (c->nprob + 255) / 256, 256, c->ctl, c->nprob, rtol, max_cycles);
+    }
+    int np, nfp;
+    const double *fpart = c->part;
+    if (c->rr) {
+        np = nfp = launch_res_rr(c, f, u, nullptr, s, true);
+        fpart = c->part + (size_t)np * c->nprob;
+    } else {
+        nfp = launch_rhs_norm(c, f, u, s);
+    }
+    if (c->nprob == 1) {
+        LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, fpart, nfp, &c->ctl->f2);
+    } else {
+        LAUNCH(TAG_CONTROL, (k_sum_to_b), c->nprob, 1024, fpart, nfp, c->ctl);
+    }
+    if (!c->rr) {
+        if (c->d.order == 4) launch_rhs4(c, f, s);
+        np = solve_residual(c, f, u, nullptr, s);
+    }
+    launch_ctrl(c, np, 1, loop, use_loop, s);
 }
 
 // Record one solve into the capture active on stream s: prefix (control
@@ -1065,20 +1135,7 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, nullptr, nullptr, nullptr));
     cudaGraphConditionalHandle loop;
     CK(cudaGraphConditionalHandleCreate(&loop, g, 0, cudaGraphCondAssignDefault));
-    if (c->nprob == 1) {
-        LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
-    } else {
-        LAUNCH(TAG_CONTROL, (k_ctrl_init_b), (c->nprob + 255) / 256, 256, c->ctl, c->nprob, rtol, max_cycles);
-    }
-    const int nfp = launch_rhs_norm(c, f, u, s);
-    if (c->nprob == 1) {
-        LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, nfp, &c->ctl->f2);
-    } else {
-        LAUNCH(TAG_CONTROL, (k_sum_to_b), c->nprob, 1024, c->part, nfp, c->ctl);
-    }
-    if (c->d.order == 4) launch_rhs4(c, f, s);
-    int np = solve_residual(c, f, u, nullptr, s);
-    launch_ctrl(c, np, 1, loop, 1, s);
+    solve_prefix(c, f, u, rtol, max_cycles, loop, 1, s);
     c->g_prefix_kernels = c->launches - l0;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
@@ -1111,7 +1168,7 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     CK(cudaStreamEndCapture(s2, &body));
     if (c->rr) {  // the carried residual ignores the rounding of u: report a direct one
         const long long l2 = c->launches;
-        const int np3 = launch_res_rr(c, f, u, nullptr, s);
+        const int np3 = launch_res_rr(c, f, u, nullptr, s, false);
         LAUNCH(TAG_CONTROL, (k_final_true), c->nprob, 1024, c->part, np3, c->ctl);
         c->g_prefix_kernels += c->launches - l2;
     }
@@ -1138,23 +1195,23 @@ static mg_status build_solve_graph(mg_ctx *c, const double *f, double *u, double
     return MG_OK;
 }
 
-// The same schedule driven from the host (one control-word read per 4 cycles);
-// used when graphs are disabled, e.g. under a kernel profiler.
+// The same schedule driven from the host (one control-word read per 4 cycles,
+// per cycle while probed); used when graphs are disabled, e.g. under a kernel
+// profiler, and while a probe is active.
 static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles,
                                  int *cycles_out, double *relres_out, double *history, cudaStream_t s) {
     const bool fp64 = c->d.precision == MG_FP64;
     const int *done = &c->ctl->done;
     cudaGraphConditionalHandle none = 0;
-    LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
-    const int nfp = launch_rhs_norm(c, f, u, s);
-    LAUNCH(TAG_CONTROL, (k_sum_to), 1, 1024, c->part, nfp, &c->ctl->f2);
-    if (c->d.order == 4) launch_rhs4(c, f, s);
-    int np = solve_residual(c, f, u, nullptr, s);
-    launch_ctrl(c, np, 1, none, 0, s);
+    solve_prefix(c, f, u, rtol, max_cycles, none, 0, s);
+    int np = 0;
     CKL("mg_solve init");
     Ctrl host{};
-    for (int cyc = 0; cyc < max_cycles; cyc += 4) {
-        for (int q = 0; q < 4 && cyc + q < max_cycles; q++) {
+    // cycles are launched in groups between reads of the control word; one
+    // per group while a probe is active, so that probed launches all do work
+    const int group = c->probe_tag >= 0 ? 1 : 4;
+    for (int cyc = 0; cyc < max_cycles; cyc += group) {
+        for (int q = 0; q < group && cyc + q < max_cycles; q++) {
             if (c->rr) {
                 np = c->d.dim == 3 ? vcycle_rr3(c, u, done, s) : vcycle_rr(c, u, done, s);
             } else {
@@ -1170,7 +1227,7 @@ static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double r
         if (host.done) break;
     }
     if (c->rr) {
-        const int np3 = launch_res_rr(c, f, u, nullptr, s);
+        const int np3 = launch_res_rr(c, f, u, nullptr, s, false);
         LAUNCH(TAG_CONTROL, (k_final_true), c->nprob, 1024, c->part, np3, c->ctl);
     }
     CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
@@ -1462,7 +1519,8 @@ std::string tune_key(const mg_ctx *c) {
     cudaDeviceProp pr{};
     cudaGetDeviceProperties(&pr, c->dev);
     char buf[320];
-    std::snprintf(buf, sizeof buf, "\"device\": \"%s\", \"dim\": %d, \"n\": %d, \"hier\": %d, \"prec\": %d, \"nprob\": %d",
+    // "kernels": the version of the tunable kernel set (classes change meaning with it)
+    std::snprintf(buf, sizeof buf, "\"kernels\": 2, \"device\": \"%s\", \"dim\": %d, \"n\": %d, \"hier\": %d, \"prec\": %d, \"nprob\": %d",
                   pr.name, c->d.dim, c->d.n, c->d.hierarchy, c->d.precision, c->nprob);
     return buf;
 }
@@ -1562,13 +1620,15 @@ mg_status tune_measure(mg_ctx *c, const double *f, double *u, cudaStream_t s) {
     if (c->fast2d) {
         for (int k = 0; k < c->kc && k < 32; k++) {
             float bd = 1e30f, bu = 1e30f;
-            for (int cls = 0; cls < 3; cls++) {
+            const int ncls = fp64 ? 3 : NCLS_FP32;
+            for (int cls = 0; cls < ncls; cls++) {
                 const float md = fp64 ? timeit([&] { down_pair<double>(c, k, cls, nullptr, s, false); }, 5)
                                       : timeit([&] { down_pair<float>(c, k, cls, nullptr, s, false); }, 5);
                 if (md < bd) { bd = md; c->tile_dn[k] = cls; }
                 float mu;
                 if (k == 0 && c->rr) {
-                    mu = timeit([&] { launch_up0_ff(c, u, cls, nullptr, s); }, 5);
+                    if (cls >= 3) continue;  // the fused finest pair exists only as a streaming kernel
+                    mu = timeit([&] { launch_up_ff(c, 0, cls, u, nullptr, s); }, 5);
                 } else {
                     mu = fp64 ? timeit([&] { up_pair<double>(c, k, cls, k == 0 ? u : nullptr, nullptr, s); }, 5)
                               : timeit([&] { up_pair<float>(c, k, cls, k == 0 ? u : nullptr, nullptr, s); }, 5);
@@ -1666,7 +1726,7 @@ mg_status mg_launch_count(const mg_ctx *c, long long *launches) {
 }
 
 mg_status mg_probe_set(mg_ctx *c, int family) {
-    if (!c || family < -1 || family > TAG_CONTROL) return MG_EINVAL;
+    if (!c || family < -1 || family > 6) return MG_EINVAL;
     if (family >= 0 && c->pev.empty()) {
         c->pev.resize(1024);
         for (auto &e : c->pev) CK(cudaEventCreate(&e));

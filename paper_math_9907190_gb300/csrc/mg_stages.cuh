@@ -86,6 +86,37 @@ __device__ __forceinline__ double widen(float x) {
 }
 __device__ __forceinline__ double widen(double x) { return x; }
 
+// f64 -> f32 rounded to nearest even with integer operations (on this GPU
+// the conversion instruction runs on the FP64 pipe at a fraction of its
+// rate).  Normal FP32 results and zero are formed here; FP64 zeros and
+// subnormals round to a signed zero; the rest (FP32 subnormal or overflow
+// range, inf, nan) falls back to the conversion instruction.
+// the conversion instruction, out of line so that it is never executed
+// speculatively on the common path
+__device__ __noinline__ float narrow_rare(double x) { return __double2float_rn(x); }
+__device__ __forceinline__ float narrow(double x) {
+    const unsigned long long X = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi = (unsigned)(X >> 32), lo = (unsigned)X;
+    const int e = (int)((hi >> 20) & 0x7ffu), fe = e - 896;  // FP32 biased exponent
+    if (fe < 1 || fe > 254) return e == 0 ? __uint_as_float(hi & 0x80000000u) : narrow_rare(x);
+    const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 mantissa bits
+    const unsigned rem = lo & 0x1fffffffu;                   // the 29 dropped bits
+    const unsigned r = (hi & 0x80000000u) | ((unsigned)fe << 23) | m;
+    return __uint_as_float(r + ((rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u));
+}
+// level value of an FP64 result: FP32 levels round with narrow()
+template <typename T> __device__ __forceinline__ T lvl(double x);
+template <> __device__ __forceinline__ float lvl<float>(double x) { return narrow(x); }
+template <> __device__ __forceinline__ double lvl<double>(double x) { return x; }
+
+// int -> f32 rounded to nearest for |d| < 2^33, with FP32 adds: the two halves
+// are exact through the 1.5 * 2^23 offset, one FMA rounds their sum
+__device__ __forceinline__ float i2f_rn(int d) {
+    const float fh = __int_as_float(0x4B400000 + (d >> 11)) - 12582912.0f;
+    const float fl = __int_as_float(0x4B400000 + (d & 0x7ff)) - 12582912.0f;
+    return fmaf(fh, 2048.0f, fl);
+}
+
 #define MG_IDX2 \
     const int tx = blockIdx.x * blockDim.x + threadIdx.x; \
     const int ty = blockIdx.y * blockDim.y + threadIdx.y;
@@ -543,7 +574,7 @@ __global__ void k_res_2d(const double *__restrict__ f, const double *__restrict_
                 res = fma(-ih2 * (1.0 / 6.0), fma(4.0, ax, dg) - 20.0 * u[c], res);
             }
         }
-        r(i, j) = (T)res;
+        r(i, j) = lvl<T>(res);
         if (r64) r64[c] = res;
         sq = res * res;
     }
@@ -586,7 +617,7 @@ __global__ void k_res_3d(const double *__restrict__ f, const double *__restrict_
                 res = fma(-ih2 * (1.0 / 6.0), fma(2.0, ax, ed) - 24.0 * u[c], res);
             }
         }
-        r(i, j, k) = (T)res;
+        r(i, j, k) = lvl<T>(res);
         if (r64) r64[c] = res;
         sq = res * res;
     }

@@ -158,6 +158,26 @@ def test_residual_with_padded_pitch():
         assert_close(H(rt), O.residual(f, u, 2), lattice(2, n, 0), tol=1e-13)
 
 
+@pytest.mark.parametrize("dim,n", [(2, 255), (3, 31)])
+def test_mixed_level_residual_rounds_to_nearest(dim, n):
+    """FP32 level values of an FP64 residual are its round-to-nearest-even
+    FP32 values (the kernels round with integer operations).  The inputs span
+    magnitudes 1e-30..1e30 and include exact zeros and rounding ties."""
+    rng = np.random.default_rng(7)
+    f = I.zero_ring(rng.uniform(-1, 1, (n + 2,) * dim) * 10.0 ** rng.integers(-30, 30, (n + 2,) * dim))
+    f.flat[rng.integers(0, f.size, 50)] = 0.0
+    ties = (1.0 + 2.0 ** -24) * 2.0 ** rng.integers(-20, 20, 40)  # halfway between two FP32 values
+    f.flat[rng.integers(0, f.size, 40)] = ties * rng.choice([-1.0, 1.0], 40)
+    f = I.zero_ring(f)
+    u = np.zeros_like(f)
+    with Context(dim, n, precision="mixed") as c:
+        r = c.new_grid()
+        c.residual(T(f), T(u), r)
+        got = c.level_get(0, "r")
+        want = r.float().double()
+        assert torch.equal(got, want)
+
+
 VC_CASES = [
     (2, 63, "diag", 2, (1.0,)), (2, 63, "diag", 2, (1.052,)), (2, 63, "usual", 2, (1.0,)),
     (2, 63, "usual", 2, (1.121,)), (2, 63, "diag", 4, (1.2,)), (2, 63, "usual", 4, (1.216,)),
