@@ -1071,13 +1071,18 @@ __global__ void __launch_bounds__(256) k_norm_f(const double *__restrict__ f, in
 // two.  Below |x| ~ 2^-74 lo is 0.
 __device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
     hi = narrow(x);
-    const long long X = __double_as_longlong(x), H = __double_as_longlong(widen(hi));
-    const int fe = (int)((X >> 52) & 0x7ff) - 948;  // FP32 biased exponent of 2^(e - 1075), x's ulp
-    const float l = fe > 0 ? i2f_rn((int)(X - H)) * __int_as_float(fe << 23) : 0.f;
-    lo = X < 0 ? -l : l;
+    // 32-bit integer operations only: D fits in 32 bits, so the low words give it
+    const unsigned xh = (unsigned)__double2hiint(x), xl = (unsigned)__double2loint(x);
+    const int D = (int)(xl - (unsigned)__double2loint(widen(hi)));
+    const int fe = (int)((xh >> 20) & 0x7ffu) - 948;  // FP32 biased exponent of 2^(e - 1075), x's ulp
+    const float l = fe > 0 ? i2f_rn(D) * __int_as_float(fe << 23) : 0.f;
+    lo = (xh >> 31) ? -l : l;
 }
 
-__device__ __forceinline__ unsigned long long bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+// OR of the magnitude bits of a double (zero iff +-0), in 32-bit operations
+__device__ __forceinline__ unsigned mag_bits(double x) {
+    return ((unsigned)__double2hiint(x) << 1) | (unsigned)__double2loint(x);
+}
 
 // Direct FP64 residual r = f - L u (Eq. Evpois) of the fused mixed path.
 // START (start of a solve): r as the float-float pair hi (the level's buffer
@@ -1102,26 +1107,32 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
         const double *u0p = u + (size_t)j0 * up + i;
         const double *f0p = f + (size_t)j0 * up + i;
         const int rows = min(RES_ROWS, n + 1 - j0);
+        // f of the thread's rows, loaded ahead of the test of u
+        double fr[RES_ROWS];
+#pragma unroll
+        for (int q = 0; q < RES_ROWS; q++) fr[q] = q < rows ? f0p[(size_t)q * up] : 0.0;
         bool zero = false;
         if (START) {  // u and its neighbours zero at every point of the thread?
-            unsigned long long ob = bits(u0p[-up]) | bits(u0p[(size_t)rows * up]);
-            for (int q = 0; q < rows; q++) {
+            unsigned ob = mag_bits(u0p[-up]) | mag_bits(u0p[(size_t)rows * up]);
+#pragma unroll
+            for (int q = 0; q < RES_ROWS; q++) {
+                if (q >= rows) break;
                 const double *c = u0p + (size_t)q * up;
-                ob |= bits(c[-1]) | bits(c[0]) | bits(c[1]);
+                ob |= mag_bits(c[-1]) | mag_bits(c[0]) | mag_bits(c[1]);
             }
-            zero = (ob << 1) == 0;
+            zero = ob == 0;
         }
         // warp-uniform: either no FP64 arithmetic at all (two separate loops,
         // so that the stencil is branched over rather than predicated) or the
         // full stencil
         auto rows_loop = [&](auto zero_tag) {
             constexpr bool Z = decltype(zero_tag)::value;
-            const double *uc = u0p, *fc = f0p;
+            const double *uc = u0p;
             double um = Z ? 0.0 : uc[-up], u0 = Z ? 0.0 : uc[0];
 #pragma unroll
             for (int q = 0; q < RES_ROWS; q++) {
                 if (q >= rows) break;
-                const double fv = fc[0];
+                const double fv = fr[q];
                 double res = fv, upn = 0.0;
                 if (!Z) {
                     upn = uc[up];
@@ -1141,7 +1152,7 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
                 }
                 acc = fmaf(hi, hi, acc);
                 um = u0; u0 = upn;
-                uc += up; fc += up;
+                uc += up;
             }
         };
         if (__all_sync(__activemask(), zero)) rows_loop(std::true_type{});
@@ -1401,23 +1412,28 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
         const double *u0p = u + k0 * pl + (size_t)j * up + i;
         const double *f0p = f + k0 * pl + (size_t)j * up + i;
         const int planes = min(RES3_PLANES, n + 1 - k0);
+        double fr[RES3_PLANES];
+#pragma unroll
+        for (int q = 0; q < RES3_PLANES; q++) fr[q] = q < planes ? f0p[(size_t)q * pl] : 0.0;
         bool zero = false;
         if (START) {  // u and its neighbours zero at every point of the thread?
-            unsigned long long ob = bits(u0p[-(long)pl]) | bits(u0p[(size_t)planes * pl]);
-            for (int q = 0; q < planes; q++) {
+            unsigned ob = mag_bits(u0p[-(long)pl]) | mag_bits(u0p[(size_t)planes * pl]);
+#pragma unroll
+            for (int q = 0; q < RES3_PLANES; q++) {
+                if (q >= planes) break;
                 const double *c = u0p + (size_t)q * pl;
-                ob |= bits(c[-1]) | bits(c[0]) | bits(c[1]) | bits(c[-up]) | bits(c[up]);
+                ob |= mag_bits(c[-1]) | mag_bits(c[0]) | mag_bits(c[1]) | mag_bits(c[-up]) | mag_bits(c[up]);
             }
-            zero = (ob << 1) == 0;
+            zero = ob == 0;
         }
         auto planes_loop = [&](auto zero_tag) {
             constexpr bool Z = decltype(zero_tag)::value;
-            const double *uc = u0p, *fc = f0p;
+            const double *uc = u0p;
             double ud = Z ? 0.0 : uc[-(long)pl], u0 = Z ? 0.0 : uc[0];
 #pragma unroll
             for (int q = 0; q < RES3_PLANES; q++) {
                 if (q >= planes) break;
-                const double fv = fc[0];
+                const double fv = fr[q];
                 double res = fv, uu = 0.0;
                 if (!Z) {
                     uu = uc[pl];
@@ -1437,7 +1453,7 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
                 }
                 acc = fmaf(hi, hi, acc);
                 ud = u0; u0 = uu;
-                uc += pl; fc += pl;
+                uc += pl;
             }
         };
         if (__all_sync(__activemask(), zero)) planes_loop(std::true_type{});

@@ -12,6 +12,7 @@
 
 #include "../../include/diagmg.h"
 #include "mg_stages.cuh"
+#include "mg_fast3d.cuh"
 #include "mg_fast2d.cuh"
 
 using namespace mg;
@@ -358,6 +359,20 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
 
 // prolongation v^(l) <- v^(l+1), r^(l); on level 0 with u != nullptr the
 // second half-sweep also applies u += v
+// z range (output planes per block) of k_green_ff_3d: about 600 blocks, at
+// most 64 and at least 8 planes each
+int green_ff_zch(int n) {
+    const int cols = ((n + GS_TX - 1) / GS_TX) * ((n + GS_TY - 1) / GS_TY);
+    const int chunks = (600 + cols - 1) / cols;
+    return std::max(8, std::min(64, (n + chunks - 1) / chunks));
+}
+dim3 green_ff_grid(int n) {
+    const int zch = green_ff_zch(n);
+    return dim3((n + GS_TX - 1) / GS_TX, (n + GS_TY - 1) / GS_TY, (n + zch - 1) / zch);
+}
+// the z-streaming green sweep pays GS_WARM steps per z range: used from 255^3 up
+bool green_ff_use(int n) { return n >= 255; }
+
 template <typename T>
 void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *done, cudaStream_t s) {
     const Level &a = c->lv[l], &b = c->lv[l + 1];
@@ -377,6 +392,19 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
                 LAUNCH_B(TAG_FINEST_UP, (k_r2g_c_upd_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
             else
                 LAUNCH_B(TAG_UP, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+        } else if (c->d.hierarchy == MG_DIAG && sizeof(T) == 4 && green_ff_use(n)) {  // FP32, z-streaming
+            const dim3 g3 = green_ff_grid(n);
+            const size_t sm = sizeof(GreenSSmem);
+            const int zch = green_ff_zch(n);
+            if (u)
+                LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_ff_3d<UP_ADD>), g3, dim3(32, 8, 1), sm,
+                              red3v<const float>(b.v, b), a3<float>(a.r[0], a), (float *)nullptr, a3<float>(a.v[0], a),
+                              (float *)nullptr, u, c->d.pitch, n, (float)cc, 0.f, zch, (double *)nullptr,
+                              (const int *)nullptr, done);
+            else
+                LAUNCH_SMEM_B(TAG_UP, (k_green_ff_3d<UP_STORE>), g3, dim3(32, 8, 1), sm, red3v<const float>(b.v, b),
+                              a3<float>(a.r[0], a), (float *)nullptr, a3<float>(a.v[0], a), (float *)nullptr, u,
+                              c->d.pitch, n, (float)cc, 0.f, zch, (double *)nullptr, (const int *)nullptr, done);
         } else if (c->d.hierarchy == MG_DIAG && sizeof(T) == 4) {  // FP32: both half-sweeps in one tile kernel
             const dim3 g3((n + TX3 - 1) / TX3, (n + TY3 - 1) / TY3, (n + TZ3 - 1) / TZ3);
             const size_t sm = sizeof(Green3Smem<T>);
@@ -727,11 +755,11 @@ int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     const Level &a = c->lv[0], &b = c->lv[1];
     const int n = c->d.n;
     const double h2 = c->h * c->h;
-    const dim3 g3((n + TX3 - 1) / TX3, (n + TY3 - 1) / TY3, (n + TZ3 - 1) / TZ3);
-    LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_3d<float, true, true>), g3, B2, sizeof(Green3Smem<float>),
-                  red3v<const float>(b.v, b), a3<const float>(a.r[0], a), (const float *)c->r32b, a3<float>(a.v[0], a),
-                  (float *)c->rlo, a.pitch, u, c->d.pitch, n, (float)(c->d.omega[3] * h2), (float)(1.0 / h2), c->part,
-                  &c->ctl->par, done);
+    const dim3 g3 = green_ff_grid(n);
+    LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_ff_3d<UP_RR>), g3, dim3(32, 8, 1), sizeof(GreenSSmem),
+                  red3v<const float>(b.v, b), a3<float>(a.r[0], a), (float *)c->r32b, a3<float>(a.v[0], a),
+                  (float *)c->rlo, u, c->d.pitch, n, (float)(c->d.omega[3] * h2), (float)(1.0 / h2),
+                  green_ff_zch(n), c->part, &c->ctl->par, done);
     return (int)(g3.x * g3.y * g3.z);
 }
 
@@ -893,6 +921,10 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
             : cudaFuncSetAttribute(k_coarse_cta_3d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
         (void)gsm;
         const int g64 = (int)sizeof(Green3Smem<double>), g32 = (int)sizeof(Green3Smem<float>);
+        const int gs = (int)sizeof(GreenSSmem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<UP_RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<UP_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<UP_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<float, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
