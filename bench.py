@@ -40,21 +40,30 @@ WORKLOAD = "2D unit square, h=1/4096 (4095^2 = 16.8M unknowns), f ~ U[-1,1] seed
            "diagonal V-cycle (p=1.052), mixed FP64/FP32, solve from u=0 to 1e-10 relative residual"
 
 # The dominant kernel of the mixed solve is the finest pair fused with u += v
-# and the next residual (k_up0_ff_2d, probe family 1).  Algorithmic bytes per
+# and the next residual (k_up_ff_2d<RR>, probe family 1).  Algorithmic bytes per
 # finest unknown: reads u (8), the carried residual as a float-float pair
 # (hi 4 + lo 4), the red residual (N/2 x 4 B = 2) and the blue correction
 # (N/4 x 4 B = 1); writes u (8) and the new pair (4 + 4): 35 B.  FP64 pipe
 # operations per point: 1 (u + v; the residual update runs in FP32 pairs).
 PROBE = {
     "family": 1,
-    "name": "k_up0_ff_2d: finest Jacobi prolongation + u += v + carried float-float residual r -= L v",
+    "name": "k_up_ff_2d<RR>: finest Jacobi prolongation + u += v + carried float-float residual r -= L v",
     "bytes_per_point": 35,
     "fp64_pipe_ops_per_point": 1,
+}
+# The dominant kernel of the 3D mixed solve: the finest triple's green-red
+# sweep fused with u += v and the carried residual (k_green_ff_3d, probe
+# family 1).  Bytes per finest unknown: reads u (8), hi 4, lo 4, the red
+# correction (N/2 x 4 B = 2); writes u (8), hi 4, lo 4: 34 B.
+PROBE3 = {
+    "name": "k_green_ff_3d<RR>: finest green-red sweep + u += v + carried float-float residual r -= L v",
+    "bytes_per_point": 34,
 }
 # DRAM traffic of one launch on the 4095^2 workload from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the
 # kernel's source is the one that was captured.
-TRAFFIC = {"kernel": "k_up0_ff_2d", "bytes": None, "source_sha1": None}
+TRAFFIC = {"kernel": "k_up_ff_2d", "bytes": 333.859072e6 + 210.871040e6,
+           "source_sha1": "c9183447365e13de4d4699e376d4835b1a9fdb86"}
 
 
 def read_peaks():
@@ -126,6 +135,18 @@ def extra_measurements(dev, stream):
             out[f"cube255_{prec}"] = {"unknowns_per_s": 255**3 / (ms * 1e-3), "ms": ms, "cycles": cyc, "relres": rel,
                                       "workload": "3D unit cube 255^3, f = -6 pi^2 sin sin sin(2 pi z) + N(0,1e-6), "
                                                   "diagonal V-cycle (1.11, 1.42, 1.08, 0.99)"}
+            if prec == "mixed":  # the dominant 3D kernel, probed inside the solve as the headline's
+                c.probe_set(PROBE["family"])
+                for _ in range(3):
+                    c.solve(f3, u.zero_(), rtol=RTOL, max_cycles=60)
+                k, pms = c.probe_read()
+                c.probe_set(-1)
+                avg = pms / max(k, 1)
+                ach = PROBE3["bytes_per_point"] * 255**3 / (avg * 1e-3) / 1e9
+                peak = read_peaks().get("hbm_gbs", 6800.0)
+                out["cube255_roofline"] = {"kernel": PROBE3["name"], "bound": "hbm", "avg_launch_ms": avg,
+                                           "launches_probed": k, "bytes_per_point": PROBE3["bytes_per_point"],
+                                           "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak}
     del f3
     sides = I.batch_sides(512)
     fs = [torch.from_numpy(I.batch_f(n, b)).to(dev) for b, n in enumerate(sides)]
