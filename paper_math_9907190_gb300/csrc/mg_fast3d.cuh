@@ -212,3 +212,200 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
 }
 
 }  // namespace mg
+
+
+namespace mg {
+
+// ---------------------------------------------------------------------------
+// Per-stage kernels of the 3D triple, z-marching: a thread owns one cell
+// column (a, b) over zm consecutive cell planes, forms each array's
+// address once and steps it by one plane; values of the previous plane that
+// the next one needs stay in registers.  The arithmetic of every value is the
+// one of the stage kernels in mg_stages.cuh, term for term.  All coset arrays
+// of a triple (and its blue level) share one layout: pitch P, plane Q = P *
+// rows.  Grid: (cells + 31) / 32 x (cells + 7) / 8 x ceil(planes / zm) per
+// problem, block 32 x 8.
+// ---------------------------------------------------------------------------
+struct ZmIdx {
+    int a, b, c0, c1;  // cell column and plane range [c0, c1)
+    size_t i;          // linear index of (a, b, c0)
+};
+// cells of the column range [lo, hi] in a and b, planes [lo, hi] in c, zm
+// planes per thread
+__device__ __forceinline__ bool zm_cell(ZmIdx &z, int lo, int hi, int zm, int P, size_t Q, const Bt &B) {
+    z.a = blockIdx.x * 32 + threadIdx.x + lo;
+    z.b = blockIdx.y * 8 + threadIdx.y + lo;
+    z.c0 = bt_z(B) * zm + lo;
+    z.c1 = min(z.c0 + zm, hi + 1);
+    z.i = (size_t)z.c0 * Q + (size_t)z.b * P + z.a;
+    return z.a <= hi && z.b <= hi;
+}
+
+// Eq. Erred (green -> red), cells [0, nb]^3; green g has its own layout
+template <typename T>
+__global__ void __launch_bounds__(256) k_g2r_zm_3d(A3<const T> g, Red3<T> red, int nb, const T *galt, const int *par,
+                                                   int zm, const int *done, Bt B) {
+    const int prob = bt_prob(B);
+    if (stop(bt_done(done, prob, B))) return;
+    if (galt && par[(size_t)prob * B.ctl_stride]) g.p = galt;
+    g = bt_at(g, prob, B);
+    red = bt_at(red, prob, B);
+    const int P = red.eee.pitch;
+    const size_t Q = (size_t)P * red.eee.rows;
+    ZmIdx z;
+    if (!zm_cell(z, 0, nb, zm, P, Q, B)) return;
+    const int gp = g.pitch;
+    const size_t gq = (size_t)gp * g.rows;
+    auto avg = [&](const T *c) {
+        return (T(6) * c[0] + (c[1] + c[-1]) + (c[gp] + c[-gp]) + (c[gq] + c[-(long)gq])) * T(1.0 / 12.0);
+    };
+    size_t i = z.i;
+    for (int c = z.c0; c < z.c1; c++, i += Q) {
+        const T *ge = g.p + ((size_t)(2 * c) * g.rows + 2 * z.b) * gp + 2 * z.a;  // green (2a, 2b, 2c)
+        if (z.a >= 1 && z.b >= 1 && c >= 1) red.eee.p[i] = avg(ge);
+        if (c >= 1) red.ooe.p[i] = avg(ge + gp + 1);
+        if (z.b >= 1) red.oeo.p[i] = avg(ge + gq + 1);
+        if (z.a >= 1) red.eoo.p[i] = avg(ge + gq + gp);
+    }
+}
+
+// Eq. Ermagc (corners) and Eq. Ermagm (centres), cells [0, nb]^3
+template <typename T>
+__global__ void __launch_bounds__(256) k_r2m_zm_3d(Red3<const T> red, Mag3<T> mag, int nb, int zm, const int *done, Bt B) {
+    const int prob = bt_prob(B);
+    if (stop(bt_done(done, prob, B))) return;
+    red = bt_at(red, prob, B);
+    mag = bt_at(mag, prob, B);
+    const int P = red.eee.pitch;
+    const size_t Q = (size_t)P * red.eee.rows;
+    ZmIdx z;
+    if (!zm_cell(z, 0, nb, zm, P, Q, B)) return;
+    const T *eee = red.eee.p, *ooe = red.ooe.p, *oeo = red.oeo.p, *eoo = red.eoo.p;
+    size_t i = z.i;
+    for (int c = z.c0; c < z.c1; c++, i += Q) {
+        if (z.a >= 1 && z.b >= 1 && c >= 1) {
+            const T s1 = (ooe[i - P - 1] + ooe[i - P]) + (ooe[i - 1] + ooe[i]);
+            const T s2 = (oeo[i - Q - 1] + oeo[i - Q]) + (oeo[i - 1] + oeo[i]);
+            const T s3 = (eoo[i - Q - P] + eoo[i - Q]) + (eoo[i - P] + eoo[i]);
+            mag.eee.p[i] = (T(12) * eee[i] + (s1 + s2 + s3)) * T(1.0 / 24.0);
+        }
+        mag.ooo.p[i] = ((eoo[i] + eoo[i + 1]) + (oeo[i] + oeo[i + P]) + (ooe[i] + ooe[i + Q])) * T(1.0 / 6.0);
+    }
+}
+
+// Eq. Erblu (magenta -> blue), cells [1, nb]^3; blue shares the coset layout
+template <typename T>
+__global__ void __launch_bounds__(256) k_m2b_zm_3d(Mag3<const T> mag, A3<T> blue, int nb, int zm, const int *done, Bt B) {
+    const int prob = bt_prob(B);
+    if (stop(bt_done(done, prob, B))) return;
+    mag = bt_at(mag, prob, B);
+    blue = bt_at(blue, prob, B);
+    const int P = mag.eee.pitch;
+    const size_t Q = (size_t)P * mag.eee.rows;
+    ZmIdx z;
+    if (!zm_cell(z, 1, nb, zm, P, Q, B)) return;
+    const T *ooo = mag.ooo.p;
+    size_t i = z.i;
+    for (int c = z.c0; c < z.c1; c++, i += Q) {
+        const size_t m = i - Q;
+        const T ctr = ((ooo[m - P - 1] + ooo[m - P]) + (ooo[m - 1] + ooo[m])) +
+                      ((ooo[i - P - 1] + ooo[i - P]) + (ooo[i - 1] + ooo[i]));
+        blue.p[i] = (T(8) * mag.eee.p[i] + ctr) * T(0.0625);
+    }
+}
+
+// Eq. Emprolm: magenta centres from the 8 blue corners, cells [0, nb]^3
+template <typename T>
+__global__ void __launch_bounds__(256) k_b2m_ooo_zm_3d(A3<const T> blue, A3<const T> rooo, A3<T> vooo, int nb, T cc,
+                                                       int zm, const int *done, Bt B) {
+    const int prob = bt_prob(B);
+    if (stop(bt_done(done, prob, B))) return;
+    blue = bt_at(blue, prob, B); rooo = bt_at(rooo, prob, B); vooo = bt_at(vooo, prob, B);
+    const int P = rooo.pitch;
+    const size_t Q = (size_t)P * rooo.rows;
+    ZmIdx z;
+    if (!zm_cell(z, 0, nb, zm, P, Q, B)) return;
+    const T *bl = blue.p;
+    size_t i = z.i;
+    for (int c = z.c0; c < z.c1; c++, i += Q) {
+        const size_t u = i + Q;
+        const T s = ((bl[i] + bl[i + 1]) + (bl[i + P] + bl[i + P + 1])) +
+                    ((bl[u] + bl[u + 1]) + (bl[u + P] + bl[u + P + 1]));
+        vooo.p[i] = (s - cc * rooo.p[i]) * T(0.125);
+    }
+}
+
+// Eq. Emprolb: blue corners refined from the 8 new centres, cells [1, nb]^3
+template <typename T>
+__global__ void __launch_bounds__(256) k_b2m_eee_zm_3d(A3<const T> vooo, A3<const T> reee, A3<T> veee, int nb, T cc,
+                                                       int zm, const int *done, Bt B) {
+    const int prob = bt_prob(B);
+    if (stop(bt_done(done, prob, B))) return;
+    vooo = bt_at(vooo, prob, B); reee = bt_at(reee, prob, B); veee = bt_at(veee, prob, B);
+    const int P = reee.pitch;
+    const size_t Q = (size_t)P * reee.rows;
+    ZmIdx z;
+    if (!zm_cell(z, 1, nb, zm, P, Q, B)) return;
+    const T *o = vooo.p;
+    size_t i = z.i;
+    for (int c = z.c0; c < z.c1; c++, i += Q) {
+        const size_t m = i - Q;
+        const T ctr = ((o[m - P - 1] + o[m - P]) + (o[m - 1] + o[m])) + ((o[i - P - 1] + o[i - P]) + (o[i - 1] + o[i]));
+        veee.p[i] = (ctr - cc * reee.p[i]) * T(0.125);
+    }
+}
+
+// Eq. Erprolr and its cyclic permutations: red face centres, cells [0, nb]^3
+template <typename T>
+__global__ void __launch_bounds__(256) k_m2r_faces_zm_3d(Mag3<const T> vm, Red3<const T> rr, Red3<T> vr, int nb, T c1,
+                                                         int zm, const int *done, Bt B) {
+    const int prob = bt_prob(B);
+    if (stop(bt_done(done, prob, B))) return;
+    vm = bt_at(vm, prob, B); rr = bt_at(rr, prob, B); vr = bt_at(vr, prob, B);
+    const int P = vm.eee.pitch;
+    const size_t Q = (size_t)P * vm.eee.rows;
+    ZmIdx z;
+    if (!zm_cell(z, 0, nb, zm, P, Q, B)) return;
+    const T *o = vm.ooo.p, *e = vm.eee.p;
+    size_t i = z.i;
+    for (int c = z.c0; c < z.c1; c++, i += Q) {
+        if (c >= 1) {  // (2a+1, 2b+1, 2c): normal z
+            const T ctr = o[i - Q] + o[i];
+            const T cor = (e[i] + e[i + 1]) + (e[i + P] + e[i + P + 1]);
+            vr.ooe.p[i] = (T(2) * ctr + cor - c1 * rr.ooe.p[i]) * T(0.125);
+        }
+        if (z.b >= 1) {  // (2a+1, 2b, 2c+1): normal y
+            const T ctr = o[i - P] + o[i];
+            const T cor = (e[i] + e[i + 1]) + (e[i + Q] + e[i + Q + 1]);
+            vr.oeo.p[i] = (T(2) * ctr + cor - c1 * rr.oeo.p[i]) * T(0.125);
+        }
+        if (z.a >= 1) {  // (2a, 2b+1, 2c+1): normal x
+            const T ctr = o[i - 1] + o[i];
+            const T cor = (e[i] + e[i + P]) + (e[i + Q] + e[i + Q + P]);
+            vr.eoo.p[i] = (T(2) * ctr + cor - c1 * rr.eoo.p[i]) * T(0.125);
+        }
+    }
+}
+
+// Eq. Erprolm: magenta corners (red EEE) from the 12 new face centres, cells [1, nb]^3
+template <typename T>
+__global__ void __launch_bounds__(256) k_m2r_corners_zm_3d(Red3<const T> vf, A3<const T> reee, A3<T> veee, int nb, T c2,
+                                                           int zm, const int *done, Bt B) {
+    const int prob = bt_prob(B);
+    if (stop(bt_done(done, prob, B))) return;
+    vf = bt_at(vf, prob, B); reee = bt_at(reee, prob, B); veee = bt_at(veee, prob, B);
+    const int P = reee.pitch;
+    const size_t Q = (size_t)P * reee.rows;
+    ZmIdx z;
+    if (!zm_cell(z, 1, nb, zm, P, Q, B)) return;
+    const T *ooe = vf.ooe.p, *oeo = vf.oeo.p, *eoo = vf.eoo.p;
+    size_t i = z.i;
+    for (int c = z.c0; c < z.c1; c++, i += Q) {
+        const T s1 = (ooe[i - P - 1] + ooe[i - P]) + (ooe[i - 1] + ooe[i]);
+        const T s2 = (oeo[i - Q - 1] + oeo[i - Q]) + (oeo[i - 1] + oeo[i]);
+        const T s3 = (eoo[i - Q - P] + eoo[i - Q]) + (eoo[i - P] + eoo[i]);
+        veee.p[i] = ((s1 + s2 + s3) - c2 * reee.p[i]) * T(1.0 / 12.0);
+    }
+}
+
+}  // namespace mg
