@@ -99,6 +99,7 @@ struct mg_ctx {
     // tuned choices (mg_tune): tile class per pair for the down / up kernels
     // (-1: the size rule), side cut-off of the coarse thread block (0: default)
     int tile_dn[32], tile_up[32];
+    int gs_resident = 608;      // resident blocks of k_green_ff_3d on this device
     int cut_side = 0;
     // 3D diagonal path: triples with side <= 15 in one thread block
     bool fast3d = false;
@@ -377,13 +378,15 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
 // second half-sweep also applies u += v
 // z range (output planes per block) of k_green_ff_3d: about 600 blocks, at
 // most 64 and at least 8 planes each
-int green_ff_zch(int n) {
+// z range of a block: the grid fills the resident block slots once (a second,
+// partial wave would double the time of a launch), at least 8 planes
+int green_ff_zch(const mg_ctx *c, int n) {
     const int cols = ((n + GS_TX - 1) / GS_TX) * ((n + GS_TY - 1) / GS_TY);
-    const int chunks = (600 + cols - 1) / cols;
-    return std::max(8, std::min(64, (n + chunks - 1) / chunks));
+    const int chunks = std::max(1, c->gs_resident / (cols * c->nprob));
+    return std::max(8, (n + chunks - 1) / chunks);
 }
-dim3 green_ff_grid(int n) {
-    const int zch = green_ff_zch(n);
+dim3 green_ff_grid(const mg_ctx *c, int n) {
+    const int zch = green_ff_zch(c, n);
     return dim3((n + GS_TX - 1) / GS_TX, (n + GS_TY - 1) / GS_TY, (n + zch - 1) / zch);
 }
 // the z-streaming green sweep pays GS_WARM steps per z range: used from 255^3 up
@@ -409,9 +412,9 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
             else
                 LAUNCH_B(TAG_UP, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
         } else if (c->d.hierarchy == MG_DIAG && sizeof(T) == 4 && green_ff_use(n)) {  // FP32, z-streaming
-            const dim3 g3 = green_ff_grid(n);
+            const dim3 g3 = green_ff_grid(c, n);
             const size_t sm = sizeof(GreenSSmem);
-            const int zch = green_ff_zch(n);
+            const int zch = green_ff_zch(c, n);
             if (u)
                 LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_ff_3d<UP_ADD>), g3, dim3(32, 8, 1), sm,
                               red3v<const float>(b.v, b), a3<float>(a.r[0], a), (float *)nullptr, a3<float>(a.v[0], a),
@@ -781,11 +784,11 @@ int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     const Level &a = c->lv[0], &b = c->lv[1];
     const int n = c->d.n;
     const double h2 = c->h * c->h;
-    const dim3 g3 = green_ff_grid(n);
+    const dim3 g3 = green_ff_grid(c, n);
     LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_ff_3d<UP_RR>), g3, dim3(32, 8, 1), sizeof(GreenSSmem),
                   red3v<const float>(b.v, b), a3<float>(a.r[0], a), (float *)c->r32b, a3<float>(a.v[0], a),
                   (float *)c->rlo, u, c->d.pitch, n, (float)(c->d.omega[3] * h2), (float)(1.0 / h2),
-                  green_ff_zch(n), c->part, &c->ctl->par, done);
+                  green_ff_zch(c, n), c->part, &c->ctl->par, done);
     return (int)(g3.x * g3.y * g3.z);
 }
 
@@ -951,6 +954,12 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<UP_RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<UP_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<UP_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
+        if (e == cudaSuccess) {
+            int per_sm = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_green_ff_3d<UP_RR>, 256, gs);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+            if (e == cudaSuccess) c->gs_resident = std::max(1, per_sm * sms);
+        }
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<float, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
