@@ -632,7 +632,7 @@ int tile_dn(const mg_ctx *c, int k) { return c->tile_dn[k] >= 0 ? c->tile_dn[k] 
 int tile_up(const mg_ctx *c, int k) { return c->tile_up[k] >= 0 ? c->tile_up[k] : tile_default(c, k, true); }
 
 void launch_down_ff(mg_ctx *c, int k, int cls, const int *done, cudaStream_t s, bool alt);
-int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s);
+int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s, bool rr);
 
 template <typename T> void down_pair(mg_ctx *c, int k, int cls, const int *done, cudaStream_t s, bool alt) {
     if (sizeof(T) == 4) {
@@ -645,12 +645,13 @@ template <typename T> void down_pair(mg_ctx *c, int k, int cls, const int *done,
     default: launch_down_pair<T, 8, 8>(c, k, done, s, alt); break;
     }
 }
-// returns the partial sums written per problem (the finest pair of the fused
-// mixed solve) or 0
-template <typename T> int up_pair(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s) {
+// rr: the finest pair of the fused mixed solve (u += v with the carried
+// residual; streaming only); returns the partial sums it wrote per problem, or 0
+template <typename T>
+int up_pair(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s, bool rr = false) {
     if (sizeof(T) == 4) {
-        if (k == 0 && c->rr) return launch_up_ff(c, 0, cls < 3 ? cls : 0, u, done, s);
-        if (cls < 3) return launch_up_ff(c, k, cls, u, done, s);
+        if (rr) return launch_up_ff(c, 0, cls < 3 ? cls : 0, u, done, s, true);
+        if (cls < 3) return launch_up_ff(c, k, cls, u, done, s, false);
         cls -= 3;
     }
     switch (cls) {
@@ -700,12 +701,12 @@ void launch_down_ff(mg_ctx *c, int k, int cls, const int *done, cudaStream_t s, 
 // solve with the carried residual (rr), the finest pair otherwise with u += v,
 // a coarser pair with v stored; returns the partial sums written per problem
 // (rr) or 0
-int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s) {
+int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s, bool rr) {
     const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
     const int nb = r.nb, tb = ff_strip(cls);
     const double hk = spacing(c, g), p = c->d.omega[0];
     const int items = ((nb + FF_W) / FF_W) * ((nb + tb) / tb);
-    const bool rr = k == 0 && c->rr, add = k == 0 && !c->rr;
+    const bool add = k == 0 && !rr;
     const dim3 grid = ff_grid(items);
     const dim3 blk(32, FF_WARPS, 1);
     const bool vu = k == 0 && c->nprob == 1 && ((uintptr_t)u % 16) == 0 && c->d.pitch % 2 == 0;
@@ -739,7 +740,7 @@ int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
                       a2<const float>(g.r[0], g), a2<float>(g.v[0], g), c->G, done);
     }
     for (int k = c->kc - 1; k >= 1; k--) up_pair<float>(c, k, tile_up(c, k), u, done, s);
-    return up_pair<float>(c, 0, tile_up(c, 0), u, done, s);
+    return up_pair<float>(c, 0, tile_up(c, 0), u, done, s, true);
 }
 
 // direct FP64 residual of the fused path.  start: the carried float-float
@@ -1695,7 +1696,7 @@ mg_status tune_measure(mg_ctx *c, const double *f, double *u, cudaStream_t s) {
                 float mu;
                 if (k == 0 && c->rr) {
                     if (cls >= 3) continue;  // the fused finest pair exists only as a streaming kernel
-                    mu = timeit([&] { launch_up_ff(c, 0, cls, u, nullptr, s); }, 5);
+                    mu = timeit([&] { launch_up_ff(c, 0, cls, u, nullptr, s, true); }, 5);
                 } else {
                     mu = fp64 ? timeit([&] { up_pair<double>(c, k, cls, k == 0 ? u : nullptr, nullptr, s); }, 5)
                               : timeit([&] { up_pair<float>(c, k, cls, k == 0 ? u : nullptr, nullptr, s); }, 5);

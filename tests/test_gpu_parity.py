@@ -80,8 +80,9 @@ def oracle_prolong(dim, hier, kind, vc, r, h, om):
     return O.prolong3d_r2g(vc, r, h, om[3])
 
 
+# (3, 127): the triple 127^3 has 64^3 cells, where the stage kernels march in z
 STAGE_CASES = [(2, 63, "diag"), (2, 127, "diag"), (2, 63, "usual"), (3, 15, "diag"), (3, 31, "diag"),
-               (3, 15, "usual")]
+               (3, 127, "diag"), (3, 15, "usual")]
 
 
 @pytest.mark.parametrize("dim,n,hier", STAGE_CASES)
@@ -205,6 +206,25 @@ def test_vcycle_iterates_match_oracle(dim, n, hier, order, om):
             got = H(ug)
             rel = np.linalg.norm(got - uo) / np.linalg.norm(uo)
             assert rel <= TOL, f"cycle {cyc}: rel {rel:.3e}"
+
+
+@pytest.mark.parametrize("dim,n,om", [(2, 511, (1.052,)), (2, 2047, (1.052,)), (3, 127, (1.11, 1.42, 1.08, 0.99)),
+                                      (3, 255, (1.11, 1.42, 1.08, 0.99))])
+def test_mixed_vcycle_iterates_follow_oracle(dim, n, om):
+    """The FP32 level kernels of the mixed path (the warp-streaming pair
+    kernels in 2D, the z-streaming and z-marching triple kernels in 3D) give
+    the oracle's V-cycle iterates to FP32 accuracy: any wrong index or
+    coefficient would show as an O(1) relative difference."""
+    f = I.uniform_f(dim, n, 3) if dim == 2 else I.cube(n)
+    uo = O.grid(dim, n)
+    with Context(dim, n, precision="mixed", omega=om) as c:
+        ug = c.new_grid()
+        ft = T(f)
+        for cyc in range(2):
+            O.vcycle(f, uo, omega=list(om))
+            c.vcycle(ft, ug)
+            rel = np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo)
+            assert rel <= 2e-6, f"cycle {cyc}: rel {rel:.3e}"
 
 
 @pytest.mark.parametrize("coarsest", [1, 3, 7])
