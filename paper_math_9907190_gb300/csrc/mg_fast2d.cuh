@@ -286,24 +286,24 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const
     rg_in = bt_at(rg_in, prob, B);
     vg_out = bt_at(vg_out, prob, B);
     const int tid = threadIdx.x, nt = blockDim.x;
+    // 32 x 32 thread grid: loops over boxes step by 32, no index division
+    const int tx = tid & 31, ty = tid >> 5;
+#define CTA_FOR2(i, j, lo_i, hi_i, lo_j, hi_j) \
+    for (int j = (lo_j) + ty; j <= (hi_j); j += 32) for (int i = (lo_i) + tx; i <= (hi_i); i += 32)
     for (int q = tid; q < P.total; q += nt) sm[q] = T(0);
     __syncthreads();
     const int npair = P.K - P.kc;
     {   // load the green residual of pair kc
         const int n = P.nk[0];
         A2<T> g{sm + P.og_r[0], n + 2};
-        for (int q = tid; q < n * n; q += nt) {
-            const int i = q % n + 1, j = q / n + 1;
-            g(i, j) = rg_in(i, j);
-        }
+        CTA_FOR2(i, j, 1, n, 1, n) g(i, j) = rg_in(i, j);
     }
     __syncthreads();
     for (int p = 0; p < npair; p++) {
         const int n = P.nk[p], nb = (n - 1) / 2;
         A2<T> g{sm + P.og_r[p], n + 2}, ee{sm + P.oe_r[p], nb + 2}, oo{sm + P.oo_r[p], nb + 2};
         A2<T> bl{sm + P.og_r[p + 1], nb + 2};
-        for (int q = tid; q < (nb + 1) * (nb + 1); q += nt) {  // Eq. Erest2r
-            const int a = q % (nb + 1), b = q / (nb + 1);
+        CTA_FOR2(a, b, 0, nb, 0, nb) {  // Eq. Erest2r
             int i = 2 * a + 1, j = 2 * b + 1;
             oo(a, b) = (T(4) * g(i, j) + (g(i - 1, j) + g(i + 1, j)) + (g(i, j - 1) + g(i, j + 1))) * T(0.125);
             if (a >= 1 && b >= 1) {
@@ -312,8 +312,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const
             }
         }
         __syncthreads();
-        for (int q = tid; q < nb * nb; q += nt) {  // Eq. Erest2b
-            const int a = q % nb + 1, b = q / nb + 1;
+        CTA_FOR2(a, b, 1, nb, 1, nb) {  // Eq. Erest2b
             bl(a, b) = (T(4) * ee(a, b) + (oo(a - 1, b - 1) + oo(a, b - 1)) + (oo(a - 1, b) + oo(a, b))) * T(0.125);
         }
         __syncthreads();
@@ -335,26 +334,22 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const
         A2<T> vee{sm + P.oe_v[p], nb + 2}, voo{sm + P.oo_v[p], nb + 2};
         A2<T> vbl{sm + P.og_v[p + 1], nb + 2};
         const T c2 = (T)P.c2[p], c1 = (T)P.c1[p];
-        for (int q = tid; q < (nb + 1) * (nb + 1); q += nt) {  // Eq. Eajacr
-            const int a = q % (nb + 1), b = q / (nb + 1);
+        CTA_FOR2(a, b, 0, nb, 0, nb) {  // Eq. Eajacr
             voo(a, b) = ((vbl(a, b) + vbl(a + 1, b)) + (vbl(a, b + 1) + vbl(a + 1, b + 1)) - c2 * roo(a, b)) * T(0.25);
         }
         __syncthreads();
-        for (int q = tid; q < nb * nb; q += nt) {  // Eq. Eajacb
-            const int a = q % nb + 1, b = q / nb + 1;
+        CTA_FOR2(a, b, 1, nb, 1, nb) {  // Eq. Eajacb
             vee(a, b) = ((voo(a - 1, b - 1) + voo(a, b - 1)) + (voo(a - 1, b) + voo(a, b)) - c2 * ree(a, b)) * T(0.25);
         }
         __syncthreads();
-        for (int q = tid; q < n * n; q += nt) {  // green-only points
-            const int i = q % n + 1, j = q / n + 1;
-            if (((i + j) & 1) == 0) continue;
+        for (int j = 1 + ty; j <= n; j += 32)  // green-only points: i + j odd
+            for (int i = 1 + (j & 1) + 2 * tx; i <= n; i += 64) {
             auto red = [&](int x, int y) { return (x & 1) ? voo(x >> 1, y >> 1) : vee(x >> 1, y >> 1); };
             vgr(i, j) = ((red(i - 1, j) + red(i + 1, j)) + (red(i, j - 1) + red(i, j + 1)) - c1 * rgr(i, j)) * T(0.25);
         }
         __syncthreads();
-        for (int q = tid; q < n * n; q += nt) {  // red points
-            const int i = q % n + 1, j = q / n + 1;
-            if ((i + j) & 1) continue;
+        for (int j = 1 + ty; j <= n; j += 32)  // red points: i + j even
+            for (int i = 2 - (j & 1) + 2 * tx; i <= n; i += 64) {
             vgr(i, j) = ((vgr(i - 1, j) + vgr(i + 1, j)) + (vgr(i, j - 1) + vgr(i, j + 1)) - c1 * rgr(i, j)) * T(0.25);
         }
         __syncthreads();
@@ -362,11 +357,9 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const
     {
         const int n = P.nk[0];
         A2<T> g{sm + P.og_v[0], n + 2};
-        for (int q = tid; q < n * n; q += nt) {
-            const int i = q % n + 1, j = q / n + 1;
-            vg_out(i, j) = g(i, j);
-        }
+        CTA_FOR2(i, j, 1, n, 1, n) vg_out(i, j) = g(i, j);
     }
+#undef CTA_FOR2
 }
 
 }  // namespace mg
@@ -483,6 +476,12 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
     rg_in = bt_at(rg_in, prob, B);
     vg_out = bt_at(vg_out, prob, B);
     const int tid = threadIdx.x, nt = blockDim.x;
+    // 16 x 8 x 8 thread grid: loops over boxes without index division
+    const int tx = tid & 15, ty = (tid >> 4) & 7, tz = tid >> 7;
+#define CTA_FOR3(i, j, k, lo, hi)                                        \
+    for (int k = (lo) + tz; k <= (hi); k += 8)                            \
+        for (int j = (lo) + ty; j <= (hi); j += 8)                        \
+            for (int i = (lo) + tx; i <= (hi); i += 16)
     for (int q = tid; q < P.total; q += nt) sm[q] = T(0);
     __syncthreads();
     const int ntri = P.K - P.kc;
@@ -491,10 +490,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
     {
         const int n = P.nk[0];
         A3<T> g = G3(P.og_r[0], n);
-        for (int q = tid; q < n * n * n; q += nt) {
-            const int i = q % n + 1, j = (q / n) % n + 1, k = q / (n * n) + 1;
-            g(i, j, k) = rg_in(i, j, k);
-        }
+        CTA_FOR3(i, j, k, 1, n) g(i, j, k) = rg_in(i, j, k);
     }
     __syncthreads();
     for (int t = 0; t < ntri; t++) {
@@ -503,8 +499,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
         A3<T> eee = C3(P.orr[t][0], nb), ooe = C3(P.orr[t][1], nb), oeo = C3(P.orr[t][2], nb), eoo = C3(P.orr[t][3], nb);
         A3<T> me = C3(P.omr[t][0], nb), mo = C3(P.omr[t][1], nb);
         A3<T> bl = G3(P.og_r[t + 1], nb);
-        for (int q = tid; q < nc * nc * nc; q += nt) {  // Eq. Erred
-            const int a = q % nc, b = (q / nc) % nc, c = q / (nc * nc);
+        CTA_FOR3(a, b, c, 0, nb) {  // Eq. Erred
             auto avg = [&](int i, int j, int k) {
                 return (T(6) * g(i, j, k) + (g(i + 1, j, k) + g(i - 1, j, k)) + (g(i, j + 1, k) + g(i, j - 1, k)) +
                         (g(i, j, k + 1) + g(i, j, k - 1))) * T(1.0 / 12.0);
@@ -515,8 +510,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
             if (a >= 1) eoo(a, b, c) = avg(2 * a, 2 * b + 1, 2 * c + 1);
         }
         __syncthreads();
-        for (int q = tid; q < nc * nc * nc; q += nt) {  // Eq. Ermagc, Eq. Ermagm
-            const int a = q % nc, b = (q / nc) % nc, c = q / (nc * nc);
+        CTA_FOR3(a, b, c, 0, nb) {  // Eq. Ermagc, Eq. Ermagm
             if (a >= 1 && b >= 1 && c >= 1)
                 me(a, b, c) = (T(12) * eee(a, b, c) +
                                fcc12(A3<const T>{ooe.p, ooe.pitch, ooe.rows}, A3<const T>{oeo.p, oeo.pitch, oeo.rows},
@@ -525,8 +519,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
                            (ooe(a, b, c) + ooe(a, b, c + 1))) * T(1.0 / 6.0);
         }
         __syncthreads();
-        for (int q = tid; q < nb * nb * nb; q += nt) {  // Eq. Erblu
-            const int a = q % nb + 1, b = (q / nb) % nb + 1, c = q / (nb * nb) + 1;
+        CTA_FOR3(a, b, c, 1, nb) {  // Eq. Erblu
             bl(a, b, c) = (T(8) * me(a, b, c) + ctr8(A3<const T>{mo.p, mo.pitch, mo.rows}, a, b, c)) * T(0.0625);
         }
         __syncthreads();
@@ -548,20 +541,17 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
         A3<T> v_e = C3(P.orv[t][0], nb), v_ooe = C3(P.orv[t][1], nb), v_oeo = C3(P.orv[t][2], nb), v_eoo = C3(P.orv[t][3], nb);
         A3<T> rme = C3(P.omr[t][0], nb), rmo = C3(P.omr[t][1], nb), vme = C3(P.omv[t][0], nb), vmo = C3(P.omv[t][1], nb);
         const T cm = (T)P.cm[t], c1 = (T)P.cr1[t], c2 = (T)P.cr2[t], cg = (T)P.cg[t];
-        for (int q = tid; q < nc * nc * nc; q += nt) {  // Eq. Emprolm: centres
-            const int a = q % nc, b = (q / nc) % nc, c = q / (nc * nc);
+        CTA_FOR3(a, b, c, 0, nb) {  // Eq. Emprolm: centres
             T s = ((vb(a, b, c) + vb(a + 1, b, c)) + (vb(a, b + 1, c) + vb(a + 1, b + 1, c))) +
                   ((vb(a, b, c + 1) + vb(a + 1, b, c + 1)) + (vb(a, b + 1, c + 1) + vb(a + 1, b + 1, c + 1)));
             vmo(a, b, c) = (s - cm * rmo(a, b, c)) * T(0.125);
         }
         __syncthreads();
-        for (int q = tid; q < nb * nb * nb; q += nt) {  // Eq. Emprolb: blue corners
-            const int a = q % nb + 1, b = (q / nb) % nb + 1, c = q / (nb * nb) + 1;
+        CTA_FOR3(a, b, c, 1, nb) {  // Eq. Emprolb: blue corners
             vme(a, b, c) = (ctr8(A3<const T>{vmo.p, vmo.pitch, vmo.rows}, a, b, c) - cm * rme(a, b, c)) * T(0.125);
         }
         __syncthreads();
-        for (int q = tid; q < nc * nc * nc; q += nt) {  // Eq. Erprolr: red face centres
-            const int a = q % nc, b = (q / nc) % nc, c = q / (nc * nc);
+        CTA_FOR3(a, b, c, 0, nb) {  // Eq. Erprolr: red face centres
             if (c >= 1) {
                 T ctr = vmo(a, b, c - 1) + vmo(a, b, c);
                 T cor = (vme(a, b, c) + vme(a + 1, b, c)) + (vme(a, b + 1, c) + vme(a + 1, b + 1, c));
@@ -579,25 +569,24 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
             }
         }
         __syncthreads();
-        for (int q = tid; q < nb * nb * nb; q += nt) {  // Eq. Erprolm: magenta corners
-            const int a = q % nb + 1, b = (q / nb) % nb + 1, c = q / (nb * nb) + 1;
+        CTA_FOR3(a, b, c, 1, nb) {  // Eq. Erprolm: magenta corners
             v_e(a, b, c) = (fcc12(A3<const T>{v_ooe.p, v_ooe.pitch, v_ooe.rows}, A3<const T>{v_oeo.p, v_oeo.pitch, v_oeo.rows},
                                   A3<const T>{v_eoo.p, v_eoo.pitch, v_eoo.rows}, a, b, c) - c2 * r_e(a, b, c)) * T(1.0 / 12.0);
         }
         __syncthreads();
         Red3<const T> vr{A3<const T>{v_e.p, v_e.pitch, v_e.rows}, A3<const T>{v_ooe.p, v_ooe.pitch, v_ooe.rows},
                          A3<const T>{v_oeo.p, v_oeo.pitch, v_oeo.rows}, A3<const T>{v_eoo.p, v_eoo.pitch, v_eoo.rows}};
-        for (int q = tid; q < n * n * n; q += nt) {  // Eq. Egprolg: green-only points
-            const int i = q % n + 1, j = (q / n) % n + 1, k = q / (n * n) + 1;
-            if (((i + j + k) & 1) == 0) continue;
+        for (int k = 1 + tz; k <= n; k += 8)  // Eq. Egprolg: green-only points, i + j + k odd
+            for (int j = 1 + ty; j <= n; j += 8)
+                for (int i = 1 + ((j + k) & 1) + 2 * tx; i <= n; i += 32) {
             T s = (red3(vr, i - 1, j, k) + red3(vr, i + 1, j, k)) + (red3(vr, i, j - 1, k) + red3(vr, i, j + 1, k)) +
                   (red3(vr, i, j, k - 1) + red3(vr, i, j, k + 1));
             vg(i, j, k) = (s - cg * rg(i, j, k)) * T(1.0 / 6.0);
         }
         __syncthreads();
-        for (int q = tid; q < n * n * n; q += nt) {  // Eq. Egprolr: red points
-            const int i = q % n + 1, j = (q / n) % n + 1, k = q / (n * n) + 1;
-            if ((i + j + k) & 1) continue;
+        for (int k = 1 + tz; k <= n; k += 8)  // Eq. Egprolr: red points, i + j + k even
+            for (int j = 1 + ty; j <= n; j += 8)
+                for (int i = 2 - ((j + k) & 1) + 2 * tx; i <= n; i += 32) {
             T s = (vg(i - 1, j, k) + vg(i + 1, j, k)) + (vg(i, j - 1, k) + vg(i, j + 1, k)) +
                   (vg(i, j, k - 1) + vg(i, j, k + 1));
             vg(i, j, k) = (s - cg * rg(i, j, k)) * T(1.0 / 6.0);
@@ -607,11 +596,9 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
     {
         const int n = P.nk[0];
         A3<T> g = G3(P.og_v[0], n);
-        for (int q = tid; q < n * n * n; q += nt) {
-            const int i = q % n + 1, j = (q / n) % n + 1, k = q / (n * n) + 1;
-            vg_out(i, j, k) = g(i, j, k);
-        }
+        CTA_FOR3(i, j, k, 1, n) vg_out(i, j, k) = g(i, j, k);
     }
+#undef CTA_FOR3
 }
 
 }  // namespace mg
