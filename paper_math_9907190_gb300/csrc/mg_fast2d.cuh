@@ -1099,15 +1099,25 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
 #pragma unroll
         for (int q = 0; q < RES_ROWS; q++) fr[q] = q < rows ? f0p[(size_t)q * up] : 0.0;
         bool zero = false;
-        if (START) {  // u and its neighbours zero at every point of the thread?
+        if (START) {  // u zero on the thread's column (rows j0-1 .. j0+rows)?
             unsigned ob = mag_bits(u0p[-up]) | mag_bits(u0p[(size_t)rows * up]);
 #pragma unroll
-            for (int q = 0; q < RES_ROWS; q++) {
-                if (q >= rows) break;
-                const double *c = u0p + (size_t)q * up;
-                ob |= mag_bits(c[-1]) | mag_bits(c[0]) | mag_bits(c[1]);
+            for (int q = 0; q < RES_ROWS; q++)
+                if (q < rows) ob |= mag_bits(u0p[(size_t)q * up]);
+            // the x neighbours are the adjacent lanes' columns; the first and
+            // the last active lane also test the column beyond them
+            const unsigned act = __activemask();
+            const bool first = (int)threadIdx.x == __ffs(act) - 1, last = (int)threadIdx.x == 31 - __clz(act);
+            if (first || last) {
+                const int dx = first ? -1 : 1;
+#pragma unroll
+                for (int q = 0; q < RES_ROWS; q++) {
+                    if (q >= rows) break;
+                    ob |= mag_bits(u0p[(size_t)q * up + dx]);
+                    if (first && last) ob |= mag_bits(u0p[(size_t)q * up + 1]);
+                }
             }
-            zero = ob == 0;
+            zero = ob == 0;  // with __all_sync below: every neighbour of every point of the warp
         }
         // warp-uniform: either no FP64 arithmetic at all (two separate loops,
         // so that the stencil is branched over rather than predicated) or the
@@ -1395,24 +1405,38 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
     const int k0 = bz * RES3_PLANES + 1;
     const size_t pl = (size_t)up * (n + 2), pr = (size_t)rp * (n + 2);
     float acc = 0.f, facc = 0.f;
-    if (i <= n && j <= n) {
-        const double *u0p = u + k0 * pl + (size_t)j * up + i;
-        const double *f0p = f + k0 * pl + (size_t)j * up + i;
-        const int planes = min(RES3_PLANES, n + 1 - k0);
-        double fr[RES3_PLANES];
-#pragma unroll
-        for (int q = 0; q < RES3_PLANES; q++) fr[q] = q < planes ? f0p[(size_t)q * pl] : 0.0;
-        bool zero = false;
-        if (START) {  // u and its neighbours zero at every point of the thread?
-            unsigned ob = mag_bits(u0p[-(long)pl]) | mag_bits(u0p[(size_t)planes * pl]);
+    const bool act = i <= n && j <= n;
+    const int planes = act ? min(RES3_PLANES, n + 1 - k0) : 0;
+    const double *u0p = u + k0 * pl + (size_t)(act ? j : 1) * up + (act ? i : 1);
+    const double *f0p = f + k0 * pl + (size_t)(act ? j : 1) * up + (act ? i : 1);
+    // u zero around every point of the block? (START only; block-uniform)
+    bool all_zero = false;
+    if (START) {
+        unsigned ob = 0;
+        if (act && planes > 0) {
+            // the thread's column (planes k0-1 .. k0+planes); x and y neighbours
+            // are other threads' columns, the block's edge threads test the
+            // columns beyond the block
+            ob = mag_bits(u0p[-(long)pl]) | mag_bits(u0p[(size_t)planes * pl]);
+            const bool xl = threadIdx.x == 0, xr = threadIdx.x == 31 || i == n;
+            const bool yl = threadIdx.y == 0, yr = threadIdx.y == 7 || j == n;
 #pragma unroll
             for (int q = 0; q < RES3_PLANES; q++) {
                 if (q >= planes) break;
                 const double *c = u0p + (size_t)q * pl;
-                ob |= mag_bits(c[-1]) | mag_bits(c[0]) | mag_bits(c[1]) | mag_bits(c[-up]) | mag_bits(c[up]);
+                ob |= mag_bits(c[0]);
+                if (xl) ob |= mag_bits(c[-1]);
+                if (xr) ob |= mag_bits(c[1]);
+                if (yl) ob |= mag_bits(c[-up]);
+                if (yr) ob |= mag_bits(c[up]);
             }
-            zero = ob == 0;
         }
+        all_zero = __syncthreads_and(ob == 0) != 0;
+    }
+    if (act && planes > 0) {
+        double fr[RES3_PLANES];
+#pragma unroll
+        for (int q = 0; q < RES3_PLANES; q++) fr[q] = q < planes ? f0p[(size_t)q * pl] : 0.0;
         auto planes_loop = [&](auto zero_tag) {
             constexpr bool Z = decltype(zero_tag)::value;
             const double *uc = u0p;
@@ -1443,7 +1467,7 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
                 uc += pl;
             }
         };
-        if (__all_sync(__activemask(), zero)) planes_loop(std::true_type{});
+        if (all_zero) planes_loop(std::true_type{});
         else planes_loop(std::false_type{});
     }
     const size_t slot = (size_t)prob * B.nparts + blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz);
