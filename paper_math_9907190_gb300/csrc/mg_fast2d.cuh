@@ -1066,12 +1066,69 @@ __device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
     lo = (xh >> 31) ? -l : l;
 }
 
+// The Laplacian part of a direct residual in integer arithmetic (the FP64
+// pipe of this GPU would otherwise bound the residual kernels).  Each u of a
+// stencil is decoded into its signed 53-bit mantissa and exponent; all are
+// aligned to the largest exponent with 6 guard bits (the bits below 2^-59 of
+// the largest |u| are truncated) and summed exactly in 64 bits; the sum is
+// rounded once to a double, already scaled by 1/h^2 = 2^lg (a power of two).
+// Against the FP64 evaluation (4 to 7 roundings of partial sums) the result
+// is at least as accurate; one FP64 subtraction from f remains.
+struct Fx {
+    long long m;  // signed mantissa with the implicit bit (0 for zeros and subnormals)
+    int e;        // biased exponent
+};
+__device__ __forceinline__ Fx fx_dec(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const long long m = e ? (((long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo) : 0;
+    return Fx{(hi >> 31) ? -m : m, e};
+}
+__device__ __forceinline__ long long fx_al(const Fx &a, int emax) {  // a * 2^6, aligned to emax
+    const int k = emax - a.e;
+    return k > 62 ? 0 : ((a.m << 6) >> k);
+}
+// the double nearest to s * 2^q (round to nearest even), s a 64-bit integer
+__device__ __forceinline__ double fx_to_double(long long s, int q) {
+    if (s == 0) return 0.0;
+    const unsigned long long sg = s < 0 ? 0x8000000000000000ull : 0ull;
+    unsigned long long a = s < 0 ? 0ull - (unsigned long long)s : (unsigned long long)s;
+    const int lz = __clzll((long long)a);
+    a <<= lz;  // leading one at bit 63
+    unsigned long long m = a >> 11;
+    const unsigned rem = (unsigned)(a & 0x7ffull);
+    m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+    int ex = 63 - lz + q + 1023;
+    if (m >> 53) { m >>= 1; ex += 1; }
+    if (ex < 1) return 0.0;  // below the normal range: far under any residual of interest
+    return __longlong_as_double((long long)(sg | ((unsigned long long)ex << 52) | (m & 0xfffffffffffffull)));
+}
+// h^-2 (sum of the four neighbours - 4 centre), 2D; lg = log2(h^-2)
+__device__ __forceinline__ double fx_lap5(double c, double w, double e, double s, double n, int lg) {
+    const Fx C = fx_dec(c), W = fx_dec(w), E = fx_dec(e), S = fx_dec(s), N = fx_dec(n);
+    const int em = max(max(max(C.e, W.e), max(E.e, S.e)), N.e);
+    const long long t = (fx_al(W, em) + fx_al(E, em)) + (fx_al(S, em) + fx_al(N, em)) - (fx_al(C, em) << 2);
+    return fx_to_double(t, em - 1081 + lg);
+}
+// h^-2 (sum of the six neighbours - 6 centre), 3D
+__device__ __forceinline__ double fx_lap7(double c, double w, double e, double s, double n, double d, double u,
+                                          int lg) {
+    const Fx C = fx_dec(c), W = fx_dec(w), E = fx_dec(e), S = fx_dec(s), N = fx_dec(n), D = fx_dec(d), U = fx_dec(u);
+    const int em = max(max(max(C.e, W.e), max(E.e, S.e)), max(max(N.e, D.e), U.e));
+    const long long c6 = fx_al(C, em);
+    const long long t = ((fx_al(W, em) + fx_al(E, em)) + (fx_al(S, em) + fx_al(N, em))) + (fx_al(D, em) + fx_al(U, em)) -
+                        ((c6 << 2) + (c6 << 1));
+    return fx_to_double(t, em - 1081 + lg);
+}
+
 // OR of the magnitude bits of a double (zero iff +-0), in 32-bit operations
 __device__ __forceinline__ unsigned mag_bits(double x) {
     return ((unsigned)__double2hiint(x) << 1) | (unsigned)__double2loint(x);
 }
 
-// Direct FP64 residual r = f - L u (Eq. Evpois) of the fused mixed path.
+// Direct residual r = f - L u (Eq. Evpois) of the fused mixed path, the
+// Laplacian in exact integer arithmetic (fx_lap5 / fx_lap7) and one FP64
+// subtraction.
 // START (start of a solve): r as the float-float pair hi (the level's buffer
 // r) and lo (rlo, pitch rp), partial sums of hi^2 to part and of f^2 (FP32
 // squares: the norm of the right-hand side) to fpart.  Where u and its four
@@ -1080,7 +1137,7 @@ __device__ __forceinline__ unsigned mag_bits(double x) {
 // of a solve): only the partial sums of r^2, nothing written.
 template <bool START>
 __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f, const double *__restrict__ u,
-                                                   int up, int n, double ih2, A2<float> r, float *rlo, int rp,
+                                                   int up, int n, int lg, A2<float> r, float *rlo, int rp,
                                                    double *part, double *fpart, const int *done, Bt B) {
     __shared__ double sh[32];
     const int prob = blockIdx.z;
@@ -1133,8 +1190,7 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
                 double res = fv, upn = 0.0;
                 if (!Z) {
                     upn = uc[up];
-                    const double s = (uc[-1] + uc[1]) + (um + upn);
-                    res = fma(-ih2, fma(-4.0, u0, s), fv);
+                    res = fv - fx_lap5(u0, uc[-1], uc[1], um, upn, lg);
                 }
                 float hi;
                 if (START) {
@@ -1394,7 +1450,7 @@ __global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> 
 // RES3_PLANES planes per thread marching in z
 template <bool START>
 __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f, const double *__restrict__ u,
-                                                   int up, int n, double ih2, A3<float> r, float *rlo, int rp,
+                                                   int up, int n, int lg, A3<float> r, float *rlo, int rp,
                                                    double *part, double *fpart, const int *done, Bt B) {
     __shared__ double sh[32];
     const int prob = bt_prob(B), bz = bt_z(B);
@@ -1448,8 +1504,7 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
                 double res = fv, uu = 0.0;
                 if (!Z) {
                     uu = uc[pl];
-                    const double s = ((uc[-1] + uc[1]) + (uc[-up] + uc[up])) + (ud + uu);
-                    res = fma(-ih2, fma(-6.0, u0, s), fv);
+                    res = fv - fx_lap7(u0, uc[-1], uc[1], uc[-up], uc[up], ud, uu, lg);
                 }
                 float hi;
                 if (START) {

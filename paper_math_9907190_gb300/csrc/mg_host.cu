@@ -750,24 +750,24 @@ int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
 int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s, bool start) {
     const int n = c->d.n;
     const Level &l0 = c->lv[0];
-    const double ih2 = 1.0 / (c->h * c->h);
+    const int lg = 2 * c->m;  // log2(1/h^2), h = 2^-m
     dim3 g = c->d.dim == 3 ? dim3((n + 31) / 32, (n + 7) / 8, (n + RES3_PLANES - 1) / RES3_PLANES)
                            : dim3((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
     const int np = (int)(g.x * g.y * g.z);
     double *fpart = start ? c->part + (size_t)np * c->nprob : nullptr;
     if (c->d.dim == 3) {
         if (start)
-            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_3d<true>), g, B2, f, u, c->d.pitch, n, ih2, a3<float>(l0.r[0], l0),
+            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_3d<true>), g, B2, f, u, c->d.pitch, n, lg, a3<float>(l0.r[0], l0),
                      (float *)c->rlo, l0.pitch, c->part, fpart, done);
         else
-            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_3d<false>), g, B2, f, u, c->d.pitch, n, ih2, a3<float>(l0.r[0], l0),
+            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_3d<false>), g, B2, f, u, c->d.pitch, n, lg, a3<float>(l0.r[0], l0),
                      (float *)c->rlo, l0.pitch, c->part, fpart, done);
     } else {
         if (start)
-            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_2d<true>), g, B2, f, u, c->d.pitch, n, ih2, a2<float>(l0.r[0], l0),
+            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_2d<true>), g, B2, f, u, c->d.pitch, n, lg, a2<float>(l0.r[0], l0),
                      (float *)c->rlo, l0.pitch, c->part, fpart, done);
         else
-            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_2d<false>), g, B2, f, u, c->d.pitch, n, ih2, a2<float>(l0.r[0], l0),
+            LAUNCH_B(TAG_RESIDUAL, (k_res_rr_2d<false>), g, B2, f, u, c->d.pitch, n, lg, a2<float>(l0.r[0], l0),
                      (float *)c->rlo, l0.pitch, c->part, fpart, done);
     }
     c->nparts = np;
