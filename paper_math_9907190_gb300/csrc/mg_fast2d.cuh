@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(256) k_res0_2d(const double *__restrict__ f, c
 
 // ft = (8f + sum4 f)/12 on the interior (order-4 right-hand side of Eq. Efos2)
 __global__ void k_rhs4_2d(const double *__restrict__ f, int up, int n, double *ft) {
+    pdl_wait();
     MG_IDX2 const int i = tx + 1, j = ty + 1;
     if (i > n || j > n) return;
     const size_t c = (size_t)j * up + i;
@@ -418,6 +419,7 @@ __global__ void __launch_bounds__(256) k_res0_3d(const double *__restrict__ f, c
 
 // ft = (6f + sum6 f)/12 on the interior (order-4 right-hand side of Eq. Efos4)
 __global__ void k_rhs4_3d(const double *__restrict__ f, int up, int n, double *ft) {
+    pdl_wait();
     MG_IDX2 const int i = tx + 1, j = ty + 1, k = (int)blockIdx.z + 1;
     if (i > n || j > n) return;
     const size_t pl = (size_t)up * (n + 2);

@@ -115,6 +115,7 @@ struct mg_ctx {
     // the solver graph (prefix + device-driven loop over V-cycles), cached per arguments
     bool capturing = false;
     bool use_graph = true;      // DIAGMG_SOLVE_GRAPH=0: host-driven loop (same kernels; for profilers)
+    bool pdl = false;           // DIAGMG_PDL=1: programmatic dependent launch (measured neutral in the solve graph)
     cudaStream_t cs1 = nullptr, cs2 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -227,16 +228,34 @@ struct Launch {
         if (slot >= 0) cudaEventRecord(c->pev[2 * slot + 1], s);
     }
 };
-#define LAUNCH(tag, kern, grid, block, ...)            \
-    do {                                               \
-        Launch l_(c, tag, s);                          \
-        kern<<<grid, block, 0, s>>>(__VA_ARGS__);      \
+// One kernel launch; with c->pdl, as a programmatic dependent launch: the
+// kernel may be scheduled while the previous one in the stream finishes and
+// waits in pdl_wait (every kernel of this library calls it before reading
+// what another kernel wrote).
+template <typename... P, typename... A>
+void launch_k(const mg_ctx *c, void (*kern)(P...), dim3 g, dim3 b, size_t sm, cudaStream_t s, A &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = c->pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
+}
+#define LAUNCH(tag, kern, grid, block, ...)                                \
+    do {                                                                   \
+        Launch l_(c, tag, s);                                              \
+        launch_k(c, kern, dim3(grid), dim3(block), 0, s, __VA_ARGS__);     \
     } while (0)
 
-#define LAUNCH_SMEM(tag, kern, grid, block, smem, ...) \
-    do {                                               \
-        Launch l_(c, tag, s);                          \
-        kern<<<grid, block, smem, s>>>(__VA_ARGS__);   \
+#define LAUNCH_SMEM(tag, kern, grid, block, smem, ...)                     \
+    do {                                                                   \
+        Launch l_(c, tag, s);                                              \
+        launch_k(c, kern, dim3(grid), dim3(block), smem, s, __VA_ARGS__);  \
     } while (0)
 
 // grid and batch descriptor of one launch: z blocks of one problem, times nprob
@@ -249,17 +268,17 @@ BL bl(const mg_ctx *c, dim3 g) {
     g.z *= (unsigned)c->nprob;
     return BL{g, b};
 }
-#define LAUNCH_B(tag, kern, grd, block, ...)                    \
-    do {                                                        \
-        BL bl_ = bl(c, grd);                                    \
-        Launch l_(c, tag, s);                                   \
-        kern<<<bl_.dims, block, 0, s>>>(__VA_ARGS__, bl_.bt);   \
+#define LAUNCH_B(tag, kern, grd, block, ...)                                   \
+    do {                                                                       \
+        BL bl_ = bl(c, grd);                                                   \
+        Launch l_(c, tag, s);                                                  \
+        launch_k(c, kern, bl_.dims, dim3(block), 0, s, __VA_ARGS__, bl_.bt);   \
     } while (0)
-#define LAUNCH_SMEM_B(tag, kern, grd, block, smem, ...)         \
-    do {                                                        \
-        BL bl_ = bl(c, grd);                                    \
-        Launch l_(c, tag, s);                                   \
-        kern<<<bl_.dims, block, smem, s>>>(__VA_ARGS__, bl_.bt); \
+#define LAUNCH_SMEM_B(tag, kern, grd, block, smem, ...)                        \
+    do {                                                                       \
+        BL bl_ = bl(c, grd);                                                   \
+        Launch l_(c, tag, s);                                                  \
+        launch_k(c, kern, bl_.dims, dim3(block), smem, s, __VA_ARGS__, bl_.bt); \
     } while (0)
 
 // accumulate the probe events of completed work (call after a stream sync)
@@ -1006,6 +1025,8 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     {
         const char *ev = std::getenv("DIAGMG_SOLVE_GRAPH");
         c->use_graph = !(ev && ev[0] == '0');
+        const char *ep = std::getenv("DIAGMG_PDL");
+        c->pdl = ep && ep[0] == '1';
     }
     if (cudaStreamCreateWithFlags(&c->cs1, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess) {

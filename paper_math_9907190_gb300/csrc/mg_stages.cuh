@@ -39,7 +39,15 @@ template <typename T> struct A3 {  // 3D array view
     }
 };
 
-__device__ __forceinline__ bool stop(const int *done) { return done != nullptr && *(volatile const int *)done; }
+// Kernels are launched with programmatic dependent launch: a kernel may start
+// while the previous one in the stream finishes, and waits here (before its
+// first read of anything another kernel wrote) for it to complete.  A kernel
+// launched without that attribute passes at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ bool stop(const int *done) {
+    pdl_wait();
+    return done != nullptr && *(volatile const int *)done;
+}
 
 // Batch descriptor: a context holds `nprob` problems of one size.  Every level
 // array of problem p lies `p * pstride` bytes after problem 0's; grid z holds
@@ -652,6 +660,7 @@ __device__ __forceinline__ double sum_parts(const double *part, int nblk, double
 // (use_loop = 1) it also sets the graph's loop condition to "not done".
 __global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, int first,
                        cudaGraphConditionalHandle loop, int use_loop) {
+    pdl_wait();
     __shared__ double sh[32];
     if (!first && ctl->done) {
         if (use_loop && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
@@ -680,18 +689,21 @@ __global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, in
 }
 
 __global__ void k_ctrl_init(Ctrl *ctl, double rtol, int max_cycles) {
+    pdl_wait();
     ctl->r2 = 0.0; ctl->relres = 0.0; ctl->rel0 = 0.0; ctl->rtol = rtol;
     ctl->done = 0; ctl->cycles = 0; ctl->max_cycles = max_cycles; ctl->status = 0; ctl->par = 0;
 }
 
 // per problem of a batch (one block each): f2 = sum of that problem's partials
 __global__ void k_sum_to_b(const double *part, int nblk, Ctrl *ctl) {
+    pdl_wait();
     __shared__ double sh[32];
     double s = sum_parts(part + (size_t)blockIdx.x * nblk, nblk, sh);
     if (threadIdx.x == 0) ctl[blockIdx.x].f2 = s;
 }
 
 __global__ void k_ctrl_init_b(Ctrl *ctl, int nprob, double rtol, int max_cycles) {
+    pdl_wait();
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nprob; p += gridDim.x * blockDim.x) {
         Ctrl &c = ctl[p];
         c.r2 = 0.0; c.relres = 0.0; c.rel0 = 0.0; c.rtol = rtol;
@@ -702,6 +714,7 @@ __global__ void k_ctrl_init_b(Ctrl *ctl, int nprob, double rtol, int max_cycles)
 // per problem of a batch (one block each): the control step of k_ctrl, with the
 // history of problem p at hist + p * hist_cap
 __global__ void k_ctrl_b(const double *part, int nblk, Ctrl *ctl, double *hist, int hist_cap, int first) {
+    pdl_wait();
     __shared__ double sh[32];
     const int p = blockIdx.x;
     Ctrl *c = ctl + p;
@@ -729,6 +742,7 @@ __global__ void k_ctrl_b(const double *part, int nblk, Ctrl *ctl, double *hist, 
 // reported relative residual by the one of a direct FP64 residual of the final
 // iterate (one block per problem); above rtol the solve counts as not converged
 __global__ void k_final_true(const double *part, int nblk, Ctrl *ctl) {
+    pdl_wait();
     __shared__ double sh[32];
     const int p = blockIdx.x;
     Ctrl *c = ctl + p;
@@ -742,6 +756,7 @@ __global__ void k_final_true(const double *part, int nblk, Ctrl *ctl) {
 
 // loop condition of a batch: continue while any problem is not done
 __global__ void k_any_active(const Ctrl *ctl, int nprob, cudaGraphConditionalHandle loop, int use_loop, int *active) {
+    pdl_wait();
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -757,6 +772,7 @@ __global__ void k_any_active(const Ctrl *ctl, int nprob, cudaGraphConditionalHan
 // power iteration step: ratio[c] = ||u|| / ||u before the cycle|| (the latter
 // is 1 after normalisation), then u <- u / ||u|| on the interior
 __global__ void k_rho_record(const double *part, int nblk, double *scal, double *ratio, int c) {
+    pdl_wait();
     __shared__ double sh[32];
     const double s = sum_parts(part, nblk, sh);
     if (threadIdx.x == 0) {
@@ -772,6 +788,7 @@ __global__ void k_scale_grid(double *u, int up, int n, int dim, const double *sc
 }
 
 __global__ void k_sum_to(const double *part, int nblk, double *out) {
+    pdl_wait();
     __shared__ double sh[32];
     double s = sum_parts(part, nblk, sh);
     if (threadIdx.x == 0) *out = s;
@@ -815,6 +832,7 @@ __global__ void k_add_axis(const T *v, int pitch, int rows, int n, int dim, doub
 template <typename T>
 __global__ void k_level_io(int dim, int kind, int s, double *grid, T *c0, T *c1, T *c2, T *c3, int pitch, int rows,
                            int to_level) {
+    pdl_wait();
     MG_IDX2 const int i = tx + 1, j = ty + 1, k = dim == 3 ? (int)blockIdx.z + 1 : 0;
     if (i > s || j > s || (dim == 3 && k > s)) return;
     const size_t gidx = ((size_t)k * (s + 2) + j) * (size_t)(s + 2) + i;
