@@ -295,11 +295,12 @@ void probe_collect(mg_ctx *c) {
 
 dim3 grid2(int nx, int ny) { return dim3((nx + 31) / 32, (ny + 7) / 8, 1); }
 dim3 grid3(int nx, int ny, int nz) { return dim3((nx + 31) / 32, (ny + 7) / 8, nz); }
-// z-marching 3D stage kernels: count cells per dimension
 // planes per thread of the z-marching 3D stage kernels by size: 8 from 128^3
-// cells, 2 from 64^3; smaller triples use the thread-per-cell kernels
+// cells, 2 from 64^3; smaller triples, and the FP64 path (bound by its FP64
+// arithmetic), use the thread-per-cell kernels
 int zm_planes(int nb) { return nb + 1 >= 128 ? 8 : 2; }
-bool zm_use(int nb) { return nb + 1 >= 64; }
+template <typename T> bool zm_use(int nb) { return sizeof(T) == 4 && nb + 1 >= 64; }
+// grid of a z-marching 3D stage kernel: count cells per dimension
 dim3 grid_zm(int count, int zm) { return dim3((count + 31) / 32, (count + 7) / 8, (count + zm - 1) / zm); }
 const dim3 B2(32, 8, 1);
 
@@ -372,7 +373,7 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
         const int nb = b.nb;
         const T *galt = (alt && l == 0 && c->rr) ? (const T *)c->r32b : nullptr;
         const int *par = galt ? &c->ctl->par : nullptr;
-        if (zm_use(nb))
+        if (zm_use<T>(nb))
             LAUNCH_B(TAG_DOWN, (k_g2r_zm_3d<T>), grid_zm(nb + 1, zm_planes(nb)), B2, a3<const T>(a.r[0], a), red3v<T>(b.r, b), nb,
                      galt, par, zm_planes(nb), done);
         else
@@ -380,13 +381,13 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
                      galt, par, done);
     } else if (a.kind == KIND_RED) {
         const int nb = a.nb;
-        if (zm_use(nb))
+        if (zm_use<T>(nb))
             LAUNCH_B(TAG_DOWN, (k_r2m_zm_3d<T>), grid_zm(nb + 1, zm_planes(nb)), B2, red3v<const T>(a.r, a), mag3v<T>(b.r, b), nb, zm_planes(nb), done);
         else
             LAUNCH_B(TAG_DOWN, (k_r2m_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, red3v<const T>(a.r, a), mag3v<T>(b.r, b), nb, done);
     } else {
         const int nb = a.nb;
-        if (zm_use(nb))
+        if (zm_use<T>(nb))
             LAUNCH_B(TAG_DOWN, (k_m2b_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, zm_planes(nb), done);
         else
             LAUNCH_B(TAG_DOWN, (k_m2b_3d<T>), grid3(nb, nb, nb), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
@@ -475,7 +476,7 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
     }
     if (a.kind == KIND_MAG) {  // Eq. Emprolm, Eq. Emprolb
         const T cc = (T)(4.0 * om[0] * hk2);
-        if (zm_use(nb)) {
+        if (zm_use<T>(nb)) {
             LAUNCH_B(TAG_UP, (k_b2m_ooo_zm_3d<T>), grid_zm(nb + 1, zm_planes(nb)), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, zm_planes(nb), done);
             LAUNCH_B(TAG_UP, (k_b2m_eee_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, zm_planes(nb), done);
         } else {
@@ -484,7 +485,7 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
         }
     } else {  // red from magenta: Eq. Erprolr (faces), Eq. Erprolm (corners)
         const T c1 = (T)(2.0 * om[1] * hk2), c2 = (T)(4.0 * om[2] * hk2);
-        if (zm_use(nb)) {
+        if (zm_use<T>(nb)) {
             LAUNCH_B(TAG_UP, (k_m2r_faces_zm_3d<T>), grid_zm(nb + 1, zm_planes(nb)), B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, zm_planes(nb), done);
             LAUNCH_B(TAG_UP, (k_m2r_corners_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, zm_planes(nb), done);
         } else {

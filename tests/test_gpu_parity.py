@@ -80,7 +80,6 @@ def oracle_prolong(dim, hier, kind, vc, r, h, om):
     return O.prolong3d_r2g(vc, r, h, om[3])
 
 
-# (3, 127): the triple 127^3 has 64^3 cells, where the stage kernels march in z
 STAGE_CASES = [(2, 63, "diag"), (2, 127, "diag"), (2, 63, "usual"), (3, 15, "diag"), (3, 31, "diag"),
                (3, 127, "diag"), (3, 15, "usual")]
 
@@ -114,6 +113,30 @@ def test_prolongation_stages(dim, n, hier):
             got = H(c.level_get(l, "v"))
             want = oracle_prolong(dim, hier, kind, vc, r, 1.0 / (side + 1), om)
             assert_close(got, want, lattice(dim, side, kind))
+
+
+@pytest.mark.parametrize("n", [127, 255])
+def test_fp32_3d_stages(n):
+    """FP32 levels (mixed context): the 3D restriction and prolongation stages,
+    for triples of 64^3 cells and more the z-marching kernels, against the
+    oracle's stages to FP32 accuracy."""
+    om = (1.3, 0.9, 1.15, 0.8)
+    with Context(3, n, precision="mixed", omega=om) as c:
+        for l in range(min(c.num_levels - 1, 6)):
+            side, kind = c.level_info(l)
+            side1, kind1 = c.level_info(l + 1)
+            r = rand_on(3, side, kind, 50 + l)
+            c.level_set(l, "r", T(r))
+            c.restrict(l)
+            assert_close(H(c.level_get(l + 1, "r")), O.restrict3d_g2r(r) if kind == 0 else
+                         O.restrict3d_r2m(r) if kind == 1 else O.restrict3d_m2b(r), lattice(3, side1, kind1), tol=1e-6)
+            if kind == 0:
+                continue  # the green sweep of level 0 is tested through the V-cycle
+            vc = rand_on(3, side1, kind1, 60 + l)
+            c.level_set(l + 1, "v", T(vc))
+            c.prolong(l)
+            want = oracle_prolong(3, "diag", kind, vc, r, 1.0 / (side + 1), om)
+            assert_close(H(c.level_get(l, "v")), want, lattice(3, side, kind), tol=1e-6)
 
 
 @pytest.mark.parametrize("dim,n,coarsest", [(2, 63, 3), (2, 63, 1), (2, 63, 7), (3, 15, 3), (3, 15, 1)])
