@@ -1227,82 +1227,6 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
 
 namespace mg {
 
-// ---------------------------------------------------------------------------
-// 3D finest triple: both halves of the green-red sweep (Eq. Egprolg, then
-// Eq. Egprolr) in one shared-memory tile of GX x GY x GZ green points, fused
-// with u += v (FINEST) or storing v.  F (odd index sum) points are computed on
-// the tile plus a one-point halo from the red values, then the C (even) points
-// of the tile from the new F values.
-// ---------------------------------------------------------------------------
-constexpr int GX3 = 32, GY3 = 8, GZ3 = 4;
-
-template <typename T, bool FINEST>
-__global__ void __launch_bounds__(256) k_up_green_3d(Red3<const T> vr, A3<const T> rg, A3<T> vg, double *u, int up,
-                                                     int n, T cg, const int *done, Bt B) {
-    constexpr int RX = GX3 + 4, RY = GY3 + 4, RZ = GZ3 + 4;  // red region: tile +- 2
-    constexpr int VX = GX3 + 2, VY = GY3 + 2, VZ = GZ3 + 2;  // F / r region: tile +- 1
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *R = reinterpret_cast<T *>(smraw);
-    T *G = R + RX * RY * RZ;
-    T *V = G + VX * VY * VZ;
-    const int prob = bt_prob(B), bz = bt_z(B);
-    if (stop(bt_done(done, prob, B))) return;
-    vr = bt_at(vr, prob, B);
-    rg = bt_at(rg, prob, B);
-    vg = bt_at(vg, prob, B);
-    if (B.utab) u = B.utab[prob];
-    const int x0 = blockIdx.x * GX3 + 1, y0 = blockIdx.y * GY3 + 1, z0 = bz * GZ3 + 1;
-    const int tid = threadIdx.x + 32 * threadIdx.y;
-    // red values at even-parity points of the tile +- 2 (zero outside the interior)
-#pragma unroll 4
-    for (int q = tid; q < RX * RY * RZ; q += 256) {
-        const int lx = q % RX, ly = (q / RX) % RY, lz = q / (RX * RY);
-        const int x = x0 - 2 + lx, y = y0 - 2 + ly, z = z0 - 2 + lz;
-        T v = T(0);
-        if (((x + y + z) & 1) == 0 && x >= 1 && x <= n && y >= 1 && y <= n && z >= 1 && z <= n) v = red3(vr, x, y, z);
-        R[q] = v;
-    }
-#pragma unroll 4
-    for (int q = tid; q < VX * VY * VZ; q += 256) {
-        const int lx = q % VX, ly = (q / VX) % VY, lz = q / (VX * VY);
-        const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
-        G[q] = (x >= 1 && x <= n && y >= 1 && y <= n && z >= 1 && z <= n) ? rg(x, y, z) : T(0);
-    }
-    __syncthreads();
-    auto Ri = [&](int lx, int ly, int lz) { return R[(lz * RY + ly) * RX + lx]; };  // region +-2 coordinates
-    // F points on the tile +- 1
-    for (int q = tid; q < VX * VY * VZ; q += 256) {
-        const int lx = q % VX, ly = (q / VX) % VY, lz = q / (VX * VY);
-        const int x = x0 - 1 + lx, y = y0 - 1 + ly, z = z0 - 1 + lz;
-        T v = T(0);
-        if (((x + y + z) & 1) && x >= 1 && x <= n && y >= 1 && y <= n && z >= 1 && z <= n) {
-            const int rx = lx + 1, ry = ly + 1, rz = lz + 1;
-            const T s = (Ri(rx - 1, ry, rz) + Ri(rx + 1, ry, rz)) + (Ri(rx, ry - 1, rz) + Ri(rx, ry + 1, rz)) +
-                        (Ri(rx, ry, rz - 1) + Ri(rx, ry, rz + 1));
-            v = (s - cg * G[q]) * T(1.0 / 6.0);
-        }
-        V[q] = v;
-    }
-    __syncthreads();
-    auto Vi = [&](int lx, int ly, int lz) { return V[(lz * VY + ly) * VX + lx]; };
-    for (int q = tid; q < GX3 * GY3 * GZ3; q += 256) {
-        const int tx = q % GX3, ty = (q / GX3) % GY3, tz = q / (GX3 * GY3);
-        const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
-        if (x > n || y > n || z > n) continue;
-        const int lx = tx + 1, ly = ty + 1, lz = tz + 1;
-        T v;
-        if ((x + y + z) & 1) {
-            v = Vi(lx, ly, lz);
-        } else {
-            const T s = (Vi(lx - 1, ly, lz) + Vi(lx + 1, ly, lz)) + (Vi(lx, ly - 1, lz) + Vi(lx, ly + 1, lz)) +
-                        (Vi(lx, ly, lz - 1) + Vi(lx, ly, lz + 1));
-            v = (s - cg * G[(lz * VY + ly) * VX + lx]) * T(1.0 / 6.0);
-        }
-        if (FINEST) u[((size_t)z * (n + 2) + y) * up + x] += widen(v);
-        else vg(x, y, z) = v;
-    }
-}
-
 }  // namespace mg
 
 namespace mg {
@@ -1311,10 +1235,9 @@ namespace mg {
 // 3D finest triple, green-red sweep (Eq. Egprolg then Eq. Egprolr) in one tile
 // of 32 x 8 x 4 green points.  The red level is staged as its four cosets
 // (coalesced loads of dense arrays), the F (odd) points are computed on the
-// tile +- 2, the C (even) points on the tile +- 1.  RR: the mixed solve's
-// fused update -- u += v and the carried float-float residual r -= L v, as in
-// k_up0_ff_2d with six neighbours (s2 = 1/h^2) -- otherwise FINEST: u += v,
-// or v stored.
+// tile +- 2, the C (even) points on the tile +- 1.  FINEST: u += v,
+// otherwise v stored.  (Triples from 255^3 up use the z-streaming
+// k_green_ff_3d.)
 // ---------------------------------------------------------------------------
 constexpr int TX3 = 32, TY3 = 8, TZ3 = 4;
 constexpr int CX3 = TX3 / 2 + 3, CY3 = TY3 / 2 + 3, CZ3 = TZ3 / 2 + 3;  // coset cells of the tile +- 3
@@ -1338,27 +1261,17 @@ __device__ __forceinline__ void lap_sum6(const float *nb, float c, float &hi, fl
     lo = ee + (((e[0] + e[1]) + (e[2] + e[3])) + (e[4] + e[5]));
 }
 
-template <typename T, bool RR, bool FINEST>
-__global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> rga, const T *rgb, A3<T> vg,
-                                                  float *__restrict__ rlo, int rp, double *__restrict__ u, int up,
-                                                  int n, T cg, float s2, double *part, const int *par,
-                                                  const int *done, Bt B) {
+template <typename T, bool FINEST>
+__global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> rg, A3<T> vg, double *__restrict__ u,
+                                                  int up, int n, T cg, const int *done, Bt B) {
     extern __shared__ __align__(16) unsigned char smraw[];
     Green3Smem<T> &S = *reinterpret_cast<Green3Smem<T> *>(smraw);
-    __shared__ double sh[32];
     const int prob = bt_prob(B), bz = bt_z(B);
     if (stop(bt_done(done, prob, B))) return;
-    A3<const T> rg = rga;
-    A3<T> rnew{const_cast<T *>(rga.p), rga.pitch, rga.rows};
-    if (RR && par[(size_t)prob * B.ctl_stride]) rg.p = rgb;
-    else if (RR) rnew.p = const_cast<T *>(rgb);
     vr = bt_at(vr, prob, B);
     rg = bt_at(rg, prob, B);
-    rnew = bt_at(rnew, prob, B);
     vg = bt_at(vg, prob, B);
-    if (RR) rlo = bt_ptr(rlo, prob, B);
     if (B.utab) u = B.utab[prob];
-    if (RR) part += (size_t)prob * B.nparts;
     const int tid = threadIdx.x + 32 * threadIdx.y;
     const int x0 = blockIdx.x * TX3 + 1, y0 = blockIdx.y * TY3 + 1, z0 = bz * TZ3 + 1;
     const int ca = (x0 - 3) >> 1, cb = (y0 - 3) >> 1, cc = (z0 - 3) >> 1;  // first coset cell
@@ -1416,35 +1329,13 @@ __global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> 
         S.v[lz][ly][lx] = val;
     }
     __syncthreads();
-    float sq = 0.f;
     for (int q = tid; q < TX3 * TY3 * TZ3; q += 256) {
         const int tx = q % TX3, ty = (q / TX3) % TY3, tz = q / (TX3 * TY3);
         const int x = x0 + tx, y = y0 + ty, z = z0 + tz;
         if (x > n || y > n || z > n) continue;
-        const int lx = tx + 2, ly = ty + 2, lz = tz + 2;
-        const T v = S.v[lz][ly][lx];
-        if (RR) {
-            const float nb[6] = {(float)S.v[lz][ly][lx - 1], (float)S.v[lz][ly][lx + 1], (float)S.v[lz][ly - 1][lx],
-                                 (float)S.v[lz][ly + 1][lx], (float)S.v[lz - 1][ly][lx], (float)S.v[lz + 1][ly][lx]};
-            float hi, lo;
-            lap_sum6(nb, (float)v, hi, lo);
-            const size_t cu = ((size_t)z * (n + 2) + y) * up + x, cr = ((size_t)z * (n + 2) + y) * rp + x;
-            u[cu] += widen(v);
-            float nh, nl;
-            ff_sub((float)S.r[lz][ly][lx], rlo[cr], hi, lo, s2, nh, nl);
-            rlo[cr] = nl;
-            rnew(x, y, z) = (T)nh;
-            sq = fmaf(nh, nh, sq);
-        } else if (FINEST) {
-            u[((size_t)z * (n + 2) + y) * up + x] += widen(v);
-        } else {
-            vg(x, y, z) = v;
-        }
-    }
-    if (RR) {
-        const double s = block_sum((double)sq, sh);
-        if (threadIdx.x == 0 && threadIdx.y == 0)
-            part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz)] = s;
+        const T v = S.v[tz + 2][ty + 2][tx + 2];
+        if (FINEST) u[((size_t)z * (n + 2) + y) * up + x] += widen(v);
+        else vg(x, y, z) = v;
     }
 }
 

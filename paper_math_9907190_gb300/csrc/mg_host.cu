@@ -448,13 +448,11 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
             const dim3 g3((n + TX3 - 1) / TX3, (n + TY3 - 1) / TY3, (n + TZ3 - 1) / TZ3);
             const size_t sm = sizeof(Green3Smem<T>);
             if (u)
-                LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_3d<T, false, true>), g3, B2, sm, red3v<const T>(b.v, b),
-                              a3<const T>(a.r[0], a), (const T *)nullptr, a3<T>(a.v[0], a), (float *)nullptr, 0, u,
-                              c->d.pitch, n, cc, 0.f, (double *)nullptr, (const int *)nullptr, done);
+                LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_3d<T, true>), g3, B2, sm, red3v<const T>(b.v, b),
+                              a3<const T>(a.r[0], a), a3<T>(a.v[0], a), u, c->d.pitch, n, cc, done);
             else
-                LAUNCH_SMEM_B(TAG_UP, (k_green_3d<T, false, false>), g3, B2, sm, red3v<const T>(b.v, b),
-                              a3<const T>(a.r[0], a), (const T *)nullptr, a3<T>(a.v[0], a), (float *)nullptr, 0, u,
-                              c->d.pitch, n, cc, 0.f, (double *)nullptr, (const int *)nullptr, done);
+                LAUNCH_SMEM_B(TAG_UP, (k_green_3d<T, false>), g3, B2, sm, red3v<const T>(b.v, b),
+                              a3<const T>(a.r[0], a), a3<T>(a.v[0], a), u, c->d.pitch, n, cc, done);
         } else {
             if (c->d.hierarchy == MG_USUAL)
                 LAUNCH_B(TAG_UP, (k_usual_odd_3d<T>), grid3(n, n, n), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), n, cc, done);
@@ -965,11 +963,9 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     plan_fast2d(c);
     plan_fast3d(c);
     if (c->fast3d) {
-        const int gsm = (int)(sizeof(double) * ((GX3 + 4) * (GY3 + 4) * (GZ3 + 4) + 2 * (GX3 + 2) * (GY3 + 2) * (GZ3 + 2)));
         cudaError_t e = d->precision == MG_FP64
             ? cudaFuncSetAttribute(k_coarse_cta_3d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes)
             : cudaFuncSetAttribute(k_coarse_cta_3d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
-        (void)gsm;
         const int g64 = (int)sizeof(Green3Smem<double>), g32 = (int)sizeof(Green3Smem<float>);
         const int gs = (int)sizeof(GreenSSmem);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<UP_RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
@@ -981,11 +977,10 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
             if (e == cudaSuccess) c->gs_resident = std::max(1, per_sm * sms);
         }
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<float, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g64);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_3d<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, g32);
         if (e != cudaSuccess) {
             mg_destroy(c);
             return cuda_fail(e, "mg_create shared-memory attributes (3D)");

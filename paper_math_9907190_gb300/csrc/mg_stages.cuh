@@ -435,24 +435,6 @@ __global__ void k_r2g_c_3d(A3<const T> rg, A3<T> vg, int n, T cc, const int *don
     vg(i, j, k) = (s - cc * rg(i, j, k)) * T(1.0 / 6.0);
 }
 
-template <typename T>
-__global__ void k_r2g_c_upd_3d(A3<const T> rg, A3<const T> vg, double *u, int up, int urows, int n, T cc,
-                               const int *done, Bt B) {
-    const int prob_ = bt_prob(B);
-    if (stop(bt_done(done, prob_, B))) return;
-    rg = bt_at(rg, prob_, B);
-    vg = bt_at(vg, prob_, B);
-    if (B.utab) u = B.utab[prob_];
-    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
-    if (i > n || j > n || k > n) return;
-    T v;
-    if ((i + j + k) & 1) v = vg(i, j, k);
-    else
-        v = ((vg(i - 1, j, k) + vg(i + 1, j, k)) + (vg(i, j - 1, k) + vg(i, j + 1, k)) +
-             (vg(i, j, k - 1) + vg(i, j, k + 1)) - cc * rg(i, j, k)) * T(1.0 / 6.0);
-    u[((size_t)k * urows + j) * up + i] += widen(v);
-}
-
 // ---------------------------------------------------------------------------
 // Conventional 2^-l hierarchy
 // ---------------------------------------------------------------------------
