@@ -617,12 +617,14 @@ namespace mg {
 // second FP32 array.  A cycle's correction v (FP32) gives
 //   u_new = u + v          (the one FP64 operation per point)
 //   r_new = r - L v,       L v = s2 * sum over the four axis neighbours of (v_nb - v)
-// where each difference v_nb - v is exact as a two-sum pair, the four pairs
-// are accumulated as a float-float pair, s2 = 1/h^2 is a power of two
-// (n = 2^m - 1) so the scaling is exact, and the subtraction is a float-float
-// operation.  Its error is ~2^-47 (|r| + s2 sum |v_nb - v|), far below the
-// FP64 rounding of a direct residual of u_new; a direct FP64 residual starts
-// and ends every solve.
+// where v is first rounded to a multiple of a quantum q set by a bound on
+// |v| over the whole level (quant_magic), so that the neighbour sum and
+// L v are exact in FP32; s2 = 1/h^2 is a power of two (n = 2^m - 1), so the
+// scaling is exact; the subtraction is a float-float operation, error
+// ~2^-48 |r|.  u += v and r -= L v use the same rounded v, so the carried r
+// stays the residual of u up to that error (and the FP64 rounding of u); a
+// direct residual starts and ends every solve.  The rounding of v itself
+// (at most 2^-21 of the bound) only perturbs the correction.
 // ---------------------------------------------------------------------------
 
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -632,25 +634,34 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = (a - av) + (b - bv);
 }
 
-// hi + lo ~= (n0 - c) + (n1 - c) + (n2 - c) + (n3 - c)
-__device__ __forceinline__ void lap_sum(float n0, float n1, float n2, float n3, float c, float &hi, float &lo) {
-    float d0, d1, d2, d3, e0, e1, e2, e3, t, e4, e5, e6;
-    two_sum(n0, -c, d0, e0);
-    two_sum(n1, -c, d1, e1);
-    two_sum(n2, -c, d2, e2);
-    two_sum(n3, -c, d3, e3);
-    two_sum(d0, d1, t, e4);
-    two_sum(t, d2, t, e5);
-    two_sum(t, d3, t, e6);
-    hi = t;
-    lo = ((e0 + e1) + (e2 + e3)) + ((e4 + e5) + e6);
+// (nh, nl) ~= (hi + lo) - s2 * l, l exact, s2 a power of two
+__device__ __forceinline__ void ff_sub1(float hi, float lo, float l, float s2, float &nh, float &nl) {
+    float s, e;
+    two_sum(hi, -s2 * l, s, e);
+    two_sum(s, lo + e, nh, nl);
 }
 
-// (nh, nl) ~= (hi + lo) - s2 * (lh + ll), s2 a power of two
-__device__ __forceinline__ void ff_sub(float hi, float lo, float lh, float ll, float s2, float &nh, float &nl) {
-    float s, e;
-    two_sum(hi, -s2 * lh, s, e);
-    two_sum(s, fmaf(-s2, ll, lo) + e, nh, nl);
+// Rounding of the finest correction of the fused mixed path to a quantum.
+// With 2^E >= |v| for every v of the level (a bound formed before the sweep
+// from the level it starts from and the residual), each v is rounded to a
+// multiple of q = 2^(E - qb): v_q = (v + M) - M with M = 1.5 * 2^(E - qb + 23),
+// whose unit in the last place is q (v + M stays in M's binade).  Then the
+// Laplacian of v_q -- the neighbour sum and the centre term, all multiples
+// of q below 2^24 q with qb = 21 (5-point) or 20 (7-point) -- is exact in
+// FP32, and u += v_q and r -= L v_q stay consistent to the float-float
+// rounding of r.  The rounding moves v by at most q / 2 <= 2^-qb of the
+// bound.  E is clamped to [-100, 100]; a bound above 2^100 or NaN gives a
+// NaN quantizer (the solve then reports divergence).
+__device__ __forceinline__ float quant_magic(float bound, int qb) {
+    if (!(bound <= 1.2676506e30f)) return __int_as_float(0x7fc00000);  // 2^100
+    const unsigned b = __float_as_uint(bound);
+    const int e = max((int)(b >> 23) - 127 + ((b & 0x7fffffu) != 0u), -100);
+    return __uint_as_float(((unsigned)(e - qb + 150) << 23) | 0x400000u);
+}
+__device__ __forceinline__ float quant(float v, float M) { return __fsub_rn(__fadd_rn(v, M), M); }
+// sum of the four neighbours - 4 c of quantized values: exact
+__device__ __forceinline__ float lap_q4(float n0, float n1, float n2, float n3, float c) {
+    return fmaf(-4.f, c, __fadd_rn(__fadd_rn(n0, n1), __fadd_rn(n2, n3)));
 }
 
 // Work decomposition of k_up0_ff_2d.  A cell (a,b) is the four green points
@@ -674,7 +685,8 @@ constexpr int FF_WARPS = 4;
 // cell of row b.  Values outside the interior are zero, as in the oracle.
 // MODE: UP_RR the mixed finest pair (u += v and the carried residual, rga/rgb
 // double-buffered by par); UP_ADD u += v; UP_STORE v stored in vg (a coarser
-// pair).  VU: u is 16-byte aligned with an even pitch (vector access to u).
+// pair; with ctl, also the largest |v| stored into ctl[p].vmax).  VU: u is
+// 16-byte aligned with an even pitch (vector access to u).
 enum { UP_RR = 0, UP_ADD = 1, UP_STORE = 2 };
 
 // Asynchronous global -> shared copies (cp.async), used to keep one step of
@@ -714,8 +726,9 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
                                                             A2<const float> roo, A2<float> rga, float *rgb, A2<float> vg,
                                                             float *__restrict__ rlo, double *__restrict__ u, int up,
                                                             int nb, float c2, float c1, float s2, int tb,
-                                                            double *part, const int *par, const int *done, Bt B) {
+                                                            double *part, Ctrl *ctl, const int *done, Bt B) {
     __shared__ double sh[32];
+    __shared__ float shm[32];
     __shared__ FFChain SC[FF_WARPS][2];
     __shared__ FFU SU[MODE != UP_STORE ? FF_WARPS : 1][2];
     __shared__ FFL SL[MODE == UP_RR ? FF_WARPS : 1][2];
@@ -725,7 +738,14 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
     const int prob = blockIdx.z;
     if (stop(bt_done(done, prob, B))) return;
     A2<float> rg = rga, rnew = rga;
-    if (RR) (par[(size_t)prob * B.ctl_stride] != 0 ? rg : rnew).p = rgb;
+    int pq = 0;      // current residual buffer
+    float M = 0.f;   // quantizer of v (quant_magic): |v| <= |blue| + (c2 + c1) max|r| / 2
+    if (RR) {
+        const Ctrl &C = ctl[prob];
+        pq = C.par;
+        (pq ? rg : rnew).p = rgb;
+        M = quant_magic((__uint_as_float(C.vmax) + 0.5f * (c2 + c1) * __uint_as_float(C.rmax[pq])) * 1.002f, 21);
+    }
     blue = bt_at(blue, prob, B); ree = bt_at(ree, prob, B); roo = bt_at(roo, prob, B);
     rg = bt_at(rg, prob, B); rnew = bt_at(rnew, prob, B); vg = bt_at(vg, prob, B);
     if (RR) rlo = bt_ptr(rlo, prob, B);
@@ -734,7 +754,7 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
     const int lane = threadIdx.x, w = threadIdx.y;
     const int n = 2 * nb + 1, gp = rga.pitch;
     const int ncol = (nb + FF_W) / FF_W, nstrip = (nb + tb) / tb;
-    float sq = 0.f;
+    float sq = 0.f, mx = 0.f;
     for (int it = blockIdx.x * FF_WARPS + w; it < ncol * nstrip; it += gridDim.x * FF_WARPS) {
         const int col = it % ncol, strip = it / ncol;
         const int A = col * FF_W - 2, a0 = A + K * lane;
@@ -836,6 +856,7 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
                     const float er = k + 1 < K ? ee1[k + 1] : ee1R, ol = k > 0 ? oo1[k - 1] : oo1L;
                     oe1[k] = (in && y_oe1) ? ((ee1[k] + er) + (oo0[k] + oo1[k]) - c1 * g2[2 * k + 1]) * 0.25f : 0.f;
                     eo1[k] = (pos[k] && y_eo1) ? ((ol + oo1[k]) + (ee1[k] + ee2[k]) - c1 * g3[2 * k]) * 0.25f : 0.f;
+                    if (RR) { oe1[k] = quant(oe1[k], M); eo1[k] = quant(eo1[k], M); }
                 }
             }
             const float oe1L = __shfl_up_sync(FULL, oe1[K - 1], 1), eo0R = __shfl_down_sync(FULL, eo0[0], 1);
@@ -844,6 +865,7 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
                 const float ol = k > 0 ? oe1[k - 1] : oe1L, er = k + 1 < K ? eo0[k + 1] : eo0R;
                 ce1[k] = (pos[k] && y_oe1) ? ((ol + oe1[k]) + (eo0[k] + eo1[k]) - c1 * g2[2 * k]) * 0.25f : 0.f;
                 co0[k] = (in && y_co0) ? ((eo0[k] + er) + (oe0[k] + oe1[k]) - c1 * r1[2 * k + 1]) * 0.25f : 0.f;
+                if (RR) { ce1[k] = quant(ce1[k], M); co0[k] = quant(co0[k], M); }
             }
             // ---- apply v to the own cells of row b
             const float oe0L = __shfl_up_sync(FULL, oe0[K - 1], 1), ce0R = __shfl_down_sync(FULL, ce0[0], 1);
@@ -852,6 +874,11 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
                 float *v0 = &vg(xo, yo), *v1 = v0 + vg.pitch;
                 if (row0) *reinterpret_cast<float4 *>(v0) = make_float4(ce0[0], oe0[0], ce0[1], oe0[1]);
                 *reinterpret_cast<float4 *>(v1) = make_float4(eo0[0], co0[0], eo0[1], co0[1]);
+                if (ctl) {
+#pragma unroll
+                    for (int k = 0; k < K; k++)
+                        mx = fmaxf(fmaxf(mx, fmaxf(fabsf(ce0[k]), fabsf(oe0[k]))), fmaxf(fabsf(eo0[k]), fabsf(co0[k])));
+                }
             }
             if (UPD && upd) {
                 double u0[2 * K], u1[2 * K];
@@ -872,48 +899,39 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
                 for (int k = 0; k < K; k++) {
                     const float oel = k > 0 ? oe0[k - 1] : oe0L, cer = k + 1 < K ? ce0[k + 1] : ce0R;
                     const float col_ = k > 0 ? co0[k - 1] : co0L, eor = k + 1 < K ? eo0[k + 1] : eo0R;
-                    float lh, ll, nh, nl;
+                    float nh, nl;
                     // EE (2a, 2b)
                     nh = nl = 0.f;
                     if (pos[k] && row0) {
-                        if (RR) {
-                            lap_sum(oel, oe0[k], eom[k], eo0[k], ce0[k], lh, ll);
-                            ff_sub(r0[2 * k], l0[2 * k], lh, ll, s2, nh, nl);
-                        }
+                        if (RR) ff_sub1(r0[2 * k], l0[2 * k], lap_q4(oel, oe0[k], eom[k], eo0[k], ce0[k]), s2, nh, nl);
                         u0[2 * k] += widen(ce0[k]);
                     }
                     h0[2 * k] = nh; l0[2 * k] = nl;
                     // OE (2a+1, 2b)
                     nh = nl = 0.f;
                     if (row0) {
-                        if (RR) {
-                            lap_sum(ce0[k], cer, com[k], co0[k], oe0[k], lh, ll);
-                            ff_sub(r0[2 * k + 1], l0[2 * k + 1], lh, ll, s2, nh, nl);
-                        }
+                        if (RR) ff_sub1(r0[2 * k + 1], l0[2 * k + 1], lap_q4(ce0[k], cer, com[k], co0[k], oe0[k]), s2, nh, nl);
                         u0[2 * k + 1] += widen(oe0[k]);
                     }
                     h0[2 * k + 1] = nh; l0[2 * k + 1] = nl;
                     // EO (2a, 2b+1)
                     nh = nl = 0.f;
                     if (pos[k]) {
-                        if (RR) {
-                            lap_sum(col_, co0[k], ce0[k], ce1[k], eo0[k], lh, ll);
-                            ff_sub(r1[2 * k], l1[2 * k], lh, ll, s2, nh, nl);
-                        }
+                        if (RR) ff_sub1(r1[2 * k], l1[2 * k], lap_q4(col_, co0[k], ce0[k], ce1[k], eo0[k]), s2, nh, nl);
                         u1[2 * k] += widen(eo0[k]);
                     }
                     h1[2 * k] = nh; l1[2 * k] = nl;
                     // OO (2a+1, 2b+1)
-                    if (RR) {
-                        lap_sum(eo0[k], eor, oe0[k], oe1[k], co0[k], lh, ll);
-                        ff_sub(r1[2 * k + 1], l1[2 * k + 1], lh, ll, s2, nh, nl);
-                    }
+                    if (RR) ff_sub1(r1[2 * k + 1], l1[2 * k + 1], lap_q4(eo0[k], eor, oe0[k], oe1[k], co0[k]), s2, nh, nl);
                     u1[2 * k + 1] += widen(co0[k]);
                     h1[2 * k + 1] = nh; l1[2 * k + 1] = nl;
                 }
                 if (RR) {
 #pragma unroll
-                    for (int q = 0; q < 2 * K; q++) sq = fmaf(h0[q], h0[q], fmaf(h1[q], h1[q], sq));
+                    for (int q = 0; q < 2 * K; q++) {
+                        sq = fmaf(h0[q], h0[q], fmaf(h1[q], h1[q], sq));
+                        mx = fmaxf(mx, fmaxf(fabsf(h0[q]), fabsf(h1[q])));
+                    }
                     float *hr0 = &rnew(xo, yo), *hr1 = hr0 + gp;
                     if (row0) {
                         *reinterpret_cast<float4 *>(hr0) = make_float4(h0[0], h0[1], h0[2], h0[3]);
@@ -951,7 +969,14 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
     }
     if (RR) {
         const double s = block_sum((double)sq, sh);
-        if (threadIdx.x == 0 && threadIdx.y == 0) part[blockIdx.x] = s;
+        const float m = block_max(mx, shm);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            part[blockIdx.x] = s;
+            atomicMax(&ctl[prob].rmax[pq ^ 1], __float_as_uint(m));
+        }
+    } else if (!UPD && ctl) {  // the blue level of the fused mixed path's finest pair: its bound on |v|
+        const float m = block_max(mx, shm);
+        if (threadIdx.x == 0 && threadIdx.y == 0) atomicMax(&ctl[prob].vmax, __float_as_uint(m));
     }
 }
 
@@ -1140,15 +1165,16 @@ __device__ __forceinline__ unsigned mag_bits(double x) {
 template <bool START>
 __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f, const double *__restrict__ u,
                                                    int up, int n, int lg, A2<float> r, float *rlo, int rp,
-                                                   double *part, double *fpart, const int *done, Bt B) {
+                                                   double *part, double *fpart, Ctrl *ctl, const int *done, Bt B) {
     __shared__ double sh[32];
+    __shared__ float shm[32];
     const int prob = blockIdx.z;
     if (stop(bt_done(done, prob, B))) return;
     if (B.ftab) { f = B.ftab[prob]; u = B.utab[prob]; }
     if (START) { r = bt_at(r, prob, B); rlo = bt_ptr(rlo, prob, B); }
     const int i = blockIdx.x * 32 + threadIdx.x + 1;
     const int j0 = (blockIdx.y * 8 + threadIdx.y) * RES_ROWS + 1;
-    float acc = 0.f, facc = 0.f;
+    float acc = 0.f, facc = 0.f, mx = 0.f;
     if (i <= n && j0 <= n) {
         const double *u0p = u + (size_t)j0 * up + i;
         const double *f0p = f + (size_t)j0 * up + i;
@@ -1202,6 +1228,7 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
                     rlo[(size_t)(j0 + q) * rp + i] = lo;
                     const float ff = Z ? hi : narrow(fv);
                     facc = fmaf(ff, ff, facc);
+                    mx = fmaxf(mx, fabsf(hi));
                 } else {
                     hi = narrow(res);
                 }
@@ -1219,7 +1246,11 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
     if (START) {
         __syncthreads();
         const double sf = block_sum((double)facc, sh);
-        if (threadIdx.x == 0 && threadIdx.y == 0) fpart[slot] = sf;
+        const float m = block_max(mx, shm);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            fpart[slot] = sf;
+            atomicMax(&ctl[prob].rmax[0], __float_as_uint(m));  // the start writes buffer 0
+        }
     }
 }
 
@@ -1248,18 +1279,6 @@ template <typename T> struct Green3Smem {
     T v[WZ3][WY3][WX3];       // F at odd points (tile +- 2), C at even points (tile +- 1)
     T r[WZ3][WY3][WX3];       // green residual
 };
-
-// hi + lo ~= sum over six neighbours of (n_q - c)
-__device__ __forceinline__ void lap_sum6(const float *nb, float c, float &hi, float &lo) {
-    float d[6], e[6];
-#pragma unroll
-    for (int q = 0; q < 6; q++) two_sum(nb[q], -c, d[q], e[q]);
-    float t = d[0], ee = 0.f, ex;
-#pragma unroll
-    for (int q = 1; q < 6; q++) { two_sum(t, d[q], t, ex); ee += ex; }
-    hi = t;
-    lo = ee + (((e[0] + e[1]) + (e[2] + e[3])) + (e[4] + e[5]));
-}
 
 template <typename T, bool FINEST>
 __global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> rg, A3<T> vg, double *__restrict__ u,
@@ -1344,8 +1363,9 @@ __global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> 
 template <bool START>
 __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f, const double *__restrict__ u,
                                                    int up, int n, int lg, A3<float> r, float *rlo, int rp,
-                                                   double *part, double *fpart, const int *done, Bt B) {
+                                                   double *part, double *fpart, Ctrl *ctl, const int *done, Bt B) {
     __shared__ double sh[32];
+    __shared__ float shm[32];
     const int prob = bt_prob(B), bz = bt_z(B);
     if (stop(bt_done(done, prob, B))) return;
     if (B.ftab) { f = B.ftab[prob]; u = B.utab[prob]; }
@@ -1353,7 +1373,7 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
     const int i = blockIdx.x * 32 + threadIdx.x + 1, j = blockIdx.y * 8 + threadIdx.y + 1;
     const int k0 = bz * RES3_PLANES + 1;
     const size_t pl = (size_t)up * (n + 2), pr = (size_t)rp * (n + 2);
-    float acc = 0.f, facc = 0.f;
+    float acc = 0.f, facc = 0.f, mx = 0.f;
     const bool act = i <= n && j <= n;
     const int planes = act ? min(RES3_PLANES, n + 1 - k0) : 0;
     const double *u0p = u + k0 * pl + (size_t)(act ? j : 1) * up + (act ? i : 1);
@@ -1407,6 +1427,7 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
                     rlo[(k0 + q) * pr + (size_t)j * rp + i] = lo;
                     const float ff = Z ? hi : narrow(fv);
                     facc = fmaf(ff, ff, facc);
+                    mx = fmaxf(mx, fabsf(hi));
                 } else {
                     hi = narrow(res);
                 }
@@ -1424,7 +1445,11 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
     if (START) {
         __syncthreads();
         const double sf = block_sum((double)facc, sh);
-        if (threadIdx.x == 0 && threadIdx.y == 0) fpart[slot] = sf;
+        const float m = block_max(mx, shm);
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            fpart[slot] = sf;
+            atomicMax(&ctl[prob].rmax[0], __float_as_uint(m));  // the start writes buffer 0
+        }
     }
 }
 

@@ -43,11 +43,12 @@ struct GreenSSmem {
 template <int MODE>
 __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<float> rga, float *rgb, A3<float> vg,
                                                      float *__restrict__ rlo, double *__restrict__ u, int up, int n,
-                                                     float cg, float s2, int zch, double *part, const int *par,
+                                                     float cg, float s2, int zch, double *part, Ctrl *ctl,
                                                      const int *done, Bt B) {
     extern __shared__ __align__(16) unsigned char smraw[];
     GreenSSmem &S = *reinterpret_cast<GreenSSmem *>(smraw);
     __shared__ double sh[32];
+    __shared__ float shm[32];
     constexpr bool RR = MODE == UP_RR, UPD = MODE != UP_STORE;
     constexpr int FPR = GS_VW / 2, NF = GS_VH * FPR;               // F points per row, per plane
     constexpr int CPR = (GS_VW - 2) / 2, NC = (GS_VH - 2) * CPR;   // C points per row, per plane
@@ -55,7 +56,14 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
     const int prob = bt_prob(B), zc = bt_z(B);
     if (stop(bt_done(done, prob, B))) return;
     A3<float> rg = rga, rnew = rga;
-    if (RR) (par[(size_t)prob * B.ctl_stride] != 0 ? rg : rnew).p = rgb;
+    int pq = 0;      // current residual buffer
+    float M = 0.f;   // quantizer of v (quant_magic): |v| <= |red| + cg max|r| / 3
+    if (RR) {
+        const Ctrl &C = ctl[prob];
+        pq = C.par;
+        (pq ? rg : rnew).p = rgb;
+        M = quant_magic((__uint_as_float(C.vmax) + cg * (1.f / 3.f) * __uint_as_float(C.rmax[pq])) * 1.002f, 20);
+    }
     vr = bt_at(vr, prob, B);
     rg = bt_at(rg, prob, B); rnew = bt_at(rnew, prob, B); vg = bt_at(vg, prob, B);
     if (RR) rlo = bt_ptr(rlo, prob, B);
@@ -122,7 +130,7 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
     for (int q = tid; q < (int)(sizeof(GreenSSmem) / 4); q += 256) reinterpret_cast<float *>(smraw)[q] = 0.f;
     __syncthreads();
     issue(zs + 3, zs + 2, zs);
-    float sq = 0.f;
+    float sq = 0.f, mx = 0.f;
     for (int z = zs; z < ze; z++) {
         cp_async_wait0();
         __syncthreads();                             // step z's planes landed; step z-1 is done with every slot
@@ -150,7 +158,7 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
                                     (Rm[ry][ac] + Rp[ry][ac]);
                     val = (s - cg * G[ly][lx + 3]) * (1.f / 6.f);
                 }
-                V[ly][lx] = val;
+                V[ly][lx] = RR ? quant(val, M) : val;
             }
         }
         __syncthreads();
@@ -173,7 +181,7 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
                                     (Vm[ly][lx] + Vp[ly][lx]);
                     val = (s - cg * G[ly][lx + 3]) * (1.f / 6.f);
                 }
-                V[ly][lx] = val;
+                V[ly][lx] = RR ? quant(val, M) : val;
             }
         }
         __syncthreads();
@@ -191,14 +199,17 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
                 const int lx = tx + 2, ly = ty + 8 * h + 2;
                 const float v = V[ly][lx];
                 if (RR) {
-                    const float nb[6] = {V[ly][lx - 1], V[ly][lx + 1], V[ly - 1][lx], V[ly + 1][lx], Vm[ly][lx], Vp[ly][lx]};
-                    float lh, ll, nh, nl;
-                    lap_sum6(nb, v, lh, ll);
-                    ff_sub(G[ly][lx + 3], S.lo[z & 1][ty + 8 * h][tx], lh, ll, s2, nh, nl);
+                    // Laplacian of the quantized v: exact (quant_magic, qb = 20)
+                    const float sn = __fadd_rn(__fadd_rn(__fadd_rn(V[ly][lx - 1], V[ly][lx + 1]),
+                                                         __fadd_rn(V[ly - 1][lx], V[ly + 1][lx])),
+                                               __fadd_rn(Vm[ly][lx], Vp[ly][lx]));
+                    float nh, nl;
+                    ff_sub1(G[ly][lx + 3], S.lo[z & 1][ty + 8 * h][tx], fmaf(-6.f, v, sn), s2, nh, nl);
                     const size_t o = (size_t)z * gpl + (size_t)yo * rg.pitch + xo;
                     rlo[o] = nl;
                     rnew.p[o] = nh;
                     sq = fmaf(nh, nh, sq);
+                    mx = fmaxf(mx, fabsf(nh));
                 }
                 if (UPD) u[(size_t)z * upl + (size_t)yo * up + xo] = S.u[z & 1][ty + 8 * h][tx] + widen(v);
                 else vg(xo, yo, z) = v;
@@ -207,7 +218,11 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
     }
     if (RR) {
         const double s = block_sum((double)sq, sh);
-        if (tid == 0) part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * zc)] = s;
+        const float m = block_max(mx, shm);
+        if (tid == 0) {
+            part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * zc)] = s;
+            atomicMax(&ctl[prob].rmax[pq ^ 1], __float_as_uint(m));
+        }
     }
 }
 
@@ -387,24 +402,42 @@ __global__ void __launch_bounds__(256) k_m2r_faces_zm_3d(Mag3<const T> vm, Red3<
     }
 }
 
-// Eq. Erprolm: magenta corners (red EEE) from the 12 new face centres, cells [1, nb]^3
+// Eq. Erprolm: magenta corners (red EEE) from the 12 new face centres, cells
+// [1, nb]^3.  vctl (the finest triple of the fused mixed path): also the
+// largest |v| of the red level (the new corners and the face values read,
+// which cover every face value) into vctl[p].vmax
 template <typename T>
 __global__ void __launch_bounds__(256) k_m2r_corners_zm_3d(Red3<const T> vf, A3<const T> reee, A3<T> veee, int nb, T c2,
-                                                           int zm, const int *done, Bt B) {
+                                                           int zm, Ctrl *vctl, const int *done, Bt B) {
+    __shared__ float shm[32];
     const int prob = bt_prob(B);
     if (stop(bt_done(done, prob, B))) return;
     vf = bt_at(vf, prob, B); reee = bt_at(reee, prob, B); veee = bt_at(veee, prob, B);
     const int P = reee.pitch;
     const size_t Q = (size_t)P * reee.rows;
     ZmIdx z;
-    if (!zm_cell(z, 1, nb, zm, P, Q, B)) return;
-    const T *ooe = vf.ooe.p, *oeo = vf.oeo.p, *eoo = vf.eoo.p;
-    size_t i = z.i;
-    for (int c = z.c0; c < z.c1; c++, i += Q) {
-        const T s1 = (ooe[i - P - 1] + ooe[i - P]) + (ooe[i - 1] + ooe[i]);
-        const T s2 = (oeo[i - Q - 1] + oeo[i - Q]) + (oeo[i - 1] + oeo[i]);
-        const T s3 = (eoo[i - Q - P] + eoo[i - Q]) + (eoo[i - P] + eoo[i]);
-        veee.p[i] = ((s1 + s2 + s3) - c2 * reee.p[i]) * T(1.0 / 12.0);
+    float mx = 0.f;
+    if (zm_cell(z, 1, nb, zm, P, Q, B)) {
+        const T *ooe = vf.ooe.p, *oeo = vf.oeo.p, *eoo = vf.eoo.p;
+        size_t i = z.i;
+        for (int c = z.c0; c < z.c1; c++, i += Q) {
+            const T q[12] = {ooe[i - P - 1], ooe[i - P], ooe[i - 1], ooe[i], oeo[i - Q - 1], oeo[i - Q],
+                             oeo[i - 1],     oeo[i],     eoo[i - Q - P], eoo[i - Q], eoo[i - P], eoo[i]};
+            const T s1 = (q[0] + q[1]) + (q[2] + q[3]);
+            const T s2 = (q[4] + q[5]) + (q[6] + q[7]);
+            const T s3 = (q[8] + q[9]) + (q[10] + q[11]);
+            const T v = ((s1 + s2 + s3) - c2 * reee.p[i]) * T(1.0 / 12.0);
+            veee.p[i] = v;
+            if (vctl) {
+                mx = fmaxf(mx, (float)fabs(v));
+#pragma unroll
+                for (int k = 0; k < 12; k++) mx = fmaxf(mx, (float)fabs(q[k]));
+            }
+        }
+    }
+    if (vctl) {
+        mx = block_max(mx, shm);
+        if (threadIdx.x == 0 && threadIdx.y == 0) atomicMax(&vctl[prob].vmax, __float_as_uint(mx));
     }
 }
 

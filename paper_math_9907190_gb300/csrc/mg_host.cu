@@ -413,7 +413,10 @@ dim3 green_ff_grid(const mg_ctx *c, int n) {
 bool green_ff_use(int n) { return n >= 255; }
 
 template <typename T>
-void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *done, cudaStream_t s) {
+// vctl: the red level of the fused mixed path's finest triple also gets its
+// bound on |v| (ctl->vmax)
+void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *done, cudaStream_t s,
+                    Ctrl *vctl = nullptr) {
     const Level &a = c->lv[l], &b = c->lv[l + 1];
     const double hk = spacing(c, a), hk2 = hk * hk;
     const int dim = c->d.dim;
@@ -439,11 +442,11 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
                 LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_ff_3d<UP_ADD>), g3, dim3(32, 8, 1), sm,
                               red3v<const float>(b.v, b), a3<float>(a.r[0], a), (float *)nullptr, a3<float>(a.v[0], a),
                               (float *)nullptr, u, c->d.pitch, n, (float)cc, 0.f, zch, (double *)nullptr,
-                              (const int *)nullptr, done);
+                              (Ctrl *)nullptr, done);
             else
                 LAUNCH_SMEM_B(TAG_UP, (k_green_ff_3d<UP_STORE>), g3, dim3(32, 8, 1), sm, red3v<const float>(b.v, b),
                               a3<float>(a.r[0], a), (float *)nullptr, a3<float>(a.v[0], a), (float *)nullptr, u,
-                              c->d.pitch, n, (float)cc, 0.f, zch, (double *)nullptr, (const int *)nullptr, done);
+                              c->d.pitch, n, (float)cc, 0.f, zch, (double *)nullptr, (Ctrl *)nullptr, done);
         } else if (c->d.hierarchy == MG_DIAG && sizeof(T) == 4) {  // FP32: both half-sweeps in one tile kernel
             const dim3 g3((n + TX3 - 1) / TX3, (n + TY3 - 1) / TY3, (n + TZ3 - 1) / TZ3);
             const size_t sm = sizeof(Green3Smem<T>);
@@ -485,10 +488,10 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
         const T c1 = (T)(2.0 * om[1] * hk2), c2 = (T)(4.0 * om[2] * hk2);
         if (zm_use<T>(nb)) {
             LAUNCH_B(TAG_UP, (k_m2r_faces_zm_3d<T>), grid_zm(nb + 1, zm_planes(nb)), B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, zm_planes(nb), done);
-            LAUNCH_B(TAG_UP, (k_m2r_corners_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, zm_planes(nb), done);
+            LAUNCH_B(TAG_UP, (k_m2r_corners_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, zm_planes(nb), vctl, done);
         } else {
             LAUNCH_B(TAG_UP, (k_m2r_faces_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, done);
-            LAUNCH_B(TAG_UP, (k_m2r_corners_3d<T>), grid3(nb, nb, nb), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, done);
+            LAUNCH_B(TAG_UP, (k_m2r_corners_3d<T>), grid3(nb, nb, nb), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, vctl, done);
         }
     }
 }
@@ -650,7 +653,8 @@ int tile_dn(const mg_ctx *c, int k) { return c->tile_dn[k] >= 0 ? c->tile_dn[k] 
 int tile_up(const mg_ctx *c, int k) { return c->tile_up[k] >= 0 ? c->tile_up[k] : tile_default(c, k, true); }
 
 void launch_down_ff(mg_ctx *c, int k, int cls, const int *done, cudaStream_t s, bool alt);
-int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s, bool rr);
+int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s, bool rr,
+                 Ctrl *vctl = nullptr);
 
 template <typename T> void down_pair(mg_ctx *c, int k, int cls, const int *done, cudaStream_t s, bool alt) {
     if (sizeof(T) == 4) {
@@ -719,7 +723,7 @@ void launch_down_ff(mg_ctx *c, int k, int cls, const int *done, cudaStream_t s, 
 // solve with the carried residual (rr), the finest pair otherwise with u += v,
 // a coarser pair with v stored; returns the partial sums written per problem
 // (rr) or 0
-int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s, bool rr) {
+int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t s, bool rr, Ctrl *vctl) {
     const Level &g = c->lv[2 * k], &r = c->lv[2 * k + 1], &b = c->lv[2 * k + 2];
     const int nb = r.nb, tb = ff_strip(cls);
     const double hk = spacing(c, g), p = c->d.omega[0];
@@ -733,7 +737,7 @@ int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStre
 #define MG_UPFF(MODE, VU)                                                                                          \
     LAUNCH_B(tag, (k_up_ff_2d<MODE, VU>), grid, blk, a2<const float>(b.v[0], b), a2<const float>(r.r[0], r),     \
              a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b, a2<float>(g.v[0], g),           \
-             (float *)c->rlo, u, c->d.pitch, nb, c2, c1, s2, tb, c->part, rr ? &c->ctl->par : nullptr, done)
+             (float *)c->rlo, u, c->d.pitch, nb, c2, c1, s2, tb, c->part, rr ? c->ctl : vctl, done)
     if (rr) {
         if (vu) MG_UPFF(UP_RR, true);
         else MG_UPFF(UP_RR, false);
@@ -747,6 +751,17 @@ int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStre
     return rr ? (int)grid.x : 0;
 }
 
+// bound on |v| of level l (every array, ring included) into ctl->vmax, for
+// the quantizer of the fused finest sweep
+void launch_absmax(mg_ctx *c, const Level &l, const int *done, cudaStream_t s) {
+    AbsArrs A{};
+    for (int q = 0; q < l.ncos && q < 4; q++) A.a[q] = (const float *)l.v[q];
+    const int narr = c->d.dim == 3 ? l.ncos : 1, nz = c->d.dim == 3 ? l.rows : 1;
+    const int nrow = narr * nz * l.rows;
+    LAUNCH_B(TAG_UP, (k_absmax), dim3(std::min((nrow + 7) / 8, 1216), 1, 1), dim3(32, 8, 1), A, narr, l.rows, nz,
+             l.pitch, l.rows, c->ctl, done);
+}
+
 // one cycle of the fused mixed 2D path: restriction, coarse block, prolongation,
 // and the finest pair fused with u += v and the next residual; returns the
 // number of norm partial sums written per problem
@@ -757,7 +772,14 @@ int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
         LAUNCH_SMEM_B(TAG_COARSE, (k_coarse_cta_2d<float>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan2d,
                       a2<const float>(g.r[0], g), a2<float>(g.v[0], g), c->G, done);
     }
-    for (int k = c->kc - 1; k >= 1; k--) up_pair<float>(c, k, tile_up(c, k), u, done, s);
+    // the blue level of the finest pair (pair 1's v) also gets its bound on |v|:
+    // in the streaming kernel that forms it, else by a separate pass
+    const bool vfused = c->kc >= 2 && tile_up(c, 1) < 3;
+    for (int k = c->kc - 1; k >= 1; k--) {
+        if (k == 1 && vfused) launch_up_ff(c, 1, tile_up(c, 1), nullptr, done, s, false, c->ctl);
+        else up_pair<float>(c, k, tile_up(c, k), u, done, s);
+    }
+    if (!vfused) launch_absmax(c, c->lv[2], done, s);
     return up_pair<float>(c, 0, tile_up(c, 0), u, done, s, true);
 }
 
@@ -776,17 +798,17 @@ int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, 
     if (c->d.dim == 3) {
         if (start)
             LAUNCH_B(TAG_RESIDUAL, (k_res_rr_3d<true>), g, B2, f, u, c->d.pitch, n, lg, a3<float>(l0.r[0], l0),
-                     (float *)c->rlo, l0.pitch, c->part, fpart, done);
+                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, done);
         else
             LAUNCH_B(TAG_RESIDUAL, (k_res_rr_3d<false>), g, B2, f, u, c->d.pitch, n, lg, a3<float>(l0.r[0], l0),
-                     (float *)c->rlo, l0.pitch, c->part, fpart, done);
+                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, done);
     } else {
         if (start)
             LAUNCH_B(TAG_RESIDUAL, (k_res_rr_2d<true>), g, B2, f, u, c->d.pitch, n, lg, a2<float>(l0.r[0], l0),
-                     (float *)c->rlo, l0.pitch, c->part, fpart, done);
+                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, done);
         else
             LAUNCH_B(TAG_RESIDUAL, (k_res_rr_2d<false>), g, B2, f, u, c->d.pitch, n, lg, a2<float>(l0.r[0], l0),
-                     (float *)c->rlo, l0.pitch, c->part, fpart, done);
+                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, done);
     }
     c->nparts = np;
     return np;
@@ -799,7 +821,7 @@ int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     const Level &gk = c->lv[lc];
     LAUNCH_SMEM_B(TAG_COARSE, (k_coarse_cta_3d<float>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan3d,
                   a3<const float>(gk.r[0], gk), a3<float>(gk.v[0], gk), c->G, done);
-    for (int l = lc - 1; l >= 1; l--) launch_prolong<float>(c, l, c->d.omega, nullptr, done, s);
+    for (int l = lc - 1; l >= 1; l--) launch_prolong<float>(c, l, c->d.omega, nullptr, done, s, l == 1 ? c->ctl : nullptr);
     const Level &a = c->lv[0], &b = c->lv[1];
     const int n = c->d.n;
     const double h2 = c->h * c->h;
@@ -807,7 +829,7 @@ int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_ff_3d<UP_RR>), g3, dim3(32, 8, 1), sizeof(GreenSSmem),
                   red3v<const float>(b.v, b), a3<float>(a.r[0], a), (float *)c->r32b, a3<float>(a.v[0], a),
                   (float *)c->rlo, u, c->d.pitch, n, (float)(c->d.omega[3] * h2), (float)(1.0 / h2),
-                  green_ff_zch(c, n), c->part, &c->ctl->par, done);
+                  green_ff_zch(c, n), c->part, c->ctl, done);
     return (int)(g3.x * g3.y * g3.z);
 }
 

@@ -81,6 +81,38 @@ __device__ __forceinline__ const int *bt_done(const int *done, int p, const Bt &
     return done ? done + (size_t)p * B.ctl_stride : nullptr;
 }
 
+// Solver control word, one per context (device memory)
+struct Ctrl {
+    double f2;      // ||r(u=0)||^2
+    double r2;      // ||r||^2 of the current iterate
+    double relres;  // sqrt(r2/f2)
+    double rel0;    // relative residual of the warm start
+    double rtol;
+    int done;       // 1: stop every kernel of the remaining cycles
+    int cycles;     // corrections applied
+    int max_cycles;
+    int status;     // 0 ok, -4 not converged, -5 diverged
+    int par;        // which of the two FP32 finest residual buffers is current (fused update path)
+    // fused mixed path: bounds that the finest sweep rounds its correction
+    // against (bit patterns of non-negative floats, which order as unsigned)
+    unsigned vmax;     // max |v| of the level the finest sweep starts from, this cycle
+    unsigned rmax[2];  // max |hi| of each of the two finest residual buffers
+};
+
+// maximum of v over the block (valid in thread 0); NaN is ignored
+__device__ __forceinline__ float block_max(float v, float *sh) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    __syncthreads();
+    if (tid < 32) {
+        v = tid < (nt + 31) / 32 ? sh[tid] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+    }
+    return v;
+}
+
 // f32 -> f64 widening with integer operations (the FP64 pipe is the scarce
 // resource on this GPU).  Exact for normal numbers and zero; FP32 subnormals
 // (|x| < 2^-126) map to signed zero.
@@ -300,6 +332,17 @@ __device__ __forceinline__ T fcc12(const A3<const T> &ooe, const A3<const T> &oe
     T s3 = (eoo(a, b - 1, c - 1) + eoo(a, b, c - 1)) + (eoo(a, b - 1, c) + eoo(a, b, c));
     return s1 + s2 + s3;
 }
+// the largest of m and the magnitudes of the 12 values fcc12 sums
+template <typename T>
+__device__ __forceinline__ float fcc12_absmax(const A3<const T> &ooe, const A3<const T> &oeo, const A3<const T> &eoo,
+                                              int a, int b, int c, float m) {
+    const T q[12] = {ooe(a - 1, b - 1, c), ooe(a, b - 1, c), ooe(a - 1, b, c), ooe(a, b, c),
+                     oeo(a - 1, b, c - 1), oeo(a, b, c - 1), oeo(a - 1, b, c), oeo(a, b, c),
+                     eoo(a, b - 1, c - 1), eoo(a, b, c - 1), eoo(a, b - 1, c), eoo(a, b, c)};
+#pragma unroll
+    for (int k = 0; k < 12; k++) m = fmaxf(m, (float)fabs(q[k]));
+    return m;
+}
 
 // red -> magenta: corners, Eq. Ermagc (12r + 12 FCC neighbours)/24; centres,
 // Eq. Ermagm mean of the 6 face-centre neighbours.  Thread per cell in [0,nb]^3.
@@ -394,16 +437,28 @@ __global__ void k_m2r_faces_3d(Mag3<const T> vm, Red3<const T> rr, Red3<T> vr, i
 
 // Eq. Erprolm: magenta corners (red EEE) from the 12 new face centres; c2 = 4 p_r2 h^2
 template <typename T>
+// vctl (the finest triple of the fused mixed path): also the largest |v| of
+// the red level -- the new corner and the 12 face values each cell reads,
+// which cover every face value -- into vctl[p].vmax
 __global__ void k_m2r_corners_3d(Red3<const T> vr_faces, A3<const T> reee, A3<T> veee, int nb, T c2,
-                                 const int *done, Bt B) {
+                                 Ctrl *vctl, const int *done, Bt B) {
+    __shared__ float shm[32];
     const int prob_ = bt_prob(B);
     if (stop(bt_done(done, prob_, B))) return;
     vr_faces = bt_at(vr_faces, prob_, B);
     reee = bt_at(reee, prob_, B);
     veee = bt_at(veee, prob_, B);
     MG_IDX3 const int a = tx + 1, b = ty + 1, c = tz + 1;
-    if (a > nb || b > nb || c > nb) return;
-    veee(a, b, c) = (fcc12(vr_faces.ooe, vr_faces.oeo, vr_faces.eoo, a, b, c) - c2 * reee(a, b, c)) * T(1.0 / 12.0);
+    float mx = 0.f;
+    if (a <= nb && b <= nb && c <= nb) {
+        const T v = (fcc12(vr_faces.ooe, vr_faces.oeo, vr_faces.eoo, a, b, c) - c2 * reee(a, b, c)) * T(1.0 / 12.0);
+        if (vctl) mx = fcc12_absmax(vr_faces.ooe, vr_faces.oeo, vr_faces.eoo, a, b, c, (float)fabs(v));
+        veee(a, b, c) = v;
+    }
+    if (vctl) {
+        mx = block_max(mx, shm);
+        if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) atomicMax(&vctl[prob_].vmax, __float_as_uint(mx));
+    }
 }
 
 // Eq. Egprolg: green-only points (i+j+k odd) from the six axis red values; c = p_g h^2
@@ -534,6 +589,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return v;
 }
 
+
 // r = f - L_h u (Eq. Evpois, 5-point) or Eq. Efos2 (ORDER 4); RHS_ONLY: u = 0.
 // Writes r (level precision) and, if r64 != nullptr, the FP64 value to the
 // caller grid; block partial sums of r^2 to part[block].
@@ -616,19 +672,6 @@ __global__ void k_res_3d(const double *__restrict__ f, const double *__restrict_
         part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bt_z(B))] = s;
 }
 
-// Solver control word, one per context (device memory)
-struct Ctrl {
-    double f2;      // ||r(u=0)||^2
-    double r2;      // ||r||^2 of the current iterate
-    double relres;  // sqrt(r2/f2)
-    double rel0;    // relative residual of the warm start
-    double rtol;
-    int done;       // 1: stop every kernel of the remaining cycles
-    int cycles;     // corrections applied
-    int max_cycles;
-    int status;     // 0 ok, -4 not converged, -5 diverged
-    int par;        // which of the two FP32 finest residual buffers is current (fused update path)
-};
 
 // deterministic sum of part[0..nblk) by one block of 1024 threads (fixed order)
 __device__ __forceinline__ double sum_parts(const double *part, int nblk, double *sh) {
@@ -651,6 +694,8 @@ __global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, in
     double s = sum_parts(part, nblk, sh);
     if (threadIdx.x != 0) return;
     if (!first) ctl->par ^= 1;
+    ctl->rmax[ctl->par ^ 1] = 0u;  // the buffer the next cycle writes
+    ctl->vmax = 0u;
     ctl->r2 = s;
     double rel = ctl->f2 > 0.0 ? sqrt(s / ctl->f2) : 0.0;
     ctl->relres = rel;
@@ -674,6 +719,7 @@ __global__ void k_ctrl_init(Ctrl *ctl, double rtol, int max_cycles) {
     pdl_wait();
     ctl->r2 = 0.0; ctl->relres = 0.0; ctl->rel0 = 0.0; ctl->rtol = rtol;
     ctl->done = 0; ctl->cycles = 0; ctl->max_cycles = max_cycles; ctl->status = 0; ctl->par = 0;
+    ctl->vmax = 0u; ctl->rmax[0] = 0u; ctl->rmax[1] = 0u;
 }
 
 // per problem of a batch (one block each): f2 = sum of that problem's partials
@@ -690,6 +736,7 @@ __global__ void k_ctrl_init_b(Ctrl *ctl, int nprob, double rtol, int max_cycles)
         Ctrl &c = ctl[p];
         c.r2 = 0.0; c.relres = 0.0; c.rel0 = 0.0; c.rtol = rtol;
         c.done = 0; c.cycles = 0; c.max_cycles = max_cycles; c.status = 0; c.par = 0;
+        c.vmax = 0u; c.rmax[0] = 0u; c.rmax[1] = 0u;
     }
 }
 
@@ -704,6 +751,8 @@ __global__ void k_ctrl_b(const double *part, int nblk, Ctrl *ctl, double *hist, 
     double s = sum_parts(part + (size_t)p * nblk, nblk, sh);
     if (threadIdx.x != 0) return;
     if (!first) c->par ^= 1;
+    c->rmax[c->par ^ 1] = 0u;
+    c->vmax = 0u;
     c->r2 = s;
     double rel = c->f2 > 0.0 ? sqrt(s / c->f2) : 0.0;
     c->relres = rel;
@@ -734,6 +783,32 @@ __global__ void k_final_true(const double *part, int nblk, Ctrl *ctl) {
     c->r2 = s;
     c->relres = rel;
     if (c->status == 0 && !(rel <= c->rtol)) c->status = -4;
+}
+
+// max |x| over the narr arrays (a[0..narr)) of a level, each ext^2 (2D, nz =
+// 1) or ext^3 values with row pitch `pitch` and `rows` rows per plane, into
+// ctl[p].vmax as float bits, per problem p of a batch.  One warp per row.
+// The fused finest sweep of the mixed path bounds its correction by it.
+struct AbsArrs {
+    const float *a[4];
+};
+__global__ void __launch_bounds__(256) k_absmax(AbsArrs A, int narr, int ext, int nz, int pitch, int rows, Ctrl *ctl,
+                                                const int *done, Bt B) {
+    __shared__ float sh[32];
+    const int prob = bt_prob(B);
+    if (stop(bt_done(done, prob, B))) return;
+    const size_t plane = (size_t)pitch * rows;
+    const int nrow = narr * nz * ext;
+    float m = 0.f;
+    for (int q = blockIdx.x * 8 + threadIdx.y; q < nrow; q += gridDim.x * 8) {
+        const int arr = q / (nz * ext), rz = q - arr * (nz * ext), z = rz / ext, y = rz - z * ext;
+        const float *a = arr == 0 ? A.a[0] : arr == 1 ? A.a[1] : arr == 2 ? A.a[2] : A.a[3];
+        const float *row = bt_ptr(a, prob, B) + (size_t)z * plane + (size_t)y * pitch;
+#pragma unroll 4
+        for (int x = threadIdx.x; x < ext; x += 32) m = fmaxf(m, fabsf(row[x]));
+    }
+    m = block_max(m, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) atomicMax(&ctl[prob].vmax, __float_as_uint(m));
 }
 
 // loop condition of a batch: continue while any problem is not done

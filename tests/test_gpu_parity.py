@@ -250,6 +250,40 @@ def test_mixed_vcycle_iterates_follow_oracle(dim, n, om):
             assert rel <= 2e-6, f"cycle {cyc}: rel {rel:.3e}"
 
 
+@pytest.mark.parametrize("dim,n,om", [(2, 511, (1.052,)), (2, 2047, (1.052,)), (3, 127, (1.11, 1.42, 1.08, 0.99)),
+                                      (3, 255, (1.11, 1.42, 1.08, 0.99))])
+def test_mixed_solve_iterates_follow_oracle(dim, n, om):
+    """The fused finest kernels of the mixed solve (correction rounded to a
+    quantum of 2^-21 (2D) / 2^-20 (3D) of a bound on its size, u += v, the
+    carried residual r -= L v) give the oracle's V-cycle iterates from u = 0
+    to FP32 accuracy, cycle by cycle."""
+    f = I.uniform_f(dim, n, 3) if dim == 2 else I.cube(n)
+    uo = O.grid(dim, n)
+    with Context(dim, n, precision="mixed", omega=om) as c:
+        ft = T(f)
+        for k in (1, 2, 3):
+            O.vcycle(f, uo, omega=list(om))
+            ug, it, _, _ = c.solve(ft, rtol=1e-300, max_cycles=k, raise_on_fail=False)
+            assert it == k
+            rel = np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo)
+            assert rel <= 4e-6, f"cycle {k}: rel {rel:.3e}"
+
+
+@pytest.mark.parametrize("dim,n", [(2, 127), (2, 1023), (3, 63), (3, 255)])
+def test_mixed_carried_residual_tracks_direct_residual(dim, n):
+    """After k cycles the carried residual (the history's last entry) equals
+    the direct residual of the returned u (the reported one): u += v and
+    r -= L v use the same rounded v and L v is exact, so they differ only by
+    the float-float rounding of r, the FP64 rounding of u and the FP32 squares
+    of the norms."""
+    f = T(I.uniform_f(dim, n, 5))
+    with Context(dim, n, precision="mixed") as c:
+        for k in (1, 2, 3, 4):
+            _, it, rel, hist = c.solve(f, rtol=1e-300, max_cycles=k, raise_on_fail=False)
+            assert it == k and len(hist) == k
+            assert abs(hist[-1] - rel) <= 1e-5 * rel, (k, hist[-1], rel)
+
+
 @pytest.mark.parametrize("coarsest", [1, 3, 7])
 def test_vcycle_coarsest_variants(coarsest):
     n = 63
