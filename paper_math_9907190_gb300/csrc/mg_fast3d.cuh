@@ -14,7 +14,10 @@ constexpr int GS_RH = GS_TY + 6;                 // red rows: tile +- 3
 constexpr int GS_RC = GS_TX / 2 + 8;             // red values per row: 16-byte chunks over the tile +- 3
 constexpr int GS_VW = GS_TX + 4, GS_VH = GS_TY + 4;  // F region: tile +- 2
 constexpr int GS_GW = GS_TX + 8;                 // residual row: 16-byte chunks over x0-5 .. x0+34
-constexpr int GS_WARM = 6;                        // steps before the first output plane
+// steps before the first output plane: the rings start with red planes
+// z+1..z+3 and residual plane z+2, so F is right from the first step; the
+// carried residual of plane z needs C of plane z-1, hence F from z-2
+constexpr int GS_WARM = 3, GS_WARM_RR = 4;
 
 __device__ __forceinline__ void cp_async4(void *dst, const void *src, bool ok) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
@@ -38,8 +41,8 @@ struct GreenSSmem {
 // plane z is final.  MODE: UP_RR the mixed finest triple (u += v and the
 // carried float-float residual r -= L v as in k_up_ff_2d, six neighbours;
 // rga/rgb double-buffered by par); UP_ADD u += v; UP_STORE v stored in vg.
-// A block's z range holds zch output planes; its first GS_WARM steps fill
-// the rings (nothing is written).
+// A block's z range holds zch output planes; its first GS_WARM (UP_RR:
+// GS_WARM_RR) steps fill the rings (nothing is written).
 template <int MODE>
 __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<float> rga, float *rgb, A3<float> vg,
                                                      float *__restrict__ rlo, double *__restrict__ u, int up, int n,
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
     const int x0 = blockIdx.x * GS_TX + 1, y0 = blockIdx.y * GS_TY + 1;
     const int zb = zc * zch + 1, ze = min(zb + zch, n + 1);  // output planes [zb, ze)
-    const int zs = zb - GS_WARM;
+    const int zs = zb - (RR ? GS_WARM_RR : GS_WARM);
     const size_t rows = (size_t)(n + 2), upl = (size_t)up * rows, gpl = (size_t)rg.pitch * rows;
     const size_t cpl = (size_t)vr.eee.pitch * vr.eee.rows;  // the four red cosets share their layout
     // the F region (tile +- 2) lies in the interior: no bounds tests but the plane's
@@ -102,13 +105,16 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
     // chunks of the dense coset / level rows; chunks outside the arrays are
     // zero-filled, and only values at interior points or the zero ring are
     // used), and u / lo of output plane zo when it is one
-    auto issue = [&](int zp, int zr, int zo) {
+    auto red_copy = [&](int zp) {
         if (rq_on) {
             const bool ok = rq_ok && zp >= 0 && zp <= n + 1;
             // the coset holding row y of plane zp: EEE, OOE (zp even), OEO, EOO (zp odd)
             const float *C = (zp & 1) ? ((rq_y & 1) ? vr.eoo.p : vr.oeo.p) : ((rq_y & 1) ? vr.ooe.p : vr.eee.p);
             cp_async16(&S.red[zp & 3][rq_ly][4 * rq_j], ok ? C + (size_t)(zp >> 1) * cpl + rq_off : C, ok);
         }
+    };
+    auto issue = [&](int zp, int zr, int zo) {
+        red_copy(zp);
         if (gq_on) {
             const bool ok = gq_ok && zr >= 0 && zr <= n + 1;
             cp_async16(&S.r[zr & 3][gq_ly][4 * gq_j], ok ? rg.p + (size_t)zr * gpl + gq_off : rg.p, ok);
@@ -129,6 +135,8 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
     // ring slots not written by a step before they are read hold zeros
     for (int q = tid; q < (int)(sizeof(GreenSSmem) / 4); q += 256) reinterpret_cast<float *>(smraw)[q] = 0.f;
     __syncthreads();
+    red_copy(zs + 1);
+    red_copy(zs + 2);
     issue(zs + 3, zs + 2, zs);
     float sq = 0.f, mx = 0.f;
     for (int z = zs; z < ze; z++) {

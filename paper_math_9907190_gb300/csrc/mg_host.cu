@@ -394,27 +394,26 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
     }
 }
 
-// prolongation v^(l) <- v^(l+1), r^(l); on level 0 with u != nullptr the
-// second half-sweep also applies u += v
-// z range (output planes per block) of k_green_ff_3d: about 600 blocks, at
-// most 64 and at least 8 planes each
-// z range of a block: the grid fills the resident block slots once (a second,
-// partial wave would double the time of a launch), at least 8 planes
+// z range (output planes per block) of k_green_ff_3d: the grid fills the
+// resident block slots once (a second, partial wave would double the time of
+// a launch), at least 4 planes
 int green_ff_zch(const mg_ctx *c, int n) {
     const int cols = ((n + GS_TX - 1) / GS_TX) * ((n + GS_TY - 1) / GS_TY);
     const int chunks = std::max(1, c->gs_resident / (cols * c->nprob));
-    return std::max(8, (n + chunks - 1) / chunks);
+    return std::max(4, (n + chunks - 1) / chunks);
 }
 dim3 green_ff_grid(const mg_ctx *c, int n) {
     const int zch = green_ff_zch(c, n);
     return dim3((n + GS_TX - 1) / GS_TX, (n + GS_TY - 1) / GS_TY, (n + zch - 1) / zch);
 }
-// the z-streaming green sweep pays GS_WARM steps per z range: used from 255^3 up
-bool green_ff_use(int n) { return n >= 255; }
+// the z-streaming green sweep pays GS_WARM steps per z range: used from 63^3 up
+// (measured faster than the 3D tile kernel there)
+bool green_ff_use(int n) { return n >= 63; }
 
+// prolongation v^(l) <- v^(l+1), r^(l); on level 0 with u != nullptr the
+// second half-sweep also applies u += v.  vctl: the red level of the fused
+// mixed path's finest triple also gets its bound on |v| (ctl->vmax)
 template <typename T>
-// vctl: the red level of the fused mixed path's finest triple also gets its
-// bound on |v| (ctl->vmax)
 void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *done, cudaStream_t s,
                     Ctrl *vctl = nullptr) {
     const Level &a = c->lv[l], &b = c->lv[l + 1];
