@@ -1267,7 +1267,7 @@ namespace mg {
 // of 32 x 8 x 4 green points.  The red level is staged as its four cosets
 // (coalesced loads of dense arrays), the F (odd) points are computed on the
 // tile +- 2, the C (even) points on the tile +- 1.  FINEST: u += v,
-// otherwise v stored.  (FP32 triples from 63^3 up use the z-streaming
+// otherwise v stored.  (FP32 triples from 31^3 up use the z-streaming
 // k_green_ff_3d.)
 // ---------------------------------------------------------------------------
 constexpr int TX3 = 32, TY3 = 8, TZ3 = 4;

@@ -28,7 +28,7 @@ struct GreenSSmem {
     // red planes z+1..z+4 (ring, slot = plane & 3): fine row y holds its red
     // points x (x = y + plane mod 2) at index (x >> 1) - (16 bx - 4)
     float red[4][GS_RH][GS_RC];
-    float r[4][GS_VH][GS_GW];    // green residual planes z..z+3 (ring), x from x0 - 5
+    float r[4][GS_VH][GS_GW];    // green residual planes z..z+3 (ring), x from x0 - 4
     float v[4][GS_VH][GS_VW];    // correction planes z-1..z+2 (ring): F at odd, C at even points
     double u[2][GS_TY][GS_TX];   // u of output planes z, z+1 (UP_RR, UP_ADD)
     float lo[2][GS_TY][GS_TX];   // lo of the carried residual, planes z, z+1 (UP_RR)
@@ -42,8 +42,11 @@ struct GreenSSmem {
 // carried float-float residual r -= L v as in k_up_ff_2d, six neighbours;
 // rga/rgb double-buffered by par); UP_ADD u += v; UP_STORE v stored in vg.
 // A block's z range holds zch output planes; its first GS_WARM (UP_RR:
-// GS_WARM_RR) steps fill the rings (nothing is written).
-template <int MODE>
+// GS_WARM_RR) steps fill the rings (nothing is written).  The tile's x range
+// starts at a multiple of 32 (x = 0 is the ring), so that a thread's two
+// adjacent output points are one aligned pair of every array; VU: u is
+// 16-byte aligned with an even pitch (vector access to u).
+template <int MODE, bool VU>
 __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<float> rga, float *rgb, A3<float> vg,
                                                      float *__restrict__ rlo, double *__restrict__ u, int up, int n,
                                                      float cg, float s2, int zch, double *part, Ctrl *ctl,
@@ -73,7 +76,7 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
     if (UPD && B.utab) u = B.utab[prob];
     if (RR) part += (size_t)prob * B.nparts;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
-    const int x0 = blockIdx.x * GS_TX + 1, y0 = blockIdx.y * GS_TY + 1;
+    const int x0 = blockIdx.x * GS_TX, y0 = blockIdx.y * GS_TY + 1;
     const int zb = zc * zch + 1, ze = min(zb + zch, n + 1);  // output planes [zb, ze)
     const int zs = zb - (RR ? GS_WARM_RR : GS_WARM);
     const size_t rows = (size_t)(n + 2), upl = (size_t)up * rows, gpl = (size_t)rg.pitch * rows;
@@ -85,13 +88,15 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
     // red copy: fine row y0-3+ly, 16-byte chunk j of coset values (x >> 1) from 16 bx - 4
     const int rq_ly = tid / RCH, rq_j = tid - rq_ly * RCH, rq_y = y0 - 3 + rq_ly;
     const bool rq_on = tid < GS_RH * RCH;
-    const bool rq_ok = rq_on && rq_y >= 0 && rq_y <= n + 1 && (x0 - 1) / 2 - 4 + 4 * rq_j >= 0;
-    const size_t rq_off = rq_ok ? (size_t)(rq_y >> 1) * vr.eee.pitch + ((x0 - 1) / 2 - 4 + 4 * rq_j) : 0;
-    // residual copy: row y0-2+ly, chunk j of x from x0 - 5
-    const int gq_ly = tid / GCH, gq_j = tid - gq_ly * GCH, gq_y = y0 - 2 + gq_ly, gq_x = x0 - 5 + 4 * gq_j;
+    const bool rq_ok = rq_on && rq_y >= 0 && rq_y <= n + 1 && (x0 >> 1) - 4 + 4 * rq_j >= 0;
+    const size_t rq_off = rq_ok ? (size_t)(rq_y >> 1) * vr.eee.pitch + ((x0 >> 1) - 4 + 4 * rq_j) : 0;
+    // residual copy: row y0-2+ly, chunk j of x from x0 - 4
+    const int gq_ly = tid / GCH, gq_j = tid - gq_ly * GCH, gq_y = y0 - 2 + gq_ly, gq_x = x0 - 4 + 4 * gq_j;
     const bool gq_on = tid < GS_VH * GCH;
     const bool gq_ok = gq_on && gq_x >= 0 && gq_y >= 0 && gq_y <= n + 1;
     const size_t gq_off = gq_ok ? (size_t)gq_y * rg.pitch + gq_x : 0;
+    // output points: row oy of the tile, columns 2 ox and 2 ox + 1
+    const int ox = tid & 15, oy = tid >> 4;
     // F items (row ly, k-th point of the row's parity) and C items
     int f_ly[2], f_k[2], f_pb[2], c_ly[2], c_k[2], c_pb[2];
 #pragma unroll
@@ -120,13 +125,21 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
             cp_async16(&S.r[zr & 3][gq_ly][4 * gq_j], ok ? rg.p + (size_t)zr * gpl + gq_off : rg.p, ok);
         }
         if (UPD && zo >= zb && zo < ze) {
-            const int xo = x0 + tx;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int ly = ty + 8 * h, yo = y0 + ly;
-                const bool ok = xo <= n && yo <= n;
-                cp_async8(&S.u[zo & 1][ly][tx], ok ? u + (size_t)zo * upl + (size_t)yo * up + xo : u, ok);
-                if (RR) cp_async4(&S.lo[zo & 1][ly][tx], ok ? rlo + (size_t)zo * gpl + (size_t)yo * rg.pitch + xo : rlo, ok);
+            // u: row oy, columns x0 + 2 ox, +1 (x0 + 31 <= n: n + 1 is a multiple of 32)
+            const int yo = y0 + oy;
+            const bool ok = yo <= n;
+            const double *src = ok ? u + (size_t)zo * upl + (size_t)yo * up + x0 + 2 * ox : u;
+            if (VU) {
+                cp_async16(&S.u[zo & 1][oy][2 * ox], src, ok);
+            } else {
+                cp_async8(&S.u[zo & 1][oy][2 * ox], src, ok);
+                cp_async8(&S.u[zo & 1][oy][2 * ox + 1], ok ? src + 1 : u, ok);
+            }
+            if (RR && tid < GS_TY * GS_TX / 4) {  // lo: row tid / 8, 16-byte chunk tid % 8
+                const int ly = tid >> 3, j = tid & 7, yl = y0 + ly;
+                const bool okl = yl <= n;
+                cp_async16(&S.lo[zo & 1][ly][4 * j],
+                           okl ? rlo + (size_t)zo * gpl + (size_t)yl * rg.pitch + x0 + 4 * j : rlo, okl);
             }
         }
         cp_async_commit();
@@ -144,7 +157,7 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
         __syncthreads();                             // step z's planes landed; step z-1 is done with every slot
         if (z + 1 < ze) issue(z + 4, z + 3, z + 1);  // the next step's planes, in flight during this one
         // F on plane z+2, tile +- 2: the red neighbours of the k-th F point of
-        // a row are the row's red values k+3, k+4 and value k+3+p of rows
+        // a row are the row's red values k+2+p, k+3+p and value k+3 of rows
         // y +- 1 and of planes z+1, z+3 (p: x parity offset of the row)
         {
             const int zf = z + 2;
@@ -161,10 +174,10 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
                 const int x = x0 - 2 + lx, y = y0 - 2 + ly;
                 float val = 0.f;
                 if (zin && (inner || (x >= 1 && x <= n && y >= 1 && y <= n))) {
-                    const int ry = ly + 1, ac = k + 3 + p;
-                    const float s = (R0[ry][k + 3] + R0[ry][k + 4]) + (R0[ry - 1][ac] + R0[ry + 1][ac]) +
-                                    (Rm[ry][ac] + Rp[ry][ac]);
-                    val = (s - cg * G[ly][lx + 3]) * (1.f / 6.f);
+                    const int ry = ly + 1, ac = k + 2 + p;
+                    const float s = (R0[ry][ac] + R0[ry][ac + 1]) + (R0[ry - 1][k + 3] + R0[ry + 1][k + 3]) +
+                                    (Rm[ry][k + 3] + Rp[ry][k + 3]);
+                    val = (s - cg * G[ly][lx + 2]) * (1.f / 6.f);
                 }
                 V[ly][lx] = RR ? quant(val, M) : val;
             }
@@ -187,40 +200,63 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
                 if (zin && (inner || (x >= 1 && x <= n && y >= 1 && y <= n))) {
                     const float s = (V[ly][lx - 1] + V[ly][lx + 1]) + (V[ly - 1][lx] + V[ly + 1][lx]) +
                                     (Vm[ly][lx] + Vp[ly][lx]);
-                    val = (s - cg * G[ly][lx + 3]) * (1.f / 6.f);
+                    val = (s - cg * G[ly][lx + 2]) * (1.f / 6.f);
                 }
                 V[ly][lx] = RR ? quant(val, M) : val;
             }
         }
         __syncthreads();
-        // plane z is final on the tile
+        // plane z is final on the tile: a thread's points (x, y), (x + 1, y),
+        // x = x0 + 2 ox even; x = 0 is the ring, and x <= n implies x + 1 <= n
         if (z >= zb) {
-            const float(&V)[GS_VH][GS_VW] = S.v[z & 3];
-            const float(&Vm)[GS_VH][GS_VW] = S.v[(z - 1) & 3];
-            const float(&Vp)[GS_VH][GS_VW] = S.v[(z + 1) & 3];
-            const float(&G)[GS_VH][GS_GW] = S.r[z & 3];
-            const int xo = x0 + tx;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int yo = y0 + ty + 8 * h;
-                if (xo > n || yo > n) continue;
-                const int lx = tx + 2, ly = ty + 8 * h + 2;
-                const float v = V[ly][lx];
+            const int xo = x0 + 2 * ox, yo = y0 + oy;
+            if (xo <= n && yo <= n) {
+                const float(&V)[GS_VH][GS_VW] = S.v[z & 3];
+                const int lx = 2 * ox + 2, ly = oy + 2;
+                const float2 c = *reinterpret_cast<const float2 *>(&V[ly][lx]);
+                const bool lft = xo >= 1;  // (x, y) is interior
+                float2 nh2 = make_float2(0.f, 0.f), nl2 = make_float2(0.f, 0.f);
                 if (RR) {
+                    const float(&Vm)[GS_VH][GS_VW] = S.v[(z - 1) & 3];
+                    const float(&Vp)[GS_VH][GS_VW] = S.v[(z + 1) & 3];
+                    const float2 dn = *reinterpret_cast<const float2 *>(&V[ly - 1][lx]);
+                    const float2 upr = *reinterpret_cast<const float2 *>(&V[ly + 1][lx]);
+                    const float2 zm = *reinterpret_cast<const float2 *>(&Vm[ly][lx]);
+                    const float2 zp = *reinterpret_cast<const float2 *>(&Vp[ly][lx]);
+                    const float2 g = *reinterpret_cast<const float2 *>(&S.r[z & 3][ly][lx + 2]);
+                    const float2 l = *reinterpret_cast<const float2 *>(&S.lo[z & 1][oy][2 * ox]);
                     // Laplacian of the quantized v: exact (quant_magic, qb = 20)
-                    const float sn = __fadd_rn(__fadd_rn(__fadd_rn(V[ly][lx - 1], V[ly][lx + 1]),
-                                                         __fadd_rn(V[ly - 1][lx], V[ly + 1][lx])),
-                                               __fadd_rn(Vm[ly][lx], Vp[ly][lx]));
-                    float nh, nl;
-                    ff_sub1(G[ly][lx + 3], S.lo[z & 1][ty + 8 * h][tx], fmaf(-6.f, v, sn), s2, nh, nl);
+                    const float sa = __fadd_rn(__fadd_rn(__fadd_rn(V[ly][lx - 1], c.y), __fadd_rn(dn.x, upr.x)),
+                                               __fadd_rn(zm.x, zp.x));
+                    const float sb = __fadd_rn(__fadd_rn(__fadd_rn(c.x, V[ly][lx + 2]), __fadd_rn(dn.y, upr.y)),
+                                               __fadd_rn(zm.y, zp.y));
+                    ff_sub1(g.x, l.x, fmaf(-6.f, c.x, sa), s2, nh2.x, nl2.x);
+                    ff_sub1(g.y, l.y, fmaf(-6.f, c.y, sb), s2, nh2.y, nl2.y);
+                    if (!lft) nh2.x = nl2.x = 0.f;
+                    sq = fmaf(nh2.x, nh2.x, fmaf(nh2.y, nh2.y, sq));
+                    mx = fmaxf(mx, fmaxf(fabsf(nh2.x), fabsf(nh2.y)));
                     const size_t o = (size_t)z * gpl + (size_t)yo * rg.pitch + xo;
-                    rlo[o] = nl;
-                    rnew.p[o] = nh;
-                    sq = fmaf(nh, nh, sq);
-                    mx = fmaxf(mx, fabsf(nh));
+                    if (lft) {
+                        *reinterpret_cast<float2 *>(rlo + o) = nl2;
+                        *reinterpret_cast<float2 *>(rnew.p + o) = nh2;
+                    } else {
+                        rlo[o + 1] = nl2.y;
+                        rnew.p[o + 1] = nh2.y;
+                    }
                 }
-                if (UPD) u[(size_t)z * upl + (size_t)yo * up + xo] = S.u[z & 1][ty + 8 * h][tx] + widen(v);
-                else vg(xo, yo, z) = v;
+                if (UPD) {
+                    const double2 uo = *reinterpret_cast<const double2 *>(&S.u[z & 1][oy][2 * ox]);
+                    double *ud = u + (size_t)z * upl + (size_t)yo * up + xo;
+                    const double ub = uo.y + widen(c.y);
+                    if (VU && lft) {
+                        *reinterpret_cast<double2 *>(ud) = make_double2(uo.x + widen(c.x), ub);
+                    } else {
+                        if (lft) ud[0] = uo.x + widen(c.x);
+                        ud[1] = ub;
+                    }
+                } else {
+                    *reinterpret_cast<float2 *>(&vg(xo, yo, z)) = c;  // v = 0 at the ring point x = 0
+                }
             }
         }
     }

@@ -406,9 +406,13 @@ dim3 green_ff_grid(const mg_ctx *c, int n) {
     const int zch = green_ff_zch(c, n);
     return dim3((n + GS_TX - 1) / GS_TX, (n + GS_TY - 1) / GS_TY, (n + zch - 1) / zch);
 }
-// the z-streaming green sweep pays GS_WARM steps per z range: used from 63^3 up
-// (measured faster than the 3D tile kernel there)
-bool green_ff_use(int n) { return n >= 63; }
+// vector access to u in k_green_ff_3d: one problem, u 16-byte aligned, even pitch
+bool green_ff_vu(const mg_ctx *c, const double *u) {
+    return c->nprob == 1 && ((uintptr_t)u % 16) == 0 && c->d.pitch % 2 == 0;
+}
+// the z-streaming green sweep pays GS_WARM steps per z range; measured faster
+// than the 3D tile kernel from 31^3 up
+bool green_ff_use(int n) { return n >= 31; }
 
 // prolongation v^(l) <- v^(l+1), r^(l); on level 0 with u != nullptr the
 // second half-sweep also applies u += v.  vctl: the red level of the fused
@@ -437,15 +441,14 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
             const dim3 g3 = green_ff_grid(c, n);
             const size_t sm = sizeof(GreenSSmem);
             const int zch = green_ff_zch(c, n);
-            if (u)
-                LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_ff_3d<UP_ADD>), g3, dim3(32, 8, 1), sm,
-                              red3v<const float>(b.v, b), a3<float>(a.r[0], a), (float *)nullptr, a3<float>(a.v[0], a),
-                              (float *)nullptr, u, c->d.pitch, n, (float)cc, 0.f, zch, (double *)nullptr,
-                              (Ctrl *)nullptr, done);
-            else
-                LAUNCH_SMEM_B(TAG_UP, (k_green_ff_3d<UP_STORE>), g3, dim3(32, 8, 1), sm, red3v<const float>(b.v, b),
-                              a3<float>(a.r[0], a), (float *)nullptr, a3<float>(a.v[0], a), (float *)nullptr, u,
-                              c->d.pitch, n, (float)cc, 0.f, zch, (double *)nullptr, (Ctrl *)nullptr, done);
+#define MG_GFF(TAG, MODE, VU)                                                                                     \
+    LAUNCH_SMEM_B(TAG, (k_green_ff_3d<MODE, VU>), g3, dim3(32, 8, 1), sm, red3v<const float>(b.v, b),               \
+                  a3<float>(a.r[0], a), (float *)nullptr, a3<float>(a.v[0], a), (float *)nullptr, u, c->d.pitch, n, \
+                  (float)cc, 0.f, zch, (double *)nullptr, (Ctrl *)nullptr, done)
+            if (u && green_ff_vu(c, u)) MG_GFF(TAG_FINEST_UP, UP_ADD, true);
+            else if (u) MG_GFF(TAG_FINEST_UP, UP_ADD, false);
+            else MG_GFF(TAG_UP, UP_STORE, false);
+#undef MG_GFF
         } else if (c->d.hierarchy == MG_DIAG && sizeof(T) == 4) {  // FP32: both half-sweeps in one tile kernel
             const dim3 g3((n + TX3 - 1) / TX3, (n + TY3 - 1) / TY3, (n + TZ3 - 1) / TZ3);
             const size_t sm = sizeof(Green3Smem<T>);
@@ -825,10 +828,14 @@ int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     const int n = c->d.n;
     const double h2 = c->h * c->h;
     const dim3 g3 = green_ff_grid(c, n);
-    LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_ff_3d<UP_RR>), g3, dim3(32, 8, 1), sizeof(GreenSSmem),
-                  red3v<const float>(b.v, b), a3<float>(a.r[0], a), (float *)c->r32b, a3<float>(a.v[0], a),
-                  (float *)c->rlo, u, c->d.pitch, n, (float)(c->d.omega[3] * h2), (float)(1.0 / h2),
-                  green_ff_zch(c, n), c->part, c->ctl, done);
+#define MG_GFF(VU)                                                                                                 \
+    LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_ff_3d<UP_RR, VU>), g3, dim3(32, 8, 1), sizeof(GreenSSmem),              \
+                  red3v<const float>(b.v, b), a3<float>(a.r[0], a), (float *)c->r32b, a3<float>(a.v[0], a),       \
+                  (float *)c->rlo, u, c->d.pitch, n, (float)(c->d.omega[3] * h2), (float)(1.0 / h2),             \
+                  green_ff_zch(c, n), c->part, c->ctl, done)
+    if (green_ff_vu(c, u)) MG_GFF(true);
+    else MG_GFF(false);
+#undef MG_GFF
     return (int)(g3.x * g3.y * g3.z);
 }
 
@@ -989,12 +996,17 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
             : cudaFuncSetAttribute(k_coarse_cta_3d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
         const int g64 = (int)sizeof(Green3Smem<double>), g32 = (int)sizeof(Green3Smem<float>);
         const int gs = (int)sizeof(GreenSSmem);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<UP_RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<UP_ADD>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<UP_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
+#define MG_GFF_ATTR(MODE, VU) \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_green_ff_3d<MODE, VU>, cudaFuncAttributeMaxDynamicSharedMemorySize, gs)
+        MG_GFF_ATTR(UP_RR, true);
+        MG_GFF_ATTR(UP_RR, false);
+        MG_GFF_ATTR(UP_ADD, true);
+        MG_GFF_ATTR(UP_ADD, false);
+        MG_GFF_ATTR(UP_STORE, false);
+#undef MG_GFF_ATTR
         if (e == cudaSuccess) {
             int per_sm = 0, sms = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_green_ff_3d<UP_RR>, 256, gs);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_green_ff_3d<UP_RR, true>, 256, gs);
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
             if (e == cudaSuccess) c->gs_resident = std::max(1, per_sm * sms);
         }
