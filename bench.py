@@ -62,8 +62,11 @@ PROBE3 = {
 # DRAM traffic of one launch on the 4095^2 workload from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the
 # kernel's source is the one that was captured.
-TRAFFIC = {"kernel": "k_up_ff_2d", "bytes": 333.859072e6 + 210.871040e6,
-           "source_sha1": "c9183447365e13de4d4699e376d4835b1a9fdb86"}
+TRAFFIC = {"kernel": "k_up_ff_2d", "file": "mg_fast2d.cuh", "bytes": 333.886464e6 + 211.283200e6,
+           "source_sha1": "ee5ec72a580d253e4dd5fb2c83ba8723587c6d07"}
+# the same for the dominant 3D kernel on the 255^3 workload
+TRAFFIC3 = {"kernel": "k_green_ff_3d", "file": "mg_fast3d.cuh", "bytes": 327.379712e6 + 209.555456e6,
+            "source_sha1": "176e781751a5ca126e64d3a200fcc2055267d8fe"}
 
 
 def read_peaks():
@@ -79,17 +82,23 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_PIPE_OPS_PEAK = 152 * 2 * 2.07e9  # FP64 pipe operations per second (an FMA counts once)
 
 
-def kernel_source_sha1(name: str) -> str | None:
-    """sha1 of a kernel's source text (from its template line to the next kernel)."""
+def kernel_source_sha1(name: str, file: str = "mg_fast2d.cuh") -> str | None:
+    """sha1 of a kernel's source text (from its template line to the end of its body)."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "paper_math_9907190_gb300", "csrc", "mg_fast2d.cuh")
+    path = os.path.join(ROOT, "paper_math_9907190_gb300", "csrc", file)
     try:
         text = open(path).read()
     except OSError:
         return None
     m = re.search(r"template <[^>]*>\s*__global__ void __launch_bounds__\([^)]*\) " + name + r"\(.*?\n}\n", text, re.S)
     return hashlib.sha1(m.group(0).encode()).hexdigest() if m else None
+
+
+def measured_traffic(t):
+    """ncu DRAM bytes of one launch, while the kernel's source is the one captured."""
+    sha = kernel_source_sha1(t["kernel"], t["file"])
+    return t["bytes"] if (t["bytes"] and sha == t["source_sha1"]) else None
 
 
 def cuda_timed(fn, reps, stream):
@@ -146,7 +155,8 @@ def extra_measurements(dev, stream):
                 peak = read_peaks().get("hbm_gbs", 6800.0)
                 out["cube255_roofline"] = {"kernel": PROBE3["name"], "bound": "hbm", "avg_launch_ms": avg,
                                            "launches_probed": k, "bytes_per_point": PROBE3["bytes_per_point"],
-                                           "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak}
+                                           "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                           "traffic": measured_traffic(TRAFFIC3)}
     del f3
     sides = I.batch_sides(512)
     fs = [torch.from_numpy(I.batch_f(n, b)).to(dev) for b, n in enumerate(sides)]
@@ -396,8 +406,7 @@ def main():
     bytes_ = PROBE["bytes_per_point"] * N
     achieved = bytes_ / (avg_ms * 1e-3) / 1e9
     pipe = PROBE["fp64_pipe_ops_per_point"] * N / (avg_ms * 1e-3)
-    sha = kernel_source_sha1(TRAFFIC["kernel"])
-    traffic = TRAFFIC["bytes"] if (TRAFFIC["bytes"] and sha == TRAFFIC["source_sha1"]) else None
+    traffic = measured_traffic(TRAFFIC)
     roofline = {"bound": "hbm", "kernel": PROBE["name"], "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic, "algorithmic_bytes": bytes_,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
