@@ -274,7 +274,26 @@ struct CoarsePlan2d {
     int og_r[CTA_MAX_PAIRS + 1], og_v[CTA_MAX_PAIRS + 1];  // smem offsets (elements), green r / v
     int oe_r[CTA_MAX_PAIRS], oo_r[CTA_MAX_PAIRS], oe_v[CTA_MAX_PAIRS], oo_v[CTA_MAX_PAIRS];
     int total;                        // smem elements
+    int gofs, ng;                     // byte offset and size (doubles) of the copy of the coarsest inverse
     double c2[CTA_MAX_PAIRS], c1[CTA_MAX_PAIRS];  // 2 p h_k^2 (red), p h_k^2 (green)
+};
+
+// The dense inverse G of the coarsest operator (at most CTA_G_MAX doubles) is
+// read into registers when a coarse block starts, stored to shared memory
+// beside the levels once they are loaded, and read from there by the coarse
+// solve (no global-memory latency on the block's critical path).
+constexpr int CTA_G_PER_THREAD = 3, CTA_G_MAX = CTA_G_PER_THREAD * 1024;
+template <int NT> struct GPrefetch {
+    double g[CTA_G_PER_THREAD];
+    __device__ __forceinline__ void load(const double *G, int ng, int tid) {
+#pragma unroll
+        for (int k = 0; k < CTA_G_PER_THREAD; k++) g[k] = tid + k * NT < ng ? G[tid + k * NT] : 0.0;
+    }
+    __device__ __forceinline__ void store(double *Gs, int ng, int tid) const {
+#pragma unroll
+        for (int k = 0; k < CTA_G_PER_THREAD; k++)
+            if (tid + k * NT < ng) Gs[tid + k * NT] = g[k];
+    }
 };
 
 template <typename T>
@@ -287,6 +306,9 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const
     rg_in = bt_at(rg_in, prob, B);
     vg_out = bt_at(vg_out, prob, B);
     const int tid = threadIdx.x, nt = blockDim.x;
+    GPrefetch<1024> gp;
+    gp.load(G, P.ng, tid);
+    double *Gs = reinterpret_cast<double *>(smraw + P.gofs);
     // 32 x 32 thread grid: loops over boxes step by 32, no index division
     const int tx = tid & 31, ty = tid >> 5;
 #define CTA_FOR2(i, j, lo_i, hi_i, lo_j, hi_j) \
@@ -299,6 +321,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const
         A2<T> g{sm + P.og_r[0], n + 2};
         CTA_FOR2(i, j, 1, n, 1, n) g(i, j) = rg_in(i, j);
     }
+    gp.store(Gs, P.ng, tid);
     __syncthreads();
     for (int p = 0; p < npair; p++) {
         const int n = P.nk[p], nb = (n - 1) / 2;
@@ -321,9 +344,12 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const
     {   // exact solve on the coarsest grid
         const int s = P.nk[npair], nn = s * s;
         A2<T> r{sm + P.og_r[npair], s + 2}, v{sm + P.og_v[npair], s + 2};
+        double *rv = Gs + P.ng;  // the right-hand side, dense
+        for (int q = tid; q < nn; q += nt) rv[q] = (double)r(q % s + 1, q / s + 1);
+        __syncthreads();
         for (int q = tid; q < nn; q += nt) {
             double acc = 0.0;
-            for (int t = 0; t < nn; t++) acc += G[(size_t)q * nn + t] * (double)r(t % s + 1, t / s + 1);
+            for (int t = 0; t < nn; t++) acc += Gs[q * nn + t] * rv[t];
             v(q % s + 1, q / s + 1) = (T)acc;
         }
     }
@@ -465,6 +491,7 @@ struct CoarsePlan3d {
     int orr[CTA3_MAX][4], orv[CTA3_MAX][4];              // red cosets EEE, OOE, OEO, EOO ((nb+2)^3)
     int omr[CTA3_MAX][2], omv[CTA3_MAX][2];              // magenta cosets EEE, OOO
     int total;
+    int gofs, ng;  // byte offset and size (doubles) of the copy of the coarsest inverse
     double cm[CTA3_MAX], cr1[CTA3_MAX], cr2[CTA3_MAX], cg[CTA3_MAX];  // 4p_m h^2, 2p_r1 h^2, 4p_r2 h^2, p_g h^2
 };
 
@@ -478,6 +505,9 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
     rg_in = bt_at(rg_in, prob, B);
     vg_out = bt_at(vg_out, prob, B);
     const int tid = threadIdx.x, nt = blockDim.x;
+    GPrefetch<1024> gp;
+    gp.load(G, P.ng, tid);
+    double *Gs = reinterpret_cast<double *>(smraw + P.gofs);
     // 16 x 8 x 8 thread grid: loops over boxes without index division
     const int tx = tid & 15, ty = (tid >> 4) & 7, tz = tid >> 7;
 #define CTA_FOR3(i, j, k, lo, hi)                                        \
@@ -494,6 +524,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
         A3<T> g = G3(P.og_r[0], n);
         CTA_FOR3(i, j, k, 1, n) g(i, j, k) = rg_in(i, j, k);
     }
+    gp.store(Gs, P.ng, tid);
     __syncthreads();
     for (int t = 0; t < ntri; t++) {
         const int n = P.nk[t], nb = (n - 1) / 2, nc = nb + 1;
@@ -529,9 +560,12 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
     {   // exact solve on the coarsest grid
         const int s = P.nk[ntri], nn = s * s * s;
         A3<T> r = G3(P.og_r[ntri], s), v = G3(P.og_v[ntri], s);
+        double *rv = Gs + P.ng;  // the right-hand side, dense
+        for (int q = tid; q < nn; q += nt) rv[q] = (double)r(q % s + 1, (q / s) % s + 1, q / (s * s) + 1);
+        __syncthreads();
         for (int q = tid; q < nn; q += nt) {
             double acc = 0.0;
-            for (int t = 0; t < nn; t++) acc += G[(size_t)q * nn + t] * (double)r(t % s + 1, (t / s) % s + 1, t / (s * s) + 1);
+            for (int t = 0; t < nn; t++) acc += Gs[q * nn + t] * rv[t];
             v(q % s + 1, (q / s) % s + 1, q / (s * s) + 1) = (T)acc;
         }
     }

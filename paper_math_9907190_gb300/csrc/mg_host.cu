@@ -505,6 +505,17 @@ template <typename T> void launch_coarse(mg_ctx *c, const int *done, cudaStream_
 
 // ---- fused 2D diagonal path ------------------------------------------------
 
+// shared memory of a coarse block: `elems` level elements, then (16-byte
+// aligned) the copy of the coarsest inverse, nn x nn doubles, and the
+// coarsest right-hand side as a dense vector of nn doubles
+static_assert(49 * 49 <= CTA_G_MAX, "coarsest inverse of a 7 x 7 grid");
+void coarse_g_slot(mg_ctx *c, int nn, int elems, int &gofs, int &ng) {
+    const size_t base = ((size_t)elems * c->esz + 15) / 16 * 16;
+    ng = nn * nn;  // the coarsest grid has side <= 7 (2D) / 3 (3D) (valid_desc)
+    gofs = (int)base;
+    c->plan_bytes = base + (size_t)(ng + nn) * sizeof(double);
+}
+
 void plan_fast2d(mg_ctx *c) {
     c->fast2d = c->d.dim == 2 && c->d.hierarchy == MG_DIAG;
     if (!c->fast2d) return;
@@ -534,7 +545,7 @@ void plan_fast2d(mg_ctx *c) {
         }
     }
     P.total = off;
-    c->plan_bytes = (size_t)off * c->esz;
+    coarse_g_slot(c, P.nk[npair] * P.nk[npair], off, P.gofs, P.ng);
 }
 
 // finest residual for every configuration: column (2D) / plane (3D) marching,
@@ -570,7 +581,7 @@ void plan_fast3d(mg_ctx *c) {
         }
     }
     P.total = off;
-    c->plan_bytes = (size_t)off * c->esz;
+    coarse_g_slot(c, P.nk[ntri] * P.nk[ntri] * P.nk[ntri], off, P.gofs, P.ng);
 }
 
 template <typename T> int launch_res_fast(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s) {
