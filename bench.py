@@ -135,8 +135,31 @@ def extra_measurements(dev, stream):
             out[f"square4095_usual_{prec}"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc,
                                                "relres": rel, "workload": "same problem, conventional V-cycle "
                                                "(full weighting, bilinear + red-black Jacobi, p = 1.121)"}
+    # fourth-order residual (2D Mehrstellen, p = 1.2), and the two-stage solve:
+    # second-order cycles to 1e-4, then fourth-order cycles to 1e-10
+    for prec in ("mixed", "fp64"):
+        with Context(2, N_SIDE, order=4, precision=prec) as c:
+            u = c.new_grid()
+            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u.zero_(), rtol=RTOL, max_cycles=80, raise_on_fail=False), 3, stream)
+            out[f"square4095_order4_{prec}"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc,
+                                                "relres": rel, "workload": "same f, fourth-order residual "
+                                                "(Mehrstellen right-hand side), diagonal V-cycle p = 1.2"}
+            if prec == "mixed":
+                ms, (_, c2, c4, rel) = cuda_timed(lambda: c.solve_two_stage(f, u.zero_(), rtol=RTOL, max_cycles=80, raise_on_fail=False),
+                                                  3, stream)
+                out["square4095_two_stage_mixed"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms,
+                                                     "cycles_order2": c2, "cycles_order4": c4, "relres": rel,
+                                                     "workload": "same f, second-order cycles (p = 1.052) to "
+                                                     "1e-4, then fourth-order cycles to 1e-10"}
     del f
     f3 = torch.from_numpy(I.cube(255)).to(dev)
+    for prec in ("mixed", "fp64"):  # fourth-order residual in 3D (19-point, Eq. Efos4)
+        with Context(3, 255, order=4, precision=prec) as c:
+            u = c.new_grid()
+            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f3, u.zero_(), rtol=RTOL, max_cycles=80, raise_on_fail=False), 3, stream)
+            out[f"cube255_order4_{prec}"] = {"unknowns_per_s": 255**3 / (ms * 1e-3), "ms": ms, "cycles": cyc,
+                                             "relres": rel, "workload": "3D unit cube 255^3, same f, 19-point "
+                                             "fourth-order residual, diagonal V-cycle (0.91, 0.80, 0.70, 1.77)"}
     for prec in ("mixed", "fp64"):
         with Context(3, 255, precision=prec) as c:
             u = c.new_grid()

@@ -315,16 +315,38 @@ __global__ void __launch_bounds__(256) k_g2r_zm_3d(A3<const T> g, Red3<T> red, i
     if (!zm_cell(z, 0, nb, zm, P, Q, B)) return;
     const int gp = g.pitch;
     const size_t gq = (size_t)gp * g.rows;
-    auto avg = [&](const T *c) {
-        return (T(6) * c[0] + (c[1] + c[-1]) + (c[gp] + c[-gp]) + (c[gq] + c[-(long)gq])) * T(1.0 / 12.0);
+    // the 20 distinct green values of a cell (X, Y, Z) = (2a, 2b, 2c) are
+    // loaded once, before any store; the 4 of planes Z+1 and Z+2 that the
+    // next cell up reads again are carried over in registers
+    auto avg = [](T c, T x0, T x1, T y0, T y1, T z0, T z1) {
+        return (T(6) * c + (x1 + x0) + (y1 + y0) + (z1 + z0)) * T(1.0 / 12.0);
     };
+    const T *ge = g.p + ((size_t)(2 * z.c0) * g.rows + 2 * z.b) * gp + 2 * z.a;  // green (2a, 2b, 2c0)
+    // carried: (X, Y, Z-1), (X+1, Y+1, Z-1), (X+1, Y, Z), (X, Y+1, Z).  Values
+    // at index -1 (read only by ring points: a, b or c = 0) are not loaded.
+    const bool ax = z.a >= 1, by = z.b >= 1;
+    T czm = T(0), czm11 = T(0), cz10 = ge[1], cz01 = ge[gp];
+    if (z.c0 >= 1) { czm = ge[-(long)gq]; czm11 = ge[1 + gp - (long)gq]; }
     size_t i = z.i;
-    for (int c = z.c0; c < z.c1; c++, i += Q) {
-        const T *ge = g.p + ((size_t)(2 * c) * g.rows + 2 * z.b) * gp + 2 * z.a;  // green (2a, 2b, 2c)
-        if (z.a >= 1 && z.b >= 1 && c >= 1) red.eee.p[i] = avg(ge);
-        if (c >= 1) red.ooe.p[i] = avg(ge + gp + 1);
-        if (z.b >= 1) red.oeo.p[i] = avg(ge + gq + 1);
-        if (z.a >= 1) red.eoo.p[i] = avg(ge + gq + gp);
+    for (int c = z.c0; c < z.c1; c++, i += Q, ge += 2 * gq) {
+        const T *g1 = ge + gq, *g2 = ge + 2 * gq;
+        // plane Z
+        const T e = ge[0], exm = ax ? ge[-1] : T(0), eym = by ? ge[-gp] : T(0), e11 = ge[1 + gp], e21 = ge[2 + gp],
+                e12 = ge[1 + 2 * gp];
+        // plane Z+1
+        const T u00 = g1[0], u11 = g1[1 + gp], u10 = g1[1], u20 = g1[2], u1m = by ? g1[1 - gp] : T(0), u01 = g1[gp],
+                um1 = ax ? g1[-1 + gp] : T(0), u02 = g1[2 * gp];
+        // plane Z+2
+        const T w10 = g2[1], w01 = g2[gp];
+        const T veee = avg(e, exm, cz10, eym, cz01, czm, u00);
+        const T vooe = avg(e11, cz01, e21, cz10, e12, czm11, u11);
+        const T voeo = avg(u10, u00, u20, u1m, u11, cz10, w10);
+        const T veoo = avg(u01, um1, u11, u00, u02, cz01, w01);
+        if (z.a >= 1 && z.b >= 1 && c >= 1) red.eee.p[i] = veee;
+        if (c >= 1) red.ooe.p[i] = vooe;
+        if (z.b >= 1) red.oeo.p[i] = voeo;
+        if (z.a >= 1) red.eoo.p[i] = veoo;
+        czm = u00; czm11 = u11; cz10 = w10; cz01 = w01;
     }
 }
 
