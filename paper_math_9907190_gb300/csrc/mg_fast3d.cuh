@@ -362,15 +362,29 @@ __global__ void __launch_bounds__(256) k_r2m_zm_3d(Red3<const T> red, Mag3<T> ma
     ZmIdx z;
     if (!zm_cell(z, 0, nb, zm, P, Q, B)) return;
     const T *eee = red.eee.p, *ooe = red.ooe.p, *oeo = red.oeo.p, *eoo = red.eoo.p;
+    // values of plane c-1 that plane c reads again are carried in registers:
+    // oeo(a-1,b,c-1), oeo(a,b,c-1), eoo(a,b-1,c-1), eoo(a,b,c-1) and ooe(a,b,c);
+    // index -1 values (read only for a, b or c = 0) are not loaded
+    const bool ab = z.a >= 1 && z.b >= 1;
     size_t i = z.i;
+    T pm1 = T(0), p0 = T(0), qm1 = T(0), q0 = T(0);
+    if (ab && z.c0 >= 1) { pm1 = oeo[i - Q - 1]; p0 = oeo[i - Q]; qm1 = eoo[i - Q - P]; q0 = eoo[i - Q]; }
+    T oc = ooe[i];
     for (int c = z.c0; c < z.c1; c++, i += Q) {
-        if (z.a >= 1 && z.b >= 1 && c >= 1) {
-            const T s1 = (ooe[i - P - 1] + ooe[i - P]) + (ooe[i - 1] + ooe[i]);
-            const T s2 = (oeo[i - Q - 1] + oeo[i - Q]) + (oeo[i - 1] + oeo[i]);
-            const T s3 = (eoo[i - Q - P] + eoo[i - Q]) + (eoo[i - P] + eoo[i]);
-            mag.eee.p[i] = (T(12) * eee[i] + (s1 + s2 + s3)) * T(1.0 / 24.0);
+        const T ou = ooe[i + Q], oeo0 = oeo[i], oeoy = oeo[i + P], eoo0 = eoo[i], eoox = eoo[i + 1];
+        T oeom = T(0), eoom = T(0);
+        if (ab) {
+            oeom = oeo[i - 1];
+            eoom = eoo[i - P];
+            if (c >= 1) {
+                const T s1 = (ooe[i - P - 1] + ooe[i - P]) + (ooe[i - 1] + oc);
+                const T s2 = (pm1 + p0) + (oeom + oeo0);
+                const T s3 = (qm1 + q0) + (eoom + eoo0);
+                mag.eee.p[i] = (T(12) * eee[i] + (s1 + s2 + s3)) * T(1.0 / 24.0);
+            }
         }
-        mag.ooo.p[i] = ((eoo[i] + eoo[i + 1]) + (oeo[i] + oeo[i + P]) + (ooe[i] + ooe[i + Q])) * T(1.0 / 6.0);
+        mag.ooo.p[i] = ((eoo0 + eoox) + (oeo0 + oeoy) + (oc + ou)) * T(1.0 / 6.0);
+        pm1 = oeom; p0 = oeo0; qm1 = eoom; q0 = eoo0; oc = ou;
     }
 }
 
@@ -387,11 +401,13 @@ __global__ void __launch_bounds__(256) k_m2b_zm_3d(Mag3<const T> mag, A3<T> blue
     if (!zm_cell(z, 1, nb, zm, P, Q, B)) return;
     const T *ooo = mag.ooo.p;
     size_t i = z.i;
+    // the four centres of plane c-1 (a sum carried from the previous plane)
+    auto quad = [&](size_t k) { return (ooo[k - P - 1] + ooo[k - P]) + (ooo[k - 1] + ooo[k]); };
+    T lower = quad(i - Q);
     for (int c = z.c0; c < z.c1; c++, i += Q) {
-        const size_t m = i - Q;
-        const T ctr = ((ooo[m - P - 1] + ooo[m - P]) + (ooo[m - 1] + ooo[m])) +
-                      ((ooo[i - P - 1] + ooo[i - P]) + (ooo[i - 1] + ooo[i]));
-        blue.p[i] = (T(8) * mag.eee.p[i] + ctr) * T(0.0625);
+        const T upper = quad(i);
+        blue.p[i] = (T(8) * mag.eee.p[i] + (lower + upper)) * T(0.0625);
+        lower = upper;
     }
 }
 
@@ -408,11 +424,13 @@ __global__ void __launch_bounds__(256) k_b2m_ooo_zm_3d(A3<const T> blue, A3<cons
     if (!zm_cell(z, 0, nb, zm, P, Q, B)) return;
     const T *bl = blue.p;
     size_t i = z.i;
+    // the four corners of plane c+1 become those of plane c at the next step
+    auto quad = [&](size_t k) { return (bl[k] + bl[k + 1]) + (bl[k + P] + bl[k + P + 1]); };
+    T lower = quad(i);
     for (int c = z.c0; c < z.c1; c++, i += Q) {
-        const size_t u = i + Q;
-        const T s = ((bl[i] + bl[i + 1]) + (bl[i + P] + bl[i + P + 1])) +
-                    ((bl[u] + bl[u + 1]) + (bl[u + P] + bl[u + P + 1]));
-        vooo.p[i] = (s - cc * rooo.p[i]) * T(0.125);
+        const T upper = quad(i + Q);
+        vooo.p[i] = ((lower + upper) - cc * rooo.p[i]) * T(0.125);
+        lower = upper;
     }
 }
 
@@ -429,10 +447,12 @@ __global__ void __launch_bounds__(256) k_b2m_eee_zm_3d(A3<const T> vooo, A3<cons
     if (!zm_cell(z, 1, nb, zm, P, Q, B)) return;
     const T *o = vooo.p;
     size_t i = z.i;
+    auto quad = [&](size_t k) { return (o[k - P - 1] + o[k - P]) + (o[k - 1] + o[k]); };
+    T lower = quad(i - Q);  // carried from plane to plane
     for (int c = z.c0; c < z.c1; c++, i += Q) {
-        const size_t m = i - Q;
-        const T ctr = ((o[m - P - 1] + o[m - P]) + (o[m - 1] + o[m])) + ((o[i - P - 1] + o[i - P]) + (o[i - 1] + o[i]));
-        veee.p[i] = (ctr - cc * reee.p[i]) * T(0.125);
+        const T upper = quad(i);
+        veee.p[i] = ((lower + upper) - cc * reee.p[i]) * T(0.125);
+        lower = upper;
     }
 }
 
@@ -449,22 +469,20 @@ __global__ void __launch_bounds__(256) k_m2r_faces_zm_3d(Mag3<const T> vm, Red3<
     if (!zm_cell(z, 0, nb, zm, P, Q, B)) return;
     const T *o = vm.ooo.p, *e = vm.eee.p;
     size_t i = z.i;
+    // carried from plane c-1: centre (a,b,c-1) and corners (a,b,c), (a+1,b,c),
+    // (a,b+1,c); index -1 values (read only for a, b or c = 0) are not loaded
+    const bool ax = z.a >= 1, by = z.b >= 1;
+    T om = z.c0 >= 1 ? o[i - Q] : T(0), e00 = e[i], e10 = e[i + 1], e01 = e[i + P];
     for (int c = z.c0; c < z.c1; c++, i += Q) {
-        if (c >= 1) {  // (2a+1, 2b+1, 2c): normal z
-            const T ctr = o[i - Q] + o[i];
-            const T cor = (e[i] + e[i + 1]) + (e[i + P] + e[i + P + 1]);
-            vr.ooe.p[i] = (T(2) * ctr + cor - c1 * rr.ooe.p[i]) * T(0.125);
-        }
-        if (z.b >= 1) {  // (2a+1, 2b, 2c+1): normal y
-            const T ctr = o[i - P] + o[i];
-            const T cor = (e[i] + e[i + 1]) + (e[i + Q] + e[i + Q + 1]);
-            vr.oeo.p[i] = (T(2) * ctr + cor - c1 * rr.oeo.p[i]) * T(0.125);
-        }
-        if (z.a >= 1) {  // (2a, 2b+1, 2c+1): normal x
-            const T ctr = o[i - 1] + o[i];
-            const T cor = (e[i] + e[i + P]) + (e[i + Q] + e[i + Q + P]);
-            vr.eoo.p[i] = (T(2) * ctr + cor - c1 * rr.eoo.p[i]) * T(0.125);
-        }
+        const T oc = o[i], e11 = e[i + P + 1], u00 = e[i + Q], u10 = e[i + Q + 1], u01 = e[i + Q + P];
+        const T oy = by ? o[i - P] : T(0), ox = ax ? o[i - 1] : T(0);
+        if (c >= 1)  // (2a+1, 2b+1, 2c): normal z
+            vr.ooe.p[i] = (T(2) * (om + oc) + ((e00 + e10) + (e01 + e11)) - c1 * rr.ooe.p[i]) * T(0.125);
+        if (by)      // (2a+1, 2b, 2c+1): normal y
+            vr.oeo.p[i] = (T(2) * (oy + oc) + ((e00 + e10) + (u00 + u10)) - c1 * rr.oeo.p[i]) * T(0.125);
+        if (ax)      // (2a, 2b+1, 2c+1): normal x
+            vr.eoo.p[i] = (T(2) * (ox + oc) + ((e00 + e01) + (u00 + u01)) - c1 * rr.eoo.p[i]) * T(0.125);
+        om = oc; e00 = u00; e10 = u10; e01 = u01;
     }
 }
 
@@ -486,9 +504,12 @@ __global__ void __launch_bounds__(256) k_m2r_corners_zm_3d(Red3<const T> vf, A3<
     if (zm_cell(z, 1, nb, zm, P, Q, B)) {
         const T *ooe = vf.ooe.p, *oeo = vf.oeo.p, *eoo = vf.eoo.p;
         size_t i = z.i;
+        // the four plane c-1 values of oeo / eoo are carried from the previous plane
+        T pm1 = oeo[i - Q - 1], p0 = oeo[i - Q], qm1 = eoo[i - Q - P], q0 = eoo[i - Q];
         for (int c = z.c0; c < z.c1; c++, i += Q) {
-            const T q[12] = {ooe[i - P - 1], ooe[i - P], ooe[i - 1], ooe[i], oeo[i - Q - 1], oeo[i - Q],
-                             oeo[i - 1],     oeo[i],     eoo[i - Q - P], eoo[i - Q], eoo[i - P], eoo[i]};
+            const T q[12] = {ooe[i - P - 1], ooe[i - P], ooe[i - 1], ooe[i], pm1, p0,
+                             oeo[i - 1],     oeo[i],     qm1, q0, eoo[i - P], eoo[i]};
+            pm1 = q[6]; p0 = q[7]; qm1 = q[10]; q0 = q[11];
             const T s1 = (q[0] + q[1]) + (q[2] + q[3]);
             const T s2 = (q[4] + q[5]) + (q[6] + q[7]);
             const T s3 = (q[8] + q[9]) + (q[10] + q[11]);
