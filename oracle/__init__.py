@@ -81,6 +81,10 @@ def _load():
                 "orc_prolong_usual": (None, [i, i, d, d, dp, dp, dp]),
                 "orc_coarse_solve": (i, [i, i, d, dp, dp]),
                 "orc_vcycle": (i, [i, i, i, i, i, dp, dp, dp]),
+                "orc_vcycle_sweeps": (i, [i, i, i, i, i, dp, i, dp, dp]),
+                "orc_sweep2d_red": (None, [i, d, d, dp, dp]),
+                "orc_sweep2d_green": (None, [i, d, d, dp, dp]),
+                "orc_solve_sweeps": (i, [i, i, i, i, i, dp, i, dp, dp, d, i, dp, dp]),
                 "orc_norm2_interior": (d, [i, i, dp]),
                 "orc_solve": (i, [i, i, i, i, i, dp, dp, dp, d, i, dp, dp]),
             }
@@ -215,17 +219,18 @@ def _omega(omega, dim, hier):
     return om
 
 
-def vcycle(f, u, *, hier=DIAG, order=2, coarsest=3, omega=None):
-    """One V-cycle in place on u (a full-grid float64 array); returns u."""
+def vcycle(f, u, *, hier=DIAG, order=2, coarsest=3, omega=None, extra=0):
+    """One V-cycle in place on u (a full-grid float64 array); returns u.
+    extra: extra Jacobi sweeps per level (2D diagonal hierarchy)."""
     dim, n = f.ndim, f.shape[0] - 2
     om = _omega(omega, dim, hier)
-    rc = _load().orc_vcycle(dim, n, hier, order, coarsest, _p(om), _p(f), _p(u))
+    rc = _load().orc_vcycle_sweeps(dim, n, hier, order, coarsest, _p(om), extra, _p(f), _p(u))
     if rc != 0:
         raise ValueError(f"orc_vcycle rejected dim={dim} n={n} coarsest={coarsest} order={order}")
     return u
 
 
-def solve(f, u=None, *, hier=DIAG, order=2, coarsest=3, omega=None, rtol=1e-10, max_cycles=100):
+def solve(f, u=None, *, hier=DIAG, order=2, coarsest=3, omega=None, rtol=1e-10, max_cycles=100, extra=0):
     """V-cycles from u (default 0) until the relative residual <= rtol.
 
     Returns (u, cycles, relres, history)."""
@@ -234,11 +239,29 @@ def solve(f, u=None, *, hier=DIAG, order=2, coarsest=3, omega=None, rtol=1e-10, 
     om = _omega(omega, dim, hier)
     hist = np.zeros(max(max_cycles, 1), dtype=np.float64)
     rel = ctypes.c_double(0.0)
-    it = _load().orc_solve(dim, n, hier, order, coarsest, _p(om), _p(f), _p(u), rtol, max_cycles,
-                           _p(hist), ctypes.byref(rel))
+    it = _load().orc_solve_sweeps(dim, n, hier, order, coarsest, _p(om), extra, _p(f), _p(u), rtol, max_cycles,
+                                  _p(hist), ctypes.byref(rel))
     if it < 0:
         raise ValueError("orc_solve rejected its arguments")
     return u, it, rel.value, hist[:it].copy()
+
+
+def sweep2d_red(rr, vr, p=1.0, h=None):
+    """One extra Jacobi sweep in place on a red (diagonal) level stored on its
+    pair's green grid: i,j odd points, then i,j even points."""
+    n = vr.shape[0] - 2
+    h = 1.0 / (n + 1) if h is None else h
+    _load().orc_sweep2d_red(n, h, p, _p(rr), _p(vr))
+    return vr
+
+
+def sweep2d_green(rg, vg, p=1.0, h=None):
+    """One extra Jacobi sweep in place on a green (axis) level: i+j odd points,
+    then i+j even points."""
+    n = vg.shape[0] - 2
+    h = 1.0 / (n + 1) if h is None else h
+    _load().orc_sweep2d_green(n, h, p, _p(rg), _p(vg))
+    return vg
 
 
 def norm2_interior(x):

@@ -191,6 +191,36 @@ void orc_prolong2d_r2g(int n, double h, double p, const double *vr, const double
         }
 }
 
+/* Extra Jacobi sweeps at each level of the 2D diagonal hierarchy, the
+ * extension Section 5 leaves open.  One extra sweep repeats the level's two
+ * half-sweeps with the level's own current values in place of the coarse
+ * ones: on a red level the points that are not blue (i,j odd) from their four
+ * diagonal neighbours, then the blue points (i,j even) from theirs, both with
+ * 2 p h^2; on a green level the green-only points (i+j odd) from their four
+ * axis neighbours, then the red points (i+j even), both with p h^2. */
+void orc_sweep2d_red(int n, double h, double p, const double *rr, double *vr)
+{
+    for (int par = 1; par >= 0; par--)
+        for (int j = 2 - par; j <= n; j += 2)
+            for (int i = 2 - par; i <= n; i += 2) {
+                double s = vr[IDX2(n, i - 1, j - 1)] + vr[IDX2(n, i + 1, j - 1)] +
+                           vr[IDX2(n, i + 1, j + 1)] + vr[IDX2(n, i - 1, j + 1)];
+                vr[IDX2(n, i, j)] = (-2.0 * p * h * h * rr[IDX2(n, i, j)] + s) / 4.0;
+            }
+}
+
+void orc_sweep2d_green(int n, double h, double p, const double *rg, double *vg)
+{
+    for (int par = 1; par >= 0; par--)
+        for (int j = 1; j <= n; j++)
+            for (int i = 1; i <= n; i++) {
+                if ((i + j) % 2 != par) continue;
+                double s = vg[IDX2(n, i - 1, j)] + vg[IDX2(n, i + 1, j)] + vg[IDX2(n, i, j - 1)] +
+                           vg[IDX2(n, i, j + 1)];
+                vg[IDX2(n, i, j)] = (-p * h * h * rg[IDX2(n, i, j)] + s) / 4.0;
+            }
+}
+
 /* ------------------------------------------------------------------------ */
 /* 3D diagonal hierarchy (Section 3): green (cubic) -> red (i+j+k even) ->   */
 /* magenta (corners (e,e,e) and centres (o,o,o)) -> blue (e,e,e)             */
@@ -503,13 +533,15 @@ int orc_coarse_solve(int dim, int n, double H, const double *r, double *v)
 
 /* omega: 2D diag {p}; 3D diag {p_m, p_r1, p_r2, p_g}; usual {p} (p_g in 3D).
  * coarsest: interior side of the coarsest axis grid (2^c - 1, <= n).
+ * extra: extra Jacobi sweeps after each level's prolongation (2D diagonal
+ * hierarchy only; 0 is the paper's cycle).
  * Returns 0, or -1 on invalid arguments / allocation failure. */
-int orc_vcycle(int dim, int n, int hier, int order, int coarsest, const double *omega, const double *f,
-               double *u)
+int orc_vcycle_sweeps(int dim, int n, int hier, int order, int coarsest, const double *omega, int extra,
+                      const double *f, double *u)
 {
     int m = log2_side(n), c = log2_side(coarsest);
     if ((dim != 2 && dim != 3) || m < 1 || c < 1 || c > m || (order != 2 && order != 4) ||
-        (hier != ORC_DIAG && hier != ORC_USUAL))
+        (hier != ORC_DIAG && hier != ORC_USUAL) || extra < 0 || (extra > 0 && (dim != 2 || hier != ORC_DIAG)))
         return -1;
     int K = m - c; /* number of pairs (2D diag), triples (3D diag) or coarsenings (usual) */
     double h = 1.0 / (n + 1);
@@ -551,7 +583,9 @@ int orc_vcycle(int dim, int n, int hier, int order, int coarsest, const double *
         if (hier == ORC_USUAL) orc_prolong_usual(dim, nk[k], hk, omega[0], vg[k + 1], rg[k], vg[k]);
         else if (dim == 2) {
             orc_prolong2d_b2r(nk[k], hk, omega[0], vg[k + 1], rr[k], vr[k]);
+            for (int e = 0; e < extra; e++) orc_sweep2d_red(nk[k], hk, omega[0], rr[k], vr[k]);
             orc_prolong2d_r2g(nk[k], hk, omega[0], vr[k], rg[k], vg[k]);
+            for (int e = 0; e < extra; e++) orc_sweep2d_green(nk[k], hk, omega[0], rg[k], vg[k]);
         } else {
             orc_prolong3d_b2m(nk[k], hk, omega[0], vg[k + 1], rm[k], vm[k]);
             orc_prolong3d_m2r(nk[k], hk, omega[1], omega[2], vm[k], rr[k], vr[k]);
@@ -574,6 +608,12 @@ int orc_vcycle(int dim, int n, int hier, int order, int coarsest, const double *
     return rc;
 }
 
+int orc_vcycle(int dim, int n, int hier, int order, int coarsest, const double *omega, const double *f,
+               double *u)
+{
+    return orc_vcycle_sweeps(dim, n, hier, order, coarsest, omega, 0, f, u);
+}
+
 /* sum of squares of the interior points of a full grid */
 double orc_norm2_interior(int dim, int n, const double *x)
 {
@@ -594,8 +634,8 @@ double orc_norm2_interior(int dim, int n, const double *x)
  * side for order 4) or max_cycles cycles.  history (nullable) receives the
  * relative residual after each cycle.  Returns the number of cycles done, or
  * -1 on invalid arguments. */
-int orc_solve(int dim, int n, int hier, int order, int coarsest, const double *omega, const double *f,
-              double *u, double rtol, int max_cycles, double *history, double *relres_out)
+int orc_solve_sweeps(int dim, int n, int hier, int order, int coarsest, const double *omega, int extra,
+                     const double *f, double *u, double rtol, int max_cycles, double *history, double *relres_out)
 {
     size_t len = grid_len(dim, n);
     double h = 1.0 / (n + 1);
@@ -608,7 +648,7 @@ int orc_solve(int dim, int n, int hier, int order, int coarsest, const double *o
     double rel = fnorm > 0.0 ? sqrt(orc_norm2_interior(dim, n, r)) / fnorm : 0.0;
     int it = 0;
     while (rel > rtol && it < max_cycles) {
-        if (orc_vcycle(dim, n, hier, order, coarsest, omega, f, u) != 0) { it = -1; break; }
+        if (orc_vcycle_sweeps(dim, n, hier, order, coarsest, omega, extra, f, u) != 0) { it = -1; break; }
         orc_residual(dim, n, h, order, f, u, r);
         rel = fnorm > 0.0 ? sqrt(orc_norm2_interior(dim, n, r)) / fnorm : 0.0;
         if (history) history[it] = rel;
@@ -618,4 +658,11 @@ int orc_solve(int dim, int n, int hier, int order, int coarsest, const double *o
     free(r);
     free(zero);
     return it;
+}
+
+int orc_solve(int dim, int n, int hier, int order, int coarsest, const double *omega, const double *f,
+              double *u, double rtol, int max_cycles, double *history, double *relres_out)
+{
+    return orc_solve_sweeps(dim, n, hier, order, coarsest, omega, 0, f, u, rtol, max_cycles, history,
+                            relres_out);
 }

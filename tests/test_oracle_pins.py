@@ -455,3 +455,78 @@ def test_simultaneous_jacobi_reading_is_rejected():
     r_diag = spectral_radius(2, 31, O.DIAG, 2, [1.0])
     r_usual = spectral_radius(2, 31, O.USUAL, 2, [1.0])
     assert r_diag < 0.12 and 0.28 < r_usual < 0.4
+
+
+# --------------------------------------------------------------------------
+# extra Jacobi sweeps per level: the extension Section 5 leaves open
+# --------------------------------------------------------------------------
+
+def test_green_sweeps_converge_to_the_level_solution():
+    """p = 1: repeated green sweeps are red-black relaxation of the 5-point
+    equation L_h v = r, so from any start they converge to its solution (a
+    direct solve of the independently assembled operator)."""
+    n = 7
+    r, v = rng_grid(2, n, 12), rng_grid(2, n, 13)
+    for _ in range(600):
+        O.sweep2d_green(r, v, p=1.0)
+    L, _ = operators(2, n, 2)
+    A = L @ _kron(_s1(n), _s1(n)).T
+    want = np.linalg.solve(A, interior(r).ravel())
+    np.testing.assert_allclose(interior(v).ravel(), want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def test_red_sweeps_converge_to_the_rotated_level_solution():
+    """p = 1: repeated red sweeps converge to the solution of the 5-point
+    equation of the 45-degree rotated red lattice (spacing sqrt(2) h):
+    (sum of the four diagonal neighbours - 4 v) / (2 h^2) = r at i + j even,
+    neighbours outside the interior being zero."""
+    n = 7
+    h = 1.0 / (n + 1)
+    r, v = rng_grid(2, n, 14), rng_grid(2, n, 15)
+    for _ in range(600):
+        O.sweep2d_red(r, v, p=1.0)
+    pts = [(i, j) for j in range(1, n + 1) for i in range(1, n + 1) if (i + j) % 2 == 0]
+    idx = {q: k for k, q in enumerate(pts)}
+    A = np.zeros((len(pts), len(pts)))
+    for k, (i, j) in enumerate(pts):
+        A[k, k] = -4.0 / (2 * h * h)
+        for di, dj in ((1, 1), (1, -1), (-1, 1), (-1, -1)):
+            q = (i + di, j + dj)
+            if q in idx:
+                A[k, idx[q]] += 1.0 / (2 * h * h)
+    want = np.linalg.solve(A, np.array([r[j, i] for i, j in pts]))
+    got = np.array([v[j, i] for i, j in pts])
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def test_extra_sweeps_make_the_finest_level_exact():
+    """p = 1 on a single pair (n = 7 above the 3 x 3 coarsest grid): with many
+    extra sweeps the finest green level of one V-cycle from u = 0 converges to
+    L_h v = f, so that cycle returns the discrete solution."""
+    n = 7
+    f = rng_grid(2, n, 16)
+    u = O.vcycle(f, O.grid(2, n), omega=[1.0], extra=600)
+    L, _ = operators(2, n, 2)
+    A = L @ _kron(_s1(n), _s1(n)).T
+    want = np.linalg.solve(A, interior(f).ravel())
+    np.testing.assert_allclose(interior(u).ravel(), want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("extra", [1, 2])
+def test_extra_sweeps_keep_the_fixed_point(extra):
+    """Extra sweeps change the cycle, not the discrete solution it converges to."""
+    n = 31
+    f = rng_grid(2, n, 17, ring=True)
+    L, M = operators(2, n, 2)
+    A = L @ _kron(_s1(n), _s1(n)).T
+    want = np.linalg.solve(A, M @ f.ravel())
+    u, it, rel, _ = O.solve(f, omega=[1.052], rtol=1e-14, max_cycles=200, extra=extra)
+    assert rel <= 1e-13, (it, rel)
+    np.testing.assert_allclose(interior(u).ravel(), want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+def test_extra_sweeps_only_for_the_2d_diagonal_hierarchy():
+    with pytest.raises(ValueError):
+        O.vcycle(rng_grid(3, 7, 18), O.grid(3, 7), omega=[1.11, 1.42, 1.08, 0.99], extra=1)
+    with pytest.raises(ValueError):
+        O.vcycle(rng_grid(2, 7, 18), O.grid(2, 7), hier=O.USUAL, omega=[1.121], extra=1)
