@@ -151,6 +151,16 @@ def extra_measurements(dev, stream):
                                                      "cycles_order2": c2, "cycles_order4": c4, "relres": rel,
                                                      "workload": "same f, second-order cycles (p = 1.052) to "
                                                      "1e-4, then fourth-order cycles to 1e-10"}
+    # one extra Jacobi sweep per level (the extension the paper leaves open;
+    # per-stage kernels, p = 1.052 as the headline)
+    with Context(2, N_SIDE, precision="mixed") as c:
+        c.set_sweeps(1)
+        u = c.new_grid()
+        ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u.zero_(), rtol=RTOL, max_cycles=60, raise_on_fail=False),
+                                          3, stream)
+        out["square4095_sweeps1_mixed"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc,
+                                           "relres": rel, "workload": "same problem, one extra Jacobi sweep per "
+                                           "level (mg_set_sweeps), per-stage kernels"}
     del f
     f3 = torch.from_numpy(I.cube(255)).to(dev)
     for prec in ("mixed", "fp64"):  # fourth-order residual in 3D (19-point, Eq. Efos4)

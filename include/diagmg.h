@@ -158,6 +158,19 @@ mg_status mg_solve(mg_ctx *ctx, const double *f, double *u, double rtol, int max
  * mg_desc.omega, host, 4 entries). */
 mg_status mg_set_omega(mg_ctx *ctx, const double *omega);
 
+/* Extra Jacobi sweeps at each level of the 2D diagonal hierarchy, the
+ * extension the paper's conclusion (Section 5) leaves open: after a level's
+ * prolongation (its two half-sweeps from the coarser values), `extra` more
+ * sweeps repeat both half-sweeps from the level's own current values, with
+ * the level's coefficients (red level 2 p h^2: not-blue points from their
+ * four diagonal neighbours, then blue points; green level p h^2: green-only
+ * points from their four axis neighbours, then red points).  0 (the default)
+ * is the paper's cycle.  extra > 0 runs every level with per-stage kernels
+ * (no fused pair kernels, no carried mixed residual) and applies to
+ * mg_vcycle, mg_solve and mg_rho.  MG_EINVAL unless 0 <= extra <= 64 and,
+ * for extra > 0, the context is a single 2D diagonal problem. */
+mg_status mg_set_sweeps(mg_ctx *ctx, int extra);
+
 /* Convergence factor of the context's V-cycle (the paper's rho, Tables 1-3:
  * the slowest decay of the error) by power iteration on its error
  * propagation: with f = 0 every V-cycle maps the error u to u + B(-L u); u is

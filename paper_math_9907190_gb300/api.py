@@ -138,6 +138,11 @@ class Context:
         N.check(N.lib().mg_set_omega(self._h, arr), "mg_set_omega")
         self.omega = tuple(omega)
 
+    def set_sweeps(self, extra: int):
+        """mg_set_sweeps: extra Jacobi sweeps per level (2D diagonal hierarchy)."""
+        N.check(N.lib().mg_set_sweeps(self._h, int(extra)), "mg_set_sweeps")
+        self.extra = int(extra)
+
     def rho(self, cycles: int = 60, skip: int = 40, seed: int = 0) -> float:
         """mg_rho: convergence factor of the V-cycle by power iteration from a
         seeded random start (interior U[-1, 1])."""

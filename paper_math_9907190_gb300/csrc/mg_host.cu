@@ -94,6 +94,8 @@ struct mg_ctx {
     // carried as a float-float pair (hi in the finest level's residual buffers,
     // double-buffered with r32b; lo in rlo; green pitch, in the pool)
     bool rr = false;
+    bool rr_alloc = false;  // the carried-residual buffers exist (rr is off while extra > 0)
+    int extra = 0;          // extra Jacobi sweeps per level (mg_set_sweeps)
     void *rlo = nullptr;
     void *r32b = nullptr;
     // tuned choices (mg_tune): tile class per pair for the down / up kernels
@@ -124,6 +126,7 @@ struct mg_ctx {
     double g_rtol = -1.0;
     int g_max = -1;
     int g_order = 0;
+    int g_extra = 0;
     double g_omega[4] = {0, 0, 0, 0};
     long long g_prefix_kernels = 0, g_body_kernels = 0;
 };
@@ -433,10 +436,17 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
                 LAUNCH_B(TAG_UP, (k_usual_odd_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
             else
                 LAUNCH_B(TAG_UP, (k_r2g_f_2d<T>), grid2(n, n), B2, a2<const T>(b.v[0], b), a2<const T>(b.v[1], b), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
-            if (u)
-                LAUNCH_B(TAG_FINEST_UP, (k_r2g_c_upd_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
-            else
-                LAUNCH_B(TAG_UP, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+            // extra sweeps (diagonal hierarchy): green-only points from the
+            // level's own red points, then the red points; u += v after the last
+            const int extra = c->d.hierarchy == MG_DIAG ? c->extra : 0;
+            for (int e = 0; e <= extra; e++) {
+                if (e > 0)
+                    LAUNCH_B(TAG_UP, (k_g2g_f_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+                if (u && e == extra)
+                    LAUNCH_B(TAG_FINEST_UP, (k_r2g_c_upd_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<const T>(a.v[0], a), u, c->d.pitch, n, cc, done);
+                else
+                    LAUNCH_B(TAG_UP, (k_r2g_c_2d<T>), grid2(n, n), B2, a2<const T>(a.r[0], a), a2<T>(a.v[0], a), n, cc, done);
+            }
         } else if (c->d.hierarchy == MG_DIAG && sizeof(T) == 4 && green_ff_use(n)) {  // FP32, z-streaming
             const dim3 g3 = green_ff_grid(c, n);
             const size_t sm = sizeof(GreenSSmem);
@@ -475,6 +485,13 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
         const T cc = (T)(2.0 * om[0] * hk2);
         LAUNCH_B(TAG_UP, (k_b2r_oo_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(b.v[0], b), a2<const T>(a.r[1], a), a2<T>(a.v[1], a), nb, cc, done);
         LAUNCH_B(TAG_UP, (k_b2r_ee_2d<T>), grid2(nb, nb), B2, a2<const T>(a.v[1], a), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), nb, cc, done);
+        // extra sweeps: the not-blue points (OO) from the level's own blue
+        // points (EE, the same (a, b) indexing and layout as the blue level),
+        // then the blue points
+        for (int e = 0; e < c->extra; e++) {
+            LAUNCH_B(TAG_UP, (k_b2r_oo_2d<T>), grid2(nb + 1, nb + 1), B2, a2<const T>(a.v[0], a), a2<const T>(a.r[1], a), a2<T>(a.v[1], a), nb, cc, done);
+            LAUNCH_B(TAG_UP, (k_b2r_ee_2d<T>), grid2(nb, nb), B2, a2<const T>(a.v[1], a), a2<const T>(a.r[0], a), a2<T>(a.v[0], a), nb, cc, done);
+        }
         return;
     }
     if (a.kind == KIND_MAG) {  // Eq. Emprolm, Eq. Emprolb
@@ -517,7 +534,7 @@ void coarse_g_slot(mg_ctx *c, int nn, int elems, int &gofs, int &ng) {
 }
 
 void plan_fast2d(mg_ctx *c) {
-    c->fast2d = c->d.dim == 2 && c->d.hierarchy == MG_DIAG;
+    c->fast2d = c->d.dim == 2 && c->d.hierarchy == MG_DIAG && c->extra == 0;
     if (!c->fast2d) return;
     // pairs whose green grid has side <= 63 (or the tuned cut-off) run in one thread block
     const int cut = c->cut_side > 0 ? c->cut_side : 63;
@@ -982,6 +999,7 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     for (auto &l : c->lv) total += (size_t)l.ncos * 2 * ((l.len * c->esz + 255) / 256 * 256);
     // fused update + residual of the mixed 2D diagonal solve (needs at least one pair outside the coarse block)
     c->rr = d->hierarchy == MG_DIAG && d->precision == MG_MIXED && d->order == 2 && d->n > (d->dim == 2 ? 63 : 15);
+    c->rr_alloc = c->rr;
     const size_t r32_bytes = c->rr ? (c->lv[0].len * 4 + 255) / 256 * 256 : 0;
     total += 2 * r32_bytes;
     c->nprob = nprob;
@@ -1320,6 +1338,7 @@ static mg_status build_solve_graph(mg_ctx *c, const double *f, double *u, double
     CK(cudaGraphInstantiate(&c->gexec, g, 0));
     c->g_f = f; c->g_u = u; c->g_rtol = rtol; c->g_max = max_cycles;
     c->g_order = c->d.order;
+    c->g_extra = c->extra;
     for (int q = 0; q < 4; q++) c->g_omega[q] = c->d.omega[q];
     return MG_OK;
 }
@@ -1380,7 +1399,8 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
     if (!c->use_graph || c->probe_tag >= 0)
         return solve_host_loop(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, s);
     if (!c->gexec || c->g_f != f || c->g_u != u || c->g_rtol != rtol || c->g_max != max_cycles ||
-        c->g_order != c->d.order || std::memcmp(c->g_omega, c->d.omega, sizeof c->g_omega) != 0) {
+        c->g_order != c->d.order || c->g_extra != c->extra ||
+        std::memcmp(c->g_omega, c->d.omega, sizeof c->g_omega) != 0) {
         mg_status st = build_solve_graph(c, f, u, rtol, max_cycles);
         if (st != MG_OK) return st;
     }
@@ -1435,6 +1455,15 @@ mg_status mg_set_omega(mg_ctx *c, const double *omega) {
     std::memcpy(c->d.omega, omega, sizeof c->d.omega);
     plan_fast2d(c);
     plan_fast3d(c);
+    return MG_OK;
+}
+
+mg_status mg_set_sweeps(mg_ctx *c, int extra) {
+    if (!c || extra < 0 || extra > 64) return MG_EINVAL;
+    if (extra > 0 && (c->d.dim != 2 || c->d.hierarchy != MG_DIAG || c->nprob != 1)) return MG_EINVAL;
+    c->extra = extra;
+    c->rr = c->rr_alloc && extra == 0;
+    plan_fast2d(c);
     return MG_OK;
 }
 

@@ -261,6 +261,21 @@ __global__ void k_r2g_c_2d(A2<const T> rg, A2<T> vg, int n, T c, const int *done
     vg(i, j) = (s - c * rg(i, j)) * T(0.25);
 }
 
+// extra sweep on a green level, first half: green-only points (i+j odd) from
+// the four axis neighbours of the level itself (extension of Section 5; the
+// second half is k_r2g_c_2d)
+template <typename T>
+__global__ void k_g2g_f_2d(A2<const T> rg, A2<T> vg, int n, T c, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    rg = bt_at(rg, prob_, B);
+    vg = bt_at(vg, prob_, B);
+    MG_IDX2 const int i = tx + 1, j = ty + 1;
+    if (i > n || j > n || ((i + j) & 1) == 0) return;
+    T s = (vg(i - 1, j) + vg(i + 1, j)) + (vg(i, j - 1) + vg(i, j + 1));
+    vg(i, j) = (s - c * rg(i, j)) * T(0.25);
+}
+
 // finest level: second half fused with the update u += v at every point
 template <typename T>
 __global__ void k_r2g_c_upd_2d(A2<const T> rg, A2<const T> vg, double *u, int up, int n, T c, const int *done, Bt B) {
