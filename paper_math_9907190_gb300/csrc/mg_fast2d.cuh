@@ -36,6 +36,49 @@ template <> struct SqAcc<double> {
     __device__ double get() const { return s; }
 };
 
+// The Laplacian part of a direct residual in integer arithmetic (the FP64
+// pipe of this GPU would otherwise bound the residual kernels).  Each u of a
+// stencil is decoded into its signed 53-bit mantissa and exponent; all are
+// aligned to the largest exponent with 6 guard bits (the bits below 2^-59 of
+// the largest |u| are truncated) and summed exactly in 64 bits; the sum is
+// rounded once to a double, already scaled by 1/h^2 = 2^lg (a power of two).
+// Against the FP64 evaluation (4 to 7 roundings of partial sums) the result
+// is at least as accurate; one FP64 subtraction from f remains.
+struct Fx {
+    long long m;  // signed mantissa with the implicit bit (0 for zeros and subnormals)
+    int e;        // biased exponent
+};
+__device__ __forceinline__ Fx fx_dec(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    const long long m = e ? (((long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo) : 0;
+    return Fx{(hi >> 31) ? -m : m, e};
+}
+__device__ __forceinline__ long long fx_al(const Fx &a, int emax) {  // a * 2^6, aligned to emax
+    const int k = emax - a.e;
+    return k > 62 ? 0 : ((a.m << 6) >> k);
+}
+// a * 2^3, aligned to emax: 3 guard bits leave room for the weights of the
+// fourth-order stencils (sums up to 48 x 2^56 < 2^62)
+__device__ __forceinline__ long long fx_al3(const Fx &a, int emax) {
+    const int k = emax - a.e;
+    return k > 62 ? 0 : ((a.m << 3) >> k);
+}
+// the double nearest to s * 2^q (round to nearest even), s a 64-bit integer
+__device__ __forceinline__ double fx_to_double(long long s, int q) {
+    if (s == 0) return 0.0;
+    const unsigned long long sg = s < 0 ? 0x8000000000000000ull : 0ull;
+    unsigned long long a = s < 0 ? 0ull - (unsigned long long)s : (unsigned long long)s;
+    const int lz = __clzll((long long)a);
+    a <<= lz;  // leading one at bit 63
+    unsigned long long m = a >> 11;
+    const unsigned rem = (unsigned)(a & 0x7ffull);
+    m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+    int ex = 63 - lz + q + 1023;
+    if (m >> 53) { m >>= 1; ex += 1; }
+    if (ex < 1) return 0.0;  // below the normal range: far under any residual of interest
+    return __longlong_as_double((long long)(sg | ((unsigned long long)ex << 52) | (m & 0xfffffffffffffull)));
+}
 constexpr int RES_ROWS = 8;  // rows per thread of the residual kernel
 
 // Finest-grid residual, 2D.  Block 32x8 threads; a thread marches RES_ROWS
@@ -47,7 +90,7 @@ constexpr int RES_ROWS = 8;  // rows per thread of the residual kernel
 // Grid z: one slice per problem of the batch.
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(256) k_res0_2d(const double *__restrict__ f, const double *__restrict__ u,
-                                                 int up, int n, double ih2, A2<T> r, double *part,
+                                                 int up, int n, double ih2, int lg, A2<T> r, double *part,
                                                  const int *done, Bt B) {
     __shared__ double sh[32];
     const int prob = blockIdx.z;
@@ -63,12 +106,32 @@ __global__ void __launch_bounds__(256) k_res0_2d(const double *__restrict__ f, c
         double um = uc[-up], u0 = uc[0];
         double wm = 0, w0 = 0, em = 0, e0 = 0;  // diagonal neighbours (order 4)
         if (ORDER == 4) { wm = uc[-up - 1]; em = uc[-up + 1]; w0 = uc[-1]; e0 = uc[1]; }
+        // FP32 levels (mixed), order 4: the Mehrstellen Laplacian in integer
+        // arithmetic (fx_dec / fx_al3): rows j-1 and j stay decoded
+        constexpr bool FX4 = ORDER == 4 && sizeof(T) == 4;
+        Fx xm[3], x0[3];
+        if (FX4) {
+            xm[0] = fx_dec(wm); xm[1] = fx_dec(um); xm[2] = fx_dec(em);
+            x0[0] = fx_dec(w0); x0[1] = fx_dec(u0); x0[2] = fx_dec(e0);
+        }
 #pragma unroll
         for (int q = 0; q < RES_ROWS; q++) {
             if (j0 + q > n) break;
             const double upn = uc[up];
             double res;
-            if (ORDER == 2) {
+            if (FX4) {
+                const Fx xp[3] = {fx_dec(uc[up - 1]), fx_dec(upn), fx_dec(uc[up + 1])};
+                const int emx = max(max(max(xm[0].e, xm[1].e), max(xm[2].e, x0[0].e)),
+                                    max(max(x0[1].e, x0[2].e), max(max(xp[0].e, xp[1].e), xp[2].e)));
+                const long long ax = (fx_al3(x0[0], emx) + fx_al3(x0[2], emx)) + (fx_al3(xm[1], emx) + fx_al3(xp[1], emx));
+                const long long dg = (fx_al3(xm[0], emx) + fx_al3(xm[2], emx)) + (fx_al3(xp[0], emx) + fx_al3(xp[2], emx));
+                const long long c = fx_al3(x0[1], emx);
+                // h^-2 (4 ax + dg - 20 c), rounded once; then / 6 and f - . (2 FP64 operations)
+                const double l6 = fx_to_double((ax << 2) + dg - ((c << 4) + (c << 2)), emx - 1078 + lg);
+                res = fc[0] - l6 * (1.0 / 6.0);
+#pragma unroll
+                for (int t = 0; t < 3; t++) { xm[t] = x0[t]; x0[t] = xp[t]; }
+            } else if (ORDER == 2) {
                 const double s = (uc[-1] + uc[1]) + (um + upn);
                 res = fma(-ih2, fma(-4.0, u0, s), fc[0]);
             } else {
@@ -401,7 +464,7 @@ constexpr int RES3_PLANES = 8;  // planes per thread of the 3D residual kernel
 //   ORDER 4: r = ft - (2 sum6 u + sum12 u - 24u)/(6h^2)   (Eq. Efos4, ft precomputed)
 template <typename T, int ORDER>
 __global__ void __launch_bounds__(256) k_res0_3d(const double *__restrict__ f, const double *__restrict__ u,
-                                                 int up, int n, double ih2, A3<T> r, double *part,
+                                                 int up, int n, double ih2, int lg, A3<T> r, double *part,
                                                  const int *done, Bt B) {
     __shared__ double sh[32];
     const int prob = bt_prob(B), bz = bt_z(B);
@@ -417,12 +480,41 @@ __global__ void __launch_bounds__(256) k_res0_3d(const double *__restrict__ f, c
         const double *uc = u + k0 * pl + (size_t)j * up + i;
         const double *fc = f + k0 * pl + (size_t)j * up + i;
         double ud = uc[-(long)pl], u0 = uc[0];
+        // FP32 levels (mixed), order 4: the 19-point Laplacian in integer
+        // arithmetic (fx_dec / fx_al3); a plane's centre and axis neighbours
+        // (c, w, e, s, n) stay decoded for the next two planes
+        constexpr bool FX4 = ORDER == 4 && sizeof(T) == 4;
+        auto dec5 = [&](const double *p, Fx *x) {
+            x[0] = fx_dec(p[0]); x[1] = fx_dec(p[-1]); x[2] = fx_dec(p[1]); x[3] = fx_dec(p[-up]); x[4] = fx_dec(p[up]);
+        };
+        Fx xm[5], x0[5];
+        if (FX4) { dec5(uc - pl, xm); dec5(uc, x0); }
 #pragma unroll
         for (int q = 0; q < RES3_PLANES; q++) {
             if (k0 + q > n) break;
             const double uu = uc[pl];
             double res;
-            if (ORDER == 2) {
+            if (FX4) {
+                Fx xp[5], dg[4];
+                dec5(uc + pl, xp);
+                dg[0] = fx_dec(uc[-up - 1]); dg[1] = fx_dec(uc[-up + 1]); dg[2] = fx_dec(uc[up - 1]); dg[3] = fx_dec(uc[up + 1]);
+                int emx = max(max(dg[0].e, dg[1].e), max(dg[2].e, dg[3].e));
+#pragma unroll
+                for (int t = 0; t < 5; t++) emx = max(emx, max(max(xm[t].e, x0[t].e), xp[t].e));
+                // faces: the plane's 4 axis neighbours and the centres of planes k-1, k+1
+                const long long fa = ((fx_al3(x0[1], emx) + fx_al3(x0[2], emx)) + (fx_al3(x0[3], emx) + fx_al3(x0[4], emx))) +
+                                     (fx_al3(xm[0], emx) + fx_al3(xp[0], emx));
+                // edges: the plane's 4 diagonal neighbours and the axis neighbours of planes k-1, k+1
+                const long long ed = ((fx_al3(dg[0], emx) + fx_al3(dg[1], emx)) + (fx_al3(dg[2], emx) + fx_al3(dg[3], emx))) +
+                                     ((fx_al3(xm[1], emx) + fx_al3(xm[2], emx)) + (fx_al3(xm[3], emx) + fx_al3(xm[4], emx))) +
+                                     ((fx_al3(xp[1], emx) + fx_al3(xp[2], emx)) + (fx_al3(xp[3], emx) + fx_al3(xp[4], emx)));
+                const long long c = fx_al3(x0[0], emx);
+                // h^-2 (2 faces + edges - 24 c), rounded once; then / 6 and f - . (2 FP64 operations)
+                const double l6 = fx_to_double((fa << 1) + ed - ((c << 4) + (c << 3)), emx - 1078 + lg);
+                res = fc[0] - l6 * (1.0 / 6.0);
+#pragma unroll
+                for (int t = 0; t < 5; t++) { xm[t] = x0[t]; x0[t] = xp[t]; }
+            } else if (ORDER == 2) {
                 const double s = ((uc[-1] + uc[1]) + (uc[-up] + uc[up])) + (ud + uu);
                 res = fma(-ih2, fma(-6.0, u0, s), fc[0]);
             } else {
@@ -1127,43 +1219,6 @@ __device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
     lo = (xh >> 31) ? -l : l;
 }
 
-// The Laplacian part of a direct residual in integer arithmetic (the FP64
-// pipe of this GPU would otherwise bound the residual kernels).  Each u of a
-// stencil is decoded into its signed 53-bit mantissa and exponent; all are
-// aligned to the largest exponent with 6 guard bits (the bits below 2^-59 of
-// the largest |u| are truncated) and summed exactly in 64 bits; the sum is
-// rounded once to a double, already scaled by 1/h^2 = 2^lg (a power of two).
-// Against the FP64 evaluation (4 to 7 roundings of partial sums) the result
-// is at least as accurate; one FP64 subtraction from f remains.
-struct Fx {
-    long long m;  // signed mantissa with the implicit bit (0 for zeros and subnormals)
-    int e;        // biased exponent
-};
-__device__ __forceinline__ Fx fx_dec(double x) {
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const int e = (int)((hi >> 20) & 0x7ffu);
-    const long long m = e ? (((long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo) : 0;
-    return Fx{(hi >> 31) ? -m : m, e};
-}
-__device__ __forceinline__ long long fx_al(const Fx &a, int emax) {  // a * 2^6, aligned to emax
-    const int k = emax - a.e;
-    return k > 62 ? 0 : ((a.m << 6) >> k);
-}
-// the double nearest to s * 2^q (round to nearest even), s a 64-bit integer
-__device__ __forceinline__ double fx_to_double(long long s, int q) {
-    if (s == 0) return 0.0;
-    const unsigned long long sg = s < 0 ? 0x8000000000000000ull : 0ull;
-    unsigned long long a = s < 0 ? 0ull - (unsigned long long)s : (unsigned long long)s;
-    const int lz = __clzll((long long)a);
-    a <<= lz;  // leading one at bit 63
-    unsigned long long m = a >> 11;
-    const unsigned rem = (unsigned)(a & 0x7ffull);
-    m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
-    int ex = 63 - lz + q + 1023;
-    if (m >> 53) { m >>= 1; ex += 1; }
-    if (ex < 1) return 0.0;  // below the normal range: far under any residual of interest
-    return __longlong_as_double((long long)(sg | ((unsigned long long)ex << 52) | (m & 0xfffffffffffffull)));
-}
 // h^-2 (sum of the four neighbours - 4 centre), 2D; lg = log2(h^-2)
 __device__ __forceinline__ double fx_lap5(double c, double w, double e, double s, double n, int lg) {
     const Fx C = fx_dec(c), W = fx_dec(w), E = fx_dec(e), S = fx_dec(s), N = fx_dec(n);

@@ -610,15 +610,15 @@ template <typename T> int launch_res_fast(mg_ctx *c, const double *f, const doub
     if (c->d.dim == 2) {
         g = dim3((n + 31) / 32, (n + 8 * RES_ROWS - 1) / (8 * RES_ROWS), 1);
         if (c->d.order == 2)
-            LAUNCH_B(TAG_RESIDUAL, (k_res0_2d<T, 2>), g, B2, fr, u, c->d.pitch, n, ih2, a2<T>(l0.r[0], l0), c->part, done);
+            LAUNCH_B(TAG_RESIDUAL, (k_res0_2d<T, 2>), g, B2, fr, u, c->d.pitch, n, ih2, 2 * c->m, a2<T>(l0.r[0], l0), c->part, done);
         else
-            LAUNCH_B(TAG_RESIDUAL, (k_res0_2d<T, 4>), g, B2, fr, u, c->d.pitch, n, ih2, a2<T>(l0.r[0], l0), c->part, done);
+            LAUNCH_B(TAG_RESIDUAL, (k_res0_2d<T, 4>), g, B2, fr, u, c->d.pitch, n, ih2, 2 * c->m, a2<T>(l0.r[0], l0), c->part, done);
     } else {
         g = dim3((n + 31) / 32, (n + 7) / 8, (n + RES3_PLANES - 1) / RES3_PLANES);
         if (c->d.order == 2)
-            LAUNCH_B(TAG_RESIDUAL, (k_res0_3d<T, 2>), g, B2, fr, u, c->d.pitch, n, ih2, a3<T>(l0.r[0], l0), c->part, done);
+            LAUNCH_B(TAG_RESIDUAL, (k_res0_3d<T, 2>), g, B2, fr, u, c->d.pitch, n, ih2, 2 * c->m, a3<T>(l0.r[0], l0), c->part, done);
         else
-            LAUNCH_B(TAG_RESIDUAL, (k_res0_3d<T, 4>), g, B2, fr, u, c->d.pitch, n, ih2, a3<T>(l0.r[0], l0), c->part, done);
+            LAUNCH_B(TAG_RESIDUAL, (k_res0_3d<T, 4>), g, B2, fr, u, c->d.pitch, n, ih2, 2 * c->m, a3<T>(l0.r[0], l0), c->part, done);
     }
     c->nparts = (int)(g.x * g.y * g.z);
     return c->nparts;

@@ -202,6 +202,23 @@ def test_mixed_level_residual_rounds_to_nearest(dim, n):
         assert torch.equal(got, want)
 
 
+@pytest.mark.parametrize("dim,n", [(2, 255), (3, 63)])
+def test_mixed_fourth_order_residual(dim, n):
+    """The fourth-order residual of a mixed cycle (Mehrstellen / 19-point
+    Laplacian in integer arithmetic, one rounding) equals the oracle's FP64
+    residual of the same u to within one FP32 unit in the last place."""
+    rng = np.random.default_rng(8)
+    f = I.zero_ring(rng.uniform(-1, 1, (n + 2,) * dim))
+    u = I.zero_ring(rng.uniform(-1, 1, (n + 2,) * dim) * 10.0 ** rng.integers(-3, 3, (n + 2,) * dim))
+    want = O.residual(f, u, order=4)[(slice(1, -1),) * dim]
+    om = default_omega(dim, "diag", 4)
+    with Context(dim, n, order=4, precision="mixed", omega=om) as c:
+        c.vcycle(T(f), T(u))  # the cycle's residual of the input u lands in level 0
+        got = H(c.level_get(0, "r"))[(slice(1, -1),) * dim]
+    ulp = np.spacing(np.abs(want).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(got - want) <= ulp), float(np.max(np.abs(got - want) / ulp))
+
+
 VC_CASES = [
     (2, 63, "diag", 2, (1.0,)), (2, 63, "diag", 2, (1.052,)), (2, 63, "usual", 2, (1.0,)),
     (2, 63, "usual", 2, (1.121,)), (2, 63, "diag", 4, (1.2,)), (2, 63, "usual", 4, (1.216,)),
