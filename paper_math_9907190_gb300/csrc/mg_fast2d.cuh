@@ -1,12 +1,17 @@
-// mg_fast2d.cuh -- fused 2D kernels of the diagonal V-cycle (Section 2).
+// mg_fast2d.cuh -- fused 2D kernels of the diagonal V-cycle (Section 2), the
+// finest residual kernels of both dimensions and the 3D coarse block.
 //
-// Per cycle: k_res0_2d (finest residual, the only FP64 stencil work),
-// k_down_pair_2d (green -> red -> blue restriction of one pair, Eq. Erest2r
-// then Eq. Erest2b, in a shared-memory tile), k_coarse_cta_2d (all pairs below
-// a size cut-off, the coarsest solve and their Jacobi prolongation in one
-// thread block, shared memory only), and k_up_pair_2d (blue -> red -> green
-// Jacobi prolongation of one pair, Eq. Eajacr, Eq. Eajacb and the green-red
-// sweep, in a shared-memory tile; on the finest pair fused with u += v).
+// Per cycle of the FP64 path: k_res0_2d (finest residual, the FP64 stencil
+// work), k_down_pair_2d (green -> red -> blue restriction of one pair, Eq.
+// Erest2r then Eq. Erest2b, in a shared-memory tile), k_coarse_cta_2d (all
+// pairs below a size cut-off, the coarsest solve and their Jacobi
+// prolongation in one thread block, shared memory only), and k_up_pair_2d
+// (blue -> red -> green Jacobi prolongation of one pair, Eq. Eajacr, Eq.
+// Eajacb and the green-red sweep, in a shared-memory tile; on the finest
+// pair fused with u += v).  The mixed path streams the large FP32 pairs
+// (k_down_ff_2d, k_up_ff_2d: one warp per strip of columns marching along
+// the rows) and carries the finest residual between cycles (k_up_ff_2d in
+// its UP_RR form, k_res_rr_2d at the start and the end of a solve).
 //
 // Tiles are indexed by coset cells: cell (a,b) of a pair whose green grid has
 // side n = 2nb+1 holds the green points (2a,2b) EE, (2a+1,2b) OE, (2a,2b+1) EO
