@@ -1224,17 +1224,15 @@ __device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
     lo = (xh >> 31) ? -l : l;
 }
 
-// h^-2 (sum of the four neighbours - 4 centre), 2D; lg = log2(h^-2)
-__device__ __forceinline__ double fx_lap5(double c, double w, double e, double s, double n, int lg) {
-    const Fx C = fx_dec(c), W = fx_dec(w), E = fx_dec(e), S = fx_dec(s), N = fx_dec(n);
+// h^-2 (sum of the four neighbours - 4 centre), 2D, of decoded values; lg = log2(h^-2)
+__device__ __forceinline__ double fx_lap5(const Fx &C, const Fx &W, const Fx &E, const Fx &S, const Fx &N, int lg) {
     const int em = max(max(max(C.e, W.e), max(E.e, S.e)), N.e);
     const long long t = (fx_al(W, em) + fx_al(E, em)) + (fx_al(S, em) + fx_al(N, em)) - (fx_al(C, em) << 2);
     return fx_to_double(t, em - 1081 + lg);
 }
-// h^-2 (sum of the six neighbours - 6 centre), 3D
-__device__ __forceinline__ double fx_lap7(double c, double w, double e, double s, double n, double d, double u,
-                                          int lg) {
-    const Fx C = fx_dec(c), W = fx_dec(w), E = fx_dec(e), S = fx_dec(s), N = fx_dec(n), D = fx_dec(d), U = fx_dec(u);
+// h^-2 (sum of the six neighbours - 6 centre), 3D, of decoded values
+__device__ __forceinline__ double fx_lap7(const Fx &C, const Fx &W, const Fx &E, const Fx &S, const Fx &N,
+                                          const Fx &D, const Fx &U, int lg) {
     const int em = max(max(max(C.e, W.e), max(E.e, S.e)), max(max(N.e, D.e), U.e));
     const long long c6 = fx_al(C, em);
     const long long t = ((fx_al(W, em) + fx_al(E, em)) + (fx_al(S, em) + fx_al(N, em))) + (fx_al(D, em) + fx_al(U, em)) -
@@ -1304,15 +1302,16 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
         auto rows_loop = [&](auto zero_tag) {
             constexpr bool Z = decltype(zero_tag)::value;
             const double *uc = u0p;
-            double um = Z ? 0.0 : uc[-up], u0 = Z ? 0.0 : uc[0];
+            // the column's u stays decoded from row to row (rows j-1, j)
+            Fx um = fx_dec(Z ? 0.0 : uc[-up]), u0 = fx_dec(Z ? 0.0 : uc[0]), upn{0, 0};
 #pragma unroll
             for (int q = 0; q < RES_ROWS; q++) {
                 if (q >= rows) break;
                 const double fv = fr[q];
-                double res = fv, upn = 0.0;
+                double res = fv;
                 if (!Z) {
-                    upn = uc[up];
-                    res = fv - fx_lap5(u0, uc[-1], uc[1], um, upn, lg);
+                    upn = fx_dec(uc[up]);
+                    res = fv - fx_lap5(u0, fx_dec(uc[-1]), fx_dec(uc[1]), um, upn, lg);
                 }
                 float hi;
                 if (START) {
@@ -1503,15 +1502,16 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
         auto planes_loop = [&](auto zero_tag) {
             constexpr bool Z = decltype(zero_tag)::value;
             const double *uc = u0p;
-            double ud = Z ? 0.0 : uc[-(long)pl], u0 = Z ? 0.0 : uc[0];
+            // the column's u stays decoded from plane to plane (planes k-1, k)
+            Fx ud = fx_dec(Z ? 0.0 : uc[-(long)pl]), u0 = fx_dec(Z ? 0.0 : uc[0]), uu{0, 0};
 #pragma unroll
             for (int q = 0; q < RES3_PLANES; q++) {
                 if (q >= planes) break;
                 const double fv = fr[q];
-                double res = fv, uu = 0.0;
+                double res = fv;
                 if (!Z) {
-                    uu = uc[pl];
-                    res = fv - fx_lap7(u0, uc[-1], uc[1], uc[-up], uc[up], ud, uu, lg);
+                    uu = fx_dec(uc[pl]);
+                    res = fv - fx_lap7(u0, fx_dec(uc[-1]), fx_dec(uc[1]), fx_dec(uc[-up]), fx_dec(uc[up]), ud, uu, lg);
                 }
                 float hi;
                 if (START) {
