@@ -30,8 +30,6 @@ struct GreenSSmem {
     float red[4][GS_RH][GS_RC];
     float r[4][GS_VH][GS_GW];    // green residual planes z..z+3 (ring), x from x0 - 4
     float v[4][GS_VH][GS_VW];    // correction planes z-1..z+2 (ring): F at odd, C at even points
-    double u[2][GS_TY][GS_TX];   // u of output planes z, z+1 (UP_RR, UP_ADD)
-    float lo[2][GS_TY][GS_TX];   // lo of the carried residual, planes z, z+1 (UP_RR)
 };
 
 // Green-red sweep of a triple's green level (Eq. Egprolg, then Eq. Egprolr,
@@ -118,29 +116,11 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
             cp_async16(&S.red[zp & 3][rq_ly][4 * rq_j], ok ? C + (size_t)(zp >> 1) * cpl + rq_off : C, ok);
         }
     };
-    auto issue = [&](int zp, int zr, int zo) {
+    auto issue = [&](int zp, int zr) {
         red_copy(zp);
         if (gq_on) {
             const bool ok = gq_ok && zr >= 0 && zr <= n + 1;
             cp_async16(&S.r[zr & 3][gq_ly][4 * gq_j], ok ? rg.p + (size_t)zr * gpl + gq_off : rg.p, ok);
-        }
-        if (UPD && zo >= zb && zo < ze) {
-            // u: row oy, columns x0 + 2 ox, +1 (x0 + 31 <= n: n + 1 is a multiple of 32)
-            const int yo = y0 + oy;
-            const bool ok = yo <= n;
-            const double *src = ok ? u + (size_t)zo * upl + (size_t)yo * up + x0 + 2 * ox : u;
-            if (VU) {
-                cp_async16(&S.u[zo & 1][oy][2 * ox], src, ok);
-            } else {
-                cp_async8(&S.u[zo & 1][oy][2 * ox], src, ok);
-                cp_async8(&S.u[zo & 1][oy][2 * ox + 1], ok ? src + 1 : u, ok);
-            }
-            if (RR && tid < GS_TY * GS_TX / 4) {  // lo: row tid / 8, 16-byte chunk tid % 8
-                const int ly = tid >> 3, j = tid & 7, yl = y0 + ly;
-                const bool okl = yl <= n;
-                cp_async16(&S.lo[zo & 1][ly][4 * j],
-                           okl ? rlo + (size_t)zo * gpl + (size_t)yl * rg.pitch + x0 + 4 * j : rlo, okl);
-            }
         }
         cp_async_commit();
     };
@@ -150,12 +130,25 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
     __syncthreads();
     red_copy(zs + 1);
     red_copy(zs + 2);
-    issue(zs + 3, zs + 2, zs);
+    issue(zs + 3, zs + 2);
     float sq = 0.f, mx = 0.f;
     for (int z = zs; z < ze; z++) {
         cp_async_wait0();
         __syncthreads();                             // step z's planes landed; step z-1 is done with every slot
-        if (z + 1 < ze) issue(z + 4, z + 3, z + 1);  // the next step's planes, in flight during this one
+        if (z + 1 < ze) issue(z + 4, z + 3);  // the next step's planes, in flight during this one
+        // u and lo of the thread's output points of plane z, loaded into
+        // registers now and used after the F and C phases (their latency
+        // hidden by that work)
+        const int xo = x0 + 2 * ox, yo = y0 + oy;
+        const bool outp = z >= zb && xo <= n && yo <= n;
+        double2 uo = make_double2(0.0, 0.0);
+        float2 lo2 = make_float2(0.f, 0.f);
+        if (UPD && outp) {
+            const double *us = u + (size_t)z * upl + (size_t)yo * up + xo;
+            if (VU) uo = *reinterpret_cast<const double2 *>(us);
+            else { uo.x = us[0]; uo.y = us[1]; }
+            if (RR) lo2 = *reinterpret_cast<const float2 *>(rlo + (size_t)z * gpl + (size_t)yo * rg.pitch + xo);
+        }
         // F on plane z+2, tile +- 2: the red neighbours of the k-th F point of
         // a row are the row's red values k+2+p, k+3+p and value k+3 of rows
         // y +- 1 and of planes z+1, z+3 (p: x parity offset of the row)
@@ -209,8 +202,7 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
         // plane z is final on the tile: a thread's points (x, y), (x + 1, y),
         // x = x0 + 2 ox even; x = 0 is the ring, and x <= n implies x + 1 <= n
         if (z >= zb) {
-            const int xo = x0 + 2 * ox, yo = y0 + oy;
-            if (xo <= n && yo <= n) {
+            if (outp) {
                 const float(&V)[GS_VH][GS_VW] = S.v[z & 3];
                 const int lx = 2 * ox + 2, ly = oy + 2;
                 const float2 c = *reinterpret_cast<const float2 *>(&V[ly][lx]);
@@ -224,7 +216,7 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
                     const float2 zm = *reinterpret_cast<const float2 *>(&Vm[ly][lx]);
                     const float2 zp = *reinterpret_cast<const float2 *>(&Vp[ly][lx]);
                     const float2 g = *reinterpret_cast<const float2 *>(&S.r[z & 3][ly][lx + 2]);
-                    const float2 l = *reinterpret_cast<const float2 *>(&S.lo[z & 1][oy][2 * ox]);
+                    const float2 l = lo2;
                     // Laplacian of the quantized v: exact (quant_magic, qb = 20)
                     const float sa = __fadd_rn(__fadd_rn(__fadd_rn(V[ly][lx - 1], c.y), __fadd_rn(dn.x, upr.x)),
                                                __fadd_rn(zm.x, zp.x));
@@ -245,7 +237,6 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
                     }
                 }
                 if (UPD) {
-                    const double2 uo = *reinterpret_cast<const double2 *>(&S.u[z & 1][oy][2 * ox]);
                     double *ud = u + (size_t)z * upl + (size_t)yo * up + xo;
                     const double ub = uo.y + widen(c.y);
                     if (VU && lft) {
