@@ -67,7 +67,9 @@ enum { MG_FP64 = 0, MG_MIXED = 1 };   /* precision of the level arithmetic */
  *   precision  MG_FP64: every level in FP64.  MG_MIXED: residual on the
  *              finest grid and the update u += v in FP64, all levels and
  *              sweeps in FP32, coarsest solve in FP64 (iterative refinement
- *              with one FP32 V-cycle per FP64 residual).
+ *              with one FP32 V-cycle per FP64 residual).  The residual norms
+ *              square FP32 values, so MG_MIXED wants residual and right-hand
+ *              side values between about 1e-18 and 1e18 in magnitude.
  *   coarsest   interior side of the coarsest axis grid: 1, 3 or 7 (2D), 1 or
  *              3 (3D), <= n.  It is solved exactly.
  *   omega      over-relaxation weights multiplying the residual term of the

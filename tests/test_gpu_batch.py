@@ -73,3 +73,23 @@ def test_batch_repeat_and_warm_start():
         assert all(c == 0 for c in cyc2)
         us3, cyc3, _ = bt.solve(fs, [torch.zeros_like(u) for u in us], rtol=1e-10)
         assert cyc3 == cyc and all(torch.equal(a, b) for a, b in zip(us, us3))
+
+
+@pytest.mark.parametrize("dim,n", [(2, 255), (3, 63)])
+def test_batch_mixed_scales_per_problem(dim, n):
+    """The quantizer of the mixed path's finest correction is bounded per
+    problem: problems of one batch whose right-hand sides differ by 1e-12 ..
+    1e12 in scale each converge as they do alone (same cycles, a direct
+    residual below the tolerance)."""
+    scales = [1e-12, 1.0, 1e12, 1e-4]
+    base = I.uniform_f(dim, n, 31)
+    fs = [base * s for s in scales]
+    with Batch(dim, [n] * len(scales), precision="mixed") as bt:
+        us, cyc, rel = bt.solve([T(f) for f in fs], rtol=1e-10, max_cycles=60)
+    with Context(dim, n, precision="mixed") as c:
+        _, c1, r1, _ = c.solve(T(base), rtol=1e-10, max_cycles=60)
+    for b, s in enumerate(scales):
+        assert cyc[b] == c1 and rel[b] <= 1e-10, (s, cyc[b], rel[b])
+        # scaling f scales u (the quantizer's bound scales with it)
+        np.testing.assert_allclose(us[b].cpu().numpy() / s, us[1].cpu().numpy(), rtol=0,
+                                   atol=1e-6 * float(us[1].abs().max()))
