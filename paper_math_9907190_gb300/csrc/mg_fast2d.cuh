@@ -33,12 +33,12 @@ template <typename T> struct SqAcc;                     // per-thread sum of r^2
 template <> struct SqAcc<float> {                       // mixed: FP32 squares
     float s = 0.f;
     __device__ void add(double r) { const float q = narrow(r); s = fmaf(q, q, s); }
-    __device__ double get() const { return (double)s; }
+    __device__ double block(double *sh) const { return block_sum_f(s, sh); }
 };
 template <> struct SqAcc<double> {
     double s = 0.0;
     __device__ void add(double r) { s = fma(r, r, s); }
-    __device__ double get() const { return s; }
+    __device__ double block(double *sh) const { return block_sum(s, sh); }
 };
 
 // The Laplacian part of a direct residual in integer arithmetic (the FP64
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_res0_2d(const double *__restrict__ f, c
             uc += up; fc += up;
         }
     }
-    double s = block_sum(acc.get(), sh);
+    double s = acc.block(sh);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         part[(size_t)prob * B.nparts + blockIdx.x + gridDim.x * blockIdx.y] = s;
 }
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(256) k_res0_3d(const double *__restrict__ f, c
             uc += pl; fc += pl;
         }
     }
-    double s = block_sum(acc.get(), sh);
+    double s = acc.block(sh);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz)] = s;
 }
@@ -1204,7 +1204,7 @@ __global__ void __launch_bounds__(256) k_norm_f(const double *__restrict__ f, in
                 acc = fmaf(v, v, acc);
             }
     }
-    const double s = block_sum((double)acc, sh);
+    const double s = block_sum_f(acc, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0)
         part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz)] = s;
 }
@@ -1334,11 +1334,11 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
         else rows_loop(std::false_type{});
     }
     const size_t slot = (size_t)prob * B.nparts + blockIdx.x + gridDim.x * blockIdx.y;
-    const double s = block_sum((double)acc, sh);
+    const double s = block_sum_f(acc, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) part[slot] = s;
     if (START) {
         __syncthreads();
-        const double sf = block_sum((double)facc, sh);
+        const double sf = block_sum_f(facc, sh);
         const float m = block_max(mx, shm);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             fpart[slot] = sf;
@@ -1534,11 +1534,11 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
         else planes_loop(std::false_type{});
     }
     const size_t slot = (size_t)prob * B.nparts + blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz);
-    const double s = block_sum((double)acc, sh);
+    const double s = block_sum_f(acc, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) part[slot] = s;
     if (START) {
         __syncthreads();
-        const double sf = block_sum((double)facc, sh);
+        const double sf = block_sum_f(facc, sh);
         const float m = block_max(mx, shm);
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             fpart[slot] = sf;

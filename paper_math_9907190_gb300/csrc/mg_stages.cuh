@@ -604,6 +604,25 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return v;
 }
 
+// block sum of per-thread FP32 sums: FP32 within each warp, FP64 across the
+// warps (result valid in thread 0).  A kernel with a few points per thread
+// would otherwise spend more FP64 instructions on the reduction than on its
+// points (a conversion and five adds per thread); the warp sums of 32
+// non-negative terms carry a relative error below 2^-19.
+__device__ __forceinline__ double block_sum_f(float v, double *sh) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((tid & 31) == 0) sh[tid >> 5] = (double)v;
+    __syncthreads();
+    double d = 0.0;
+    if (tid < 32) {
+        d = tid < (nt + 31) / 32 ? sh[tid] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    }
+    return d;
+}
+
 
 // r = f - L_h u (Eq. Evpois, 5-point) or Eq. Efos2 (ORDER 4); RHS_ONLY: u = 0.
 // Writes r (level precision) and, if r64 != nullptr, the FP64 value to the
