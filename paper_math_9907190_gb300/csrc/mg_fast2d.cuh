@@ -1240,6 +1240,10 @@ __device__ __forceinline__ double fx_lap7(const Fx &C, const Fx &W, const Fx &E,
     return fx_to_double(t, em - 1081 + lg);
 }
 
+// warps of a residual block (of 8) that evaluate the stencil in FP64 rather
+// than with the integer Laplacian: both pipes then share the work
+constexpr int RES_F64_WARPS = 3;
+
 // OR of the magnitude bits of a double (zero iff +-0), in 32-bit operations
 __device__ __forceinline__ unsigned mag_bits(double x) {
     return ((unsigned)__double2hiint(x) << 1) | (unsigned)__double2loint(x);
@@ -1296,22 +1300,30 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
             }
             zero = ob == 0;  // with __all_sync below: every neighbour of every point of the warp
         }
-        // warp-uniform: either no FP64 arithmetic at all (two separate loops,
-        // so that the stencil is branched over rather than predicated) or the
-        // full stencil
-        auto rows_loop = [&](auto zero_tag) {
-            constexpr bool Z = decltype(zero_tag)::value;
+        // warp-uniform: either no FP64 arithmetic at all (separate loops, so
+        // that the stencil is branched over rather than predicated) or the
+        // full stencil, in integer arithmetic (fx_lap5) in most warps and in
+        // FP64 in the last RES_F64_WARPS of the block, so that the FP64 pipe
+        // works beside the integer ones
+        auto rows_loop = [&](auto mode_tag) {
+            constexpr int MODE = decltype(mode_tag)::value;  // 0 u = 0, 1 integer, 2 FP64
+            constexpr bool Z = MODE == 0;
             const double *uc = u0p;
-            // the column's u stays decoded from row to row (rows j-1, j)
-            Fx um = fx_dec(Z ? 0.0 : uc[-up]), u0 = fx_dec(Z ? 0.0 : uc[0]), upn{0, 0};
+            // the column's u stays decoded (or loaded) from row to row (rows j-1, j)
+            Fx um = fx_dec(MODE == 1 ? uc[-up] : 0.0), u0 = fx_dec(MODE == 1 ? uc[0] : 0.0), upn{0, 0};
+            double dm = MODE == 2 ? uc[-up] : 0.0, d0 = MODE == 2 ? uc[0] : 0.0, dp = 0.0;
+            const double ih2 = __longlong_as_double((long long)(1023 + lg) << 52);  // 2^lg
 #pragma unroll
             for (int q = 0; q < RES_ROWS; q++) {
                 if (q >= rows) break;
                 const double fv = fr[q];
                 double res = fv;
-                if (!Z) {
+                if (MODE == 1) {
                     upn = fx_dec(uc[up]);
                     res = fv - fx_lap5(u0, fx_dec(uc[-1]), fx_dec(uc[1]), um, upn, lg);
+                } else if (MODE == 2) {
+                    dp = uc[up];
+                    res = fma(-ih2, fma(-4.0, d0, (uc[-1] + uc[1]) + (dm + dp)), fv);
                 }
                 float hi;
                 if (START) {
@@ -1327,11 +1339,13 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
                 }
                 acc = fmaf(hi, hi, acc);
                 um = u0; u0 = upn;
+                dm = d0; d0 = dp;
                 uc += up;
             }
         };
-        if (__all_sync(__activemask(), zero)) rows_loop(std::true_type{});
-        else rows_loop(std::false_type{});
+        if (__all_sync(__activemask(), zero)) rows_loop(std::integral_constant<int, 0>{});
+        else if ((int)threadIdx.y < 8 - RES_F64_WARPS) rows_loop(std::integral_constant<int, 1>{});
+        else rows_loop(std::integral_constant<int, 2>{});
     }
     const size_t slot = (size_t)prob * B.nparts + blockIdx.x + gridDim.x * blockIdx.y;
     const double s = block_sum_f(acc, sh);
@@ -1499,19 +1513,27 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
         double fr[RES3_PLANES];
 #pragma unroll
         for (int q = 0; q < RES3_PLANES; q++) fr[q] = q < planes ? f0p[(size_t)q * pl] : 0.0;
-        auto planes_loop = [&](auto zero_tag) {
-            constexpr bool Z = decltype(zero_tag)::value;
+        // as in k_res_rr_2d: no arithmetic where u is 0, else the integer
+        // Laplacian, or FP64 in the last RES_F64_WARPS warps of the block
+        auto planes_loop = [&](auto mode_tag) {
+            constexpr int MODE = decltype(mode_tag)::value;  // 0 u = 0, 1 integer, 2 FP64
+            constexpr bool Z = MODE == 0;
             const double *uc = u0p;
-            // the column's u stays decoded from plane to plane (planes k-1, k)
-            Fx ud = fx_dec(Z ? 0.0 : uc[-(long)pl]), u0 = fx_dec(Z ? 0.0 : uc[0]), uu{0, 0};
+            // the column's u stays decoded (or loaded) from plane to plane (planes k-1, k)
+            Fx ud = fx_dec(MODE == 1 ? uc[-(long)pl] : 0.0), u0 = fx_dec(MODE == 1 ? uc[0] : 0.0), uu{0, 0};
+            double dd = MODE == 2 ? uc[-(long)pl] : 0.0, d0 = MODE == 2 ? uc[0] : 0.0, du = 0.0;
+            const double ih2 = __longlong_as_double((long long)(1023 + lg) << 52);  // 2^lg
 #pragma unroll
             for (int q = 0; q < RES3_PLANES; q++) {
                 if (q >= planes) break;
                 const double fv = fr[q];
                 double res = fv;
-                if (!Z) {
+                if (MODE == 1) {
                     uu = fx_dec(uc[pl]);
                     res = fv - fx_lap7(u0, fx_dec(uc[-1]), fx_dec(uc[1]), fx_dec(uc[-up]), fx_dec(uc[up]), ud, uu, lg);
+                } else if (MODE == 2) {
+                    du = uc[pl];
+                    res = fma(-ih2, fma(-6.0, d0, ((uc[-1] + uc[1]) + (uc[-up] + uc[up])) + (dd + du)), fv);
                 }
                 float hi;
                 if (START) {
@@ -1527,11 +1549,13 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
                 }
                 acc = fmaf(hi, hi, acc);
                 ud = u0; u0 = uu;
+                dd = d0; d0 = du;
                 uc += pl;
             }
         };
-        if (all_zero) planes_loop(std::true_type{});
-        else planes_loop(std::false_type{});
+        if (all_zero) planes_loop(std::integral_constant<int, 0>{});
+        else if ((int)threadIdx.y < 8 - RES_F64_WARPS) planes_loop(std::integral_constant<int, 1>{});
+        else planes_loop(std::integral_constant<int, 2>{});
     }
     const size_t slot = (size_t)prob * B.nparts + blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * bz);
     const double s = block_sum_f(acc, sh);
