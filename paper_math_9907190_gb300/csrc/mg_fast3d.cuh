@@ -353,29 +353,15 @@ __global__ void __launch_bounds__(256) k_r2m_zm_3d(Red3<const T> red, Mag3<T> ma
     ZmIdx z;
     if (!zm_cell(z, 0, nb, zm, P, Q, B)) return;
     const T *eee = red.eee.p, *ooe = red.ooe.p, *oeo = red.oeo.p, *eoo = red.eoo.p;
-    // values of plane c-1 that plane c reads again are carried in registers:
-    // oeo(a-1,b,c-1), oeo(a,b,c-1), eoo(a,b-1,c-1), eoo(a,b,c-1) and ooe(a,b,c);
-    // index -1 values (read only for a, b or c = 0) are not loaded
-    const bool ab = z.a >= 1 && z.b >= 1;
     size_t i = z.i;
-    T pm1 = T(0), p0 = T(0), qm1 = T(0), q0 = T(0);
-    if (ab && z.c0 >= 1) { pm1 = oeo[i - Q - 1]; p0 = oeo[i - Q]; qm1 = eoo[i - Q - P]; q0 = eoo[i - Q]; }
-    T oc = ooe[i];
     for (int c = z.c0; c < z.c1; c++, i += Q) {
-        const T ou = ooe[i + Q], oeo0 = oeo[i], oeoy = oeo[i + P], eoo0 = eoo[i], eoox = eoo[i + 1];
-        T oeom = T(0), eoom = T(0);
-        if (ab) {
-            oeom = oeo[i - 1];
-            eoom = eoo[i - P];
-            if (c >= 1) {
-                const T s1 = (ooe[i - P - 1] + ooe[i - P]) + (ooe[i - 1] + oc);
-                const T s2 = (pm1 + p0) + (oeom + oeo0);
-                const T s3 = (qm1 + q0) + (eoom + eoo0);
-                mag.eee.p[i] = (T(12) * eee[i] + (s1 + s2 + s3)) * T(1.0 / 24.0);
-            }
+        if (z.a >= 1 && z.b >= 1 && c >= 1) {
+            const T s1 = (ooe[i - P - 1] + ooe[i - P]) + (ooe[i - 1] + ooe[i]);
+            const T s2 = (oeo[i - Q - 1] + oeo[i - Q]) + (oeo[i - 1] + oeo[i]);
+            const T s3 = (eoo[i - Q - P] + eoo[i - Q]) + (eoo[i - P] + eoo[i]);
+            mag.eee.p[i] = (T(12) * eee[i] + (s1 + s2 + s3)) * T(1.0 / 24.0);
         }
-        mag.ooo.p[i] = ((eoo0 + eoox) + (oeo0 + oeoy) + (oc + ou)) * T(1.0 / 6.0);
-        pm1 = oeom; p0 = oeo0; qm1 = eoom; q0 = eoo0; oc = ou;
+        mag.ooo.p[i] = ((eoo[i] + eoo[i + 1]) + (oeo[i] + oeo[i + P]) + (ooe[i] + ooe[i + Q])) * T(1.0 / 6.0);
     }
 }
 
