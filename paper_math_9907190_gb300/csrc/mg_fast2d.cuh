@@ -183,7 +183,6 @@ __global__ void __launch_bounds__(256) k_down_pair_2d(A2<const T> g, A2<T> ee, A
     g = bt_at(g, prob, B); ee = bt_at(ee, prob, B); oo = bt_at(oo, prob, B); blue = bt_at(blue, prob, B);
     const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
     const int n = 2 * nb + 1;
-    const int tid = threadIdx.x + 32 * threadIdx.y;
     MG_FOR2(GX, GY) {
         const int gx = 2 * a0 - 2 + x, gy = 2 * b0 - 2 + y;
         sg[y][x] = (gx >= 0 && gx <= n + 1 && gy >= 0 && gy <= n + 1) ? g(gx, gy) : T(0);
@@ -242,7 +241,6 @@ __global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T
     if (B.utab) u = B.utab[prob];
     const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
     const int n = 2 * nb + 1;
-    const int tid = threadIdx.x + 32 * threadIdx.y;
     // loads
 MG_FOR2(TA + 5, TB + 5) {
         const int a = a0 - 2 + x, b = b0 - 2 + y;
@@ -624,7 +622,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
     gp.store(Gs, P.ng, tid);
     __syncthreads();
     for (int t = 0; t < ntri; t++) {
-        const int n = P.nk[t], nb = (n - 1) / 2, nc = nb + 1;
+        const int n = P.nk[t], nb = (n - 1) / 2;
         A3<T> g = G3(P.og_r[t], n);
         A3<T> eee = C3(P.orr[t][0], nb), ooe = C3(P.orr[t][1], nb), oeo = C3(P.orr[t][2], nb), eoo = C3(P.orr[t][3], nb);
         A3<T> me = C3(P.omr[t][0], nb), mo = C3(P.omr[t][1], nb);
@@ -668,7 +666,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
     }
     __syncthreads();
     for (int t = ntri - 1; t >= 0; t--) {
-        const int n = P.nk[t], nb = (n - 1) / 2, nc = nb + 1;
+        const int n = P.nk[t], nb = (n - 1) / 2;
         A3<T> rg = G3(P.og_r[t], n), vg = G3(P.og_v[t], n), vb = G3(P.og_v[t + 1], nb);
         A3<T> r_e = C3(P.orr[t][0], nb), r_ooe = C3(P.orr[t][1], nb), r_oeo = C3(P.orr[t][2], nb), r_eoo = C3(P.orr[t][3], nb);
         A3<T> v_e = C3(P.orv[t][0], nb), v_ooe = C3(P.orv[t][1], nb), v_oeo = C3(P.orv[t][2], nb), v_eoo = C3(P.orv[t][3], nb);

@@ -763,7 +763,7 @@ int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStre
     const dim3 blk(32, FF_WARPS, 1);
     const bool vu = k == 0 && c->nprob == 1 && ((uintptr_t)u % 16) == 0 && c->d.pitch % 2 == 0;
     const float c2 = (float)(2.0 * p * hk * hk), c1 = (float)(p * hk * hk), s2 = (float)(1.0 / (hk * hk));
-    const int tag = k == 0 ? TAG_FINEST_UP : TAG_UP;
+    const int tag = k == 0 ? (int)TAG_FINEST_UP : (int)TAG_UP;
 #define MG_UPFF(MODE, VU)                                                                                          \
     LAUNCH_B(tag, (k_up_ff_2d<MODE, VU>), grid, blk, a2<const float>(b.v[0], b), a2<const float>(r.r[0], r),     \
              a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b, a2<float>(g.v[0], g),           \
@@ -1246,7 +1246,7 @@ static void solve_prefix(mg_ctx *c, const double *f, const double *u, double rto
     } else {
         LAUNCH(TAG_CONTROL, (k_ctrl_init_b), (c->nprob + 255) / 256, 256, c->ctl, c->nprob, rtol, max_cycles);
     }
-    int np, nfp;
+    int np = 0, nfp;
     const double *fpart = c->part;
     if (c->rr) {
         np = nfp = launch_res_rr(c, f, u, nullptr, s, true);
@@ -1676,7 +1676,7 @@ namespace {
 std::string tune_key(const mg_ctx *c) {
     cudaDeviceProp pr{};
     cudaGetDeviceProperties(&pr, c->dev);
-    char buf[320];
+    char buf[400];
     // "kernels": the version of the tunable kernel set (classes change meaning with it)
     std::snprintf(buf, sizeof buf, "\"kernels\": 2, \"device\": \"%s\", \"dim\": %d, \"n\": %d, \"hier\": %d, \"prec\": %d, \"nprob\": %d",
                   pr.name, c->d.dim, c->d.n, c->d.hierarchy, c->d.precision, c->nprob);
