@@ -119,17 +119,33 @@ struct mg_ctx {
     bool use_graph = true;      // DIAGMG_SOLVE_GRAPH=0: host-driven loop (same kernels; for profilers)
     bool pdl = false;           // DIAGMG_PDL=1: programmatic dependent launch (measured neutral in the solve graph)
     cudaStream_t cs1 = nullptr, cs2 = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
-    const double *g_f = nullptr;
-    double *g_u = nullptr;
-    double g_rtol = -1.0;
-    int g_max = -1;
-    int g_order = 0;
-    int g_extra = 0;
-    double g_omega[4] = {0, 0, 0, 0};
-    long long g_prefix_kernels = 0, g_body_kernels = 0;
+    // instantiated solve graphs, keyed by their arguments and the context's
+    // settings; a few are kept (least recently used replaced) so that a caller
+    // alternating between buffers does not rebuild a graph per solve
+    struct SolveGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const double *f = nullptr;
+        double *u = nullptr;
+        double rtol = -1.0;
+        int max = -1, order = 0, extra = 0;
+        double omega[4] = {0, 0, 0, 0};
+        long long prefix_kernels = 0, body_kernels = 0;  // launches of the prefix and of one cycle
+        unsigned long long used = 0;
+    };
+    SolveGraph gcache[4];
+    unsigned long long gtick = 0;
+    long long g_prefix_kernels = 0, g_body_kernels = 0;  // of the last capture
 };
+
+static void drop_solve_graph(mg_ctx::SolveGraph &e) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.graph) cudaGraphDestroy(e.graph);
+    e = mg_ctx::SolveGraph{};
+}
+static void drop_solve_graphs(mg_ctx *c) {
+    for (auto &e : c->gcache) drop_solve_graph(e);
+}
 
 namespace {
 
@@ -963,8 +979,7 @@ mg_status mg_destroy(mg_ctx *c) {
     if (!c) return MG_OK;
     cudaDeviceSynchronize();
     for (auto e : c->pev) cudaEventDestroy(e);
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    if (c->graph) cudaGraphDestroy(c->graph);
+    drop_solve_graphs(c);
     if (c->cs1) cudaStreamDestroy(c->cs1);
     if (c->cs2) cudaStreamDestroy(c->cs2);
     cudaFree(c->pool);
@@ -1324,9 +1339,15 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     return MG_OK;
 }
 
-static mg_status build_solve_graph(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles) {
-    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+static bool solve_graph_matches(const mg_ctx *c, const mg_ctx::SolveGraph &e, const double *f, const double *u,
+                                double rtol, int max_cycles) {
+    return e.exec && e.f == f && e.u == u && e.rtol == rtol && e.max == max_cycles && e.order == c->d.order &&
+           e.extra == c->extra && std::memcmp(e.omega, c->d.omega, sizeof e.omega) == 0;
+}
+
+static mg_status build_solve_graph(mg_ctx *c, mg_ctx::SolveGraph &slot, const double *f, double *u, double rtol,
+                                   int max_cycles) {
+    drop_solve_graph(slot);
     cudaStream_t s = c->cs1;
     CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     mg_status st = capture_solve(c, f, u, rtol, max_cycles, s, c->cs2);
@@ -1334,12 +1355,15 @@ static mg_status build_solve_graph(mg_ctx *c, const double *f, double *u, double
     const cudaError_t e = cudaStreamEndCapture(s, &g);
     if (st != MG_OK) { if (g) cudaGraphDestroy(g); return st; }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    c->graph = g;
-    CK(cudaGraphInstantiate(&c->gexec, g, 0));
-    c->g_f = f; c->g_u = u; c->g_rtol = rtol; c->g_max = max_cycles;
-    c->g_order = c->d.order;
-    c->g_extra = c->extra;
-    for (int q = 0; q < 4; q++) c->g_omega[q] = c->d.omega[q];
+    slot.graph = g;
+    const cudaError_t ei = cudaGraphInstantiate(&slot.exec, g, 0);
+    if (ei != cudaSuccess) { drop_solve_graph(slot); return cuda_fail(ei, "cudaGraphInstantiate"); }
+    slot.f = f; slot.u = u; slot.rtol = rtol; slot.max = max_cycles;
+    slot.order = c->d.order;
+    slot.extra = c->extra;
+    for (int q = 0; q < 4; q++) slot.omega[q] = c->d.omega[q];
+    slot.prefix_kernels = c->g_prefix_kernels;
+    slot.body_kernels = c->g_body_kernels;
     return MG_OK;
 }
 
@@ -1398,17 +1422,22 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
     // a probe needs one event pair per launch, which a replayed graph cannot give
     if (!c->use_graph || c->probe_tag >= 0)
         return solve_host_loop(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, s);
-    if (!c->gexec || c->g_f != f || c->g_u != u || c->g_rtol != rtol || c->g_max != max_cycles ||
-        c->g_order != c->d.order || c->g_extra != c->extra ||
-        std::memcmp(c->g_omega, c->d.omega, sizeof c->g_omega) != 0) {
-        mg_status st = build_solve_graph(c, f, u, rtol, max_cycles);
-        if (st != MG_OK) return st;
+    mg_ctx::SolveGraph *hit = nullptr, *lru = &c->gcache[0];
+    for (auto &e : c->gcache) {
+        if (solve_graph_matches(c, e, f, u, rtol, max_cycles)) { hit = &e; break; }
+        if (e.used < lru->used) lru = &e;
     }
-    CK(cudaGraphLaunch(c->gexec, s));
+    if (!hit) {
+        mg_status st = build_solve_graph(c, *lru, f, u, rtol, max_cycles);
+        if (st != MG_OK) return st;
+        hit = lru;
+    }
+    hit->used = ++c->gtick;
+    CK(cudaGraphLaunch(hit->exec, s));
     Ctrl host{};
     CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    c->launches += c->g_prefix_kernels + (long long)host.cycles * c->g_body_kernels;
+    c->launches += hit->prefix_kernels + (long long)host.cycles * hit->body_kernels;
     if (cycles_out) *cycles_out = host.cycles;
     if (relres_out) *relres_out = host.relres;
     if (history && host.cycles > 0) {
@@ -1738,8 +1767,7 @@ void cache_append(const char *path, const std::string &key, const mg_ctx *c) {
 void replan(mg_ctx *c) {
     plan_fast2d(c);
     plan_fast3d(c);
-    if (c->gexec) { cudaGraphExecDestroy(c->gexec); c->gexec = nullptr; }
-    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    drop_solve_graphs(c);
 }
 
 // Measure and apply: the coarse-block cut-off by whole V-cycles, then the tile
