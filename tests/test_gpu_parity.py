@@ -393,3 +393,26 @@ def test_mixed_carried_residual_equals_direct_residual(dim, n):
     # both are direct residuals of size ~1e-11 |f| formed from O(|f|) terms: the
     # FP64 rounding of mg_residual's evaluation alone is ~1e-5 of the result
     assert abs(true_rel - rel) <= 1e-3 * true_rel, (true_rel, rel)
+
+
+def test_solve_graphs_cached_per_buffers():
+    """A context keeps one solve graph per argument set (up to four): solves
+    alternating between buffer pairs give the results of fresh contexts, and
+    the launch count grows by the same amount for every repeat."""
+    n = 255
+    fa, fb = I.uniform_f(2, n, 41), I.uniform_f(2, n, 42)
+    with Context(2, n, precision="mixed") as c:
+        bufs = [(T(fa), c.new_grid()), (T(fb), c.new_grid())]
+        outs, counts = [], []
+        for k in range(6):
+            f, u = bufs[k % 2]
+            l0 = c.launch_count()
+            u2, it, rel, _ = c.solve(f, u.zero_(), rtol=1e-10)
+            counts.append(c.launch_count() - l0)
+            outs.append(u2.clone())
+    for k in range(2, 6):
+        assert torch.equal(outs[k], outs[k - 2]) and counts[k] == counts[k - 2]
+    for k, f in ((0, fa), (1, fb)):
+        with Context(2, n, precision="mixed") as c:
+            u, _, _, _ = c.solve(T(f), rtol=1e-10)
+        assert torch.equal(u, outs[k])
