@@ -48,7 +48,7 @@ template <int MODE, bool VU>
 __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<float> rga, float *rgb, A3<float> vg,
                                                      float *__restrict__ rlo, double *__restrict__ u, int up, int n,
                                                      float cg, float s2, int zch, double *part, Ctrl *ctl,
-                                                     const int *done, Bt B) {
+                                                     CtrlFuse cf, const int *done, Bt B) {
     extern __shared__ __align__(16) unsigned char smraw[];
     GreenSSmem &S = *reinterpret_cast<GreenSSmem *>(smraw);
     __shared__ double sh[32];
@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(256) k_green_ff_3d(Red3<const float> vr, A3<fl
             part[blockIdx.x + gridDim.x * (blockIdx.y + (size_t)gridDim.y * zc)] = s;
             atomicMax(&ctl[prob].rmax[pq ^ 1], __float_as_uint(m));
         }
+        if (cf.arrive) ctrl_last_block(cf, ctl + prob, part, gridDim.x * gridDim.y * gridDim.z, sh);  // one problem only
     }
 }
 

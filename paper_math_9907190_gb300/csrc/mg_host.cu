@@ -470,7 +470,7 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
 #define MG_GFF(TAG, MODE, VU)                                                                                     \
     LAUNCH_SMEM_B(TAG, (k_green_ff_3d<MODE, VU>), g3, dim3(32, 8, 1), sm, red3v<const float>(b.v, b),               \
                   a3<float>(a.r[0], a), (float *)nullptr, a3<float>(a.v[0], a), (float *)nullptr, u, c->d.pitch, n, \
-                  (float)cc, 0.f, zch, (double *)nullptr, (Ctrl *)nullptr, done)
+                  (float)cc, 0.f, zch, (double *)nullptr, (Ctrl *)nullptr, CtrlFuse{}, done)
             if (u && green_ff_vu(c, u)) MG_GFF(TAG_FINEST_UP, UP_ADD, true);
             else if (u) MG_GFF(TAG_FINEST_UP, UP_ADD, false);
             else MG_GFF(TAG_UP, UP_STORE, false);
@@ -861,7 +861,7 @@ int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, 
 }
 
 // one cycle of the fused mixed 3D path; returns the partial sums per problem
-int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
+int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s, CtrlFuse cf) {
     const int lc = 3 * c->kc;
     for (int l = 0; l < lc; l++) launch_restrict<float>(c, l, done, s, true);
     const Level &gk = c->lv[lc];
@@ -876,7 +876,7 @@ int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
     LAUNCH_SMEM_B(TAG_FINEST_UP, (k_green_ff_3d<UP_RR, VU>), g3, dim3(32, 8, 1), sizeof(GreenSSmem),              \
                   red3v<const float>(b.v, b), a3<float>(a.r[0], a), (float *)c->r32b, a3<float>(a.v[0], a),       \
                   (float *)c->rlo, u, c->d.pitch, n, (float)(c->d.omega[3] * h2), (float)(1.0 / h2),             \
-                  green_ff_zch(c, n), c->part, c->ctl, done)
+                  green_ff_zch(c, n), c->part, c->ctl, cf, done)
     if (green_ff_vu(c, u)) MG_GFF(true);
     else MG_GFF(false);
 #undef MG_GFF
@@ -1314,8 +1314,13 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     CK(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const long long l1 = c->launches;
     int np2;
+    // a single mixed 3D problem: the finest kernel's last block runs the
+    // control step (in 2D the fused epilogue slowed the finest kernel more
+    // than the launch it saves)
+    const bool fuse = c->rr && c->nprob == 1 && c->d.dim == 3;
     if (c->rr) {
-        np2 = c->d.dim == 3 ? vcycle_rr3(c, u, done, s2) : vcycle_rr(c, u, done, s2);
+        const CtrlFuse cf = fuse ? CtrlFuse{&c->ctl->arrive, c->hist, loop, 1} : CtrlFuse{};
+        np2 = c->d.dim == 3 ? vcycle_rr3(c, u, done, s2, cf) : vcycle_rr(c, u, done, s2);
     } else {
         mg_status stv = fp64 ? vcycle_t<double>(c, f, u, done, false, s2) : vcycle_t<float>(c, f, u, done, false, s2);
         if (stv != MG_OK) {
@@ -1325,7 +1330,7 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
         }
         np2 = solve_residual(c, f, u, nullptr, s2);
     }
-    launch_ctrl(c, np2, 0, loop, 1, s2);
+    if (!fuse) launch_ctrl(c, np2, 0, loop, 1, s2);
     c->g_body_kernels = c->launches - l1;
     CK(cudaStreamEndCapture(s2, &body));
     if (c->rr) {  // the carried residual ignores the rounding of u: report a direct one
@@ -1384,14 +1389,16 @@ static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double r
     const int group = c->probe_tag >= 0 ? 1 : 4;
     for (int cyc = 0; cyc < max_cycles; cyc += group) {
         for (int q = 0; q < group && cyc + q < max_cycles; q++) {
+            const bool fuse = c->rr && c->nprob == 1 && c->d.dim == 3;  // control step in the finest kernel
             if (c->rr) {
-                np = c->d.dim == 3 ? vcycle_rr3(c, u, done, s) : vcycle_rr(c, u, done, s);
+                const CtrlFuse cf = fuse ? CtrlFuse{&c->ctl->arrive, c->hist, none, 0} : CtrlFuse{};
+                np = c->d.dim == 3 ? vcycle_rr3(c, u, done, s, cf) : vcycle_rr(c, u, done, s);
             } else {
                 mg_status st = fp64 ? vcycle_t<double>(c, f, u, done, false, s) : vcycle_t<float>(c, f, u, done, false, s);
                 if (st != MG_OK) return st;
                 np = solve_residual(c, f, u, done, s);
             }
-            launch_ctrl(c, np, 0, none, 0, s);
+            if (!fuse) launch_ctrl(c, np, 0, none, 0, s);
         }
         CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));

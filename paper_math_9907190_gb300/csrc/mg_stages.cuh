@@ -97,6 +97,7 @@ struct Ctrl {
     // against (bit patterns of non-negative floats, which order as unsigned)
     unsigned vmax;     // max |v| of the level the finest sweep starts from, this cycle
     unsigned rmax[2];  // max |hi| of each of the two finest residual buffers
+    unsigned arrive;   // blocks of the fused finest kernel that finished this cycle
 };
 
 // maximum of v over the block (valid in thread 0); NaN is ignored
@@ -717,16 +718,10 @@ __device__ __forceinline__ double sum_parts(const double *part, int nblk, double
 // after the residual of the warm start (first = 1) or of a new iterate:
 // record the history, decide whether to stop.  Inside the solver's graph
 // (use_loop = 1) it also sets the graph's loop condition to "not done".
-__global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, int first,
-                       cudaGraphConditionalHandle loop, int use_loop) {
-    pdl_wait();
-    __shared__ double sh[32];
-    if (!first && ctl->done) {
-        if (use_loop && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
-        return;
-    }
-    double s = sum_parts(part, nblk, sh);
-    if (threadIdx.x != 0) return;
+// the control step, given the residual sum s of the new iterate (first: of
+// the warm start); one thread
+__device__ __forceinline__ void ctrl_step(Ctrl *ctl, double s, double *hist, int first,
+                                          cudaGraphConditionalHandle loop, int use_loop) {
     if (!first) ctl->par ^= 1;
     ctl->rmax[ctl->par ^ 1] = 0u;  // the buffer the next cycle writes
     ctl->vmax = 0u;
@@ -749,11 +744,57 @@ __global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, in
     if (use_loop) cudaGraphSetConditional(loop, ctl->done ? 0u : 1u);
 }
 
+__global__ void k_ctrl(const double *part, int nblk, Ctrl *ctl, double *hist, int first,
+                       cudaGraphConditionalHandle loop, int use_loop) {
+    pdl_wait();
+    __shared__ double sh[32];
+    if (!first && ctl->done) {
+        if (use_loop && threadIdx.x == 0) cudaGraphSetConditional(loop, 0);
+        return;
+    }
+    double s = sum_parts(part, nblk, sh);
+    if (threadIdx.x == 0) ctrl_step(ctl, s, hist, first, loop, use_loop);
+}
+
+// The control step fused into the finest kernel of a single-problem mixed
+// solve (no separate launch per cycle): every block writes its partial sum,
+// and the last block of the launch to finish (counted in ctl->arrive) sums
+// all partials in a fixed order and runs the control step.  arrive == nullptr:
+// not fused.
+struct CtrlFuse {
+    unsigned *arrive;
+    double *hist;
+    cudaGraphConditionalHandle loop;
+    int use_loop;
+};
+// every block, after its thread 0 wrote part[own]; sh: 32 doubles
+__device__ __noinline__ void ctrl_last_block(const CtrlFuse &cf, Ctrl *ctl, const double *part, int nblk,
+                                                double *sh) {
+    __shared__ int last;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();  // the block's partial (and its atomics) before its arrival
+        last = atomicAdd(cf.arrive, 1u) == (unsigned)nblk - 1u;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double v = 0.0;
+    for (int q = tid; q < nblk; q += nt) v += __ldcg(part + q);
+    const double sum = block_sum(v, sh);
+    if (tid == 0) {
+        *cf.arrive = 0u;
+        ctrl_step(ctl, sum, cf.hist, 0, cf.loop, cf.use_loop);
+    }
+}
+
 __global__ void k_ctrl_init(Ctrl *ctl, double rtol, int max_cycles) {
     pdl_wait();
     ctl->r2 = 0.0; ctl->relres = 0.0; ctl->rel0 = 0.0; ctl->rtol = rtol;
     ctl->done = 0; ctl->cycles = 0; ctl->max_cycles = max_cycles; ctl->status = 0; ctl->par = 0;
-    ctl->vmax = 0u; ctl->rmax[0] = 0u; ctl->rmax[1] = 0u;
+    ctl->vmax = 0u; ctl->rmax[0] = 0u; ctl->rmax[1] = 0u; ctl->arrive = 0u;
 }
 
 // per problem of a batch (one block each): f2 = sum of that problem's partials
@@ -770,7 +811,7 @@ __global__ void k_ctrl_init_b(Ctrl *ctl, int nprob, double rtol, int max_cycles)
         Ctrl &c = ctl[p];
         c.r2 = 0.0; c.relres = 0.0; c.rel0 = 0.0; c.rtol = rtol;
         c.done = 0; c.cycles = 0; c.max_cycles = max_cycles; c.status = 0; c.par = 0;
-        c.vmax = 0u; c.rmax[0] = 0u; c.rmax[1] = 0u;
+        c.vmax = 0u; c.rmax[0] = 0u; c.rmax[1] = 0u; c.arrive = 0u;
     }
 }
 
