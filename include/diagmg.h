@@ -147,7 +147,11 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *u, void *stream);
 
 /* V-cycles from the warm start u until ||r||_2 / ||r(u=0)||_2 <= rtol, where
  * r is the residual of the context's order, or until max_cycles cycles.  The
- * convergence test runs on the device; the host waits once at the end.
+ * convergence test runs on the device; the host waits once at the end.  The
+ * whole solve is one CUDA graph launch; the context keeps the graphs of its
+ * four most recent argument sets (f, u, rtol, max_cycles, with its weights,
+ * order and sweeps), so alternating between a few buffers does not rebuild
+ * them (set DIAGMG_SOLVE_GRAPH=0 for a host-driven loop of the same kernels).
  *   cycles_out  (host, nullable) cycles applied
  *   relres_out  (host, nullable) final relative residual
  *   history     (host, nullable, length max_cycles) relative residual after
