@@ -416,3 +416,21 @@ def test_solve_graphs_cached_per_buffers():
         with Context(2, n, precision="mixed") as c:
             u, _, _, _ = c.solve(T(f), rtol=1e-10)
         assert torch.equal(u, outs[k])
+
+
+@pytest.mark.parametrize("dim,n", [(2, 255), (3, 63)])
+def test_mixed_warm_start(dim, n):
+    """The fused mixed path from a nonzero warm start: the start residual then
+    evaluates the stencil (integer and FP64 warps); a converged start needs no
+    cycle, a partly converged one finishes the solve."""
+    f = T(I.uniform_f(dim, n, 51))
+    with Context(dim, n, precision="mixed") as c:
+        u, it, rel, _ = c.solve(f, rtol=1e-10)
+        u2, it2, rel2, _ = c.solve(f, u.clone(), rtol=1e-10)
+        assert it2 == 0 and abs(rel2 - rel) <= 1e-6 * rel
+        up, itp, relp, _ = c.solve(f, rtol=1e-10, max_cycles=3, raise_on_fail=False)
+        uw, itw, relw, _ = c.solve(f, up.clone(), rtol=1e-10)
+        assert relw <= 1e-10 and itw <= it - 2
+        r2 = c.residual(f, uw)
+        f2 = c.residual(f, torch.zeros_like(uw))
+        assert math.sqrt(r2 / f2) <= 1.02e-10
