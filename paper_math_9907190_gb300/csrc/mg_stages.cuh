@@ -39,11 +39,17 @@ template <typename T> struct A3 {  // 3D array view
     }
 };
 
-// Kernels are launched with programmatic dependent launch: a kernel may start
-// while the previous one in the stream finishes, and waits here (before its
-// first read of anything another kernel wrote) for it to complete.  A kernel
-// launched without that attribute passes at once.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+// Kernels may be launched with programmatic dependent launch: a kernel may
+// start while the previous one in the stream finishes, and waits here (before
+// its first access to memory that another kernel reads or writes) for it to
+// complete.  Once every block of this kernel has passed the wait, the next
+// kernel may be scheduled onto the free SM slots, where its blocks wait in
+// turn; so the launch of one kernel overlaps the tail of the one before.  A
+// kernel launched without that attribute passes at once.
+__device__ __forceinline__ void pdl_wait() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
 __device__ __forceinline__ bool stop(const int *done) {
     pdl_wait();
     return done != nullptr && *(volatile const int *)done;
@@ -914,6 +920,7 @@ __global__ void k_rho_record(const double *part, int nblk, double *scal, double 
     }
 }
 __global__ void k_scale_grid(double *u, int up, int n, int dim, const double *scal) {
+    pdl_wait();
     MG_IDX2 const int i = tx + 1, j = ty + 1, k = dim == 3 ? (int)blockIdx.z + 1 : 0;
     if (i > n || j > n) return;
     u[((size_t)k * (n + 2) + j) * up + i] *= scal[0];

@@ -79,3 +79,44 @@ def test_binding_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(N, "LIB_PATH", os.path.join(os.path.dirname(N.LIB_PATH), "missing-libdiagmg.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         N.lib()
+
+
+def _kernel_heads(path):
+    """(name, statements before the first wait) of every __global__ function."""
+    import re
+    src = open(path).read()
+    out = []
+    for m in re.finditer(r"__global__[^{;]*?\b(k_\w+)\s*\(", src):
+        body = src.index("{", m.end())
+        head = []
+        for line in src[body + 1:].split("\n"):
+            t = line.strip()
+            if "pdl_wait()" in t or "stop(" in t:
+                break
+            t = t.split("//")[0].strip()
+            if t:
+                head.append(t)
+            if len(head) > 40:
+                break
+        out.append((m.group(1), head))
+    return out
+
+
+def test_every_context_kernel_waits_before_touching_memory():
+    """With programmatic dependent launch a kernel starts while the previous
+    one finishes, so each kernel a context launches must wait (pdl_wait, or
+    stop, which calls it) before it reads or writes global memory: only
+    declarations, shared arrays and index arithmetic may come first."""
+    import re
+    csrc = os.path.join(os.path.dirname(N.__file__), "csrc")
+    allowed = re.compile(r"^(__shared__|extern __shared__|constexpr|const int|MG_IDX2|UpSmem|GreenSSmem|Green3Smem"
+                         r"|T \*sm = reinterpret_cast)")
+    seen = 0
+    for name in ("mg_stages.cuh", "mg_fast2d.cuh", "mg_fast3d.cuh"):
+        for kern, head in _kernel_heads(os.path.join(csrc, name)):
+            seen += 1
+            assert len(head) <= 12, (kern, head)
+            for t in head:
+                assert allowed.match(t), (kern, t)
+                assert "[" not in t.split("=")[-1] or "__shared__" in t, (kern, t)
+    assert seen >= 55
