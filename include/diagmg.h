@@ -152,10 +152,11 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *u, void *stream);
  * four most recent argument sets (f, u, rtol, max_cycles, with its weights,
  * order and sweeps), so alternating between a few buffers does not rebuild
  * them (set DIAGMG_SOLVE_GRAPH=0 for a host-driven loop of the same kernels).
- * Single 2D problems in FP32 levels launch their kernels with programmatic
- * dependent launch, so that a kernel's launch overlaps the tail of the one
- * before; DIAGMG_PDL=1 or 0, read at mg_create, turns it on or off for any
- * context.  The results are the same bit for bit.
+ * Single 2D problems launch their kernels with programmatic dependent
+ * launch (in FP64, only the grids of at most 256 blocks), so that a kernel's
+ * launch overlaps the tail of the one before.  DIAGMG_PDL=1 or 0 and
+ * DIAGMG_PDL_MAX_BLOCKS=<blocks> (0: no limit), read at mg_create, override
+ * that for any context.  The results are the same bit for bit.
  *   cycles_out  (host, nullable) cycles applied
  *   relres_out  (host, nullable) final relative residual
  *   history     (host, nullable, length max_cycles) relative residual after

@@ -118,6 +118,7 @@ struct mg_ctx {
     bool capturing = false;
     bool use_graph = true;      // DIAGMG_SOLVE_GRAPH=0: host-driven loop (same kernels; for profilers)
     bool pdl = false;           // programmatic dependent launch (default per configuration; DIAGMG_PDL=0/1)
+    int pdl_max_blocks = 0;     // > 0: only for grids of at most this many blocks (DIAGMG_PDL_MAX_BLOCKS)
     cudaStream_t cs1 = nullptr, cs2 = nullptr;
     // instantiated solve graphs, keyed by their arguments and the context's
     // settings; a few are kept (least recently used replaced) so that a caller
@@ -262,7 +263,8 @@ void launch_k(const mg_ctx *c, void (*kern)(P...), dim3 g, dim3 b, size_t sm, cu
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = c->pdl ? 1 : 0;
+    const long long nblk = (long long)g.x * g.y * g.z;
+    cfg.numAttrs = c->pdl && (c->pdl_max_blocks <= 0 || nblk <= c->pdl_max_blocks) ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kern, std::forward<A>(args)...);
 }
 #define LAUNCH(tag, kern, grid, block, ...)                                \
@@ -1098,12 +1100,18 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     {
         const char *ev = std::getenv("DIAGMG_SOLVE_GRAPH");
         c->use_graph = !(ev && ev[0] == '0');
-        // programmatic dependent launch: on by default where it measured
-        // faster (single 2D problems in FP32 levels: 1-2%); 3D and FP64
-        // cycles measured 1-2% slower with it.  DIAGMG_PDL=0/1 overrides.
+        // programmatic dependent launch, by default where it measured faster
+        // (medians of 6 x 10 solves): single 2D problems, every launch in
+        // FP32 levels (4095^2: 2.224 -> 2.207 ms) and the grids of at most
+        // 256 blocks in FP64 (9.573 -> 9.458 ms; every launch: 9.60 ms).  3D
+        // cycles measured 1-2% slower with it on every launch and no faster
+        // on the small grids alone.  DIAGMG_PDL=0/1 and
+        // DIAGMG_PDL_MAX_BLOCKS=<blocks> (0: no limit) override.
         const char *ep = std::getenv("DIAGMG_PDL");
-        c->pdl = ep && (ep[0] == '0' || ep[0] == '1') ? ep[0] == '1'
-                                                       : d->dim == 2 && d->precision != MG_FP64 && nprob == 1;
+        const bool by_default = d->dim == 2 && nprob == 1;
+        c->pdl = ep && (ep[0] == '0' || ep[0] == '1') ? ep[0] == '1' : by_default;
+        const char *eb = std::getenv("DIAGMG_PDL_MAX_BLOCKS");
+        c->pdl_max_blocks = eb ? std::atoi(eb) : (d->precision == MG_FP64 ? 256 : 0);
     }
     if (cudaStreamCreateWithFlags(&c->cs1, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess) {
