@@ -1,0 +1,102 @@
+"""Edge cases of the solve through the C ABI: the smallest grids in mixed
+precision, caller arrays with a padded row pitch (the padding is neither
+read into the result nor written), and the launch settings (programmatic
+dependent launch on, off, or on small grids only) giving the same bits."""
+
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+from paper_math_9907190_gb300 import Context, default_omega
+from paper_math_9907190_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DEV = torch.device("cuda", 0)
+
+
+def _f(dim, n, seed=1):
+    return I.uniform_f(dim, n, seed) if dim == 2 else I.cube(n)
+
+
+def _check_against_oracle(dim, n, f, u, rel, order=2):
+    """Final relative residual by the oracle, and the solution against the
+    oracle's converged FP64 solution."""
+    assert rel <= 1e-10
+    r = O.residual(f, u, order)
+    r0 = O.residual(f, O.grid(dim, n), order)
+    assert math.sqrt(O.norm2_interior(r) / O.norm2_interior(r0)) <= 1.05e-10
+    uo, _, _, _ = O.solve(f, omega=list(default_omega(dim, "diag", order)), rtol=1e-13, max_cycles=200)
+    assert np.linalg.norm(u - uo) / np.linalg.norm(uo) <= 1e-8
+
+
+@pytest.mark.parametrize("dim,n", [(2, 3), (2, 7), (2, 15), (3, 3), (3, 7), (3, 15)])
+def test_smallest_grids_mixed(dim, n):
+    """Grids with one to three levels above the coarsest: every level runs in
+    the single coarse thread block."""
+    f = _f(dim, n)
+    with Context(dim, n, precision="mixed", omega=default_omega(dim, "diag", 2)) as c:
+        u, it, rel, hist = c.solve(torch.from_numpy(f).to(DEV), rtol=1e-10, max_cycles=40)
+    assert 1 <= it <= 12 and len(hist) == it
+    _check_against_oracle(dim, n, f, u.cpu().numpy(), rel)
+
+
+def _padded(a, pitch, fill):
+    """A device copy of the full grid `a` inside rows of `pitch` elements; the
+    columns beyond n + 2 hold `fill`.  Returns (view, backing tensor)."""
+    shape = a.shape[:-1] + (pitch,)
+    back = torch.full(shape, fill, dtype=torch.float64, device=DEV)
+    view = back[..., : a.shape[-1]]
+    view.copy_(torch.from_numpy(a))
+    return view, back
+
+
+@pytest.mark.parametrize("dim,n,pad", [(2, 255, 45), (2, 1023, 7), (3, 31, 6), (3, 63, 11)])
+def test_padded_pitch_solve_leaves_padding_alone(dim, n, pad):
+    """The fused mixed path (carried residual) with a caller pitch above n + 2:
+    the padding holds NaN, which must neither reach the result nor be
+    overwritten."""
+    f = _f(dim, n)
+    pitch = n + 2 + pad
+    fv, fb = _padded(f, pitch, float("nan"))
+    uv, ub = _padded(np.zeros_like(f), pitch, float("nan"))
+    with Context(dim, n, precision="mixed", omega=default_omega(dim, "diag", 2), pitch=pitch) as c:
+        _, it, rel, _ = c.solve(fv, uv, rtol=1e-10, max_cycles=40)
+    assert torch.isnan(ub[..., n + 2:]).all() and torch.isnan(fb[..., n + 2:]).all()
+    u = uv.cpu().numpy()
+    assert np.isfinite(u).all()
+    ring = np.ones(u.shape, dtype=bool)
+    ring[(slice(1, -1),) * dim] = False
+    assert (u[ring] == 0.0).all()
+    # the same solve on unpadded arrays gives the same bits
+    with Context(dim, n, precision="mixed", omega=default_omega(dim, "diag", 2)) as c:
+        u2, it2, rel2, _ = c.solve(torch.from_numpy(f).to(DEV), rtol=1e-10, max_cycles=40)
+    assert it2 == it and rel2 == rel
+    assert np.array_equal(u2.cpu().numpy(), u)
+    _check_against_oracle(dim, n, f, u, rel)
+
+
+@pytest.mark.parametrize("dim,n,prec", [(2, 1023, "mixed"), (2, 255, "fp64"), (3, 63, "mixed"), (3, 31, "fp64")])
+def test_launch_settings_give_the_same_bits(dim, n, prec, monkeypatch):
+    """Programmatic dependent launch changes when a kernel is scheduled, never
+    what it computes: every kernel waits for the previous one before its first
+    access to memory."""
+    f = torch.from_numpy(_f(dim, n)).to(DEV)
+    outs = []
+    for pdl, maxb in (("0", "0"), ("1", "0"), ("1", "64")):
+        monkeypatch.setenv("DIAGMG_PDL", pdl)
+        monkeypatch.setenv("DIAGMG_PDL_MAX_BLOCKS", maxb)
+        with Context(dim, n, precision=prec, omega=default_omega(dim, "diag", 2)) as c:
+            u, it, rel, hist = c.solve(f, rtol=1e-10, max_cycles=40)
+            c.vcycle(f, u)  # the per-cycle entry point too
+            outs.append((u.cpu().numpy(), it, rel, hist))
+    for u, it, rel, hist in outs[1:]:
+        assert it == outs[0][1] and rel == outs[0][2] and hist == outs[0][3]
+        assert np.array_equal(u, outs[0][0])
