@@ -15,7 +15,9 @@
  *     ring, x fastest: element (i,j) at [j*pitch + i], (i,j,k) at
  *     [(k*(n+2) + j)*pitch + i], 0 <= i,j,k <= n+1, pitch >= n+2 elements.
  *   - Memory.  Every array pointer is caller-owned DEVICE memory on the
- *     context's device unless the parameter says "host".  The library never
+ *     context's device unless the parameter says "host".  A grid pointer
+ *     (f, u, r, a level grid) must be 8-byte aligned (an FP64 element
+ *     boundary); a null or misaligned one gives MG_EINVAL.  The library never
  *     keeps a caller pointer after a call returns.  All workspace (level
  *     buffers, norms, control words) is allocated by mg_create and freed by
  *     mg_destroy; no other call allocates device memory.

@@ -36,6 +36,11 @@ mg_status cuda_fail(cudaError_t e, const char *where) {
         if (e_ != cudaSuccess) return cuda_fail(e_, where);    \
     } while (0)
 
+// a caller grid pointer the kernels can take: not null, on an FP64 element
+// boundary (8 bytes; 16-byte vector paths are chosen only where the pointer
+// and the pitch allow them)
+bool bad_grid(const void *p) { return !p || ((uintptr_t)p & 7u) != 0; }
+
 int log2_side(int n) {
     if (n < 1) return -1;
     long v = (long)n + 1;
@@ -1145,7 +1150,7 @@ mg_status mg_level_info(const mg_ctx *c, int level, int *side, int *kind) {
 
 mg_status mg_residual(mg_ctx *c, const double *f, const double *u, double h, int order, double *r, double *norm2,
                       void *stream) {
-    if (!c || !f || !u) return MG_EINVAL;
+    if (!c || bad_grid(f) || bad_grid(u) || (r && bad_grid(r))) return MG_EINVAL;
     if (order != c->d.order) return MG_EINVAL;
     if (std::fabs(h - c->h) > 1e-15 * c->h) return MG_EINVAL;
     cudaStream_t s = S(stream);
@@ -1187,7 +1192,7 @@ mg_status mg_jacobi_prolong(mg_ctx *c, int level, const double *omega, void *str
 }
 
 static mg_status level_io(mg_ctx *c, int level, int which, double *grid, int to_level, void *stream) {
-    if (!c || !grid || level < 0 || level > c->L || (which != 0 && which != 1)) return MG_EINVAL;
+    if (!c || bad_grid(grid) || level < 0 || level > c->L || (which != 0 && which != 1)) return MG_EINVAL;
     const Level &l = c->lv[level];
     void *const *arr = which == 0 ? l.r : l.v;
     const int side = l.side, dim = c->d.dim;
@@ -1214,7 +1219,7 @@ mg_status mg_level_set(mg_ctx *c, int level, int which, const double *grid, void
 }
 
 mg_status mg_vcycle(mg_ctx *c, const double *f, double *u, void *stream) {
-    if (!c || !f || !u) return MG_EINVAL;
+    if (!c || bad_grid(f) || bad_grid(u)) return MG_EINVAL;
     if (c->d.order == 4) {
         cudaStream_t s = S(stream);
         launch_rhs4(c, f, s);
@@ -1436,7 +1441,8 @@ static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double r
 
 mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
                    double *relres_out, double *history, void *stream) {
-    if (!c || !f || !u || !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap) return MG_EINVAL;
+    if (!c || bad_grid(f) || bad_grid(u) || !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap)
+        return MG_EINVAL;
     cudaStream_t s = S(stream);
     // a probe needs one event pair per launch, which a replayed graph cannot give
     if (!c->use_graph || c->probe_tag >= 0)
@@ -1473,7 +1479,7 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
 // then running a few cycles on the fourth-order residual.
 mg_status mg_solve_two_stage(mg_ctx *c, const double *f, double *u, const double *omega2, double rtol2, double rtol,
                              int max_cycles, int *cycles2_out, int *cycles4_out, double *relres_out, void *stream) {
-    if (!c || !f || !u || c->d.order != 4 || !(rtol2 >= 0.0)) return MG_EINVAL;
+    if (!c || bad_grid(f) || bad_grid(u) || c->d.order != 4 || !(rtol2 >= 0.0)) return MG_EINVAL;
     double om4[4];
     std::memcpy(om4, c->d.omega, sizeof om4);
     // stage 1: the same levels and schedule with the second-order residual
@@ -1519,7 +1525,7 @@ mg_status mg_set_sweeps(mg_ctx *c, int extra) {
 // propagation u <- u + B(0 - L u) (f = 0): the geometric mean of the norm
 // ratios of the last (cycles - skip) cycles, u renormalised every cycle.
 mg_status mg_rho(mg_ctx *c, const double *zero_f, double *u, int cycles, int skip, double *rho_out, void *stream) {
-    if (!c || !zero_f || !u || !rho_out || cycles < 2 || skip < 0 || skip >= cycles || cycles > c->hist_cap ||
+    if (!c || bad_grid(zero_f) || bad_grid(u) || !rho_out || cycles < 2 || skip < 0 || skip >= cycles || cycles > c->hist_cap ||
         c->nprob != 1)
         return MG_EINVAL;
     cudaStream_t s = S(stream);
@@ -1639,7 +1645,7 @@ mg_status mg_solve_batched(mg_batch *b, const double *const *f, double *const *u
                            int *cycles_out, double *relres_out, void *stream) {
     if (!b || !f || !u || !(rtol >= 0.0) || max_cycles < 0) return MG_EINVAL;
     for (int p = 0; p < b->nprob; p++)
-        if (!f[p] || !u[p]) return MG_EINVAL;
+        if (bad_grid(f[p]) || bad_grid(u[p])) return MG_EINVAL;
     for (auto c : b->grp)
         if (max_cycles > c->hist_cap) return MG_EINVAL;
     cudaStream_t s = S(stream);
@@ -1859,7 +1865,7 @@ mg_status zero_u(mg_ctx *c, double *u, cudaStream_t s) {
 extern "C" {
 
 mg_status mg_tune(mg_ctx *c, const double *f, double *u, const char *cache_path, int *measured_out, void *stream) {
-    if (!c || !f || !u) return MG_EINVAL;
+    if (!c || bad_grid(f) || bad_grid(u)) return MG_EINVAL;
     if (measured_out) *measured_out = 0;
     if (!c->fast2d && !c->fast3d) return MG_OK;  // nothing tunable on this path
     const char *path = cache_path ? cache_path : std::getenv("DIAGMG_TUNE_CACHE");
@@ -1893,6 +1899,8 @@ mg_status mg_tune_info(const mg_ctx *c, int *cut_side, int *npairs, int *tiles_d
 mg_status mg_batch_tune(mg_batch *b, const double *const *f, double *const *u, const char *cache_path,
                         void *stream) {
     if (!b || !f || !u) return MG_EINVAL;
+    for (int p = 0; p < b->nprob; p++)
+        if (bad_grid(f[p]) || bad_grid(u[p])) return MG_EINVAL;
     cudaStream_t s = S(stream);
     for (size_t g = 0; g < b->grp.size(); g++) {
         mg_ctx *c = b->grp[g];

@@ -104,6 +104,8 @@ extern "C" mg_status mg_residual_noalloc(int dim, int n, int pitch, double h, in
                                          const double *u, double *r, double *norm2, void *stream) {
     if (dim != 2 && dim != 3) return MG_EINVAL;
     if (log2_side(n) < 1 || pitch < n + 2 || (order != 2 && order != 4) || !f || !u) return MG_EINVAL;
+    // FP64 element boundaries (8 bytes) for every grid pointer
+    if (((uintptr_t)f | (uintptr_t)u | (uintptr_t)r) & 7u) return MG_EINVAL;
     if (!(h > 0.0) || std::fabs(h - 1.0 / (n + 1)) > 1e-15 / (n + 1)) return MG_EINVAL;
     // the size limit of the static scratch: one partial sum per thread block
     const long long nblk = (long long)((n + 31) / 32) * ((n + 7) / 8) * (dim == 3 ? n : 1);

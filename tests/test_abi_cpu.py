@@ -68,6 +68,19 @@ def test_null_arguments_rejected(lib):
     assert lib.mg_destroy(None) == N.MG_OK
 
 
+def test_noalloc_rejects_misaligned_grids_before_touching_cuda(lib):
+    """Grid pointers must sit on FP64 element boundaries; the check comes
+    before any CUDA call, so it runs without a GPU (the addresses are never
+    dereferenced)."""
+    f = ctypes.c_void_p(0x10000)
+    for bad in (0x10001, 0x10004, 0x1000C):
+        p = ctypes.c_void_p(bad)
+        h = 1.0 / 64
+        assert lib.mg_residual_noalloc(2, 63, 65, ctypes.c_double(h), 2, p, f, None, None, None) == N.MG_EINVAL
+        assert lib.mg_residual_noalloc(2, 63, 65, ctypes.c_double(h), 2, f, p, None, None, None) == N.MG_EINVAL
+        assert lib.mg_residual_noalloc(2, 63, 65, ctypes.c_double(h), 2, f, f, p, None, None) == N.MG_EINVAL
+
+
 def test_strerror(lib):
     for st in (0, -1, -2, -3, -4, -5, -6):
         assert lib.mg_strerror(st)

@@ -1,7 +1,8 @@
 """Edge cases of the solve through the C ABI: the smallest grids in mixed
 precision, caller arrays with a padded row pitch (the padding is neither
-read into the result nor written), and the launch settings (programmatic
-dependent launch on, off, or on small grids only) giving the same bits."""
+read into the result nor written), the launch settings (programmatic
+dependent launch on, off, or on small grids only) giving the same bits, and
+misaligned grid pointers refused before any launch."""
 
 import math
 
@@ -100,3 +101,31 @@ def test_launch_settings_give_the_same_bits(dim, n, prec, monkeypatch):
     for u, it, rel, hist in outs[1:]:
         assert it == outs[0][1] and rel == outs[0][2] and hist == outs[0][3]
         assert np.array_equal(u, outs[0][0])
+
+
+def test_misaligned_grid_pointers_are_refused_before_any_launch():
+    """A grid pointer off an FP64 element boundary is an argument error: the
+    call returns MG_EINVAL and launches nothing."""
+    import ctypes
+
+    from paper_math_9907190_gb300 import _native as N
+
+    n = 63
+    with Context(2, n, precision="mixed") as c:
+        f = torch.from_numpy(_f(2, n)).to(DEV)
+        u = c.new_grid()
+        lib = N.lib()
+        before = c.launch_count()
+        ok, bad = ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u.data_ptr() + 4)
+        fp = ctypes.c_void_p(f.data_ptr())
+        cyc, rel = ctypes.c_int(), ctypes.c_double()
+        assert lib.mg_solve(c._h, fp, bad, 1e-10, 10, ctypes.byref(cyc), ctypes.byref(rel), None, None) == N.MG_EINVAL
+        assert lib.mg_solve(c._h, ctypes.c_void_p(f.data_ptr() + 2), ok, 1e-10, 10, None, None, None,
+                            None) == N.MG_EINVAL
+        assert lib.mg_vcycle(c._h, fp, bad, None) == N.MG_EINVAL
+        assert lib.mg_residual(c._h, fp, bad, ctypes.c_double(1.0 / (n + 1)), 2, None, None, None) == N.MG_EINVAL
+        assert lib.mg_level_get(c._h, 0, 0, bad, None) == N.MG_EINVAL
+        assert c.launch_count() == before
+        # the same context still solves
+        _, it, rel2, _ = c.solve(f, u, rtol=1e-10, max_cycles=40)
+        assert rel2 <= 1e-10
