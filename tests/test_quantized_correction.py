@@ -3,7 +3,8 @@ correction's precision): once the finest correction v is rounded to a
 multiple of q = 2^(E - qb) of a level-wide bound 2^E >= max|v| (qb = 21 for
 the 5-point Laplacian, 20 for the 7-point one), the neighbour sum and
 L v = sum - 2d c are exact in FP32, so r -= L v can be carried without a
-float-float Laplacian.  Checked here with IEEE FP32 arithmetic emulated by
+float-float Laplacian; and the float-float update hi + lo <- hi + lo - s2 L v
+keeps about 48 bits.  Checked here with IEEE FP32 arithmetic emulated by
 numpy (each float32 operation correctly rounded; the fused multiply-add of
 the centre term rounded once) against exact FP64 values.  No GPU."""
 
@@ -90,3 +91,49 @@ def test_headroom_bound(dim, qb):
     """|sum| + 2d |c| <= 4d 2^E stays within 2^24 quanta: the bound that makes
     every intermediate an integer multiple of q representable in FP32."""
     assert 4 * dim * 2.0 ** qb <= 2.0**24
+
+
+def two_sum32(a, b):
+    """Knuth's two-sum in FP32: s = fl(a + b) and the exact error e, a + b = s + e."""
+    s = a + b
+    bv = s - a
+    av = s - bv
+    return s, (a - av) + (b - bv)
+
+
+def ff_sub(hi, lo, lap, s2):
+    """(hi + lo) - s2 * lap as a float-float pair; lap exact, s2 a power of two."""
+    s, e = two_sum32(hi, -(s2 * lap))
+    return two_sum32(s, lo + e)
+
+
+def test_two_sum_is_exact():
+    rng = np.random.default_rng(14)
+    a = (rng.uniform(-1, 1, 50000) * 2.0 ** rng.integers(-40, 40, 50000)).astype(F32)
+    b = (rng.uniform(-1, 1, 50000) * 2.0 ** rng.integers(-40, 40, 50000)).astype(F32)
+    s, e = two_sum32(a, b)
+    lhs = a.astype(np.float64) + b.astype(np.float64)  # exact in float64 for these exponent ranges
+    assert np.array_equal(s.astype(np.float64) + e.astype(np.float64), lhs)
+
+
+def test_float_float_update_error():
+    """The carried residual's update r <- r - s2 L v keeps about 48 bits: the
+    only rounding is that of lo + e, below 2^-47 of |hi| + |s2 L v|."""
+    rng = np.random.default_rng(15)
+    size = 50000
+    hi = (rng.uniform(-1, 1, size) * 2.0 ** rng.integers(-20, 0, size)).astype(F32)
+    lo = (hi.astype(np.float64) * rng.uniform(-1, 1, size) * 2.0**-25).astype(F32)
+    # a correction of size h^2 |r| (h = 2^-12, the 4095^2 grid) rounded to
+    # its quantum; s2 = 1/h^2 = 2^24 is a power of two, so s2 * lap is exact
+    b = 2.0**-24
+    M, E = magic(b, 21)
+    lap = ((quant(rng.uniform(-b, b, size), M) + quant(rng.uniform(-b, b, size), M))
+           - F32(2.0) * quant(rng.uniform(-b, b, size), M))
+    s2 = F32(2.0**24)
+    nh, nl = ff_sub(hi, lo, lap, s2)
+    exact = hi.astype(np.float64) + lo.astype(np.float64) - float(s2) * lap.astype(np.float64)
+    err = np.abs(nh.astype(np.float64) + nl.astype(np.float64) - exact)
+    scale = np.abs(hi.astype(np.float64)) + np.abs(float(s2) * lap.astype(np.float64))
+    assert np.all(err <= 2.0**-47 * scale)
+    # the pair stays normalised: lo is below half an ulp of hi
+    assert np.all(np.abs(nl) <= np.spacing(np.abs(nh)) / 2 + 0.0)
