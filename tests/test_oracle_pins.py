@@ -530,3 +530,80 @@ def test_extra_sweeps_only_for_the_2d_diagonal_hierarchy():
         O.vcycle(rng_grid(3, 7, 18), O.grid(3, 7), omega=[1.11, 1.42, 1.08, 0.99], extra=1)
     with pytest.raises(ValueError):
         O.vcycle(rng_grid(2, 7, 18), O.grid(2, 7), hier=O.USUAL, omega=[1.121], extra=1)
+
+
+# --------------------------------------------------------------------------
+# an exact eigenspace of the diagonal V-cycle, derived by hand
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,n,omega", [
+    (2, 15, [1.052]), (2, 31, [1.3]), (2, 63, [1.0]), (2, 31, [0.8]),
+    (3, 7, [1.11, 1.42, 1.08, 0.99]), (3, 15, [0.9, 1.2, 1.3, 1.25]), (3, 15, [1.0, 1.0, 1.0, 1.0]),
+])
+def test_odd_point_errors_are_scaled_by_one_minus_p(dim, n, omega):
+    """Let the error e = u - u* vanish except on the finest grid's points with
+    an odd index sum (the points the final half-sweep updates first).  With
+    f = 0 the residual is r = -L e: at such a point r = 2d e / h^2, at an
+    even point r = -(sum of the odd neighbours' e) / h^2.  The first
+    restriction weights a point 2d times as much as each axis neighbour
+    (Eq. Erest2r, Eq. Erred), so the restricted residual is
+    (2d r_even + sum r_odd) / (4d) = 0 everywhere, and every coarse correction
+    vanishes.  The final sweep then sets, at odd points,
+    v = (0 - p h^2 r) / (2d) = -p e (the coarse neighbours' v being zero),
+    and at even points v = (sum of the new odd v - p h^2 r) / (2d)
+    = (-p sum e + p sum e) / (2d) = 0.  So one cycle maps e to
+    (1 - p) e, p the finest weight (p_g in 3D), whatever the other weights.
+    A wrong restriction weight, sign, sweep order or place of p breaks it."""
+    rng = np.random.default_rng(19)
+    idx = np.indices((n + 2,) * dim)
+    inner = np.zeros((n + 2,) * dim, dtype=bool)
+    inner[(slice(1, -1),) * dim] = True
+    e = np.where(inner & (idx.sum(0) % 2 == 1), rng.standard_normal((n + 2,) * dim), 0.0)
+    u = O.vcycle(O.grid(dim, n), e.copy(), omega=omega)
+    p = omega[-1]
+    np.testing.assert_allclose(u, (1.0 - p) * e, rtol=0, atol=1e-14 * np.abs(e).max())
+
+
+def _cycle_matrix(dim, n, hier, order, omega):
+    """The V-cycle's error propagation (f = 0) assembled column by column."""
+    N, sl = n ** dim, (slice(1, -1),) * dim
+    A = np.zeros((N, N))
+    for j in range(N):
+        u = O.grid(dim, n)
+        x = np.zeros(N)
+        x[j] = 1.0
+        u[sl] = x.reshape((n,) * dim)
+        O.vcycle(O.grid(dim, n), u, hier=hier, order=order, omega=omega)
+        A[:, j] = u[sl].ravel()
+    return A
+
+
+@pytest.mark.parametrize("dim,n,hier,order,omega", [
+    (2, 7, O.DIAG, 2, [1.0]), (2, 15, O.DIAG, 2, [1.052]), (2, 15, O.USUAL, 2, [1.0]), (2, 15, O.DIAG, 4, [1.2]),
+    (3, 7, O.DIAG, 2, [1.11, 1.42, 1.08, 0.99]), (3, 7, O.USUAL, 2, [1.3]), (3, 7, O.DIAG, 4, [0.91, 0.80, 0.70, 1.77]),
+])
+def test_convergence_factor_estimators_agree(dim, n, hier, order, omega):
+    """The spectral radius of the explicitly assembled cycle matrix (dense
+    eigenvalues), the Arnoldi estimate used against the paper's tables, and
+    the power iteration of the GPU's estimator (geometric mean of the norm
+    ratios of cycles 41-60 from a seeded random start) agree."""
+    A = _cycle_matrix(dim, n, hier, order, omega)
+    lam = float(np.abs(np.linalg.eigvals(A)).max())
+    assert spectral_radius(dim, n, hier, order, omega) == pytest.approx(lam, rel=1e-8)
+    sl = (slice(1, -1),) * dim
+    u = O.grid(dim, n)
+    u[sl] = np.random.default_rng(5).standard_normal((n,) * dim)
+    logs = []
+    for _ in range(60):
+        a = np.linalg.norm(u[sl])
+        O.vcycle(O.grid(dim, n), u, hier=hier, order=order, omega=omega)
+        b = np.linalg.norm(u[sl])
+        logs.append(math.log(b / a))
+        u[sl] /= b
+    assert math.exp(np.mean(logs[-20:])) == pytest.approx(lam, rel=0.02)
+    if hier == O.DIAG and order == 2:
+        # 1 - p is an eigenvalue (odd-point errors), so |1 - p| bounds the factor
+        # from below; at the paper's optimum p = 1.052 (Table 1) it is the factor
+        assert lam >= abs(1.0 - omega[-1]) - 1e-12
+        if omega == [1.052]:
+            assert lam == pytest.approx(0.052, rel=1e-9)
