@@ -129,3 +129,23 @@ def test_misaligned_grid_pointers_are_refused_before_any_launch():
         # the same context still solves
         _, it, rel2, _ = c.solve(f, u, rtol=1e-10, max_cycles=40)
         assert rel2 <= 1e-10
+
+
+@pytest.mark.parametrize("dim,n,omega", [(2, 63, (1.052,)), (2, 255, (1.3,)), (3, 15, (1.11, 1.42, 1.08, 0.99)),
+                                         (3, 31, (0.9, 1.2, 1.3, 1.25))])
+def test_odd_point_errors_are_scaled_by_one_minus_p(dim, n, omega):
+    """An error supported on the finest grid's odd-index-sum points has a zero
+    restricted residual (the first restriction weights a point 2d times each
+    axis neighbour), so every coarse correction vanishes and the final
+    half-sweeps return exactly (1 - p) e, p the finest weight (p_g in 3D).
+    The FP64 cycle on the GPU meets this to rounding."""
+    rng = np.random.default_rng(19)
+    idx = np.indices((n + 2,) * dim)
+    inner = np.zeros((n + 2,) * dim, dtype=bool)
+    inner[(slice(1, -1),) * dim] = True
+    e = np.where(inner & (idx.sum(0) % 2 == 1), rng.standard_normal((n + 2,) * dim), 0.0)
+    with Context(dim, n, precision="fp64", omega=omega) as c:
+        u = torch.from_numpy(e.copy()).to(DEV)
+        c.vcycle(torch.zeros_like(u), u)
+        got = u.cpu().numpy()
+    assert np.abs(got - (1.0 - omega[-1]) * e).max() <= 1e-12 * np.abs(e).max()
