@@ -41,3 +41,19 @@ def test_reference_arm_other_ranks_exit_quietly():
     p = _run({"RANK": "1", "WORLD_SIZE": "2"}, "--steps", "1", "--warmup", "3")
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_traffic_counters_belong_to_the_current_kernels():
+    """The DRAM traffic bench.py reports for the dominant kernels was captured
+    on the kernel source it names by hash; a kernel edited since reports no
+    traffic (null) until it is captured again.  Both are current."""
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for t in (bench.TRAFFIC, bench.TRAFFIC3):
+        assert bench.kernel_source_sha1(t["kernel"], t["file"]) == t["source_sha1"], t["kernel"]
+        assert bench.measured_traffic(t) == t["bytes"] > 0
+    stale = dict(bench.TRAFFIC, source_sha1="0" * 40)
+    assert bench.measured_traffic(stale) is None
