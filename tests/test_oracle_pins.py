@@ -607,3 +607,58 @@ def test_convergence_factor_estimators_agree(dim, n, hier, order, omega):
         assert lam >= abs(1.0 - omega[-1]) - 1e-12
         if omega == [1.052]:
             assert lam == pytest.approx(0.052, rel=1e-9)
+
+
+def _diag_sum(e, dim):
+    """Sum of the 2^dim diagonal neighbours (+-1 in every index); e vanishes
+    on the ring, so the wrap-around of np.roll only brings in zeros."""
+    out = np.zeros_like(e)
+    for s in np.ndindex(*(2,) * dim):
+        out += np.roll(e, tuple(1 - 2 * b for b in s), axis=tuple(range(dim)))
+    return out
+
+
+def test_red_level_errors_on_odd_points_2d():
+    """The same eigenspace one level down (Eq. Erest2b, Eq. Eajacr/Eajacb): on
+    the red level of a pair (points i + j even of its green grid, spacing
+    sqrt(2) h) take e on the red points with i, j odd.  With
+    L e = (sum of the 4 diagonal neighbours - 4 e) / (2 h^2), r = -L e is
+    2 e / h^2 there and -(sum of e) / (2 h^2) at the blue points (i, j even),
+    so the restriction (4 r_blue + sum r) / 8 vanishes; from v_blue = 0 the
+    half-sweeps give v = -2 p h^2 r / 4 = -p e at the odd points and
+    (-p sum e + 2 p h^2 sum e / (2 h^2)) / 4 = 0 at the blue ones."""
+    n, p = 31, 1.3
+    h = 1.0 / (n + 1)
+    j, i = np.indices((n + 2, n + 2))
+    inner = np.zeros((n + 2, n + 2), dtype=bool)
+    inner[1:-1, 1:-1] = True
+    red = inner & ((i + j) % 2 == 0)
+    e = np.where(inner & (i % 2 == 1) & (j % 2 == 1), np.random.default_rng(3).standard_normal((n + 2, n + 2)), 0.0)
+    r = np.where(red, -(_diag_sum(e, 2) - 4 * e) / (2 * h * h), 0.0)
+    rb = O.restrict2d_r2b(r)
+    assert np.abs(rb).max() <= 1e-14 * np.abs(r).max()
+    v = O.prolong2d_b2r(np.zeros_like(rb), r, h, p)
+    np.testing.assert_allclose(np.where(red, v, 0.0), -p * e, rtol=0, atol=1e-14 * np.abs(e).max())
+
+
+def test_magenta_level_errors_on_centres_3d():
+    """The magenta-blue step (Eq. Erblu, Eq. Emprolm/Emprolb): on the magenta
+    level (cube corners, all indices even, and centres, all odd) take e on
+    the centres.  With L e = (sum of the 8 diagonal neighbours - 8 e) / (4 h^2)
+    (the operator whose Jacobi step has the coefficient 4 p_m h^2 / 8),
+    r = 2 e / h^2 at the centres and -(sum of e) / (4 h^2) at the corners, so
+    the restriction to the blue corners vanishes; from v_blue = 0 the centres
+    get v = -4 p_m h^2 r / 8 = -p_m e and the corners v = 0."""
+    n, pm = 15, 1.11
+    h = 1.0 / (n + 1)
+    k, j, i = np.indices((n + 2,) * 3)
+    inner = np.zeros((n + 2,) * 3, dtype=bool)
+    inner[1:-1, 1:-1, 1:-1] = True
+    centre = inner & (i % 2 == 1) & (j % 2 == 1) & (k % 2 == 1)
+    mag = centre | (inner & (i % 2 == 0) & (j % 2 == 0) & (k % 2 == 0))
+    e = np.where(centre, np.random.default_rng(4).standard_normal((n + 2,) * 3), 0.0)
+    r = np.where(mag, -(_diag_sum(e, 3) - 8 * e) / (4 * h * h), 0.0)
+    rb = O.restrict3d_m2b(r)
+    assert np.abs(rb).max() <= 1e-14 * np.abs(r).max()
+    v = O.prolong3d_b2m(np.zeros_like(rb), r, h, pm)
+    np.testing.assert_allclose(np.where(mag, v, 0.0), -pm * e, rtol=0, atol=1e-14 * np.abs(e).max())
