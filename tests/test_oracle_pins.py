@@ -662,3 +662,19 @@ def test_magenta_level_errors_on_centres_3d():
     assert np.abs(rb).max() <= 1e-14 * np.abs(r).max()
     v = O.prolong3d_b2m(np.zeros_like(rb), r, h, pm)
     np.testing.assert_allclose(np.where(mag, v, 0.0), -pm * e, rtol=0, atol=1e-14 * np.abs(e).max())
+
+
+@pytest.mark.parametrize("dim,n,hier,order,omega", [
+    (2, 31, O.DIAG, 2, [1.052]), (2, 31, O.USUAL, 2, [1.121]), (2, 31, O.DIAG, 4, [1.2]),
+    (3, 15, O.DIAG, 2, [1.11, 1.42, 1.08, 0.99]), (3, 15, O.USUAL, 4, [1.7]),
+])
+def test_vcycle_is_linear_in_f_and_u(dim, n, hier, order, omega):
+    """Every step of the cycle is linear in (f, u): no hidden offset, clamp or
+    data-dependent branch."""
+    f1, f2 = rng_grid(dim, n, 40, ring=True), rng_grid(dim, n, 41, ring=True)
+    u1, u2 = rng_grid(dim, n, 42), rng_grid(dim, n, 43)
+    a, b = 0.75, -2.5
+    lhs = O.vcycle(a * f1 + b * f2, a * u1 + b * u2, hier=hier, order=order, omega=omega)
+    r1 = O.vcycle(f1, u1.copy(), hier=hier, order=order, omega=omega)
+    r2 = O.vcycle(f2, u2.copy(), hier=hier, order=order, omega=omega)
+    np.testing.assert_allclose(lhs, a * r1 + b * r2, rtol=0, atol=1e-12 * np.abs(lhs).max())
