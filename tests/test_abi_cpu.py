@@ -133,3 +133,18 @@ def test_every_context_kernel_waits_before_touching_memory():
                 assert allowed.match(t), (kern, t)
                 assert "[" not in t.split("=")[-1] or "__shared__" in t, (kern, t)
     assert seen >= 55
+
+
+def test_every_environment_setting_is_documented_in_the_header():
+    """Each environment variable the library reads is described where the
+    ABI is: in include/diagmg.h."""
+    import glob
+    import re
+    csrc = os.path.join(os.path.dirname(N.__file__), "csrc")
+    read = set()
+    for path in glob.glob(os.path.join(csrc, "*.cu*")):
+        read |= set(re.findall(r'getenv\("([A-Z_0-9]+)"\)', open(path).read()))
+    assert read, "no settings found"
+    header = open(os.path.join(os.path.dirname(os.path.dirname(N.__file__)), "include", "diagmg.h")).read()
+    for name in sorted(read):
+        assert name in header, name
