@@ -22,11 +22,15 @@ solution of Poisson's equation using diagonally oriented grids"):
 * ``coarse_solve``        exact solve of the coarsest axis grid (the paper is silent)
 * ``vcycle``, ``solve``   the V-cycle of Sections 2.3 and 3.3
 
-Pins (tests/test_oracle_*.py): closed-form stencil weights and the 17-point
+Pins (tests/test_oracle_pins.py): closed-form stencil weights and the 17-point
 composite restriction, exactness of every Jacobi sweep on quadratics, the
 fixed point against a Kronecker-assembled direct solve, O(h^2)/O(h^4)
 discretisation error, operator symmetry, the paper's flop counts rebuilt from
-level point counts, and the convergence factors of the paper's tables.
+level point counts, the convergence factors of the paper's tables, an
+eigenspace derived by hand (errors on the odd-index-sum points scaled by
+exactly 1 - p; the same one level down on the 2D red and 3D magenta
+levels), the spectral radius of the assembled cycle matrix, and linearity
+of the cycle in (f, u).
 """
 
 from __future__ import annotations
