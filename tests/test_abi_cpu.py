@@ -148,3 +148,19 @@ def test_every_environment_setting_is_documented_in_the_header():
     header = open(os.path.join(os.path.dirname(os.path.dirname(N.__file__)), "include", "diagmg.h")).read()
     for name in sorted(read):
         assert name in header, name
+
+
+def test_python_api_surface():
+    """The calls the package documents exist (no GPU needed to look them up)."""
+    import inspect
+
+    import paper_math_9907190_gb300 as P
+    for name in ("Batch", "Context", "PoissonSolve", "default_omega", "solve"):
+        assert hasattr(P, name), name
+    for m in ("solve", "vcycle", "residual", "solve_two_stage", "set_omega", "set_sweeps", "rho", "tune",
+              "tune_info", "restrict", "coarse_solve", "prolong", "level_get", "level_set", "new_grid", "close"):
+        assert callable(getattr(P.Context, m)), m
+    for m in ("solve", "tune", "close"):
+        assert callable(getattr(P.Batch, m)), m
+    assert list(inspect.signature(P.Context.__init__).parameters)[1:3] == ["dim", "n"]
+    assert P.default_omega(2, "diag", 2) == (1.052,)
