@@ -69,6 +69,43 @@ TRAFFIC3 = {"kernel": "k_green_ff_3d", "file": "mg_fast3d.cuh", "bytes": 326.936
             "source_sha1": "d3cc2abc3f1704b3286d2f0682dc9c363a98f5bf"}
 
 
+# Whole-solve traffic model of the mixed path (the algorithmic bytes the
+# method must move per finest unknown): the outer FP64 step -- u and f read,
+# u written, the FP32 residual and correction -- about 40 B, and every inner
+# FP32 V-cycle about 36 B (finest level two passes, coarse levels ~N points
+# of r and v written and read).  A solve of c cycles: 40 + 36 c bytes.
+CYCLE_MODEL = {"outer_bytes": 40, "per_cycle_bytes": 36}
+# The paper's flop count of one diagonal V-cycle per finest unknown (2D,
+# second order; Section 2.3), used for the FP64 path's arithmetic roofline.
+PAPER_FLOPS_2D = 25.0
+
+
+def cycle_roofline(n_unknowns, cycles, ms, peak):
+    bpu = CYCLE_MODEL["outer_bytes"] + CYCLE_MODEL["per_cycle_bytes"] * cycles
+    ach = bpu * n_unknowns / (ms * 1e-3) / 1e9
+    return {"bytes_per_unknown": bpu, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "model": "40 B (outer FP64 step) + 36 B x cycles (FP32 V-cycles) per finest unknown, "
+                     "over the whole solve time"}
+
+
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def read_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -128,6 +165,28 @@ def extra_measurements(dev, stream):
         u = c.new_grid()
         ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u.zero_(), rtol=RTOL, max_cycles=60), 5, stream)
         out["square4095_fp64"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc, "relres": rel}
+        # the FP64 path's arithmetic roofline: its finest residual kernel
+        # (k_res0_2d: 5 FP64 operations per point, probed live inside the
+        # solve) and the whole solve at the paper's 25 flops per unknown and
+        # cycle, against this device's measured FP64 pipe rate
+        rate = c.fp64_rate()
+        c.probe_set(0)
+        for _ in range(3):
+            c.solve(f, u.zero_(), rtol=RTOL, max_cycles=60)
+        k, pms = c.probe_read()
+        c.probe_set(-1)
+        avg = pms / max(k, 1)
+        ops = 5 * N_SIDE**2 / (avg * 1e-3)
+        peak_hbm = read_peaks().get("hbm_gbs", 6800.0)
+        flops = PAPER_FLOPS_2D * N_SIDE**2 * cyc / (ms * 1e-3)
+        out["square4095_fp64"]["roofline_fp64"] = {
+            "bound": "fp64", "kernel": "k_res0_2d<double>: finest residual r = f - L u, FP64 (5 FP64 ops per point)",
+            "avg_launch_ms": avg, "launches_probed": k, "achieved": ops, "peak": rate, "unit": "FP64 ops/s",
+            "frac": ops / rate, "hbm_frac": 24 * N_SIDE**2 / (avg * 1e-3) / 1e9 / peak_hbm,
+            "peak_source": "measured on this device by mg_fp64_rate (independent FP64 FMA chains on every SM; "
+                           "an FMA counts one operation)",
+            "solve": {"paper_flops_per_unknown_cycle": PAPER_FLOPS_2D, "achieved_flop_s": flops,
+                      "peak_flop_s": 2 * rate, "frac": flops / (2 * rate)}}
     for prec in ("mixed", "fp64"):  # the conventional 2^-l V-cycle the paper compares with
         with Context(2, N_SIDE, hierarchy="usual", precision=prec) as c:
             u = c.new_grid()
@@ -177,6 +236,9 @@ def extra_measurements(dev, stream):
             out[f"cube255_{prec}"] = {"unknowns_per_s": 255**3 / (ms * 1e-3), "ms": ms, "cycles": cyc, "relres": rel,
                                       "workload": "3D unit cube 255^3, f = -6 pi^2 sin sin sin(2 pi z) + N(0,1e-6), "
                                                   "diagonal V-cycle (1.11, 1.42, 1.08, 0.99)"}
+            if prec == "mixed":
+                out["cube255_mixed"]["cycle_roofline"] = cycle_roofline(255**3, cyc, ms,
+                                                                         read_peaks().get("hbm_gbs", 6800.0))
             if prec == "mixed":  # the dominant 3D kernel, probed inside the solve as the headline's
                 c.probe_set(PROBE["family"])
                 for _ in range(3):
@@ -280,51 +342,60 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())}
 
 
-def oracle_cpu_baseline(f, u_gpu=None, max_seconds=60.0):
-    """The oracle as it stands (single-threaded C, FP64) solving the full
-    workload from u = 0 to 1e-10; returns the baseline dict and its solution."""
+def oracle_cpu_baseline(f):
+    """The oracle as it stands (C, FP64) solving the full workload from u = 0
+    to 1e-10, on all host cores (its per-point loops under OpenMP; sums and
+    the coarsest solve serial, so the result does not depend on the thread
+    count) and on one core.  Returns the baseline dict and its solution."""
     import oracle as O
-    t0 = time.perf_counter()
-    u, cycles, rel, hist = O.solve(f, omega=[1.052], rtol=RTOL, max_cycles=40)
-    dt = time.perf_counter() - t0
-    out = {"value": N_SIDE**2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"one full oracle solve of the benchmark workload ({cycles} FP64 V-cycles to "
-                     f"relres {rel:.2e}, {dt:.1f} s on 1 host core)"}
+    nproc = os.cpu_count() or 1
+    legs = {}
+    u = None
+    for threads in (nproc, 1):
+        used = O.set_threads(threads)
+        t0 = time.perf_counter()
+        u, cycles, rel, _ = O.solve(f, omega=[1.052], rtol=RTOL, max_cycles=40)
+        dt = time.perf_counter() - t0
+        legs[threads] = {"value": N_SIDE**2 / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": f"one full oracle solve of the benchmark workload ({cycles} FP64 V-cycles to "
+                                   f"relres {rel:.2e}, {dt:.2f} s on {used} host thread(s))"}
+    O.set_threads(1)
+    out = dict(legs[nproc])
+    out["nproc"] = nproc
+    out["cpu_model"] = cpu_model()
+    out["single_core"] = legs[1]
     return out, u
 
 
 def run_reference(args):
-    """Reference arm: the CPU FP64 oracle, one V-cycle per step, on rank 0."""
+    """Reference arm: the CPU FP64 oracle on all host cores, rank 0 only; a
+    step is one full oracle solve of the workload from u = 0 to 1e-10."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle as O
     from paper_math_9907190_gb300 import inputs as I
     f = I.square_large(N_SIDE)
-    u = O.grid(2, N_SIDE)
-    f0 = math.sqrt(O.norm2_interior(O.residual(f, u)))
-    times, rels = [], []
+    nproc = os.cpu_count() or 1
+    used = O.set_threads(nproc)
+    times, cycles, rel = [], 0, 0.0
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        O.vcycle(f, u, omega=[1.052])
+        _, cycles, rel, _ = O.solve(f, omega=[1.052], rtol=RTOL, max_cycles=40)
         dt = time.perf_counter() - t0
-        rels.append(math.sqrt(O.norm2_interior(O.residual(f, u))) / f0)
         if s >= args.warmup:
             times.append(dt)
-    t_cycle = statistics.mean(times)
-    hit = next((i + 1 for i, r in enumerate(rels) if r <= RTOL), None)
-    if hit is None:  # extrapolate from the measured contraction of the last cycles
-        rho = (rels[-1] / rels[max(0, len(rels) - 4)]) ** (1.0 / min(3, len(rels) - 1))
-        hit = len(rels) + math.ceil(math.log(RTOL / rels[-1]) / math.log(rho))
-    value = N_SIDE**2 / (t_cycle * hit)
+    t_step = statistics.mean(times)
+    value = N_SIDE**2 / t_step
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_cycle * 1e3, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD.replace("mixed FP64/FP32", "FP64 CPU oracle"),
-                       "step": "one oracle V-cycle", "cycles_to_rtol": hit},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.warmup + args.steps} oracle V-cycles of the full workload; "
-                                       f"{hit} cycles reach 1e-10"},
+                       "step": "one full oracle solve", "cycles_to_rtol": cycles, "relres": rel},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "nproc": nproc, "cpu_model": cpu_model(),
+                             "kind": "oracle",
+                             "sample": f"{args.warmup + args.steps} full oracle solves of the workload "
+                                       f"({cycles} V-cycles each to 1e-10) on {used} host thread(s)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -454,7 +525,23 @@ def main():
 
     e2e_run(2)
     barrier()
-    e2e_ms = D.max_over_ranks(e2e_run(args.steps), dev)
+    e2e_pipe_ms = D.max_over_ranks(e2e_run(args.steps), dev)
+    barrier()
+
+    # end to end through the C ABI with HOST buffers (mg_solve_host): every
+    # step copies f from pinned host memory to the device, solves from u = 0
+    # and copies u back to pinned host memory, one call after the other (no
+    # overlap between steps); wall-clock time per call
+    u_host = torch.empty_like(f_pin).pin_memory()
+    for _ in range(2):
+        ctx.solve_host(f_pin, u_host, rtol=RTOL, max_cycles=60)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, e2e_cyc, e2e_rel = ctx.solve_host(f_pin, u_host, rtol=RTOL, max_cycles=60)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_ms = D.max_over_ranks(e2e_ms, dev)
+    e2e_ok = bool(np.array_equal(u_host.numpy(), u.cpu().numpy()))
     barrier()
 
     # live probe of the dominant kernel inside the same solve: every launch of
@@ -476,6 +563,8 @@ def main():
                 "frac": achieved / hbm_peak, "traffic": traffic, "algorithmic_bytes": bytes_,
                 "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback",
                 "avg_launch_ms": avg_ms, "launches_probed": nprobe,
+                "cycle_frac": cycle_roofline(N, cycles[-1], ms_max, hbm_peak)["frac"],
+                "cycle": cycle_roofline(N, cycles[-1], ms_max, hbm_peak),
                 "fp64_pipe": {"ops_per_point": PROBE["fp64_pipe_ops_per_point"], "achieved_ops_s": pipe,
                               "peak_ops_s": FP64_PIPE_OPS_PEAK, "frac": pipe / FP64_PIPE_OPS_PEAK,
                               "peak_note": "152 SMs x 2 FP64 ops/clk x 2.07 GHz (nominal, derived)"}}
@@ -490,10 +579,14 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),
             "e2e": {"value": world * N / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
-                    "h2d_bytes_per_step": int(f_pin.numel() * 8), "d2h_bytes_per_step": int(u_pins[0].numel() * 8),
-                    "pipelined": "copies on a copy stream: step k+1's input and step k-1's output move "
-                                 "during step k's solve; the first input and the last output are inside the "
-                                 "timed region"},
+                    "h2d_bytes_per_step": int(f_pin.numel() * 8), "d2h_bytes_per_step": int(u_host.numel() * 8),
+                    "api": "mg_solve_host (C ABI): f from pinned host memory, solve from u = 0, u back to pinned "
+                           "host memory; one call per step, copies not overlapped, wall-clock time",
+                    "cycles": e2e_cyc, "relres": e2e_rel, "same_u_as_device_solve": e2e_ok,
+                    "pipelined": {"value": world * N / (e2e_pipe_ms * 1e-3), "ms_per_step": e2e_pipe_ms,
+                                  "how": "Python API with torch copies on a copy stream: step k+1's input and "
+                                         "step k-1's output move during step k's solve; the first input and the "
+                                         "last output are inside the timed region"}},
             "gpu_launches": int(launches),
             "roofline": roofline}
 
@@ -510,6 +603,7 @@ def main():
         line["cpu_baseline"] = cb
         ug = u.cpu().numpy()
         line["config"]["rel_err_vs_oracle"] = float(np.linalg.norm(ug - u_orc) / np.linalg.norm(u_orc))
+        line["config"]["max_pointwise_err_vs_oracle"] = float(np.abs(ug - u_orc).max() / np.abs(u_orc).max())
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

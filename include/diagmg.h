@@ -20,7 +20,8 @@
  *     boundary); a null or misaligned one gives MG_EINVAL.  The library never
  *     keeps a caller pointer after a call returns.  All workspace (level
  *     buffers, norms, control words) is allocated by mg_create and freed by
- *     mg_destroy; no other call allocates device memory.
+ *     mg_destroy; no other call allocates device memory, except the first
+ *     mg_solve_host of a context (its device copies of f and u).
  *   - Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
  *     default stream).  Calls are stream-ordered; a call that returns a value
  *     to a host pointer synchronises that stream before returning.
@@ -54,7 +55,7 @@ typedef enum {
     MG_ECUDA = -3,      /* CUDA runtime error (message: mg_last_error) */
     MG_ENOCONV = -4,    /* max_cycles reached above rtol */
     MG_EDIVERGED = -5,  /* residual became non-finite or grew 1e3-fold */
-    MG_ETIMEOUT = -6    /* a bounded device wait gave up (batched launch) */
+    MG_ETIMEOUT = -6    /* reserved: no call returns it (no kernel waits on another block) */
 } mg_status;
 
 enum { MG_DIAG = 0, MG_USUAL = 1 };   /* hierarchy */
@@ -107,8 +108,9 @@ mg_status mg_level_info(const mg_ctx *ctx, int level, int *side, int *kind);
  * Eq. Efos4 (3D) (order 4).  h must equal 1/(n+1).  The result is stored in
  * the context as the level-0 residual (in the context's level precision) and,
  * when r is not NULL, also written in FP64 to r (caller pitch, interior points
- * only).  norm2 (host, nullable) receives sum(r^2) over interior points; the
- * call then synchronises `stream`. */
+ * only; r's extent must not overlap f's or u's, else MG_EINVAL).  norm2
+ * (host, nullable) receives sum(r^2) over interior points; the call then
+ * synchronises `stream`. */
 mg_status mg_residual(mg_ctx *ctx, const double *f, const double *u, double h, int order, double *r,
                       double *norm2, void *stream);
 
@@ -166,6 +168,20 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *u, void *stream);
  * Returns MG_OK, MG_ENOCONV or MG_EDIVERGED (u holds the last iterate). */
 mg_status mg_solve(mg_ctx *ctx, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
                    double *relres_out, double *history, void *stream);
+
+/* mg_solve with HOST arrays, for callers whose data live in host memory:
+ * f_host (the right-hand side), u0_host (the warm start, zero ring; NULL:
+ * start from u = 0) and u_host (receives the result; may equal u0_host) are
+ * full grids in the caller layout (pitch).  The call copies f and the warm
+ * start to device copies owned by the context, runs mg_solve there and copies
+ * u back, all on `stream`, and returns once u_host holds the result.  The
+ * copies overlap nothing else in the call; for full copy bandwidth the host
+ * arrays should be page-locked (cudaHostAlloc / cudaHostRegister).  The first
+ * call allocates the two device copies (MG_ENOMEM if that fails); later calls
+ * allocate nothing.  Single-problem contexts only; u_host must not overlap
+ * f_host.  Returns what mg_solve returns. */
+mg_status mg_solve_host(mg_ctx *ctx, const double *f_host, const double *u0_host, double *u_host, double rtol,
+                        int max_cycles, int *cycles_out, double *relres_out, void *stream);
 
 /* Replace the context's over-relaxation weights (same meaning as
  * mg_desc.omega, host, 4 entries). */
@@ -232,6 +248,11 @@ mg_status mg_batch_destroy(mg_batch *batch);
 mg_status mg_solve_batched(mg_batch *batch, const double *const *f, double *const *u, double rtol, int max_cycles,
                            int *cycles_out, double *relres_out, void *stream);
 mg_status mg_batch_launch_count(const mg_batch *batch, long long *launches);
+/* Per-problem outcome of the batch's last mg_solve_batched: status[p] (host,
+ * nprob entries) is MG_OK, MG_ENOCONV (max_cycles reached above rtol) or
+ * MG_EDIVERGED (its residual became non-finite, grew 1e3-fold, or its
+ * right-hand side carried a NaN).  MG_EINVAL before the first solve. */
+mg_status mg_batch_status(const mg_batch *batch, int *status);
 
 /* Autotuning (no paper counterpart).  mg_tune times, on this context's own
  * buffers with the caller's f and u, the size cut-off below which whole
@@ -268,17 +289,24 @@ mg_status mg_batch_tune(mg_batch *batch, const double *const *f, double *const *
 mg_status mg_launch_count(const mg_ctx *ctx, long long *launches);
 mg_status mg_probe_set(mg_ctx *ctx, int family);
 mg_status mg_probe_read(mg_ctx *ctx, long long *launches, double *ms, void *stream);
+/* Measured FP64 pipe rate of this device (the roofline of the FP64 path's
+ * arithmetic): a kernel of independent FP64 FMA chains on every SM, timed with
+ * CUDA events on `stream`, best of three launches after a warm-up; *ops_per_s
+ * (host) counts one FMA as one operation.  Synchronous. */
+mg_status mg_fp64_rate(mg_ctx *ctx, double *ops_per_s, void *stream);
 
 /* Residual and squared norm without any device allocation (the paper has no
  * counterpart; this serves callers that may not allocate device memory: code
  * inside another framework's allocator or fixed memory budget, latency-bound
  * loops where cudaMalloc/cudaFree could stall the device, plug-ins that keep
  * no workspace between calls).  No context is needed.
- *   r = f - L_h u exactly as mg_residual computes it for the same order
- *   (5/7-point, or Eq. Efos2 / Eq. Efos4 with order 4); h must be 1/(n+1).
+ *   r = f - L_h u exactly as mg_residual computes it for the same order (the
+ *   5/7-point Laplacian, or with order 4 the compact fourth-order 9-point
+ *   (2D) / 19-point (3D) forms that mg_residual uses); h must be 1/(n+1).
  *   f, u      caller device arrays, full grid (n+2)^dim, row pitch `pitch`
  *   r         caller device array (same layout) receiving r on the interior
- *             points, or NULL
+ *             points, or NULL; its extent must not overlap f's or u's
+ *             (MG_EINVAL)
  *   norm2     caller DEVICE pointer to one double receiving sum(r^2) over the
  *             interior, or NULL; written in stream order (no host sync)
  * Scratch: one partial sum per 256-thread block lives in a static device
@@ -290,8 +318,9 @@ mg_status mg_probe_read(mg_ctx *ctx, long long *launches, double *ms, void *stre
  * on one device share the array, so calls that may overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * The first call on each device looks up the array's device address (with
- * that device current) and keeps it; make that first call before any stream
- * capture.  Allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * that device current) and keeps it for the life of the process; make that
+ * first call before any stream capture, and do not reset the device
+ * (cudaDeviceReset) after it.  Allocates nothing: no cudaMalloc, cudaFree or allocating library
  * routine is called. */
 mg_status mg_residual_noalloc(int dim, int n, int pitch, double h, int order, const double *f, const double *u,
                               double *r, double *norm2, void *stream);

@@ -52,12 +52,13 @@ DIAG, USUAL = 0, 1
 
 
 def build(force: bool = False) -> str:
-    """Compile mg_oracle.c with gcc (no FMA contraction) and return the .so path."""
+    """Compile mg_oracle.c with gcc (no FMA contraction; OpenMP when the
+    compiler has it) and return the .so path."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
-             _SRC, "-o", tmp, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
+        if subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], capture_output=True).returncode != 0:
+            subprocess.check_call(base + [_SRC, "-o", tmp, "-lm"])  # no OpenMP: the pragmas are ignored
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -91,13 +92,21 @@ def _load():
                 "orc_solve_sweeps": (i, [i, i, i, i, i, dp, i, dp, dp, d, i, dp, dp]),
                 "orc_norm2_interior": (d, [i, i, dp]),
                 "orc_solve": (i, [i, i, i, i, i, dp, dp, dp, d, i, dp, dp]),
+                "orc_set_threads": (i, [i]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
                 fn.restype = res
                 fn.argtypes = args
+            lib.orc_set_threads(1)
             _lib = lib
     return _lib
+
+
+def set_threads(t: int) -> int:
+    """Threads of the oracle's per-point loops (results do not depend on it);
+    returns the count in effect (1 when the library was built without OpenMP)."""
+    return int(_load().orc_set_threads(int(t)))
 
 
 def _p(a: np.ndarray):

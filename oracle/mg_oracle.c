@@ -24,16 +24,39 @@
  *     keeps rings at zero (homogeneous Dirichlet data).
  *   - Floating-point expressions are written in the order of the paper's
  *     formulas; the library is built without FMA contraction.
+ *   - Threads.  In an OpenMP build the loops over the points of a stage (each
+ *     point computed from inputs the loop does not write) are split across
+ *     threads; sums (norms) and the coarsest solve stay serial, so the
+ *     results do not depend on the thread count.  One thread by default
+ *     (orc_set_threads).
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define IDX2(n, i, j) ((size_t)(j) * (size_t)((n) + 2) + (size_t)(i))
 #define IDX3(n, i, j, k) \
     (((size_t)(k) * (size_t)((n) + 2) + (size_t)(j)) * (size_t)((n) + 2) + (size_t)(i))
 
 enum { ORC_DIAG = 0, ORC_USUAL = 1 };
+
+#define ORC_PAR _Pragma("omp parallel for schedule(static)")
+
+/* threads of the per-point loops (OpenMP builds; ignored otherwise); returns
+ * the count in effect */
+int orc_set_threads(int t)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(t > 0 ? t : 1);
+    return omp_get_max_threads();
+#else
+    (void)t;
+    return 1;
+#endif
+}
 
 static size_t grid_len(int dim, int n)
 {
@@ -60,6 +83,7 @@ static int log2_side(int n)
  *                  - [-20u + 4 sum4axis u + sum4diag u]/(6h^2)     (Eq. Efos2) */
 void orc_residual2d(int n, double h, int order, const double *f, const double *u, double *r)
 {
+    ORC_PAR
     for (int j = 1; j <= n; j++)
         for (int i = 1; i <= n; i++) {
             double res;
@@ -84,6 +108,7 @@ void orc_residual2d(int n, double h, int order, const double *f, const double *u
  *     order 4: r = (6f + sum6 f)/12 - [-24u + 2 sum6 u + sum12 u]/(6h^2)  (Eq. Efos4) */
 void orc_residual3d(int n, double h, int order, const double *f, const double *u, double *r)
 {
+    ORC_PAR
     for (int k = 1; k <= n; k++)
         for (int j = 1; j <= n; j++)
             for (int i = 1; i <= n; i++) {
@@ -124,6 +149,7 @@ void orc_residual(int dim, int n, double h, int order, const double *f, const do
 /* green -> red, Eq. Erest2r: at i+j even, r' = (4r + 4 axis neighbours)/8 */
 void orc_restrict2d_g2r(int n, const double *rg, double *rr)
 {
+    ORC_PAR
     for (int j = 1; j <= n; j++)
         for (int i = 1; i <= n; i++) {
             if ((i + j) % 2 != 0) continue;
@@ -138,6 +164,7 @@ void orc_restrict2d_g2r(int n, const double *rg, double *rr)
 void orc_restrict2d_r2b(int n, const double *rr, double *rb)
 {
     int nb = (n - 1) / 2;
+    ORC_PAR
     for (int b = 1; b <= nb; b++)
         for (int a = 1; a <= nb; a++) {
             int i = 2 * a, j = 2 * b;
@@ -155,6 +182,7 @@ void orc_restrict2d_r2b(int n, const double *rr, double *rb)
 void orc_prolong2d_b2r(int n, double h, double p, const double *vb, const double *rr, double *vr)
 {
     int nb = (n - 1) / 2;
+    ORC_PAR
     for (int j = 1; j <= n; j += 2)
         for (int i = 1; i <= n; i += 2) {
             /* diagonal neighbours (i+-1, j+-1) are blue points ((i+-1)/2, (j+-1)/2) */
@@ -162,6 +190,7 @@ void orc_prolong2d_b2r(int n, double h, double p, const double *vb, const double
                        vb[IDX2(nb, (i + 1) / 2, (j + 1) / 2)] + vb[IDX2(nb, (i - 1) / 2, (j + 1) / 2)];
             vr[IDX2(n, i, j)] = (-2.0 * p * h * h * rr[IDX2(n, i, j)] + s) / 4.0;
         }
+    ORC_PAR
     for (int j = 2; j <= n; j += 2)
         for (int i = 2; i <= n; i += 2) {
             double s = vr[IDX2(n, i - 1, j - 1)] + vr[IDX2(n, i + 1, j - 1)] +
@@ -175,6 +204,7 @@ void orc_prolong2d_b2r(int n, double h, double p, const double *vb, const double
  * points (i+j even) from the four new green values; spacing h. */
 void orc_prolong2d_r2g(int n, double h, double p, const double *vr, const double *rg, double *vg)
 {
+    ORC_PAR
     for (int j = 1; j <= n; j++)
         for (int i = 1; i <= n; i++) {
             if ((i + j) % 2 == 0) continue;
@@ -182,6 +212,7 @@ void orc_prolong2d_r2g(int n, double h, double p, const double *vr, const double
                        vr[IDX2(n, i, j + 1)];
             vg[IDX2(n, i, j)] = (-p * h * h * rg[IDX2(n, i, j)] + s) / 4.0;
         }
+    ORC_PAR
     for (int j = 1; j <= n; j++)
         for (int i = 1; i <= n; i++) {
             if ((i + j) % 2 != 0) continue;
@@ -201,6 +232,7 @@ void orc_prolong2d_r2g(int n, double h, double p, const double *vr, const double
 void orc_sweep2d_red(int n, double h, double p, const double *rr, double *vr)
 {
     for (int par = 1; par >= 0; par--)
+        ORC_PAR
         for (int j = 2 - par; j <= n; j += 2)
             for (int i = 2 - par; i <= n; i += 2) {
                 double s = vr[IDX2(n, i - 1, j - 1)] + vr[IDX2(n, i + 1, j - 1)] +
@@ -212,6 +244,7 @@ void orc_sweep2d_red(int n, double h, double p, const double *rr, double *vr)
 void orc_sweep2d_green(int n, double h, double p, const double *rg, double *vg)
 {
     for (int par = 1; par >= 0; par--)
+        ORC_PAR
         for (int j = 1; j <= n; j++)
             for (int i = 1; i <= n; i++) {
                 if ((i + j) % 2 != par) continue;
@@ -231,6 +264,7 @@ static int is_even(int x) { return (x % 2) == 0; }
 /* green -> red, Eq. Erred: at i+j+k even, r' = (6r + 6 axis neighbours)/12 */
 void orc_restrict3d_g2r(int n, const double *rg, double *rr)
 {
+    ORC_PAR
     for (int k = 1; k <= n; k++)
         for (int j = 1; j <= n; j++)
             for (int i = 1; i <= n; i++) {
@@ -246,6 +280,7 @@ void orc_restrict3d_g2r(int n, const double *rg, double *rr)
  * centres (o,o,o), Eq. Ermagm: mean of the 6 axis (face-centre) red values. */
 void orc_restrict3d_r2m(int n, const double *rr, double *rm)
 {
+    ORC_PAR
     for (int k = 1; k <= n; k++)
         for (int j = 1; j <= n; j++)
             for (int i = 1; i <= n; i++) {
@@ -271,6 +306,7 @@ void orc_restrict3d_r2m(int n, const double *rr, double *rm)
 void orc_restrict3d_m2b(int n, const double *rm, double *rb)
 {
     int nb = (n - 1) / 2;
+    ORC_PAR
     for (int c = 1; c <= nb; c++)
         for (int b = 1; b <= nb; b++)
             for (int a = 1; a <= nb; a++) {
@@ -289,6 +325,7 @@ void orc_restrict3d_m2b(int n, const double *rm, double *rb)
 void orc_prolong3d_b2m(int n, double h, double pm, const double *vb, const double *rm, double *vm)
 {
     int nb = (n - 1) / 2;
+    ORC_PAR
     for (int k = 1; k <= n; k += 2)
         for (int j = 1; j <= n; j += 2)
             for (int i = 1; i <= n; i += 2) {
@@ -300,6 +337,7 @@ void orc_prolong3d_b2m(int n, double h, double pm, const double *vb, const doubl
                            vb[IDX3(nb, a0, b0, c1)] + vb[IDX3(nb, a0, b0, c0)];
                 vm[IDX3(n, i, j, k)] = (-4.0 * pm * h * h * rm[IDX3(n, i, j, k)] + s) / 8.0;
             }
+    ORC_PAR
     for (int k = 2; k <= n; k += 2)
         for (int j = 2; j <= n; j += 2)
             for (int i = 2; i <= n; i += 2) {
@@ -319,6 +357,7 @@ void orc_prolong3d_b2m(int n, double h, double pm, const double *vb, const doubl
 void orc_prolong3d_m2r(int n, double h, double pr1, double pr2, const double *vm, const double *rr,
                        double *vr)
 {
+    ORC_PAR
     for (int k = 1; k <= n; k++)
         for (int j = 1; j <= n; j++)
             for (int i = 1; i <= n; i++) {
@@ -341,6 +380,7 @@ void orc_prolong3d_m2r(int n, double h, double pr1, double pr2, const double *vm
                 vr[IDX3(n, i, j, k)] =
                     (-2.0 * pr1 * h * h * rr[IDX3(n, i, j, k)] + 2.0 * centres + corners) / 8.0;
             }
+    ORC_PAR
     for (int k = 2; k <= n; k += 2)
         for (int j = 2; j <= n; j += 2)
             for (int i = 2; i <= n; i += 2) {
@@ -360,6 +400,7 @@ void orc_prolong3d_r2g(int n, double h, double pg, const double *vr, const doubl
 {
     for (int pass = 0; pass < 2; pass++) {
         const double *src = pass == 0 ? vr : vg;
+        ORC_PAR
         for (int k = 1; k <= n; k++)
             for (int j = 1; j <= n; j++)
                 for (int i = 1; i <= n; i++) {
@@ -383,6 +424,7 @@ void orc_restrict_fw(int dim, int n, const double *rf, double *rc)
     static const double w[3] = {1.0, 2.0, 1.0};
     int nc = (n - 1) / 2;
     if (dim == 2) {
+        ORC_PAR
         for (int b = 1; b <= nc; b++)
             for (int a = 1; a <= nc; a++) {
                 double s = 0.0;
@@ -392,6 +434,7 @@ void orc_restrict_fw(int dim, int n, const double *rf, double *rc)
                 rc[IDX2(nc, a, b)] = s / 16.0;
             }
     } else {
+        ORC_PAR
         for (int c = 1; c <= nc; c++)
             for (int b = 1; b <= nc; b++)
                 for (int a = 1; a <= nc; a++) {
@@ -412,6 +455,7 @@ static void interp_usual(int dim, int n, const double *vc, double *vf)
 {
     int nc = (n - 1) / 2;
     if (dim == 2) {
+        ORC_PAR
         for (int j = 1; j <= n; j++)
             for (int i = 1; i <= n; i++) {
                 int a0 = i / 2, a1 = (i + 1) / 2, b0 = j / 2, b1 = (j + 1) / 2;
@@ -419,6 +463,7 @@ static void interp_usual(int dim, int n, const double *vc, double *vf)
                                      vc[IDX2(nc, a0, b1)] + vc[IDX2(nc, a1, b1)]) / 4.0;
             }
     } else {
+        ORC_PAR
         for (int k = 1; k <= n; k++)
             for (int j = 1; j <= n; j++)
                 for (int i = 1; i <= n; i++) {
@@ -445,6 +490,7 @@ void orc_prolong_usual(int dim, int n, double h, double p, const double *vc, con
     interp_usual(dim, n, vc, vf);
     for (int parity = 1; parity >= 0; parity--) {
         if (dim == 2) {
+            ORC_PAR
             for (int j = 1; j <= n; j++)
                 for (int i = 1; i <= n; i++) {
                     if ((i + j) % 2 != parity) continue;
@@ -453,6 +499,7 @@ void orc_prolong_usual(int dim, int n, double h, double p, const double *vc, con
                     vf[IDX2(n, i, j)] = (-p * h * h * rf[IDX2(n, i, j)] + s) / 4.0;
                 }
         } else {
+            ORC_PAR
             for (int k = 1; k <= n; k++)
                 for (int j = 1; j <= n; j++)
                     for (int i = 1; i <= n; i++) {
@@ -594,9 +641,11 @@ int orc_vcycle_sweeps(int dim, int n, int hier, int order, int coarsest, const d
     }
     if (rc == 0) {
         if (dim == 2) {
+            ORC_PAR
             for (int j = 1; j <= n; j++)
                 for (int i = 1; i <= n; i++) u[IDX2(n, i, j)] += vg[0][IDX2(n, i, j)];
         } else {
+            ORC_PAR
             for (int k = 1; k <= n; k++)
                 for (int j = 1; j <= n; j++)
                     for (int i = 1; i <= n; i++) u[IDX3(n, i, j, k)] += vg[0][IDX3(n, i, j, k)];

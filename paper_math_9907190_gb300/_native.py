@@ -41,6 +41,8 @@ SIGNATURES = {
     "mg_level_set": (_i, [_vp, _i, _i, _vp, _vp]),
     "mg_vcycle": (_i, [_vp, _vp, _vp, _vp]),
     "mg_solve": (_i, [_vp, _vp, _vp, _d, _i, _ip, _dp, _dp, _vp]),
+    "mg_solve_host": (_i, [_vp, _vp, _vp, _vp, _d, _i, _ip, _dp, _vp]),
+    "mg_fp64_rate": (_i, [_vp, _dp, _vp]),
     "mg_launch_count": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "mg_probe_set": (_i, [_vp, _i]),
     "mg_probe_read": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _dp, _vp]),
@@ -49,6 +51,7 @@ SIGNATURES = {
     "mg_batch_destroy": (_i, [_vp]),
     "mg_solve_batched": (_i, [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _d, _i, _ip, _dp, _vp]),
     "mg_batch_launch_count": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "mg_batch_status": (_i, [_vp, _ip]),
     "mg_tune": (_i, [_vp, _vp, _vp, ctypes.c_char_p, _ip, _vp]),
     "mg_set_omega": (_i, [_vp, _dp]),
     "mg_set_sweeps": (_i, [_vp, _i]),

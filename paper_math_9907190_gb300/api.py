@@ -132,6 +132,33 @@ class Context:
             N.check(st, "mg_solve_two_stage")
         return u, c2.value, c4.value, rel.value
 
+    def solve_host(self, f, u=None, *, u0=None, rtol: float = 1e-10, max_cycles: int = 100,
+                   raise_on_fail: bool = True):
+        """mg_solve_host: f, u0 (warm start; None: u = 0) and u (the result;
+        default a new tensor) are CPU float64 full grids -- pin them for full
+        copy bandwidth.  Returns (u, cycles, relres)."""
+        shape = (self.n + 2,) * (self.dim - 1) + (self.pitch,)
+        u = torch.empty(shape, dtype=torch.float64) if u is None else u
+        for name, t in (("f", f), ("u", u), ("u0", u0)):
+            if t is None:
+                continue
+            if t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != shape:
+                raise ValueError(f"{name}: expected a contiguous CPU float64 tensor of shape {shape}")
+        cyc, rel = ctypes.c_int(), ctypes.c_double()
+        st = N.lib().mg_solve_host(self._h, ctypes.c_void_p(f.data_ptr()),
+                                   ctypes.c_void_p(u0.data_ptr()) if u0 is not None else None,
+                                   ctypes.c_void_p(u.data_ptr()), rtol, max_cycles, ctypes.byref(cyc),
+                                   ctypes.byref(rel), self._stream())
+        if raise_on_fail:
+            N.check(st, "mg_solve_host")
+        return u, cyc.value, rel.value
+
+    def fp64_rate(self) -> float:
+        """mg_fp64_rate: measured FP64 pipe operations per second of this device."""
+        v = ctypes.c_double()
+        N.check(N.lib().mg_fp64_rate(self._h, ctypes.byref(v), self._stream()), "mg_fp64_rate")
+        return v.value
+
     def set_omega(self, omega):
         """mg_set_omega: new over-relaxation weights for later cycles."""
         arr = (ctypes.c_double * 4)(*(list(omega) + [1.0] * (4 - len(omega))))
@@ -267,6 +294,12 @@ class Batch:
         v = ctypes.c_longlong()
         N.check(N.lib().mg_batch_launch_count(self._h, ctypes.byref(v)), "mg_batch_launch_count")
         return v.value
+
+    def statuses(self):
+        """mg_batch_status: per problem of the last solve, MG_OK, MG_ENOCONV or MG_EDIVERGED."""
+        st = (ctypes.c_int * len(self.sides))()
+        N.check(N.lib().mg_batch_status(self._h, st), "mg_batch_status")
+        return list(st)
 
     def tune(self, fs, us=None, cache: str | None = None):
         """mg_batch_tune: tune every size group (us are scratch, left zero)."""

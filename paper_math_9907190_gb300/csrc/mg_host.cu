@@ -40,6 +40,8 @@ mg_status cuda_fail(cudaError_t e, const char *where) {
 // boundary (8 bytes; 16-byte vector paths are chosen only where the pointer
 // and the pitch allow them)
 bool bad_grid(const void *p) { return !p || ((uintptr_t)p & 7u) != 0; }
+// two full grids of len doubles starting at a and b share memory
+bool grids_overlap(const double *a, const double *b, size_t len) { return a < b + len && b < a + len; }
 
 int log2_side(int n) {
     if (n < 1) return -1;
@@ -112,6 +114,8 @@ struct mg_ctx {
     bool fast3d = false;
     CoarsePlan3d plan3d{};
     double *ft = nullptr;       // order-4 right-hand side (caller pitch), FP64
+    double *io_f = nullptr;     // device copies of f and u for mg_solve_host (allocated by its first call)
+    double *io_u = nullptr;
     int nparts = 0;             // partial sums written by the last residual (per problem)
     // batch: nprob problems of this size, level pools pstride bytes apart,
     // f/u from device pointer tables (nullptr for a single problem)
@@ -996,6 +1000,8 @@ mg_status mg_destroy(mg_ctx *c) {
     cudaFree(c->G);
     cudaFree(c->scal);
     cudaFree(c->ft);
+    cudaFree(c->io_f);
+    cudaFree(c->io_u);
     cudaFree(c->ftab);
     cudaFree(c->utab);
     delete c;
@@ -1151,6 +1157,10 @@ mg_status mg_level_info(const mg_ctx *c, int level, int *side, int *kind) {
 mg_status mg_residual(mg_ctx *c, const double *f, const double *u, double h, int order, double *r, double *norm2,
                       void *stream) {
     if (!c || bad_grid(f) || bad_grid(u) || (r && bad_grid(r))) return MG_EINVAL;
+    if (r) {  // r is written while f and u are read: their extents must not overlap
+        const size_t len = (size_t)c->d.pitch * (c->d.n + 2) * (c->d.dim == 3 ? (size_t)(c->d.n + 2) : 1);
+        if (grids_overlap(r, f, len) || grids_overlap(r, u, len)) return MG_EINVAL;
+    }
     if (order != c->d.order) return MG_EINVAL;
     if (std::fabs(h - c->h) > 1e-15 * c->h) return MG_EINVAL;
     cudaStream_t s = S(stream);
@@ -1474,6 +1484,34 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
     return MG_OK;
 }
 
+mg_status mg_solve_host(mg_ctx *c, const double *f_host, const double *u0_host, double *u_host, double rtol,
+                        int max_cycles, int *cycles_out, double *relres_out, void *stream) {
+    if (!c || c->nprob != 1 || bad_grid(f_host) || bad_grid(u_host) || (u0_host && bad_grid(u0_host)) ||
+        !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap)
+        return MG_EINVAL;
+    const size_t len = (size_t)c->d.pitch * (c->d.n + 2) * (c->d.dim == 3 ? (size_t)(c->d.n + 2) : 1);
+    const size_t bytes = sizeof(double) * len;
+    if (grids_overlap(f_host, u_host, len)) return MG_EINVAL;
+    if (!c->io_f) {  // the first call: device copies of f and u, kept by the context
+        if (cudaMalloc(&c->io_f, bytes) != cudaSuccess || cudaMalloc(&c->io_u, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->io_f);
+            cudaFree(c->io_u);
+            c->io_f = c->io_u = nullptr;
+            return MG_ENOMEM;
+        }
+    }
+    cudaStream_t s = S(stream);
+    CK(cudaMemcpyAsync(c->io_f, f_host, bytes, cudaMemcpyHostToDevice, s));
+    if (u0_host) CK(cudaMemcpyAsync(c->io_u, u0_host, bytes, cudaMemcpyHostToDevice, s));
+    else CK(cudaMemsetAsync(c->io_u, 0, bytes, s));
+    const mg_status st = mg_solve(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out, nullptr, stream);
+    if (st != MG_OK && st != MG_ENOCONV && st != MG_EDIVERGED) return st;
+    CK(cudaMemcpyAsync(u_host, c->io_u, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return st;
+}
+
 // Section 2.4 / 3.4: a fourth-order solution is reached fastest by first
 // converging the second-order problem (its V-cycles contract ~10x faster) and
 // then running a few cycles on the fourth-order residual.
@@ -1710,6 +1748,16 @@ mg_status mg_solve_batched(mg_batch *b, const double *const *f, double *const *u
     }
     if (diverged) return MG_EDIVERGED;
     if (noconv) return MG_ENOCONV;
+    return MG_OK;
+}
+
+mg_status mg_batch_status(const mg_batch *b, int *status) {
+    if (!b || !status) return MG_EINVAL;
+    if ((int)b->host.size() != b->nprob) return MG_EINVAL;  // no solve yet
+    for (int p = 0; p < b->nprob; p++) {
+        const Ctrl &h = b->host[p];
+        status[p] = h.status == -5 ? MG_EDIVERGED : (h.status == -4 || !h.done) ? MG_ENOCONV : MG_OK;
+    }
     return MG_OK;
 }
 
@@ -1957,6 +2005,34 @@ mg_status mg_probe_read(mg_ctx *c, long long *launches, double *ms, void *stream
     probe_collect(c);
     if (launches) *launches = c->probe_n;
     if (ms) *ms = c->probe_ms;
+    return MG_OK;
+}
+
+mg_status mg_fp64_rate(mg_ctx *c, double *ops_per_s, void *stream) {
+    if (!c || !ops_per_s) return MG_EINVAL;
+    cudaStream_t s = S(stream);
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev));
+    const int blocks = 4 * sms, threads = 256, iters = 4096;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(cudaGetLastError(), "mg_fp64_rate"); }
+    double best = 0.0;
+    cudaError_t err = cudaSuccess;
+    for (int rep = 0; rep < 4 && err == cudaSuccess; rep++) {
+        cudaEventRecord(e0, s);
+        k_dfma_rate<<<blocks, threads, 0, s>>>(1.0 + rep, iters, c->scal);
+        cudaEventRecord(e1, s);
+        err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        if (err == cudaSuccess && rep > 0 && ms > 0.f)  // the first launch is a warm-up
+            best = std::max(best, (double)blocks * threads * iters * DFMA_CHAINS / (ms * 1e-3));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "mg_fp64_rate");
+    *ops_per_s = best;
     return MG_OK;
 }
 

@@ -106,6 +106,13 @@ extern "C" mg_status mg_residual_noalloc(int dim, int n, int pitch, double h, in
     if (log2_side(n) < 1 || pitch < n + 2 || (order != 2 && order != 4) || !f || !u) return MG_EINVAL;
     // FP64 element boundaries (8 bytes) for every grid pointer
     if (((uintptr_t)f | (uintptr_t)u | (uintptr_t)r) & 7u) return MG_EINVAL;
+    // r is written while neighbouring threads still read f and u: the
+    // extents of the full grids must not overlap
+    if (r) {
+        const size_t len = (size_t)pitch * (n + 2) * (dim == 3 ? (size_t)(n + 2) : 1);
+        auto overlap = [len](const double *a, const double *b) { return a < b + len && b < a + len; };
+        if (overlap(r, f) || overlap(r, u)) return MG_EINVAL;
+    }
     if (!(h > 0.0) || std::fabs(h - 1.0 / (n + 1)) > 1e-15 / (n + 1)) return MG_EINVAL;
     // the size limit of the static scratch: one partial sum per thread block
     const long long nblk = (long long)((n + 31) / 32) * ((n + 7) / 8) * (dim == 3 ? n : 1);
@@ -116,7 +123,10 @@ extern "C" mg_status mg_residual_noalloc(int dim, int n, int pitch, double h, in
     double *part = nullptr;
     {
         // first call on this device: look up the array's device address with
-        // the device current (the host-side name is not a device address)
+        // the device current (the host-side name is not a device address).
+        // The address is kept for the life of the process: after a
+        // cudaDeviceReset the module is reloaded and this copy would be stale,
+        // so resetting a device after its first call is not supported.
         std::lock_guard<std::mutex> lock(g_mu);
         if (!g_partials_addr[dev]) {
             void *p = nullptr;

@@ -721,6 +721,35 @@ __device__ __forceinline__ double sum_parts(const double *part, int nblk, double
     return block_sum(v, sh);
 }
 
+// relative residual sqrt(r2 / f2); 0 for a zero right-hand side (any iterate
+// is then as good as the exact solution 0 in relative terms), NaN when f2 is
+// not a number (a right-hand side carrying NaN), so that the solve reports
+// divergence instead of convergence
+__device__ __forceinline__ double rel_residual(double r2, double f2) {
+    return f2 > 0.0 ? sqrt(r2 / f2) : (f2 == 0.0 ? 0.0 : __longlong_as_double(0x7ff8000000000000ll));
+}
+
+// FP64 pipe throughput probe (mg_fp64_rate): every thread runs DFMA_CHAINS
+// independent chains of `iters` dependent FP64 FMAs (x <- x * m + c, one
+// FP64 pipe operation each); the result is stored only when it equals a
+// value it never takes, so the chains stay live without memory traffic
+constexpr int DFMA_CHAINS = 8;
+__global__ void __launch_bounds__(256) k_dfma_rate(double seed, int iters, double *sink) {
+    pdl_wait();
+    double x[DFMA_CHAINS];
+#pragma unroll
+    for (int q = 0; q < DFMA_CHAINS; q++) x[q] = seed + 1e-3 * (threadIdx.x + q);
+    const double m = 1.0 - 1e-12, c = 1e-13;
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int q = 0; q < DFMA_CHAINS; q++) x[q] = fma(x[q], m, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < DFMA_CHAINS; q++) t += x[q];
+    if (t == -1.0) *sink = t;
+}
+
 // after the residual of the warm start (first = 1) or of a new iterate:
 // record the history, decide whether to stop.  Inside the solver's graph
 // (use_loop = 1) it also sets the graph's loop condition to "not done".
@@ -732,7 +761,7 @@ __device__ __forceinline__ void ctrl_step(Ctrl *ctl, double s, double *hist, int
     ctl->rmax[ctl->par ^ 1] = 0u;  // the buffer the next cycle writes
     ctl->vmax = 0u;
     ctl->r2 = s;
-    double rel = ctl->f2 > 0.0 ? sqrt(s / ctl->f2) : 0.0;
+    double rel = rel_residual(s, ctl->f2);
     ctl->relres = rel;
     if (first) ctl->rel0 = rel;
     else hist[ctl->cycles - 1] = rel;
@@ -835,7 +864,7 @@ __global__ void k_ctrl_b(const double *part, int nblk, Ctrl *ctl, double *hist, 
     c->rmax[c->par ^ 1] = 0u;
     c->vmax = 0u;
     c->r2 = s;
-    double rel = c->f2 > 0.0 ? sqrt(s / c->f2) : 0.0;
+    double rel = rel_residual(s, c->f2);
     c->relres = rel;
     if (first) c->rel0 = rel;
     else hist[(size_t)p * hist_cap + c->cycles - 1] = rel;
@@ -860,7 +889,7 @@ __global__ void k_final_true(const double *part, int nblk, Ctrl *ctl) {
     Ctrl *c = ctl + p;
     const double s = sum_parts(part + (size_t)p * nblk, nblk, sh);
     if (threadIdx.x != 0) return;
-    const double rel = c->f2 > 0.0 ? sqrt(s / c->f2) : 0.0;
+    const double rel = rel_residual(s, c->f2);
     c->r2 = s;
     c->relres = rel;
     if (c->status == 0 && !(rel <= c->rtol)) c->status = -4;

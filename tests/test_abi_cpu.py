@@ -65,6 +65,9 @@ def test_null_arguments_rejected(lib):
     assert lib.mg_vcycle(None, None, None, None) == N.MG_EINVAL
     assert lib.mg_solve(None, None, None, 1e-10, 10, None, None, None, None) == N.MG_EINVAL
     assert lib.mg_level_get(None, 0, 0, None, None) == N.MG_EINVAL
+    assert lib.mg_solve_host(None, None, None, None, 1e-10, 10, None, None, None) == N.MG_EINVAL
+    assert lib.mg_fp64_rate(None, None, None) == N.MG_EINVAL
+    assert lib.mg_batch_status(None, None) == N.MG_EINVAL
     assert lib.mg_destroy(None) == N.MG_OK
 
 
@@ -158,9 +161,10 @@ def test_python_api_surface():
     for name in ("Batch", "Context", "PoissonSolve", "default_omega", "solve"):
         assert hasattr(P, name), name
     for m in ("solve", "vcycle", "residual", "solve_two_stage", "set_omega", "set_sweeps", "rho", "tune",
-              "tune_info", "restrict", "coarse_solve", "prolong", "level_get", "level_set", "new_grid", "close"):
+              "tune_info", "restrict", "coarse_solve", "prolong", "level_get", "level_set", "new_grid", "close",
+              "solve_host", "fp64_rate"):
         assert callable(getattr(P.Context, m)), m
-    for m in ("solve", "tune", "close"):
+    for m in ("solve", "tune", "close", "statuses"):
         assert callable(getattr(P.Batch, m)), m
     assert list(inspect.signature(P.Context.__init__).parameters)[1:3] == ["dim", "n"]
     assert P.default_omega(2, "diag", 2) == (1.052,)

@@ -29,12 +29,52 @@ def test_reference_arm_prints_one_contract_line():
     assert d["unit"] == "unknowns/s" and d["higher_is_better"] is True
     assert d["dtype"] == "f64" and d["data"] == "synthetic"
     assert d["value"] > 0 and d["ms_per_step"] > 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"]
+    assert cb["nproc"] == os.cpu_count() and 1 <= cb["cores"] <= cb["nproc"] and cb["cpu_model"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    # four V-cycles of the diagonal hierarchy do not reach 1e-10; the cycle
-    # count to reach it comes from the measured contraction (about 0.06 per
-    # cycle for this workload, so about nine cycles)
-    assert 7 <= d["config"]["cycles_to_rtol"] <= 12
+    # a step is a full oracle solve to 1e-10: about nine cycles of the
+    # diagonal hierarchy (contraction about 0.06 per cycle for this workload)
+    assert 7 <= d["config"]["cycles_to_rtol"] <= 12 and d["config"]["relres"] <= 1e-10
+
+
+def _bench_module():
+    import importlib.util
+
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    return bench
+
+
+def test_cpu_baseline_legs_on_all_cores_and_one_core():
+    """bench.py's cpu_baseline: the oracle solve of the benchmark workload on
+    all host cores, with the one-core leg beside it; the two solutions are
+    the same bits (the threads split only per-point loops)."""
+    import numpy as np
+
+    from paper_math_9907190_gb300 import inputs as I
+    bench = _bench_module()
+    cb, u = bench.oracle_cpu_baseline(I.square_large(bench.N_SIDE))
+    for key in ("value", "unit", "cores", "kind", "sample", "nproc", "cpu_model", "single_core"):
+        assert key in cb, key
+    assert cb["single_core"]["cores"] == 1 and cb["value"] > 0 and cb["single_core"]["value"] > 0
+    assert np.isfinite(u).all()
+
+
+def test_main_line_carries_the_roofline_and_e2e_keys():
+    """The keys of the GPU arm's line (built on a GPU only): the cycle-level
+    HBM fraction, the FP64 path's roofline, the C-ABI end-to-end number with
+    its pipelined variant, and the all-cores CPU baseline."""
+    bench = _bench_module()
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    for key in ('"cycle_frac"', '"cycle"', '"roofline_fp64"', '"cycle_roofline"', '"pipelined"', '"api"',
+                '"single_core"', '"cpu_model"', '"nproc"', '"roofline"', '"cpu_baseline"', '"e2e"', '"clocks"',
+                '"gpu_launches"'):
+        assert key in src, key
+    r = bench.cycle_roofline(4095**2, 9, 2.0, 6746.3)
+    assert r["bytes_per_unknown"] == 40 + 36 * 9
+    assert abs(r["frac"] - 364 * 4095**2 / 2e-3 / 1e9 / 6746.3) < 1e-12
 
 
 def test_reference_arm_other_ranks_exit_quietly():
@@ -47,11 +87,7 @@ def test_traffic_counters_belong_to_the_current_kernels():
     """The DRAM traffic bench.py reports for the dominant kernels was captured
     on the kernel source it names by hash; a kernel edited since reports no
     traffic (null) until it is captured again.  Both are current."""
-    import importlib.util
-
-    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
-    bench = importlib.util.module_from_spec(spec)
-    spec.loader.exec_module(bench)
+    bench = _bench_module()
     for t in (bench.TRAFFIC, bench.TRAFFIC3):
         assert bench.kernel_source_sha1(t["kernel"], t["file"]) == t["source_sha1"], t["kernel"]
         assert bench.measured_traffic(t) == t["bytes"] > 0

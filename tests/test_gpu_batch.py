@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 import oracle as O
 from paper_math_9907190_gb300 import Batch, Context, default_omega
 from paper_math_9907190_gb300 import inputs as I
+from _iterates import assert_iterate
 
 pytestmark = pytest.mark.gpu
 
@@ -44,8 +45,7 @@ def test_batch_2d_matches_single_contexts_and_oracle(precision):
                                max_cycles=100)
         if precision == "fp64":
             assert co == cyc[b]
-        err = np.linalg.norm(us[b].cpu().numpy() - uo) / np.linalg.norm(uo)
-        assert err <= (1e-12 if precision == "fp64" else 1e-8), (b, n, err)
+        assert_iterate(us[b].cpu().numpy(), uo, 1e-12 if precision == "fp64" else 1e-8, what=f"problem {b} (n={n})")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
@@ -60,8 +60,7 @@ def test_batch_3d_matches_oracle(precision):
             u1, c1, _, _ = c.solve(T(fs[b]), rtol=1e-10, max_cycles=60)
         assert cyc[b] == c1 and torch.equal(us[b], u1)
         uo, _, _, _ = O.solve(fs[b], omega=list(om), rtol=1e-10 if precision == "fp64" else 1e-13, max_cycles=100)
-        err = np.linalg.norm(us[b].cpu().numpy() - uo) / np.linalg.norm(uo)
-        assert err <= (1e-12 if precision == "fp64" else 1e-8), (b, n, err)
+        assert_iterate(us[b].cpu().numpy(), uo, 1e-12 if precision == "fp64" else 1e-8, what=f"problem {b} (n={n})")
 
 
 def test_batch_repeat_and_warm_start():

@@ -1,0 +1,59 @@
+"""mg_solve_host (the solve with HOST arrays) and mg_fp64_rate, through the C ABI.
+
+mg_solve_host must give the bits of mg_solve on device copies of the same
+arrays (it copies, solves with the same graph, copies back), from u = 0 and
+from a warm start, and refuse bad arguments before any copy."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_math_9907190_gb300 import Context
+from paper_math_9907190_gb300 import _native as N
+from paper_math_9907190_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+DEV = torch.device("cuda", 0)
+
+
+@pytest.mark.parametrize("dim,n,prec", [(2, 255, "mixed"), (2, 1023, "fp64"), (3, 63, "mixed")])
+def test_host_solve_equals_device_solve(dim, n, prec):
+    f = torch.from_numpy(I.uniform_f(dim, n, 71)).pin_memory()
+    with Context(dim, n, precision=prec) as c:
+        ud, cd, rd, _ = c.solve(f.to(DEV), rtol=1e-10)
+        uh = torch.empty_like(f).pin_memory()
+        u2, ch, rh = c.solve_host(f, uh, rtol=1e-10)
+        assert u2 is uh and ch == cd and rh == rd
+        assert np.array_equal(uh.numpy(), ud.cpu().numpy())
+        # warm start from a partial solve, result written over the warm start
+        up, _, _, _ = c.solve(f.to(DEV), rtol=1e-300, max_cycles=3, raise_on_fail=False)
+        w = up.cpu().pin_memory()
+        ud2, cd2, rd2, _ = c.solve(f.to(DEV), up.clone(), rtol=1e-10)
+        _, ch2, rh2 = c.solve_host(f, w, u0=w, rtol=1e-10)
+        assert ch2 == cd2 and rh2 == rd2 and np.array_equal(w.numpy(), ud2.cpu().numpy())
+
+
+def test_host_solve_refuses_bad_arguments():
+    with Context(2, 63) as c:
+        f = torch.zeros((65, 65), dtype=torch.float64)
+        L = N.lib()
+        P = lambda t: N.ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        s = c._stream()
+        assert L.mg_solve_host(c._h, None, None, P(f), 1e-10, 10, None, None, s) == N.MG_EINVAL
+        assert L.mg_solve_host(c._h, P(f), None, P(f), 1e-10, 10, None, None, s) == N.MG_EINVAL  # u over f
+        assert L.mg_solve_host(c._h, P(f), None, N.ctypes.c_void_p(f.data_ptr() + 4), 1e-10, 10, None, None,
+                               s) == N.MG_EINVAL
+        assert L.mg_solve_host(c._h, P(f), None, P(torch.zeros_like(f)), -1.0, 10, None, None, s) == N.MG_EINVAL
+
+
+def test_fp64_rate_is_plausible():
+    """Measured FP64 pipe rate: between a tenth of and twice the nominal
+    152 SMs x 2 FP64 operations per clock x 2.07 GHz (6.3e11 /s)."""
+    with Context(2, 63) as c:
+        r = c.fp64_rate()
+    assert 6.3e10 < r < 1.26e12, r

@@ -18,6 +18,7 @@ torch = pytest.importorskip("torch")
 import oracle as O
 from paper_math_9907190_gb300 import Context, default_omega
 from paper_math_9907190_gb300 import inputs as I
+from _iterates import assert_iterate
 
 pytestmark = pytest.mark.gpu
 
@@ -26,6 +27,13 @@ if not torch.cuda.is_available():
 
 DEV = torch.device("cuda", 0)
 TOL = 1e-12
+# Mixed path (FP32 levels): the oracle's FP64 iterate reproduced to FP32
+# accuracy at every point.  A cycle's correction is formed from FP32 level
+# values (relative rounding 2^-24 per operation, a few dozen operations deep
+# through the hierarchy) and, in the fused solve, rounded to 2^-21 (2D) /
+# 2^-20 (3D) of a bound on its size; relative to max|u| that is a few 1e-6
+# at most, while a wrong index or coefficient moves a point by O(1).
+MIXED_ELEM_TOL = 1e-5
 
 
 def T(a):
@@ -243,9 +251,7 @@ def test_vcycle_iterates_match_oracle(dim, n, hier, order, om):
         for cyc in range(12):
             O.vcycle(f, uo, hier=O.DIAG if hier == "diag" else O.USUAL, order=order, omega=list(om))
             c.vcycle(ft, ug)
-            got = H(ug)
-            rel = np.linalg.norm(got - uo) / np.linalg.norm(uo)
-            assert rel <= TOL, f"cycle {cyc}: rel {rel:.3e}"
+            assert_iterate(H(ug), uo, TOL, what=f"cycle {cyc}")
 
 
 @pytest.mark.parametrize("dim,n,om", [(2, 511, (1.052,)), (2, 2047, (1.052,)), (3, 127, (1.11, 1.42, 1.08, 0.99)),
@@ -263,8 +269,7 @@ def test_mixed_vcycle_iterates_follow_oracle(dim, n, om):
         for cyc in range(2):
             O.vcycle(f, uo, omega=list(om))
             c.vcycle(ft, ug)
-            rel = np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo)
-            assert rel <= 2e-6, f"cycle {cyc}: rel {rel:.3e}"
+            assert_iterate(H(ug), uo, MIXED_ELEM_TOL, l2_tol=2e-6, what=f"cycle {cyc}")
 
 
 @pytest.mark.parametrize("dim,n,om", [(2, 511, (1.052,)), (2, 2047, (1.052,)), (3, 127, (1.11, 1.42, 1.08, 0.99)),
@@ -282,8 +287,7 @@ def test_mixed_solve_iterates_follow_oracle(dim, n, om):
             O.vcycle(f, uo, omega=list(om))
             ug, it, _, _ = c.solve(ft, rtol=1e-300, max_cycles=k, raise_on_fail=False)
             assert it == k
-            rel = np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo)
-            assert rel <= 4e-6, f"cycle {k}: rel {rel:.3e}"
+            assert_iterate(H(ug), uo, MIXED_ELEM_TOL, l2_tol=4e-6, what=f"cycle {k}")
 
 
 @pytest.mark.parametrize("dim,n", [(2, 127), (2, 1023), (3, 63), (3, 255)])
@@ -311,7 +315,7 @@ def test_vcycle_coarsest_variants(coarsest):
         for _ in range(4):
             O.vcycle(f, uo, coarsest=coarsest, omega=[1.052])
             c.vcycle(T(f), ug)
-        assert np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo) <= TOL
+            assert_iterate(H(ug), uo, TOL)
 
 
 @pytest.mark.parametrize("dim,n,hier", [(2, 63, "diag"), (2, 63, "usual"), (3, 15, "diag"), (3, 31, "usual")])
@@ -324,7 +328,7 @@ def test_solve_fp64_matches_oracle(dim, n, hier):
     assert it_g == it_o
     assert rel_g <= 1e-10
     np.testing.assert_allclose(hist_g, hist_o, rtol=1e-6, atol=1e-13)
-    assert np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo) <= TOL
+    assert_iterate(H(ug), uo, TOL)
 
 
 @pytest.mark.parametrize("dim,n,hier,order", [(2, 63, "diag", 2), (2, 255, "diag", 2), (2, 255, "diag", 4),
@@ -342,8 +346,7 @@ def test_solve_mixed_reaches_tolerance(dim, n, hier, order):
     r = O.residual(f, H(ug), order)
     f0 = O.residual(f, O.grid(dim, n), order)
     assert math.sqrt(O.norm2_interior(r) / O.norm2_interior(f0)) <= 1.05e-10
-    err = np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo)
-    assert err <= 1e-8, err
+    assert_iterate(H(ug), uo, 1e-8)
 
 
 def test_solve_reports_nonconvergence():
@@ -363,18 +366,18 @@ def test_solve_warm_start_already_converged():
 
 @pytest.mark.parametrize("dim,n", [(2, 4095), (3, 255)])
 def test_full_size_vcycle_matches_oracle(dim, n):
-    """The benchmarked sizes: two FP64 V-cycles compared element by element."""
+    """The benchmarked sizes: two FP64 V-cycles compared element by element
+    (every one of the 16.8M / 16.6M points after each cycle)."""
     f = I.square_large(n) if dim == 2 else I.cube(n)
     om = default_omega(dim, "diag", 2)
     uo = O.grid(dim, n)
     with Context(dim, n, omega=om) as c:
         ug = c.new_grid()
         ft = T(f)
-        for _ in range(2):
+        for cyc in range(2):
             O.vcycle(f, uo, omega=list(om))
             c.vcycle(ft, ug)
-        got = H(ug)
-    assert np.linalg.norm(got - uo) / np.linalg.norm(uo) <= TOL
+            assert_iterate(H(ug), uo, TOL, what=f"cycle {cyc}")
 
 
 @pytest.mark.parametrize("dim,n", [(2, 127), (2, 1023), (2, 4095), (3, 63), (3, 255)])

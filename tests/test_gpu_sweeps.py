@@ -1,7 +1,8 @@
 """GPU parity of the extra Jacobi sweeps per level (mg_set_sweeps), the
 extension the paper's conclusion leaves open, against the oracle: V-cycle
-iterates element by element (FP64 1e-12, mixed FP32 levels 2e-6), solves
-cycle by cycle, and the argument checks."""
+iterates element by element (max pointwise difference over max |u|: FP64
+1e-12, mixed FP32 levels 1e-5, with the L2 ratio 2e-6 as a second bar),
+solves cycle by cycle, and the argument checks."""
 
 import numpy as np
 import pytest
@@ -12,6 +13,7 @@ import oracle as O
 from paper_math_9907190_gb300 import Context
 from paper_math_9907190_gb300 import inputs as I
 from paper_math_9907190_gb300._native import MGError
+from _iterates import assert_iterate
 
 pytestmark = pytest.mark.gpu
 
@@ -29,9 +31,10 @@ def H(t):
     return t.detach().cpu().numpy()
 
 
-@pytest.mark.parametrize("n,prec,tol", [(63, "fp64", 1e-12), (255, "fp64", 1e-12), (255, "mixed", 2e-6)])
+@pytest.mark.parametrize("n,prec,tol,l2", [(63, "fp64", 1e-12, 1e-12), (255, "fp64", 1e-12, 1e-12),
+                                           (255, "mixed", 1e-5, 2e-6)])
 @pytest.mark.parametrize("extra", [1, 2])
-def test_extra_sweeps_vcycle_matches_oracle(n, prec, tol, extra):
+def test_extra_sweeps_vcycle_matches_oracle(n, prec, tol, l2, extra):
     f = I.uniform_f(2, n, 21)
     uo = O.grid(2, n)
     with Context(2, n, precision=prec, omega=(1.052,)) as c:
@@ -40,8 +43,7 @@ def test_extra_sweeps_vcycle_matches_oracle(n, prec, tol, extra):
         for cyc in range(2):
             O.vcycle(f, uo, omega=[1.052], extra=extra)
             c.vcycle(ft, ug)
-            rel = np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo)
-            assert rel <= tol, f"cycle {cyc}: rel {rel:.3e}"
+            assert_iterate(H(ug), uo, tol, l2_tol=l2, what=f"cycle {cyc}")
 
 
 def test_extra_sweeps_solve_matches_oracle_fp64():
@@ -53,7 +55,7 @@ def test_extra_sweeps_solve_matches_oracle_fp64():
         ug, it, rel, hist = c.solve(T(f), rtol=1e-10)
     assert it == it_o and rel <= 1e-10
     np.testing.assert_allclose(hist, hist_o, rtol=1e-8, atol=1e-14)
-    assert np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo) <= 1e-12
+    assert_iterate(H(ug), uo, 1e-12)
 
 
 def test_extra_sweeps_solve_mixed_reaches_tolerance():
@@ -66,7 +68,7 @@ def test_extra_sweeps_solve_mixed_reaches_tolerance():
         c.set_sweeps(1)
         ug, it, rel, hist = c.solve(T(f), rtol=1e-10)
         assert rel <= 1e-10
-        assert np.linalg.norm(H(ug) - uo) / np.linalg.norm(uo) <= 1e-8
+        assert_iterate(H(ug), uo, 1e-8)
         c.set_sweeps(0)  # back to the paper's cycle (fused kernels, carried residual)
         _, it0, rel0, _ = c.solve(T(f), rtol=1e-10)
         assert rel0 <= 1e-10

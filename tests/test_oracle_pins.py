@@ -418,21 +418,26 @@ def _golden_rho():
     for line in open(os.path.join(GOLDEN, "convergence_factors.txt")):
         if not line.strip() or line.startswith("#"):
             continue
-        d, hier, order, om, rho, tol, src = line.split()
+        d, hier, order, om, coarsest, rho, tol, src = line.split()
         rows.append((int(d), O.DIAG if hier == "diag" else O.USUAL, int(order),
-                     [float(x) for x in om.split(",")], float(rho), float(tol), src))
+                     [float(x) for x in om.split(",")], int(coarsest), float(rho), float(tol), src))
     return rows
 
 
-def spectral_radius(dim, n, hier, order, omega):
+def spectral_radius(dim, n, hier, order, omega, coarsest=3, vcycle=None):
+    """Largest |eigenvalue| of the cycle's error propagation (f = 0), by
+    Arnoldi iteration on the cycle as a black box (the paper's "sparse
+    eigenvalue routine", Section 2.3).  vcycle: a stand-in for O.vcycle with
+    the same signature (a planted-mistake copy of the oracle)."""
     N = n ** dim
     f = O.grid(dim, n)
     sl = (slice(1, -1),) * dim
+    cyc = O.vcycle if vcycle is None else vcycle
 
     def mv(x):
         u = O.grid(dim, n)
         u[sl] = x.reshape((n,) * dim)
-        O.vcycle(f, u, hier=hier, order=order, omega=omega)
+        cyc(f, u, hier=hier, order=order, omega=omega, coarsest=coarsest)
         return u[sl].ravel().copy()
 
     A = LinearOperator((N, N), matvec=mv, dtype=np.float64)
@@ -440,12 +445,84 @@ def spectral_radius(dim, n, hier, order, omega):
     return float(np.max(np.abs(vals)))
 
 
-@pytest.mark.parametrize("row", _golden_rho(), ids=lambda r: f"{r[0]}d-{'diag' if r[1] == 0 else 'usual'}-o{r[2]}-{r[3]}")
+@pytest.mark.parametrize("row", _golden_rho(), ids=lambda r: f"{r[0]}d-{'diag' if r[1] == 0 else 'usual'}-o{r[2]}-{r[3]}-c{r[4]}")
 def test_convergence_factor_matches_paper_table(row):
-    dim, hier, order, omega, rho_paper, tol, _ = row
+    dim, hier, order, omega, coarsest, rho_paper, tol, _ = row
+    assert tol <= 0.10
     n = 63 if dim == 2 else 15
-    rho = spectral_radius(dim, n, hier, order, omega)
+    rho = spectral_radius(dim, n, hier, order, omega, coarsest)
     assert abs(rho - rho_paper) <= tol * rho_paper, (rho, rho_paper)
+
+
+def test_3d_coarsest_readings():
+    """The readings of the 17^3 analysis (Tables 2-3) that the golden rows
+    fix: the diagonal rows are met with a 7^3 coarsest grid and missed by more
+    than the tolerance with the deep hierarchy to 3^3 (Table 3's optimised
+    row); the conventional rows are met with the deep hierarchy and missed by
+    the two-grid cycle (Table 2's p = 1 row).  The product's default for 3D
+    stays the deep hierarchy to 3^3; its factors are the ones printed here."""
+    opt = [1.11, 1.42, 1.08, 0.99]
+    assert spectral_radius(3, 15, O.DIAG, 2, opt, 3) > 1.2 * 0.043
+    assert spectral_radius(3, 15, O.DIAG, 2, opt, 1) == pytest.approx(0.0468, abs=5e-4)
+    assert spectral_radius(3, 15, O.USUAL, 2, [1.0], 7) < 0.9 * 0.477
+
+
+# --------------------------------------------------------------------------
+# planted mistakes: a copy of the oracle with one plausible error breaks a
+# table pin by far more than its tolerance
+# --------------------------------------------------------------------------
+
+_MUTANTS = {
+    # p_r1 and p_r2 exchanged: the face-centre and corner sweeps of Eq. Erprolr / Eq. Erprolm
+    "swap_pr1_pr2": ("void orc_prolong3d_m2r(int n, double h, double pr1, double pr2,",
+                     "void orc_prolong3d_m2r(int n, double h, double pr2, double pr1,"),
+    # centre weight of Eq. Erest2r 4 -> 2 (still a mean-like stencil)
+    "g2r_centre_weight": ("rr[IDX2(n, i, j)] = (4.0 * rg[IDX2(n, i, j)]",
+                          "rr[IDX2(n, i, j)] = (2.0 * rg[IDX2(n, i, j)]"),
+    # sign of the residual term in Eq. Eajacr
+    "b2r_residual_sign": ("(j + 1) / 2)];\n            vr[IDX2(n, i, j)] = (-2.0 * p * h * h",
+                          "(j + 1) / 2)];\n            vr[IDX2(n, i, j)] = (2.0 * p * h * h"),
+    # p on the whole update of the green-only points (a damped sweep) instead of the residual term only
+    "r2g_p_on_whole_update": ("vr[IDX2(n, i, j + 1)];\n            vg[IDX2(n, i, j)] = (-p * h * h * rg[IDX2(n, i, j)] + s) / 4.0;",
+                              "vr[IDX2(n, i, j + 1)];\n            vg[IDX2(n, i, j)] = p * (-h * h * rg[IDX2(n, i, j)] + s) / 4.0;"),
+}
+
+
+def _mutant_vcycle(tmp_path, name):
+    import ctypes
+    import subprocess
+    src = open(os.path.join(os.path.dirname(O.__file__), "mg_oracle.c")).read()
+    old, new = _MUTANTS[name]
+    assert src.count(old) == 1, name
+    c, so = tmp_path / "mutant.c", tmp_path / "mutant.so"
+    c.write_text(src.replace(old, new))
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-shared", "-fPIC", str(c), "-o", str(so),
+                           "-lm"])
+    lib = ctypes.CDLL(str(so))
+    dp, i = ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    lib.orc_vcycle.argtypes = [i, i, i, i, i, dp, dp, dp]
+    lib.orc_vcycle.restype = i
+
+    def vcycle(f, u, *, hier, order, omega, coarsest):
+        om = np.zeros(4)
+        om[: len(omega)] = omega
+        ptr = lambda a: a.ctypes.data_as(dp)  # noqa: E731
+        assert lib.orc_vcycle(f.ndim, f.shape[0] - 2, hier, order, coarsest, ptr(om), ptr(f), ptr(u)) == 0
+        return u
+    return vcycle
+
+
+@pytest.mark.parametrize("name,row", [
+    ("swap_pr1_pr2", (3, O.DIAG, 2, [1.11, 1.42, 1.08, 0.99], 7, 0.043)),
+    ("g2r_centre_weight", (2, O.DIAG, 2, [1.0], 3, 0.099)),
+    ("b2r_residual_sign", (2, O.DIAG, 2, [1.0], 3, 0.099)),
+    ("r2g_p_on_whole_update", (2, O.DIAG, 2, [1.052], 3, 0.052)),
+])
+def test_planted_mistake_breaks_a_table_pin(tmp_path, name, row):
+    dim, hier, order, omega, coarsest, rho_paper = row
+    n = 63 if dim == 2 else 15
+    rho = spectral_radius(dim, n, hier, order, omega, coarsest, vcycle=_mutant_vcycle(tmp_path, name))
+    assert abs(rho - rho_paper) > 0.5 * rho_paper, (name, rho)
 
 
 def test_simultaneous_jacobi_reading_is_rejected():

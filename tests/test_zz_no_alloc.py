@@ -84,3 +84,74 @@ def test_refuses_sizes_beyond_static_limit_and_bad_arguments():
     assert _call(2, 63, 3, t, t, None, None) == N.MG_EINVAL
     assert _call(2, 64, 2, t, t, None, None) == N.MG_EINVAL
     assert _call(2, 63, 2, t, t, None, None, pitch=64) == N.MG_EINVAL
+
+
+def test_refuses_output_overlapping_an_input():
+    """r is written while neighbouring threads still read f and u, so an r
+    whose extent overlaps either is refused before anything is launched."""
+    n = 63
+    f, u = _inputs(2, n, 31)
+    big = torch.zeros(2 * (n + 2) ** 2, dtype=torch.float64, device=DEV)
+    assert _call(2, n, 2, f, u, f, None) == N.MG_EINVAL
+    assert _call(2, n, 2, f, u, u, None) == N.MG_EINVAL
+    # r starting inside u's extent
+    ub = big[: (n + 2) ** 2].view(n + 2, n + 2)
+    ub.copy_(u)
+    rb = big[(n + 2) ** 2 // 2: (n + 2) ** 2 // 2 + (n + 2) ** 2]
+    assert _call(2, n, 2, f, ub, rb, None) == N.MG_EINVAL
+
+
+def test_allocates_no_device_memory():
+    """After a first call (which may load the library's module on the device),
+    further calls leave the device's free memory and torch's reserved memory
+    unchanged."""
+    f, u = _inputs(2, 1023, 41)
+    r = torch.zeros_like(f)
+    n2 = torch.zeros(1, dtype=torch.float64, device=DEV)
+    assert _call(2, 1023, 2, f, u, r, n2) == N.MG_OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(DEV)
+    res0 = torch.cuda.memory_reserved(DEV)
+    for _ in range(5):
+        assert _call(2, 1023, 2, f, u, r, n2) == N.MG_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info(DEV)[0] == free0
+    assert torch.cuda.memory_reserved(DEV) == res0
+
+
+_FRESH = r"""
+import ctypes, sys, torch
+sys.path.insert(0, sys.argv[1])
+from paper_math_9907190_gb300 import _native as N
+from paper_math_9907190_gb300 import inputs as I
+dev = torch.device("cuda", 0)
+n = 255
+f = torch.from_numpy(I.uniform_f(2, n, 5)).to(dev)
+u = torch.from_numpy(I.zero_ring(I.uniform_f(2, n, 6))).to(dev)
+r = torch.zeros_like(f)
+n2 = torch.zeros(1, dtype=torch.float64, device=dev)
+s = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+P = lambda t: ctypes.c_void_p(t.data_ptr())
+for _ in range(2):
+    assert N.lib().mg_residual_noalloc(2, n, n + 2, 1.0 / (n + 1), 2, P(f), P(u), P(r), P(n2), s) == N.MG_OK
+torch.cuda.synchronize()
+print(repr(n2.item()))
+"""
+
+
+def test_works_in_a_fresh_process_without_any_context():
+    """No mg_create anywhere in the process: the entry point needs nothing
+    that a context would have set up."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    got = float(out.stdout.strip().splitlines()[-1])
+    n = 255
+    f = torch.from_numpy(I.uniform_f(2, n, 5)).to(DEV)
+    u = torch.from_numpy(I.zero_ring(I.uniform_f(2, n, 6))).to(DEV)
+    with Context(2, n) as c:
+        want = c.residual(f, u)
+    assert got == pytest.approx(want, rel=1e-12)
