@@ -161,6 +161,13 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *u, void *stream);
  * launch overlaps the tail of the one before.  DIAGMG_PDL=1 or 0 and
  * DIAGMG_PDL_MAX_BLOCKS=<blocks> (0: no limit), read at mg_create, override
  * that for any context.  The results are the same bit for bit.
+ * DIAGMG_CLUSTER=1, read at mg_create, runs the 2D pairs whose green side
+ * lies between 63 and 255 (127 with FP64 levels) and everything coarser in
+ * one launch of a thread-block cluster of 8 blocks that keeps those levels in
+ * distributed shared memory (the finest pair of a mixed solve stays outside
+ * it), instead of the per-pair kernels and the single coarse thread block
+ * (same arithmetic, term for term).  It is off by default: on GB300 it
+ * measured slower; mg_tune tries both.
  *   cycles_out  (host, nullable) cycles applied
  *   relres_out  (host, nullable) final relative residual
  *   history     (host, nullable, length max_cycles) relative residual after
@@ -256,9 +263,11 @@ mg_status mg_batch_status(const mg_batch *batch, int *status);
 
 /* Autotuning (no paper counterpart).  mg_tune times, on this context's own
  * buffers with the caller's f and u, the size cut-off below which whole
- * pairs/triples run in one thread block (whole V-cycles for each candidate)
- * and the tile shape of every pair kernel (each kernel alone, three shapes),
- * and keeps the fastest.  The choice is appended to the cache file
+ * pairs/triples run in one thread block and, in 2D, whether the middle pairs
+ * run in the thread-block cluster (whole V-cycles for each candidate; a
+ * candidate whose launch fails is never chosen), then the tile shape of every
+ * pair kernel outside them (each kernel alone, three shapes), and keeps the
+ * fastest.  The choice is appended to the cache file
  * `cache_path` (NULL: the file named by the environment variable
  * DIAGMG_TUNE_CACHE; neither: no file) as one JSON object per line keyed by
  * device name, dim, n, hierarchy, precision and batch size; a later mg_tune
@@ -266,7 +275,8 @@ mg_status mg_batch_status(const mg_batch *batch, int *status);
  * left zero (interior and ring).  measured_out (host, nullable): 1 if timed,
  * 0 if taken from the cache or nothing is tunable.  Synchronous.
  * mg_tune_info reports the cut-off (0 = default) and the tile class of each
- * pair kernel outside the thread block (FP64 levels: tiles of 0: 32x16 cells,
+ * pair kernel outside the thread block and the cluster, npairs of them (FP64
+ * levels: tiles of 0: 32x16 cells,
  * 1: 16x8, 2: 8x8; FP32 levels: strips of 0: 32, 1: 16, 2: 8 cell rows for
  * the prolongation and 16, 8, 4 for the restriction);
  * tiles_down / tiles_up need 32 entries.  mg_batch_tune does the same for

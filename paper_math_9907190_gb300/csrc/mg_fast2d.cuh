@@ -362,33 +362,19 @@ template <int NT> struct GPrefetch {
     }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const T> rg_in, A2<T> vg_out,
-                                                        const double *G, const int *done, Bt B) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *sm = reinterpret_cast<T *>(smraw);
-    const int prob = blockIdx.z;
-    if (stop(bt_done(done, prob, B))) return;
-    rg_in = bt_at(rg_in, prob, B);
-    vg_out = bt_at(vg_out, prob, B);
+// Pairs P.kc..P.K-1 and the exact coarsest solve in one block of 1024
+// threads, all in shared memory.  On entry the green residual of pair P.kc
+// is at sm + og_r[0] (ring and unused entries zero), every other level array
+// is zero and the coarsest inverse is at Gs; on return the green correction
+// of pair P.kc is at sm + og_v[0].  Restriction Eq. Erest2r, Eq. Erest2b;
+// prolongation Eq. Eajacr, Eq. Eajacb and the green-red sweep.
+template <typename T> __device__ __forceinline__ void cta_pairs_2d(const CoarsePlan2d &P, T *sm, const double *Gs) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    GPrefetch<1024> gp;
-    gp.load(G, P.ng, tid);
-    double *Gs = reinterpret_cast<double *>(smraw + P.gofs);
     // 32 x 32 thread grid: loops over boxes step by 32, no index division
     const int tx = tid & 31, ty = tid >> 5;
 #define CTA_FOR2(i, j, lo_i, hi_i, lo_j, hi_j) \
     for (int j = (lo_j) + ty; j <= (hi_j); j += 32) for (int i = (lo_i) + tx; i <= (hi_i); i += 32)
-    for (int q = tid; q < P.total; q += nt) sm[q] = T(0);
-    __syncthreads();
     const int npair = P.K - P.kc;
-    {   // load the green residual of pair kc
-        const int n = P.nk[0];
-        A2<T> g{sm + P.og_r[0], n + 2};
-        CTA_FOR2(i, j, 1, n, 1, n) g(i, j) = rg_in(i, j);
-    }
-    gp.store(Gs, P.ng, tid);
-    __syncthreads();
     for (int p = 0; p < npair; p++) {
         const int n = P.nk[p], nb = (n - 1) / 2;
         A2<T> g{sm + P.og_r[p], n + 2}, ee{sm + P.oe_r[p], nb + 2}, oo{sm + P.oo_r[p], nb + 2};
@@ -410,7 +396,7 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const
     {   // exact solve on the coarsest grid
         const int s = P.nk[npair], nn = s * s;
         A2<T> r{sm + P.og_r[npair], s + 2}, v{sm + P.og_v[npair], s + 2};
-        double *rv = Gs + P.ng;  // the right-hand side, dense
+        double *rv = const_cast<double *>(Gs) + P.ng;  // the right-hand side, dense
         for (int q = tid; q < nn; q += nt) rv[q] = (double)r(q % s + 1, q / s + 1);
         __syncthreads();
         for (int q = tid; q < nn; q += nt) {
@@ -447,12 +433,40 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const
         }
         __syncthreads();
     }
+#undef CTA_FOR2
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const T> rg_in, A2<T> vg_out,
+                                                        const double *G, const int *done, Bt B) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sm = reinterpret_cast<T *>(smraw);
+    const int prob = blockIdx.z;
+    if (stop(bt_done(done, prob, B))) return;
+    rg_in = bt_at(rg_in, prob, B);
+    vg_out = bt_at(vg_out, prob, B);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    GPrefetch<1024> gp;
+    gp.load(G, P.ng, tid);
+    double *Gs = reinterpret_cast<double *>(smraw + P.gofs);
+    const int tx = tid & 31, ty = tid >> 5;
+    for (int q = tid; q < P.total; q += nt) sm[q] = T(0);
+    __syncthreads();
+    {   // load the green residual of pair kc
+        const int n = P.nk[0];
+        A2<T> g{sm + P.og_r[0], n + 2};
+        for (int j = 1 + ty; j <= n; j += 32)
+            for (int i = 1 + tx; i <= n; i += 32) g(i, j) = rg_in(i, j);
+    }
+    gp.store(Gs, P.ng, tid);
+    __syncthreads();
+    cta_pairs_2d<T>(P, sm, Gs);
     {
         const int n = P.nk[0];
         A2<T> g{sm + P.og_v[0], n + 2};
-        CTA_FOR2(i, j, 1, n, 1, n) vg_out(i, j) = g(i, j);
+        for (int j = 1 + ty; j <= n; j += 32)
+            for (int i = 1 + tx; i <= n; i += 32) vg_out(i, j) = g(i, j);
     }
-#undef CTA_FOR2
 }
 
 }  // namespace mg

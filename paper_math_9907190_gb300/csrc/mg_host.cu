@@ -14,6 +14,7 @@
 #include "mg_stages.cuh"
 #include "mg_fast3d.cuh"
 #include "mg_fast2d.cuh"
+#include "mg_cluster.cuh"
 
 using namespace mg;
 
@@ -97,6 +98,14 @@ struct mg_ctx {
     int kc = 0;                 // first pair run by the coarse thread block
     CoarsePlan2d plan2d{};
     size_t plan_bytes = 0;
+    // 2D: the middle pairs kd..kc-1 in one thread-block cluster (distributed
+    // shared memory), its first block running pairs kc.. as the coarse block
+    bool cl = false;            // the cluster kernel is in use (kd < kc)
+    int kd = 0;                 // first pair of the coarse kernel (cluster: kd; else kc)
+    int cl_top = 0;             // largest green side of a distributed pair (0: no cluster; mg_tune, DIAGMG_CLUSTER)
+    bool cl_ok = true;          // clusters of this kernel can run on the device (checked by mg_create)
+    ClPlan2d plancl{};
+    size_t cl_bytes = 0;
     // mixed path: finest pair (2D) / triple (3D) fused with the next residual,
     // carried as a float-float pair (hi in the finest level's residual buffers,
     // double-buffered with r32b; lo in rlo; green pitch, in the pool)
@@ -418,7 +427,12 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
     } else {
         const int nb = a.nb;
         if (zm_use<T>(nb))
-            LAUNCH_B(TAG_DOWN, (k_m2b_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, zm_planes(nb), done);
+        {
+            if (zm_planes(nb) == 8)
+                LAUNCH_B(TAG_DOWN, (k_m2b_zm_3d<T, 8>), grid_zm(nb, 8), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
+            else
+                LAUNCH_B(TAG_DOWN, (k_m2b_zm_3d<T, 2>), grid_zm(nb, 2), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
+        }
         else
             LAUNCH_B(TAG_DOWN, (k_m2b_3d<T>), grid3(nb, nb, nb), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
     }
@@ -524,8 +538,13 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
     if (a.kind == KIND_MAG) {  // Eq. Emprolm, Eq. Emprolb
         const T cc = (T)(4.0 * om[0] * hk2);
         if (zm_use<T>(nb)) {
-            LAUNCH_B(TAG_UP, (k_b2m_ooo_zm_3d<T>), grid_zm(nb + 1, zm_planes(nb)), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, zm_planes(nb), done);
-            LAUNCH_B(TAG_UP, (k_b2m_eee_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, zm_planes(nb), done);
+#define MG_B2M(ZM)                                                                                                 \
+    LAUNCH_B(TAG_UP, (k_b2m_ooo_zm_3d<T, ZM>), grid_zm(nb + 1, ZM), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), \
+             a3<T>(a.v[1], a), nb, cc, done);                                                                        \
+    LAUNCH_B(TAG_UP, (k_b2m_eee_zm_3d<T, ZM>), grid_zm(nb, ZM), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a),    \
+             a3<T>(a.v[0], a), nb, cc, done)
+            if (zm_planes(nb) == 8) { MG_B2M(8); } else { MG_B2M(2); }
+#undef MG_B2M
         } else {
             LAUNCH_B(TAG_UP, (k_b2m_ooo_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, done);
             LAUNCH_B(TAG_UP, (k_b2m_eee_3d<T>), grid3(nb, nb, nb), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, done);
@@ -560,11 +579,53 @@ void coarse_g_slot(mg_ctx *c, int nn, int elems, int &gofs, int &ng) {
     c->plan_bytes = base + (size_t)(ng + nn) * sizeof(double);
 }
 
+// the largest dynamic shared memory a block may use on this device
+size_t smem_optin(const mg_ctx *c) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
+    return v > 0 ? (size_t)v : 48 * 1024;
+}
+
+// The cluster kernel's plan: pairs kd..kc-1 split by rows over CL2 blocks
+// (each array: its band of R rows, R = (side + 1) / 8, plus two halo rows),
+// then block 0's own plan (c->plan2d, c->plan_bytes).  Returns the dynamic
+// shared memory per block, 0 if the pairs do not fit.
+size_t plan_cl2d(mg_ctx *c, int kd, int kc) {
+    ClPlan2d &P = c->plancl;
+    P = ClPlan2d{};
+    P.nd = kc - kd;
+    int off = 0;
+    auto take = [&](int rows, int pitch) {
+        DistArr A{off, pitch, rows};
+        off += ((rows + 2) * pitch + 3) / 4 * 4;
+        return A;
+    };
+    for (int i = 0; i <= P.nd; i++) {
+        const int n = c->lv[2 * (kd + i)].side, R = (n + 1) / CL2, nb = (n - 1) / 2;
+        P.nk[i] = n;
+        P.gr[i] = take(R, n + 2);
+        P.gv[i] = take(R, n + 2);
+        if (i < P.nd) {
+            P.er[i] = take(R / 2, nb + 2); P.orr[i] = take(R / 2, nb + 2);
+            P.ev[i] = take(R / 2, nb + 2); P.ov[i] = take(R / 2, nb + 2);
+            const double hk = c->h * (double)(1 << (kd + i));
+            P.c2[i] = 2.0 * c->d.omega[0] * hk * hk;
+            P.c1[i] = c->d.omega[0] * hk * hk;
+        }
+    }
+    P.doff = (int)(((size_t)off * c->esz + 15) / 16 * 16 / c->esz);
+    P.cta = c->plan2d;
+    const size_t bytes = (size_t)P.doff * c->esz + c->plan_bytes;
+    return bytes <= smem_optin(c) ? bytes : 0;
+}
+
 void plan_fast2d(mg_ctx *c) {
     c->fast2d = c->d.dim == 2 && c->d.hierarchy == MG_DIAG && c->extra == 0;
     if (!c->fast2d) return;
-    // pairs whose green grid has side <= 63 (or the tuned cut-off) run in one thread block
-    const int cut = c->cut_side > 0 ? c->cut_side : 63;
+    // pairs whose green grid has side <= 63 (or the tuned cut-off; 31 below a
+    // cluster) run in one thread block
+    const bool want_cl = c->cl_ok && c->cl_top >= 15;
+    const int cut = c->cut_side > 0 ? c->cut_side : (want_cl ? 31 : 63);
     int kc = 0;
     while (kc < c->K && c->lv[2 * kc].side > cut) kc++;
     c->kc = kc;
@@ -590,6 +651,21 @@ void plan_fast2d(mg_ctx *c) {
     }
     P.total = off;
     coarse_g_slot(c, P.nk[npair] * P.nk[npair], off, P.gofs, P.ng);
+    // pairs above the coarse block with green side <= cl_top (at least 15 and
+    // block 0's first pair at least 7, so that every band has rows) in the
+    // cluster; the finest pair of the fused mixed solve stays outside it
+    c->cl = false;
+    c->kd = kc;
+    c->cl_bytes = 0;
+    if (want_cl && kc < c->K && c->lv[2 * kc].side >= 7) {
+        int kd = 0;
+        while (kd < kc && (c->lv[2 * kd].side > c->cl_top || (kd == 0 && c->rr))) kd++;
+        while (kd < kc && c->lv[2 * (kc - 1)].side >= 15) {
+            const size_t bytes = plan_cl2d(c, kd, kc);
+            if (bytes) { c->cl = true; c->kd = kd; c->cl_bytes = bytes; break; }
+            kd++;  // the largest pair does not fit in shared memory: leave it to the pair kernels
+        }
+    }
 }
 
 // finest residual for every configuration: column (2D) / plane (3D) marching,
@@ -741,15 +817,23 @@ int up_pair(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStream_t 
     return 0;
 }
 
-template <typename T> void vcycle_fast2d(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
-    for (int k = 0; k < c->kc; k++) down_pair<T>(c, k, tile_dn(c, k), done, s, false);
-    {
-        const Level &g = c->lv[2 * c->kc];
+// the coarse kernel of a 2D cycle: pairs kd.. in the cluster kernel, or
+// pairs kc.. in the coarse thread block
+template <typename T> void launch_coarse2d(mg_ctx *c, const int *done, cudaStream_t s) {
+    const Level &g = c->lv[2 * c->kd];
+    if (c->cl)
+        LAUNCH_SMEM_B(TAG_COARSE, (k_coarse_cl_2d<T>), dim3(CL2, 1, 1), 1024, c->cl_bytes, c->plancl,
+                      a2<const T>(g.r[0], g), a2<T>(g.v[0], g), c->G, done);
+    else
         LAUNCH_SMEM_B(TAG_COARSE, (k_coarse_cta_2d<T>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan2d,
                       a2<const T>(g.r[0], g), a2<T>(g.v[0], g), c->G, done);
-    }
-    for (int k = c->kc - 1; k >= 0; k--) up_pair<T>(c, k, tile_up(c, k), u, done, s);
-    if (c->kc == 0) {  // the whole hierarchy ran in the coarse block: apply v to u
+}
+
+template <typename T> void vcycle_fast2d(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
+    for (int k = 0; k < c->kd; k++) down_pair<T>(c, k, tile_dn(c, k), done, s, false);
+    launch_coarse2d<T>(c, done, s);
+    for (int k = c->kd - 1; k >= 0; k--) up_pair<T>(c, k, tile_up(c, k), u, done, s);
+    if (c->kd == 0) {  // the whole hierarchy ran in the coarse kernel: apply v to u
         const Level &l0 = c->lv[0];
         const int n = c->d.n;
         LAUNCH_B(TAG_FINEST_UP, (k_add_axis<T>), grid2(n, n), B2, (const T *)l0.v[0], l0.pitch, l0.rows, n, 2, u,
@@ -823,16 +907,12 @@ void launch_absmax(mg_ctx *c, const Level &l, const int *done, cudaStream_t s) {
 // and the finest pair fused with u += v and the next residual; returns the
 // number of norm partial sums written per problem
 int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
-    for (int k = 0; k < c->kc; k++) down_pair<float>(c, k, tile_dn(c, k), done, s, true);
-    {
-        const Level &g = c->lv[2 * c->kc];
-        LAUNCH_SMEM_B(TAG_COARSE, (k_coarse_cta_2d<float>), dim3(1, 1, 1), 1024, c->plan_bytes, c->plan2d,
-                      a2<const float>(g.r[0], g), a2<float>(g.v[0], g), c->G, done);
-    }
+    for (int k = 0; k < c->kd; k++) down_pair<float>(c, k, tile_dn(c, k), done, s, true);
+    launch_coarse2d<float>(c, done, s);
     // the blue level of the finest pair (pair 1's v) also gets its bound on |v|:
     // in the streaming kernel that forms it, else by a separate pass
-    const bool vfused = c->kc >= 2 && tile_up(c, 1) < 3;
-    for (int k = c->kc - 1; k >= 1; k--) {
+    const bool vfused = c->kd >= 2 && tile_up(c, 1) < 3;
+    for (int k = c->kd - 1; k >= 1; k--) {
         if (k == 1 && vfused) launch_up_ff(c, 1, tile_up(c, 1), nullptr, done, s, false, c->ctl);
         else up_pair<float>(c, k, tile_up(c, k), u, done, s);
     }
@@ -895,7 +975,9 @@ int vcycle_rr3(mg_ctx *c, double *u, const int *done, cudaStream_t s, CtrlFuse c
 }
 
 template <typename T> cudaError_t set_smem_attrs(const mg_ctx *c) {
-    cudaError_t e = cudaFuncSetAttribute(k_coarse_cta_2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
+    // the limit is a property of the function, shared by every context (and
+    // every plan a later mg_tune may choose): the device's maximum
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_cta_2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin(c));
 #define MG_UP_ATTR(TA, TB)                                                                                         \
     if (e == cudaSuccess)                                                                                          \
         e = cudaFuncSetAttribute(k_up_pair_2d<T, true, TA, TB>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
@@ -907,7 +989,25 @@ template <typename T> cudaError_t set_smem_attrs(const mg_ctx *c) {
     MG_UP_ATTR(16, 8)
     MG_UP_ATTR(8, 8)
 #undef MG_UP_ATTR
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_coarse_cl_2d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin(c));
     return e;
+}
+
+// can a cluster of the coarse kernel, with the planned shared memory, run on
+// this device?  If not, the coarse thread block takes its pairs
+template <typename T> void check_cluster2d(mg_ctx *c) {
+    if (!c->cl) return;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(CL2, 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = c->cl_bytes;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, k_coarse_cl_2d<T>, &cfg) != cudaSuccess || ncl < 1) {
+        cudaGetLastError();
+        c->cl_ok = false;
+        plan_fast2d(c);
+    }
 }
 
 template <typename T>
@@ -1045,12 +1145,18 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
         c->r32b = p; p += r32_bytes;
     }
     c->max_blocks = residual_blocks(c);
+    {
+        // 1: the middle pairs in the cluster kernel (measured slower than the
+        // pair kernels and the coarse block on GB300, so off by default)
+        const char *ec = std::getenv("DIAGMG_CLUSTER");
+        if (ec && ec[0] == '1') c->cl_top = 255;
+    }
     plan_fast2d(c);
     plan_fast3d(c);
     if (c->fast3d) {
         cudaError_t e = d->precision == MG_FP64
-            ? cudaFuncSetAttribute(k_coarse_cta_3d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes)
-            : cudaFuncSetAttribute(k_coarse_cta_3d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->plan_bytes);
+            ? cudaFuncSetAttribute(k_coarse_cta_3d<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin(c))
+            : cudaFuncSetAttribute(k_coarse_cta_3d<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_optin(c));
         const int g64 = (int)sizeof(Green3Smem<double>), g32 = (int)sizeof(Green3Smem<float>);
         const int gs = (int)sizeof(GreenSSmem);
 #define MG_GFF_ATTR(MODE, VU) \
@@ -1082,6 +1188,8 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
             mg_destroy(c);
             return cuda_fail(e, "mg_create shared-memory attributes");
         }
+        if (d->precision == MG_FP64) check_cluster2d<double>(c);
+        else check_cluster2d<float>(c);
     }
     if (d->order == 4 &&
         cudaMalloc(&c->ft, sizeof(double) * (size_t)d->pitch * (d->n + 2) * (d->dim == 3 ? (size_t)(d->n + 2) : 1)) !=
@@ -1328,7 +1436,15 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     c->g_prefix_kernels = c->launches - l0;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
+    {   // a launch that failed (and so invalidated the capture) ends it here
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) { c->capturing = false; return cuda_fail(le, "solve capture (prefix)"); }
+    }
     CK(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
+    if (st != cudaStreamCaptureStatusActive) {
+        c->capturing = false;
+        return cuda_fail(cudaErrorStreamCaptureInvalidated, "solve capture (prefix)");
+    }
     cudaGraphNodeParams cp{};
     cp.type = cudaGraphNodeTypeConditional;
     cp.conditional.handle = loop;
@@ -1359,7 +1475,14 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     }
     if (!fuse) launch_ctrl(c, np2, 0, loop, 1, s2);
     c->g_body_kernels = c->launches - l1;
-    CK(cudaStreamEndCapture(s2, &body));
+    {
+        const cudaError_t le = cudaGetLastError();
+        const cudaError_t ee = cudaStreamEndCapture(s2, &body);
+        if (le != cudaSuccess || ee != cudaSuccess) {
+            c->capturing = false;
+            return cuda_fail(le != cudaSuccess ? le : ee, "solve capture (cycle)");
+        }
+    }
     if (c->rr) {  // the carried residual ignores the rounding of u: report a direct one
         const long long l2 = c->launches;
         const int np3 = launch_res_rr(c, f, u, nullptr, s, false);
@@ -1780,12 +1903,12 @@ std::string tune_key(const mg_ctx *c) {
     cudaGetDeviceProperties(&pr, c->dev);
     char buf[400];
     // "kernels": the version of the tunable kernel set (classes change meaning with it)
-    std::snprintf(buf, sizeof buf, "\"kernels\": 2, \"device\": \"%s\", \"dim\": %d, \"n\": %d, \"hier\": %d, \"prec\": %d, \"nprob\": %d",
+    std::snprintf(buf, sizeof buf, "\"kernels\": 3, \"device\": \"%s\", \"dim\": %d, \"n\": %d, \"hier\": %d, \"prec\": %d, \"nprob\": %d",
                   pr.name, c->d.dim, c->d.n, c->d.hierarchy, c->d.precision, c->nprob);
     return buf;
 }
 
-int ntiles(const mg_ctx *c) { return c->fast2d ? c->kc : 0; }
+int ntiles(const mg_ctx *c) { return c->fast2d ? c->kd : 0; }
 
 // one JSON object per line: {<key>, "cut": C, "down": [..], "up": [..]}
 bool cache_lookup(const char *path, const std::string &key, mg_ctx *c) {
@@ -1798,6 +1921,8 @@ bool cache_lookup(const char *path, const std::string &key, mg_ctx *c) {
         const char *q = std::strstr(line, "\"cut\": ");
         if (!q) continue;
         int cut = std::atoi(q + 7);
+        const char *qc = std::strstr(line, "\"cl\": ");
+        if (qc) c->cl_top = std::atoi(qc + 6);
         int dn[32], upv[32], ndn = 0, nup = 0;
         auto read_list = [&](const char *name, int *out, int &cnt) {
             const char *r = std::strstr(line, name);
@@ -1829,7 +1954,7 @@ bool cache_lookup(const char *path, const std::string &key, mg_ctx *c) {
 void cache_append(const char *path, const std::string &key, const mg_ctx *c) {
     FILE *fp = std::fopen(path, "a");
     if (!fp) return;
-    std::fprintf(fp, "{%s, \"cut\": %d, \"down\": [", key.c_str(), c->cut_side);
+    std::fprintf(fp, "{%s, \"cut\": %d, \"cl\": %d, \"down\": [", key.c_str(), c->cut_side, c->cl_top);
     for (int k = 0; k < ntiles(c); k++) std::fprintf(fp, "%s%d", k ? ", " : "", c->tile_dn[k]);
     std::fprintf(fp, "], \"up\": [");
     for (int k = 0; k < ntiles(c); k++) std::fprintf(fp, "%s%d", k ? ", " : "", c->tile_up[k]);
@@ -1850,7 +1975,10 @@ mg_status tune_measure(mg_ctx *c, const double *f, double *u, cudaStream_t s) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // the time of fn, or +inf when a launch of it failed (e.g. a shared-
+    // memory plan this device cannot give): never chosen
     auto timeit = [&](auto fn, int reps) {
+        cudaGetLastError();
         fn();
         cudaEventRecord(e0, s);
         for (int q = 0; q < reps; q++) fn();
@@ -1858,7 +1986,7 @@ mg_status tune_measure(mg_ctx *c, const double *f, double *u, cudaStream_t s) {
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        return ms / reps;
+        return cudaGetLastError() == cudaSuccess ? ms / reps : 1e30f;
     };
     auto vcyc = [&]() {
         if (fp64) vcycle_t<double>(c, f, u, nullptr, true, s);
@@ -1866,18 +1994,23 @@ mg_status tune_measure(mg_ctx *c, const double *f, double *u, cudaStream_t s) {
     };
     vcyc();  // realistic contents in every level buffer
     std::vector<int> cuts = c->fast2d ? std::vector<int>{15, 31, 63} : std::vector<int>{7, 15};
-    int best_cut = 0;
+    // 2D: with the middle pairs in the cluster kernel (largest side 255) and without
+    std::vector<int> tops = c->fast2d && c->cl_ok ? std::vector<int>{0, 255} : std::vector<int>{c->cl_top};
+    int best_cut = 0, best_top = c->cl_top;
     float best = 1e30f;
-    for (int cut : cuts) {
-        c->cut_side = cut;
-        replan(c);
-        const float ms = timeit(vcyc, 5);
-        if (ms < best) { best = ms; best_cut = cut; }
-    }
+    for (int top : tops)
+        for (int cut : cuts) {
+            c->cl_top = top;
+            c->cut_side = cut;
+            replan(c);
+            const float ms = timeit(vcyc, 5);
+            if (ms < best) { best = ms; best_cut = cut; best_top = top; }
+        }
+    c->cl_top = best_top;
     c->cut_side = best_cut;
     replan(c);
     if (c->fast2d) {
-        for (int k = 0; k < c->kc && k < 32; k++) {
+        for (int k = 0; k < c->kd && k < 32; k++) {
             float bd = 1e30f, bu = 1e30f;
             const int ncls = fp64 ? 3 : NCLS_FP32;
             for (int cls = 0; cls < ncls; cls++) {

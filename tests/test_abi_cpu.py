@@ -128,7 +128,7 @@ def test_every_context_kernel_waits_before_touching_memory():
     allowed = re.compile(r"^(__shared__|extern __shared__|constexpr|const int|MG_IDX2|UpSmem|GreenSSmem|Green3Smem"
                          r"|T \*sm = reinterpret_cast)")
     seen = 0
-    for name in ("mg_stages.cuh", "mg_fast2d.cuh", "mg_fast3d.cuh"):
+    for name in ("mg_stages.cuh", "mg_fast2d.cuh", "mg_fast3d.cuh", "mg_cluster.cuh"):
         for kern, head in _kernel_heads(os.path.join(csrc, name)):
             seen += 1
             assert len(head) <= 12, (kern, head)

@@ -437,3 +437,30 @@ def test_mixed_warm_start(dim, n):
         r2 = c.residual(f, uw)
         f2 = c.residual(f, torch.zeros_like(uw))
         assert math.sqrt(r2 / f2) <= 1.02e-10
+
+
+@pytest.mark.parametrize("n,prec,tol", [(255, "fp64", 1e-13), (4095, "fp64", 1e-13), (1023, "mixed", 2e-6),
+                                        (127, "mixed", 2e-6)])
+def test_cluster_and_block_coarse_kernels_agree(n, prec, tol):
+    """The middle pairs in one thread-block cluster (distributed shared
+    memory, the default) and the same pairs in per-pair kernels plus the
+    single coarse thread block (DIAGMG_CLUSTER=0) compute the same arithmetic:
+    the same cycle count and, point by point, the same iterate up to the
+    rounding of fused multiply-adds."""
+    import os
+    f = T(I.uniform_f(2, n, 81))
+    outs = []
+    for flag in ("1", "0"):
+        old = os.environ.get("DIAGMG_CLUSTER")
+        os.environ["DIAGMG_CLUSTER"] = flag
+        try:
+            with Context(2, n, precision=prec, omega=(1.052,)) as c:
+                u, it, rel, _ = c.solve(f, rtol=1e-300, max_cycles=4, raise_on_fail=False)
+                outs.append((H(u), it))
+        finally:
+            if old is None:
+                os.environ.pop("DIAGMG_CLUSTER")
+            else:
+                os.environ["DIAGMG_CLUSTER"] = old
+    assert outs[0][1] == outs[1][1] == 4
+    assert_iterate(outs[0][0], outs[1][0], tol)
