@@ -366,11 +366,9 @@ __global__ void __launch_bounds__(256) k_r2m_zm_3d(Red3<const T> red, Mag3<T> ma
     }
 }
 
-// Eq. Erblu (magenta -> blue), cells [1, nb]^3; blue shares the coset layout.
-// ZM planes per thread: every input of them is loaded before the first
-// value is computed (the loads are independent and in flight together)
-template <typename T, int ZM>
-__global__ void __launch_bounds__(256) k_m2b_zm_3d(Mag3<const T> mag, A3<T> blue, int nb, const int *done, Bt B) {
+// Eq. Erblu (magenta -> blue), cells [1, nb]^3; blue shares the coset layout
+template <typename T>
+__global__ void __launch_bounds__(256) k_m2b_zm_3d(Mag3<const T> mag, A3<T> blue, int nb, int zm, const int *done, Bt B) {
     const int prob = bt_prob(B);
     if (stop(bt_done(done, prob, B))) return;
     mag = bt_at(mag, prob, B);
@@ -378,72 +376,62 @@ __global__ void __launch_bounds__(256) k_m2b_zm_3d(Mag3<const T> mag, A3<T> blue
     const int P = mag.eee.pitch;
     const size_t Q = (size_t)P * mag.eee.rows;
     ZmIdx z;
-    if (!zm_cell(z, 1, nb, ZM, P, Q, B)) return;
-    const T *__restrict__ ooo = mag.ooo.p;
-    const T *__restrict__ eee = mag.eee.p;
-    const int np = z.c1 - z.c0;
-    // the four centres of a plane: quad[k] is plane c0 - 1 + k
+    if (!zm_cell(z, 1, nb, zm, P, Q, B)) return;
+    const T *ooo = mag.ooo.p;
+    size_t i = z.i;
+    // the four centres of plane c-1 (a sum carried from the previous plane)
     auto quad = [&](size_t k) { return (ooo[k - P - 1] + ooo[k - P]) + (ooo[k - 1] + ooo[k]); };
-    T qd[ZM + 1], ec[ZM];
-#pragma unroll
-    for (int k = 0; k <= ZM; k++) qd[k] = k <= np ? quad(z.i + (size_t)k * Q - Q) : T(0);
-#pragma unroll
-    for (int k = 0; k < ZM; k++) ec[k] = k < np ? eee[z.i + (size_t)k * Q] : T(0);
-#pragma unroll
-    for (int k = 0; k < ZM; k++)
-        if (k < np) blue.p[z.i + (size_t)k * Q] = (T(8) * ec[k] + (qd[k] + qd[k + 1])) * T(0.0625);
+    T lower = quad(i - Q);
+    for (int c = z.c0; c < z.c1; c++, i += Q) {
+        const T upper = quad(i);
+        blue.p[i] = (T(8) * mag.eee.p[i] + (lower + upper)) * T(0.0625);
+        lower = upper;
+    }
 }
 
 // Eq. Emprolm: magenta centres from the 8 blue corners, cells [0, nb]^3
-template <typename T, int ZM>
+template <typename T>
 __global__ void __launch_bounds__(256) k_b2m_ooo_zm_3d(A3<const T> blue, A3<const T> rooo, A3<T> vooo, int nb, T cc,
-                                                       const int *done, Bt B) {
+                                                       int zm, const int *done, Bt B) {
     const int prob = bt_prob(B);
     if (stop(bt_done(done, prob, B))) return;
     blue = bt_at(blue, prob, B); rooo = bt_at(rooo, prob, B); vooo = bt_at(vooo, prob, B);
     const int P = rooo.pitch;
     const size_t Q = (size_t)P * rooo.rows;
     ZmIdx z;
-    if (!zm_cell(z, 0, nb, ZM, P, Q, B)) return;
-    const T *__restrict__ bl = blue.p;
-    const T *__restrict__ rr = rooo.p;
-    const int np = z.c1 - z.c0;
-    // the four corners of a plane: quad[k] is plane c0 + k
+    if (!zm_cell(z, 0, nb, zm, P, Q, B)) return;
+    const T *bl = blue.p;
+    size_t i = z.i;
+    // the four corners of plane c+1 become those of plane c at the next step
     auto quad = [&](size_t k) { return (bl[k] + bl[k + 1]) + (bl[k + P] + bl[k + P + 1]); };
-    T qd[ZM + 1], rc[ZM];
-#pragma unroll
-    for (int k = 0; k <= ZM; k++) qd[k] = k <= np ? quad(z.i + (size_t)k * Q) : T(0);
-#pragma unroll
-    for (int k = 0; k < ZM; k++) rc[k] = k < np ? rr[z.i + (size_t)k * Q] : T(0);
-#pragma unroll
-    for (int k = 0; k < ZM; k++)
-        if (k < np) vooo.p[z.i + (size_t)k * Q] = ((qd[k] + qd[k + 1]) - cc * rc[k]) * T(0.125);
+    T lower = quad(i);
+    for (int c = z.c0; c < z.c1; c++, i += Q) {
+        const T upper = quad(i + Q);
+        vooo.p[i] = ((lower + upper) - cc * rooo.p[i]) * T(0.125);
+        lower = upper;
+    }
 }
 
 // Eq. Emprolb: blue corners refined from the 8 new centres, cells [1, nb]^3
-template <typename T, int ZM>
+template <typename T>
 __global__ void __launch_bounds__(256) k_b2m_eee_zm_3d(A3<const T> vooo, A3<const T> reee, A3<T> veee, int nb, T cc,
-                                                       const int *done, Bt B) {
+                                                       int zm, const int *done, Bt B) {
     const int prob = bt_prob(B);
     if (stop(bt_done(done, prob, B))) return;
     vooo = bt_at(vooo, prob, B); reee = bt_at(reee, prob, B); veee = bt_at(veee, prob, B);
     const int P = reee.pitch;
     const size_t Q = (size_t)P * reee.rows;
     ZmIdx z;
-    if (!zm_cell(z, 1, nb, ZM, P, Q, B)) return;
-    const T *__restrict__ o = vooo.p;
-    const T *__restrict__ rr = reee.p;
-    const int np = z.c1 - z.c0;
-    // the four centres of a plane: quad[k] is plane c0 - 1 + k
+    if (!zm_cell(z, 1, nb, zm, P, Q, B)) return;
+    const T *o = vooo.p;
+    size_t i = z.i;
     auto quad = [&](size_t k) { return (o[k - P - 1] + o[k - P]) + (o[k - 1] + o[k]); };
-    T qd[ZM + 1], rc[ZM];
-#pragma unroll
-    for (int k = 0; k <= ZM; k++) qd[k] = k <= np ? quad(z.i + (size_t)k * Q - Q) : T(0);
-#pragma unroll
-    for (int k = 0; k < ZM; k++) rc[k] = k < np ? rr[z.i + (size_t)k * Q] : T(0);
-#pragma unroll
-    for (int k = 0; k < ZM; k++)
-        if (k < np) veee.p[z.i + (size_t)k * Q] = ((qd[k] + qd[k + 1]) - cc * rc[k]) * T(0.125);
+    T lower = quad(i - Q);  // carried from plane to plane
+    for (int c = z.c0; c < z.c1; c++, i += Q) {
+        const T upper = quad(i);
+        veee.p[i] = ((lower + upper) - cc * reee.p[i]) * T(0.125);
+        lower = upper;
+    }
 }
 
 // Eq. Erprolr and its cyclic permutations: red face centres, cells [0, nb]^3

@@ -427,12 +427,7 @@ template <typename T> void launch_restrict(mg_ctx *c, int l, const int *done, cu
     } else {
         const int nb = a.nb;
         if (zm_use<T>(nb))
-        {
-            if (zm_planes(nb) == 8)
-                LAUNCH_B(TAG_DOWN, (k_m2b_zm_3d<T, 8>), grid_zm(nb, 8), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
-            else
-                LAUNCH_B(TAG_DOWN, (k_m2b_zm_3d<T, 2>), grid_zm(nb, 2), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
-        }
+            LAUNCH_B(TAG_DOWN, (k_m2b_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, zm_planes(nb), done);
         else
             LAUNCH_B(TAG_DOWN, (k_m2b_3d<T>), grid3(nb, nb, nb), B2, mag3v<const T>(a.r, a), a3<T>(b.r[0], b), nb, done);
     }
@@ -538,13 +533,8 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
     if (a.kind == KIND_MAG) {  // Eq. Emprolm, Eq. Emprolb
         const T cc = (T)(4.0 * om[0] * hk2);
         if (zm_use<T>(nb)) {
-#define MG_B2M(ZM)                                                                                                 \
-    LAUNCH_B(TAG_UP, (k_b2m_ooo_zm_3d<T, ZM>), grid_zm(nb + 1, ZM), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), \
-             a3<T>(a.v[1], a), nb, cc, done);                                                                        \
-    LAUNCH_B(TAG_UP, (k_b2m_eee_zm_3d<T, ZM>), grid_zm(nb, ZM), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a),    \
-             a3<T>(a.v[0], a), nb, cc, done)
-            if (zm_planes(nb) == 8) { MG_B2M(8); } else { MG_B2M(2); }
-#undef MG_B2M
+            LAUNCH_B(TAG_UP, (k_b2m_ooo_zm_3d<T>), grid_zm(nb + 1, zm_planes(nb)), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, zm_planes(nb), done);
+            LAUNCH_B(TAG_UP, (k_b2m_eee_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, zm_planes(nb), done);
         } else {
             LAUNCH_B(TAG_UP, (k_b2m_ooo_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, done);
             LAUNCH_B(TAG_UP, (k_b2m_eee_3d<T>), grid3(nb, nb, nb), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, done);
