@@ -73,8 +73,12 @@ enum { MG_FP64 = 0, MG_MIXED = 1 };   /* precision of the level arithmetic */
  *              with one FP32 V-cycle per FP64 residual).  The residual norms
  *              square FP32 values, so MG_MIXED wants residual and right-hand
  *              side values between about 1e-18 and 1e18 in magnitude.
- *   coarsest   interior side of the coarsest axis grid: 1, 3 or 7 (2D), 1 or
- *              3 (3D), <= n.  It is solved exactly.
+ *   coarsest   interior side of the coarsest axis grid: 1, 3 or 7, <= n.  It is
+ *              solved exactly.  In 3D a 7^3 coarsest grid (the grid under
+ *              which the paper's 17^3 convergence factors of the diagonal
+ *              cycle are reproduced) runs every level with the per-stage
+ *              kernels and a dense inverse in global memory, and its mixed
+ *              solves take a direct residual every cycle.
  *   omega      over-relaxation weights multiplying the residual term of the
  *              Jacobi sweeps.  2D: {p} (Eq. Eajacr, Eq. Eajacb); 3D diagonal:
  *              {p_m, p_r1, p_r2, p_g} (Eq. Emprolm .. Eq. Egprolr);

@@ -661,7 +661,9 @@ void plan_fast2d(mg_ctx *c) {
 // finest residual for every configuration: column (2D) / plane (3D) marching,
 // FP64 stencil, level-precision output, FP32 squares in mixed precision
 void plan_fast3d(mg_ctx *c) {
-    c->fast3d = c->d.dim == 3 && c->d.hierarchy == MG_DIAG;
+    // the coarse block keeps the coarsest inverse in shared memory: 3^3 grids
+    // at most (a 7^3 coarsest grid runs with per-stage kernels and k_coarse)
+    c->fast3d = c->d.dim == 3 && c->d.hierarchy == MG_DIAG && c->d.coarsest <= 3;
     if (!c->fast3d) return;
     const int cut = c->cut_side > 0 ? c->cut_side : 15;
     int kc = 0;
@@ -1043,7 +1045,7 @@ bool valid_desc(const mg_desc *d) {
     const int m = log2_side(d->n), cm = log2_side(d->coarsest);
     if (m < 2 || cm < 1 || cm > m) return false;
     if (d->dim == 2 && d->coarsest > 7) return false;
-    if (d->dim == 3 && d->coarsest > 3) return false;
+    if (d->dim == 3 && d->coarsest > 7) return false;
     if (d->pitch < d->n + 2) return false;
     if (d->hierarchy != MG_DIAG && d->hierarchy != MG_USUAL) return false;
     if (d->order != 2 && d->order != 4) return false;
@@ -1116,7 +1118,10 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     size_t total = 0;
     for (auto &l : c->lv) total += (size_t)l.ncos * 2 * ((l.len * c->esz + 255) / 256 * 256);
     // fused update + residual of the mixed 2D diagonal solve (needs at least one pair outside the coarse block)
-    c->rr = d->hierarchy == MG_DIAG && d->precision == MG_MIXED && d->order == 2 && d->n > (d->dim == 2 ? 63 : 15);
+    // (3D with a 7^3 coarsest grid runs every level with per-stage kernels:
+    // its inverse does not fit the coarse block, on which the fused path rests)
+    c->rr = d->hierarchy == MG_DIAG && d->precision == MG_MIXED && d->order == 2 && d->n > (d->dim == 2 ? 63 : 15) &&
+            !(d->dim == 3 && d->coarsest > 3);
     c->rr_alloc = c->rr;
     const size_t r32_bytes = c->rr ? (c->lv[0].len * 4 + 255) / 256 * 256 : 0;
     total += 2 * r32_bytes;

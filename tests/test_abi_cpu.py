@@ -39,7 +39,7 @@ def _desc(**kw):
 @pytest.mark.parametrize("bad", [
     dict(dim=1), dict(dim=4), dict(n=64), dict(n=1), dict(n=0), dict(n=-1), dict(pitch=64),
     dict(hierarchy=2), dict(order=3), dict(precision=7), dict(coarsest=2), dict(coarsest=127),
-    dict(dim=3, n=15, pitch=17, coarsest=7), dict(coarsest=15),
+    dict(dim=3, n=15, pitch=17, coarsest=15), dict(coarsest=15), dict(dim=3, n=31, pitch=33, coarsest=5),
 ])
 def test_create_rejects_invalid_descriptions(lib, bad):
     h = ctypes.c_void_p()
