@@ -21,7 +21,8 @@
  *     keeps a caller pointer after a call returns.  All workspace (level
  *     buffers, norms, control words) is allocated by mg_create and freed by
  *     mg_destroy; no other call allocates device memory, except the first
- *     mg_solve_host of a context (its device copies of f and u).
+ *     mg_solve_host of a context (its device copies of f and u) and the
+ *     first mg_set_gamma with gamma > 1 (its coarse-level work arrays).
  *   - Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
  *     default stream).  Calls are stream-ordered; a call that returns a value
  *     to a host pointer synchronises that stream before returning.
@@ -210,6 +211,22 @@ mg_status mg_set_omega(mg_ctx *ctx, const double *omega);
  * mg_vcycle, mg_solve and mg_rho.  MG_EINVAL unless 0 <= extra <= 64 and,
  * for extra > 0, the context is a single 2D diagonal problem. */
 mg_status mg_set_sweeps(mg_ctx *ctx, int extra);
+
+/* Gamma-cycles (W-cycles for gamma = 2) of the 2D diagonal hierarchy, the
+ * other extension the paper's conclusion (Section 5) leaves open.  In the
+ * cycle of each pair the coarse problem on its blue grid -- the next pair's
+ * green grid, an axis grid with the 5-point Laplacian at its spacing -- is
+ * approximated by `gamma` cycles of the next pair from a zero correction,
+ * each after the first on the residual of the corrections accumulated so far
+ * (the coarsest grid is solved exactly).  gamma = 1 (the default) is the
+ * paper's V-cycle.  gamma > 1 runs every level with per-stage kernels
+ * (combined with mg_set_sweeps if set) and applies to mg_vcycle, mg_solve and
+ * mg_rho; the number of visits of a level grows as gamma^depth.  The first
+ * call with gamma > 1 allocates, per green level below the finest, a kept
+ * residual and an accumulator (MG_ENOMEM if that fails).  MG_EINVAL unless
+ * 1 <= gamma <= 4 and, for gamma > 1, the context is a single 2D diagonal
+ * problem. */
+mg_status mg_set_gamma(mg_ctx *ctx, int gamma);
 
 /* Convergence factor of the context's V-cycle (the paper's rho, Tables 1-3:
  * the slowest decay of the error) by power iteration on its error

@@ -657,6 +657,92 @@ int orc_vcycle_sweeps(int dim, int n, int hier, int order, int coarsest, const d
     return rc;
 }
 
+/* ------------------------------------------------------------------------ */
+/* W-cycles (gamma-cycles) of the 2D diagonal hierarchy: the extension the   */
+/* paper's conclusion (Section 5) leaves open.                                */
+/* ------------------------------------------------------------------------ */
+
+/* 5-point residual on an axis grid of side n and spacing h: out = r - L v */
+static void green_residual(int n, double h, const double *r, const double *v, double *out)
+{
+    ORC_PAR
+    for (int j = 1; j <= n; j++)
+        for (int i = 1; i <= n; i++) {
+            double lap = (v[IDX2(n, i + 1, j)] + v[IDX2(n, i - 1, j)] + v[IDX2(n, i, j + 1)] +
+                          v[IDX2(n, i, j - 1)] - 4.0 * v[IDX2(n, i, j)]) / (h * h);
+            out[IDX2(n, i, j)] = r[IDX2(n, i, j)] - lap;
+        }
+}
+
+/* The correction of pair k (green grid of side nk[k], spacing h 2^k) for the
+ * green residual rg, into vg: restriction to the red and blue levels (Eq.
+ * Erest2r, Eq. Erest2b); on the blue grid -- the next pair's green grid, an
+ * axis grid with the 5-point Laplacian at spacing h 2^(k+1) -- gamma cycles of
+ * pair k+1 from a zero correction, each after the first on the residual of
+ * the correction so far (the exact solve when it is the coarsest grid); then
+ * the prolongation sweeps (Eq. Eajacr, Eq. Eajacb, the green-red sweep).
+ * gamma = 1 is the V-cycle of orc_vcycle. */
+static int gamma_pair(int k, int K, const int *nk, double h, double p, int gamma, const double *rg, double *vg)
+{
+    const int n = nk[k], nb = nk[k + 1];
+    const double hk = h * (double)(1 << k);
+    size_t len = grid_len(2, n), lb = grid_len(2, nb);
+    double *rr = (double *)calloc(len, sizeof(double)), *vr = (double *)calloc(len, sizeof(double));
+    double *rb = (double *)calloc(lb, sizeof(double)), *vb = (double *)calloc(lb, sizeof(double));
+    double *res = (double *)calloc(lb, sizeof(double)), *w = (double *)calloc(lb, sizeof(double));
+    int rc = (rr && vr && rb && vb && res && w) ? 0 : -1;
+    if (rc == 0) {
+        orc_restrict2d_g2r(n, rg, rr);
+        orc_restrict2d_r2b(n, rr, rb);
+        if (k + 1 == K) {
+            rc = orc_coarse_solve(2, nb, 2.0 * hk, rb, vb);
+        } else {
+            for (int it = 0; it < gamma && rc == 0; it++) {
+                if (it == 0) memcpy(res, rb, lb * sizeof(double));
+                else green_residual(nb, 2.0 * hk, rb, vb, res);
+                memset(w, 0, lb * sizeof(double));
+                rc = gamma_pair(k + 1, K, nk, h, p, gamma, res, w);
+                for (int b = 1; b <= nb; b++)
+                    for (int a = 1; a <= nb; a++) vb[IDX2(nb, a, b)] += w[IDX2(nb, a, b)];
+            }
+        }
+    }
+    if (rc == 0) {
+        orc_prolong2d_b2r(n, hk, p, vb, rr, vr);
+        orc_prolong2d_r2g(n, hk, p, vr, rg, vg);
+    }
+    free(rr); free(vr); free(rb); free(vb); free(res); free(w);
+    return rc;
+}
+
+/* One gamma-cycle of the 2D diagonal hierarchy in place on u (order 2 or 4
+ * residual on the finest grid).  Returns 0, or -1 on invalid arguments. */
+int orc_wcycle2d(int n, int order, int coarsest, double p, int gamma, const double *f, double *u)
+{
+    int m = log2_side(n), c = log2_side(coarsest);
+    if (m < 1 || c < 1 || c > m || gamma < 1 || (order != 2 && order != 4)) return -1;
+    const int K = m - c;
+    const double h = 1.0 / (n + 1);
+    int nk[64];
+    for (int k = 0; k <= K; k++) nk[k] = (1 << (m - k)) - 1;
+    size_t len = grid_len(2, n);
+    double *r = (double *)calloc(len, sizeof(double)), *v = (double *)calloc(len, sizeof(double));
+    int rc = (r && v) ? 0 : -1;
+    if (rc == 0) {
+        orc_residual2d(n, h, order, f, u, r);
+        if (K == 0) rc = orc_coarse_solve(2, n, h, r, v);
+        else rc = gamma_pair(0, K, nk, h, p, gamma, r, v);
+    }
+    if (rc == 0) {
+        ORC_PAR
+        for (int j = 1; j <= n; j++)
+            for (int i = 1; i <= n; i++) u[IDX2(n, i, j)] += v[IDX2(n, i, j)];
+    }
+    free(r);
+    free(v);
+    return rc;
+}
+
 int orc_vcycle(int dim, int n, int hier, int order, int coarsest, const double *omega, const double *f,
                double *u)
 {

@@ -55,6 +55,7 @@ SIGNATURES = {
     "mg_tune": (_i, [_vp, _vp, _vp, ctypes.c_char_p, _ip, _vp]),
     "mg_set_omega": (_i, [_vp, _dp]),
     "mg_set_sweeps": (_i, [_vp, _i]),
+    "mg_set_gamma": (_i, [_vp, _i]),
     "mg_rho": (_i, [_vp, _vp, _vp, _i, _i, _dp, _vp]),
     "mg_solve_two_stage": (_i, [_vp, _vp, _vp, _dp, _d, _d, _i, _ip, _ip, _dp, _vp]),
     "mg_tune_info": (_i, [_vp, _ip, _ip, _ip, _ip]),

@@ -165,6 +165,11 @@ class Context:
         N.check(N.lib().mg_set_omega(self._h, arr), "mg_set_omega")
         self.omega = tuple(omega)
 
+    def set_gamma(self, gamma: int):
+        """mg_set_gamma: gamma cycles of each coarse problem per visit (2D
+        diagonal; 1 is the V-cycle, 2 the W-cycle)."""
+        N.check(N.lib().mg_set_gamma(self._h, gamma), "mg_set_gamma")
+
     def set_sweeps(self, extra: int):
         """mg_set_sweeps: extra Jacobi sweeps per level (2D diagonal hierarchy)."""
         N.check(N.lib().mg_set_sweeps(self._h, int(extra)), "mg_set_sweeps")

@@ -112,6 +112,9 @@ struct mg_ctx {
     bool rr = false;
     bool rr_alloc = false;  // the carried-residual buffers exist (rr is off while extra > 0)
     int extra = 0;          // extra Jacobi sweeps per level (mg_set_sweeps)
+    int gamma = 1;          // coarse-problem cycles per pair (mg_set_gamma; 1: the V-cycle)
+    void *wpool = nullptr;  // gamma > 1: per green level k >= 1, the kept residual and the accumulated correction
+    std::vector<void *> wr, wv;
     void *rlo = nullptr;
     void *r32b = nullptr;
     // tuned choices (mg_tune): tile class per pair for the down / up kernels
@@ -147,7 +150,7 @@ struct mg_ctx {
         const double *f = nullptr;
         double *u = nullptr;
         double rtol = -1.0;
-        int max = -1, order = 0, extra = 0;
+        int max = -1, order = 0, extra = 0, gamma = 1;
         double omega[4] = {0, 0, 0, 0};
         long long prefix_kernels = 0, body_kernels = 0;  // launches of the prefix and of one cycle
         unsigned long long used = 0;
@@ -610,7 +613,7 @@ size_t plan_cl2d(mg_ctx *c, int kd, int kc) {
 }
 
 void plan_fast2d(mg_ctx *c) {
-    c->fast2d = c->d.dim == 2 && c->d.hierarchy == MG_DIAG && c->extra == 0;
+    c->fast2d = c->d.dim == 2 && c->d.hierarchy == MG_DIAG && c->extra == 0 && c->gamma == 1;
     if (!c->fast2d) return;
     // pairs whose green grid has side <= 63 (or the tuned cut-off; 31 below a
     // cluster) run in one thread block
@@ -1002,6 +1005,33 @@ template <typename T> void check_cluster2d(mg_ctx *c) {
     }
 }
 
+// Pair k of a 2D gamma-cycle: restriction to the red and blue levels; on the
+// blue grid (the green level of pair k+1) gamma cycles of pair k+1 from a
+// zero correction, each after the first on the 5-point residual of the
+// correction accumulated so far (the exact solve on the coarsest grid); then
+// the prolongation sweeps; at k = 0 they also apply u += v.
+template <typename T> void wpair(mg_ctx *c, int k, double *u, const int *done, cudaStream_t s) {
+    launch_restrict<T>(c, 2 * k, done, s);
+    launch_restrict<T>(c, 2 * k + 1, done, s);
+    if (k + 1 == c->K) {
+        launch_coarse<T>(c, done, s);
+    } else {
+        const Level &b = c->lv[2 * k + 2];
+        const int nb = b.side;
+        const T ih2 = (T)(1.0 / (spacing(c, b) * spacing(c, b)));
+        T *rkeep = (T *)c->wr[k + 1], *vacc = (T *)c->wv[k + 1], *rb = (T *)b.r[0], *vb = (T *)b.v[0];
+        cudaMemcpyAsync(rkeep, rb, b.len * sizeof(T), cudaMemcpyDeviceToDevice, s);
+        for (int it = 0; it < c->gamma; it++) {
+            if (it > 0) LAUNCH_B(TAG_DOWN, (k_gres_2d<T>), grid2(nb, nb), B2, (const T *)rkeep, (const T *)vacc, rb, b.pitch, nb, ih2, done);
+            wpair<T>(c, k + 1, nullptr, done, s);
+            LAUNCH_B(TAG_UP, (k_acc_2d<T>), grid2(nb, nb), B2, (const T *)vb, vacc, b.pitch, nb, it == 0 ? 1 : 0, done);
+        }
+        cudaMemcpyAsync(vb, vacc, b.len * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    }
+    launch_prolong<T>(c, 2 * k + 1, c->d.omega, nullptr, done, s);
+    launch_prolong<T>(c, 2 * k, c->d.omega, k == 0 ? u : nullptr, done, s);
+}
+
 template <typename T>
 mg_status vcycle_t(mg_ctx *c, const double *f, double *u, const int *done, bool with_residual, cudaStream_t s) {
     if (with_residual) launch_res_fast<T>(c, f, u, done, s);
@@ -1023,6 +1053,11 @@ mg_status vcycle_t(mg_ctx *c, const double *f, double *u, const int *done, bool 
             LAUNCH_B(TAG_FINEST_UP, (k_add_axis<T>), grid3(n, n, n), B2, (const T *)l0.v[0], l0.pitch, l0.rows, n, 3, u,
                      c->d.pitch, n + 2, done);
         }
+        CKL("vcycle launch");
+        return MG_OK;
+    }
+    if (c->gamma > 1 && c->K >= 1) {  // a 2D diagonal gamma-cycle (mg_set_gamma)
+        wpair<T>(c, 0, u, done, s);
         CKL("vcycle launch");
         return MG_OK;
     }
@@ -1092,6 +1127,7 @@ mg_status mg_destroy(mg_ctx *c) {
     cudaFree(c->G);
     cudaFree(c->scal);
     cudaFree(c->ft);
+    cudaFree(c->wpool);
     cudaFree(c->io_f);
     cudaFree(c->io_u);
     cudaFree(c->ftab);
@@ -1492,7 +1528,7 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
 static bool solve_graph_matches(const mg_ctx *c, const mg_ctx::SolveGraph &e, const double *f, const double *u,
                                 double rtol, int max_cycles) {
     return e.exec && e.f == f && e.u == u && e.rtol == rtol && e.max == max_cycles && e.order == c->d.order &&
-           e.extra == c->extra && std::memcmp(e.omega, c->d.omega, sizeof e.omega) == 0;
+           e.extra == c->extra && e.gamma == c->gamma && std::memcmp(e.omega, c->d.omega, sizeof e.omega) == 0;
 }
 
 static mg_status build_solve_graph(mg_ctx *c, mg_ctx::SolveGraph &slot, const double *f, double *u, double rtol,
@@ -1511,6 +1547,7 @@ static mg_status build_solve_graph(mg_ctx *c, mg_ctx::SolveGraph &slot, const do
     slot.f = f; slot.u = u; slot.rtol = rtol; slot.max = max_cycles;
     slot.order = c->d.order;
     slot.extra = c->extra;
+    slot.gamma = c->gamma;
     for (int q = 0; q < 4; q++) slot.omega[q] = c->d.omega[q];
     slot.prefix_kernels = c->g_prefix_kernels;
     slot.body_kernels = c->g_body_kernels;
@@ -1672,7 +1709,30 @@ mg_status mg_set_sweeps(mg_ctx *c, int extra) {
     if (!c || extra < 0 || extra > 64) return MG_EINVAL;
     if (extra > 0 && (c->d.dim != 2 || c->d.hierarchy != MG_DIAG || c->nprob != 1)) return MG_EINVAL;
     c->extra = extra;
-    c->rr = c->rr_alloc && extra == 0;
+    c->rr = c->rr_alloc && extra == 0 && c->gamma == 1;
+    plan_fast2d(c);
+    return MG_OK;
+}
+
+mg_status mg_set_gamma(mg_ctx *c, int gamma) {
+    if (!c || gamma < 1 || gamma > 4) return MG_EINVAL;
+    if (gamma > 1 && (c->d.dim != 2 || c->d.hierarchy != MG_DIAG || c->nprob != 1)) return MG_EINVAL;
+    if (gamma > 1 && !c->wpool && c->K >= 2) {  // the first gamma > 1: a kept residual and an accumulator per green level
+        size_t total = 0;
+        for (int k = 1; k < c->K; k++) total += 2 * ((c->lv[2 * k].len * c->esz + 255) / 256 * 256);
+        if (cudaMalloc(&c->wpool, total) != cudaSuccess) { cudaGetLastError(); c->wpool = nullptr; return MG_ENOMEM; }
+        if (cudaMemset(c->wpool, 0, total) != cudaSuccess) return cuda_fail(cudaGetLastError(), "mg_set_gamma");
+        c->wr.assign(c->K, nullptr);
+        c->wv.assign(c->K, nullptr);
+        char *p = (char *)c->wpool;
+        for (int k = 1; k < c->K; k++) {
+            const size_t bytes = (c->lv[2 * k].len * c->esz + 255) / 256 * 256;
+            c->wr[k] = p; p += bytes;
+            c->wv[k] = p; p += bytes;
+        }
+    }
+    c->gamma = gamma;
+    c->rr = c->rr_alloc && c->extra == 0 && gamma == 1;
     plan_fast2d(c);
     return MG_OK;
 }

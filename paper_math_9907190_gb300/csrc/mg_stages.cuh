@@ -982,6 +982,30 @@ __global__ void k_coarse(const T *r, int pitch, int rows, int nc, int dim, const
     }
 }
 
+// gamma-cycles (Section 5 leaves them open): on the blue grid of a pair --
+// an axis level of side n and spacing H -- the residual of the corrections
+// accumulated so far, out = r - L v with the 5-point Laplacian, and the
+// accumulation v_acc += v
+template <typename T>
+__global__ void k_gres_2d(const T *r, const T *v, T *out, int pitch, int n, T ih2, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    MG_IDX2 const int i = tx + 1, j = ty + 1;
+    if (i > n || j > n) return;
+    const size_t c = (size_t)j * pitch + i;
+    const T lap = (v[c + 1] + v[c - 1] + v[c + pitch] + v[c - pitch] - T(4) * v[c]) * ih2;
+    out[c] = r[c] - lap;
+}
+template <typename T>
+__global__ void k_acc_2d(const T *v, T *acc, int pitch, int n, int first, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    MG_IDX2 const int i = tx + 1, j = ty + 1;
+    if (i > n || j > n) return;
+    const size_t c = (size_t)j * pitch + i;
+    acc[c] = first ? v[c] : acc[c] + v[c];
+}
+
 // u += v on an axis level (only used when the finest grid is the coarsest)
 template <typename T>
 __global__ void k_add_axis(const T *v, int pitch, int rows, int n, int dim, double *u, int up, int urows,

@@ -771,3 +771,58 @@ def test_optimal_weight_2d_is_where_one_minus_p_meets_the_other_modes():
     assert abs(res.x - 1.052) <= 0.005
     assert abs(res.fun - 0.052) <= 0.1 * 0.052
     assert res.fun == pytest.approx(res.x - 1.0, abs=2e-4)
+
+
+# --------------------------------------------------------------------------
+# gamma-cycles (W-cycles) of the 2D diagonal hierarchy (Section 5, open)
+# --------------------------------------------------------------------------
+
+def test_gamma_one_is_the_v_cycle():
+    f = rng_grid(2, 63, 91, ring=True)
+    u0 = rng_grid(2, 63, 92)
+    a = O.vcycle(f, u0.copy(), omega=[1.052])
+    b = O.wcycle2d(f, u0.copy(), p=1.052, gamma=1)
+    assert np.array_equal(a, b)
+
+
+def test_large_gamma_tends_to_the_two_grid_cycle():
+    """gamma cycles of pair 1 from zero converge to the exact solution of the
+    blue grid's 5-point system, so for large gamma the cycle becomes the
+    two-grid cycle whose coarsest grid is the first blue grid, solved
+    exactly (the V-cycle with coarsest = (n - 1) / 2).  A wrong sign, spacing
+    or operator in the coarse residual would leave a different limit."""
+    n = 31
+
+    def w8(f, u):
+        return O.wcycle2d(f, u, p=1.0, gamma=8)
+
+    def two_grid(f, u):
+        return O.vcycle(f, u, omega=[1.0], coarsest=(n - 1) // 2)
+
+    r_w = spectral_radius(2, n, O.DIAG, 2, [1.0], 3, vcycle=lambda f, u, **kw: w8(f, u))
+    r_2 = spectral_radius(2, n, O.DIAG, 2, [1.0], 3, vcycle=lambda f, u, **kw: two_grid(f, u))
+    assert r_w == pytest.approx(r_2, rel=1e-6)
+    r_v = spectral_radius(2, n, O.DIAG, 2, [1.0], 3)
+    assert r_2 < r_v  # an exact coarse problem contracts faster than its V-cycle approximation
+
+
+def test_gamma_cycle_fixed_point_and_odd_point_eigenspace():
+    """The fixed point of the gamma-cycle is the direct solution of the
+    5-point system, and an error on the odd-index-sum points is scaled by
+    exactly 1 - p (its restricted residual vanishes, whatever the coarse
+    problem's solver)."""
+    n = 15
+    L, M = operators(2, n, 2)
+    f = rng_grid(2, n, 93, ring=True)
+    A = L @ _kron(_s1(n), _s1(n)).T  # acts on interior values
+    ustar = np.linalg.solve(A, M @ f.ravel())
+    u = O.grid(2, n)
+    for _ in range(60):
+        O.wcycle2d(f, u, p=1.0, gamma=2)
+    np.testing.assert_allclose(interior(u).ravel(), ustar, rtol=0, atol=1e-11 * np.abs(ustar).max())
+    idx = np.indices((n + 2, n + 2))
+    inner = np.zeros((n + 2, n + 2), dtype=bool)
+    inner[1:-1, 1:-1] = True
+    e = np.where(inner & (idx.sum(0) % 2 == 1), np.random.default_rng(94).standard_normal((n + 2, n + 2)), 0.0)
+    w = O.wcycle2d(O.grid(2, n), e.copy(), p=1.3, gamma=3)
+    np.testing.assert_allclose(w, (1.0 - 1.3) * e, rtol=0, atol=1e-14 * np.abs(e).max())
