@@ -21,7 +21,7 @@ solution of Poisson's equation using diagonally oriented grids"):
 * ``restrict_fw``, ``prolong_usual``  the conventional cycle of Sections 2.1-2.2, 3.1-3.2
 * ``coarse_solve``        exact solve of the coarsest axis grid (the paper is silent)
 * ``vcycle``, ``solve``   the V-cycle of Sections 2.3 and 3.3
-* ``wcycle2d``            gamma-cycles of the 2D diagonal hierarchy (Section 5 leaves them open)
+* ``wcycle``              gamma-cycles of the diagonal hierarchy (Section 5 leaves them open)
 
 Pins (tests/test_oracle_pins.py): closed-form stencil weights and the 17-point
 composite restriction, exactness of every Jacobi sweep on quadratics, the
@@ -94,7 +94,7 @@ def _load():
                 "orc_norm2_interior": (d, [i, i, dp]),
                 "orc_solve": (i, [i, i, i, i, i, dp, dp, dp, d, i, dp, dp]),
                 "orc_set_threads": (i, [i]),
-                "orc_wcycle2d": (i, [i, i, i, d, i, dp, dp]),
+                "orc_wcycle": (i, [i, i, i, i, dp, i, dp, dp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -261,12 +261,13 @@ def solve(f, u=None, *, hier=DIAG, order=2, coarsest=3, omega=None, rtol=1e-10, 
     return u, it, rel.value, hist[:it].copy()
 
 
-def wcycle2d(f, u, *, order=2, coarsest=3, p=1.0, gamma=2):
-    """One gamma-cycle of the 2D diagonal hierarchy in place on u (gamma = 1:
-    the V-cycle); returns u."""
-    n = f.shape[0] - 2
-    if _load().orc_wcycle2d(n, order, coarsest, p, gamma, _p(f), _p(u)) != 0:
-        raise ValueError(f"orc_wcycle2d rejected n={n} coarsest={coarsest} gamma={gamma}")
+def wcycle(f, u, *, order=2, coarsest=3, omega=None, gamma=2):
+    """One gamma-cycle of the diagonal hierarchy in place on u (gamma = 1: the
+    V-cycle); omega as for vcycle.  Returns u."""
+    dim, n = f.ndim, f.shape[0] - 2
+    om = _omega(omega, dim, DIAG)
+    if _load().orc_wcycle(dim, n, order, coarsest, _p(om), gamma, _p(f), _p(u)) != 0:
+        raise ValueError(f"orc_wcycle rejected dim={dim} n={n} coarsest={coarsest} gamma={gamma}")
     return u
 
 

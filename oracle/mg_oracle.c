@@ -658,85 +658,120 @@ int orc_vcycle_sweeps(int dim, int n, int hier, int order, int coarsest, const d
 }
 
 /* ------------------------------------------------------------------------ */
-/* W-cycles (gamma-cycles) of the 2D diagonal hierarchy: the extension the   */
-/* paper's conclusion (Section 5) leaves open.                                */
+/* Gamma-cycles (W-cycles for gamma = 2) of the diagonal hierarchy: the      */
+/* extension the paper's conclusion (Section 5) leaves open.                 */
 /* ------------------------------------------------------------------------ */
 
-/* 5-point residual on an axis grid of side n and spacing h: out = r - L v */
-static void green_residual(int n, double h, const double *r, const double *v, double *out)
+/* 5/7-point residual on an axis grid of side n and spacing h: out = r - L v */
+static void green_residual(int dim, int n, double h, const double *r, const double *v, double *out)
 {
-    ORC_PAR
-    for (int j = 1; j <= n; j++)
-        for (int i = 1; i <= n; i++) {
-            double lap = (v[IDX2(n, i + 1, j)] + v[IDX2(n, i - 1, j)] + v[IDX2(n, i, j + 1)] +
-                          v[IDX2(n, i, j - 1)] - 4.0 * v[IDX2(n, i, j)]) / (h * h);
-            out[IDX2(n, i, j)] = r[IDX2(n, i, j)] - lap;
-        }
+    if (dim == 2) {
+        ORC_PAR
+        for (int j = 1; j <= n; j++)
+            for (int i = 1; i <= n; i++) {
+                double lap = (v[IDX2(n, i + 1, j)] + v[IDX2(n, i - 1, j)] + v[IDX2(n, i, j + 1)] +
+                              v[IDX2(n, i, j - 1)] - 4.0 * v[IDX2(n, i, j)]) / (h * h);
+                out[IDX2(n, i, j)] = r[IDX2(n, i, j)] - lap;
+            }
+    } else {
+        ORC_PAR
+        for (int k = 1; k <= n; k++)
+            for (int j = 1; j <= n; j++)
+                for (int i = 1; i <= n; i++) {
+                    double lap = (v[IDX3(n, i + 1, j, k)] + v[IDX3(n, i - 1, j, k)] + v[IDX3(n, i, j + 1, k)] +
+                                  v[IDX3(n, i, j - 1, k)] + v[IDX3(n, i, j, k + 1)] + v[IDX3(n, i, j, k - 1)] -
+                                  6.0 * v[IDX3(n, i, j, k)]) / (h * h);
+                    out[IDX3(n, i, j, k)] = r[IDX3(n, i, j, k)] - lap;
+                }
+    }
 }
 
-/* The correction of pair k (green grid of side nk[k], spacing h 2^k) for the
- * green residual rg, into vg: restriction to the red and blue levels (Eq.
- * Erest2r, Eq. Erest2b); on the blue grid -- the next pair's green grid, an
- * axis grid with the 5-point Laplacian at spacing h 2^(k+1) -- gamma cycles of
- * pair k+1 from a zero correction, each after the first on the residual of
- * the correction so far (the exact solve when it is the coarsest grid); then
- * the prolongation sweeps (Eq. Eajacr, Eq. Eajacb, the green-red sweep).
- * gamma = 1 is the V-cycle of orc_vcycle. */
-static int gamma_pair(int k, int K, const int *nk, double h, double p, int gamma, const double *rg, double *vg)
+/* The correction of pair / triple k (green grid of side nk[k], spacing
+ * h 2^k) for the green residual rg, into vg: restriction down to the blue
+ * level (2D: Eq. Erest2r, Eq. Erest2b; 3D: Eq. Erred, Eq. Ermagc/Ermagm,
+ * Eq. Erblu); on the blue grid -- the next green grid, an axis grid with the
+ * 5/7-point Laplacian at spacing h 2^(k+1) -- gamma cycles of pair / triple
+ * k+1 from a zero correction, each after the first on the residual of the
+ * correction so far (the exact solve when it is the coarsest grid); then the
+ * prolongation sweeps (2D: Eq. Eajacr, Eq. Eajacb, the green-red sweep; 3D:
+ * Eq. Emprolm .. Eq. Egprolr).  gamma = 1 is the V-cycle of orc_vcycle. */
+static int gamma_level(int dim, int k, int K, const int *nk, double h, const double *om, int gamma,
+                       const double *rg, double *vg)
 {
     const int n = nk[k], nb = nk[k + 1];
     const double hk = h * (double)(1 << k);
-    size_t len = grid_len(2, n), lb = grid_len(2, nb);
+    const size_t len = grid_len(dim, n), lb = grid_len(dim, nb);
     double *rr = (double *)calloc(len, sizeof(double)), *vr = (double *)calloc(len, sizeof(double));
+    double *rm = dim == 3 ? (double *)calloc(len, sizeof(double)) : NULL;
+    double *vm = dim == 3 ? (double *)calloc(len, sizeof(double)) : NULL;
     double *rb = (double *)calloc(lb, sizeof(double)), *vb = (double *)calloc(lb, sizeof(double));
     double *res = (double *)calloc(lb, sizeof(double)), *w = (double *)calloc(lb, sizeof(double));
-    int rc = (rr && vr && rb && vb && res && w) ? 0 : -1;
+    int rc = (rr && vr && rb && vb && res && w && (dim == 2 || (rm && vm))) ? 0 : -1;
     if (rc == 0) {
-        orc_restrict2d_g2r(n, rg, rr);
-        orc_restrict2d_r2b(n, rr, rb);
+        if (dim == 2) {
+            orc_restrict2d_g2r(n, rg, rr);
+            orc_restrict2d_r2b(n, rr, rb);
+        } else {
+            orc_restrict3d_g2r(n, rg, rr);
+            orc_restrict3d_r2m(n, rr, rm);
+            orc_restrict3d_m2b(n, rm, rb);
+        }
         if (k + 1 == K) {
-            rc = orc_coarse_solve(2, nb, 2.0 * hk, rb, vb);
+            rc = orc_coarse_solve(dim, nb, 2.0 * hk, rb, vb);
         } else {
             for (int it = 0; it < gamma && rc == 0; it++) {
                 if (it == 0) memcpy(res, rb, lb * sizeof(double));
-                else green_residual(nb, 2.0 * hk, rb, vb, res);
+                else green_residual(dim, nb, 2.0 * hk, rb, vb, res);
                 memset(w, 0, lb * sizeof(double));
-                rc = gamma_pair(k + 1, K, nk, h, p, gamma, res, w);
-                for (int b = 1; b <= nb; b++)
-                    for (int a = 1; a <= nb; a++) vb[IDX2(nb, a, b)] += w[IDX2(nb, a, b)];
+                rc = gamma_level(dim, k + 1, K, nk, h, om, gamma, res, w);
+                for (size_t q = 0; q < lb; q++) vb[q] += w[q];  /* w is zero on the ring */
             }
         }
     }
     if (rc == 0) {
-        orc_prolong2d_b2r(n, hk, p, vb, rr, vr);
-        orc_prolong2d_r2g(n, hk, p, vr, rg, vg);
+        if (dim == 2) {
+            orc_prolong2d_b2r(n, hk, om[0], vb, rr, vr);
+            orc_prolong2d_r2g(n, hk, om[0], vr, rg, vg);
+        } else {
+            orc_prolong3d_b2m(n, hk, om[0], vb, rm, vm);
+            orc_prolong3d_m2r(n, hk, om[1], om[2], vm, rr, vr);
+            orc_prolong3d_r2g(n, hk, om[3], vr, rg, vg);
+        }
     }
-    free(rr); free(vr); free(rb); free(vb); free(res); free(w);
+    free(rr); free(vr); free(rm); free(vm); free(rb); free(vb); free(res); free(w);
     return rc;
 }
 
-/* One gamma-cycle of the 2D diagonal hierarchy in place on u (order 2 or 4
- * residual on the finest grid).  Returns 0, or -1 on invalid arguments. */
-int orc_wcycle2d(int n, int order, int coarsest, double p, int gamma, const double *f, double *u)
+/* One gamma-cycle of the diagonal hierarchy in place on u (order 2 or 4
+ * residual on the finest grid; omega as for orc_vcycle).  Returns 0, or -1
+ * on invalid arguments. */
+int orc_wcycle(int dim, int n, int order, int coarsest, const double *omega, int gamma, const double *f, double *u)
 {
     int m = log2_side(n), c = log2_side(coarsest);
-    if (m < 1 || c < 1 || c > m || gamma < 1 || (order != 2 && order != 4)) return -1;
+    if ((dim != 2 && dim != 3) || m < 1 || c < 1 || c > m || gamma < 1 || (order != 2 && order != 4)) return -1;
     const int K = m - c;
     const double h = 1.0 / (n + 1);
     int nk[64];
     for (int k = 0; k <= K; k++) nk[k] = (1 << (m - k)) - 1;
-    size_t len = grid_len(2, n);
+    const size_t len = grid_len(dim, n);
     double *r = (double *)calloc(len, sizeof(double)), *v = (double *)calloc(len, sizeof(double));
     int rc = (r && v) ? 0 : -1;
     if (rc == 0) {
-        orc_residual2d(n, h, order, f, u, r);
-        if (K == 0) rc = orc_coarse_solve(2, n, h, r, v);
-        else rc = gamma_pair(0, K, nk, h, p, gamma, r, v);
+        orc_residual(dim, n, h, order, f, u, r);
+        if (K == 0) rc = orc_coarse_solve(dim, n, h, r, v);
+        else rc = gamma_level(dim, 0, K, nk, h, omega, gamma, r, v);
     }
     if (rc == 0) {
-        ORC_PAR
-        for (int j = 1; j <= n; j++)
-            for (int i = 1; i <= n; i++) u[IDX2(n, i, j)] += v[IDX2(n, i, j)];
+        if (dim == 2) {
+            ORC_PAR
+            for (int j = 1; j <= n; j++)
+                for (int i = 1; i <= n; i++) u[IDX2(n, i, j)] += v[IDX2(n, i, j)];
+        } else {
+            ORC_PAR
+            for (int k = 1; k <= n; k++)
+                for (int j = 1; j <= n; j++)
+                    for (int i = 1; i <= n; i++) u[IDX3(n, i, j, k)] += v[IDX3(n, i, j, k)];
+        }
     }
     free(r);
     free(v);

@@ -666,7 +666,7 @@ void plan_fast2d(mg_ctx *c) {
 void plan_fast3d(mg_ctx *c) {
     // the coarse block keeps the coarsest inverse in shared memory: 3^3 grids
     // at most (a 7^3 coarsest grid runs with per-stage kernels and k_coarse)
-    c->fast3d = c->d.dim == 3 && c->d.hierarchy == MG_DIAG && c->d.coarsest <= 3;
+    c->fast3d = c->d.dim == 3 && c->d.hierarchy == MG_DIAG && c->d.coarsest <= 3 && c->gamma == 1;
     if (!c->fast3d) return;
     const int cut = c->cut_side > 0 ? c->cut_side : 15;
     int kc = 0;
@@ -1005,31 +1005,37 @@ template <typename T> void check_cluster2d(mg_ctx *c) {
     }
 }
 
-// Pair k of a 2D gamma-cycle: restriction to the red and blue levels; on the
-// blue grid (the green level of pair k+1) gamma cycles of pair k+1 from a
-// zero correction, each after the first on the 5-point residual of the
+// Pair / triple k of a gamma-cycle: restriction down to the blue level; on
+// the blue grid (the green level of k+1) gamma cycles of k+1 from a zero
+// correction, each after the first on the 5/7-point residual of the
 // correction accumulated so far (the exact solve on the coarsest grid); then
 // the prolongation sweeps; at k = 0 they also apply u += v.
-template <typename T> void wpair(mg_ctx *c, int k, double *u, const int *done, cudaStream_t s) {
-    launch_restrict<T>(c, 2 * k, done, s);
-    launch_restrict<T>(c, 2 * k + 1, done, s);
+template <typename T> void wlevel(mg_ctx *c, int k, double *u, const int *done, cudaStream_t s) {
+    const int per = c->d.dim == 2 ? 2 : 3;  // levels per pair / triple
+    for (int l = per * k; l < per * (k + 1); l++) launch_restrict<T>(c, l, done, s);
     if (k + 1 == c->K) {
         launch_coarse<T>(c, done, s);
     } else {
-        const Level &b = c->lv[2 * k + 2];
+        const Level &b = c->lv[per * (k + 1)];
         const int nb = b.side;
         const T ih2 = (T)(1.0 / (spacing(c, b) * spacing(c, b)));
         T *rkeep = (T *)c->wr[k + 1], *vacc = (T *)c->wv[k + 1], *rb = (T *)b.r[0], *vb = (T *)b.v[0];
         cudaMemcpyAsync(rkeep, rb, b.len * sizeof(T), cudaMemcpyDeviceToDevice, s);
         for (int it = 0; it < c->gamma; it++) {
-            if (it > 0) LAUNCH_B(TAG_DOWN, (k_gres_2d<T>), grid2(nb, nb), B2, (const T *)rkeep, (const T *)vacc, rb, b.pitch, nb, ih2, done);
-            wpair<T>(c, k + 1, nullptr, done, s);
-            LAUNCH_B(TAG_UP, (k_acc_2d<T>), grid2(nb, nb), B2, (const T *)vb, vacc, b.pitch, nb, it == 0 ? 1 : 0, done);
+            if (c->d.dim == 2) {
+                if (it > 0) LAUNCH_B(TAG_DOWN, (k_gres_2d<T>), grid2(nb, nb), B2, (const T *)rkeep, (const T *)vacc, rb, b.pitch, nb, ih2, done);
+                wlevel<T>(c, k + 1, nullptr, done, s);
+                LAUNCH_B(TAG_UP, (k_acc_2d<T>), grid2(nb, nb), B2, (const T *)vb, vacc, b.pitch, nb, it == 0 ? 1 : 0, done);
+            } else {
+                if (it > 0) LAUNCH_B(TAG_DOWN, (k_gres_3d<T>), grid3(nb, nb, nb), B2, (const T *)rkeep, (const T *)vacc, rb, b.pitch, b.rows, nb, ih2, done);
+                wlevel<T>(c, k + 1, nullptr, done, s);
+                LAUNCH_B(TAG_UP, (k_acc_3d<T>), grid3(nb, nb, nb), B2, (const T *)vb, vacc, b.pitch, b.rows, nb, it == 0 ? 1 : 0, done);
+            }
         }
         cudaMemcpyAsync(vb, vacc, b.len * sizeof(T), cudaMemcpyDeviceToDevice, s);
     }
-    launch_prolong<T>(c, 2 * k + 1, c->d.omega, nullptr, done, s);
-    launch_prolong<T>(c, 2 * k, c->d.omega, k == 0 ? u : nullptr, done, s);
+    for (int l = per * (k + 1) - 1; l >= per * k; l--)
+        launch_prolong<T>(c, l, c->d.omega, l == 0 ? u : nullptr, done, s);
 }
 
 template <typename T>
@@ -1056,8 +1062,8 @@ mg_status vcycle_t(mg_ctx *c, const double *f, double *u, const int *done, bool 
         CKL("vcycle launch");
         return MG_OK;
     }
-    if (c->gamma > 1 && c->K >= 1) {  // a 2D diagonal gamma-cycle (mg_set_gamma)
-        wpair<T>(c, 0, u, done, s);
+    if (c->gamma > 1 && c->K >= 1) {  // a diagonal gamma-cycle (mg_set_gamma)
+        wlevel<T>(c, 0, u, done, s);
         CKL("vcycle launch");
         return MG_OK;
     }
@@ -1716,17 +1722,18 @@ mg_status mg_set_sweeps(mg_ctx *c, int extra) {
 
 mg_status mg_set_gamma(mg_ctx *c, int gamma) {
     if (!c || gamma < 1 || gamma > 4) return MG_EINVAL;
-    if (gamma > 1 && (c->d.dim != 2 || c->d.hierarchy != MG_DIAG || c->nprob != 1)) return MG_EINVAL;
+    if (gamma > 1 && (c->d.hierarchy != MG_DIAG || c->nprob != 1)) return MG_EINVAL;
+    const int per = c->d.dim == 2 ? 2 : 3;
     if (gamma > 1 && !c->wpool && c->K >= 2) {  // the first gamma > 1: a kept residual and an accumulator per green level
         size_t total = 0;
-        for (int k = 1; k < c->K; k++) total += 2 * ((c->lv[2 * k].len * c->esz + 255) / 256 * 256);
+        for (int k = 1; k < c->K; k++) total += 2 * ((c->lv[per * k].len * c->esz + 255) / 256 * 256);
         if (cudaMalloc(&c->wpool, total) != cudaSuccess) { cudaGetLastError(); c->wpool = nullptr; return MG_ENOMEM; }
         if (cudaMemset(c->wpool, 0, total) != cudaSuccess) return cuda_fail(cudaGetLastError(), "mg_set_gamma");
         c->wr.assign(c->K, nullptr);
         c->wv.assign(c->K, nullptr);
         char *p = (char *)c->wpool;
         for (int k = 1; k < c->K; k++) {
-            const size_t bytes = (c->lv[2 * k].len * c->esz + 255) / 256 * 256;
+            const size_t bytes = (c->lv[per * k].len * c->esz + 255) / 256 * 256;
             c->wr[k] = p; p += bytes;
             c->wv[k] = p; p += bytes;
         }
@@ -1734,6 +1741,7 @@ mg_status mg_set_gamma(mg_ctx *c, int gamma) {
     c->gamma = gamma;
     c->rr = c->rr_alloc && c->extra == 0 && gamma == 1;
     plan_fast2d(c);
+    plan_fast3d(c);
     return MG_OK;
 }
 

@@ -1006,6 +1006,26 @@ __global__ void k_acc_2d(const T *v, T *acc, int pitch, int n, int first, const 
     acc[c] = first ? v[c] : acc[c] + v[c];
 }
 
+template <typename T>
+__global__ void k_gres_3d(const T *r, const T *v, T *out, int pitch, int rows, int n, T ih2, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
+    if (i > n || j > n) return;
+    const size_t pl = (size_t)pitch * rows, c = (size_t)k * pl + (size_t)j * pitch + i;
+    const T lap = (v[c + 1] + v[c - 1] + v[c + pitch] + v[c - pitch] + v[c + pl] + v[c - pl] - T(6) * v[c]) * ih2;
+    out[c] = r[c] - lap;
+}
+template <typename T>
+__global__ void k_acc_3d(const T *v, T *acc, int pitch, int rows, int n, int first, const int *done, Bt B) {
+    const int prob_ = bt_prob(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    MG_IDX3 const int i = tx + 1, j = ty + 1, k = tz + 1;
+    if (i > n || j > n) return;
+    const size_t c = ((size_t)k * rows + j) * pitch + i;
+    acc[c] = first ? v[c] : acc[c] + v[c];
+}
+
 // u += v on an axis level (only used when the finest grid is the coarsest)
 template <typename T>
 __global__ void k_add_axis(const T *v, int pitch, int rows, int n, int dim, double *u, int up, int urows,

@@ -1,6 +1,6 @@
-"""GPU parity of the gamma-cycles (W-cycles) of the 2D diagonal hierarchy
+"""GPU parity of the gamma-cycles (W-cycles) of the diagonal hierarchy (2D, 3D)
 (mg_set_gamma), the extension the paper's conclusion leaves open, against
-the oracle's orc_wcycle2d: iterates point by point (FP64 1e-12, mixed FP32
+the oracle's orc_wcycle: iterates point by point (FP64 1e-12, mixed FP32
 levels 1e-5 with the L2 ratio 2e-6 as a second bar), a mixed solve to 1e-10,
 the GPU's convergence factor against the oracle's, and the argument checks."""
 
@@ -33,16 +33,19 @@ def H(t):
     return t.detach().cpu().numpy()
 
 
-@pytest.mark.parametrize("n,prec,gamma,tol,l2", [(63, "fp64", 2, 1e-12, 1e-12), (255, "fp64", 2, 1e-12, 1e-12),
-                                                (127, "fp64", 3, 1e-12, 1e-12), (255, "mixed", 2, 1e-5, 2e-6)])
-def test_gamma_cycle_iterates_match_oracle(n, prec, gamma, tol, l2):
-    f = I.uniform_f(2, n, 101)
-    uo = O.grid(2, n)
-    with Context(2, n, precision=prec, omega=(1.052,)) as c:
+@pytest.mark.parametrize("dim,n,prec,gamma,tol,l2", [
+    (2, 63, "fp64", 2, 1e-12, 1e-12), (2, 255, "fp64", 2, 1e-12, 1e-12), (2, 127, "fp64", 3, 1e-12, 1e-12),
+    (2, 255, "mixed", 2, 1e-5, 2e-6), (3, 15, "fp64", 2, 1e-12, 1e-12), (3, 31, "fp64", 2, 1e-12, 1e-12),
+    (3, 63, "mixed", 2, 1e-5, 2e-6)])
+def test_gamma_cycle_iterates_match_oracle(dim, n, prec, gamma, tol, l2):
+    f = I.uniform_f(2, n, 101) if dim == 2 else I.cube(n)
+    om = (1.052,) if dim == 2 else (1.11, 1.42, 1.08, 0.99)
+    uo = O.grid(dim, n)
+    with Context(dim, n, precision=prec, omega=om) as c:
         c.set_gamma(gamma)
         ug, ft = c.new_grid(), T(f)
         for cyc in range(3):
-            O.wcycle2d(f, uo, p=1.052, gamma=gamma)
+            O.wcycle(f, uo, omega=list(om), gamma=gamma)
             c.vcycle(ft, ug)
             assert_iterate(H(ug), uo, tol, l2_tol=l2, what=f"cycle {cyc}")
 
@@ -78,8 +81,8 @@ def test_gamma_cycle_convergence_factor_matches_oracle():
     assert rho_v == pytest.approx(0.09868, rel=0.03)
 
 
-def test_gamma_rejected_outside_2d_diagonal():
-    with Context(3, 15) as c:
+def test_gamma_rejected_outside_the_diagonal_hierarchy():
+    with Context(3, 15, hierarchy="usual") as c:
         with pytest.raises(MGError):
             c.set_gamma(2)
         c.set_gamma(1)
@@ -90,3 +93,14 @@ def test_gamma_rejected_outside_2d_diagonal():
         for bad in (0, 5, -1):
             with pytest.raises(MGError):
                 c.set_gamma(bad)
+
+
+def test_3d_gamma_cycle_solve_reaches_tolerance():
+    n = 63
+    f = I.cube(n)
+    with Context(3, n, precision="mixed") as c:
+        c.set_gamma(2)
+        ug, it, rel, _ = c.solve(T(f), rtol=1e-10)
+    assert rel <= 1e-10
+    uo, _, _, _ = O.solve(f, omega=[1.11, 1.42, 1.08, 0.99], rtol=1e-13, max_cycles=200)
+    assert_iterate(H(ug), uo, 1e-8)

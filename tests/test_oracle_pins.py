@@ -777,32 +777,32 @@ def test_optimal_weight_2d_is_where_one_minus_p_meets_the_other_modes():
 # gamma-cycles (W-cycles) of the 2D diagonal hierarchy (Section 5, open)
 # --------------------------------------------------------------------------
 
-def test_gamma_one_is_the_v_cycle():
-    f = rng_grid(2, 63, 91, ring=True)
-    u0 = rng_grid(2, 63, 92)
-    a = O.vcycle(f, u0.copy(), omega=[1.052])
-    b = O.wcycle2d(f, u0.copy(), p=1.052, gamma=1)
+@pytest.mark.parametrize("dim,n,omega", [(2, 63, [1.052]), (3, 15, [1.11, 1.42, 1.08, 0.99])])
+def test_gamma_one_is_the_v_cycle(dim, n, omega):
+    f = rng_grid(dim, n, 91, ring=True)
+    u0 = rng_grid(dim, n, 92)
+    a = O.vcycle(f, u0.copy(), omega=omega)
+    b = O.wcycle(f, u0.copy(), omega=omega, gamma=1)
     assert np.array_equal(a, b)
 
 
-def test_large_gamma_tends_to_the_two_grid_cycle():
+@pytest.mark.parametrize("dim,n,omega", [(2, 31, [1.0]), (3, 15, [1.0, 1.0, 1.0, 1.0])])
+def test_large_gamma_tends_to_the_two_grid_cycle(dim, n, omega):
     """gamma cycles of pair 1 from zero converge to the exact solution of the
     blue grid's 5-point system, so for large gamma the cycle becomes the
     two-grid cycle whose coarsest grid is the first blue grid, solved
     exactly (the V-cycle with coarsest = (n - 1) / 2).  A wrong sign, spacing
     or operator in the coarse residual would leave a different limit."""
-    n = 31
-
     def w8(f, u):
-        return O.wcycle2d(f, u, p=1.0, gamma=8)
+        return O.wcycle(f, u, omega=omega, gamma=8, coarsest=1)
 
     def two_grid(f, u):
-        return O.vcycle(f, u, omega=[1.0], coarsest=(n - 1) // 2)
+        return O.vcycle(f, u, omega=omega, coarsest=(n - 1) // 2)
 
-    r_w = spectral_radius(2, n, O.DIAG, 2, [1.0], 3, vcycle=lambda f, u, **kw: w8(f, u))
-    r_2 = spectral_radius(2, n, O.DIAG, 2, [1.0], 3, vcycle=lambda f, u, **kw: two_grid(f, u))
-    assert r_w == pytest.approx(r_2, rel=1e-6)
-    r_v = spectral_radius(2, n, O.DIAG, 2, [1.0], 3)
+    r_w = spectral_radius(dim, n, O.DIAG, 2, omega, 3, vcycle=lambda f, u, **kw: w8(f, u))
+    r_2 = spectral_radius(dim, n, O.DIAG, 2, omega, 3, vcycle=lambda f, u, **kw: two_grid(f, u))
+    assert r_w == pytest.approx(r_2, rel=1e-5)
+    r_v = spectral_radius(dim, n, O.DIAG, 2, omega, 3)
     assert r_2 < r_v  # an exact coarse problem contracts faster than its V-cycle approximation
 
 
@@ -818,11 +818,11 @@ def test_gamma_cycle_fixed_point_and_odd_point_eigenspace():
     ustar = np.linalg.solve(A, M @ f.ravel())
     u = O.grid(2, n)
     for _ in range(60):
-        O.wcycle2d(f, u, p=1.0, gamma=2)
+        O.wcycle(f, u, omega=[1.0], gamma=2)
     np.testing.assert_allclose(interior(u).ravel(), ustar, rtol=0, atol=1e-11 * np.abs(ustar).max())
     idx = np.indices((n + 2, n + 2))
     inner = np.zeros((n + 2, n + 2), dtype=bool)
     inner[1:-1, 1:-1] = True
     e = np.where(inner & (idx.sum(0) % 2 == 1), np.random.default_rng(94).standard_normal((n + 2, n + 2)), 0.0)
-    w = O.wcycle2d(O.grid(2, n), e.copy(), p=1.3, gamma=3)
+    w = O.wcycle(O.grid(2, n), e.copy(), omega=[1.3], gamma=3)
     np.testing.assert_allclose(w, (1.0 - 1.3) * e, rtol=0, atol=1e-14 * np.abs(e).max())
