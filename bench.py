@@ -163,7 +163,7 @@ def extra_measurements(dev, stream):
     f = torch.from_numpy(I.square_large(N_SIDE)).to(dev)
     with Context(2, N_SIDE, precision="fp64") as c:
         u = c.new_grid()
-        ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u.zero_(), rtol=RTOL, max_cycles=60), 5, stream)
+        ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u, from_zero=True, rtol=RTOL, max_cycles=60), 5, stream)
         out["square4095_fp64"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc, "relres": rel}
         # the FP64 path's arithmetic roofline: its finest residual kernel
         # (k_res0_2d: 5 FP64 operations per point, probed live inside the
@@ -172,7 +172,7 @@ def extra_measurements(dev, stream):
         rate = c.fp64_rate()
         c.probe_set(0)
         for _ in range(3):
-            c.solve(f, u.zero_(), rtol=RTOL, max_cycles=60)
+            c.solve(f, u, from_zero=True, rtol=RTOL, max_cycles=60)
         k, pms = c.probe_read()
         c.probe_set(-1)
         avg = pms / max(k, 1)
@@ -190,7 +190,7 @@ def extra_measurements(dev, stream):
     for prec in ("mixed", "fp64"):  # the conventional 2^-l V-cycle the paper compares with
         with Context(2, N_SIDE, hierarchy="usual", precision=prec) as c:
             u = c.new_grid()
-            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u.zero_(), rtol=RTOL, max_cycles=80), 3, stream)
+            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u, from_zero=True, rtol=RTOL, max_cycles=80), 3, stream)
             out[f"square4095_usual_{prec}"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc,
                                                "relres": rel, "workload": "same problem, conventional V-cycle "
                                                "(full weighting, bilinear + red-black Jacobi, p = 1.121)"}
@@ -199,7 +199,7 @@ def extra_measurements(dev, stream):
     for prec in ("mixed", "fp64"):
         with Context(2, N_SIDE, order=4, precision=prec) as c:
             u = c.new_grid()
-            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u.zero_(), rtol=RTOL, max_cycles=80, raise_on_fail=False), 3, stream)
+            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u, from_zero=True, rtol=RTOL, max_cycles=80, raise_on_fail=False), 3, stream)
             out[f"square4095_order4_{prec}"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc,
                                                 "relres": rel, "workload": "same f, fourth-order residual "
                                                 "(Mehrstellen right-hand side), diagonal V-cycle p = 1.2"}
@@ -215,7 +215,7 @@ def extra_measurements(dev, stream):
     with Context(2, N_SIDE, precision="mixed") as c:
         c.set_sweeps(1)
         u = c.new_grid()
-        ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u.zero_(), rtol=RTOL, max_cycles=60, raise_on_fail=False),
+        ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f, u, from_zero=True, rtol=RTOL, max_cycles=60, raise_on_fail=False),
                                           3, stream)
         out["square4095_sweeps1_mixed"] = {"unknowns_per_s": N_SIDE**2 / (ms * 1e-3), "ms": ms, "cycles": cyc,
                                            "relres": rel, "workload": "same problem, one extra Jacobi sweep per "
@@ -225,14 +225,14 @@ def extra_measurements(dev, stream):
     for prec in ("mixed", "fp64"):  # fourth-order residual in 3D (19-point, Eq. Efos4)
         with Context(3, 255, order=4, precision=prec) as c:
             u = c.new_grid()
-            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f3, u.zero_(), rtol=RTOL, max_cycles=80, raise_on_fail=False), 3, stream)
+            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f3, u, from_zero=True, rtol=RTOL, max_cycles=80, raise_on_fail=False), 3, stream)
             out[f"cube255_order4_{prec}"] = {"unknowns_per_s": 255**3 / (ms * 1e-3), "ms": ms, "cycles": cyc,
                                              "relres": rel, "workload": "3D unit cube 255^3, same f, 19-point "
                                              "fourth-order residual, diagonal V-cycle (0.91, 0.80, 0.70, 1.77)"}
     for prec in ("mixed", "fp64"):
         with Context(3, 255, precision=prec) as c:
             u = c.new_grid()
-            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f3, u.zero_(), rtol=RTOL, max_cycles=60), 5, stream)
+            ms, (_, cyc, rel, _) = cuda_timed(lambda: c.solve(f3, u, from_zero=True, rtol=RTOL, max_cycles=60), 5, stream)
             out[f"cube255_{prec}"] = {"unknowns_per_s": 255**3 / (ms * 1e-3), "ms": ms, "cycles": cyc, "relres": rel,
                                       "workload": "3D unit cube 255^3, f = -6 pi^2 sin sin sin(2 pi z) + N(0,1e-6), "
                                                   "diagonal V-cycle (1.11, 1.42, 1.08, 0.99)"}
@@ -242,7 +242,7 @@ def extra_measurements(dev, stream):
             if prec == "mixed":  # the dominant 3D kernel, probed inside the solve as the headline's
                 c.probe_set(PROBE["family"])
                 for _ in range(3):
-                    c.solve(f3, u.zero_(), rtol=RTOL, max_cycles=60)
+                    c.solve(f3, u, from_zero=True, rtol=RTOL, max_cycles=60)
                 k, pms = c.probe_read()
                 c.probe_set(-1)
                 avg = pms / max(k, 1)
@@ -448,9 +448,8 @@ def main():
     u = ctx.new_grid()
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        u.zero_()
-        return ctx.solve(f, u, rtol=RTOL, max_cycles=60)
+    def step():  # a solve from u = 0 (mg_solve_zero: u is output only, zeroed inside the solve's graph)
+        return ctx.solve(f, u, rtol=RTOL, max_cycles=60, from_zero=True)
 
     warm = max(args.warmup, 3)  # at least three untimed warm-up steps
     for _ in range(warm):
@@ -512,7 +511,7 @@ def main():
             stream.wait_event(h2d[b])
             if k >= 2:
                 stream.wait_event(d2h[b])
-            ctx.solve(f_devs[b], u_devs[b].zero_(), rtol=RTOL, max_cycles=60)
+            ctx.solve(f_devs[b], u_devs[b], rtol=RTOL, max_cycles=60, from_zero=True)
             sol[b].record(stream)
         last = (steps - 1) % 2
         end = torch.cuda.Event(enable_timing=True)

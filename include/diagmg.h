@@ -181,11 +181,24 @@ mg_status mg_vcycle(mg_ctx *ctx, const double *f, double *u, void *stream);
 mg_status mg_solve(mg_ctx *ctx, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
                    double *relres_out, double *history, void *stream);
 
+/* mg_solve from u = 0: the same V-cycles (Sections 2.3, 3.3), but u (device,
+ * full grid, caller layout) is output only -- its contents on entry are never
+ * read, and it need not be zeroed.  On return it holds the same iterate, bit
+ * for bit, as mg_solve from a zeroed u.  The call zeroes u itself (a memset
+ * on `stream`, inside the solve's graph on the fused mixed path, whose start
+ * residual then is f itself and reads no u), which saves the caller's fill
+ * and one read of u per solve.  u must not overlap f (MG_EINVAL).  Arguments
+ * and returns as mg_solve; the graph cache keys a solve from zero apart from
+ * a warm start on the same arrays. */
+mg_status mg_solve_zero(mg_ctx *ctx, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
+                        double *relres_out, double *history, void *stream);
+
 /* mg_solve with HOST arrays, for callers whose data live in host memory:
  * f_host (the right-hand side), u0_host (the warm start, zero ring; NULL:
  * start from u = 0) and u_host (receives the result; may equal u0_host) are
  * full grids in the caller layout (pitch).  The call copies f and the warm
- * start to device copies owned by the context, runs mg_solve there and copies
+ * start to device copies owned by the context, runs mg_solve there (mg_solve_zero
+ * when u0_host is NULL) and copies
  * u back, all on `stream`, and returns once u_host holds the result.  The
  * copies overlap nothing else in the call; for full copy bandwidth the host
  * arrays should be page-locked (cudaHostAlloc / cudaHostRegister).  The first

@@ -41,6 +41,7 @@ SIGNATURES = {
     "mg_level_set": (_i, [_vp, _i, _i, _vp, _vp]),
     "mg_vcycle": (_i, [_vp, _vp, _vp, _vp]),
     "mg_solve": (_i, [_vp, _vp, _vp, _d, _i, _ip, _dp, _dp, _vp]),
+    "mg_solve_zero": (_i, [_vp, _vp, _vp, _d, _i, _ip, _dp, _dp, _vp]),
     "mg_solve_host": (_i, [_vp, _vp, _vp, _vp, _d, _i, _ip, _dp, _vp]),
     "mg_fp64_rate": (_i, [_vp, _dp, _vp]),
     "mg_launch_count": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),

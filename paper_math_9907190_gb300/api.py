@@ -247,15 +247,21 @@ class Context:
         N.check(N.lib().mg_vcycle(self._h, self._grid(f, "f"), self._grid(u, "u"), self._stream()), "mg_vcycle")
         return u
 
-    def solve(self, f, u=None, *, rtol: float = 1e-10, max_cycles: int = 100, raise_on_fail: bool = True):
-        """mg_solve from the warm start u (default zeros).  Returns (u, cycles, relres, history)."""
-        u = self.new_grid() if u is None else u
+    def solve(self, f, u=None, *, rtol: float = 1e-10, max_cycles: int = 100, raise_on_fail: bool = True,
+              from_zero: bool = False):
+        """mg_solve from the warm start u, or mg_solve_zero (from u = 0; u is
+        output only) when from_zero or when u is None (a new grid).  Returns
+        (u, cycles, relres, history)."""
+        if u is None:
+            u = torch.empty((self.n + 2,) * self.dim, dtype=torch.float64, device=self.device)
+            from_zero = True
         cyc, rel = ctypes.c_int(), ctypes.c_double()
         hist = (ctypes.c_double * max(1, max_cycles))()
-        st = N.lib().mg_solve(self._h, self._grid(f, "f"), self._grid(u, "u"), rtol, max_cycles, ctypes.byref(cyc),
-                              ctypes.byref(rel), hist, self._stream())
+        name = "mg_solve_zero" if from_zero else "mg_solve"
+        st = getattr(N.lib(), name)(self._h, self._grid(f, "f"), self._grid(u, "u"), rtol, max_cycles,
+                                    ctypes.byref(cyc), ctypes.byref(rel), hist, self._stream())
         if raise_on_fail:
-            N.check(st, "mg_solve")
+            N.check(st, name)
         return u, cyc.value, rel.value, list(hist[: cyc.value])
 
 

@@ -1268,12 +1268,14 @@ __device__ __forceinline__ unsigned mag_bits(double x) {
 // r) and lo (rlo, pitch rp), partial sums of hi^2 to part and of f^2 (FP32
 // squares: the norm of the right-hand side) to fpart.  Where u and its four
 // neighbours are all zero r = f, and a warp whose points all are skips the
-// FP64 arithmetic (a solve from u = 0 then moves bytes only).  Otherwise (end
-// of a solve): only the partial sums of r^2, nothing written.
+// FP64 arithmetic (a solve from u = 0 then moves bytes only); zu (a solve
+// from zero, mg_solve_zero): u is not read at all, r = f.  Otherwise (end of
+// a solve): only the partial sums of r^2, nothing written.
 template <bool START>
 __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f, const double *__restrict__ u,
                                                    int up, int n, int lg, A2<float> r, float *rlo, int rp,
-                                                   double *part, double *fpart, Ctrl *ctl, const int *done, Bt B) {
+                                                   double *part, double *fpart, Ctrl *ctl, int zu, const int *done,
+                                                   Bt B) {
     __shared__ double sh[32];
     __shared__ float shm[32];
     const int prob = blockIdx.z;
@@ -1291,8 +1293,8 @@ __global__ void __launch_bounds__(256) k_res_rr_2d(const double *__restrict__ f,
         double fr[RES_ROWS];
 #pragma unroll
         for (int q = 0; q < RES_ROWS; q++) fr[q] = q < rows ? f0p[(size_t)q * up] : 0.0;
-        bool zero = false;
-        if (START) {  // u zero on the thread's column (rows j0-1 .. j0+rows)?
+        bool zero = START && zu;
+        if (START && !zu) {  // u zero on the thread's column (rows j0-1 .. j0+rows)?
             unsigned ob = mag_bits(u0p[-up]) | mag_bits(u0p[(size_t)rows * up]);
 #pragma unroll
             for (int q = 0; q < RES_ROWS; q++)
@@ -1482,7 +1484,8 @@ __global__ void __launch_bounds__(256) k_green_3d(Red3<const T> vr, A3<const T> 
 template <bool START>
 __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f, const double *__restrict__ u,
                                                    int up, int n, int lg, A3<float> r, float *rlo, int rp,
-                                                   double *part, double *fpart, Ctrl *ctl, const int *done, Bt B) {
+                                                   double *part, double *fpart, Ctrl *ctl, int zu, const int *done,
+                                                   Bt B) {
     __shared__ double sh[32];
     __shared__ float shm[32];
     const int prob = bt_prob(B), bz = bt_z(B);
@@ -1497,9 +1500,10 @@ __global__ void __launch_bounds__(256) k_res_rr_3d(const double *__restrict__ f,
     const int planes = act ? min(RES3_PLANES, n + 1 - k0) : 0;
     const double *u0p = u + k0 * pl + (size_t)(act ? j : 1) * up + (act ? i : 1);
     const double *f0p = f + k0 * pl + (size_t)(act ? j : 1) * up + (act ? i : 1);
-    // u zero around every point of the block? (START only; block-uniform)
-    bool all_zero = false;
-    if (START) {
+    // u zero around every point of the block? (START only; block-uniform;
+    // zu: a solve from zero, u not read)
+    bool all_zero = START && zu;
+    if (START && !zu) {
         unsigned ob = 0;
         if (act && planes > 0) {
             // the thread's column (planes k0-1 .. k0+planes); x and y neighbours

@@ -111,6 +111,7 @@ struct mg_ctx {
     // double-buffered with r32b; lo in rlo; green pitch, in the pool)
     bool rr = false;
     bool rr_alloc = false;  // the carried-residual buffers exist (rr is off while extra > 0)
+    bool zstart = false;    // the solve being recorded or run starts from zero (mg_solve_zero, fused path)
     int extra = 0;          // extra Jacobi sweeps per level (mg_set_sweeps)
     int gamma = 1;          // coarse-problem cycles per pair (mg_set_gamma; 1: the V-cycle)
     void *wpool = nullptr;  // gamma > 1: per green level k >= 1, the kept residual and the accumulated correction
@@ -151,6 +152,7 @@ struct mg_ctx {
         double *u = nullptr;
         double rtol = -1.0;
         int max = -1, order = 0, extra = 0, gamma = 1;
+        bool zero = false;  // a solve from zero (mg_solve_zero)
         double omega[4] = {0, 0, 0, 0};
         long long prefix_kernels = 0, body_kernels = 0;  // launches of the prefix and of one cycle
         unsigned long long used = 0;
@@ -918,8 +920,11 @@ int vcycle_rr(mg_ctx *c, double *u, const int *done, cudaStream_t s) {
 // direct FP64 residual of the fused path.  start: the carried float-float
 // pair (hi in the current buffer, parity 0 at the start; lo in rlo), partial
 // sums of r^2 at part and of f^2 right after every problem's (fpart); end of
-// a solve: the partial sums of r^2 only.  Returns the partial sums per problem.
-int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s, bool start) {
+// a solve: the partial sums of r^2 only.  zu (start of a solve from zero): u
+// is not read.  Returns the partial sums per problem.
+int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, cudaStream_t s, bool start,
+                  bool zu = false) {
+    const int z = start && zu ? 1 : 0;
     const int n = c->d.n;
     const Level &l0 = c->lv[0];
     const int lg = 2 * c->m;  // log2(1/h^2), h = 2^-m
@@ -930,17 +935,17 @@ int launch_res_rr(mg_ctx *c, const double *f, const double *u, const int *done, 
     if (c->d.dim == 3) {
         if (start)
             LAUNCH_B(TAG_RESIDUAL, (k_res_rr_3d<true>), g, B2, f, u, c->d.pitch, n, lg, a3<float>(l0.r[0], l0),
-                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, done);
+                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, z, done);
         else
             LAUNCH_B(TAG_RESIDUAL, (k_res_rr_3d<false>), g, B2, f, u, c->d.pitch, n, lg, a3<float>(l0.r[0], l0),
-                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, done);
+                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, z, done);
     } else {
         if (start)
             LAUNCH_B(TAG_RESIDUAL, (k_res_rr_2d<true>), g, B2, f, u, c->d.pitch, n, lg, a2<float>(l0.r[0], l0),
-                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, done);
+                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, z, done);
         else
             LAUNCH_B(TAG_RESIDUAL, (k_res_rr_2d<false>), g, B2, f, u, c->d.pitch, n, lg, a2<float>(l0.r[0], l0),
-                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, done);
+                     (float *)c->rlo, l0.pitch, c->part, fpart, c->ctl, z, done);
     }
     c->nparts = np;
     return np;
@@ -1422,11 +1427,16 @@ static void launch_ctrl(mg_ctx *c, int np, int first, cudaGraphConditionalHandle
     }
 }
 
+// doubles of one full grid of the context (caller pitch)
+static size_t grid_len(const mg_ctx *c) {
+    return (size_t)c->d.pitch * (c->d.n + 2) * (c->d.dim == 3 ? (size_t)(c->d.n + 2) : 1);
+}
+
 // Prefix of a solve: control words, the norm of the right-hand side, the
 // residual of the warm start and the first control step (which sets the loop
 // condition when use_loop).  The fused mixed path takes the norm of f from
 // its start residual kernel.
-static void solve_prefix(mg_ctx *c, const double *f, const double *u, double rtol, int max_cycles,
+static void solve_prefix(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles,
                          cudaGraphConditionalHandle loop, int use_loop, cudaStream_t s) {
     if (c->nprob == 1) {
         LAUNCH(TAG_CONTROL, (k_ctrl_init), 1, 1, c->ctl, rtol, max_cycles);
@@ -1436,7 +1446,10 @@ static void solve_prefix(mg_ctx *c, const double *f, const double *u, double rto
     int np = 0, nfp;
     const double *fpart = c->part;
     if (c->rr) {
-        np = nfp = launch_res_rr(c, f, u, nullptr, s, true);
+        // a solve from zero: u zeroed here (an error shows in the caller's
+        // launch check), and the start residual reads none of it
+        if (c->zstart) (void)cudaMemsetAsync(u, 0, sizeof(double) * grid_len(c), s);
+        np = nfp = launch_res_rr(c, f, u, nullptr, s, true, c->zstart);
         fpart = c->part + (size_t)np * c->nprob;
     } else {
         nfp = launch_rhs_norm(c, f, u, s);
@@ -1534,7 +1547,8 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
 static bool solve_graph_matches(const mg_ctx *c, const mg_ctx::SolveGraph &e, const double *f, const double *u,
                                 double rtol, int max_cycles) {
     return e.exec && e.f == f && e.u == u && e.rtol == rtol && e.max == max_cycles && e.order == c->d.order &&
-           e.extra == c->extra && e.gamma == c->gamma && std::memcmp(e.omega, c->d.omega, sizeof e.omega) == 0;
+           e.extra == c->extra && e.gamma == c->gamma && e.zero == c->zstart &&
+           std::memcmp(e.omega, c->d.omega, sizeof e.omega) == 0;
 }
 
 static mg_status build_solve_graph(mg_ctx *c, mg_ctx::SolveGraph &slot, const double *f, double *u, double rtol,
@@ -1554,6 +1568,7 @@ static mg_status build_solve_graph(mg_ctx *c, mg_ctx::SolveGraph &slot, const do
     slot.order = c->d.order;
     slot.extra = c->extra;
     slot.gamma = c->gamma;
+    slot.zero = c->zstart;
     for (int q = 0; q < 4; q++) slot.omega[q] = c->d.omega[q];
     slot.prefix_kernels = c->g_prefix_kernels;
     slot.body_kernels = c->g_body_kernels;
@@ -1645,6 +1660,22 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
     return MG_OK;
 }
 
+mg_status mg_solve_zero(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
+                        double *relres_out, double *history, void *stream) {
+    if (!c || bad_grid(f) || bad_grid(u) || !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap)
+        return MG_EINVAL;
+    if (grids_overlap(f, u, grid_len(c))) return MG_EINVAL;
+    if (!c->rr || c->nprob != 1) {
+        // the per-stage paths read u from their first kernel on: zeros first
+        CK(cudaMemsetAsync(u, 0, sizeof(double) * grid_len(c), S(stream)));
+        return mg_solve(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, stream);
+    }
+    c->zstart = true;
+    const mg_status st = mg_solve(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, stream);
+    c->zstart = false;
+    return st;
+}
+
 mg_status mg_solve_host(mg_ctx *c, const double *f_host, const double *u0_host, double *u_host, double rtol,
                         int max_cycles, int *cycles_out, double *relres_out, void *stream) {
     if (!c || c->nprob != 1 || bad_grid(f_host) || bad_grid(u_host) || (u0_host && bad_grid(u0_host)) ||
@@ -1665,8 +1696,9 @@ mg_status mg_solve_host(mg_ctx *c, const double *f_host, const double *u0_host, 
     cudaStream_t s = S(stream);
     CK(cudaMemcpyAsync(c->io_f, f_host, bytes, cudaMemcpyHostToDevice, s));
     if (u0_host) CK(cudaMemcpyAsync(c->io_u, u0_host, bytes, cudaMemcpyHostToDevice, s));
-    else CK(cudaMemsetAsync(c->io_u, 0, bytes, s));
-    const mg_status st = mg_solve(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out, nullptr, stream);
+    const mg_status st = u0_host ? mg_solve(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out, nullptr, stream)
+                                 : mg_solve_zero(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out,
+                                                 nullptr, stream);
     if (st != MG_OK && st != MG_ENOCONV && st != MG_EDIVERGED) return st;
     CK(cudaMemcpyAsync(u_host, c->io_u, bytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

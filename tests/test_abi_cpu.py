@@ -64,6 +64,7 @@ def test_null_arguments_rejected(lib):
     assert lib.mg_coarse_solve(None, None) == N.MG_EINVAL
     assert lib.mg_vcycle(None, None, None, None) == N.MG_EINVAL
     assert lib.mg_solve(None, None, None, 1e-10, 10, None, None, None, None) == N.MG_EINVAL
+    assert lib.mg_solve_zero(None, None, None, 1e-10, 10, None, None, None, None) == N.MG_EINVAL
     assert lib.mg_level_get(None, 0, 0, None, None) == N.MG_EINVAL
     assert lib.mg_solve_host(None, None, None, None, 1e-10, 10, None, None, None) == N.MG_EINVAL
     assert lib.mg_fp64_rate(None, None, None) == N.MG_EINVAL
@@ -168,4 +169,5 @@ def test_python_api_surface():
     for m in ("solve", "tune", "close", "statuses"):
         assert callable(getattr(P.Batch, m)), m
     assert list(inspect.signature(P.Context.__init__).parameters)[1:3] == ["dim", "n"]
+    assert "from_zero" in inspect.signature(P.Context.solve).parameters
     assert P.default_omega(2, "diag", 2) == (1.052,)
