@@ -542,6 +542,21 @@ def main():
     e2e_ms = D.max_over_ranks(e2e_ms, dev)
     e2e_ok = bool(np.array_equal(u_host.numpy(), u.cpu().numpy()))
     barrier()
+    # the host link's own speed on the same buffers (best of 5 single copies,
+    # CUDA events on the stream): the end-to-end step's floor is the device
+    # solve plus one copy each way at these rates
+    def copy_ms(dst, src):
+        best = 1e30
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+    h2d_ms, d2h_ms = copy_ms(f, f_pin), copy_ms(u_host, u)
+    e2e_floor_ms = ms_max + h2d_ms + d2h_ms
 
     # live probe of the dominant kernel inside the same solve: every launch of
     # its family bracketed by CUDA events on the launching stream (the solver
@@ -582,6 +597,11 @@ def main():
                     "api": "mg_solve_host (C ABI): f from pinned host memory, solve from u = 0, u back to pinned "
                            "host memory; one call per step, copies not overlapped, wall-clock time",
                     "cycles": e2e_cyc, "relres": e2e_rel, "same_u_as_device_solve": e2e_ok,
+                    "link": {"h2d_gbs": f_pin.numel() * 8 / (h2d_ms * 1e-3) / 1e9,
+                             "d2h_gbs": u_host.numel() * 8 / (d2h_ms * 1e-3) / 1e9,
+                             "floor_ms": e2e_floor_ms, "frac": e2e_floor_ms / e2e_ms,
+                             "how": "one pinned-host copy each way on the step's buffers, timed alone; "
+                                    "floor = device solve + both copies at those rates"},
                     "pipelined": {"value": world * N / (e2e_pipe_ms * 1e-3), "ms_per_step": e2e_pipe_ms,
                                   "how": "Python API with torch copies on a copy stream: step k+1's input and "
                                          "step k-1's output move during step k's solve; the first input and the "

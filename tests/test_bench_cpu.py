@@ -68,7 +68,7 @@ def test_main_line_carries_the_roofline_and_e2e_keys():
     its pipelined variant, and the all-cores CPU baseline."""
     bench = _bench_module()
     src = open(os.path.join(ROOT, "bench.py")).read()
-    for key in ('"cycle_frac"', '"cycle"', '"roofline_fp64"', '"cycle_roofline"', '"pipelined"', '"api"',
+    for key in ('"cycle_frac"', '"cycle"', '"roofline_fp64"', '"cycle_roofline"', '"pipelined"', '"api"', '"link"',
                 '"single_core"', '"cpu_model"', '"nproc"', '"roofline"', '"cpu_baseline"', '"e2e"', '"clocks"',
                 '"gpu_launches"'):
         assert key in src, key
