@@ -86,6 +86,7 @@ struct mg_ctx {
     double *G = nullptr;        // coarsest dense inverse
     double *scal = nullptr;     // device scalar for norms
     int dev = 0;
+    int sms = 152;              // multiprocessors of the device
     // launch accounting and the optional event probe of one kernel family
     long long launches = 0;
     int probe_tag = -1;
@@ -617,10 +618,11 @@ size_t plan_cl2d(mg_ctx *c, int kd, int kc) {
 void plan_fast2d(mg_ctx *c) {
     c->fast2d = c->d.dim == 2 && c->d.hierarchy == MG_DIAG && c->extra == 0 && c->gamma == 1;
     if (!c->fast2d) return;
-    // pairs whose green grid has side <= 63 (or the tuned cut-off; 31 below a
-    // cluster) run in one thread block
+    // pairs whose green grid has side <= 63 (FP64 levels: 15, where the one
+    // block's FP64 arithmetic costs more than the launches it saves; or the
+    // tuned cut-off; 31 below a cluster) run in one thread block
     const bool want_cl = c->cl_ok && c->cl_top >= 15;
-    const int cut = c->cut_side > 0 ? c->cut_side : (want_cl ? 31 : 63);
+    const int cut = c->cut_side > 0 ? c->cut_side : (want_cl ? 31 : c->esz == 8 ? 15 : 63);
     int kc = 0;
     while (kc < c->K && c->lv[2 * kc].side > cut) kc++;
     c->kc = kc;
@@ -770,11 +772,24 @@ void launch_up_pair(mg_ctx *c, int k, double *u, const int *done, cudaStream_t s
 // order above.  Untuned: by size, as measured on the 4095^2 hierarchy (the
 // finest pair of the fused mixed solve is always streaming).
 constexpr int NCLS_FP32 = 6;
+int ff_strip(int cls);
 int tile_default(const mg_ctx *c, int k, bool up) {
     const int cells = c->lv[2 * k + 1].nb + 1, cls = tile_class(cells - 1);
-    if (c->esz == 8) return cls;
+    // FP64 levels (as measured by mg_tune on GB300): 16 x 8 tiles from 256
+    // cells up, 32 x 16 only for restrictions from 2048 cells
+    if (c->esz == 8) return up ? (cells >= 256 ? 1 : 2) : (cells >= 2048 ? 0 : cls == 0 ? 1 : cls);
     if (up) {
-        if (k == 0 && c->rr) return 0;
+        if (k == 0 && c->rr) {
+            // the fused finest pair: the longest strips (fewest warm-up rows)
+            // that still give 9/10 of one wave of warps (4 blocks of 4 warps
+            // per SM), else the shortest
+            const long long nb = c->lv[1].nb;
+            for (int q = 0; q < 2; q++) {
+                const long long items = ((nb + FF_W) / FF_W) * ((nb + ff_strip(q)) / ff_strip(q)) * c->nprob;
+                if (items * 10 >= 9LL * 16 * c->sms) return q;
+            }
+            return 2;
+        }
         return cells >= 512 ? 2 : cells >= 128 ? 4 : 5;
     }
     return cells >= 1024 ? 1 : cells >= 512 ? 2 : cls + 3;
@@ -1161,6 +1176,10 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
     c->h = 1.0 / (d->n + 1);
     c->esz = d->precision == MG_FP64 ? 8 : 4;
     cudaGetDevice(&c->dev);
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess || c->sms < 1) {
+        cudaGetLastError();
+        c->sms = 152;
+    }
     build_levels(c);
     size_t total = 0;
     for (auto &l : c->lv) total += (size_t)l.ncos * 2 * ((l.len * c->esz + 255) / 256 * 256);
