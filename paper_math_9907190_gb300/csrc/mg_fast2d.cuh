@@ -22,6 +22,30 @@
 
 namespace mg {
 
+// Asynchronous global -> shared copies (cp.async): 16, 8 or 4 bytes, the
+// destination zero-filled where ok is false (src is then any address inside
+// its array; no byte of it is read).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool ok) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+// one level value (FP32 or FP64)
+template <typename T> __device__ __forceinline__ void cp_async_el(T *dst, const T *src, bool ok) {
+    if (sizeof(T) == 4) cp_async4(dst, src, ok);
+    else cp_async8(dst, src, ok);
+}
+
 // loop of a 256-thread block over the points (x, y) of a W x H region, the
 // points spread evenly over all threads (x fastest)
 #define MG_FOR2(W, H)                                                                             \
@@ -183,10 +207,15 @@ __global__ void __launch_bounds__(256) k_down_pair_2d(A2<const T> g, A2<T> ee, A
     g = bt_at(g, prob, B); ee = bt_at(ee, prob, B); oo = bt_at(oo, prob, B); blue = bt_at(blue, prob, B);
     const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
     const int n = 2 * nb + 1;
+    // all of a thread's copies in flight at once (one L2 round trip, not one
+    // per element)
     MG_FOR2(GX, GY) {
         const int gx = 2 * a0 - 2 + x, gy = 2 * b0 - 2 + y;
-        sg[y][x] = (gx >= 0 && gx <= n + 1 && gy >= 0 && gy <= n + 1) ? g(gx, gy) : T(0);
+        const bool ok = gx >= 0 && gx <= n + 1 && gy >= 0 && gy <= n + 1;
+        cp_async_el(&sg[y][x], ok ? &g(gx, gy) : g.p, ok);
     }
+    cp_async_commit();
+    cp_async_wait0();
     __syncthreads();
     // OO(c,d) at green (2c+1, 2d+1) -> smem index (2c+1) - (2a0-2) = 2(c-a0)+3
     MG_FOR2(OX, OY) {
@@ -241,23 +270,30 @@ __global__ void __launch_bounds__(256) k_up_pair_2d(A2<const T> blue, A2<const T
     if (B.utab) u = B.utab[prob];
     const int a0 = blockIdx.x * TA, b0 = blockIdx.y * TB;
     const int n = 2 * nb + 1;
-    // loads
-MG_FOR2(TA + 5, TB + 5) {
+    // loads: all of a thread's copies in flight at once (one L2 round trip,
+    // not one per element); out-of-range values are zero-filled
+    MG_FOR2(TA + 5, TB + 5) {
         const int a = a0 - 2 + x, b = b0 - 2 + y;
-        S.b[y][x] = (a >= 0 && a <= nb + 1 && b >= 0 && b <= nb + 1) ? blue(a, b) : T(0);
+        const bool ok = a >= 0 && a <= nb + 1 && b >= 0 && b <= nb + 1;
+        cp_async_el(&S.b[y][x], ok ? &blue(a, b) : blue.p, ok);
     }
-MG_FOR2(TA + 4, TB + 4) {
+    MG_FOR2(TA + 4, TB + 4) {
         const int a = a0 - 2 + x, b = b0 - 2 + y;
-        S.roo[y][x] = (a >= 0 && a <= nb && b >= 0 && b <= nb) ? roo(a, b) : T(0);
+        const bool ok = a >= 0 && a <= nb && b >= 0 && b <= nb;
+        cp_async_el(&S.roo[y][x], ok ? &roo(a, b) : roo.p, ok);
     }
-MG_FOR2(TA + 3, TB + 3) {
+    MG_FOR2(TA + 3, TB + 3) {
         const int a = a0 - 1 + x, b = b0 - 1 + y;
-        S.ree[y][x] = (a >= 1 && a <= nb && b >= 1 && b <= nb) ? ree(a, b) : T(0);
+        const bool ok = a >= 1 && a <= nb && b >= 1 && b <= nb;
+        cp_async_el(&S.ree[y][x], ok ? &ree(a, b) : ree.p, ok);
     }
-MG_FOR2(2 * TA + 4, 2 * TB + 4) {
+    MG_FOR2(2 * TA + 4, 2 * TB + 4) {
         const int gx = 2 * a0 - 2 + x, gy = 2 * b0 - 2 + y;
-        S.rg[y][x] = (gx >= 1 && gx <= n && gy >= 1 && gy <= n) ? rg(gx, gy) : T(0);
+        const bool ok = gx >= 1 && gx <= n && gy >= 1 && gy <= n;
+        cp_async_el(&S.rg[y][x], ok ? &rg(gx, gy) : rg.p, ok);
     }
+    cp_async_commit();
+    cp_async_wait0();
     __syncthreads();
     // red points not blue: OO(c,d), c in [a0-2, a0+TA+1]; smem x = c - a0 + 2 in voo and in b
     MG_FOR2(TA + 4, TB + 4) {
@@ -452,13 +488,15 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_2d(CoarsePlan2d P, A2<const
     const int tx = tid & 31, ty = tid >> 5;
     for (int q = tid; q < P.total; q += nt) sm[q] = T(0);
     __syncthreads();
-    {   // load the green residual of pair kc
+    {   // load the green residual of pair kc (a thread's copies all in flight at once)
         const int n = P.nk[0];
         A2<T> g{sm + P.og_r[0], n + 2};
         for (int j = 1 + ty; j <= n; j += 32)
-            for (int i = 1 + tx; i <= n; i += 32) g(i, j) = rg_in(i, j);
+            for (int i = 1 + tx; i <= n; i += 32) cp_async_el(&g(i, j), &rg_in(i, j), true);
+        cp_async_commit();
     }
     gp.store(Gs, P.ng, tid);
+    cp_async_wait0();
     __syncthreads();
     cta_pairs_2d<T>(P, sm, Gs);
     {
@@ -832,22 +870,9 @@ constexpr int FF_WARPS = 4;
 // 16-byte aligned with an even pitch (vector access to u).
 enum { UP_RR = 0, UP_ADD = 1, UP_STORE = 2 };
 
-// Asynchronous global -> shared copies (cp.async), used to keep one step of
-// every warp's inputs in flight while it computes the current step.  Each
-// lane copies and later reads only its own slots, so a lane's own
-// wait_group orders them; src_bytes 0 fills the slot with zeros (the address
-// is then not read and must only be a valid pointer).
-__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool ok) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-                 "l"(src), "r"(ok ? 16 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool ok) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-                 "l"(src), "r"(ok ? 8 : 0) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// The streaming kernels below keep one step of every warp's inputs in flight
+// (cp.async) while the warp computes the current step.  Each lane copies and
+// later reads only its own slots, so a lane's own wait_group orders them.
 
 // one step's inputs of one warp in shared memory (slot = lane): the chain's
 // blue row b+3, red OO / EE rows b+2 and green residual rows 2b+2, 2b+3 over

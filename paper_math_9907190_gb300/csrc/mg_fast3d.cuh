@@ -19,11 +19,6 @@ constexpr int GS_GW = GS_TX + 8;                 // residual row: 16-byte chunks
 // carried residual of plane z needs C of plane z-1, hence F from z-2
 constexpr int GS_WARM = 3, GS_WARM_RR = 4;
 
-__device__ __forceinline__ void cp_async4(void *dst, const void *src, bool ok) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
-                 "l"(src), "r"(ok ? 4 : 0) : "memory");
-}
-
 struct GreenSSmem {
     // red planes z+1..z+4 (ring, slot = plane & 3): fine row y holds its red
     // points x (x = y + plane mod 2) at index (x >> 1) - (16 bx - 4)
