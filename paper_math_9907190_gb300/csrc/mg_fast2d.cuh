@@ -35,6 +35,7 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src, bool ok) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async4(void *dst, const void *src, bool ok) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
@@ -897,9 +898,14 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
                                                             double *part, Ctrl *ctl, const int *done, Bt B) {
     __shared__ double sh[32];
     __shared__ float shm[32];
-    __shared__ FFChain SC[FF_WARPS][2];
-    __shared__ FFU SU[MODE != UP_STORE ? FF_WARPS : 1][2];
-    __shared__ FFL SL[MODE == UP_RR ? FF_WARPS : 1][2];
+    // stages of the copy pipeline: a coarser pair (UP_STORE, latency-bound:
+    // few steps per warp and little arithmetic per step) copies two steps
+    // ahead, the finest pair one (its registers and shared memory are the
+    // limit there)
+    constexpr int NST = MODE == UP_STORE ? 3 : 2;
+    __shared__ FFChain SC[FF_WARPS][NST];
+    __shared__ FFU SU[MODE != UP_STORE ? FF_WARPS : 1][NST];
+    __shared__ FFL SL[MODE == UP_RR ? FF_WARPS : 1][NST];
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int K = FF_K;
     constexpr bool RR = MODE == UP_RR, UPD = MODE != UP_STORE;
@@ -979,11 +985,17 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
             bl2[0] = q.x; bl2[1] = q.y;
         }
         issue(0, bs);
-        for (int b = bs; b < b1; b++) {
-            const int st = (b - bs) & 1;
-            if (b + 1 < b1) issue(st ^ 1, b + 1);
+        if (NST == 3) {
+            if (bs + 1 < b1) issue(1, bs + 1);
             else cp_async_commit();
-            cp_async_wait1();  // this lane's copies of step b have landed
+        }
+        for (int b = bs; b < b1; b++) {
+            const int st = NST == 2 ? (b - bs) & 1 : (b - bs) % 3;
+            // one group committed per step: the copies of step b + NST - 1
+            if (b + NST - 1 < b1) issue(NST == 2 ? st ^ 1 : (st + 2) % 3, b + NST - 1);
+            else cp_async_commit();
+            if (NST == 2) cp_async_wait1();  // this lane's copies of step b have landed
+            else cp_async_wait2();
             float bl3[K], ro2[K], re2[K], g2[2 * K], g3[2 * K];
             {
                 const FFChain &C = SC[w][st];
@@ -1183,12 +1195,15 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_down_ff_2d(A2<const float> g,
             if (in && y >= 0 && y <= n + 1) return *reinterpret_cast<const float4 *>(&g(2 * a0, y));
             return make_float4(0.f, 0.f, 0.f, 0.f);
         };
-        // green rows 2b-1 .. 2b+2 of step b; the next step's two rows are
-        // loaded one step ahead
+        // green rows 2b-1 .. 2b+2 of step b; the two rows a step adds are
+        // loaded two steps ahead (a warp's few steps are latency-bound)
         float4 gm = row(2 * bs - 1), g0 = row(2 * bs), g1 = row(2 * bs + 1), g2 = row(2 * bs + 2);
+        float4 p1 = row(2 * bs + 3), p2 = row(2 * bs + 4);  // the rows step bs adds
         float om0 = 0.f, om1 = 0.f;  // OO(a0, b-1), OO(a0+1, b-1)
         for (int b = bs; b < b1; b++) {
-            const float4 n1 = row(2 * b + 3), n2 = row(2 * b + 4);
+            const float4 n1 = p1, n2 = p2;
+            p1 = row(2 * b + 5);  // the rows step b + 1 adds
+            p2 = row(2 * b + 6);
             const float g0L = __shfl_up_sync(FULL, g0.w, 1), g1R = __shfl_down_sync(FULL, g1.x, 1);
             // red EE of cells a0, a0+1 at green (2a, 2b); OO at (2a+1, 2b+1)
             const bool yb = b >= 1;
