@@ -672,7 +672,10 @@ void plan_fast3d(mg_ctx *c) {
     // at most (a 7^3 coarsest grid runs with per-stage kernels and k_coarse)
     c->fast3d = c->d.dim == 3 && c->d.hierarchy == MG_DIAG && c->d.coarsest <= 3 && c->gamma == 1;
     if (!c->fast3d) return;
-    const int cut = c->cut_side > 0 ? c->cut_side : 15;
+    // triples whose green side is <= 15 (FP64 levels: 7, where the one
+    // block's FP64 arithmetic costs more than the launches it saves; or the
+    // tuned cut-off) run in one thread block
+    const int cut = c->cut_side > 0 ? c->cut_side : c->esz == 8 ? 7 : 15;
     int kc = 0;
     while (kc < c->K && c->lv[3 * kc].side > cut) kc++;
     c->kc = kc;
@@ -775,6 +778,14 @@ constexpr int NCLS_FP32 = 6;
 int ff_strip(int cls);
 int tile_default(const mg_ctx *c, int k, bool up) {
     const int cells = c->lv[2 * k + 1].nb + 1, cls = tile_class(cells - 1);
+    // a batch's problems of one size share each launch, which then has
+    // parallelism to spare: the largest tiles (FP64) or the streaming kernels
+    // (FP32) at every level (as measured by mg_batch_tune on GB300 with ~80
+    // problems per size)
+    if (c->nprob > 1 && !(k == 0 && c->rr && up)) {
+        if (c->esz == 8) return cells >= 128 ? 0 : cells >= 64 ? 1 : 2;
+        return 1;
+    }
     // FP64 levels (as measured by mg_tune on GB300): 16 x 8 tiles from 256
     // cells up, 32 x 16 only for restrictions from 2048 cells
     if (c->esz == 8) return up ? (cells >= 256 ? 1 : 2) : (cells >= 2048 ? 0 : cls == 0 ? 1 : cls);
