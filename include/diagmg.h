@@ -199,11 +199,14 @@ mg_status mg_solve_zero(mg_ctx *ctx, const double *f, double *u, double rtol, in
  * full grids in the caller layout (pitch).  The call copies f and the warm
  * start to device copies owned by the context, runs mg_solve there (mg_solve_zero
  * when u0_host is NULL) and copies
- * u back, all on `stream`, and returns once u_host holds the result.  The
- * copies overlap nothing else in the call; for full copy bandwidth the host
- * arrays should be page-locked (cudaHostAlloc / cudaHostRegister).  The first
- * call allocates the two device copies (MG_ENOMEM if that fails); later calls
- * allocate nothing.  Single-problem contexts only; u_host must not overlap
+ * u back, and returns once u_host holds the result.  The copy in runs on
+ * `stream`; on the fused mixed path the copy back starts as soon as the last
+ * cycle has written u (an event the solve's graph records) and runs on a
+ * stream of the context beside the direct residual that closes the solve,
+ * otherwise it follows the solve on `stream`.  For full copy bandwidth the
+ * host arrays should be page-locked (cudaHostAlloc / cudaHostRegister).  The
+ * first call allocates the two device copies and creates that stream
+ * (MG_ENOMEM / MG_ECUDA if that fails); later calls allocate nothing.  Single-problem contexts only; u_host must not overlap
  * f_host.  Returns what mg_solve returns. */
 mg_status mg_solve_host(mg_ctx *ctx, const double *f_host, const double *u0_host, double *u_host, double rtol,
                         int max_cycles, int *cycles_out, double *relres_out, void *stream);

@@ -143,6 +143,11 @@ struct mg_ctx {
     bool pdl = false;           // programmatic dependent launch (default per configuration; DIAGMG_PDL=0/1)
     int pdl_max_blocks = 0;     // > 0: only for grids of at most this many blocks (DIAGMG_PDL_MAX_BLOCKS)
     cudaStream_t cs1 = nullptr, cs2 = nullptr;
+    // fused mixed path: recorded once the last cycle has written u (before the
+    // direct residual that closes a solve), so that mg_solve_host copies u
+    // back while that residual runs, on its own stream cs_io
+    cudaEvent_t ev_ufinal = nullptr, ev_io = nullptr;
+    cudaStream_t cs_io = nullptr;
     // instantiated solve graphs, keyed by their arguments and the context's
     // settings; a few are kept (least recently used replaced) so that a caller
     // alternating between buffers does not rebuild a graph per solve
@@ -1157,6 +1162,9 @@ mg_status mg_destroy(mg_ctx *c) {
     drop_solve_graphs(c);
     if (c->cs1) cudaStreamDestroy(c->cs1);
     if (c->cs2) cudaStreamDestroy(c->cs2);
+    if (c->cs_io) cudaStreamDestroy(c->cs_io);
+    if (c->ev_ufinal) cudaEventDestroy(c->ev_ufinal);
+    if (c->ev_io) cudaEventDestroy(c->ev_io);
     cudaFree(c->pool);
     cudaFree(c->part);
     cudaFree(c->ctl);
@@ -1305,7 +1313,8 @@ static mg_status create_ctx(mg_ctx **out, const mg_desc *d, int nprob) {
         c->pdl_max_blocks = eb ? std::atoi(eb) : (d->precision == MG_FP64 ? 256 : 0);
     }
     if (cudaStreamCreateWithFlags(&c->cs1, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&c->cs2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_ufinal, cudaEventDisableTiming) != cudaSuccess) {
         mg_destroy(c);
         return cuda_fail(cudaGetLastError(), "mg_create streams");
     }
@@ -1565,6 +1574,12 @@ static mg_status capture_solve(mg_ctx *c, const double *f, double *u, double rto
     }
     if (c->rr) {  // the carried residual ignores the rounding of u: report a direct one
         const long long l2 = c->launches;
+        // u is final here: an event record node of the graph (External: a
+        // plain record inside a capture would only order the capture's streams)
+        if (cudaEventRecordWithFlags(c->ev_ufinal, s, cudaEventRecordExternal) != cudaSuccess) {
+            c->capturing = false;
+            return cuda_fail(cudaGetLastError(), "solve capture (u final)");
+        }
         const int np3 = launch_res_rr(c, f, u, nullptr, s, false);
         LAUNCH(TAG_CONTROL, (k_final_true), c->nprob, 1024, c->part, np3, c->ctl);
         c->g_prefix_kernels += c->launches - l2;
@@ -1655,29 +1670,47 @@ static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double r
     return MG_OK;
 }
 
-mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
-                   double *relres_out, double *history, void *stream) {
-    if (!c || bad_grid(f) || bad_grid(u) || !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap)
-        return MG_EINVAL;
+// mg_solve; with u_host, u is also copied to that host array before the call
+// returns: on the fused mixed path's graph the copy starts once the last
+// cycle has written u (event ev_ufinal) and runs on cs_io beside the direct
+// residual that closes the solve, else after the solve on the stream
+static mg_status solve_impl(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
+                            double *relres_out, double *history, void *stream, double *u_host) {
     cudaStream_t s = S(stream);
+    const size_t ubytes = sizeof(double) * grid_len(c);
+    mg_status st;
+    Ctrl host{};
     // a probe needs one event pair per launch, which a replayed graph cannot give
-    if (!c->use_graph || c->probe_tag >= 0)
-        return solve_host_loop(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, s);
+    if (!c->use_graph || c->probe_tag >= 0) {
+        st = solve_host_loop(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, s);
+        if (u_host && (st == MG_OK || st == MG_ENOCONV || st == MG_EDIVERGED)) {
+            CK(cudaMemcpyAsync(u_host, u, ubytes, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+        }
+        return st;
+    }
     mg_ctx::SolveGraph *hit = nullptr, *lru = &c->gcache[0];
     for (auto &e : c->gcache) {
         if (solve_graph_matches(c, e, f, u, rtol, max_cycles)) { hit = &e; break; }
         if (e.used < lru->used) lru = &e;
     }
     if (!hit) {
-        mg_status st = build_solve_graph(c, *lru, f, u, rtol, max_cycles);
+        st = build_solve_graph(c, *lru, f, u, rtol, max_cycles);
         if (st != MG_OK) return st;
         hit = lru;
     }
     hit->used = ++c->gtick;
     CK(cudaGraphLaunch(hit->exec, s));
-    Ctrl host{};
+    const bool early = u_host && c->rr;  // the copy of u overlaps the closing residual
+    if (early) {
+        CK(cudaStreamWaitEvent(c->cs_io, c->ev_ufinal, 0));
+        CK(cudaMemcpyAsync(u_host, u, ubytes, cudaMemcpyDeviceToHost, c->cs_io));
+        CK(cudaEventRecord(c->ev_io, c->cs_io));
+    }
     CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    if (u_host && !early) CK(cudaMemcpyAsync(u_host, u, ubytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (early) CK(cudaEventSynchronize(c->ev_io));
     c->launches += hit->prefix_kernels + (long long)host.cycles * hit->body_kernels;
     if (cycles_out) *cycles_out = host.cycles;
     if (relres_out) *relres_out = host.relres;
@@ -1690,20 +1723,34 @@ mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_c
     return MG_OK;
 }
 
-mg_status mg_solve_zero(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
-                        double *relres_out, double *history, void *stream) {
+mg_status mg_solve(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
+                   double *relres_out, double *history, void *stream) {
+    if (!c || bad_grid(f) || bad_grid(u) || !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap)
+        return MG_EINVAL;
+    return solve_impl(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, stream, nullptr);
+}
+
+// mg_solve_zero, with the optional host destination of solve_impl
+static mg_status solve_zero_impl(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles,
+                                 int *cycles_out, double *relres_out, double *history, void *stream,
+                                 double *u_host) {
     if (!c || bad_grid(f) || bad_grid(u) || !(rtol >= 0.0) || max_cycles < 0 || max_cycles > c->hist_cap)
         return MG_EINVAL;
     if (grids_overlap(f, u, grid_len(c))) return MG_EINVAL;
     if (!c->rr || c->nprob != 1) {
         // the per-stage paths read u from their first kernel on: zeros first
         CK(cudaMemsetAsync(u, 0, sizeof(double) * grid_len(c), S(stream)));
-        return mg_solve(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, stream);
+        return solve_impl(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, stream, u_host);
     }
     c->zstart = true;
-    const mg_status st = mg_solve(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, stream);
+    const mg_status st = solve_impl(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, stream, u_host);
     c->zstart = false;
     return st;
+}
+
+mg_status mg_solve_zero(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
+                        double *relres_out, double *history, void *stream) {
+    return solve_zero_impl(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, stream, nullptr);
 }
 
 mg_status mg_solve_host(mg_ctx *c, const double *f_host, const double *u0_host, double *u_host, double rtol,
@@ -1723,16 +1770,21 @@ mg_status mg_solve_host(mg_ctx *c, const double *f_host, const double *u0_host, 
             return MG_ENOMEM;
         }
     }
+    if (!c->cs_io) {  // the copy-back stream and its completion event
+        if (cudaStreamCreateWithFlags(&c->cs_io, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_io, cudaEventDisableTiming) != cudaSuccess) {
+            if (c->cs_io) cudaStreamDestroy(c->cs_io);
+            c->cs_io = nullptr;
+            return cuda_fail(cudaGetLastError(), "mg_solve_host stream");
+        }
+    }
     cudaStream_t s = S(stream);
     CK(cudaMemcpyAsync(c->io_f, f_host, bytes, cudaMemcpyHostToDevice, s));
     if (u0_host) CK(cudaMemcpyAsync(c->io_u, u0_host, bytes, cudaMemcpyHostToDevice, s));
-    const mg_status st = u0_host ? mg_solve(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out, nullptr, stream)
-                                 : mg_solve_zero(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out,
-                                                 nullptr, stream);
-    if (st != MG_OK && st != MG_ENOCONV && st != MG_EDIVERGED) return st;
-    CK(cudaMemcpyAsync(u_host, c->io_u, bytes, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    return st;
+    // the solve copies u back itself (overlapped with its closing residual)
+    return u0_host ? solve_impl(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out, nullptr, stream, u_host)
+                   : solve_zero_impl(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out, nullptr, stream,
+                                     u_host);
 }
 
 // Section 2.4 / 3.4: a fourth-order solution is reached fastest by first

@@ -38,6 +38,23 @@ def test_host_solve_equals_device_solve(dim, n, prec):
         assert ch2 == cd2 and rh2 == rd2 and np.array_equal(w.numpy(), ud2.cpu().numpy())
 
 
+@pytest.mark.parametrize("dim,n", [(2, 1023), (3, 127)])
+def test_host_solve_copy_back_waits_for_the_last_cycle(dim, n):
+    """On the fused mixed path u is copied back while the closing direct
+    residual still runs (from an event the solve's graph records once the
+    last cycle has written u).  Alternating two right-hand sides, every result
+    must be that of its own solve: a copy that did not wait would return the
+    previous call's u."""
+    fs = [torch.from_numpy(I.uniform_f(dim, n, 80 + k)).pin_memory() for k in range(2)]
+    with Context(dim, n, precision="mixed") as c:
+        want = [c.solve(f.to(DEV), rtol=1e-10)[0].cpu().numpy() for f in fs]
+        uh = torch.empty_like(fs[0]).pin_memory()
+        for k in (0, 1, 0, 1, 1, 0):
+            uh.fill_(float("nan"))
+            c.solve_host(fs[k], uh, rtol=1e-10)
+            assert np.array_equal(uh.numpy(), want[k]), k
+
+
 def test_host_solve_refuses_bad_arguments():
     with Context(2, 63) as c:
         f = torch.zeros((65, 65), dtype=torch.float64)
