@@ -367,6 +367,56 @@ def oracle_cpu_baseline(f):
     return out, u
 
 
+def oracle_cpu_configs():
+    """The oracle (C, FP64) on all host cores on the other configurations of
+    the measurement table: the 3D unit cube 255^3 in full, and seeded subsets
+    of the 512-problem batch (16 problems) and of the 64 x 127^3 gradient
+    batch (2 problems, forward and adjoint solve); per-unknown rates, the
+    subsets stated.  About 5 s of host time."""
+    import numpy as np
+
+    import oracle as O
+    from paper_math_9907190_gb300 import inputs as I
+    used = O.set_threads(os.cpu_count() or 1)
+    out = {}
+    f3 = I.cube(255)
+    t0 = time.perf_counter()
+    _, cyc, rel, _ = O.solve(f3, omega=[1.11, 1.42, 1.08, 0.99], rtol=RTOL, max_cycles=40)
+    dt = time.perf_counter() - t0
+    out["cube255"] = {"value": 255**3 / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+                      "sample": f"one full oracle solve of the 3D 255^3 workload ({cyc} FP64 V-cycles to relres "
+                                f"{rel:.2e}, {dt:.2f} s)"}
+    del f3
+    sides = I.batch_sides(512)
+    pick = sorted(np.random.default_rng(3).choice(len(sides), 16, replace=False).tolist())
+    tot, dt = 0, 0.0
+    for b in pick:
+        fb = I.batch_f(sides[b], b)
+        t0 = time.perf_counter()
+        O.solve(fb, rtol=RTOL, max_cycles=40)
+        dt += time.perf_counter() - t0
+        tot += sides[b] ** 2
+    out["batch512_subset"] = {"value": tot / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+                              "sample": f"16 of the 512 problems (seed 3: sides {[sides[b] for b in pick]}), "
+                                        f"each solved in full one after the other, {tot} unknowns in {dt:.2f} s"}
+    n = 127
+    ut = I.grad_target(n)
+    dt = 0.0
+    for b in range(2):
+        fb = I.grad_f(n, b)
+        t0 = time.perf_counter()
+        u, _, _, _ = O.solve(fb, omega=[1.11, 1.42, 1.08, 0.99], rtol=RTOL, max_cycles=40)
+        g = I.zero_ring(2.0 * (u - ut))
+        O.solve(g, omega=[1.11, 1.42, 1.08, 0.99], rtol=RTOL, max_cycles=40)  # the adjoint (L is symmetric)
+        dt += time.perf_counter() - t0
+    out["grad64x127_subset"] = {"solves_per_s": 4 / dt, "unknowns_per_s": 4 * n**3 / dt, "cores": used,
+                                "kind": "oracle",
+                                "sample": f"2 of the 64 problems at 127^3, forward and adjoint solve each, "
+                                          f"{dt:.2f} s"}
+    O.set_threads(1)
+    return out
+
+
 def run_reference(args):
     """Reference arm: the CPU FP64 oracle on all host cores, rank 0 only; a
     step is one full oracle solve of the workload from u = 0 to 1e-10."""
@@ -621,6 +671,8 @@ def main():
             line["extra"]["square4095_usual_mixed"]["ms"] / ms_max)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb, u_orc = oracle_cpu_baseline(f_host)
+        if not args.no_extra:  # the oracle on the other configurations of the measurement table
+            cb["configs"] = oracle_cpu_configs()
         line["cpu_baseline"] = cb
         ug = u.cpu().numpy()
         line["config"]["rel_err_vs_oracle"] = float(np.linalg.norm(ug - u_orc) / np.linalg.norm(u_orc))

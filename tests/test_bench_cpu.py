@@ -70,6 +70,7 @@ def test_main_line_carries_the_roofline_and_e2e_keys():
     src = open(os.path.join(ROOT, "bench.py")).read()
     for key in ('"cycle_frac"', '"cycle"', '"roofline_fp64"', '"cycle_roofline"', '"pipelined"', '"api"', '"link"',
                 '"single_core"', '"cpu_model"', '"nproc"', '"roofline"', '"cpu_baseline"', '"e2e"', '"clocks"',
+                '"configs"', '"cube255"', '"batch512_subset"', '"grad64x127_subset"',
                 '"gpu_launches"'):
         assert key in src, key
     r = bench.cycle_roofline(4095**2, 9, 2.0, 6746.3)
