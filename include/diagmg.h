@@ -313,11 +313,19 @@ mg_status mg_batch_status(const mg_batch *batch, int *status);
  * 0 if taken from the cache or nothing is tunable.  Synchronous.
  * mg_tune_info reports the cut-off (0 = default) and the tile class of each
  * pair kernel outside the thread block and the cluster, npairs of them (FP64
- * levels: tiles of 0: 32x16 cells,
- * 1: 16x8, 2: 8x8; FP32 levels: strips of 0: 32, 1: 16, 2: 8 cell rows for
- * the prolongation and 16, 8, 4 for the restriction);
+ * levels: tiles of 0: 32x16 cells, 1: 16x8, 2: 8x8; FP32 levels: streaming
+ * kernels with strips of 0: 32, 1: 16, 2: 8 cell rows for the prolongation
+ * and 16, 8, 4 for the restriction, 3-5: the tiles of 0-2);
  * tiles_down / tiles_up need 32 entries.  mg_batch_tune does the same for
- * every size group of a batch (f, u as in mg_solve_batched). */
+ * every size group of a batch (f, u as in mg_solve_batched).
+ * Untuned contexts take defaults fitted to the tuner's choices on GB300 from
+ * 255^2 to 4095^2 (within 2% of them there): the coarse thread block takes
+ * pairs of green side <= 63 (FP64: 15) and triples <= 15 (FP64: 7); the
+ * fused finest pair of the mixed path the longest strips that still fill the
+ * device with warps, the coarser FP32 pairs streaming kernels from 512 cells
+ * and tiles below, FP64 pairs 16x8 tiles from 256 cells; a context of
+ * several problems (a batch's size group) the largest FP64 tiles or the
+ * FP32 streaming kernels at every level. */
 mg_status mg_tune(mg_ctx *ctx, const double *f, double *u, const char *cache_path, int *measured_out,
                   void *stream);
 mg_status mg_tune_info(const mg_ctx *ctx, int *cut_side, int *npairs, int *tiles_down, int *tiles_up);
