@@ -667,12 +667,14 @@ __global__ void __launch_bounds__(1024) k_coarse_cta_3d(CoarsePlan3d P, A3<const
     const int ntri = P.K - P.kc;
     auto G3 = [&](int off, int n) { return A3<T>{sm + off, n + 2, n + 2}; };
     auto C3 = [&](int off, int nb) { return A3<T>{sm + off, nb + 2, nb + 2}; };
-    {
+    {   // the green residual of the top triple (a thread's copies all in flight at once)
         const int n = P.nk[0];
         A3<T> g = G3(P.og_r[0], n);
-        CTA_FOR3(i, j, k, 1, n) g(i, j, k) = rg_in(i, j, k);
+        CTA_FOR3(i, j, k, 1, n) cp_async_el(&g(i, j, k), &rg_in(i, j, k), true);
+        cp_async_commit();
     }
     gp.store(Gs, P.ng, tid);
+    cp_async_wait0();
     __syncthreads();
     for (int t = 0; t < ntri; t++) {
         const int n = P.nk[t], nb = (n - 1) / 2;
