@@ -184,8 +184,9 @@ mg_status mg_solve(mg_ctx *ctx, const double *f, double *u, double rtol, int max
 /* mg_solve from u = 0: the same V-cycles (Sections 2.3, 3.3), but u (device,
  * full grid, caller layout) is output only -- its contents on entry are never
  * read, and it need not be zeroed.  On return it holds the same iterate, bit
- * for bit, as mg_solve from a zeroed u.  The call zeroes u itself (a memset
- * on `stream`, inside the solve's graph on the fused mixed path, whose start
+ * for bit, as mg_solve from a zeroed u.  The call zeroes u's (n+2)^d points
+ * itself (a 2D memset on `stream` that leaves the padding of a larger pitch
+ * alone; inside the solve's graph on the fused mixed path, whose start
  * residual then is f itself and reads no u), which saves the caller's fill
  * and one read of u per solve.  u must not overlap f (MG_EINVAL).  Arguments
  * and returns as mg_solve; the graph cache keys a solve from zero apart from

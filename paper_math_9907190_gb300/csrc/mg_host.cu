@@ -1470,6 +1470,12 @@ static void launch_ctrl(mg_ctx *c, int np, int first, cudaGraphConditionalHandle
 static size_t grid_len(const mg_ctx *c) {
     return (size_t)c->d.pitch * (c->d.n + 2) * (c->d.dim == 3 ? (size_t)(c->d.n + 2) : 1);
 }
+// zeros on the (n+2)^d points of a caller grid; the padding of a pitch above
+// n + 2 is left alone
+static cudaError_t zero_grid(const mg_ctx *c, double *u, cudaStream_t s) {
+    const size_t rows = (size_t)(c->d.n + 2) * (c->d.dim == 3 ? (size_t)(c->d.n + 2) : 1);
+    return cudaMemset2DAsync(u, sizeof(double) * c->d.pitch, 0, sizeof(double) * (c->d.n + 2), rows, s);
+}
 
 // Prefix of a solve: control words, the norm of the right-hand side, the
 // residual of the warm start and the first control step (which sets the loop
@@ -1487,7 +1493,7 @@ static void solve_prefix(mg_ctx *c, const double *f, double *u, double rtol, int
     if (c->rr) {
         // a solve from zero: u zeroed here (an error shows in the caller's
         // launch check), and the start residual reads none of it
-        if (c->zstart) (void)cudaMemsetAsync(u, 0, sizeof(double) * grid_len(c), s);
+        if (c->zstart) (void)zero_grid(c, u, s);
         np = nfp = launch_res_rr(c, f, u, nullptr, s, true, c->zstart);
         fpart = c->part + (size_t)np * c->nprob;
     } else {
@@ -1739,7 +1745,7 @@ static mg_status solve_zero_impl(mg_ctx *c, const double *f, double *u, double r
     if (grids_overlap(f, u, grid_len(c))) return MG_EINVAL;
     if (!c->rr || c->nprob != 1) {
         // the per-stage paths read u from their first kernel on: zeros first
-        CK(cudaMemsetAsync(u, 0, sizeof(double) * grid_len(c), S(stream)));
+        CK(zero_grid(c, u, S(stream)));
         return solve_impl(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, stream, u_host);
     }
     c->zstart = true;

@@ -85,6 +85,24 @@ def test_padded_pitch_solve_leaves_padding_alone(dim, n, pad):
     _check_against_oracle(dim, n, f, u, rel)
 
 
+@pytest.mark.parametrize("dim,n,prec", [(2, 255, "mixed"), (3, 31, "mixed"), (2, 127, "fp64")])
+def test_padded_pitch_solve_from_zero_leaves_padding_alone(dim, n, prec):
+    """mg_solve_zero zeroes u itself: its (n+2)^d points only, not the
+    padding of a larger caller pitch (which holds NaN here), and with the same
+    bits as the unpadded solve."""
+    f = _f(dim, n)
+    pitch = n + 2 + 5
+    fv, fb = _padded(f, pitch, float("nan"))
+    uv, ub = _padded(np.full_like(f, 3.0), pitch, float("nan"))
+    with Context(dim, n, precision=prec, omega=default_omega(dim, "diag", 2), pitch=pitch) as c:
+        _, it, rel, _ = c.solve(fv, uv, rtol=1e-10, max_cycles=40, from_zero=True)
+    assert torch.isnan(ub[..., n + 2:]).all() and torch.isnan(fb[..., n + 2:]).all()
+    with Context(dim, n, precision=prec, omega=default_omega(dim, "diag", 2)) as c:
+        u2, it2, rel2, _ = c.solve(torch.from_numpy(f).to(DEV), rtol=1e-10, max_cycles=40)
+    assert it2 == it and rel2 == rel
+    assert np.array_equal(u2.cpu().numpy(), uv.cpu().numpy())
+
+
 @pytest.mark.parametrize("dim,n,prec", [(2, 1023, "mixed"), (2, 255, "fp64"), (3, 63, "mixed"), (3, 31, "fp64")])
 def test_launch_settings_give_the_same_bits(dim, n, prec, monkeypatch):
     """Programmatic dependent launch changes when a kernel is scheduled, never
