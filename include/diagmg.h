@@ -197,7 +197,8 @@ mg_status mg_solve_zero(mg_ctx *ctx, const double *f, double *u, double rtol, in
 /* mg_solve with HOST arrays, for callers whose data live in host memory:
  * f_host (the right-hand side), u0_host (the warm start, zero ring; NULL:
  * start from u = 0) and u_host (receives the result; may equal u0_host) are
- * full grids in the caller layout (pitch).  The call copies f and the warm
+ * full grids in the caller layout (pitch; only their (n+2)^d points are read
+ * or written, never the padding of a larger pitch).  The call copies f and the warm
  * start to device copies owned by the context, runs mg_solve there (mg_solve_zero
  * when u0_host is NULL) and copies
  * u back, and returns once u_host holds the result.  The copy in runs on

@@ -1470,6 +1470,14 @@ static void launch_ctrl(mg_ctx *c, int np, int first, cudaGraphConditionalHandle
 static size_t grid_len(const mg_ctx *c) {
     return (size_t)c->d.pitch * (c->d.n + 2) * (c->d.dim == 3 ? (size_t)(c->d.n + 2) : 1);
 }
+// a copy of the (n+2)^d points of a caller grid (both sides in the caller
+// pitch); the padding of a pitch above n + 2 is neither read nor written
+static cudaError_t copy_grid(const mg_ctx *c, double *dst, const double *src, cudaMemcpyKind kind, cudaStream_t s) {
+    const size_t rows = (size_t)(c->d.n + 2) * (c->d.dim == 3 ? (size_t)(c->d.n + 2) : 1);
+    const size_t pb = sizeof(double) * c->d.pitch;
+    if (c->d.pitch == c->d.n + 2) return cudaMemcpyAsync(dst, src, pb * rows, kind, s);  // contiguous
+    return cudaMemcpy2DAsync(dst, pb, src, pb, sizeof(double) * (c->d.n + 2), rows, kind, s);
+}
 // zeros on the (n+2)^d points of a caller grid; the padding of a pitch above
 // n + 2 is left alone
 static cudaError_t zero_grid(const mg_ctx *c, double *u, cudaStream_t s) {
@@ -1683,14 +1691,13 @@ static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double r
 static mg_status solve_impl(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
                             double *relres_out, double *history, void *stream, double *u_host) {
     cudaStream_t s = S(stream);
-    const size_t ubytes = sizeof(double) * grid_len(c);
     mg_status st;
     Ctrl host{};
     // a probe needs one event pair per launch, which a replayed graph cannot give
     if (!c->use_graph || c->probe_tag >= 0) {
         st = solve_host_loop(c, f, u, rtol, max_cycles, cycles_out, relres_out, history, s);
         if (u_host && (st == MG_OK || st == MG_ENOCONV || st == MG_EDIVERGED)) {
-            CK(cudaMemcpyAsync(u_host, u, ubytes, cudaMemcpyDeviceToHost, s));
+            CK(copy_grid(c, u_host, u, cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
         }
         return st;
@@ -1710,11 +1717,11 @@ static mg_status solve_impl(mg_ctx *c, const double *f, double *u, double rtol, 
     const bool early = u_host && c->rr;  // the copy of u overlaps the closing residual
     if (early) {
         CK(cudaStreamWaitEvent(c->cs_io, c->ev_ufinal, 0));
-        CK(cudaMemcpyAsync(u_host, u, ubytes, cudaMemcpyDeviceToHost, c->cs_io));
+        CK(copy_grid(c, u_host, u, cudaMemcpyDeviceToHost, c->cs_io));
         CK(cudaEventRecord(c->ev_io, c->cs_io));
     }
     CK(cudaMemcpyAsync(&host, c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-    if (u_host && !early) CK(cudaMemcpyAsync(u_host, u, ubytes, cudaMemcpyDeviceToHost, s));
+    if (u_host && !early) CK(copy_grid(c, u_host, u, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (early) CK(cudaEventSynchronize(c->ev_io));
     c->launches += hit->prefix_kernels + (long long)host.cycles * hit->body_kernels;
@@ -1785,8 +1792,8 @@ mg_status mg_solve_host(mg_ctx *c, const double *f_host, const double *u0_host, 
         }
     }
     cudaStream_t s = S(stream);
-    CK(cudaMemcpyAsync(c->io_f, f_host, bytes, cudaMemcpyHostToDevice, s));
-    if (u0_host) CK(cudaMemcpyAsync(c->io_u, u0_host, bytes, cudaMemcpyHostToDevice, s));
+    CK(copy_grid(c, c->io_f, f_host, cudaMemcpyHostToDevice, s));
+    if (u0_host) CK(copy_grid(c, c->io_u, u0_host, cudaMemcpyHostToDevice, s));
     // the solve copies u back itself (overlapped with its closing residual)
     return u0_host ? solve_impl(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out, nullptr, stream, u_host)
                    : solve_zero_impl(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out, nullptr, stream,

@@ -55,6 +55,24 @@ def test_host_solve_copy_back_waits_for_the_last_cycle(dim, n):
             assert np.array_equal(uh.numpy(), want[k]), k
 
 
+@pytest.mark.parametrize("dim,n,prec", [(2, 255, "mixed"), (3, 31, "mixed"), (2, 127, "fp64")])
+def test_host_solve_with_padded_pitch_leaves_padding_alone(dim, n, prec):
+    """Host arrays in a pitch above n + 2: only the (n+2)^d points move in
+    either direction; the padding (NaN here) is neither read nor written."""
+    pitch = n + 5 + 2
+    f0 = I.uniform_f(dim, n, 77)
+    fh = torch.full(f0.shape[:-1] + (pitch,), float("nan"), dtype=torch.float64)
+    fh[..., : n + 2] = torch.from_numpy(f0)
+    uh = torch.full_like(fh, float("nan"))
+    with Context(dim, n, precision=prec, pitch=pitch) as c:
+        _, ch, rh = c.solve_host(fh, uh, rtol=1e-10)
+    assert torch.isnan(uh[..., n + 2:]).all() and torch.isnan(fh[..., n + 2:]).all()
+    with Context(dim, n, precision=prec) as c:
+        ud, cd, rd, _ = c.solve(torch.from_numpy(f0).to(DEV), rtol=1e-10)
+    assert ch == cd and rh == rd
+    assert np.array_equal(uh[..., : n + 2].numpy(), ud.cpu().numpy())
+
+
 def test_host_solve_refuses_bad_arguments():
     with Context(2, 63) as c:
         f = torch.zeros((65, 65), dtype=torch.float64)
