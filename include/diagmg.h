@@ -213,6 +213,22 @@ mg_status mg_solve_zero(mg_ctx *ctx, const double *f, double *u, double rtol, in
 mg_status mg_solve_host(mg_ctx *ctx, const double *f_host, const double *u0_host, double *u_host, double rtol,
                         int max_cycles, int *cycles_out, double *relres_out, void *stream);
 
+/* mg_solve_host for a sequence of `count` problems of the context's size, each
+ * solved from u = 0 (as mg_solve_zero): f_host[k] (host, full grid, caller
+ * layout) in, u_host[k] out (must not overlap f_host[k]).  The call pipelines
+ * the problems over two pairs of device copies: the copy in of problem k + 1
+ * and the copy back of problem k run on a stream of the context while problem
+ * k is solved on `stream`, so the host link and the solve overlap; every
+ * result is the one mg_solve_host gives for that problem alone, bit for bit.
+ * cycles_out, relres_out: host arrays of count entries (nullable).  Returns
+ * MG_EDIVERGED if any problem diverged, else MG_ENOCONV if any did not
+ * converge, else MG_OK (the per-problem outcome is in relres_out); returns
+ * once every u_host[k] holds its result.  The first call allocates a second
+ * pair of device copies (MG_ENOMEM) and two page-locked control words; with
+ * DIAGMG_SOLVE_GRAPH=0 the problems run one after the other. */
+mg_status mg_solve_host_many(mg_ctx *ctx, int count, const double *const *f_host, double *const *u_host,
+                             double rtol, int max_cycles, int *cycles_out, double *relres_out, void *stream);
+
 /* Replace the context's over-relaxation weights (same meaning as
  * mg_desc.omega, host, 4 entries). */
 mg_status mg_set_omega(mg_ctx *ctx, const double *omega);

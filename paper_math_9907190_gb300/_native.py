@@ -43,6 +43,7 @@ SIGNATURES = {
     "mg_solve": (_i, [_vp, _vp, _vp, _d, _i, _ip, _dp, _dp, _vp]),
     "mg_solve_zero": (_i, [_vp, _vp, _vp, _d, _i, _ip, _dp, _dp, _vp]),
     "mg_solve_host": (_i, [_vp, _vp, _vp, _vp, _d, _i, _ip, _dp, _vp]),
+    "mg_solve_host_many": (_i, [_vp, _i, _vp, _vp, _d, _i, _ip, _dp, _vp]),
     "mg_fp64_rate": (_i, [_vp, _dp, _vp]),
     "mg_launch_count": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
     "mg_probe_set": (_i, [_vp, _i]),

@@ -153,6 +153,30 @@ class Context:
             N.check(st, "mg_solve_host")
         return u, cyc.value, rel.value
 
+    def solve_host_many(self, fs, us=None, *, rtol: float = 1e-10, max_cycles: int = 100,
+                        raise_on_fail: bool = True):
+        """mg_solve_host_many: each f in fs (CPU float64 full grids, pinned for
+        full copy bandwidth) solved from u = 0 into the matching u of us
+        (default new tensors), copies and solves pipelined.  Returns (us,
+        cycles, relres) with per-problem lists."""
+        shape = (self.n + 2,) * (self.dim - 1) + (self.pitch,)
+        us = [torch.empty(shape, dtype=torch.float64) for _ in fs] if us is None else us
+        if len(us) != len(fs):
+            raise ValueError("fs and us differ in length")
+        for name, ts in (("f", fs), ("u", us)):
+            for t in ts:
+                if t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != shape:
+                    raise ValueError(f"{name}: expected contiguous CPU float64 tensors of shape {shape}")
+        k = len(fs)
+        fp = (ctypes.c_void_p * max(1, k))(*[t.data_ptr() for t in fs])
+        up = (ctypes.c_void_p * max(1, k))(*[t.data_ptr() for t in us])
+        cyc = (ctypes.c_int * max(1, k))()
+        rel = (ctypes.c_double * max(1, k))()
+        st = N.lib().mg_solve_host_many(self._h, k, fp, up, rtol, max_cycles, cyc, rel, self._stream())
+        if raise_on_fail:
+            N.check(st, "mg_solve_host_many")
+        return us, list(cyc)[:k], list(rel)[:k]
+
     def fp64_rate(self) -> float:
         """mg_fp64_rate: measured FP64 pipe operations per second of this device."""
         v = ctypes.c_double()

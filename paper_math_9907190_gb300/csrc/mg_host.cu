@@ -148,6 +148,11 @@ struct mg_ctx {
     // back while that residual runs, on its own stream cs_io
     cudaEvent_t ev_ufinal = nullptr, ev_io = nullptr;
     cudaStream_t cs_io = nullptr;
+    // mg_solve_host_many: the second pair of device copies and the events of
+    // its two-buffer pipeline; Ctrl of the last two solves in page-locked memory
+    double *io_f2 = nullptr, *io_u2 = nullptr;
+    cudaEvent_t ev_in[2] = {}, ev_sol[2] = {}, ev_out[2] = {}, ev_ctl[2] = {};
+    Ctrl *hctl = nullptr;
     // instantiated solve graphs, keyed by their arguments and the context's
     // settings; a few are kept (least recently used replaced) so that a caller
     // alternating between buffers does not rebuild a graph per solve
@@ -1165,6 +1170,12 @@ mg_status mg_destroy(mg_ctx *c) {
     if (c->cs_io) cudaStreamDestroy(c->cs_io);
     if (c->ev_ufinal) cudaEventDestroy(c->ev_ufinal);
     if (c->ev_io) cudaEventDestroy(c->ev_io);
+    for (int b = 0; b < 2; b++)
+        for (cudaEvent_t e : {c->ev_in[b], c->ev_sol[b], c->ev_out[b], c->ev_ctl[b]})
+            if (e) cudaEventDestroy(e);
+    if (c->hctl) cudaFreeHost(c->hctl);
+    cudaFree(c->io_f2);
+    cudaFree(c->io_u2);
     cudaFree(c->pool);
     cudaFree(c->part);
     cudaFree(c->ctl);
@@ -1688,6 +1699,25 @@ static mg_status solve_host_loop(mg_ctx *c, const double *f, double *u, double r
 // returns: on the fused mixed path's graph the copy starts once the last
 // cycle has written u (event ev_ufinal) and runs on cs_io beside the direct
 // residual that closes the solve, else after the solve on the stream
+// the solve graph of these arguments: from the cache, else recorded into its
+// least recently used slot
+static mg_status solve_graph(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles,
+                             mg_ctx::SolveGraph **out) {
+    mg_ctx::SolveGraph *hit = nullptr, *lru = &c->gcache[0];
+    for (auto &e : c->gcache) {
+        if (solve_graph_matches(c, e, f, u, rtol, max_cycles)) { hit = &e; break; }
+        if (e.used < lru->used) lru = &e;
+    }
+    if (!hit) {
+        const mg_status st = build_solve_graph(c, *lru, f, u, rtol, max_cycles);
+        if (st != MG_OK) return st;
+        hit = lru;
+    }
+    hit->used = ++c->gtick;
+    *out = hit;
+    return MG_OK;
+}
+
 static mg_status solve_impl(mg_ctx *c, const double *f, double *u, double rtol, int max_cycles, int *cycles_out,
                             double *relres_out, double *history, void *stream, double *u_host) {
     cudaStream_t s = S(stream);
@@ -1702,17 +1732,9 @@ static mg_status solve_impl(mg_ctx *c, const double *f, double *u, double rtol, 
         }
         return st;
     }
-    mg_ctx::SolveGraph *hit = nullptr, *lru = &c->gcache[0];
-    for (auto &e : c->gcache) {
-        if (solve_graph_matches(c, e, f, u, rtol, max_cycles)) { hit = &e; break; }
-        if (e.used < lru->used) lru = &e;
-    }
-    if (!hit) {
-        st = build_solve_graph(c, *lru, f, u, rtol, max_cycles);
-        if (st != MG_OK) return st;
-        hit = lru;
-    }
-    hit->used = ++c->gtick;
+    mg_ctx::SolveGraph *hit = nullptr;
+    st = solve_graph(c, f, u, rtol, max_cycles, &hit);
+    if (st != MG_OK) return st;
     CK(cudaGraphLaunch(hit->exec, s));
     const bool early = u_host && c->rr;  // the copy of u overlaps the closing residual
     if (early) {
@@ -1798,6 +1820,133 @@ mg_status mg_solve_host(mg_ctx *c, const double *f_host, const double *u0_host, 
     return u0_host ? solve_impl(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out, nullptr, stream, u_host)
                    : solve_zero_impl(c, c->io_f, c->io_u, rtol, max_cycles, cycles_out, relres_out, nullptr, stream,
                                      u_host);
+}
+
+static mg_status status_of(const Ctrl &h) {
+    if (h.status == -5) return MG_EDIVERGED;
+    if (h.status == -4 || !h.done) return MG_ENOCONV;
+    return MG_OK;
+}
+
+mg_status mg_solve_host_many(mg_ctx *c, int count, const double *const *f_host, double *const *u_host, double rtol,
+                             int max_cycles, int *cycles_out, double *relres_out, void *stream) {
+    if (!c || c->nprob != 1 || count < 0 || (count > 0 && (!f_host || !u_host)) || !(rtol >= 0.0) || max_cycles < 0 ||
+        max_cycles > c->hist_cap)
+        return MG_EINVAL;
+    const size_t len = grid_len(c), bytes = sizeof(double) * len;
+    for (int k = 0; k < count; k++)
+        if (bad_grid(f_host[k]) || bad_grid(u_host[k]) || grids_overlap(f_host[k], u_host[k], len)) return MG_EINVAL;
+    if (count == 0) return MG_OK;
+    // host-driven loop (no graph): one problem after the other
+    if (!c->use_graph || c->probe_tag >= 0) {
+        mg_status worst = MG_OK;
+        for (int k = 0; k < count; k++) {
+            const mg_status st = mg_solve_host(c, f_host[k], nullptr, u_host[k], rtol, max_cycles,
+                                               cycles_out ? cycles_out + k : nullptr,
+                                               relres_out ? relres_out + k : nullptr, stream);
+            if (st != MG_OK && st != MG_ENOCONV && st != MG_EDIVERGED) return st;
+            if (st == MG_EDIVERGED || (st == MG_ENOCONV && worst == MG_OK)) worst = st;
+        }
+        return worst;
+    }
+    // the first call: a second pair of device copies, the copy stream, the
+    // pipeline's events and two page-locked control words
+    if (!c->io_f) {
+        if (cudaMalloc(&c->io_f, bytes) != cudaSuccess || cudaMalloc(&c->io_u, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->io_f);
+            cudaFree(c->io_u);
+            c->io_f = c->io_u = nullptr;
+            return MG_ENOMEM;
+        }
+    }
+    if (!c->io_f2) {
+        if (cudaMalloc(&c->io_f2, bytes) != cudaSuccess || cudaMalloc(&c->io_u2, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->io_f2);
+            cudaFree(c->io_u2);
+            c->io_f2 = c->io_u2 = nullptr;
+            return MG_ENOMEM;
+        }
+    }
+    if (!c->cs_io) {
+        if (cudaStreamCreateWithFlags(&c->cs_io, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_io, cudaEventDisableTiming) != cudaSuccess) {
+            if (c->cs_io) cudaStreamDestroy(c->cs_io);
+            c->cs_io = nullptr;
+            return cuda_fail(cudaGetLastError(), "mg_solve_host_many stream");
+        }
+    }
+    if (!c->hctl) {
+        for (int b = 0; b < 2; b++)
+            for (cudaEvent_t *e : {&c->ev_in[b], &c->ev_sol[b], &c->ev_out[b], &c->ev_ctl[b]})
+                if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        if (cudaHostAlloc(reinterpret_cast<void **>(&c->hctl), 2 * sizeof(Ctrl), cudaHostAllocDefault) != cudaSuccess) {
+            c->hctl = nullptr;
+            return cuda_fail(cudaGetLastError(), "mg_solve_host_many control words");
+        }
+    }
+    cudaStream_t s = S(stream), io = c->cs_io;
+    double *F[2] = {c->io_f, c->io_f2}, *U[2] = {c->io_u, c->io_u2};
+    mg_ctx::SolveGraph *hit[2] = {nullptr, nullptr};
+    mg_status worst = MG_OK;
+    // the results of solve k (control word slot k & 1) once it has run
+    auto collect = [&](int k) -> mg_status {
+        const int b = k & 1;
+        CK(cudaEventSynchronize(c->ev_ctl[b]));
+        const Ctrl &h = c->hctl[b];
+        c->launches += hit[b]->prefix_kernels + (long long)h.cycles * hit[b]->body_kernels;
+        if (cycles_out) cycles_out[k] = h.cycles;
+        if (relres_out) relres_out[k] = h.relres;
+        const mg_status st = status_of(h);
+        if (st == MG_EDIVERGED || (st == MG_ENOCONV && worst == MG_OK)) worst = st;
+        return MG_OK;
+    };
+    CK(cudaEventRecord(c->ev_io, s));  // the copies start after the caller's earlier work
+    CK(cudaStreamWaitEvent(io, c->ev_io, 0));
+    CK(copy_grid(c, F[0], f_host[0], cudaMemcpyHostToDevice, io));
+    CK(cudaEventRecord(c->ev_in[0], io));
+    for (int k = 0; k < count; k++) {
+        const int b = k & 1;
+        if (k + 1 < count) {  // the next input, into the buffer solve k - 1 used
+            if (k >= 1) CK(cudaStreamWaitEvent(io, c->ev_sol[b ^ 1], 0));
+            CK(copy_grid(c, F[b ^ 1], f_host[k + 1], cudaMemcpyHostToDevice, io));
+            CK(cudaEventRecord(c->ev_in[b ^ 1], io));
+        }
+        CK(cudaStreamWaitEvent(s, c->ev_in[b], 0));
+        if (k >= 2) CK(cudaStreamWaitEvent(s, c->ev_out[b], 0));  // solve k - 2's u has left this buffer
+        if (k >= 2) {  // slot b of the control words holds solve k - 2's, read before it is reused
+            const mg_status st = collect(k - 2);
+            if (st != MG_OK) return st;
+        }
+        mg_status st;
+        if (c->rr) {  // a solve from zero: u zeroed inside the graph
+            c->zstart = true;
+            st = solve_graph(c, F[b], U[b], rtol, max_cycles, &hit[b]);
+            c->zstart = false;
+        } else {
+            CK(zero_grid(c, U[b], s));
+            st = solve_graph(c, F[b], U[b], rtol, max_cycles, &hit[b]);
+        }
+        if (st != MG_OK) return st;
+        CK(cudaGraphLaunch(hit[b]->exec, s));
+        CK(cudaMemcpyAsync(&c->hctl[b], c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        CK(cudaEventRecord(c->ev_ctl[b], s));
+        CK(cudaEventRecord(c->ev_sol[b], s));
+        // u back once the solve and its control word have left the device: the
+        // control word's small copy shares the copy engine, and queued behind
+        // this 134 MB one it would hold the next solve back
+        CK(cudaStreamWaitEvent(io, c->ev_ctl[b], 0));
+        CK(copy_grid(c, u_host[k], U[b], cudaMemcpyDeviceToHost, io));
+        CK(cudaEventRecord(c->ev_out[b], io));
+    }
+    for (int k = std::max(0, count - 2); k < count; k++) {
+        const mg_status st = collect(k);
+        if (st != MG_OK) return st;
+    }
+    CK(cudaStreamSynchronize(io));
+    CK(cudaStreamSynchronize(s));
+    return worst;
 }
 
 // Section 2.4 / 3.4: a fourth-order solution is reached fastest by first

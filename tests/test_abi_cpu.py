@@ -67,6 +67,7 @@ def test_null_arguments_rejected(lib):
     assert lib.mg_solve_zero(None, None, None, 1e-10, 10, None, None, None, None) == N.MG_EINVAL
     assert lib.mg_level_get(None, 0, 0, None, None) == N.MG_EINVAL
     assert lib.mg_solve_host(None, None, None, None, 1e-10, 10, None, None, None) == N.MG_EINVAL
+    assert lib.mg_solve_host_many(None, 2, None, None, 1e-10, 10, None, None, None) == N.MG_EINVAL
     assert lib.mg_fp64_rate(None, None, None) == N.MG_EINVAL
     assert lib.mg_batch_status(None, None) == N.MG_EINVAL
     assert lib.mg_set_gamma(None, 2) == N.MG_EINVAL
@@ -164,7 +165,7 @@ def test_python_api_surface():
         assert hasattr(P, name), name
     for m in ("solve", "vcycle", "residual", "solve_two_stage", "set_omega", "set_sweeps", "rho", "tune",
               "tune_info", "restrict", "coarse_solve", "prolong", "level_get", "level_set", "new_grid", "close",
-              "solve_host", "fp64_rate", "set_gamma"):
+              "solve_host", "solve_host_many", "fp64_rate", "set_gamma"):
         assert callable(getattr(P.Context, m)), m
     for m in ("solve", "tune", "close", "statuses"):
         assert callable(getattr(P.Batch, m)), m

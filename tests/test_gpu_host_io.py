@@ -73,6 +73,40 @@ def test_host_solve_with_padded_pitch_leaves_padding_alone(dim, n, prec):
     assert np.array_equal(uh[..., : n + 2].numpy(), ud.cpu().numpy())
 
 
+@pytest.mark.parametrize("dim,n,prec,count", [(2, 255, "mixed", 5), (2, 1023, "mixed", 3), (3, 63, "mixed", 4),
+                                               (2, 127, "fp64", 3), (2, 255, "mixed", 1)])
+def test_host_solve_many_equals_one_call_per_problem(dim, n, prec, count):
+    """mg_solve_host_many pipelines the copies and solves of several
+    problems over two device buffers; each result must be the bits of
+    mg_solve_host on that problem alone (distinct right-hand sides, so a
+    result taken from the wrong buffer or too early would show)."""
+    fs = [torch.from_numpy(I.uniform_f(dim, n, 90 + k)).pin_memory() for k in range(count)]
+    with Context(dim, n, precision=prec) as c:
+        want = []
+        for f in fs:
+            uh = torch.empty_like(f).pin_memory()
+            _, ch, rh = c.solve_host(f, uh, rtol=1e-10)
+            want.append((uh, ch, rh))
+        us = [torch.full_like(f, float("nan")).pin_memory() for f in fs]
+        for _ in range(2):  # twice: the second call reuses the graphs and buffers
+            for u in us:
+                u.fill_(float("nan"))
+            _, cyc, rel = c.solve_host_many(fs, us, rtol=1e-10)
+            for k in range(count):
+                assert cyc[k] == want[k][1] and rel[k] == want[k][2], k
+                assert np.array_equal(us[k].numpy(), want[k][0].numpy()), k
+
+
+def test_host_solve_many_edge_cases():
+    with Context(2, 63) as c:
+        assert c.solve_host_many([], []) == ([], [], [])
+        f = torch.zeros((65, 65), dtype=torch.float64)
+        L = N.lib()
+        fp = (N.ctypes.c_void_p * 1)(f.data_ptr())
+        assert L.mg_solve_host_many(c._h, 1, fp, fp, 1e-10, 10, None, None, c._stream()) == N.MG_EINVAL  # u over f
+        assert L.mg_solve_host_many(c._h, -1, fp, fp, 1e-10, 10, None, None, c._stream()) == N.MG_EINVAL
+
+
 def test_host_solve_refuses_bad_arguments():
     with Context(2, 63) as c:
         f = torch.zeros((65, 65), dtype=torch.float64)
