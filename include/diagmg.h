@@ -215,7 +215,9 @@ mg_status mg_solve_host(mg_ctx *ctx, const double *f_host, const double *u0_host
 
 /* mg_solve_host for a sequence of `count` problems of the context's size, each
  * solved from u = 0 (as mg_solve_zero): f_host[k] (host, full grid, caller
- * layout) in, u_host[k] out (must not overlap f_host[k]).  The call pipelines
+ * layout) in, u_host[k] out; no u_host may overlap any f_host (MG_EINVAL),
+ * and outputs that share a buffer are written in the order of k.  The call
+ * pipelines
  * the problems over two pairs of device copies: the copy in of problem k + 1
  * and the copy back of problem k run on a stream of the context while problem
  * k is solved on `stream`, so the host link and the solve overlap; every

@@ -1835,7 +1835,12 @@ mg_status mg_solve_host_many(mg_ctx *c, int count, const double *const *f_host, 
         return MG_EINVAL;
     const size_t len = grid_len(c), bytes = sizeof(double) * len;
     for (int k = 0; k < count; k++)
-        if (bad_grid(f_host[k]) || bad_grid(u_host[k]) || grids_overlap(f_host[k], u_host[k], len)) return MG_EINVAL;
+        if (bad_grid(f_host[k]) || bad_grid(u_host[k])) return MG_EINVAL;
+    // no output may overlap any input (a result copied back early would
+    // change a later problem's right-hand side); outputs may share a buffer
+    for (int k = 0; k < count; k++)
+        for (int j = 0; j < count; j++)
+            if (grids_overlap(f_host[j], u_host[k], len)) return MG_EINVAL;
     if (count == 0) return MG_OK;
     // host-driven loop (no graph): one problem after the other
     if (!c->use_graph || c->probe_tag >= 0) {

@@ -97,6 +97,30 @@ def test_host_solve_many_equals_one_call_per_problem(dim, n, prec, count):
                 assert np.array_equal(us[k].numpy(), want[k][0].numpy()), k
 
 
+def test_host_solve_many_host_driven_loop():
+    """With DIAGMG_SOLVE_GRAPH=0 (read when the context is created) the
+    problems run one after the other through mg_solve_host: the same bits."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import numpy as np, torch\n"
+        "from paper_math_9907190_gb300 import Context\n"
+        "from paper_math_9907190_gb300 import inputs as I\n"
+        "fs = [torch.from_numpy(I.uniform_f(2, 255, 95 + k)).pin_memory() for k in range(3)]\n"
+        "with Context(2, 255, precision='mixed') as c:\n"
+        "    want = [c.solve_host(f, torch.empty_like(f), rtol=1e-10) for f in fs]\n"
+        "    us, cyc, rel = c.solve_host_many(fs, rtol=1e-10)\n"
+        "    for k in range(3):\n"
+        "        assert cyc[k] == want[k][1] and rel[k] == want[k][2], k\n"
+        "        assert np.array_equal(us[k].numpy(), want[k][0].numpy()), k\n"
+        "print('ok')\n")
+    env = dict(os.environ, DIAGMG_SOLVE_GRAPH="0", PYTHONPATH=root)
+    p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0 and p.stdout.strip().endswith("ok"), p.stdout + p.stderr
+
+
 def test_host_solve_many_edge_cases():
     with Context(2, 63) as c:
         assert c.solve_host_many([], []) == ([], [], [])
@@ -105,6 +129,11 @@ def test_host_solve_many_edge_cases():
         fp = (N.ctypes.c_void_p * 1)(f.data_ptr())
         assert L.mg_solve_host_many(c._h, 1, fp, fp, 1e-10, 10, None, None, c._stream()) == N.MG_EINVAL  # u over f
         assert L.mg_solve_host_many(c._h, -1, fp, fp, 1e-10, 10, None, None, c._stream()) == N.MG_EINVAL
+        # problem 0's output over problem 1's input
+        g = torch.zeros_like(f)
+        fp2 = (N.ctypes.c_void_p * 2)(f.data_ptr(), g.data_ptr())
+        up2 = (N.ctypes.c_void_p * 2)(g.data_ptr(), torch.zeros_like(f).data_ptr())
+        assert L.mg_solve_host_many(c._h, 2, fp2, up2, 1e-10, 10, None, None, c._stream()) == N.MG_EINVAL
 
 
 def test_host_solve_refuses_bad_arguments():
