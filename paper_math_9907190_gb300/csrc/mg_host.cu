@@ -551,6 +551,10 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
         if (zm_use<T>(nb)) {
             LAUNCH_B(TAG_UP, (k_b2m_ooo_zm_3d<T>), grid_zm(nb + 1, zm_planes(nb)), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, zm_planes(nb), done);
             LAUNCH_B(TAG_UP, (k_b2m_eee_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, zm_planes(nb), done);
+        } else if (nb + 1 <= 32) {  // small levels: both half-sweeps in one launch, a tile of cells per block
+            const dim3 g((nb + BM_X) / BM_X, (nb + BM_Y) / BM_Y, (nb + BM_Z) / BM_Z);
+            LAUNCH_B(TAG_UP, (k_b2m_3d<T>), g, B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<const T>(a.r[0], a),
+                     a3<T>(a.v[1], a), a3<T>(a.v[0], a), nb, cc, done);
         } else {
             LAUNCH_B(TAG_UP, (k_b2m_ooo_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, a3<const T>(b.v[0], b), a3<const T>(a.r[1], a), a3<T>(a.v[1], a), nb, cc, done);
             LAUNCH_B(TAG_UP, (k_b2m_eee_3d<T>), grid3(nb, nb, nb), B2, a3<const T>(a.v[1], a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, cc, done);
@@ -560,6 +564,10 @@ void launch_prolong(mg_ctx *c, int l, const double *om, double *u, const int *do
         if (zm_use<T>(nb)) {
             LAUNCH_B(TAG_UP, (k_m2r_faces_zm_3d<T>), grid_zm(nb + 1, zm_planes(nb)), B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, zm_planes(nb), done);
             LAUNCH_B(TAG_UP, (k_m2r_corners_zm_3d<T>), grid_zm(nb, zm_planes(nb)), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, zm_planes(nb), vctl, done);
+        } else if (nb + 1 <= 32 && !vctl) {  // small levels: both half-sweeps in one launch
+            const dim3 g((nb + BM_X) / BM_X, (nb + BM_Y) / BM_Y, (nb + BM_Z) / BM_Z);
+            LAUNCH_B(TAG_UP, (k_m2r_3d<T>), g, B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb,
+                     c1, c2, done);
         } else {
             LAUNCH_B(TAG_UP, (k_m2r_faces_3d<T>), grid3(nb + 1, nb + 1, nb + 1), B2, mag3v<const T>(b.v, b), red3v<const T>(a.r, a), red3v<T>(a.v, a), nb, c1, done);
             LAUNCH_B(TAG_UP, (k_m2r_corners_3d<T>), grid3(nb, nb, nb), B2, red3v<const T>(a.v, a), a3<const T>(a.r[0], a), a3<T>(a.v[0], a), nb, c2, vctl, done);

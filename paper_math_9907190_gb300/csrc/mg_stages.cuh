@@ -428,6 +428,50 @@ __global__ void k_b2m_eee_3d(A3<const T> vooo, A3<const T> reee, A3<T> veee, int
     veee(a, b, c) = (ctr8(vooo, a, b, c) - cc * reee(a, b, c)) * T(0.125);
 }
 
+// Eq. Emprolm then Eq. Emprolb in one launch (the small triples): a block of
+// 8 x 8 x 4 cells forms the magenta centres of its cells and of the cell
+// before them in each direction (the corners' 8 centres), stores its own, and
+// then refines its own blue corners from those values in shared memory; the
+// terms of both half-sweeps in the order of k_b2m_ooo_3d / k_b2m_eee_3d.
+constexpr int BM_X = 8, BM_Y = 8, BM_Z = 4;
+template <typename T>
+__global__ void __launch_bounds__(256) k_b2m_3d(A3<const T> blue, A3<const T> rooo, A3<const T> reee, A3<T> vooo,
+                                                A3<T> veee, int nb, T cc, const int *done, Bt B) {
+    __shared__ T so[BM_Z + 1][BM_Y + 1][BM_X + 1];
+    const int prob_ = bt_prob(B), bz = bt_z(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    blue = bt_at(blue, prob_, B);
+    rooo = bt_at(rooo, prob_, B);
+    reee = bt_at(reee, prob_, B);
+    vooo = bt_at(vooo, prob_, B);
+    veee = bt_at(veee, prob_, B);
+    const int x0 = blockIdx.x * BM_X, y0 = blockIdx.y * BM_Y, z0 = bz * BM_Z;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    // centres of cells [x0-1, x0+8) x [y0-1, y0+8) x [z0-1, z0+4)
+    for (int q = tid; q < (BM_X + 1) * (BM_Y + 1) * (BM_Z + 1); q += 256) {
+        const int lx = q % (BM_X + 1), ly = (q / (BM_X + 1)) % (BM_Y + 1), lz = q / ((BM_X + 1) * (BM_Y + 1));
+        const int a = x0 - 1 + lx, b = y0 - 1 + ly, c = z0 - 1 + lz;
+        T v = T(0);
+        if (a >= 0 && a <= nb && b >= 0 && b <= nb && c >= 0 && c <= nb) {
+            const T s = ((blue(a, b, c) + blue(a + 1, b, c)) + (blue(a, b + 1, c) + blue(a + 1, b + 1, c))) +
+                        ((blue(a, b, c + 1) + blue(a + 1, b, c + 1)) + (blue(a, b + 1, c + 1) + blue(a + 1, b + 1, c + 1)));
+            v = (s - cc * rooo(a, b, c)) * T(0.125);
+            if (lx >= 1 && ly >= 1 && lz >= 1) vooo(a, b, c) = v;
+        }
+        so[lz][ly][lx] = v;
+    }
+    __syncthreads();
+    // corners of the own cells: the 8 centres (a-1..a) x (b-1..b) x (c-1..c)
+    const int lx = tid & 7, ly = (tid >> 3) & 7, lz = tid >> 6;  // 8 x 8 x 4
+    const int a = x0 + lx, b = y0 + ly, c = z0 + lz;
+    if (a >= 1 && a <= nb && b >= 1 && b <= nb && c >= 1 && c <= nb) {
+        const int i = lx + 1, j = ly + 1, k = lz + 1;  // smem index of cell (a, b, c)
+        const T s8 = ((so[k - 1][j - 1][i - 1] + so[k - 1][j - 1][i]) + (so[k - 1][j][i - 1] + so[k - 1][j][i])) +
+                     ((so[k][j - 1][i - 1] + so[k][j - 1][i]) + (so[k][j][i - 1] + so[k][j][i]));
+        veee(a, b, c) = (s8 - cc * reee(a, b, c)) * T(0.125);
+    }
+}
+
 // Eq. Erprolr and its cyclic permutations: red face centres from the two
 // magenta centres along the face normal (weight 2) and the four in-plane
 // magenta corners; c1 = 2 p_r1 h^2.  Thread per cell in [0,nb]^3.
@@ -454,6 +498,62 @@ __global__ void k_m2r_faces_3d(Mag3<const T> vm, Red3<const T> rr, Red3<T> vr, i
         T ctr = vm.ooo(a - 1, b, c) + vm.ooo(a, b, c);
         T cor = (vm.eee(a, b, c) + vm.eee(a, b + 1, c)) + (vm.eee(a, b, c + 1) + vm.eee(a, b + 1, c + 1));
         vr.eoo(a, b, c) = (T(2) * ctr + cor - c1 * rr.eoo(a, b, c)) * T(0.125);
+    }
+}
+
+// Eq. Erprolr then Eq. Erprolm in one launch (small levels, no bound on |v|
+// wanted): a block of 8 x 8 x 4 cells forms the three face centres of its
+// cells and of the cell before them in each direction, stores its own, then
+// its own corners from those values in shared memory; the terms of both
+// half-sweeps in the order of k_m2r_faces_3d / k_m2r_corners_3d (fcc12).
+template <typename T>
+__global__ void __launch_bounds__(256) k_m2r_3d(Mag3<const T> vm, Red3<const T> rr, Red3<T> vr, int nb, T c1, T c2,
+                                                const int *done, Bt B) {
+    __shared__ T sf[3][BM_Z + 1][BM_Y + 1][BM_X + 1];  // OOE, OEO, EOO
+    const int prob_ = bt_prob(B), bz = bt_z(B);
+    if (stop(bt_done(done, prob_, B))) return;
+    vm = bt_at(vm, prob_, B);
+    rr = bt_at(rr, prob_, B);
+    vr = bt_at(vr, prob_, B);
+    const int x0 = blockIdx.x * BM_X, y0 = blockIdx.y * BM_Y, z0 = bz * BM_Z;
+    const int tid = threadIdx.x + 32 * threadIdx.y;
+    for (int q = tid; q < (BM_X + 1) * (BM_Y + 1) * (BM_Z + 1); q += 256) {
+        const int lx = q % (BM_X + 1), ly = (q / (BM_X + 1)) % (BM_Y + 1), lz = q / ((BM_X + 1) * (BM_Y + 1));
+        const int a = x0 - 1 + lx, b = y0 - 1 + ly, c = z0 - 1 + lz;
+        const bool in = a >= 0 && a <= nb && b >= 0 && b <= nb && c >= 0 && c <= nb;
+        const bool own = in && lx >= 1 && ly >= 1 && lz >= 1;
+        T fz = T(0), fy = T(0), fx = T(0);
+        if (in && c >= 1) {  // (2a+1, 2b+1, 2c): normal z
+            T ctr = vm.ooo(a, b, c - 1) + vm.ooo(a, b, c);
+            T cor = (vm.eee(a, b, c) + vm.eee(a + 1, b, c)) + (vm.eee(a, b + 1, c) + vm.eee(a + 1, b + 1, c));
+            fz = (T(2) * ctr + cor - c1 * rr.ooe(a, b, c)) * T(0.125);
+            if (own) vr.ooe(a, b, c) = fz;
+        }
+        if (in && b >= 1) {  // (2a+1, 2b, 2c+1): normal y
+            T ctr = vm.ooo(a, b - 1, c) + vm.ooo(a, b, c);
+            T cor = (vm.eee(a, b, c) + vm.eee(a + 1, b, c)) + (vm.eee(a, b, c + 1) + vm.eee(a + 1, b, c + 1));
+            fy = (T(2) * ctr + cor - c1 * rr.oeo(a, b, c)) * T(0.125);
+            if (own) vr.oeo(a, b, c) = fy;
+        }
+        if (in && a >= 1) {  // (2a, 2b+1, 2c+1): normal x
+            T ctr = vm.ooo(a - 1, b, c) + vm.ooo(a, b, c);
+            T cor = (vm.eee(a, b, c) + vm.eee(a, b + 1, c)) + (vm.eee(a, b, c + 1) + vm.eee(a, b + 1, c + 1));
+            fx = (T(2) * ctr + cor - c1 * rr.eoo(a, b, c)) * T(0.125);
+            if (own) vr.eoo(a, b, c) = fx;
+        }
+        sf[0][lz][ly][lx] = fz;
+        sf[1][lz][ly][lx] = fy;
+        sf[2][lz][ly][lx] = fx;
+    }
+    __syncthreads();
+    const int lx = tid & 7, ly = (tid >> 3) & 7, lz = tid >> 6;  // 8 x 8 x 4
+    const int a = x0 + lx, b = y0 + ly, c = z0 + lz;
+    if (a >= 1 && a <= nb && b >= 1 && b <= nb && c >= 1 && c <= nb) {
+        const int i = lx + 1, j = ly + 1, k = lz + 1;  // smem index of cell (a, b, c)
+        const T s1 = (sf[0][k][j - 1][i - 1] + sf[0][k][j - 1][i]) + (sf[0][k][j][i - 1] + sf[0][k][j][i]);
+        const T s2 = (sf[1][k - 1][j][i - 1] + sf[1][k - 1][j][i]) + (sf[1][k][j][i - 1] + sf[1][k][j][i]);
+        const T s3 = (sf[2][k - 1][j - 1][i] + sf[2][k - 1][j][i]) + (sf[2][k][j - 1][i] + sf[2][k][j][i]);
+        vr.eee(a, b, c) = (s1 + s2 + s3 - c2 * rr.eee(a, b, c)) * T(1.0 / 12.0);
     }
 }
 
