@@ -870,7 +870,10 @@ constexpr int FF_WARPS = 4;
 // MODE: UP_RR the mixed finest pair (u += v and the carried residual, rga/rgb
 // double-buffered by par); UP_ADD u += v; UP_STORE v stored in vg (a coarser
 // pair; with ctl, also the largest |v| stored into ctl[p].vmax).  VU: u is
-// 16-byte aligned with an even pitch (vector access to u).
+// 16-byte aligned with an even pitch (vector access to u).  UD: u and the
+// residual's low part of the own cells are loaded into registers at the
+// start of each step instead of being copied into shared memory one step
+// ahead (more registers per thread: for launches with few warps per SM).
 enum { UP_RR = 0, UP_ADD = 1, UP_STORE = 2 };
 
 // The streaming kernels below keep one step of every warp's inputs in flight
@@ -892,7 +895,7 @@ struct FFL {
     float4 l[2][32];
 };
 
-template <int MODE, bool VU>
+template <int MODE, bool VU, bool UD = false>
 __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue, A2<const float> ree,
                                                             A2<const float> roo, A2<float> rga, float *rgb, A2<float> vg,
                                                             float *__restrict__ rlo, double *__restrict__ u, int up,
@@ -906,8 +909,8 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
     // limit there)
     constexpr int NST = MODE == UP_STORE ? 3 : 2;
     __shared__ FFChain SC[FF_WARPS][NST];
-    __shared__ FFU SU[MODE != UP_STORE ? FF_WARPS : 1][NST];
-    __shared__ FFL SL[MODE == UP_RR ? FF_WARPS : 1][NST];
+    __shared__ FFU SU[MODE != UP_STORE && !UD ? FF_WARPS : 1][UD ? 1 : NST];
+    __shared__ FFL SL[MODE == UP_RR && !UD ? FF_WARPS : 1][UD ? 1 : NST];
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int K = FF_K;
     constexpr bool RR = MODE == UP_RR, UPD = MODE != UP_STORE;
@@ -952,7 +955,7 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
             const bool y2 = in && 2 * bb + 2 >= 1 && 2 * bb + 2 <= n, y3 = in && 2 * bb + 3 >= 1 && 2 * bb + 3 <= n;
             cp_async16(&C.g2[lane], &rg(2 * ac, y2 ? 2 * bb + 2 : 0), y2);
             cp_async16(&C.g3[lane], &rg(2 * ac, y3 ? 2 * bb + 3 : 0), y3);
-            if (UPD && own && bb >= b0) {
+            if (UPD && !UD && own && bb >= b0) {
                 const bool row0 = bb >= 1;
 #pragma unroll
                 for (int r = 0; r < 2; r++) {
@@ -1012,6 +1015,24 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
             const int yo = upd ? 2 * b : 0, xo = upd ? 2 * a0 : 0;  // pointers formed for own cells only
             double *ur0 = UPD ? u + (size_t)yo * up + xo : nullptr, *ur1 = UPD ? ur0 + up : nullptr;
             float *lr0 = RR ? rlo + (size_t)yo * gp + xo : nullptr, *lr1 = RR ? lr0 + gp : nullptr;
+            double u0[2 * K], u1[2 * K];
+            float l0[2 * K], l1[2 * K];
+            if (UD && UPD && upd) {  // rows 2b and 2b+1 of the own cells (row 0 is the ring: read, not used)
+                if (VU) {
+                    const double2 a = reinterpret_cast<const double2 *>(ur0)[0], bq = reinterpret_cast<const double2 *>(ur0)[1];
+                    const double2 c = reinterpret_cast<const double2 *>(ur1)[0], d = reinterpret_cast<const double2 *>(ur1)[1];
+                    u0[0] = a.x; u0[1] = a.y; u0[2] = bq.x; u0[3] = bq.y;
+                    u1[0] = c.x; u1[1] = c.y; u1[2] = d.x; u1[3] = d.y;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 2 * K; q++) { u0[q] = ur0[q]; u1[q] = ur1[q]; }
+                }
+                if (RR) {
+                    const float4 a = *reinterpret_cast<const float4 *>(lr0), c = *reinterpret_cast<const float4 *>(lr1);
+                    l0[0] = a.x; l0[1] = a.y; l0[2] = a.z; l0[3] = a.w;
+                    l1[0] = c.x; l1[1] = c.y; l1[2] = c.z; l1[3] = c.w;
+                }
+            }
             // ---- the chain
             const bool y_oo2 = b + 2 >= 0 && b + 2 <= nb, y_ee2 = b + 2 >= 1 && b + 2 <= nb;
             const bool y_oe1 = b + 1 >= 1 && b + 1 <= nb, y_eo1 = b + 1 >= 0 && b + 1 <= nb;
@@ -1063,15 +1084,13 @@ __global__ void __launch_bounds__(32 * FF_WARPS) k_up_ff_2d(A2<const float> blue
                 }
             }
             if (UPD && upd) {
-                double u0[2 * K], u1[2 * K];
-                float l0[2 * K], l1[2 * K];
-                {
+                if (!UD) {
                     const double2 a = SU[w][st].u[0][0][lane], bq = SU[w][st].u[0][1][lane];
                     const double2 c = SU[w][st].u[1][0][lane], d = SU[w][st].u[1][1][lane];
                     u0[0] = a.x; u0[1] = a.y; u0[2] = bq.x; u0[3] = bq.y;
                     u1[0] = c.x; u1[1] = c.y; u1[2] = d.x; u1[3] = d.y;
                 }
-                if (RR) {
+                if (RR && !UD) {
                     const float4 a = SL[w][st].l[0][lane], c = SL[w][st].l[1][lane];
                     l0[0] = a.x; l0[1] = a.y; l0[2] = a.z; l0[3] = a.w;
                     l1[0] = c.x; l1[1] = c.y; l1[2] = c.z; l1[3] = c.w;

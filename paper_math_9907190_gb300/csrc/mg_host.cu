@@ -916,12 +916,22 @@ int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStre
     const bool vu = k == 0 && c->nprob == 1 && ((uintptr_t)u % 16) == 0 && c->d.pitch % 2 == 0;
     const float c2 = (float)(2.0 * p * hk * hk), c1 = (float)(p * hk * hk), s2 = (float)(1.0 / (hk * hk));
     const int tag = k == 0 ? (int)TAG_FINEST_UP : (int)TAG_UP;
-#define MG_UPFF(MODE, VU)                                                                                          \
-    LAUNCH_B(tag, (k_up_ff_2d<MODE, VU>), grid, blk, a2<const float>(b.v[0], b), a2<const float>(r.r[0], r),     \
+#define MG_UPFF(MODE, VU, ...)                                                                                     \
+    LAUNCH_B(tag, (k_up_ff_2d<MODE, VU, ##__VA_ARGS__>), grid, blk, a2<const float>(b.v[0], b), a2<const float>(r.r[0], r),     \
              a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b, a2<float>(g.v[0], g),           \
              (float *)c->rlo, u, c->d.pitch, nb, c2, c1, s2, tb, c->part, rr ? c->ctl : vctl, done)
+    // the fused finest pair with 2..12 warps' worth of items per SM: u and the
+    // residual's low part straight into registers (as measured on GB300,
+    // mixed 1023^2 with 576 items 0.658 -> 0.611 ms; with a full wave of
+    // items, 2047^2 and up, the extra registers cost a quarter of the warps,
+    // and with at most two warps per SM, 511^2 and below, the loads' latency
+    // is no longer hidden: 0.430 -> 0.442 ms at 255^2)
+    const bool ud = rr && items > 2 * c->sms && items <= 12 * c->sms;
     if (rr) {
-        if (vu) MG_UPFF(UP_RR, true);
+        if (ud) {
+            if (vu) MG_UPFF(UP_RR, true, true);
+            else MG_UPFF(UP_RR, false, true);
+        } else if (vu) MG_UPFF(UP_RR, true);
         else MG_UPFF(UP_RR, false);
     } else if (add) {
         if (vu) MG_UPFF(UP_ADD, true);
