@@ -225,7 +225,8 @@ mg_status mg_solve_host(mg_ctx *ctx, const double *f_host, const double *u0_host
  * cycles_out, relres_out: host arrays of count entries (nullable).  Returns
  * MG_EDIVERGED if any problem diverged, else MG_ENOCONV if any did not
  * converge, else MG_OK (the per-problem outcome is in relres_out); returns
- * once every u_host[k] holds its result.  The first call allocates a second
+ * once every u_host[k] holds its result, and on an error only after every
+ * copy it issued has finished.  The first call allocates a second
  * pair of device copies (MG_ENOMEM) and two page-locked control words; with
  * DIAGMG_SOLVE_GRAPH=0 the problems run one after the other. */
 mg_status mg_solve_host_many(mg_ctx *ctx, int count, const double *const *f_host, double *const *u_host,

@@ -1925,50 +1925,58 @@ mg_status mg_solve_host_many(mg_ctx *c, int count, const double *const *f_host, 
         if (st == MG_EDIVERGED || (st == MG_ENOCONV && worst == MG_OK)) worst = st;
         return MG_OK;
     };
-    CK(cudaEventRecord(c->ev_io, s));  // the copies start after the caller's earlier work
-    CK(cudaStreamWaitEvent(io, c->ev_io, 0));
-    CK(copy_grid(c, F[0], f_host[0], cudaMemcpyHostToDevice, io));
-    CK(cudaEventRecord(c->ev_in[0], io));
-    for (int k = 0; k < count; k++) {
-        const int b = k & 1;
-        if (k + 1 < count) {  // the next input, into the buffer solve k - 1 used
-            if (k >= 1) CK(cudaStreamWaitEvent(io, c->ev_sol[b ^ 1], 0));
-            CK(copy_grid(c, F[b ^ 1], f_host[k + 1], cudaMemcpyHostToDevice, io));
-            CK(cudaEventRecord(c->ev_in[b ^ 1], io));
+    auto pipeline = [&]() -> mg_status {
+        CK(cudaEventRecord(c->ev_io, s));  // the copies start after the caller's earlier work
+        CK(cudaStreamWaitEvent(io, c->ev_io, 0));
+        CK(copy_grid(c, F[0], f_host[0], cudaMemcpyHostToDevice, io));
+        CK(cudaEventRecord(c->ev_in[0], io));
+        for (int k = 0; k < count; k++) {
+            const int b = k & 1;
+            if (k + 1 < count) {  // the next input, into the buffer solve k - 1 used
+                if (k >= 1) CK(cudaStreamWaitEvent(io, c->ev_sol[b ^ 1], 0));
+                CK(copy_grid(c, F[b ^ 1], f_host[k + 1], cudaMemcpyHostToDevice, io));
+                CK(cudaEventRecord(c->ev_in[b ^ 1], io));
+            }
+            CK(cudaStreamWaitEvent(s, c->ev_in[b], 0));
+            if (k >= 2) CK(cudaStreamWaitEvent(s, c->ev_out[b], 0));  // solve k - 2's u has left this buffer
+            if (k >= 2) {  // slot b of the control words holds solve k - 2's, read before it is reused
+                const mg_status st = collect(k - 2);
+                if (st != MG_OK) return st;
+            }
+            mg_status st;
+            if (c->rr) {  // a solve from zero: u zeroed inside the graph
+                c->zstart = true;
+                st = solve_graph(c, F[b], U[b], rtol, max_cycles, &hit[b]);
+                c->zstart = false;
+            } else {
+                CK(zero_grid(c, U[b], s));
+                st = solve_graph(c, F[b], U[b], rtol, max_cycles, &hit[b]);
+            }
+            if (st != MG_OK) return st;
+            CK(cudaGraphLaunch(hit[b]->exec, s));
+            CK(cudaMemcpyAsync(&c->hctl[b], c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+            CK(cudaEventRecord(c->ev_ctl[b], s));
+            CK(cudaEventRecord(c->ev_sol[b], s));
+            // u back once the solve and its control word have left the device: the
+            // control word's small copy shares the copy engine, and queued behind
+            // this 134 MB one it would hold the next solve back
+            CK(cudaStreamWaitEvent(io, c->ev_ctl[b], 0));
+            CK(copy_grid(c, u_host[k], U[b], cudaMemcpyDeviceToHost, io));
+            CK(cudaEventRecord(c->ev_out[b], io));
         }
-        CK(cudaStreamWaitEvent(s, c->ev_in[b], 0));
-        if (k >= 2) CK(cudaStreamWaitEvent(s, c->ev_out[b], 0));  // solve k - 2's u has left this buffer
-        if (k >= 2) {  // slot b of the control words holds solve k - 2's, read before it is reused
-            const mg_status st = collect(k - 2);
+        for (int k = std::max(0, count - 2); k < count; k++) {
+            const mg_status st = collect(k);
             if (st != MG_OK) return st;
         }
-        mg_status st;
-        if (c->rr) {  // a solve from zero: u zeroed inside the graph
-            c->zstart = true;
-            st = solve_graph(c, F[b], U[b], rtol, max_cycles, &hit[b]);
-            c->zstart = false;
-        } else {
-            CK(zero_grid(c, U[b], s));
-            st = solve_graph(c, F[b], U[b], rtol, max_cycles, &hit[b]);
-        }
-        if (st != MG_OK) return st;
-        CK(cudaGraphLaunch(hit[b]->exec, s));
-        CK(cudaMemcpyAsync(&c->hctl[b], c->ctl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-        CK(cudaEventRecord(c->ev_ctl[b], s));
-        CK(cudaEventRecord(c->ev_sol[b], s));
-        // u back once the solve and its control word have left the device: the
-        // control word's small copy shares the copy engine, and queued behind
-        // this 134 MB one it would hold the next solve back
-        CK(cudaStreamWaitEvent(io, c->ev_ctl[b], 0));
-        CK(copy_grid(c, u_host[k], U[b], cudaMemcpyDeviceToHost, io));
-        CK(cudaEventRecord(c->ev_out[b], io));
-    }
-    for (int k = std::max(0, count - 2); k < count; k++) {
-        const mg_status st = collect(k);
-        if (st != MG_OK) return st;
-    }
-    CK(cudaStreamSynchronize(io));
-    CK(cudaStreamSynchronize(s));
+        return MG_OK;
+    };
+    const mg_status st = pipeline();
+    // both streams drained on every path, an error included: no copy this call
+    // issued touches the caller's host arrays after it returns
+    const cudaError_t e_io = cudaStreamSynchronize(io), e_s = cudaStreamSynchronize(s);
+    if (st != MG_OK) return st;
+    if (e_io != cudaSuccess || e_s != cudaSuccess)
+        return cuda_fail(e_io != cudaSuccess ? e_io : e_s, "mg_solve_host_many streams");
     return worst;
 }
 
