@@ -343,8 +343,9 @@ mg_status mg_batch_status(const mg_batch *batch, int *status);
  * 255^2 to 4095^2 (within 2% of them there): the coarse thread block takes
  * pairs of green side <= 63 (FP64: 15) and triples <= 15 (FP64: 7); the
  * fused finest pair of the mixed path the longest strips that still fill the
- * device with warps (with 2-12 warps' worth of strips per SM it loads u and
- * the residual's low part straight into registers), the coarser FP32 pairs streaming kernels from 512 cells
+ * device with warps (for a single problem with 2-12 warps' worth of strips
+ * per SM it loads u and the residual's low part straight into registers),
+ * the coarser FP32 pairs streaming kernels from 512 cells
  * and tiles below, FP64 pairs 16x8 tiles from 256 cells; a context of
  * several problems (a batch's size group) the largest FP64 tiles or the
  * FP32 streaming kernels at every level. */

@@ -920,13 +920,14 @@ int launch_up_ff(mg_ctx *c, int k, int cls, double *u, const int *done, cudaStre
     LAUNCH_B(tag, (k_up_ff_2d<MODE, VU, ##__VA_ARGS__>), grid, blk, a2<const float>(b.v[0], b), a2<const float>(r.r[0], r),     \
              a2<const float>(r.r[1], r), a2<float>(g.r[0], g), (float *)c->r32b, a2<float>(g.v[0], g),           \
              (float *)c->rlo, u, c->d.pitch, nb, c2, c1, s2, tb, c->part, rr ? c->ctl : vctl, done)
-    // the fused finest pair with 2..12 warps' worth of items per SM: u and the
-    // residual's low part straight into registers (as measured on GB300,
-    // mixed 1023^2 with 576 items 0.658 -> 0.611 ms; with a full wave of
-    // items, 2047^2 and up, the extra registers cost a quarter of the warps,
-    // and with at most two warps per SM, 511^2 and below, the loads' latency
-    // is no longer hidden: 0.430 -> 0.442 ms at 255^2)
-    const bool ud = rr && items > 2 * c->sms && items <= 12 * c->sms;
+    // the fused finest pair of a single problem with 2..12 warps' worth of
+    // items per SM: u and the residual's low part straight into registers (as
+    // measured on GB300, mixed 1023^2 with 576 items 0.658 -> 0.611 ms; with a
+    // full wave of items, 2047^2 and up, the extra registers cost a quarter of
+    // the warps, and with at most two warps per SM, 511^2 and below, the
+    // loads' latency is no longer hidden: 0.430 -> 0.442 ms at 255^2).  A
+    // batch's launch covers all problems of its size, a full wave or more.
+    const bool ud = rr && c->nprob == 1 && items > 2 * c->sms && items <= 12 * c->sms;
     if (rr) {
         if (ud) {
             if (vu) MG_UPFF(UP_RR, true, true);
